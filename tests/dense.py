@@ -1,0 +1,46 @@
+"""Dense-matrix helpers for the tests: build full matrices from bands with
+numpy only, so that library routines (LAPACK through numpy/scipy) can check
+the oracle independently of its own code."""
+import numpy as np
+
+
+def dense_from_bands(bands: np.ndarray) -> np.ndarray:
+    """Full N x N matrix with band k of row i at column i + k - width//2."""
+    w, N = bands.shape
+    h = w // 2
+    A = np.zeros((N, N))
+    for i in range(N):
+        for k in range(w):
+            col = i + k - h
+            if 0 <= col < N:
+                A[i, col] = bands[k, i]
+    return A
+
+
+def second_difference(n: int) -> np.ndarray:
+    """tridiag(1, -2, 1), homogeneous Dirichlet."""
+    return np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+
+
+def periodic_tri(N: int, a: float, b: float, c: float) -> np.ndarray:
+    """Periodic tridiagonal matrix with a in the top-right and c in the
+    bottom-left corner (the constant periodic matrix of Sec. 3.3)."""
+    A = np.diag(b * np.ones(N)) + np.diag(a * np.ones(N - 1), -1) + np.diag(c * np.ones(N - 1), 1)
+    A[0, N - 1] = a
+    A[N - 1, 0] = c
+    return A
+
+
+def to_layout(X_nm: np.ndarray, layout: str) -> np.ndarray:
+    """(N, M) interleaved block to the requested storage."""
+    return np.ascontiguousarray(X_nm if layout == "interleaved" else X_nm.T)
+
+
+def from_layout(X: np.ndarray, layout: str) -> np.ndarray:
+    return X if layout == "interleaved" else X.T
+
+
+def rel_l2(x, ref) -> float:
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
