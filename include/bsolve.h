@@ -1,0 +1,130 @@
+/*
+ * bsolve: batched shared-LHS tridiagonal / pentadiagonal solves on GB300
+ * (sm_103a).  C ABI.
+ *
+ * The method is that of "Efficient Interleaved Batch Matrix Solvers for CUDA"
+ * (Gloster, Carroll, Bustamante, O Naraigh, arXiv:1909.04539): one banded
+ * LHS A (N x N) is factorised once and kept as a single copy shared by every
+ * system of the batch (Sec. 2); M right-hand sides are stored interleaved,
+ * row i of system j at B[i*M + j] (Sec. 2, Sec. 3.1); each system is solved
+ * by one forward and one backward sweep, one thread per system.
+ *
+ * Conventions for every entry point below:
+ *  - Bands are passed row-aligned as width x N doubles: band k of row i at
+ *    bands[k*N + i].  Tridiagonal (width 3, Sec. 3.1): a_i, b_i, c_i at
+ *    columns i-1, i, i+1.  Pentadiagonal (width 5, Sec. 4.1, diagonal c):
+ *    a_i .. e_i at columns i-2 .. i+2.  Entries outside the matrix are ignored.
+ *  - B, G, X, U and dbands are caller-owned DEVICE memory on the current
+ *    device.  The library never frees or keeps them.
+ *  - Layouts: BS_INTERLEAVED puts row i of system j at [i*M + j] (the
+ *    paper's layout); BS_STRIDED puts it at [j*N + i] (system-contiguous,
+ *    the second axis of a 2D ADI step).
+ *  - Every solve is enqueued on `stream` (NULL = legacy default stream) and
+ *    returns without waiting.  Argument errors are reported synchronously
+ *    and nothing is enqueued; a kernel never traps.  Sizes are row counts and
+ *    system counts, not bytes.
+ *  - A handle is immutable after bs_factor, so solves with one handle may run
+ *    concurrently on different streams.  bs_destroy must not race with them.
+ */
+#ifndef BSOLVE_H
+#define BSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* bs_stream; /* a cudaStream_t */
+
+typedef struct bs_factor_s* bs_handle; /* opaque, owned by the library */
+
+typedef enum {
+  BS_OK = 0,
+  BS_EINVAL = 1,      /* bad argument: null pointer, size, alignment, combination */
+  BS_ESINGULAR = 2,   /* zero or non-finite pivot met while factorising */
+  BS_ENOMEM = 3,      /* device allocation failed */
+  BS_ECUDA = 4,       /* a CUDA runtime call failed (see bs_last_error) */
+  BS_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
+  BS_EUNSUPPORTED = 6 /* valid request this build does not implement */
+} bs_status;
+
+typedef enum {
+  BS_F64 = 0,  /* FP64 storage, FP64 arithmetic */
+  BS_F32 = 1,  /* FP32 storage, FP32 arithmetic */
+  BS_BF16 = 2  /* BF16 storage of the input, FP32 arithmetic and output */
+} bs_dtype;
+
+typedef enum { BS_INTERLEAVED = 0, BS_STRIDED = 1 } bs_layout;
+
+/* Factorise the shared LHS once (Sec. 3.1 Thomas pre-factorisation for
+ * width 3; Sec. 4.1 A = L R for width 5) on the host in FP64, then copy the
+ * sweep coefficients (FP64 and FP32 copies) and the bands to the current
+ * device.  bands: host pointer, width x N doubles (read only, not kept).
+ * N >= 2 for width 3, N >= 4 for width 5.  No pivoting (the paper relies on
+ * diagonal dominance or symmetric positive definiteness, Sec. 4.3): a zero
+ * or non-finite pivot returns BS_ESINGULAR and *out stays NULL.
+ * Blocking (synchronous device copies).  The handle owns its device memory
+ * until bs_destroy. */
+bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out);
+
+/* Release a handle's device memory.  The caller must ensure no solve using it
+ * is still running (synchronise its streams first).  NULL is a no-op. */
+bs_status bs_destroy(bs_handle h);
+
+/* Width, N and device bytes held by a handle (any pointer may be NULL). */
+bs_status bs_handle_info(bs_handle h, int* width, int64_t* N, size_t* device_bytes);
+
+/* Bytes of shared LHS data one solve reads: width x N values of the sweep
+ * coefficients (3N tridiagonal, 5N pentadiagonal; Sec. 3.1, Sec. 4.1), for an
+ * element of elem_bytes.  Host-only arithmetic. */
+int64_t bs_lhs_bytes(int width, int64_t N, int elem_bytes);
+
+/* Solve A X = B for M systems, in place (the paper overwrites the RHS with
+ * the solution, Sec. 3.1): forward sweep then backward sweep per system
+ * (Sec. 3.1 tridiagonal, Sec. 4.1 pentadiagonal).
+ *   dtype BS_F64: B is double[N*M], FP64 arithmetic.
+ *   dtype BS_F32: B is float[N*M], FP32 arithmetic.
+ *   dtype BS_BF16: not in place -- use bs_solve_bf16.
+ * The intermediate forward-sweep values are kept in B itself between the two
+ * sweeps.  M >= 1. */
+bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64_t M,
+                   bs_stream stream);
+
+/* BF16 storage, FP32 arithmetic: reads B (bf16[N*M]), writes X (float[N*M]).
+ * X also holds the forward-sweep intermediates.  B and X must not overlap. */
+bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, int64_t M,
+                        bs_stream stream);
+
+/* Adjoint solve: G <- A^{-T} G, in place, reusing the same factorisation
+ * (A^T = R^T L^T, a forward sweep with R^T then a backward sweep with L^T).
+ * If X (the primal solution A^{-1} B, same dtype and layout as G) and dbands
+ * are both non-NULL, also writes the gradient of a scalar loss with respect
+ * to the band entries, given dL/dX = G on entry:
+ *   dbands[k*N + i] = -sum_j (A^{-T} G)[i, j] * X[i + k - width/2, j]
+ * (0 for entries outside the matrix), as double[width*N] in device memory,
+ * reduced over the batch in a fixed order (deterministic, no atomics).
+ * dtype BS_F64 or BS_F32.  Band gradients are accumulated in FP64. */
+bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M,
+                           const void* X, double* dbands, bs_stream stream);
+
+/* Launch tuning knobs (process-wide; 0 restores the default).
+ *  BS_OPT_INFLIGHT_BYTES: upper bound on the bytes of forward-sweep values
+ *    that all systems in flight keep between their two sweeps (default: half
+ *    of the device's L2), which sets how many systems run at once.
+ *  BS_OPT_BLOCKS_PER_SM: resident CTAs per SM the persistent grids aim for
+ *    (default 8). */
+typedef enum { BS_OPT_INFLIGHT_BYTES = 0, BS_OPT_BLOCKS_PER_SM = 1, BS_OPT_COUNT = 2 } bs_option;
+bs_status bs_set_option(int opt, int64_t value);
+
+/* Last error message of the calling thread (static storage, never NULL). */
+const char* bs_last_error(void);
+const char* bs_strerror(bs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSOLVE_H */

@@ -1,0 +1,7 @@
+"""GB300-native batched shared-LHS tridiagonal/pentadiagonal solver
+(arXiv:1909.04539).  The compute path is the CUDA library ``libbsolve.so``
+behind the C ABI in ``include/bsolve.h``; this package only marshals torch
+tensors into it."""
+from .api import (Factor, SolveFn, solve, solve_adjoint, solve_bf16,  # noqa: F401
+                  set_option, lhs_bytes)
+from ._lib import BsolveError  # noqa: F401

@@ -1,0 +1,55 @@
+"""ctypes binding of libbsolve.so: symbol signatures only.  The library must
+have been built (``paper_1909_04539_gb300.build.build()``); there is no
+fallback implementation."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libbsolve.so")
+
+_LIB = None
+
+i32, i64, vp, dp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); kept in the order of include/*.h
+SIGNATURES = {
+    "bs_factor": (i32, [dp, i32, i64, ctypes.POINTER(vp)]),
+    "bs_destroy": (i32, [vp]),
+    "bs_handle_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)]),
+    "bs_lhs_bytes": (i64, [i32, i64, i32]),
+    "bs_solve": (i32, [vp, vp, i32, i32, i64, vp]),
+    "bs_solve_bf16": (i32, [vp, vp, vp, i32, i64, vp]),
+    "bs_solve_adjoint": (i32, [vp, vp, i32, i32, i64, vp, vp, vp]),
+    "bs_set_option": (i32, [i32, i64]),
+    "bs_last_error": (ctypes.c_char_p, []),
+    "bs_strerror": (ctypes.c_char_p, [i32]),
+}
+
+
+class BsolveError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libbsolve.so is not built ({LIB_PATH} missing); run "
+                "paper_1909_04539_gb300.build.build() -- there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status: int, fn: str) -> None:
+    if status != 0:
+        L = lib()
+        raise BsolveError(status, f"{fn}: {L.bs_strerror(status).decode()}: {L.bs_last_error().decode()}")

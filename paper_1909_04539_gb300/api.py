@@ -1,0 +1,175 @@
+"""Torch-facing wrappers of the C ABI (argument marshalling only).
+
+Layouts: an interleaved batch is a contiguous tensor of shape (N, M) (row i
+of system j at [i, j], the paper's B[i*M + j]); a strided batch has shape
+(M, N) (system-contiguous).  Every call is enqueued on the current torch
+CUDA stream unless ``stream`` is given.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import check, lib
+
+_DTYPE = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
+_LAYOUT = {"interleaved": 0, "strided": 1}
+
+OPT_INFLIGHT_BYTES = 0
+OPT_BLOCKS_PER_SM = 1
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def set_option(opt: int, value: int) -> None:
+    check(lib().bs_set_option(int(opt), int(value)), "bs_set_option")
+
+
+def lhs_bytes(width: int, N: int, elem_bytes: int) -> int:
+    return int(lib().bs_lhs_bytes(width, N, elem_bytes))
+
+
+class Factor:
+    """One factorised shared LHS resident on a device (``bs_factor``).
+
+    ``bands``: (width, N) float64 array-like, width 3 (a, b, c) or 5
+    (a, b, c, d, e), row-aligned as in the paper."""
+
+    def __init__(self, bands, device=None):
+        if isinstance(bands, torch.Tensor):
+            bands = bands.detach().to("cpu", torch.float64).numpy()
+        b = np.ascontiguousarray(np.asarray(bands, dtype=np.float64))
+        if b.ndim != 2:
+            raise ValueError("bands must be a (width, N) array")
+        self.width, self.N = int(b.shape[0]), int(b.shape[1])
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("Factor lives on a CUDA device")
+        self.device = dev
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            check(lib().bs_factor(b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.width, self.N,
+                                  ctypes.byref(h)), "bs_factor")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("Factor has been closed")
+        return self._h
+
+    @property
+    def device_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(lib().bs_handle_info(self.handle, None, None, ctypes.byref(n)), "bs_handle_info")
+        return int(n.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            lib().bs_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch(f: Factor, T: torch.Tensor, layout: str, what: str) -> int:
+    if layout not in _LAYOUT:
+        raise ValueError(f"layout must be one of {list(_LAYOUT)}")
+    if not T.is_cuda or T.device != f.device:
+        raise ValueError(f"{what} must be a CUDA tensor on {f.device}")
+    if not T.is_contiguous() or T.dim() != 2:
+        raise ValueError(f"{what} must be a contiguous 2-D tensor")
+    N, M = (T.shape[0], T.shape[1]) if layout == "interleaved" else (T.shape[1], T.shape[0])
+    if N != f.N:
+        raise ValueError(f"{what} has {N} rows, the factor has N={f.N}")
+    return int(M)
+
+
+def solve(f: Factor, B: torch.Tensor, layout: str = "interleaved", stream=None) -> torch.Tensor:
+    """In-place solve A X = B (float64: FP64 arithmetic; float32: FP32)."""
+    M = _batch(f, B, layout, "B")
+    if B.dtype not in (torch.float64, torch.float32):
+        raise ValueError("B must be float64 or float32 (bfloat16: solve_bf16)")
+    check(lib().bs_solve(f.handle, ctypes.c_void_p(B.data_ptr()), _DTYPE[B.dtype], _LAYOUT[layout], M,
+                         _stream(stream)), "bs_solve")
+    return B
+
+
+def solve_bf16(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, layout: str = "interleaved",
+               stream=None) -> torch.Tensor:
+    """BF16-stored B, FP32 arithmetic, FP32 solution X (returned)."""
+    M = _batch(f, B, layout, "B")
+    if B.dtype != torch.bfloat16:
+        raise ValueError("B must be bfloat16")
+    if X is None:
+        X = torch.empty(B.shape, dtype=torch.float32, device=B.device)
+    _batch(f, X, layout, "X")
+    if X.dtype != torch.float32 or X.shape != B.shape:
+        raise ValueError("X must be float32 with B's shape")
+    check(lib().bs_solve_bf16(f.handle, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                              _LAYOUT[layout], M, _stream(stream)), "bs_solve_bf16")
+    return X
+
+
+def solve_adjoint(f: Factor, G: torch.Tensor, layout: str = "interleaved", X: torch.Tensor | None = None,
+                  dbands: torch.Tensor | None = None, stream=None):
+    """In-place G <- A^{-T} G.  With X (the primal solution) also returns the
+    band gradient -(A^{-T} G) X^T on the bands, shape (width, N) float64."""
+    M = _batch(f, G, layout, "G")
+    if G.dtype not in (torch.float64, torch.float32):
+        raise ValueError("G must be float64 or float32")
+    xp = dp = None
+    if X is not None:
+        _batch(f, X, layout, "X")
+        if X.dtype != G.dtype or X.shape != G.shape:
+            raise ValueError("X must match G in dtype and shape")
+        if dbands is None:
+            dbands = torch.empty((f.width, f.N), dtype=torch.float64, device=G.device)
+        if dbands.dtype != torch.float64 or not dbands.is_contiguous() or dbands.numel() != f.width * f.N:
+            raise ValueError("dbands must be a contiguous float64 (width, N) tensor")
+        xp, dp = ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(dbands.data_ptr())
+    check(lib().bs_solve_adjoint(f.handle, ctypes.c_void_p(G.data_ptr()), _DTYPE[G.dtype], _LAYOUT[layout], M,
+                                 xp, dp, _stream(stream)), "bs_solve_adjoint")
+    return (G, dbands) if X is not None else G
+
+
+class SolveFn(torch.autograd.Function):
+    """X = A^{-1} B with gradients for B and for the band entries of A.
+
+    ``SolveFn.apply(bands, B, factor=None, layout="interleaved")``: bands is a
+    (width, N) float64 tensor (its values define A; pass ``factor`` to reuse
+    an existing factorisation of the same bands).  The backward pass is the
+    hand-written adjoint: one transposed solve with the same factors plus the
+    band-gradient reduction over the batch."""
+
+    @staticmethod
+    def forward(ctx, bands, B, factor=None, layout="interleaved"):
+        f = factor if factor is not None else Factor(bands.detach(), device=B.device)
+        X = solve(f, B.detach().clone().contiguous(), layout)
+        ctx.factor = f
+        ctx.layout = layout
+        ctx.bands_device = bands.device
+        ctx.save_for_backward(X)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        (X,) = ctx.saved_tensors
+        GB = gX.detach().to(X.dtype).contiguous().clone()
+        need_bands = ctx.needs_input_grad[0]
+        if need_bands:
+            GB, db = solve_adjoint(ctx.factor, GB, ctx.layout, X=X)
+            db = db.to(ctx.bands_device)
+        else:
+            solve_adjoint(ctx.factor, GB, ctx.layout)
+            db = None
+        return db, (GB if ctx.needs_input_grad[1] else None), None, None

@@ -1,0 +1,312 @@
+// Host side of the library: one-off FP64 factorisation of the shared LHS,
+// handle lifetime, error reporting.
+//
+// The factorisation is done once on the host in FP64, as in the paper
+// ("pre-factorisation step for the single LHS performed on the CPU", Sec. 2),
+// and turned into the per-row sweep coefficients the kernels read.  Divisions
+// by pivots are replaced by stored reciprocals so the sweeps contain no
+// divides; every coefficient is a plain FP64 expression of the paper's
+// factors, rounded once more to FP32 for the reduced-precision sweeps.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace bs {
+
+static thread_local std::string g_last_error = "no error";
+static std::mutex g_handles_mu;
+static std::set<bs_handle> g_handles;
+
+bs_status set_error(bs_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+bs_status cuda_error(cudaError_t e, const char* what) {
+  return set_error(BS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_handle(bs_handle h) {
+  std::lock_guard<std::mutex> lk(g_handles_mu);
+  return h != nullptr && g_handles.count(h) != 0;
+}
+
+const DeviceInfo& device_info() {
+  static DeviceInfo info[64];
+  static bool have[64] = {false};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[dev]) {
+    DeviceInfo d{};
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev);
+    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (d.sms <= 0) d.sms = 1;
+    info[dev] = d;
+    have[dev] = true;
+  }
+  return info[dev];
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+namespace {
+
+// Host copies of one plan before upload: C_COUNT arrays of N.
+struct HostPlan {
+  int bw = 1;
+  bool fwd_scale = false, bwd_scale = false;
+  std::vector<double> c;
+};
+
+bool bad(double v) { return v == 0.0 || !std::isfinite(v); }
+
+// Thomas pre-factorisation (Sec. 3.1): pivots p_i = b_i - a_i chat_{i-1}
+// (p_1 = b_1), chat_i = c_i / p_i, with c_N taken as 0.  Returns the row of
+// the first bad pivot (1-based) or 0.
+int64_t tri_factor(const double* a, const double* b, const double* c, int64_t N,
+                   std::vector<double>& r, std::vector<double>& chat) {
+  r.assign(N, 0.0);
+  chat.assign(N, 0.0);
+  for (int64_t i = 0; i < N; i++) {
+    const double p = (i == 0) ? b[0] : b[i] - a[i] * chat[i - 1];
+    if (bad(p)) return i + 1;
+    r[i] = 1.0 / p;
+    chat[i] = (i + 1 < N) ? c[i] * r[i] : 0.0;
+  }
+  return 0;
+}
+
+// Pentadiagonal A = L R (Sec. 4.1), written as one loop over rows with the
+// entries that fall outside the matrix read as zero; this reproduces the
+// paper's special-cased first, second, (N-1)-th and N-th rows.
+int64_t penta_factor(const double* const* bd, int64_t N, std::vector<double>& al,
+                     std::vector<double>& be, std::vector<double>& ga, std::vector<double>& de,
+                     std::vector<double>& ep) {
+  al.assign(N, 0.0);
+  be.assign(N, 0.0);
+  ga.assign(N, 0.0);
+  de.assign(N, 0.0);
+  ep.assign(N, 0.0);
+  auto at = [&](int k, int64_t i) { return bd[k][i]; };
+  for (int64_t i = 0; i < N; i++) {
+    const double a = (i >= 2) ? at(0, i) : 0.0;
+    const double b = (i >= 1) ? at(1, i) : 0.0;
+    const double c = at(2, i);
+    const double d = (i + 1 < N) ? at(3, i) : 0.0;
+    const double e = (i + 2 < N) ? at(4, i) : 0.0;
+    const double ga2 = (i >= 2) ? ga[i - 2] : 0.0, de2 = (i >= 2) ? de[i - 2] : 0.0;
+    const double ga1 = (i >= 1) ? ga[i - 1] : 0.0, de1 = (i >= 1) ? de[i - 1] : 0.0;
+    ep[i] = a;
+    be[i] = b - a * ga2;
+    al[i] = c - a * de2 - be[i] * ga1;
+    if (bad(al[i])) return i + 1;
+    ga[i] = (d - be[i] * de1) / al[i];
+    de[i] = e / al[i];
+  }
+  return 0;
+}
+
+void free_handle(bs_handle h) {
+  if (!h) return;
+  for (auto& p : h->plan) {
+    if (p.c64) cudaFree(p.c64);
+    if (p.c32) cudaFree(p.c32);
+  }
+  if (h->bands64) cudaFree(h->bands64);
+  if (h->bands_hi) cudaFree(h->bands_hi);
+  if (h->bands_lo) cudaFree(h->bands_lo);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bs_last_error(void) { return g_last_error.c_str(); }
+
+const char* bs_strerror(bs_status s) {
+  switch (s) {
+    case BS_OK: return "ok";
+    case BS_EINVAL: return "invalid argument";
+    case BS_ESINGULAR: return "zero or non-finite pivot (matrix needs pivoting or is singular)";
+    case BS_ENOMEM: return "device allocation failed";
+    case BS_ECUDA: return "CUDA runtime error";
+    case BS_ETIMEOUT: return "bounded device wait timed out";
+    case BS_EUNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown status";
+}
+
+int64_t bs_lhs_bytes(int width, int64_t N, int elem_bytes) {
+  if ((width != 3 && width != 5) || N < 0 || elem_bytes <= 0) return -1;
+  return (int64_t)width * N * elem_bytes;
+}
+
+bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
+  if (!out) return set_error(BS_EINVAL, "bs_factor: out is NULL");
+  *out = nullptr;
+  if (!bands) return set_error(BS_EINVAL, "bs_factor: bands is NULL");
+  if (width != 3 && width != 5) return set_error(BS_EINVAL, "bs_factor: width must be 3 or 5");
+  if ((width == 3 && N < 2) || (width == 5 && N < 4))
+    return set_error(BS_EINVAL, "bs_factor: N must be >= 2 (tri) or >= 4 (penta)");
+  if (N > (int64_t)1 << 28) return set_error(BS_EINVAL, "bs_factor: N too large");
+
+  const double* bd[5];
+  for (int k = 0; k < width; k++) bd[k] = bands + (size_t)k * N;
+
+  HostPlan hp[2];
+  for (auto& p : hp) p.c.assign((size_t)C_COUNT * N, 0.0);
+  auto C = [&](HostPlan& p, int k, int64_t i) -> double& { return p.c[(size_t)k * N + i]; };
+
+  if (width == 3) {
+    std::vector<double> r, chat;
+    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat);
+    if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
+    // primal: dhat_i = r_i d_i - (a_i r_i) dhat_{i-1};  x_i = dhat_i - chat_i x_{i+1}
+    hp[0].bw = 1;
+    hp[0].fwd_scale = true;
+    hp[0].bwd_scale = false;
+    for (int64_t i = 0; i < N; i++) {
+      C(hp[0], C_S, i) = r[i];
+      C(hp[0], C_L1, i) = (i > 0) ? bd[0][i] * r[i] : 0.0;
+      C(hp[0], C_T, i) = 1.0;
+      C(hp[0], C_U1, i) = chat[i];
+    }
+    // adjoint, A^T = U^T L^T with L = (p_i diag, a_i sub), U = (1, chat_i super):
+    // z_i = g_i - chat_{i-1} z_{i-1};  y_i = r_i z_i - (a_{i+1} r_i) y_{i+1}
+    hp[1].bw = 1;
+    hp[1].fwd_scale = false;
+    hp[1].bwd_scale = true;
+    for (int64_t i = 0; i < N; i++) {
+      C(hp[1], C_S, i) = 1.0;
+      C(hp[1], C_L1, i) = (i > 0) ? chat[i - 1] : 0.0;
+      C(hp[1], C_T, i) = r[i];
+      C(hp[1], C_U1, i) = (i + 1 < N) ? bd[0][i + 1] * r[i] : 0.0;
+    }
+  } else {
+    std::vector<double> al, be, ga, de, ep;
+    const int64_t bad_row = penta_factor(bd, N, al, be, ga, de, ep);
+    if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
+    // primal: g_i = f_i/al_i - (ep_i/al_i) g_{i-2} - (be_i/al_i) g_{i-1};
+    //         x_i = g_i - ga_i x_{i+1} - de_i x_{i+2}
+    hp[0].bw = 2;
+    hp[0].fwd_scale = true;
+    hp[0].bwd_scale = false;
+    for (int64_t i = 0; i < N; i++) {
+      const double ia = 1.0 / al[i];
+      C(hp[0], C_S, i) = ia;
+      C(hp[0], C_L1, i) = (i >= 1) ? be[i] * ia : 0.0;
+      C(hp[0], C_L2, i) = (i >= 2) ? ep[i] * ia : 0.0;
+      C(hp[0], C_T, i) = 1.0;
+      C(hp[0], C_U1, i) = (i + 1 < N) ? ga[i] : 0.0;
+      C(hp[0], C_U2, i) = (i + 2 < N) ? de[i] : 0.0;
+    }
+    // adjoint, A^T = R^T L^T:
+    // z_i = g_i - ga_{i-1} z_{i-1} - de_{i-2} z_{i-2};
+    // y_i = z_i/al_i - (be_{i+1}/al_i) y_{i+1} - (ep_{i+2}/al_i) y_{i+2}
+    hp[1].bw = 2;
+    hp[1].fwd_scale = false;
+    hp[1].bwd_scale = true;
+    for (int64_t i = 0; i < N; i++) {
+      const double ia = 1.0 / al[i];
+      C(hp[1], C_S, i) = 1.0;
+      C(hp[1], C_L1, i) = (i >= 1) ? ga[i - 1] : 0.0;
+      C(hp[1], C_L2, i) = (i >= 2) ? de[i - 2] : 0.0;
+      C(hp[1], C_T, i) = ia;
+      C(hp[1], C_U1, i) = (i + 1 < N) ? be[i + 1] * ia : 0.0;
+      C(hp[1], C_U2, i) = (i + 2 < N) ? ep[i + 2] * ia : 0.0;
+    }
+  }
+
+  // Bands with the outside entries zeroed, and their FP32 hi/lo split.
+  std::vector<double> b64((size_t)width * N, 0.0);
+  std::vector<float> bhi((size_t)width * N), blo((size_t)width * N);
+  const int h = width / 2;
+  for (int k = 0; k < width; k++)
+    for (int64_t i = 0; i < N; i++) {
+      const int64_t col = i + k - h;
+      const double v = (col >= 0 && col < N) ? bd[k][i] : 0.0;
+      b64[(size_t)k * N + i] = v;
+      const float hi = (float)v;
+      bhi[(size_t)k * N + i] = hi;
+      blo[(size_t)k * N + i] = (float)(v - (double)hi);
+    }
+
+  bs_handle hd = new (std::nothrow) bs_factor_s();
+  if (!hd) return set_error(BS_ENOMEM, "bs_factor: host allocation failed");
+  std::memset(hd, 0, sizeof(*hd));
+  hd->width = width;
+  hd->N = N;
+  cudaGetDevice(&hd->device);
+  size_t bytes = 0;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 2 && e == cudaSuccess; p++) {
+    SweepPlan& sp = hd->plan[p];
+    sp.bw = hp[p].bw;
+    sp.fwd_scale = hp[p].fwd_scale;
+    sp.bwd_scale = hp[p].bwd_scale;
+    std::vector<float> c32(hp[p].c.size());
+    for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp[p].c[q];
+    e = cudaMalloc(&sp.c64, sizeof(double) * hp[p].c.size());
+    if (e == cudaSuccess) e = cudaMalloc(&sp.c32, sizeof(float) * c32.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sp.c64, hp[p].c.data(), sizeof(double) * hp[p].c.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
+    bytes += (sizeof(double) + sizeof(float)) * hp[p].c.size();
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands64, sizeof(double) * b64.size());
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_hi, sizeof(float) * bhi.size());
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_lo, sizeof(float) * blo.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands64, b64.data(), sizeof(double) * b64.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands_hi, bhi.data(), sizeof(float) * bhi.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands_lo, blo.data(), sizeof(float) * blo.size(), cudaMemcpyHostToDevice);
+  bytes += (sizeof(double) + 2 * sizeof(float)) * b64.size();
+  if (e != cudaSuccess) {
+    free_handle(hd);
+    if (e == cudaErrorMemoryAllocation) return set_error(BS_ENOMEM, "bs_factor: cudaMalloc failed");
+    return cuda_error(e, "bs_factor");
+  }
+  hd->device_bytes = bytes;
+  {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    g_handles.insert(hd);
+  }
+  *out = hd;
+  return BS_OK;
+}
+
+bs_status bs_destroy(bs_handle h) {
+  if (!h) return BS_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    if (!g_handles.erase(h)) return set_error(BS_EINVAL, "bs_destroy: unknown handle");
+  }
+  free_handle(h);
+  return BS_OK;
+}
+
+bs_status bs_handle_info(bs_handle h, int* width, int64_t* N, size_t* device_bytes) {
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_handle_info: unknown handle");
+  if (width) *width = h->width;
+  if (N) *N = h->N;
+  if (device_bytes) *device_bytes = h->device_bytes;
+  return BS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bsolve.h"
+
+namespace bs {
+
+// Coefficients of one sweep pair, each an array of N values.  Every solve of
+// the library (primal and adjoint, tri and penta) has the form
+//   forward : w_i = s_i f_i - l1_i w_{i-1} - l2_i w_{i-2}          (i = 0..N-1)
+//   backward: x_i = t_i w_i - u1_i x_{i+1} - u2_i x_{i+2}          (i = N-1..0)
+// with s == 1 or t == 1 where the flags say so, l2 == u2 == 0 for width 3,
+// and every coefficient that would reach outside the matrix stored as 0.
+enum { C_S = 0, C_L1, C_L2, C_T, C_U1, C_U2, C_COUNT };
+
+template <typename C>
+struct Coefs {
+  const C* s;
+  const C* l1;
+  const C* l2;
+  const C* t;
+  const C* u1;
+  const C* u2;
+};
+
+struct SweepPlan {
+  int bw;          // band half-width: 1 (tri) or 2 (penta)
+  bool fwd_scale;  // s present
+  bool bwd_scale;  // t present
+  double* c64;     // device, C_COUNT * N
+  float* c32;      // device, C_COUNT * N
+};
+
+template <typename C>
+inline Coefs<C> coefs_of(const C* base, int64_t N) {
+  return Coefs<C>{base + C_S * N, base + C_L1 * N, base + C_L2 * N,
+                  base + C_T * N, base + C_U1 * N, base + C_U2 * N};
+}
+
+}  // namespace bs
+
+struct bs_factor_s {
+  int width;
+  int64_t N;
+  int device;
+  bs::SweepPlan plan[2];   // [0] primal A^{-1}, [1] adjoint A^{-T}
+  double* bands64;         // device, width * N, entries outside the matrix zeroed
+  float* bands_hi;         // device, width * N: FP32 rounding of the bands
+  float* bands_lo;         // device, width * N: FP32 rounding of (band - hi)
+  size_t device_bytes;
+};
+
+namespace bs {
+
+bs_status set_error(bs_status s, const std::string& msg);
+bs_status cuda_error(cudaError_t e, const char* what);
+bool valid_handle(bs_handle h);
+
+struct DeviceInfo {
+  int sms;
+  int l2_bytes;
+  int smem_optin;
+};
+const DeviceInfo& device_info();
+
+// Launchers (sweep.cu)
+bs_status launch_sweep(const SweepPlan& p, int64_t N, const void* in, void* out, bs_dtype in_t,
+                       bs_dtype out_t, bs_layout layout, int64_t M, cudaStream_t st);
+bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout,
+                           int64_t M, double* dbands, cudaStream_t st);
+
+}  // namespace bs

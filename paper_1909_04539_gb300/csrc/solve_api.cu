@@ -1,0 +1,124 @@
+// C-ABI entry points of the solves and the launch-shape policy.
+#include <climits>
+#include <string>
+
+#include "sweep_kernels.cuh"
+
+namespace bs {
+
+cudaError_t sweep_f64(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
+cudaError_t sweep_f32(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
+cudaError_t sweep_bf16(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
+
+static int64_t g_opt[BS_OPT_COUNT] = {0};
+
+int64_t option(int o) { return (o >= 0 && o < BS_OPT_COUNT) ? g_opt[o] : 0; }
+
+LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
+                        int per_thread_systems, bool strided, int blocks_per_sm) {
+  const DeviceInfo& d = device_info();
+  LaunchShape sh{};
+  const size_t coef_bytes = (size_t)(1 + 2 * bw) * N * coef_elem;
+  const size_t tiles = strided ? (size_t)(kSweepThreads / 32) * kStRows * kStPad * coef_elem : 0;
+  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
+  sh.smem_coefs = coef_bytes + tiles <= limit;
+  sh.smem = sh.smem_coefs ? coef_bytes : 0;
+  const int64_t blocks_needed = (threads_needed + kSweepThreads - 1) / kSweepThreads;
+  const size_t per_block_smem = sh.smem + tiles + 1024;
+  int by_smem = (int)((228 * 1024) / per_block_smem);
+  if (blocks_per_sm <= 0) blocks_per_sm = (int)(option(BS_OPT_BLOCKS_PER_SM) > 0 ? option(BS_OPT_BLOCKS_PER_SM) : 8);
+  int per_sm = by_smem < blocks_per_sm ? by_smem : blocks_per_sm;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)d.sms * per_sm;
+  // Bound the forward values in flight: each thread keeps N rows of its
+  // systems between the sweeps.
+  int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
+  if (budget <= 0) budget = (int64_t)d.l2_bytes / 2;
+  const int64_t per_block = (int64_t)kSweepThreads * per_thread_systems * N * (int64_t)spill_elem;
+  int64_t cap = per_block > 0 ? budget / per_block : grid;
+  if (cap < d.sms) cap = d.sms;
+  if (grid > cap) grid = cap;
+  if (grid > blocks_needed) grid = blocks_needed;
+  if (grid < 1) grid = 1;
+  sh.grid = (int)grid;
+  return sh;
+}
+
+static bs_status check_common(bs_handle h, const void* B, bs_layout layout, int64_t M, const char* fn) {
+  if (!valid_handle(h)) return set_error(BS_EINVAL, std::string(fn) + ": unknown handle");
+  if (!B) return set_error(BS_EINVAL, std::string(fn) + ": null data pointer");
+  if (M < 1) return set_error(BS_EINVAL, std::string(fn) + ": M must be >= 1");
+  if (layout != BS_INTERLEAVED && layout != BS_STRIDED)
+    return set_error(BS_EINVAL, std::string(fn) + ": bad layout");
+  if (M > INT64_MAX / 16 / h->N) return set_error(BS_EINVAL, std::string(fn) + ": N*M too large");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device)
+    return set_error(BS_EINVAL, std::string(fn) + ": handle belongs to device " + std::to_string(h->device) +
+                                    ", current device is " + std::to_string(dev));
+  return BS_OK;
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+bs_status bs_set_option(int opt, int64_t value) {
+  if (opt < 0 || opt >= BS_OPT_COUNT) return set_error(BS_EINVAL, "bs_set_option: unknown option");
+  if (value < 0) return set_error(BS_EINVAL, "bs_set_option: negative value");
+  g_opt[opt] = value;
+  return BS_OK;
+}
+
+bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64_t M, bs_stream stream) {
+  bs_status s = check_common(h, B, layout, M, "bs_solve");
+  if (s != BS_OK) return s;
+  cudaError_t e;
+  const int N = (int)h->N;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == BS_F64)
+    e = sweep_f64(h->plan[0], false, N, B, B, layout, M, st);
+  else if (dtype == BS_F32)
+    e = sweep_f32(h->plan[0], false, N, B, B, layout, M, st);
+  else
+    return set_error(BS_EINVAL, "bs_solve: dtype must be BS_F64 or BS_F32 (BF16 input: bs_solve_bf16)");
+  if (e != cudaSuccess) return cuda_error(e, "bs_solve launch");
+  return BS_OK;
+}
+
+bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, int64_t M, bs_stream stream) {
+  bs_status s = check_common(h, B, layout, M, "bs_solve_bf16");
+  if (s != BS_OK) return s;
+  if (!X) return set_error(BS_EINVAL, "bs_solve_bf16: X is NULL");
+  const char* b0 = static_cast<const char*>(B);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  const size_t nm = (size_t)h->N * (size_t)M;
+  if (b0 < x0 + nm * 4 && x0 < b0 + nm * 2) return set_error(BS_EINVAL, "bs_solve_bf16: B and X overlap");
+  cudaError_t e = sweep_bf16(h->plan[0], false, (int)h->N, B, X, layout, M, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "bs_solve_bf16 launch");
+  return BS_OK;
+}
+
+bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M, const void* X,
+                           double* dbands, bs_stream stream) {
+  bs_status s = check_common(h, G, layout, M, "bs_solve_adjoint");
+  if (s != BS_OK) return s;
+  if ((X == nullptr) != (dbands == nullptr))
+    return set_error(BS_EINVAL, "bs_solve_adjoint: X and dbands must both be given or both be NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  const int N = (int)h->N;
+  if (dtype == BS_F64)
+    e = sweep_f64(h->plan[1], true, N, G, G, layout, M, st);
+  else if (dtype == BS_F32)
+    e = sweep_f32(h->plan[1], true, N, G, G, layout, M, st);
+  else
+    return set_error(BS_EINVAL, "bs_solve_adjoint: dtype must be BS_F64 or BS_F32");
+  if (e != cudaSuccess) return cuda_error(e, "bs_solve_adjoint launch");
+  if (X) return launch_band_grad(h, G, X, dtype, layout, M, dbands, st);
+  return BS_OK;
+}
+
+}  // extern "C"

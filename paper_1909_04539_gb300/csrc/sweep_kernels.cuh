@@ -1,0 +1,377 @@
+// Batched shared-LHS sweep kernels (sm_103a).
+//
+// One thread owns V neighbouring systems (V = one 128-bit load of the input
+// type, or 1 for ragged M) and runs, for each of them, the forward sweep over
+// rows 0..N-1 and then the backward sweep over rows N-1..0 (Sec. 2: "each
+// thread handles a particular system ... forward sweep followed by a backward
+// sweep").  The LHS coefficients are one shared copy (Sec. 2, Fig. 1), staged
+// once per CTA into shared memory and read as warp-wide broadcasts.  The
+// forward-sweep values are kept in the output buffer between the sweeps, as
+// the paper overwrites the RHS in place (Sec. 3.1); the launcher bounds the
+// number of systems in flight so that these values are still in L2 when the
+// backward sweep reads them back.
+//
+// Both the primal solve (A^{-1}) and the adjoint solve (A^{-T}) of both band
+// widths use the same recurrence pair
+//   forward : w_i = s_i f_i - l1_i w_{i-1} - l2_i w_{i-2}
+//   backward: x_i = t_i w_i - u1_i x_{i+1} - u2_i x_{i+2}
+// where the primal has t == 1 and the adjoint s == 1 (ADJ).  Each step's
+// dependency on the previous row goes through a single FMA.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace bs {
+
+constexpr int kSweepThreads = 128;
+
+// ------------------------------------------------------------------ I/O
+
+template <typename S, typename C, int V>
+struct IO;
+
+template <>
+struct IO<double, double, 2> {
+  static __device__ __forceinline__ void load(const double* p, double (&o)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <>
+struct IO<double, double, 1> {
+  static __device__ __forceinline__ void load(const double* p, double (&o)[1]) { o[0] = *p; }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[1]) { *p = v[0]; }
+};
+template <>
+struct IO<float, float, 4> {
+  static __device__ __forceinline__ void load(const float* p, float (&o)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct IO<float, float, 1> {
+  static __device__ __forceinline__ void load(const float* p, float (&o)[1]) { o[0] = *p; }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[1]) { *p = v[0]; }
+};
+// bf16 storage is widened exactly to FP32 (bf16 is the top half of an FP32).
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t h) { return __uint_as_float(h << 16); }
+template <>
+struct IO<__nv_bfloat16, float, 4> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    o[0] = bf16_bits_to_float(t.x & 0xffffu);
+    o[1] = bf16_bits_to_float(t.x >> 16);
+    o[2] = bf16_bits_to_float(t.y & 0xffffu);
+    o[3] = bf16_bits_to_float(t.y >> 16);
+  }
+};
+template <>
+struct IO<__nv_bfloat16, float, 1> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float (&o)[1]) {
+    o[0] = bf16_bits_to_float(*reinterpret_cast<const unsigned short*>(p));
+  }
+};
+
+// ------------------------------------------------------- coefficient staging
+
+// Copies the coefficient arrays a sweep of kind (BW, ADJ) uses into shared
+// memory (when SMEM) and returns pointers to wherever they live.
+template <int BW, bool ADJ, bool SMEM, typename C>
+__device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
+  if (SMEM) {
+    int off = 0;
+    auto stage = [&](const C*& p) {
+      C* dst = sm + off;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = p[i];
+      p = dst;
+      off += N;
+    };
+    if (!ADJ) stage(cf.s);
+    stage(cf.l1);
+    if (BW == 2) stage(cf.l2);
+    if (ADJ) stage(cf.t);
+    stage(cf.u1);
+    if (BW == 2) stage(cf.u2);
+    __syncthreads();
+  }
+  return cf;
+}
+
+template <int BW>
+__host__ __device__ constexpr int coef_arrays() {
+  return 1 + 2 * BW;  // scale + BW lower + BW upper
+}
+
+// One forward step for V systems at row i (f holds the input on entry and
+// the forward value on exit).
+template <int BW, bool ADJ, typename C, int V>
+__device__ __forceinline__ void fwd_step(const Coefs<C>& cf, int i, C (&f)[V], C (&w1)[V], C (&w2)[V]) {
+  const C l1 = cf.l1[i];
+  C s = C(1), l2 = C(0);
+  if (!ADJ) s = cf.s[i];
+  if (BW == 2) l2 = cf.l2[i];
+#pragma unroll
+  for (int v = 0; v < V; v++) {
+    C w = ADJ ? f[v] : f[v] * s;
+    if (BW == 2) w = fma(-l2, w2[v], w);
+    w = fma(-l1, w1[v], w);
+    if (BW == 2) w2[v] = w1[v];
+    w1[v] = w;
+    f[v] = w;
+  }
+}
+
+// One backward step for V systems at row i (f holds w_i on entry, x_i on exit).
+template <int BW, bool ADJ, typename C, int V>
+__device__ __forceinline__ void bwd_step(const Coefs<C>& cf, int i, C (&f)[V], C (&x1)[V], C (&x2)[V]) {
+  const C u1 = cf.u1[i];
+  C t = C(1), u2 = C(0);
+  if (ADJ) t = cf.t[i];
+  if (BW == 2) u2 = cf.u2[i];
+#pragma unroll
+  for (int v = 0; v < V; v++) {
+    C x = ADJ ? f[v] * t : f[v];
+    if (BW == 2) x = fma(-u2, x2[v], x);
+    x = fma(-u1, x1[v], x);
+    if (BW == 2) x2[v] = x1[v];
+    x1[v] = x;
+    f[v] = x;
+  }
+}
+
+// ---------------------------------------------------- interleaved layout
+
+// Row i of system j at [i*M + j].  Thread g owns systems [g*V, g*V + V).
+// Rows are moved in blocks of U with a two-block register pipeline: the loads
+// of the next block are issued before the current block is computed, so each
+// thread keeps up to 2*U*V loads in flight.
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const int64_t ngroups = M / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    const Sin* pin = in + g * V;
+    Sout* pout = out + g * V;
+    C a[U][V], b[U][V];
+    C r1[V], r2[V];
+
+    auto load_fwd = [&](C (&blk)[U][V], int i0) {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (i0 + u < N) IO<Sin, C, V>::load(pin + (int64_t)(i0 + u) * M, blk[u]);
+    };
+    auto run_fwd = [&](C (&blk)[U][V], int i0) {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (i0 + u < N) {
+          fwd_step<BW, ADJ, C, V>(cf, i0 + u, blk[u], r1, r2);
+          IO<Sout, C, V>::store(pout + (int64_t)(i0 + u) * M, blk[u]);
+        }
+    };
+    auto load_bwd = [&](C (&blk)[U][V], int top) {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (top - u >= 0) IO<Sout, C, V>::load(pout + (int64_t)(top - u) * M, blk[u]);
+    };
+    auto run_bwd = [&](C (&blk)[U][V], int top) {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (top - u >= 0) {
+          bwd_step<BW, ADJ, C, V>(cf, top - u, blk[u], r1, r2);
+          IO<Sout, C, V>::store(pout + (int64_t)(top - u) * M, blk[u]);
+        }
+    };
+
+    // forward sweep
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    load_fwd(a, 0);
+    for (int i0 = 0; i0 < N; i0 += 2 * U) {
+      if (i0 + U < N) load_fwd(b, i0 + U);
+      run_fwd(a, i0);
+      if (i0 + U >= N) break;
+      if (i0 + 2 * U < N) load_fwd(a, i0 + 2 * U);
+      run_fwd(b, i0 + U);
+    }
+    // backward sweep
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    load_bwd(a, N - 1);
+    for (int top = N - 1; top >= 0; top -= 2 * U) {
+      if (top - U >= 0) load_bwd(b, top - U);
+      run_bwd(a, top);
+      if (top - U < 0) break;
+      if (top - 2 * U >= 0) load_bwd(a, top - 2 * U);
+      run_bwd(b, top - U);
+    }
+  }
+}
+
+// ------------------------------------------------------ strided layout
+
+// Row i of system j at [j*N + i] (system-contiguous).  Each warp owns 32
+// systems, one per lane, and moves rows in chunks of 32 through a private
+// shared-memory tile: for each system the 32 lanes load 32 consecutive rows
+// (one coalesced segment) into a tile column, then each lane sweeps its own
+// system down the tile, then the tile goes back the same way.
+constexpr int kStRows = 32;
+constexpr int kStPad = 33;
+
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smc = reinterpret_cast<C*>(smem_raw);
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kSweepThreads / 32;
+  C* tile = smc + (SMEM ? coef_arrays<BW>() * N : 0) + warp * kStRows * kStPad;
+  const int64_t nwg = (M + 31) / 32;
+  for (int64_t wg = (int64_t)blockIdx.x * kWarps + warp; wg < nwg; wg += (int64_t)gridDim.x * kWarps) {
+    const int64_t j0 = wg * 32;
+    const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
+    const bool mine = lane < nsys;
+    C r1[1] = {C(0)}, r2[1] = {C(0)};
+    // forward sweep, chunks of rows in increasing order
+    for (int c0 = 0; c0 < N; c0 += kStRows) {
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) {
+          C v[1];
+          IO<Sin, C, 1>::load(in + (j0 + s) * (int64_t)N + c0 + lane, v);
+          tile[lane * kStPad + s] = v[0];
+        }
+      __syncwarp();
+      if (mine)
+        for (int r = 0; r < rows; r++) {
+          C f[1] = {tile[r * kStPad + lane]};
+          fwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
+          tile[r * kStPad + lane] = f[0];
+        }
+      __syncwarp();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) {
+          const C v[1] = {tile[lane * kStPad + s]};
+          IO<Sout, C, 1>::store(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+        }
+      __syncwarp();
+    }
+    // backward sweep, chunks in decreasing order
+    r1[0] = r2[0] = C(0);
+    const int last = ((N - 1) / kStRows) * kStRows;
+    for (int c0 = last; c0 >= 0; c0 -= kStRows) {
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) {
+          C v[1];
+          IO<Sout, C, 1>::load(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+          tile[lane * kStPad + s] = v[0];
+        }
+      __syncwarp();
+      if (mine)
+        for (int r = rows - 1; r >= 0; r--) {
+          C f[1] = {tile[r * kStPad + lane]};
+          bwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
+          tile[r * kStPad + lane] = f[0];
+        }
+      __syncwarp();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) {
+          const C v[1] = {tile[lane * kStPad + s]};
+          IO<Sout, C, 1>::store(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+        }
+      __syncwarp();
+    }
+  }
+}
+
+// --------------------------------------------------------------- launcher
+
+struct LaunchShape {
+  int grid;
+  size_t smem;
+  bool smem_coefs;
+};
+
+// Chooses the grid and shared memory of one sweep launch.  The grid is
+// persistent (each thread loops over groups of systems); it is capped so that
+// the forward values of all systems in flight take at most half of L2.
+LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
+                        int per_thread_systems, bool strided, int blocks_per_sm);
+
+template <int BW, bool ADJ, typename C, typename Sin, typename Sout, int V>
+cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
+  constexpr int U = sizeof(C) == 8 ? 8 : 8;
+  const int64_t groups = M / V;
+  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, false, 0);
+  if (sh.smem_coefs) {
+    auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    k<<<sh.grid, kSweepThreads, sh.smem, st>>>(cf, N, in, out, M);
+  } else {
+    k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U><<<sh.grid, kSweepThreads, 0, st>>>(cf, N, in, out, M);
+  }
+  return cudaGetLastError();
+}
+
+template <int BW, bool ADJ, typename C, typename Sin, typename Sout>
+cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
+  const int64_t threads = ((M + 31) / 32) * 32;
+  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, true, 0);
+  const size_t tiles = (size_t)(kSweepThreads / 32) * kStRows * kStPad * sizeof(C);
+  if (sh.smem_coefs) {
+    auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
+    if (e != cudaSuccess) return e;
+    k<<<sh.grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, in, out, M);
+  } else {
+    k_sweep_st<BW, ADJ, false, C, Sin, Sout><<<sh.grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M);
+  }
+  return cudaGetLastError();
+}
+
+// Dispatch over band width, direction, layout and vector width for one
+// storage/compute type combination.
+template <typename C, typename Sin, typename Sout, int VEC>
+cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* in, Sout* out,
+                           bs_layout layout, int64_t M, cudaStream_t st) {
+  const C* base;
+  if constexpr (sizeof(C) == 8)
+    base = reinterpret_cast<const C*>(p.c64);
+  else
+    base = reinterpret_cast<const C*>(p.c32);
+  const Coefs<C> cf = coefs_of<C>(base, N);
+  const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
+                   (reinterpret_cast<uintptr_t>(out) % (VEC * sizeof(Sout)) == 0);
+#define BS_DISPATCH(BWV, ADJV)                                                          \
+  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, C, Sin, Sout>(cf, N, in, out, M, st); \
+  if (vec) return launch_il<BWV, ADJV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);        \
+  return launch_il<BWV, ADJV, C, Sin, Sout, 1>(cf, N, in, out, M, st);
+  if (p.bw == 1) {
+    if (!adjoint) { BS_DISPATCH(1, false) } else { BS_DISPATCH(1, true) }
+  } else {
+    if (!adjoint) { BS_DISPATCH(2, false) } else { BS_DISPATCH(2, true) }
+  }
+#undef BS_DISPATCH
+}
+
+}  // namespace bs

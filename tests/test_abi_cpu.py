@@ -1,0 +1,72 @@
+"""Host-only checks of the C ABI: the library builds and loads without a
+GPU, exports every function that include/*.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1909_04539_gb300 import build as libbuild
+from paper_1909_04539_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(bs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding covers the same set
+    assert set(names) == set(_lib.SIGNATURES), set(names) ^ set(_lib.SIGNATURES)
+
+
+def test_lhs_bytes_matches_paper_storage(L):
+    # Sec. 3.1: one shared copy of 3N coefficients (tri); Sec. 4.1: 5N (penta)
+    assert L.bs_lhs_bytes(3, 1024, 8) == 3 * 1024 * 8
+    assert L.bs_lhs_bytes(5, 512, 8) == 5 * 512 * 8
+    assert L.bs_lhs_bytes(4, 10, 8) == -1
+
+
+def test_factor_argument_errors(L):
+    h = ctypes.c_void_p()
+    bands = (ctypes.c_double * 15)()
+    assert L.bs_factor(None, 3, 5, ctypes.byref(h)) == 1
+    assert L.bs_factor(bands, 4, 3, ctypes.byref(h)) == 1
+    assert L.bs_factor(bands, 3, 1, ctypes.byref(h)) == 1
+    assert L.bs_factor(bands, 5, 3, ctypes.byref(h)) == 1
+    assert L.bs_factor(bands, 3, 5, None) == 1
+    assert b"width" in L.bs_last_error() or b"N must" in L.bs_last_error() or b"NULL" in L.bs_last_error()
+
+
+def test_solve_rejects_unknown_handle(L):
+    bogus = ctypes.c_void_p(0x1234)
+    assert L.bs_solve(bogus, ctypes.c_void_p(0x1000), 0, 0, 4, None) == 1
+    assert L.bs_solve(None, ctypes.c_void_p(0x1000), 0, 0, 4, None) == 1
+    assert L.bs_solve_adjoint(None, ctypes.c_void_p(0x1000), 0, 0, 4, None, None, None) == 1
+    assert L.bs_destroy(bogus) == 1
+    assert L.bs_destroy(None) == 0
+    assert L.bs_strerror(2).startswith(b"zero or non-finite pivot")
+
+
+def test_set_option(L):
+    assert L.bs_set_option(0, 0) == 0
+    assert L.bs_set_option(99, 1) == 1
+    assert L.bs_set_option(0, -5) == 1

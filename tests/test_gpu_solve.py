@@ -1,0 +1,178 @@
+"""GPU parity of the plain sweeps against the CPU FP64 oracle, through the C
+ABI.  Tolerances (relative L2 over the whole batch):
+  FP64: 1e-12 (the stated target for every FP64 path);
+  FP32 storage and arithmetic: 2e-5 -- the matrices here are diagonally
+    dominant with condition numbers below ~10, so a forward-stable sweep in
+    FP32 (u = 6e-8) lands within ~10 kappa u;
+  BF16 storage, FP32 arithmetic: compared with the oracle's solve of the
+    BF16-rounded B, so only the FP32 arithmetic differs: 2e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    return m
+
+
+def _bands(width, N, seed):
+    rng = np.random.default_rng(seed)
+    return synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
+
+
+def _rhs(N, M, seed, layout):
+    rng = np.random.default_rng(seed + 7)
+    B = rng.uniform(-1, 1, (N, M))
+    return B if layout == "interleaved" else np.ascontiguousarray(B.T)
+
+
+def _gpu_solve(bs, f, Bh, dtype, layout):
+    B = torch.tensor(Bh, dtype=dtype, device="cuda")
+    bs.solve(f, B, layout)
+    torch.cuda.synchronize()
+    return B.double().cpu().numpy()
+
+
+def test_config0_random_tri_fp64(bs):
+    """Tridiagonal, N=64, M=1024, a,c ~ U(-1,1), b = |a|+|c|+U(1,2), RHS ~
+    U(-1,1), seed 0 -- the full workload against the oracle."""
+    bands, Bh = synth.random_tri_case(64, 1024, 0)
+    f = bs.Factor(bands)
+    for layout in ("interleaved", "strided"):
+        B_in = Bh if layout == "interleaved" else np.ascontiguousarray(Bh.T)
+        X = _gpu_solve(bs, f, B_in, torch.float64, layout)
+        ref = oracle.solve(bands, B_in, layout)
+        assert rel_l2(X, ref) < TOL64, (layout, rel_l2(X, ref))
+
+
+SHAPES = [(3, 2, 1), (3, 2, 5), (3, 3, 7), (3, 33, 31), (3, 100, 1000), (3, 257, 1027), (3, 64, 4096),
+          (5, 4, 1), (5, 5, 6), (5, 37, 33), (5, 130, 515), (5, 512, 2048)]
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("width,N,M", SHAPES)
+def test_fp64_ragged(bs, width, N, M, layout):
+    bands = _bands(width, N, N * 7 + M)
+    Bh = _rhs(N, M, M, layout)
+    f = bs.Factor(bands)
+    X = _gpu_solve(bs, f, Bh, torch.float64, layout)
+    assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL64
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("width,N,M", SHAPES)
+def test_fp32_ragged(bs, width, N, M, layout):
+    bands = _bands(width, N, N * 11 + M)
+    Bh = _rhs(N, M, M + 1, layout).astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    X = _gpu_solve(bs, f, Bh, torch.float32, layout)
+    assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL32
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("width,N,M", [(3, 64, 1024), (5, 37, 33), (3, 257, 1027), (5, 512, 4096)])
+def test_bf16_storage(bs, width, N, M, layout):
+    bands = _bands(width, N, N + M)
+    Bh = _rhs(N, M, M + 2, layout)
+    B = torch.tensor(Bh, dtype=torch.bfloat16, device="cuda")
+    f = bs.Factor(bands)
+    X = bs.solve_bf16(f, B, layout=layout)
+    torch.cuda.synchronize()
+    ref = oracle.solve(bands, B.double().cpu().numpy(), layout)
+    assert rel_l2(X.double().cpu().numpy(), ref) < TOL32
+
+
+def test_misaligned_pointer_uses_scalar_path(bs):
+    """A view starting one element into a buffer cannot take 128-bit loads."""
+    N, M = 40, 64
+    bands = _bands(3, N, 5)
+    Bh = _rhs(N, M, 9, "interleaved")
+    buf = torch.zeros(N * M + 1, dtype=torch.float64, device="cuda")
+    B = buf[1:].view(N, M)
+    B.copy_(torch.tensor(Bh, device="cuda"))
+    f = bs.Factor(bands)
+    bs.solve(f, B)
+    torch.cuda.synchronize()
+    assert rel_l2(B.cpu().numpy(), oracle.solve(bands, Bh)) < TOL64
+    assert buf[0].item() == 0.0
+
+
+def test_solve_leaves_other_memory_alone(bs):
+    """Canaries on both sides of the batch stay untouched."""
+    N, M = 77, 333
+    bands = _bands(5, N, 8)
+    Bh = _rhs(N, M, 10, "interleaved")
+    pad = 4096
+    buf = torch.full((pad + N * M + pad,), 12345.0, dtype=torch.float64, device="cuda")
+    B = buf[pad:pad + N * M].view(N, M)
+    B.copy_(torch.tensor(Bh, device="cuda"))
+    f = bs.Factor(bands)
+    bs.solve(f, B)
+    torch.cuda.synchronize()
+    assert torch.all(buf[:pad] == 12345.0) and torch.all(buf[pad + N * M:] == 12345.0)
+    assert rel_l2(B.cpu().numpy(), oracle.solve(bands, Bh)) < TOL64
+
+
+def test_deterministic(bs):
+    bands = _bands(5, 300, 1)
+    Bh = _rhs(300, 5000, 2, "interleaved")
+    f = bs.Factor(bands)
+    a = _gpu_solve(bs, f, Bh, torch.float64, "interleaved")
+    b = _gpu_solve(bs, f, Bh, torch.float64, "interleaved")
+    assert np.array_equal(a, b)
+
+
+def test_singular_rejected(bs):
+    bands = synth.toeplitz_bands(6, (1.0, 0.0, 1.0))
+    with pytest.raises(bs.BsolveError) as ei:
+        bs.Factor(bands)
+    assert ei.value.status == 2
+
+
+def test_wrong_shape_rejected(bs):
+    f = bs.Factor(_bands(3, 10, 0))
+    with pytest.raises(ValueError):
+        bs.solve(f, torch.zeros(11, 4, dtype=torch.float64, device="cuda"))
+
+
+def test_config1_penta_full_size_sampled(bs):
+    """A = I + 0.1 D4 clamped, N=512, M=65536, RHS ~ N(0,1) (seed 0) at full
+    size in the launch configuration the benchmark times; 512 sampled systems
+    are checked against the oracle one by one, the rest via the residual."""
+    N, M = 512, 65536
+    bands = synth.clamped_hyperdiffusion_bands(N, 0.1)
+    f = bs.Factor(bands)
+    B0 = synth.normal_rhs(N, M, 0, "cuda")
+    X = B0.clone()
+    bs.solve(f, X)
+    torch.cuda.synchronize()
+    cols = np.random.default_rng(3).choice(M, 512, replace=False)
+    cols = np.union1d(cols, [0, 1, M - 2, M - 1])
+    Bs = B0[:, cols].cpu().numpy()
+    ref = oracle.solve(bands, Bs)
+    assert rel_l2(X[:, cols].cpu().numpy(), ref) < TOL64
+    # every system: relative residual with the banded product on the GPU in FP64
+    b = torch.tensor(bands, device="cuda")
+    R = B0.clone()
+    for k, off in enumerate(range(-2, 3)):
+        lo, hi = max(0, -off), N - max(0, off)
+        R[lo:hi] -= b[k, lo:hi, None] * X[lo + off:hi + off]
+    assert (torch.linalg.norm(R) / torch.linalg.norm(B0)).item() < 1e-13
+    # FP32 on the same data: error stated against the oracle
+    X32 = B0.float()
+    bs.solve(f, X32)
+    torch.cuda.synchronize()
+    assert rel_l2(X32[:, cols].double().cpu().numpy(), ref) < TOL32
