@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the batched shared-LHS banded solve on GB300.
+
+Workload: pentadiagonal A = I + 0.1 D4 ([1, -4, 6, -4, 1] stencil, first and
+last two rows clamped), N = 512 rows, M = 65536 systems per GPU, interleaved
+(B[i*M + j]), RHS ~ N(0, 1), FP64.  One step is one pass of every row of the
+hot path over that batch:
+  1. the plain FP64 solve (forward + backward sweep, FP64 arithmetic),
+  2. the FP32-stored solve (FP32 sweeps; FP32 storage),
+  3. the adjoint solve A^{-T} G and the band-gradient reduction over the batch.
+Each solve works in place on the previous step's result (implicit time
+stepping: X <- A^{-1} X), so no copy is needed between steps; every operand
+(256 MiB FP64) is larger than L2, so L2 is not flushed.
+
+``value`` is unknowns solved per second over the whole job: 3 * N * M per GPU
+per step, summed over GPUs, divided by the slowest rank's time.
+
+``--impl reference`` times the plain CPU FP64 oracle on the same kind of step
+(a bounded column sample) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ROWS, M_SYS, S_HYPER = 512, 65536, 0.1
+METRIC = "unknowns/s & HBM GB/s vs 8 TB/s at stated rel err; serving p50/p99 latency"
+WORKLOAD = ("penta A=I+0.1*D4 clamped, N=512, M=65536 RHS ~ N(0,1) per GPU, interleaved, FP64; "
+            "step = FP64 solve + FP32 solve + adjoint solve with band gradient")
+NOMINAL_HBM_GBS = 8000.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "MEASURED_PEAKS.json (driver-measured copy bandwidth)"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "profiling-recipe fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------------ clocks
+
+REASON_COLS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed
+    region."""
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.lines = []
+        exe = shutil.which("nvidia-smi")
+        if exe is None:
+            return
+        import torch
+        p = torch.cuda.get_device_properties(device_index)
+        ident = str(device_index)
+        try:
+            ident = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        except AttributeError:
+            pass
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.cmd = [exe, f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50", "-i", ident]
+
+    def __enter__(self):
+        if getattr(self, "cmd", None):
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            time.sleep(0.15)
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(REASON_COLS, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1909_04539_gb300 import build as libbuild
+    if rank == 0 or world == 1:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1909_04539_gb300 as bs
+    import synth
+
+    N, M = N_ROWS, M_SYS
+    bands = synth.clamped_hyperdiffusion_bands(N, S_HYPER)
+    f = bs.Factor(bands)
+    X64 = synth.normal_rhs(N, M, rank, "cuda")
+    B0 = X64.clone()
+    X32 = X64.float()
+    G = synth.uniform_rhs(N, M, 1000 + rank, "cuda")
+    db = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+
+    # accuracy: the first solve of this rank's batch, kept on sampled columns
+    # for the oracle comparison in the CPU-baseline leg, and checked on every
+    # system through the FP64 residual |B - A X| / |B| (torch ops)
+    Xchk = B0.clone()
+    bs.solve(f, Xchk)
+    X32chk = B0.float()
+    bs.solve(f, X32chk)
+    torch.cuda.synchronize()
+    cols = np.random.default_rng(7).choice(M, 1024, replace=False)
+    sample = {"cols": cols, "B": B0[:, cols].cpu().numpy(), "X64": Xchk[:, cols].cpu().numpy(),
+              "X32": X32chk[:, cols].double().cpu().numpy()}
+    resid64 = rel_residual(bands, B0, Xchk)
+    resid32 = rel_residual(bands, B0, X32chk.double())
+    del Xchk, X32chk
+
+    names = ["f64_solve", "f32_solve", "adjoint_f64", "band_grad_f64"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+
+    def step(k=None):
+        e = ev[k] if k is not None else None
+        if e: e[0].record(st)
+        bs.solve(f, X64)
+        if e: e[1].record(st)
+        bs.solve(f, X32)
+        if e: e[2].record(st)
+        bs.solve_adjoint(f, G)
+        if e: e[3].record(st)
+        bs.band_grad(f, G, X64, dbands=db)
+        if e: e[4].record(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(st)
+        for k in range(args.steps):
+            step(k)
+        t1.record(st)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per = {n: 0.0 for n in names}
+    for k in range(args.steps):
+        for q, n in enumerate(names):
+            per[n] += ev[k][q].elapsed_time(ev[k][q + 1]) / args.steps
+    ms_step = ms / args.steps
+    units_step = 3 * N * M  # solves with N*M unknowns each: f64, f32, adjoint
+    value = units_step * world / (ms_step * 1e-3)
+
+    peaks, peak_src = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    fp64_fma = bs.measure_fp64_rate()
+    fp64_tflops = 2 * fp64_fma / 1e12
+    nm = N * M
+    # algorithmic bytes and flops per launch (pentadiagonal)
+    paths = {
+        "f64_solve": {"bytes": 16 * nm, "flops": 9 * nm, "dp_instr": 5 * nm, "bound": "alu"},
+        "f32_solve": {"bytes": 8 * nm, "flops": 9 * nm, "bound": "hbm"},
+        "adjoint_f64": {"bytes": 16 * nm, "flops": 9 * nm, "dp_instr": 5 * nm, "bound": "alu"},
+        "band_grad_f64": {"bytes": 16 * nm, "flops": 10 * nm, "dp_instr": 5 * nm, "bound": "alu"},
+    }
+    for n, p in paths.items():
+        t = per[n] * 1e-3
+        p["ms"] = round(per[n], 5)
+        p["unknowns_per_s"] = nm / t
+        p["hbm_gbs"] = p["bytes"] / t / 1e9
+        p["hbm_frac_of_measured"] = p["hbm_gbs"] / hbm
+        p["hbm_frac_of_8tbs"] = p["hbm_gbs"] / NOMINAL_HBM_GBS
+        if "dp_instr" in p:
+            p["fp64_tflops"] = p["flops"] / t / 1e12
+            p["fp64_instr_frac_of_measured"] = p["dp_instr"] / t / fp64_fma
+    dom = max(paths, key=lambda n: per[n])
+    dp = paths[dom]
+    if dp["bound"] == "alu":
+        roof = {"bound": "alu", "kernel": dom, "achieved": dp["fp64_tflops"], "peak": fp64_tflops,
+                "unit": "TFLOP/s", "frac": dp["fp64_tflops"] / fp64_tflops, "traffic": None,
+                "peak_source": "FP64 FMA rate measured live by bs_measure_fp64_rate (FMA = 2 flop)",
+                "algorithmic": "9 FP64 flop per unknown (forward MUL + 2 FMA, backward 2 FMA)"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": dp["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": dp["hbm_gbs"] / hbm, "traffic": None, "peak_source": peak_src}
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(bs, f, N, M, st, args, world)
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "width": 5, "layout": "interleaved",
+                   "l2": "no flush: every operand (256 MiB FP64 / 128 MiB FP32) exceeds L2",
+                   "parallelism": f"replicas x{world} (systems partitioned, no collective)"},
+        "rel_residual": {"f64_solve": resid64, "f32_solve": resid32},
+        "hbm_gbs_step": (sum(p["bytes"] for p in paths.values())) / (ms_step * 1e-3) / 1e9,
+        "paths": {n: {k: (round(v, 6) if isinstance(v, float) else v) for k, v in p.items()}
+                  for n, p in paths.items()},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, errs = cpu_baseline(args, bands, sample)
+        line["cpu_baseline"] = cb
+        line["rel_err_vs_oracle"] = errs
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(bs, f, N, M, st, args, world):
+    """Same three solves through the public API with pinned host buffers:
+    each step copies its inputs host->device and its results back."""
+    import torch
+
+    steps = max(1, min(args.steps, 10))
+    hB = torch.empty((N, M), dtype=torch.float64, pin_memory=True).normal_()
+    hB32 = hB.float().pin_memory()
+    hG = torch.empty((N, M), dtype=torch.float64, pin_memory=True).uniform_(-1, 1)
+    oX = torch.empty_like(hB).pin_memory()
+    oX32 = torch.empty_like(hB32).pin_memory()
+    oG = torch.empty_like(hG).pin_memory()
+    odb = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
+    dB = torch.empty((N, M), dtype=torch.float64, device="cuda")
+    dB32 = torch.empty((N, M), dtype=torch.float32, device="cuda")
+    dG = torch.empty((N, M), dtype=torch.float64, device="cuda")
+
+    def one():
+        dB.copy_(hB, non_blocking=True)
+        dB32.copy_(hB32, non_blocking=True)
+        dG.copy_(hG, non_blocking=True)
+        bs.solve(f, dB)
+        bs.solve(f, dB32)
+        _, db = bs.solve_adjoint(f, dG, X=dB)
+        oX.copy_(dB, non_blocking=True)
+        oX32.copy_(dB32, non_blocking=True)
+        oG.copy_(dG, non_blocking=True)
+        odb.copy_(db, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for _ in range(steps):
+        one()
+    t1.record(st)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    h2d = N * M * (8 + 4 + 8)
+    d2h = N * M * (8 + 4 + 8) + 5 * N * 8
+    return {"value": 3 * N * M * world / (ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": steps}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+
+def _oracle_step(oracle, bands, B, G):
+    X = oracle.solve(bands, B)            # FP64 solve
+    oracle.solve(bands, B)                # the FP32-stored solve has the same FP64 reference
+    GB = oracle.solve_adjoint(bands, G)   # adjoint
+    oracle.band_grad(5, GB, X)            # band gradient
+    return X
+
+
+def cpu_baseline(args, bands, sample, target_s: float = 12.0):
+    """The oracle, as it stands, timed on a bounded column sample of the
+    workload (the very columns the GPU solved first), which also gives the
+    GPU's error against it."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    N = N_ROWS
+    B, cols = sample["B"], sample["cols"]
+    rng = np.random.default_rng(1)
+    G = rng.uniform(-1, 1, B.shape)
+    m0 = B.shape[1]
+    t = time.perf_counter()
+    X = _oracle_step(oracle, bands, B, G)
+    dt = time.perf_counter() - t
+    errs = {"f64_solve": float(np.linalg.norm(sample["X64"] - X) / np.linalg.norm(X)),
+            "f32_solve": float(np.linalg.norm(sample["X32"] - X) / np.linalg.norm(X)),
+            "tolerance_f64": 1e-12, "systems_checked": int(m0)}
+    reps = max(1, int(target_s / max(dt, 1e-3)))
+    reps = min(reps, 64)
+    t = time.perf_counter()
+    for _ in range(reps):
+        _oracle_step(oracle, bands, B, G)
+    dt = (time.perf_counter() - t) / reps
+    cb = {"value": 3 * N * m0 / dt, "unit": "unknowns/s", "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"{reps} repetitions of one step (FP64 solve, FP64 solve, adjoint + band gradient) on "
+                    f"{m0} of the {M_SYS} systems, {dt * reps:.1f} s in total"}
+    return cb, errs
+
+
+def rel_residual(bands, B, X) -> float:
+    """|B - A X|_F / |B|_F over every system, in FP64 on the device."""
+    import torch
+
+    b = torch.tensor(bands, device=X.device)
+    w = b.shape[0]
+    h = w // 2
+    N = X.shape[0]
+    R = B.clone()
+    for k in range(w):
+        off = k - h
+        lo, hi = max(0, -off), N - max(0, off)
+        R[lo:hi] -= b[k, lo:hi, None] * X[lo + off:hi + off]
+    return float((torch.linalg.norm(R) / torch.linalg.norm(B)).item())
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, same metric and units."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    N = N_ROWS
+    bands = synth.clamped_hyperdiffusion_bands(N, S_HYPER)
+    rng = np.random.default_rng(0)
+    m = 2048
+    B = rng.standard_normal((N, m))
+    G = rng.uniform(-1, 1, (N, m))
+    t = time.perf_counter()
+    _oracle_step(oracle, bands, B, G)
+    dt = time.perf_counter() - t
+    # each step a bounded sample: the whole run (warm-up + timed) in about a minute
+    per_step = 60.0 / max(1, args.steps + args.warmup)
+    m = int(min(M_SYS, max(256, m * per_step / max(dt, 1e-6))))
+    B = rng.standard_normal((N, m))
+    G = rng.uniform(-1, 1, (N, m))
+    for _ in range(args.warmup):
+        _oracle_step(oracle, bands, B, G)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(oracle, bands, B, G)
+    dt = (time.perf_counter() - t) / args.steps
+    value = 3 * N * m / dt
+    sample = f"each step on {m} of the {M_SYS} systems (FP64 solve, FP64 solve, adjoint + band gradient)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M_SYS, "width": 5, "layout": "interleaved",
+                   "sample_M": m},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -110,6 +110,15 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
 bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M,
                            const void* X, double* dbands, bs_stream stream);
 
+/* Band-gradient reduction alone, for a caller that already holds
+ * GB = A^{-T} (dL/dX) (e.g. from bs_solve_adjoint without X):
+ *   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - width/2, j]
+ * (0 for entries outside the matrix), reduced in a fixed order.  GB and X:
+ * device, same dtype (BS_F64 or BS_F32) and layout; dbands: device
+ * double[width*N], overwritten. */
+bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout,
+                       int64_t M, double* dbands, bs_stream stream);
+
 /* Launch tuning knobs (process-wide; 0 restores the default).
  *  BS_OPT_INFLIGHT_BYTES: upper bound on the bytes of forward-sweep values
  *    that all systems in flight keep between their two sweeps (default: half
@@ -118,6 +127,13 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  *    (default 8). */
 typedef enum { BS_OPT_INFLIGHT_BYTES = 0, BS_OPT_BLOCKS_PER_SM = 1, BS_OPT_COUNT = 2 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
+
+/* Measurement aid (the paper has no counterpart): runs a short kernel of
+ * independent FP64 fused multiply-adds on `stream`, waits for it, and stores
+ * the device's FP64 FMA rate in FMA instructions per second.  This is the
+ * ceiling of the sweeps that compute in native FP64 (on GB300 they are bound
+ * by it before HBM).  Allocates and frees 8 bytes of device memory. */
+bs_status bs_measure_fp64_rate(double* fma_per_s, bs_stream stream);
 
 /* Last error message of the calling thread (static storage, never NULL). */
 const char* bs_last_error(void);

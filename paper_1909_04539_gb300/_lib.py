@@ -21,7 +21,9 @@ SIGNATURES = {
     "bs_solve": (i32, [vp, vp, i32, i32, i64, vp]),
     "bs_solve_bf16": (i32, [vp, vp, vp, i32, i64, vp]),
     "bs_solve_adjoint": (i32, [vp, vp, i32, i32, i64, vp, vp, vp]),
+    "bs_band_grad": (i32, [vp, vp, vp, i32, i32, i64, vp, vp]),
     "bs_set_option": (i32, [i32, i64]),
+    "bs_measure_fp64_rate": (i32, [dp, vp]),
     "bs_last_error": (ctypes.c_char_p, []),
     "bs_strerror": (ctypes.c_char_p, [i32]),
 }

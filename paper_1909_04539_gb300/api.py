@@ -30,6 +30,13 @@ def set_option(opt: int, value: int) -> None:
     check(lib().bs_set_option(int(opt), int(value)), "bs_set_option")
 
 
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 FMA instructions per second of the current device (blocking)."""
+    v = ctypes.c_double()
+    check(lib().bs_measure_fp64_rate(ctypes.byref(v), _stream(stream)), "bs_measure_fp64_rate")
+    return float(v.value)
+
+
 def lhs_bytes(width: int, N: int, elem_bytes: int) -> int:
     return int(lib().bs_lhs_bytes(width, N, elem_bytes))
 
@@ -140,6 +147,23 @@ def solve_adjoint(f: Factor, G: torch.Tensor, layout: str = "interleaved", X: to
     check(lib().bs_solve_adjoint(f.handle, ctypes.c_void_p(G.data_ptr()), _DTYPE[G.dtype], _LAYOUT[layout], M,
                                  xp, dp, _stream(stream)), "bs_solve_adjoint")
     return (G, dbands) if X is not None else G
+
+
+def band_grad(f: Factor, GB: torch.Tensor, X: torch.Tensor, layout: str = "interleaved",
+              dbands: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """-(GB) X^T on the bands, given GB = A^{-T} dL/dX; (width, N) float64."""
+    M = _batch(f, GB, layout, "GB")
+    _batch(f, X, layout, "X")
+    if X.dtype != GB.dtype or X.shape != GB.shape or GB.dtype not in (torch.float64, torch.float32):
+        raise ValueError("GB and X must be float64 or float32 tensors of one shape")
+    if dbands is None:
+        dbands = torch.empty((f.width, f.N), dtype=torch.float64, device=GB.device)
+    if dbands.dtype != torch.float64 or not dbands.is_contiguous() or dbands.numel() != f.width * f.N:
+        raise ValueError("dbands must be a contiguous float64 (width, N) tensor")
+    check(lib().bs_band_grad(f.handle, ctypes.c_void_p(GB.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                             _DTYPE[GB.dtype], _LAYOUT[layout], M, ctypes.c_void_p(dbands.data_ptr()),
+                             _stream(stream)), "bs_band_grad")
+    return dbands
 
 
 class SolveFn(torch.autograd.Function):

@@ -121,4 +121,13 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
   return BS_OK;
 }
 
+bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout, int64_t M,
+                       double* dbands, bs_stream stream) {
+  bs_status s = check_common(h, GB, layout, M, "bs_band_grad");
+  if (s != BS_OK) return s;
+  if (!X || !dbands) return set_error(BS_EINVAL, "bs_band_grad: X and dbands must be non-NULL");
+  if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_band_grad: dtype must be BS_F64 or BS_F32");
+  return launch_band_grad(h, GB, X, dtype, layout, M, dbands, reinterpret_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
