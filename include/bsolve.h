@@ -98,6 +98,24 @@ bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64
 bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, int64_t M,
                         bs_stream stream);
 
+/* Mixed-precision solve (FP32 storage, FP64 result): X = A^{-1} B with B
+ * stored in FP32 (float[N*M], device, read only) and X written in FP64
+ * (double[N*M], device).  The sweeps run in FP32; with refine_steps = 1 one
+ * step of iterative refinement follows, with the residual r = B - A X0 of
+ * the FP32 solution X0 evaluated to FP64 accuracy (FP64 bands split into
+ * FP32 pairs, error-free products and sums) and the correction added in
+ * FP64.  The correction solve uses the reversed elimination A = U' L',
+ * factorised once with the handle, so the whole solve is three passes over
+ * each system in one kernel.  refine_steps = 0 returns the FP32 solution
+ * widened to FP64.  X doubles as the workspace of the passes.  Only
+ * BS_INTERLEAVED and b_dtype BS_F32 are implemented (BS_EUNSUPPORTED
+ * otherwise); refine_steps > 1 is BS_EUNSUPPORTED.  B and X must not
+ * overlap.  Returns BS_ESINGULAR if the reversed elimination of A met a bad
+ * pivot when the handle was built (plain solves still work then).
+ * Not in the paper: the paper's solvers work in a single precision. */
+bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
+                          int64_t M, int refine_steps, bs_stream stream);
+
 /* Adjoint solve: G <- A^{-T} G, in place, reusing the same factorisation
  * (A^T = R^T L^T, a forward sweep with R^T then a backward sweep with L^T).
  * If X (the primal solution A^{-1} B, same dtype and layout as G) and dbands
@@ -121,10 +139,11 @@ bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtyp
 
 /* Launch tuning knobs (process-wide; 0 restores the default).
  *  BS_OPT_INFLIGHT_BYTES: upper bound on the bytes of forward-sweep values
- *    that all systems in flight keep between their two sweeps (default: half
- *    of the device's L2), which sets how many systems run at once.
- *  BS_OPT_BLOCKS_PER_SM: resident CTAs per SM the persistent grids aim for
- *    (default 8). */
+ *    that all systems in flight keep between their two sweeps, which sets how
+ *    many systems run at once (default 0: no bound, every system that fits
+ *    on the device runs at once).
+ *  BS_OPT_BLOCKS_PER_SM: cap on resident CTAs per SM of the persistent grids
+ *    (default 0: as many as shared memory and threads allow). */
 typedef enum { BS_OPT_INFLIGHT_BYTES = 0, BS_OPT_BLOCKS_PER_SM = 1, BS_OPT_COUNT = 2 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

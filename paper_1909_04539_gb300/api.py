@@ -127,6 +127,25 @@ def solve_bf16(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, layout
     return X
 
 
+def solve_refine(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, refine_steps: int = 1,
+                 layout: str = "interleaved", stream=None) -> torch.Tensor:
+    """FP32-stored B (float32), FP32 sweeps plus ``refine_steps`` (0 or 1)
+    steps of iterative refinement with an FP64-accurate residual; returns the
+    FP64 solution X (also used as workspace)."""
+    M = _batch(f, B, layout, "B")
+    if B.dtype != torch.float32:
+        raise ValueError("B must be float32")
+    if X is None:
+        X = torch.empty(B.shape, dtype=torch.float64, device=B.device)
+    _batch(f, X, layout, "X")
+    if X.dtype != torch.float64 or X.shape != B.shape:
+        raise ValueError("X must be float64 with B's shape")
+    check(lib().bs_solve_refine(f.handle, ctypes.c_void_p(B.data_ptr()), _DTYPE[B.dtype],
+                                ctypes.c_void_p(X.data_ptr()), _LAYOUT[layout], M, int(refine_steps),
+                                _stream(stream)), "bs_solve_refine")
+    return X
+
+
 def solve_adjoint(f: Factor, G: torch.Tensor, layout: str = "interleaved", X: torch.Tensor | None = None,
                   dbands: torch.Tensor | None = None, stream=None):
     """In-place G <- A^{-T} G.  With X (the primal solution) also returns the

@@ -118,6 +118,72 @@ int64_t penta_factor(const double* const* bd, int64_t N, std::vector<double>& al
   return 0;
 }
 
+// Sweep coefficients of the primal (A^{-1}) and adjoint (A^{-T}) solves.
+// Returns the 1-based row of a bad pivot, or 0.
+int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, HostPlan& Q) {
+  auto C = [&](HostPlan& p, int k, int64_t i) -> double& { return p.c[(size_t)k * N + i]; };
+  if (width == 3) {
+    std::vector<double> r, chat;
+    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat);
+    if (bad_row) return bad_row;
+    // primal: dhat_i = r_i d_i - (a_i r_i) dhat_{i-1};  x_i = dhat_i - chat_i x_{i+1}
+    P.bw = 1;
+    P.fwd_scale = true;
+    P.bwd_scale = false;
+    for (int64_t i = 0; i < N; i++) {
+      C(P, C_S, i) = r[i];
+      C(P, C_L1, i) = (i > 0) ? bd[0][i] * r[i] : 0.0;
+      C(P, C_T, i) = 1.0;
+      C(P, C_U1, i) = chat[i];
+    }
+    // adjoint, A^T = U^T L^T with L = (p_i diag, a_i sub), U = (1, chat_i super):
+    // z_i = g_i - chat_{i-1} z_{i-1};  y_i = r_i z_i - (a_{i+1} r_i) y_{i+1}
+    Q.bw = 1;
+    Q.fwd_scale = false;
+    Q.bwd_scale = true;
+    for (int64_t i = 0; i < N; i++) {
+      C(Q, C_S, i) = 1.0;
+      C(Q, C_L1, i) = (i > 0) ? chat[i - 1] : 0.0;
+      C(Q, C_T, i) = r[i];
+      C(Q, C_U1, i) = (i + 1 < N) ? bd[0][i + 1] * r[i] : 0.0;
+    }
+    return 0;
+  }
+  std::vector<double> al, be, ga, de, ep;
+  const int64_t bad_row = penta_factor(bd, N, al, be, ga, de, ep);
+  if (bad_row) return bad_row;
+  // primal: g_i = f_i/al_i - (ep_i/al_i) g_{i-2} - (be_i/al_i) g_{i-1};
+  //         x_i = g_i - ga_i x_{i+1} - de_i x_{i+2}
+  P.bw = 2;
+  P.fwd_scale = true;
+  P.bwd_scale = false;
+  for (int64_t i = 0; i < N; i++) {
+    const double ia = 1.0 / al[i];
+    C(P, C_S, i) = ia;
+    C(P, C_L1, i) = (i >= 1) ? be[i] * ia : 0.0;
+    C(P, C_L2, i) = (i >= 2) ? ep[i] * ia : 0.0;
+    C(P, C_T, i) = 1.0;
+    C(P, C_U1, i) = (i + 1 < N) ? ga[i] : 0.0;
+    C(P, C_U2, i) = (i + 2 < N) ? de[i] : 0.0;
+  }
+  // adjoint, A^T = R^T L^T:
+  // z_i = g_i - ga_{i-1} z_{i-1} - de_{i-2} z_{i-2};
+  // y_i = z_i/al_i - (be_{i+1}/al_i) y_{i+1} - (ep_{i+2}/al_i) y_{i+2}
+  Q.bw = 2;
+  Q.fwd_scale = false;
+  Q.bwd_scale = true;
+  for (int64_t i = 0; i < N; i++) {
+    const double ia = 1.0 / al[i];
+    C(Q, C_S, i) = 1.0;
+    C(Q, C_L1, i) = (i >= 1) ? ga[i - 1] : 0.0;
+    C(Q, C_L2, i) = (i >= 2) ? de[i - 2] : 0.0;
+    C(Q, C_T, i) = ia;
+    C(Q, C_U1, i) = (i + 1 < N) ? be[i + 1] * ia : 0.0;
+    C(Q, C_U2, i) = (i + 2 < N) ? ep[i + 2] * ia : 0.0;
+  }
+  return 0;
+}
+
 void free_handle(bs_handle h) {
   if (!h) return;
   for (auto& p : h->plan) {
@@ -166,68 +232,32 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   const double* bd[5];
   for (int k = 0; k < width; k++) bd[k] = bands + (size_t)k * N;
 
-  HostPlan hp[2];
+  HostPlan hp[3];
+  bool has_ul = false;
   for (auto& p : hp) p.c.assign((size_t)C_COUNT * N, 0.0);
-  auto C = [&](HostPlan& p, int k, int64_t i) -> double& { return p.c[(size_t)k * N + i]; };
-
-  if (width == 3) {
-    std::vector<double> r, chat;
-    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat);
-    if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
-    // primal: dhat_i = r_i d_i - (a_i r_i) dhat_{i-1};  x_i = dhat_i - chat_i x_{i+1}
-    hp[0].bw = 1;
-    hp[0].fwd_scale = true;
-    hp[0].bwd_scale = false;
-    for (int64_t i = 0; i < N; i++) {
-      C(hp[0], C_S, i) = r[i];
-      C(hp[0], C_L1, i) = (i > 0) ? bd[0][i] * r[i] : 0.0;
-      C(hp[0], C_T, i) = 1.0;
-      C(hp[0], C_U1, i) = chat[i];
+  int64_t bad_row = make_plans(bd, width, N, hp[0], hp[1]);
+  if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
+  {
+    // Reversed matrix J A J (J the row reversal): band k of row i is band
+    // (width-1-k) of row N-1-i.  Its primal plan, read back in original row
+    // order, solves A = U' L' with a first sweep over decreasing rows.
+    std::vector<double> rev((size_t)width * N);
+    const double* rbd[5];
+    for (int k = 0; k < width; k++) {
+      for (int64_t i = 0; i < N; i++) rev[(size_t)k * N + i] = bd[width - 1 - k][N - 1 - i];
+      rbd[k] = rev.data() + (size_t)k * N;
     }
-    // adjoint, A^T = U^T L^T with L = (p_i diag, a_i sub), U = (1, chat_i super):
-    // z_i = g_i - chat_{i-1} z_{i-1};  y_i = r_i z_i - (a_{i+1} r_i) y_{i+1}
-    hp[1].bw = 1;
-    hp[1].fwd_scale = false;
-    hp[1].bwd_scale = true;
-    for (int64_t i = 0; i < N; i++) {
-      C(hp[1], C_S, i) = 1.0;
-      C(hp[1], C_L1, i) = (i > 0) ? chat[i - 1] : 0.0;
-      C(hp[1], C_T, i) = r[i];
-      C(hp[1], C_U1, i) = (i + 1 < N) ? bd[0][i + 1] * r[i] : 0.0;
-    }
-  } else {
-    std::vector<double> al, be, ga, de, ep;
-    const int64_t bad_row = penta_factor(bd, N, al, be, ga, de, ep);
-    if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
-    // primal: g_i = f_i/al_i - (ep_i/al_i) g_{i-2} - (be_i/al_i) g_{i-1};
-    //         x_i = g_i - ga_i x_{i+1} - de_i x_{i+2}
-    hp[0].bw = 2;
-    hp[0].fwd_scale = true;
-    hp[0].bwd_scale = false;
-    for (int64_t i = 0; i < N; i++) {
-      const double ia = 1.0 / al[i];
-      C(hp[0], C_S, i) = ia;
-      C(hp[0], C_L1, i) = (i >= 1) ? be[i] * ia : 0.0;
-      C(hp[0], C_L2, i) = (i >= 2) ? ep[i] * ia : 0.0;
-      C(hp[0], C_T, i) = 1.0;
-      C(hp[0], C_U1, i) = (i + 1 < N) ? ga[i] : 0.0;
-      C(hp[0], C_U2, i) = (i + 2 < N) ? de[i] : 0.0;
-    }
-    // adjoint, A^T = R^T L^T:
-    // z_i = g_i - ga_{i-1} z_{i-1} - de_{i-2} z_{i-2};
-    // y_i = z_i/al_i - (be_{i+1}/al_i) y_{i+1} - (ep_{i+2}/al_i) y_{i+2}
-    hp[1].bw = 2;
-    hp[1].fwd_scale = false;
-    hp[1].bwd_scale = true;
-    for (int64_t i = 0; i < N; i++) {
-      const double ia = 1.0 / al[i];
-      C(hp[1], C_S, i) = 1.0;
-      C(hp[1], C_L1, i) = (i >= 1) ? ga[i - 1] : 0.0;
-      C(hp[1], C_L2, i) = (i >= 2) ? de[i - 2] : 0.0;
-      C(hp[1], C_T, i) = ia;
-      C(hp[1], C_U1, i) = (i + 1 < N) ? be[i + 1] * ia : 0.0;
-      C(hp[1], C_U2, i) = (i + 2 < N) ? ep[i + 2] * ia : 0.0;
-    }
+    HostPlan rp, ra;
+    rp.c.assign((size_t)C_COUNT * N, 0.0);
+    ra.c.assign((size_t)C_COUNT * N, 0.0);
+    // A matrix whose reversed elimination meets a bad pivot still gets a
+    // handle; only the refined solve (which needs U' L') is then refused.
+    has_ul = make_plans(rbd, width, N, rp, ra) == 0;
+    hp[2].bw = rp.bw;
+    hp[2].fwd_scale = rp.fwd_scale;
+    hp[2].bwd_scale = rp.bwd_scale;
+    for (int k = 0; k < C_COUNT; k++)
+      for (int64_t i = 0; i < N; i++) hp[2].c[(size_t)k * N + i] = rp.c[(size_t)k * N + (N - 1 - i)];
   }
 
   // Bands with the outside entries zeroed, and their FP32 hi/lo split.
@@ -252,7 +282,7 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   cudaGetDevice(&hd->device);
   size_t bytes = 0;
   cudaError_t e = cudaSuccess;
-  for (int p = 0; p < 2 && e == cudaSuccess; p++) {
+  for (int p = 0; p < 3 && e == cudaSuccess; p++) {
     SweepPlan& sp = hd->plan[p];
     sp.bw = hp[p].bw;
     sp.fwd_scale = hp[p].fwd_scale;
@@ -283,6 +313,7 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
     return cuda_error(e, "bs_factor");
   }
   hd->device_bytes = bytes;
+  hd->has_ul = has_ul;
   {
     std::lock_guard<std::mutex> lk(g_handles_mu);
     g_handles.insert(hd);

@@ -48,11 +48,14 @@ struct bs_factor_s {
   int width;
   int64_t N;
   int device;
-  bs::SweepPlan plan[2];   // [0] primal A^{-1}, [1] adjoint A^{-T}
+  bs::SweepPlan plan[3];   // [0] primal A^{-1} (A = L U), [1] adjoint A^{-T},
+                           // [2] primal through the reversed factorisation A = U' L'
+                           //     (first sweep runs over decreasing rows)
   double* bands64;         // device, width * N, entries outside the matrix zeroed
   float* bands_hi;         // device, width * N: FP32 rounding of the bands
   float* bands_lo;         // device, width * N: FP32 rounding of (band - hi)
   size_t device_bytes;
+  bool has_ul;             // plan[2] is valid (reversed elimination met no bad pivot)
 };
 
 namespace bs {
@@ -68,9 +71,11 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info();
 
-// Launchers (sweep.cu)
+// Launchers
 bs_status launch_sweep(const SweepPlan& p, int64_t N, const void* in, void* out, bs_dtype in_t,
                        bs_dtype out_t, bs_layout layout, int64_t M, cudaStream_t st);
+bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps,
+                        cudaStream_t st);
 bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout,
                            int64_t M, double* dbands, cudaStream_t st);
 

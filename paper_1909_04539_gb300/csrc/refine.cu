@@ -1,0 +1,308 @@
+// Mixed-precision solve: FP32 storage and FP32 sweeps, one step of iterative
+// refinement with the residual r = B - A X0 evaluated to FP64 accuracy, FP64
+// solution.  One thread per system, all in one kernel.
+//
+//   pass 1 (rows up)  : w = L^{-1} B                       (FP32 sweep of A = L U)
+//   pass 2 (rows down): X0 = U^{-1} w                      (FP32)
+//                       r  = B - A X0                      (exact to ~2^-48, see below)
+//                       z  = U'^{-1} r                     (FP32 sweep of A = U' L')
+//   pass 3 (rows up)  : d  = L'^{-1} z,  X = X0 + d        (FP32 sweep, FP64 sum)
+//
+// The correction solve uses the reversed factorisation A = U' L' (the LU of
+// the row- and column-reversed matrix, computed once with the handle) so that
+// its first sweep runs over decreasing rows, right behind the backward sweep
+// that produces X0: the residual of row q is formed as soon as X0_{q-h} is
+// known.  A refinement step therefore costs one extra pass instead of two.
+//
+// Between the passes each system keeps two FP32 values per row, stored in the
+// 8-byte slot of the FP64 output X itself: {w, B} after pass 1, {X0, z} after
+// pass 2, and the FP64 solution after pass 3.
+//
+// Residual accuracy: B and X0 are FP32, each band value a = ahi + alo is the
+// FP64 band split into two FP32 numbers.  ahi * X0 is split exactly into a
+// rounded product and its FMA-computed error; the large terms B - sum ahi X0
+// are accumulated with TwoSum (error-free addition), the small terms (the
+// product and sum errors, alo * X0) in plain FP32.  So r carries an absolute
+// error of a few FP32 ulps of r itself plus ~2^-48 |A||X0| -- what one step
+// of refinement needs to bring the FP32 solution to ~1e-15 relative error for
+// well-conditioned bands.
+#include "sweep_kernels.cuh"
+
+namespace bs {
+
+template <int BW>
+struct RefineCoefs {
+  const float* lu[5];   // s, l1, l2, u1, u2 of A = L U   (l2, u2 unused when BW == 1)
+  const float* ul[5];   // s, l1, l2, u1, u2 of A = U' L'
+  const float* ahi[2 * BW + 1];
+  const float* alo[2 * BW + 1];
+};
+
+template <int BW>
+__host__ __device__ constexpr int refine_arrays() {
+  return 2 * (1 + 2 * BW) + 2 * (2 * BW + 1);
+}
+
+// r = b - sum_k (ahi_k + alo_k) x_k with error-free products and sums.
+template <int W>
+__device__ __forceinline__ float residual_row(float b, const float (&x)[W], const float (&ahi)[W],
+                                              const float (&alo)[W]) {
+  float s = b, c = 0.f;
+#pragma unroll
+  for (int k = 0; k < W; k++) {
+    const float p = __fmul_rn(ahi[k], x[k]);
+    const float e = fmaf(ahi[k], x[k], -p);  // ahi * x = p + e exactly
+    const float t = __fsub_rn(s, p);         // TwoSum(s, -p) = t + err exactly
+    const float bv = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(-p, bv));
+    s = t;
+    c = __fadd_rn(c, __fsub_rn(err, e));
+    c = fmaf(-alo[k], x[k], c);
+  }
+  return __fadd_rn(s, c);
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// FP32 B (4-byte lane rows in pass 1), 8-byte slots in passes 2 and 3; ring of
+// D slots of 8 bytes per lane.
+template <int BW, int D, bool SMEM>
+__global__ void __launch_bounds__(128)
+k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int steps) {
+  constexpr int W = 2 * BW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RefineCoefs<BW> cf = cg;
+  size_t coef_bytes = 0;
+  if (SMEM) {
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    int off = 0;
+    auto stage = [&](const float*& p) {
+      float* dst = sm + off;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = p[i];
+      p = dst;
+      off += N;
+    };
+    stage(cf.lu[0]);
+    stage(cf.lu[1]);
+    if (BW == 2) stage(cf.lu[2]);
+    stage(cf.lu[3]);
+    if (BW == 2) stage(cf.lu[4]);
+    stage(cf.ul[0]);
+    stage(cf.ul[1]);
+    if (BW == 2) stage(cf.ul[2]);
+    stage(cf.ul[3]);
+    if (BW == 2) stage(cf.ul[4]);
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+      stage(cf.ahi[k]);
+      stage(cf.alo[k]);
+    }
+    coef_bytes = align_up((size_t)off * sizeof(float), 16);
+    __syncthreads();
+  }
+  unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 8;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * 8;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    const float* pb = B + j;
+    double* px = X + j;
+    float2* ps = reinterpret_cast<float2*>(X) + j;  // the 8-byte slots, as float pairs
+
+    // ---- pass 1: w = L^{-1} B, slot <- {w, B}
+    {
+      float w1 = 0.f, w2 = 0.f;
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        if (r < N) cp_async4(ring_s + r * pitch, pb + (int64_t)r * M);
+        cp_commit();
+      }
+      int slot = 0;
+#pragma unroll 1
+      for (int i = 0; i < N; i++) {
+        cp_wait<D - 1>();
+        const float b = *reinterpret_cast<const float*>(ring + (size_t)slot * pitch);
+        if (i + D < N) cp_async4(ring_s + slot * pitch, pb + (int64_t)(i + D) * M);
+        cp_commit();
+        float w = b * cf.lu[0][i];
+        if (BW == 2) w = fmaf(-cf.lu[2][i], w2, w);
+        w = fmaf(-cf.lu[1][i], w1, w);
+        w2 = w1;
+        w1 = w;
+        ps[(int64_t)i * M] = make_float2(w, b);
+        slot = (slot + 1 == D) ? 0 : slot + 1;
+      }
+      cp_wait<0>();
+    }
+
+    // ---- pass 2: X0 = U^{-1} w; r = B - A X0; z = U'^{-1} r; slot <- {X0, z}
+    {
+      float xw[W];  // X0 of rows i .. i+2BW (rows >= N are 0)
+      float bw[BW + 1];  // B of rows i .. i+BW
+#pragma unroll
+      for (int k = 0; k < W; k++) xw[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k <= BW; k++) bw[k] = 0.f;
+      float z1 = 0.f, z2 = 0.f;
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        const int row = N - 1 - r;
+        if (row >= 0) cp_async8(ring_s + r * pitch, ps + (int64_t)row * M);
+        cp_commit();
+      }
+      int slot = 0;
+#pragma unroll 1
+      for (int i = N - 1; i >= -BW; i--) {
+        float x0 = 0.f, b = 0.f;
+        if (i >= 0) {
+          cp_wait<D - 1>();
+          const float2 wb = *reinterpret_cast<const float2*>(ring + (size_t)slot * pitch);
+          if (i - D >= 0) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i - D) * M);
+          cp_commit();
+          slot = (slot + 1 == D) ? 0 : slot + 1;
+          x0 = wb.x;
+          if (BW == 2) x0 = fmaf(-cf.lu[4][i], xw[1], x0);
+          x0 = fmaf(-cf.lu[3][i], xw[0], x0);
+          b = wb.y;
+        }
+#pragma unroll
+        for (int k = W - 1; k > 0; k--) xw[k] = xw[k - 1];
+        xw[0] = x0;
+#pragma unroll
+        for (int k = BW; k > 0; k--) bw[k] = bw[k - 1];
+        bw[0] = b;
+        const int q = i + BW;  // row whose neighbourhood x0_{q-BW..q+BW} is now complete
+        if (q < N) {
+          if (steps == 0) {
+            px[(int64_t)q * M] = (double)xw[BW];
+          } else {
+            float ah[W], al[W];
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+              ah[k] = cf.ahi[k][q];
+              al[k] = cf.alo[k][q];
+            }
+            const float r = residual_row<W>(bw[BW], xw, ah, al);
+            float z = r * cf.ul[0][q];
+            if (BW == 2) z = fmaf(-cf.ul[2][q], z2, z);
+            z = fmaf(-cf.ul[1][q], z1, z);
+            z2 = z1;
+            z1 = z;
+            ps[(int64_t)q * M] = make_float2(xw[BW], z);
+          }
+        }
+      }
+      cp_wait<0>();
+    }
+    if (steps == 0) continue;
+
+    // ---- pass 3: d = L'^{-1} z; X = X0 + d in FP64
+    {
+      float d1 = 0.f, d2 = 0.f;
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        if (r < N) cp_async8(ring_s + r * pitch, ps + (int64_t)r * M);
+        cp_commit();
+      }
+      int slot = 0;
+#pragma unroll 1
+      for (int i = 0; i < N; i++) {
+        cp_wait<D - 1>();
+        const float2 xz = *reinterpret_cast<const float2*>(ring + (size_t)slot * pitch);
+        if (i + D < N) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i + D) * M);
+        cp_commit();
+        slot = (slot + 1 == D) ? 0 : slot + 1;
+        float d = xz.y;
+        if (BW == 2) d = fmaf(-cf.ul[4][i], d2, d);
+        d = fmaf(-cf.ul[3][i], d1, d);
+        d2 = d1;
+        d1 = d;
+        px[(int64_t)i * M] = (double)xz.x + (double)d;
+      }
+      cp_wait<0>();
+    }
+  }
+}
+
+template <int BW>
+static cudaError_t launch_refine_bw(bs_handle h, const float* B, double* X, int64_t M, int steps, cudaStream_t st) {
+  constexpr int D = 16;
+  const int N = (int)h->N;
+  const int64_t n = N;
+  RefineCoefs<BW> cf{};
+  const float* lu = h->plan[0].c32;
+  const float* ul = h->plan[2].c32;
+  const int idx[5] = {C_S, C_L1, C_L2, C_U1, C_U2};
+  for (int k = 0; k < 5; k++) {
+    cf.lu[k] = lu + idx[k] * n;
+    cf.ul[k] = ul + idx[k] * n;
+  }
+  for (int k = 0; k < 2 * BW + 1; k++) {
+    cf.ahi[k] = h->bands_hi + k * n;
+    cf.alo[k] = h->bands_lo + k * n;
+  }
+  const DeviceInfo& d = device_info();
+  int tpb = 128;
+  while (tpb > 32 && M < (int64_t)2 * d.sms * tpb) tpb /= 2;
+  const size_t coef = align_up((size_t)refine_arrays<BW>() * N * sizeof(float), 16);
+  const size_t ring = (size_t)tpb * D * 8;
+  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
+  const bool smem = coef + ring <= limit;
+  const size_t bytes = (smem ? coef : 0) + ring;
+  int per_sm = (int)((228 * 1024) / (bytes + 1024));
+  if (per_sm > 2048 / tpb) per_sm = 2048 / tpb;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)d.sms * per_sm;
+  const int64_t need = (M + tpb - 1) / tpb;
+  if (grid > need) grid = need;
+  cudaError_t e;
+  if (smem) {
+    auto k = k_refine<BW, D, true>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k<<<(int)grid, tpb, bytes, st>>>(cf, N, B, X, M, steps);
+  } else {
+    auto k = k_refine<BW, D, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k<<<(int)grid, tpb, bytes, st>>>(cf, N, B, X, M, steps);
+  }
+  return cudaGetLastError();
+}
+
+bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, cudaStream_t st) {
+  if (b_t != BS_F32) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: B must be BS_F32");
+  cudaError_t e = h->width == 3 ? launch_refine_bw<1>(h, (const float*)B, X, M, steps, st)
+                                : launch_refine_bw<2>(h, (const float*)B, X, M, steps, st);
+  if (e != cudaSuccess) return cuda_error(e, "bs_solve_refine launch");
+  return BS_OK;
+}
+
+}  // namespace bs
+
+extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
+                                     int64_t M, int refine_steps, bs_stream stream) {
+  using namespace bs;
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_solve_refine: unknown handle");
+  if (!B || !X) return set_error(BS_EINVAL, "bs_solve_refine: null data pointer");
+  if (M < 1) return set_error(BS_EINVAL, "bs_solve_refine: M must be >= 1");
+  if (layout != BS_INTERLEAVED)
+    return set_error(BS_EUNSUPPORTED, "bs_solve_refine: only the interleaved layout is implemented");
+  if (refine_steps < 0 || refine_steps > 1)
+    return set_error(BS_EUNSUPPORTED, "bs_solve_refine: refine_steps must be 0 or 1");
+  if (refine_steps > 0 && !h->has_ul)
+    return set_error(BS_ESINGULAR, "bs_solve_refine: the reversed elimination of this matrix met a bad pivot");
+  if (reinterpret_cast<uintptr_t>(X) % 8 || reinterpret_cast<uintptr_t>(B) % 4)
+    return set_error(BS_EINVAL, "bs_solve_refine: misaligned pointer");
+  const char* b0 = static_cast<const char*>(B);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  const size_t nm = (size_t)h->N * (size_t)M;
+  if (b0 < x0 + nm * 8 && x0 < b0 + nm * 4) return set_error(BS_EINVAL, "bs_solve_refine: B and X overlap");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(BS_EINVAL, "bs_solve_refine: handle belongs to another device");
+  return launch_refine(h, B, b_dtype, X, M, refine_steps, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -15,29 +15,37 @@ static int64_t g_opt[BS_OPT_COUNT] = {0};
 int64_t option(int o) { return (o >= 0 && o < BS_OPT_COUNT) ? g_opt[o] : 0; }
 
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
-                        int per_thread_systems, bool strided, int blocks_per_sm) {
+                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb) {
   const DeviceInfo& d = device_info();
   LaunchShape sh{};
-  const size_t coef_bytes = (size_t)(1 + 2 * bw) * N * coef_elem;
-  const size_t tiles = strided ? (size_t)(kSweepThreads / 32) * kStRows * kStPad * coef_elem : 0;
+  if (tpb <= 0) {
+    tpb = 128;
+    while (tpb > 32 && threads_needed < (int64_t)2 * d.sms * tpb) tpb /= 2;
+  }
+  sh.threads = tpb;
+  const size_t coef_bytes = align_up((size_t)(1 + 2 * bw) * N * coef_elem, 16);
+  const size_t extra = extra_smem_fixed + extra_smem_per_thread * (size_t)tpb;
   const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
-  sh.smem_coefs = coef_bytes + tiles <= limit;
+  sh.smem_coefs = coef_bytes + extra <= limit;
   sh.smem = sh.smem_coefs ? coef_bytes : 0;
-  const int64_t blocks_needed = (threads_needed + kSweepThreads - 1) / kSweepThreads;
-  const size_t per_block_smem = sh.smem + tiles + 1024;
+  const int64_t blocks_needed = (threads_needed + tpb - 1) / tpb;
+  const size_t per_block_smem = sh.smem + extra + 1024;
   int by_smem = (int)((228 * 1024) / per_block_smem);
-  if (blocks_per_sm <= 0) blocks_per_sm = (int)(option(BS_OPT_BLOCKS_PER_SM) > 0 ? option(BS_OPT_BLOCKS_PER_SM) : 8);
-  int per_sm = by_smem < blocks_per_sm ? by_smem : blocks_per_sm;
+  int by_threads = 2048 / tpb;
+  int per_sm = (int)(option(BS_OPT_BLOCKS_PER_SM) > 0 ? option(BS_OPT_BLOCKS_PER_SM) : 32);
+  if (per_sm > by_smem) per_sm = by_smem;
+  if (per_sm > by_threads) per_sm = by_threads;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)d.sms * per_sm;
-  // Bound the forward values in flight: each thread keeps N rows of its
-  // systems between the sweeps.
-  int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
-  if (budget <= 0) budget = (int64_t)d.l2_bytes / 2;
-  const int64_t per_block = (int64_t)kSweepThreads * per_thread_systems * N * (int64_t)spill_elem;
-  int64_t cap = per_block > 0 ? budget / per_block : grid;
-  if (cap < d.sms) cap = d.sms;
-  if (grid > cap) grid = cap;
+  // Optional bound on the forward values in flight (each thread keeps N rows
+  // of its systems between the sweeps); off by default.
+  const int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
+  if (budget > 0) {
+    const int64_t per_block = (int64_t)tpb * per_thread_systems * N * (int64_t)spill_elem;
+    int64_t cap = per_block > 0 ? budget / per_block : grid;
+    if (cap < d.sms) cap = d.sms;
+    if (grid > cap) grid = cap;
+  }
   if (grid > blocks_needed) grid = blocks_needed;
   if (grid < 1) grid = 1;
   sh.grid = (int)grid;

@@ -154,6 +154,48 @@ __device__ __forceinline__ void bwd_step(const Coefs<C>& cf, int i, C (&f)[V], C
   }
 }
 
+// ------------------------------------------------------ async row copies
+
+// Per-lane rings of rows in shared memory, filled with cp.async.  Each lane
+// copies and later reads only its own bytes, so no barrier is needed: a lane
+// waits for its own copy groups (cp.async.wait_group), which complete in
+// order.  Slot r of lane t sits at ring + (r * blockDim.x + t) * SLOT, so a
+// warp reads 32 * SLOT contiguous bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// 16 bytes through L2 only (.cg): also safe for data this thread stored
+// earlier in the same kernel.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+// 8 bytes through L1 (.ca); used only for inputs the kernel never writes.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// One lane-row copy of V elements of S (V * sizeof(S) is 8, 16 or 32 bytes).
+template <typename S, int V>
+__device__ __forceinline__ void copy_row(uint32_t dst, const S* src) {
+  constexpr int bytes = V * (int)sizeof(S);
+  static_assert(bytes == 8 || bytes == 16 || bytes == 32, "lane row must be 8, 16 or 32 bytes");
+  if constexpr (bytes == 8) {
+    cp_async8(dst, src);
+  } else if constexpr (bytes == 16) {
+    cp_async16(dst, src);
+  } else {
+    cp_async16(dst, src);
+    cp_async16(dst + 16, reinterpret_cast<const unsigned char*>(src) + 16);
+  }
+}
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 // ---------------------------------------------------- interleaved layout
 
 // Row i of system j at [i*M + j].  Thread g owns systems [g*V, g*V + V).
@@ -222,6 +264,76 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (top - 2 * U >= 0) load_bwd(a, top - 2 * U);
       run_bwd(b, top - U);
     }
+  }
+}
+
+
+// Interleaved layout, deep-pipelined variant for V > 1.  Each lane streams
+// its rows through a private ring of D slots (16 bytes each): D rows of
+// input are in flight per lane while the recurrence runs.  The forward values
+// of the last D rows stay in the ring, so the backward sweep starts without
+// reloading them; the earlier ones go to the output buffer and are streamed
+// back through the same ring.
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+  static_assert(V * sizeof(Sout) == 16, "output lane row must be 16 bytes");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+  unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * 16;
+  const int64_t ngroups = M / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    const Sin* pin = in + g * V;
+    Sout* pout = out + g * V;
+    C r1[V], r2[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    // forward sweep: rows 0..D-1 requested up front, row i + D after row i
+#pragma unroll 1
+    for (int r = 0; r < D; r++) {
+      if (r < N) copy_row<Sin, V>(ring_s + r * pitch, pin + (int64_t)r * M);
+      cp_commit();
+    }
+    int slot = 0;
+#pragma unroll 1
+    for (int i = 0; i < N; i++) {
+      cp_wait<D - 1>();
+      unsigned char* sp = ring + (size_t)slot * pitch;
+      C f[V];
+      IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(sp), f);
+      fwd_step<BW, ADJ, C, V>(cf, i, f, r1, r2);
+      if (i + D < N) {
+        IO<Sout, C, V>::store(pout + (int64_t)i * M, f);
+        copy_row<Sin, V>(ring_s + slot * pitch, pin + (int64_t)(i + D) * M);
+      } else {
+        IO<Sout, C, V>::store(reinterpret_cast<Sout*>(sp), f);  // tail stays on chip
+      }
+      cp_commit();
+      slot = (slot + 1 == D) ? 0 : slot + 1;
+    }
+    // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
+    // into the slot row i frees
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    const int tail = N - D;
+    slot = (N - 1) % D;
+#pragma unroll 1
+    for (int i = N - 1; i >= 0; i--) {
+      if (i < tail) cp_wait<D - 1>();
+      unsigned char* sp = ring + (size_t)slot * pitch;
+      C f[V];
+      IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(sp), f);
+      bwd_step<BW, ADJ, C, V>(cf, i, f, r1, r2);
+      IO<Sout, C, V>::store(pout + (int64_t)i * M, f);
+      if (i - D >= 0) copy_row<Sout, V>(ring_s + slot * pitch, pout + (int64_t)(i - D) * M);
+      cp_commit();
+      slot = (slot == 0) ? D - 1 : slot - 1;
+    }
+    cp_wait<0>();
   }
 }
 
@@ -307,37 +419,61 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 
 struct LaunchShape {
   int grid;
-  size_t smem;
+  int threads;     // per CTA
+  size_t smem;     // coefficient bytes staged in shared memory (0 if read from global)
   bool smem_coefs;
 };
 
 // Chooses the grid and shared memory of one sweep launch.  The grid is
 // persistent (each thread loops over groups of systems); it is capped so that
 // the forward values of all systems in flight take at most half of L2.
+// extra_smem_per_thread: shared bytes each thread needs beyond the
+// coefficients (ring slots); extra_smem_fixed: per CTA (transpose tiles).
+// tpb = 0 lets the policy pick 32, 64 or 128 threads per CTA so that small
+// batches still spread over every SM.
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
-                        int per_thread_systems, bool strided, int blocks_per_sm);
+                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb);
 
 template <int BW, bool ADJ, typename C, typename Sin, typename Sout, int V>
 cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
-  constexpr int U = sizeof(C) == 8 ? 8 : 8;
+  constexpr int U = 8;
   const int64_t groups = M / V;
-  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, false, 0);
-  if (sh.smem_coefs) {
-    auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-    if (e != cudaSuccess) return e;
-    k<<<sh.grid, kSweepThreads, sh.smem, st>>>(cf, N, in, out, M);
+  if constexpr (V > 1) {
+    // pipelined kernel: ring of kRingRows 16-byte slots per lane
+    constexpr int D = 16;
+    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, D * 16, 0, 0);
+    const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
+    if (sh.smem_coefs) {
+      auto k = k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
+    } else {
+      auto k = k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
+    }
+    return cudaGetLastError();
   } else {
-    k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U><<<sh.grid, kSweepThreads, 0, st>>>(cf, N, in, out, M);
+    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, 0, 0, 0);
+    if (sh.smem_coefs) {
+      auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      if (e != cudaSuccess) return e;
+      k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, N, in, out, M);
+    } else {
+      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U><<<sh.grid, sh.threads, 0, st>>>(cf, N, in, out, M);
+    }
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
 }
 
 template <int BW, bool ADJ, typename C, typename Sin, typename Sout>
 cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
   const int64_t threads = ((M + 31) / 32) * 32;
-  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, true, 0);
   const size_t tiles = (size_t)(kSweepThreads / 32) * kStRows * kStPad * sizeof(C);
+  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads);
   if (sh.smem_coefs) {
     auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
