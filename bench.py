@@ -260,6 +260,7 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = run_e2e(bs, f, N, M, st, args, world)
+    serving = None if args.no_serving else run_serving(bs)
 
     clocks = clk.summary()
     line = {
@@ -276,6 +277,7 @@ def run_ours(args):
                   for n, p in paths.items()},
         "roofline": roof,
         "e2e": e2e,
+        "serving": serving,
         "gpu_launches": 4 * args.steps,  # f64 solve, refine solve, adjoint, band gradient
         "clocks": clocks,
     }
@@ -287,6 +289,95 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=400, load=0.7, budget=24 << 30, seed=0):
+    """Serving workload: 256 resident LHS (tri/penta 50/50, N log-uniform in
+    [64, 4096], diagonally dominant), requests with M log-uniform in
+    [1, 65536], FP64 or FP32-stored + refinement 50/50, RHS ~ U(-1,1) in pinned
+    host memory, results copied back to host memory.  First a closed burst
+    (all requests queued at once) gives the saturation rate, then a Poisson
+    stream at `load` times that rate gives p50/p99 latency (submission to
+    host-observed completion) at sustained load."""
+    import torch
+    import synth
+    from paper_1909_04539_gb300 import serve as sv
+
+    specs = [synth.serving_lhs(i) for i in range(n_lhs)]
+    facs = [bs.Factor(sp.bands) for sp in specs]
+    reqs = synth.serving_requests(n_burst + n_poisson, rate_hz=1.0, n_lhs=n_lhs, seed=seed)
+    max_nm = max(specs[r.lhs_id].N * r.M for r in reqs)
+    g = torch.Generator().manual_seed(seed)
+    pool = (torch.rand(max_nm + 4096, dtype=torch.float64, generator=g) * 2 - 1).pin_memory()
+    pool32 = pool.float().pin_memory()
+    out = torch.empty(max_nm, dtype=torch.float64).pin_memory()
+    rng = np.random.default_rng(seed + 1)
+
+    def views(r):
+        sp = specs[r.lhs_id]
+        nm = sp.N * r.M
+        o = int(rng.integers(0, 4096))
+        src = pool32 if r.refine else pool
+        return src[o:o + nm].view(sp.N, r.M), out[:nm].view(sp.N, r.M)
+
+    srv = sv.Server(budget, n_streams=4)
+    # warm-up
+    for r in reqs[:8]:
+        B, X = views(r)
+        srv.wait(srv.submit(facs[r.lhs_id], B, X, sv.F32_REFINE if r.refine else sv.F64), 120)
+    # saturation: closed burst
+    burst = reqs[:n_burst]
+    t0 = time.perf_counter()
+    ids = []
+    for r in burst:
+        B, X = views(r)
+        ids.append(srv.submit(facs[r.lhs_id], B, X, sv.F32_REFINE if r.refine else sv.F64))
+    for i in ids:
+        srv.wait(i, 600)
+    t_burst = time.perf_counter() - t0
+    unk_burst = sum(specs[r.lhs_id].N * r.M for r in burst)
+    bytes_burst = sum(specs[r.lhs_id].N * r.M * (12 if r.refine else 16) for r in burst)
+    sat_rps = n_burst / t_burst
+    for i in ids:
+        srv.release(i)
+    # sustained: Poisson at load * saturation
+    rate = load * sat_rps
+    stream = reqs[n_burst:]
+    gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, len(stream))
+    ids = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for r, gap in zip(stream, gaps):
+        t_next += gap
+        while True:
+            d = t_next - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(min(d, 0.0005))
+        B, X = views(r)
+        ids.append(srv.submit(facs[r.lhs_id], B, X, sv.F32_REFINE if r.refine else sv.F64))
+    lat = []
+    for i in ids:
+        srv.wait(i, 600)
+        lat.append(srv.poll(i)[1])
+    t_stream = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    unk_stream = sum(specs[r.lhs_id].N * r.M for r in stream)
+    return {
+        "workload": "256 resident LHS (tri/penta, N log-uniform [64,4096]); M log-uniform [1,65536]; "
+                    "FP64 or FP32+refine 50/50; host (pinned) RHS in, host results out; Poisson arrivals",
+        "saturation": {"requests_per_s": sat_rps, "unknowns_per_s": unk_burst / t_burst,
+                       "host_device_gbs": bytes_burst / t_burst / 1e9, "requests": n_burst},
+        "sustained": {"offered_requests_per_s": rate, "load_of_saturation": load, "requests": len(stream),
+                      "achieved_requests_per_s": len(stream) / t_stream, "unknowns_per_s": unk_stream / t_stream,
+                      "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                      "mean_ms": float(lat_ms.mean())},
+        "server": {"hbm_budget_bytes": budget, "streams": 4, "batches": st["batches"],
+                   "max_batch_requests": st["max_batch_requests"],
+                   "max_concurrent_batches": st["max_concurrent_batches"]},
+    }
 
 
 def time_alone(fn, st, reps=50, warm=3) -> float:
@@ -465,6 +556,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -128,6 +128,26 @@ bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* 
 bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M,
                            const void* X, double* dbands, bs_stream stream);
 
+/* One Peaceman-Rachford ADI half-step for u_t = u_xx + u_yy on an ny x nx
+ * grid stored row-major (U[y*nx + x], device), homogeneous Dirichlet
+ * boundaries (zero outside the grid):
+ *   implicit_axis 0: S out = (I + r d2/dy2) U, S solved along x for every row
+ *                    y (each row is a system of nx unknowns; h->N == nx);
+ *   implicit_axis 1: S out = (I + r d2/dx2) U, S solved
+ *                    along y for every column x (interleaved, M = nx;
+ *                    h->N == ny),
+ * where S is the handle's shared LHS (for the heat equation the tridiagonal
+ * I - r d2, one copy for every grid line -- the ADI use the paper's Sec. 1
+ * names) and d2 the second difference.  The explicit operator is applied
+ * while the forward sweep loads its rows.  adjoint = 1 applies the transpose
+ * of the map U -> out instead: out = S^{-T} (I + r d2) U (the explicit
+ * operator is symmetric and commutes with S, which acts on the other axis).
+ * dtype BS_F64 or BS_F32 for both U and out; U and out must not overlap
+ * (out also holds the forward-sweep values).  Not in the paper beyond the
+ * motivation: the paper benchmarks 1D problems only. */
+bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_dtype dtype, int64_t ny, int64_t nx,
+                          double r, int implicit_axis, int adjoint, bs_stream stream);
+
 /* Band-gradient reduction alone, for a caller that already holds
  * GB = A^{-T} (dL/dX) (e.g. from bs_solve_adjoint without X):
  *   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - width/2, j]
@@ -136,6 +156,64 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  * double[width*N], overwritten. */
 bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout,
                        int64_t M, double* dbands, bs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Request server (not in the paper): continuous batching of solves with many
+ * factorised LHS resident on one GPU.
+ *
+ * A server reserves `hbm_budget_bytes` of device memory as an arena and runs
+ * a worker thread.  Each request names a resident handle, a host input B and
+ * a host output X (both must stay valid until the request has finished; pinned
+ * host memory gives the fastest copies):
+ *   mode BS_SERVE_F64        : B double[N*M], X double[N*M] (X may equal B);
+ *                              plain FP64 solve (as bs_solve); arena N*M*8 B.
+ *   mode BS_SERVE_F32_REFINE : B float[N*M], X double[N*M]; mixed-precision
+ *                              solve with one refinement step (as
+ *                              bs_solve_refine); arena N*M*12 B.
+ * Layout is interleaved.  The worker admits queued requests in arrival order
+ * while their arena bytes fit, puts every newly admitted request into one
+ * batch and runs the batch on one of `n_streams` streams: host-to-device
+ * copies, one replay of a captured CUDA graph (work-list copy + one grouped
+ * persistent launch for all requests of the batch), device-to-host copies.
+ * Batches overlap across streams; requests arriving meanwhile join the next
+ * batch as soon as memory and a stream are free.  A request's result is
+ * bitwise the same whatever else shares its batch (one lane per system, the
+ * arithmetic of the standalone solves).
+ * Request states: 0 queued, 1 running, 2 done, 3 cancelled, 4 failed.
+ * Latency = host submission to host-observed completion.
+ * ---------------------------------------------------------------------- */
+typedef struct bs_server_s* bs_server;
+enum { BS_SERVE_F64 = 0, BS_SERVE_F32_REFINE = 1 };
+
+/* Creates a server on the current device (1 <= n_streams <= 16).  Fails with
+ * BS_ENOMEM if the budget cannot be reserved. */
+bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* out);
+/* Stops the worker (in-flight batches finish first) and frees everything.
+ * Requests still queued are dropped. */
+bs_status bs_server_destroy(bs_server s);
+/* Queues one request; *request_id identifies it.  BS_ENOMEM if the request
+ * alone exceeds the budget (it could never be admitted); 1 <= M <= 524288. */
+bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* host_X, int mode, int64_t M,
+                           int64_t* request_id);
+/* Non-blocking state query; *latency_s is -1 until the request has finished. */
+bs_status bs_server_poll(bs_server s, int64_t request_id, int* state, double* latency_s);
+/* Blocks until the request has finished or `timeout_s` passed (BS_ETIMEOUT). */
+bs_status bs_server_wait(bs_server s, int64_t request_id, double timeout_s, int* state);
+/* Cancels a request that has not been admitted yet (BS_EINVAL otherwise). */
+bs_status bs_server_cancel(bs_server s, int64_t request_id);
+/* Forgets a finished request (its id becomes unknown). */
+bs_status bs_server_release(bs_server s, int64_t request_id);
+/* Stops (paused != 0) or resumes admitting new batches; running batches
+ * continue.  For draining and for tests. */
+bs_status bs_server_pause(bs_server s, int paused);
+/* Host-side fault injection for tests: the queued request fails at admission
+ * as a failed device copy would make it fail (its memory is released, the
+ * other requests are unaffected). */
+bs_status bs_server_fail_on_admit(bs_server s, int64_t request_id);
+/* Counters, first n of: batches, completed, failed, queued, running, arena
+ * bytes in use, peak arena bytes, arena size, most requests in one batch,
+ * most batches in flight at once.  Returns BS_ECUDA if a batch ever failed. */
+bs_status bs_server_stats(bs_server s, int64_t* out, int n);
 
 /* Launch tuning knobs (process-wide; 0 restores the default).
  *  BS_OPT_INFLIGHT_BYTES: upper bound on the bytes of forward-sweep values

@@ -2,6 +2,6 @@
 (arXiv:1909.04539).  The compute path is the CUDA library ``libbsolve.so``
 behind the C ABI in ``include/bsolve.h``; this package only marshals torch
 tensors into it."""
-from .api import (Factor, SolveFn, band_grad, solve, solve_adjoint, solve_bf16, solve_refine,  # noqa: F401
+from .api import (ADIHalfStepFn, Factor, SolveFn, adi_halfstep, band_grad, solve, solve_adjoint, solve_bf16, solve_refine,  # noqa: F401
                   set_option, lhs_bytes, measure_fp64_rate)
 from ._lib import BsolveError  # noqa: F401

@@ -22,7 +22,18 @@ SIGNATURES = {
     "bs_solve_bf16": (i32, [vp, vp, vp, i32, i64, vp]),
     "bs_solve_refine": (i32, [vp, vp, i32, vp, i32, i64, i32, vp]),
     "bs_solve_adjoint": (i32, [vp, vp, i32, i32, i64, vp, vp, vp]),
+    "bs_adi_halfstep": (i32, [vp, vp, vp, i32, i64, i64, ctypes.c_double, i32, i32, vp]),
     "bs_band_grad": (i32, [vp, vp, vp, i32, i32, i64, vp, vp]),
+    "bs_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(vp)]),
+    "bs_server_destroy": (i32, [vp]),
+    "bs_server_submit": (i32, [vp, vp, vp, vp, i32, i64, ctypes.POINTER(i64)]),
+    "bs_server_poll": (i32, [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]),
+    "bs_server_wait": (i32, [vp, i64, ctypes.c_double, ctypes.POINTER(i32)]),
+    "bs_server_cancel": (i32, [vp, i64]),
+    "bs_server_release": (i32, [vp, i64]),
+    "bs_server_pause": (i32, [vp, i32]),
+    "bs_server_fail_on_admit": (i32, [vp, i64]),
+    "bs_server_stats": (i32, [vp, ctypes.POINTER(i64), i32]),
     "bs_set_option": (i32, [i32, i64]),
     "bs_measure_fp64_rate": (i32, [dp, vp]),
     "bs_last_error": (ctypes.c_char_p, []),

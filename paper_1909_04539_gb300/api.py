@@ -185,6 +185,43 @@ def band_grad(f: Factor, GB: torch.Tensor, X: torch.Tensor, layout: str = "inter
     return dbands
 
 
+def adi_halfstep(f: Factor, u: torch.Tensor, r: float, implicit_axis: int, out: torch.Tensor | None = None,
+                 adjoint: bool = False, stream=None) -> torch.Tensor:
+    """One Peaceman-Rachford half-step on the (ny, nx) field u (row-major,
+    Dirichlet 0 outside): axis 0 solves along x with the explicit operator
+    along y, axis 1 the other way round.  ``f`` factorises the implicit LHS
+    (e.g. I - r d2 of the grid length along that axis).  ``adjoint`` applies
+    the transposed map."""
+    if u.dim() != 2 or not u.is_contiguous() or not u.is_cuda or u.device != f.device:
+        raise ValueError("u must be a contiguous 2-D CUDA tensor on the factor's device")
+    if u.dtype not in (torch.float64, torch.float32):
+        raise ValueError("u must be float64 or float32")
+    ny, nx = u.shape
+    if out is None:
+        out = torch.empty_like(u)
+    if out.shape != u.shape or out.dtype != u.dtype or not out.is_contiguous() or out.device != u.device:
+        raise ValueError("out must match u")
+    check(lib().bs_adi_halfstep(f.handle, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                _DTYPE[u.dtype], ny, nx, float(r), int(implicit_axis), int(bool(adjoint)),
+                                _stream(stream)), "bs_adi_halfstep")
+    return out
+
+
+class ADIHalfStepFn(torch.autograd.Function):
+    """out = S^{-1} E u for one ADI half-step, differentiable in u; the
+    backward pass is the transposed half-step (adjoint sweeps)."""
+
+    @staticmethod
+    def forward(ctx, u, factor, r, implicit_axis):
+        ctx.factor, ctx.r, ctx.axis = factor, r, implicit_axis
+        return adi_halfstep(factor, u.detach().contiguous(), r, implicit_axis)
+
+    @staticmethod
+    def backward(ctx, g):
+        gu = adi_halfstep(ctx.factor, g.detach().contiguous(), ctx.r, ctx.axis, adjoint=True)
+        return gu, None, None, None
+
+
 class SolveFn(torch.autograd.Function):
     """X = A^{-1} B with gradients for B and for the band entries of A.
 

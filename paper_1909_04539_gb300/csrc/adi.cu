@@ -1,0 +1,212 @@
+// Peaceman-Rachford ADI half-step for u_t = u_xx + u_yy on a 2D grid
+// u[y * nx + x] with homogeneous Dirichlet boundaries (zero outside):
+//   implicit along x:  S_x out = E_y u,   S_x = the factorised LHS along x,
+//                                        E_y = I + r d2/dy2 (second difference)
+//   implicit along y:  S_y out = E_x u.
+// The shared LHS (for the heat equation I - r d2, one tridiagonal copy for all
+// grid lines; the paper's motivation, Sec. 1) is the handle.  The explicit
+// operator acts across systems, so it is applied while the forward sweep loads
+// its rows (one neighbour on each side), and the result goes to a separate
+// output buffer: the sweep cannot overwrite u in place because neighbouring
+// systems still read it.
+//
+// Adjoint: for the map u -> S^{-1} E u the transpose is E^T S^{-T}.  E and S
+// act on different axes and therefore commute, and E is symmetric, so the
+// adjoint is the same fused step with the adjoint sweep coefficients.
+//
+// Implicit along y: system j = column x, row i = y, at u[i * nx + j]
+//   (interleaved, M = nx).  Implicit along x: system j = row y, row i = x, at
+//   u[j * nx + i] (system-contiguous); a warp moves 32 rows of 34 systems (its
+//   32 plus one neighbour each side) through a shared-memory tile.
+#include "sweep_kernels.cuh"
+
+namespace bs {
+
+// ----------------------------------------------------- implicit along y
+
+template <int BW, bool ADJ, bool SMEM, typename C>
+__global__ void __launch_bounds__(kSweepThreads)
+k_adi_il(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    const C* pu = u + j;
+    C* po = out + j;
+    const bool has_l = j > 0, has_r = j + 1 < M;
+    C r1[1] = {C(0)}, r2[1] = {C(0)};
+    constexpr int U = 8;
+#pragma unroll 1
+    for (int i0 = 0; i0 < N; i0 += U) {
+      C c[U], l[U], rr[U];
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (i0 + q < N) {
+          const int64_t o = (int64_t)(i0 + q) * M;
+          c[q] = pu[o];
+          l[q] = has_l ? pu[o - 1] : C(0);
+          rr[q] = has_r ? pu[o + 1] : C(0);
+        }
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (i0 + q < N) {
+          C f[1] = {c[q] + r * (l[q] - C(2) * c[q] + rr[q])};
+          fwd_step<BW, ADJ, C, 1>(cf, i0 + q, f, r1, r2);
+          po[(int64_t)(i0 + q) * M] = f[0];
+        }
+    }
+    r1[0] = r2[0] = C(0);
+#pragma unroll 1
+    for (int top = N - 1; top >= 0; top -= U) {
+      C w[U];
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (top - q >= 0) w[q] = po[(int64_t)(top - q) * M];
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (top - q >= 0) {
+          C f[1] = {w[q]};
+          bwd_step<BW, ADJ, C, 1>(cf, top - q, f, r1, r2);
+          po[(int64_t)(top - q) * M] = f[0];
+        }
+    }
+  }
+}
+
+// ----------------------------------------------------- implicit along x
+
+constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
+constexpr int kAdiWarpTile = kStRows * kAdiTile + kStRows * kStPad;  // input tile + output tile
+
+template <int BW, bool ADJ, bool SMEM, typename C>
+__global__ void __launch_bounds__(kSweepThreads)
+k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smc = reinterpret_cast<C*>(smem_raw);
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kSweepThreads / 32;
+  C* tin = smc + (SMEM ? coef_arrays<BW>() * N : 0) + warp * kAdiWarpTile;
+  C* tout = tin + kStRows * kAdiTile;
+  const int64_t nwg = (M + 31) / 32;
+  for (int64_t wg = (int64_t)blockIdx.x * kWarps + warp; wg < nwg; wg += (int64_t)gridDim.x * kWarps) {
+    const int64_t j0 = wg * 32;
+    const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
+    const bool mine = lane < nsys;
+    C r1[1] = {C(0)}, r2[1] = {C(0)};
+    // forward sweep with the explicit operator applied on load
+    for (int c0 = 0; c0 < N; c0 += kStRows) {
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      // input tile column s + 1 holds system j0 + s, s = -1 .. nsys
+      if (lane < rows)
+        for (int s = -1; s <= nsys; s++) {
+          const int64_t jj = j0 + s;
+          tin[lane * kAdiTile + s + 1] = (jj >= 0 && jj < M) ? u[jj * (int64_t)N + c0 + lane] : C(0);
+        }
+      __syncwarp();
+      if (mine)
+        for (int q = 0; q < rows; q++) {
+          const C* t = tin + q * kAdiTile + lane;
+          C f[1] = {t[1] + r * (t[0] - C(2) * t[1] + t[2])};
+          fwd_step<BW, ADJ, C, 1>(cf, c0 + q, f, r1, r2);
+          tout[q * kStPad + lane] = f[0];
+        }
+      __syncwarp();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
+      __syncwarp();
+    }
+    // backward sweep, chunks in decreasing order, through the output tile
+    r1[0] = r2[0] = C(0);
+    const int last = ((N - 1) / kStRows) * kStRows;
+    for (int c0 = last; c0 >= 0; c0 -= kStRows) {
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) tout[lane * kStPad + s] = out[(j0 + s) * (int64_t)N + c0 + lane];
+      __syncwarp();
+      if (mine)
+        for (int q = rows - 1; q >= 0; q--) {
+          C f[1] = {tout[q * kStPad + lane]};
+          bwd_step<BW, ADJ, C, 1>(cf, c0 + q, f, r1, r2);
+          tout[q * kStPad + lane] = f[0];
+        }
+      __syncwarp();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
+      __syncwarp();
+    }
+  }
+}
+
+template <int BW, bool ADJ, typename C>
+static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int64_t M, C r, int axis,
+                              cudaStream_t st) {
+  const C* base;
+  if constexpr (sizeof(C) == 8)
+    base = reinterpret_cast<const C*>(p.c64);
+  else
+    base = reinterpret_cast<const C*>(p.c32);
+  const Coefs<C> cf = coefs_of<C>(base, N);
+  if (axis == 1) {
+    const LaunchShape sh = sweep_shape(BW, N, M, sizeof(C), sizeof(C), 1, 0, 0, 0);
+    auto k = sh.smem_coefs ? k_adi_il<BW, ADJ, true, C> : k_adi_il<BW, ADJ, false, C>;
+    if (sh.smem_coefs) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, N, u, out, M, r);
+  } else {
+    const size_t tiles = (size_t)(kSweepThreads / 32) * kAdiWarpTile * sizeof(C);
+    const int64_t threads = ((M + 31) / 32) * 32;
+    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, 0, tiles, kSweepThreads);
+    auto k = sh.smem_coefs ? k_adi_st<BW, ADJ, true, C> : k_adi_st<BW, ADJ, false, C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
+    if (e != cudaSuccess) return e;
+    k<<<sh.grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, u, out, M, r);
+  }
+  return cudaGetLastError();
+}
+
+template <typename C>
+static cudaError_t dispatch_adi(bs_handle h, int N, const C* u, C* out, int64_t M, C r, int axis, bool adj,
+                                cudaStream_t st) {
+  const SweepPlan& p = h->plan[adj ? 1 : 0];
+  if (h->width == 3)
+    return adj ? launch_adi<1, true, C>(p, N, u, out, M, r, axis, st)
+               : launch_adi<1, false, C>(p, N, u, out, M, r, axis, st);
+  return adj ? launch_adi<2, true, C>(p, N, u, out, M, r, axis, st)
+             : launch_adi<2, false, C>(p, N, u, out, M, r, axis, st);
+}
+
+}  // namespace bs
+
+extern "C" bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_dtype dtype, int64_t ny, int64_t nx,
+                                     double r, int implicit_axis, int adjoint, bs_stream stream) {
+  using namespace bs;
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_adi_halfstep: unknown handle");
+  if (!U || !out) return set_error(BS_EINVAL, "bs_adi_halfstep: null data pointer");
+  if (ny < 1 || nx < 1) return set_error(BS_EINVAL, "bs_adi_halfstep: empty grid");
+  if (implicit_axis != 0 && implicit_axis != 1) return set_error(BS_EINVAL, "bs_adi_halfstep: axis must be 0 or 1");
+  if (adjoint != 0 && adjoint != 1) return set_error(BS_EINVAL, "bs_adi_halfstep: adjoint must be 0 or 1");
+  const int64_t N = implicit_axis == 0 ? nx : ny;
+  const int64_t M = implicit_axis == 0 ? ny : nx;
+  if (N != h->N)
+    return set_error(BS_EINVAL, "bs_adi_halfstep: the handle's N must equal the grid length along the implicit axis");
+  if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_adi_halfstep: dtype must be F64 or F32");
+  const size_t es = dtype == BS_F64 ? 8 : 4;
+  const char* a = static_cast<const char*>(U);
+  const char* b = static_cast<const char*>(out);
+  const size_t n = (size_t)ny * (size_t)nx * es;
+  if (a < b + n && b < a + n) return set_error(BS_EINVAL, "bs_adi_halfstep: U and out overlap");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(BS_EINVAL, "bs_adi_halfstep: handle belongs to another device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (dtype == BS_F64)
+    e = dispatch_adi<double>(h, (int)N, (const double*)U, (double*)out, M, r, implicit_axis, adjoint != 0, st);
+  else
+    e = dispatch_adi<float>(h, (int)N, (const float*)U, (float*)out, M, (float)r, implicit_axis, adjoint != 0, st);
+  if (e != cudaSuccess) return cuda_error(e, "bs_adi_halfstep launch");
+  return BS_OK;
+}

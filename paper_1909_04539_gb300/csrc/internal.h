@@ -8,6 +8,12 @@
 
 #include "../../include/bsolve.h"
 
+#ifdef __CUDACC__
+#define BS_HD __host__ __device__
+#else
+#define BS_HD
+#endif
+
 namespace bs {
 
 // Coefficients of one sweep pair, each an array of N values.  Every solve of
@@ -37,7 +43,7 @@ struct SweepPlan {
 };
 
 template <typename C>
-inline Coefs<C> coefs_of(const C* base, int64_t N) {
+BS_HD inline Coefs<C> coefs_of(const C* base, int64_t N) {
   return Coefs<C>{base + C_S * N, base + C_L1 * N, base + C_L2 * N,
                   base + C_T * N, base + C_U1 * N, base + C_U2 * N};
 }

@@ -26,41 +26,9 @@
 // error of a few FP32 ulps of r itself plus ~2^-48 |A||X0| -- what one step
 // of refinement needs to bring the FP32 solution to ~1e-15 relative error for
 // well-conditioned bands.
-#include "sweep_kernels.cuh"
+#include "refine_math.cuh"
 
 namespace bs {
-
-template <int BW>
-struct RefineCoefs {
-  const float* lu[5];   // s, l1, l2, u1, u2 of A = L U   (l2, u2 unused when BW == 1)
-  const float* ul[5];   // s, l1, l2, u1, u2 of A = U' L'
-  const float* ahi[2 * BW + 1];
-  const float* alo[2 * BW + 1];
-};
-
-template <int BW>
-__host__ __device__ constexpr int refine_arrays() {
-  return 2 * (1 + 2 * BW) + 2 * (2 * BW + 1);
-}
-
-// r = b - sum_k (ahi_k + alo_k) x_k with error-free products and sums.
-template <int W>
-__device__ __forceinline__ float residual_row(float b, const float (&x)[W], const float (&ahi)[W],
-                                              const float (&alo)[W]) {
-  float s = b, c = 0.f;
-#pragma unroll
-  for (int k = 0; k < W; k++) {
-    const float p = __fmul_rn(ahi[k], x[k]);
-    const float e = fmaf(ahi[k], x[k], -p);  // ahi * x = p + e exactly
-    const float t = __fsub_rn(s, p);         // TwoSum(s, -p) = t + err exactly
-    const float bv = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(-p, bv));
-    s = t;
-    c = __fadd_rn(c, __fsub_rn(err, e));
-    c = fmaf(-alo[k], x[k], c);
-  }
-  return __fadd_rn(s, c);
-}
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
@@ -127,11 +95,7 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
         const float b = *reinterpret_cast<const float*>(ring + (size_t)slot * pitch);
         if (i + D < N) cp_async4(ring_s + slot * pitch, pb + (int64_t)(i + D) * M);
         cp_commit();
-        float w = b * cf.lu[0][i];
-        if (BW == 2) w = fmaf(-cf.lu[2][i], w2, w);
-        w = fmaf(-cf.lu[1][i], w1, w);
-        w2 = w1;
-        w1 = w;
+        const float w = refine_fwd<BW>(cf, i, b, w1, w2);
         ps[(int64_t)i * M] = make_float2(w, b);
         slot = (slot + 1 == D) ? 0 : slot + 1;
       }
@@ -163,9 +127,7 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
           if (i - D >= 0) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i - D) * M);
           cp_commit();
           slot = (slot + 1 == D) ? 0 : slot + 1;
-          x0 = wb.x;
-          if (BW == 2) x0 = fmaf(-cf.lu[4][i], xw[1], x0);
-          x0 = fmaf(-cf.lu[3][i], xw[0], x0);
+          x0 = refine_bwd<BW>(cf, i, wb.x, xw);
           b = wb.y;
         }
 #pragma unroll
@@ -179,18 +141,7 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
           if (steps == 0) {
             px[(int64_t)q * M] = (double)xw[BW];
           } else {
-            float ah[W], al[W];
-#pragma unroll
-            for (int k = 0; k < W; k++) {
-              ah[k] = cf.ahi[k][q];
-              al[k] = cf.alo[k][q];
-            }
-            const float r = residual_row<W>(bw[BW], xw, ah, al);
-            float z = r * cf.ul[0][q];
-            if (BW == 2) z = fmaf(-cf.ul[2][q], z2, z);
-            z = fmaf(-cf.ul[1][q], z1, z);
-            z2 = z1;
-            z1 = z;
+            const float z = refine_resid_z<BW>(cf, q, bw[BW], xw, z1, z2);
             ps[(int64_t)q * M] = make_float2(xw[BW], z);
           }
         }
@@ -215,12 +166,7 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
         if (i + D < N) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i + D) * M);
         cp_commit();
         slot = (slot + 1 == D) ? 0 : slot + 1;
-        float d = xz.y;
-        if (BW == 2) d = fmaf(-cf.ul[4][i], d2, d);
-        d = fmaf(-cf.ul[3][i], d1, d);
-        d2 = d1;
-        d1 = d;
-        px[(int64_t)i * M] = (double)xz.x + (double)d;
+        px[(int64_t)i * M] = refine_out<BW>(cf, i, xz.x, xz.y, d1, d2);
       }
       cp_wait<0>();
     }

@@ -1,0 +1,478 @@
+// Request server: continuous batching of shared-LHS solves on one GPU.
+//
+// Requests arrive with host buffers and a resident factorised LHS.  A worker
+// thread admits queued requests in arrival order while their device memory
+// fits in an arena of fixed size (the HBM budget), gathers every newly
+// admitted request into one batch, and runs the batch on one of a few
+// streams: host-to-device copies, one replay of a captured CUDA graph (the
+// work-list copy and one grouped persistent launch covering all requests of
+// the batch), device-to-host copies, an event.  Batches on different streams
+// overlap on the device; requests that arrive while batches run are admitted
+// as soon as memory and a stream are free.  Completion is observed by polling
+// the batch events; latency is host submission to host-observed completion.
+// No device-side waits are involved: a batch is a finite work list.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+#include "serve.h"
+
+namespace bs {
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device allocation; blocks are 256-byte aligned.
+class Arena {
+ public:
+  void init(size_t size) {
+    size_ = size;
+    free_.clear();
+    free_[0] = size;
+    used_ = peak_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) / 256 * 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        if (used_ > peak_) peak_ = used_;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+  size_t peak() const { return peak_; }
+  size_t size() const { return size_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t size_ = 0, used_ = 0, peak_ = 0;
+};
+
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_CANCELLED = 3, RQ_FAILED = 4 };
+
+struct Req {
+  bs_handle h;
+  const void* hB;
+  void* hX;
+  int mode;
+  int64_t M;
+  size_t bytes;      // arena bytes
+  size_t off;        // arena offset
+  double t_submit = 0, t_done = 0;
+  int state = RQ_QUEUED;
+  bool fail_on_admit = false;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  unsigned char* h_work = nullptr;  // pinned
+  unsigned char* d_work = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  std::vector<int64_t> reqs;
+};
+
+}  // namespace
+}  // namespace bs
+
+struct bs_server_s {
+  int device = 0;
+  char* arena_base = nullptr;
+  bs::Arena arena;
+  std::vector<bs::Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, bs::Req> reqs;
+  int64_t next_id = 1;
+  std::thread worker;
+  bool stop = false;
+  bool paused = false;
+  cudaError_t sticky = cudaSuccess;
+  // statistics
+  int64_t batches = 0, completed = 0, failed = 0, max_batch_reqs = 0, max_concurrent = 0;
+};
+
+namespace bs {
+namespace {
+
+size_t req_bytes(int width, int64_t N, int mode, int64_t M) {
+  (void)width;
+  const size_t nm = (size_t)N * (size_t)M;
+  return mode == SERVE_F64 ? nm * 8 : nm * 4 + nm * 8;
+}
+
+// Admit queued requests (in order) while they fit; returns the admitted ids.
+std::vector<int64_t> admit(bs_server s) {
+  std::vector<int64_t> out;
+  int tiles = 0;
+  while (!s->queue.empty() && (int)out.size() < kGroupMaxReq) {
+    const int64_t id = s->queue.front();
+    Req& r = s->reqs[id];
+    if (r.state == RQ_CANCELLED) {
+      s->queue.pop_front();
+      continue;
+    }
+    const int t = (int)((r.M + 31) / 32);
+    if (tiles + t > kGroupMaxTiles) break;
+    size_t off = 0;
+    if (!s->arena.alloc(r.bytes, &off)) break;  // wait for memory (arrival order is kept)
+    s->queue.pop_front();
+    r.off = off;
+    if (r.fail_on_admit) {  // host-side fault injection for tests
+      s->arena.release(off, r.bytes);
+      r.state = RQ_FAILED;
+      r.t_done = now_s();
+      s->failed++;
+      continue;
+    }
+    r.state = RQ_RUNNING;
+    tiles += t;
+    out.push_back(id);
+  }
+  return out;
+}
+
+cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<int64_t>& ids) {
+  GHeader* hdr = reinterpret_cast<GHeader*>(sl.h_work);
+  GReq* greq = reinterpret_cast<GReq*>(sl.h_work + kGroupReqOff);
+  GTile* gt = reinterpret_cast<GTile*>(sl.h_work + kGroupTileOff);
+  int nt = 0;
+  cudaError_t e = cudaSuccess;
+  for (size_t q = 0; q < ids.size() && e == cudaSuccess; q++) {
+    Req& r = s->reqs[ids[q]];
+    const bs_handle h = r.h;
+    const size_t nm = (size_t)h->N * (size_t)r.M;
+    char* dB = s->arena_base + r.off;
+    GReq g{};
+    g.c64 = h->plan[0].c64;
+    g.c32 = h->plan[0].c32;
+    g.ul32 = h->plan[2].c32;
+    g.bhi = h->bands_hi;
+    g.blo = h->bands_lo;
+    g.M = r.M;
+    g.N = (int)h->N;
+    g.width = h->width;
+    g.mode = r.mode;
+    if (r.mode == SERVE_F64) {
+      g.B = dB;
+      g.X = reinterpret_cast<double*>(dB);
+      e = cudaMemcpyAsync(dB, r.hB, nm * 8, cudaMemcpyHostToDevice, sl.st);
+    } else {
+      g.X = reinterpret_cast<double*>(dB);                   // nm * 8 bytes
+      g.B = dB + nm * 8;                                     // nm * 4 bytes
+      e = cudaMemcpyAsync(g.B, r.hB, nm * 4, cudaMemcpyHostToDevice, sl.st);
+    }
+    greq[q] = g;
+    for (int64_t j0 = 0; j0 < r.M; j0 += 32) gt[nt++] = GTile{(int)q, (int)j0};
+  }
+  hdr->n_req = (int)ids.size();
+  hdr->n_tiles = nt;
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, sl.st);
+  for (size_t q = 0; q < ids.size() && e == cudaSuccess; q++) {
+    Req& r = s->reqs[ids[q]];
+    const size_t nm = (size_t)r.h->N * (size_t)r.M;
+    e = cudaMemcpyAsync(r.hX, s->arena_base + r.off, nm * 8, cudaMemcpyDeviceToHost, sl.st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
+  return e;
+}
+
+void worker_loop(bs_server s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop) {
+    bool progressed = false;
+    // completions
+    for (Slot& sl : s->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      const double t = now_s();
+      for (int64_t id : sl.reqs) {
+        Req& r = s->reqs[id];
+        s->arena.release(r.off, r.bytes);
+        r.t_done = t;
+        if (q == cudaSuccess) {
+          r.state = RQ_DONE;
+          s->completed++;
+        } else {
+          r.state = RQ_FAILED;
+          s->failed++;
+        }
+      }
+      if (q != cudaSuccess) s->sticky = q;
+      sl.reqs.clear();
+      sl.busy = false;
+      progressed = true;
+    }
+    if (progressed) s->cv.notify_all();
+    // admission and launch
+    if (!s->paused) {
+      for (Slot& sl : s->slots) {
+        if (sl.busy || s->queue.empty()) continue;
+        std::vector<int64_t> ids = admit(s);
+        if (ids.empty()) {
+          s->cv.notify_all();  // failures injected at admission are final
+          break;
+        }
+        const cudaError_t e = launch_batch(s, sl, ids);
+        progressed = true;
+        if (e != cudaSuccess) {  // nothing of this batch can be trusted: fail its requests
+          s->sticky = e;
+          cudaStreamSynchronize(sl.st);
+          const double t = now_s();
+          for (int64_t id : ids) {
+            Req& r = s->reqs[id];
+            s->arena.release(r.off, r.bytes);
+            r.state = RQ_FAILED;
+            r.t_done = t;
+            s->failed++;
+          }
+          s->cv.notify_all();
+          continue;
+        }
+        sl.reqs = ids;
+        sl.busy = true;
+        s->batches++;
+        if ((int64_t)ids.size() > s->max_batch_reqs) s->max_batch_reqs = (int64_t)ids.size();
+      }
+      int busy = 0;
+      for (Slot& sl : s->slots) busy += sl.busy;
+      if (busy > s->max_concurrent) s->max_concurrent = busy;
+    }
+    bool any_busy = false;
+    for (Slot& sl : s->slots) any_busy |= sl.busy;
+    if (!progressed) {
+      if (any_busy)
+        s->cv.wait_for(lk, std::chrono::microseconds(20));
+      else
+        s->cv.wait_for(lk, std::chrono::milliseconds(5));
+    }
+  }
+}
+
+void destroy_server(bs_server s) {
+  for (Slot& sl : s->slots) {
+    if (sl.st) cudaStreamSynchronize(sl.st);
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.h_work) cudaFreeHost(sl.h_work);
+    if (sl.d_work) cudaFree(sl.d_work);
+    if (sl.st) cudaStreamDestroy(sl.st);
+  }
+  if (s->arena_base) cudaFree(s->arena_base);
+  delete s;
+}
+
+}  // namespace
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* out) {
+  if (!out) return set_error(BS_EINVAL, "bs_server_create: out is NULL");
+  *out = nullptr;
+  if (hbm_budget_bytes < 4096) return set_error(BS_EINVAL, "bs_server_create: budget too small");
+  if (n_streams < 1 || n_streams > 16) return set_error(BS_EINVAL, "bs_server_create: n_streams must be 1..16");
+  bs_server s = new bs_server_s();
+  cudaGetDevice(&s->device);
+  cudaError_t e = cudaMalloc(&s->arena_base, hbm_budget_bytes);
+  if (e != cudaSuccess) {
+    delete s;
+    return set_error(BS_ENOMEM, "bs_server_create: cannot reserve the HBM budget");
+  }
+  s->arena.init(hbm_budget_bytes);
+  s->slots.resize(n_streams);
+  const int grid = grouped_grid();
+  for (Slot& sl : s->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl.h_work, kGroupWorkBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_work, kGroupWorkBytes);
+    if (e == cudaSuccess) std::memset(sl.h_work, 0, kGroupWorkBytes);
+    // capture: work-list copy + grouped launch, replayed once per batch
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemcpyAsync(sl.d_work, sl.h_work, kGroupWorkBytes, cudaMemcpyHostToDevice, sl.st);
+      cudaError_t e2 = e1 == cudaSuccess ? launch_grouped(sl.d_work, grid, sl.st) : e1;
+      cudaError_t e3 = cudaStreamEndCapture(sl.st, &g);
+      e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+  }
+  if (e != cudaSuccess) {
+    destroy_server(s);
+    return cuda_error(e, "bs_server_create");
+  }
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return BS_OK;
+}
+
+bs_status bs_server_destroy(bs_server s) {
+  if (!s) return BS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  destroy_server(s);
+  return BS_OK;
+}
+
+bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* host_X, int mode, int64_t M,
+                           int64_t* request_id) {
+  if (!s || !request_id) return set_error(BS_EINVAL, "bs_server_submit: null argument");
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_server_submit: unknown handle");
+  if (h->device != s->device) return set_error(BS_EINVAL, "bs_server_submit: handle on another device");
+  if (!host_B || !host_X) return set_error(BS_EINVAL, "bs_server_submit: null buffer");
+  if (mode != SERVE_F64 && mode != SERVE_F32_REFINE) return set_error(BS_EINVAL, "bs_server_submit: bad mode");
+  if (mode == SERVE_F32_REFINE && !h->has_ul)
+    return set_error(BS_ESINGULAR, "bs_server_submit: the reversed elimination of this matrix met a bad pivot");
+  if (M < 1 || M > (int64_t)kGroupMaxTiles * 32) return set_error(BS_EINVAL, "bs_server_submit: M out of range");
+  const size_t bytes = req_bytes(h->width, h->N, mode, M);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (bytes > s->arena.size())
+    return set_error(BS_ENOMEM, "bs_server_submit: request larger than the server's HBM budget");
+  const int64_t id = s->next_id++;
+  Req r;
+  r.h = h;
+  r.hB = host_B;
+  r.hX = host_X;
+  r.mode = mode;
+  r.M = M;
+  r.bytes = bytes;
+  r.off = 0;
+  r.t_submit = now_s();
+  s->reqs[id] = r;
+  s->queue.push_back(id);
+  *request_id = id;
+  s->cv.notify_all();
+  return BS_OK;
+}
+
+bs_status bs_server_poll(bs_server s, int64_t id, int* state, double* latency_s) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_poll: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(BS_EINVAL, "bs_server_poll: unknown request");
+  if (state) *state = it->second.state;
+  if (latency_s) *latency_s = it->second.t_done > 0 ? it->second.t_done - it->second.t_submit : -1.0;
+  return BS_OK;
+}
+
+bs_status bs_server_wait(bs_server s, int64_t id, double timeout_s, int* state) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_wait: null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(BS_EINVAL, "bs_server_wait: unknown request");
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (it->second.state == RQ_QUEUED || it->second.state == RQ_RUNNING) {
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+        (it->second.state == RQ_QUEUED || it->second.state == RQ_RUNNING)) {
+      if (state) *state = it->second.state;
+      return set_error(BS_ETIMEOUT, "bs_server_wait: timed out");
+    }
+  }
+  if (state) *state = it->second.state;
+  return BS_OK;
+}
+
+bs_status bs_server_cancel(bs_server s, int64_t id) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_cancel: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(BS_EINVAL, "bs_server_cancel: unknown request");
+  if (it->second.state != RQ_QUEUED) return set_error(BS_EINVAL, "bs_server_cancel: request already admitted");
+  it->second.state = RQ_CANCELLED;
+  it->second.t_done = now_s();
+  s->cv.notify_all();
+  return BS_OK;
+}
+
+bs_status bs_server_release(bs_server s, int64_t id) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_release: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(BS_EINVAL, "bs_server_release: unknown request");
+  if (it->second.state == RQ_QUEUED || it->second.state == RQ_RUNNING)
+    return set_error(BS_EINVAL, "bs_server_release: request still pending");
+  s->reqs.erase(it);
+  return BS_OK;
+}
+
+bs_status bs_server_pause(bs_server s, int paused) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_pause: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->paused = paused != 0;
+  s->cv.notify_all();
+  return BS_OK;
+}
+
+bs_status bs_server_fail_on_admit(bs_server s, int64_t id) {
+  if (!s) return set_error(BS_EINVAL, "bs_server_fail_on_admit: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end() || it->second.state != RQ_QUEUED)
+    return set_error(BS_EINVAL, "bs_server_fail_on_admit: request not queued");
+  it->second.fail_on_admit = true;
+  return BS_OK;
+}
+
+bs_status bs_server_stats(bs_server s, int64_t* out, int n) {
+  if (!s || !out || n < 1) return set_error(BS_EINVAL, "bs_server_stats: bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  int64_t queued = 0, running = 0;
+  for (auto& kv : s->reqs) {
+    queued += kv.second.state == RQ_QUEUED;
+    running += kv.second.state == RQ_RUNNING;
+  }
+  const int64_t v[10] = {s->batches, s->completed, s->failed, queued, running, (int64_t)s->arena.used(),
+                         (int64_t)s->arena.peak(), (int64_t)s->arena.size(), s->max_batch_reqs, s->max_concurrent};
+  for (int q = 0; q < n && q < 10; q++) out[q] = v[q];
+  if (s->sticky != cudaSuccess) return cuda_error(s->sticky, "bs_server: a batch failed");
+  return BS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+"""GPU parity of the fused ADI half-steps (explicit second difference across
+systems + shared tridiagonal solve) against the oracle, both axes, FP64
+(1e-12) and FP32 (2e-5), forward and adjoint; the autograd wrapper against
+finite differences."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2, second_difference
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    return m
+
+
+def _factor(bs, n, r):
+    return bs.Factor(synth.adi_bands(n, r))
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("ny,nx", [(1, 1), (3, 5), (33, 17), (100, 64), (70, 257)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+def test_adi_halfstep(bs, axis, ny, nx, dtype, tol):
+    r = 0.5
+    n = nx if axis == 0 else ny
+    if n < 2:
+        pytest.skip("a tridiagonal handle needs N >= 2")
+    rng = np.random.default_rng(ny * 1000 + nx)
+    u = rng.uniform(-1, 1, (ny, nx))
+    if dtype == torch.float32:
+        u = u.astype(np.float32).astype(np.float64)
+    f = _factor(bs, n, r)
+    out = bs.adi_halfstep(f, torch.tensor(u, dtype=dtype, device="cuda"), r, axis)
+    torch.cuda.synchronize()
+    assert rel_l2(out.double().cpu().numpy(), oracle.adi_halfstep(u, r, axis)) < tol
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_adi_adjoint_is_transpose(bs, axis):
+    """<out(u), g> == <u, adjoint(g)> and the adjoint against the dense
+    transpose on a small rectangular grid."""
+    ny, nx, r = 9, 13, 0.5
+    n = nx if axis == 0 else ny
+    f = _factor(bs, n, r)
+    rng = np.random.default_rng(axis)
+    u = rng.uniform(-1, 1, (ny, nx))
+    g = rng.uniform(-1, 1, (ny, nx))
+    out = bs.adi_halfstep(f, torch.tensor(u, device="cuda"), r, axis).cpu().numpy()
+    adj = bs.adi_halfstep(f, torch.tensor(g, device="cuda"), r, axis, adjoint=True).cpu().numpy()
+    assert abs(np.sum(out * g) - np.sum(u * adj)) < 1e-12 * (1 + abs(np.sum(out * g)))
+    Dx, Dy = second_difference(nx), second_difference(ny)
+    I = np.eye(nx * ny)
+    Kxx, Kyy = np.kron(np.eye(ny), Dx), np.kron(Dy, np.eye(nx))
+    T = np.linalg.solve(I - r * Kxx, I + r * Kyy) if axis == 0 else np.linalg.solve(I - r * Kyy, I + r * Kxx)
+    assert rel_l2(adj.ravel(), T.T @ g.ravel()) < 1e-12
+
+
+def test_adi_full_grid_4096(bs):
+    """The 4096 x 4096 heat-equation grid, r = 0.5, u ~ U(-1,1) (seed 0): one
+    full Peaceman-Rachford step (x-implicit then y-implicit) in FP64 against
+    the oracle on the whole grid, and in FP32 within 2e-5."""
+    n, r = 4096, 0.5
+    f = _factor(bs, n, r)
+    u = synth.adi_field(n, 0, "cuda")
+    half = bs.adi_halfstep(f, u, r, 0)
+    full = bs.adi_halfstep(f, half, r, 1)
+    u32 = u.float()
+    full32 = bs.adi_halfstep(f, bs.adi_halfstep(f, u32, r, 0), r, 1)
+    torch.cuda.synchronize()
+    uh = u.cpu().numpy()
+    ref = oracle.adi_halfstep(oracle.adi_halfstep(uh, r, 0), r, 1)
+    assert rel_l2(full.cpu().numpy(), ref) < 1e-12
+    ref32 = oracle.adi_halfstep(oracle.adi_halfstep(u32.double().cpu().numpy(), r, 0), r, 1)
+    assert rel_l2(full32.double().cpu().numpy(), ref32) < 2e-5
+
+
+def test_adi_autograd_finite_differences(bs):
+    """Gradient of L = sum(W * step(u)) for a full ADI step (both half-steps)
+    against central differences in FP64, along a random direction."""
+    ny, nx, r = 12, 10, 0.5
+    fx, fy = _factor(bs, nx, r), _factor(bs, ny, r)
+    rng = np.random.default_rng(3)
+    u0 = rng.uniform(-1, 1, (ny, nx))
+    W = rng.uniform(-1, 1, (ny, nx))
+    du = rng.uniform(-1, 1, (ny, nx))
+    u = torch.tensor(u0, device="cuda", requires_grad=True)
+    out = bs.ADIHalfStepFn.apply(bs.ADIHalfStepFn.apply(u, fx, r, 0), fy, r, 1)
+    (out * torch.tensor(W, device="cuda")).sum().backward()
+    analytic = float((u.grad.cpu().numpy() * du).sum())
+
+    def L(t):
+        v = oracle.adi_halfstep(oracle.adi_halfstep(u0 + t * du, r, 0), r, 1)
+        return float(np.sum(W * v))
+
+    eps = 1e-6
+    fd = (L(eps) - L(-eps)) / (2 * eps)
+    assert abs(analytic - fd) < 1e-7 * (1 + abs(fd))

@@ -1,0 +1,140 @@
+"""Request server: results against the oracle and bitwise against the direct
+solves, the same whether a request runs alone or in a mix, admission under a
+small HBM budget, and host-side failure handling (oversized request,
+cancellation, a request that fails at admission, wait time-outs)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def serve(bs):
+    from paper_1909_04539_gb300 import serve as sv
+    return sv
+
+
+def _lhs_pool(bs, n=6):
+    specs = [synth.serving_lhs(i, 16, 600) for i in range(n)]
+    return specs, [bs.Factor(s.bands) for s in specs]
+
+
+def _request(spec, M, mode, seed):
+    rng = np.random.default_rng(seed)
+    B = torch.tensor(rng.uniform(-1, 1, (spec.N, M)), dtype=torch.float64 if mode == 0 else torch.float32)
+    return B.pin_memory(), torch.empty((spec.N, M), dtype=torch.float64).pin_memory()
+
+
+def test_mix_equals_alone_and_direct(bs, serve):
+    specs, facs = _lhs_pool(bs)
+    rng = np.random.default_rng(0)
+    reqs = []
+    for r in range(24):
+        k = int(rng.integers(len(specs)))
+        M = int(rng.integers(1, 3000))
+        mode = int(rng.integers(2))
+        reqs.append((k, M, mode, 100 + r))
+    srv = serve.Server(1 << 30, n_streams=3)
+    # the mix: everything submitted at once
+    mix = []
+    for k, M, mode, seed in reqs:
+        B, X = _request(specs[k], M, mode, seed)
+        mix.append((srv.submit(facs[k], B, X, mode), B, X))
+    for rid, _, _ in mix:
+        assert srv.wait(rid, 60) == "done"
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    # alone: one at a time
+    for (k, M, mode, seed), (rid, B, X) in zip(reqs, mix):
+        B2, X2 = _request(specs[k], M, mode, seed)
+        r2 = srv.submit(facs[k], B2, X2, mode)
+        assert srv.wait(r2, 60) == "done"
+        assert torch.equal(X, X2), "result depends on the batch"
+        # bitwise equal to the direct API, and right against the oracle
+        if mode == 0:
+            D = B.cuda()
+            bs.solve(facs[k], D)
+        else:
+            D = bs.solve_refine(facs[k], B.cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(D.cpu(), X)  # same per-system arithmetic as the direct solves
+        ref = oracle.solve(specs[k].bands, B.double().numpy())
+        assert rel_l2(X.numpy(), ref) < 1e-12
+    srv.close()
+
+
+def test_admission_under_small_budget(bs, serve):
+    """Requests totalling ~8x the budget all complete; the arena never holds
+    more than the budget."""
+    specs, facs = _lhs_pool(bs, 3)
+    budget = 4 << 20
+    srv = serve.Server(budget, n_streams=2)
+    ids = []
+    total = 0
+    for r in range(40):
+        k = r % 3
+        M = 300 + 17 * r
+        B, X = _request(specs[k], M, r % 2, r)
+        total += specs[k].N * M * (8 if r % 2 == 0 else 12)
+        ids.append((srv.submit(facs[k], B, X, r % 2), k, B, X))
+    for rid, k, B, X in ids:
+        assert srv.wait(rid, 120) == "done"
+        assert rel_l2(X.numpy(), oracle.solve(specs[k].bands, B.double().numpy())) < 1e-12
+    st = srv.stats()
+    assert total > 4 * budget
+    assert st["arena_peak"] <= budget and st["arena_used"] == 0
+    srv.close()
+
+
+def test_oversized_request_rejected(bs, serve):
+    specs, facs = _lhs_pool(bs, 1)
+    srv = serve.Server(1 << 20, n_streams=1)
+    B, X = _request(specs[0], 20000, 0, 1)
+    with pytest.raises(bs.BsolveError) as ei:
+        srv.submit(facs[0], B, X, 0)
+    assert ei.value.status == 3
+    srv.close()
+
+
+def test_cancel_failure_and_timeout(bs, serve):
+    specs, facs = _lhs_pool(bs, 2)
+    srv = serve.Server(64 << 20, n_streams=2)
+    srv.pause(True)
+    subs = []
+    for r in range(6):
+        B, X = _request(specs[r % 2], 500 + r, r % 2, 50 + r)
+        subs.append((srv.submit(facs[r % 2], B, X, r % 2), r % 2, B, X))
+    # nothing is admitted while paused: a bounded wait times out
+    with pytest.raises(bs.BsolveError) as ei:
+        srv.wait(subs[0][0], 0.2)
+    assert ei.value.status == 5
+    srv.cancel(subs[1][0])
+    srv.fail_on_admit(subs[2][0])
+    srv.pause(False)
+    states = [srv.wait(rid, 60) for rid, _, _, _ in subs]
+    assert states[1] == "cancelled" and states[2] == "failed"
+    for (rid, k, B, X), s in zip(subs, states):
+        if s == "done":
+            assert rel_l2(X.numpy(), oracle.solve(specs[k].bands, B.double().numpy())) < 1e-12
+    assert states.count("done") == 4
+    with pytest.raises(bs.BsolveError):
+        srv.cancel(subs[0][0])  # already finished
+    st = srv.stats()
+    assert st["failed"] == 1 and st["arena_used"] == 0
+    srv.release(subs[0][0])
+    with pytest.raises(bs.BsolveError):
+        srv.poll(subs[0][0])
+    srv.close()
