@@ -124,7 +124,10 @@ bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* 
  *   dbands[k*N + i] = -sum_j (A^{-T} G)[i, j] * X[i + k - width/2, j]
  * (0 for entries outside the matrix), as double[width*N] in device memory,
  * reduced over the batch in a fixed order (deterministic, no atomics).
- * dtype BS_F64 or BS_F32.  Band gradients are accumulated in FP64. */
+ * dtype BS_F64 or BS_F32.  Band gradients are accumulated in FP64.  The
+ * reduction takes stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on
+ * `stream`) of (number of system chunks) x width x N doubles, about 160 KB for
+ * N = 512. */
 bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M,
                            const void* X, double* dbands, bs_stream stream);
 
@@ -151,9 +154,11 @@ bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_dtype dtype,
 /* Band-gradient reduction alone, for a caller that already holds
  * GB = A^{-T} (dL/dX) (e.g. from bs_solve_adjoint without X):
  *   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - width/2, j]
- * (0 for entries outside the matrix), reduced in a fixed order.  GB and X:
+ * (0 for entries outside the matrix), reduced in a fixed order (rows x
+ * chunks of systems, then chunks in order), bitwise reproducible.  GB and X:
  * device, same dtype (BS_F64 or BS_F32) and layout; dbands: device
- * double[width*N], overwritten. */
+ * double[width*N], overwritten.  Uses stream-ordered scratch as
+ * bs_solve_adjoint does. */
 bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout,
                        int64_t M, double* dbands, bs_stream stream);
 
@@ -221,8 +226,16 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    many systems run at once (default 0: no bound, every system that fits
  *    on the device runs at once).
  *  BS_OPT_BLOCKS_PER_SM: cap on resident CTAs per SM of the persistent grids
- *    (default 0: as many as shared memory and threads allow). */
-typedef enum { BS_OPT_INFLIGHT_BYTES = 0, BS_OPT_BLOCKS_PER_SM = 1, BS_OPT_COUNT = 2 } bs_option;
+ *    (default 0: as many as shared memory and threads allow).
+ *  BS_OPT_SWEEP_KERNEL: 0 (default) lets FP32-arithmetic interleaved solves
+ *    use the on-chip kernel (forward values kept in shared memory, rows moved
+ *    by TMA) where the shape qualifies; 1 forces the streaming kernels. */
+typedef enum {
+  BS_OPT_INFLIGHT_BYTES = 0,
+  BS_OPT_BLOCKS_PER_SM = 1,
+  BS_OPT_SWEEP_KERNEL = 2,
+  BS_OPT_COUNT = 3
+} bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 
 /* Measurement aid (the paper has no counterpart): runs a short kernel of
@@ -231,6 +244,12 @@ bs_status bs_set_option(int opt, int64_t value);
  * ceiling of the sweeps that compute in native FP64 (on GB300 they are bound
  * by it before HBM).  Allocates and frees 8 bytes of device memory. */
 bs_status bs_measure_fp64_rate(double* fma_per_s, bs_stream stream);
+
+/* Sticky device-side status of the kernels with bounded waits (the on-chip
+ * TMA sweeps): 0 = no problem, 1 = a wait for a TMA load ran out of its
+ * iteration limit (the kernel then abandoned its tile; results of that launch
+ * are invalid).  Synchronous (reads device memory); `reset` != 0 clears it. */
+bs_status bs_device_status(int* code, int reset);
 
 /* Last error message of the calling thread (static storage, never NULL). */
 const char* bs_last_error(void);

@@ -35,6 +35,7 @@ SIGNATURES = {
     "bs_server_fail_on_admit": (i32, [vp, i64]),
     "bs_server_stats": (i32, [vp, ctypes.POINTER(i64), i32]),
     "bs_set_option": (i32, [i32, i64]),
+    "bs_device_status": (i32, [ctypes.POINTER(i32), i32]),
     "bs_measure_fp64_rate": (i32, [dp, vp]),
     "bs_last_error": (ctypes.c_char_p, []),
     "bs_strerror": (ctypes.c_char_p, [i32]),

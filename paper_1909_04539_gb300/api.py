@@ -19,6 +19,14 @@ _LAYOUT = {"interleaved": 0, "strided": 1}
 
 OPT_INFLIGHT_BYTES = 0
 OPT_BLOCKS_PER_SM = 1
+OPT_SWEEP_KERNEL = 2
+
+
+def device_status(reset: bool = False) -> int:
+    """Sticky device status of the bounded-wait kernels (0 = fine)."""
+    v = ctypes.c_int()
+    check(lib().bs_device_status(ctypes.byref(v), int(bool(reset))), "bs_device_status")
+    return int(v.value)
 
 
 def _stream(stream) -> ctypes.c_void_p:

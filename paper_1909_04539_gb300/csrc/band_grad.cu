@@ -3,32 +3,69 @@
 // For a scalar loss L with dL/dX given, X = A^{-1} B and GB = A^{-T} dL/dX,
 // dL/dA = -GB X^T; the entries on the bands are
 //   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - h, j],   h = width / 2.
-// Each CTA owns kGradRows consecutive rows and reduces them over all M
-// systems: threads stride over the systems accumulating in FP64, then a
-// fixed-order warp-shuffle and shared-memory tree combines the threads.  The
-// grid depends on N only, so the result is bitwise reproducible.
+// Two levels, fixed order, no atomics:
+//   1. a 2D grid of CTAs, each owning kGradRows rows and one chunk of the
+//      systems, accumulates its products in FP64 (threads stride over the
+//      chunk's systems; warp shuffles and a shared-memory tree combine the
+//      threads) and writes one partial per (chunk, band, row) to scratch;
+//   2. one thread per (band, row) adds the chunks' partials in chunk order.
+// The grid shape is a function of N and M only, so the result is bitwise
+// reproducible.  Work per unknown: `width` FP64 FMAs (the kernel is bound by
+// the FP64 pipe on GB300), 16 bytes of compulsory reads (GB and X; the X
+// halo of 2h rows per block of kGradRows comes mostly from L2).
 #include "sweep_kernels.cuh"
 
 namespace bs {
 
 constexpr int kGradThreads = 256;
-constexpr int kGradRows = 4;
+constexpr int kGradRows = 8;
+constexpr int kGradTargetCtas = 512;
+constexpr int64_t kGradMinChunk = 1024;  // systems per chunk at least
 
+struct GradShape {
+  int row_blocks;
+  int chunks;
+  int64_t chunk;  // systems per chunk (multiple of 2)
+};
+
+GradShape grad_shape(int N, int64_t M) {
+  GradShape g{};
+  g.row_blocks = (N + kGradRows - 1) / kGradRows;
+  int64_t c = (kGradTargetCtas + g.row_blocks - 1) / g.row_blocks;
+  const int64_t cmax = (M + kGradMinChunk - 1) / kGradMinChunk;
+  if (c > cmax) c = cmax;
+  if (c < 1) c = 1;
+  int64_t chunk = (M + c - 1) / c;
+  chunk = (chunk + 1) / 2 * 2;
+  g.chunks = (int)((M + chunk - 1) / chunk);
+  g.chunk = chunk;
+  return g;
+}
+
+size_t band_grad_scratch_bytes(int width, int N, int64_t M) {
+  const GradShape g = grad_shape(N, M);
+  return (size_t)g.chunks * width * N * sizeof(double);
+}
+
+// Level 1.  blockIdx.x = row block, blockIdx.y = chunk.  partial layout:
+// [chunk][band][row].
 template <typename T, int W>
 __global__ void __launch_bounds__(kGradThreads)
-k_band_grad(int N, int64_t M, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs, int64_t ss,
-            double* __restrict__ dbands) {
+k_band_grad_partial(int N, int64_t M, int64_t chunk, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
+                    int64_t ss, double* __restrict__ partial) {
   constexpr int H = W / 2;
   constexpr int NX = kGradRows + 2 * H;
   __shared__ double red[kGradThreads / 32][kGradRows * W];
   const int i0 = blockIdx.x * kGradRows;
+  const int64_t jlo = (int64_t)blockIdx.y * chunk;
+  const int64_t jhi = (jlo + chunk) < M ? (jlo + chunk) : M;
   double acc[kGradRows][W];
 #pragma unroll
   for (int r = 0; r < kGradRows; r++)
 #pragma unroll
     for (int k = 0; k < W; k++) acc[r][k] = 0.0;
 
-  for (int64_t j = threadIdx.x; j < M; j += kGradThreads) {
+  for (int64_t j = jlo + threadIdx.x; j < jhi; j += kGradThreads) {
     double x[NX], g[kGradRows];
 #pragma unroll
     for (int q = 0; q < NX; q++) {
@@ -61,30 +98,64 @@ k_band_grad(int N, int64_t M, const T* __restrict__ GB, const T* __restrict__ X,
     const int r = threadIdx.x / W, k = threadIdx.x % W;
     double s = 0.0;
     for (int w = 0; w < kGradThreads / 32; w++) s += red[w][threadIdx.x];
-    const int row = i0 + r, col = row + k - H;
-    if (row < N) dbands[(int64_t)k * N + row] = (col >= 0 && col < N) ? -s : 0.0;
+    const int row = i0 + r;
+    if (row < N) partial[((int64_t)blockIdx.y * W + k) * N + row] = s;
   }
+}
+
+// Level 2: dbands[k*N + i] = -(sum over chunks, in order); 0 outside the matrix.
+__global__ void k_band_grad_finish(int W, int N, int chunks, const double* __restrict__ partial,
+                                   double* __restrict__ dbands) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)W * N) return;
+  const int k = (int)(t / N), i = (int)(t % N);
+  const int col = i + k - W / 2;
+  double s = 0.0;
+  for (int c = 0; c < chunks; c++) s += partial[(int64_t)c * W * N + t];
+  dbands[t] = (col >= 0 && col < N) ? -s : 0.0;
+}
+
+// Both levels with caller-provided scratch of band_grad_scratch_bytes().
+cudaError_t band_grad_with_scratch(int width, int N, const void* GB, const void* X, bs_dtype t, bs_layout layout,
+                                   int64_t M, double* dbands, double* scratch, cudaStream_t st) {
+  const int64_t rs = layout == BS_INTERLEAVED ? M : 1;
+  const int64_t ss = layout == BS_INTERLEAVED ? 1 : N;
+  const GradShape g = grad_shape(N, M);
+  const dim3 grid(g.row_blocks, g.chunks);
+  if (t == BS_F64) {
+    if (width == 3)
+      k_band_grad_partial<double, 3><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
+                                                                     (const double*)X, rs, ss, scratch);
+    else
+      k_band_grad_partial<double, 5><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
+                                                                     (const double*)X, rs, ss, scratch);
+  } else {
+    if (width == 3)
+      k_band_grad_partial<float, 3><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
+                                                                    (const float*)X, rs, ss, scratch);
+    else
+      k_band_grad_partial<float, 5><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
+                                                                    (const float*)X, rs, ss, scratch);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)width * N;
+  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, g.chunks, scratch, dbands);
+  return cudaGetLastError();
 }
 
 bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout, int64_t M,
                            double* dbands, cudaStream_t st) {
   const int N = (int)h->N;
-  const int64_t rs = layout == BS_INTERLEAVED ? M : 1;
-  const int64_t ss = layout == BS_INTERLEAVED ? 1 : N;
-  const int grid = (N + kGradRows - 1) / kGradRows;
-  if (t == BS_F64) {
-    if (h->width == 3)
-      k_band_grad<double, 3><<<grid, kGradThreads, 0, st>>>(N, M, (const double*)GB, (const double*)X, rs, ss, dbands);
-    else
-      k_band_grad<double, 5><<<grid, kGradThreads, 0, st>>>(N, M, (const double*)GB, (const double*)X, rs, ss, dbands);
-  } else {
-    if (h->width == 3)
-      k_band_grad<float, 3><<<grid, kGradThreads, 0, st>>>(N, M, (const float*)GB, (const float*)X, rs, ss, dbands);
-    else
-      k_band_grad<float, 5><<<grid, kGradThreads, 0, st>>>(N, M, (const float*)GB, (const float*)X, rs, ss, dbands);
-  }
-  const cudaError_t e = cudaGetLastError();
+  double* scratch = nullptr;
+  const size_t bytes = band_grad_scratch_bytes(h->width, N, M);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, st);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(BS_ENOMEM, "band gradient: scratch")
+                                                              : cuda_error(e, "band gradient scratch");
+  e = band_grad_with_scratch(h->width, N, GB, X, t, layout, M, dbands, scratch, st);
+  const cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_error(e, "band gradient launch");
+  if (e2 != cudaSuccess) return cuda_error(e2, "band gradient scratch release");
   return BS_OK;
 }
 
