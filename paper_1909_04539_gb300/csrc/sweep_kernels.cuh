@@ -154,6 +154,66 @@ __device__ __forceinline__ void bwd_step(const Coefs<C>& cf, int i, C (&f)[V], C
   }
 }
 
+// Block versions of the two steps: U consecutive rows (n of them valid).
+// All coefficient loads of the block are issued before any arithmetic, so
+// they do not wait behind the caller's stores of the previous block (which
+// the compiler must assume may alias them).  Per row and system the
+// arithmetic is exactly that of fwd_step / bwd_step.
+template <int BW, bool ADJ, typename C, int V, int U>
+__device__ __forceinline__ void fwd_block(const Coefs<C>& cf, int i0, int n, C (&f)[U][V], C (&w1)[V],
+                                          C (&w2)[V]) {
+  C s[U], l1[U], l2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (u < n) ? i0 + u : i0;
+    l1[u] = cf.l1[i];
+    s[u] = ADJ ? C(1) : cf.s[i];
+    l2[u] = (BW == 2) ? cf.l2[i] : C(0);
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        C w = ADJ ? f[u][v] : f[u][v] * s[u];
+        if (BW == 2) w = fma(-l2[u], w2[v], w);
+        w = fma(-l1[u], w1[v], w);
+        if (BW == 2) w2[v] = w1[v];
+        w1[v] = w;
+        f[u][v] = w;
+      }
+    }
+  }
+}
+
+// Backward block: rows top, top-1, ..., top-n+1 held in f[0..n-1].
+template <int BW, bool ADJ, typename C, int V, int U>
+__device__ __forceinline__ void bwd_block(const Coefs<C>& cf, int top, int n, C (&f)[U][V], C (&x1)[V],
+                                          C (&x2)[V]) {
+  C t[U], u1[U], u2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (u < n) ? top - u : top;
+    u1[u] = cf.u1[i];
+    t[u] = ADJ ? cf.t[i] : C(1);
+    u2[u] = (BW == 2) ? cf.u2[i] : C(0);
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        C x = ADJ ? f[u][v] * t[u] : f[u][v];
+        if (BW == 2) x = fma(-u2[u], x2[v], x);
+        x = fma(-u1[u], x1[v], x);
+        if (BW == 2) x2[v] = x1[v];
+        x1[v] = x;
+        f[u][v] = x;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------ async row copies
 
 // Per-lane rings of rows in shared memory, filled with cp.async.  Each lane
@@ -221,12 +281,11 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
         if (i0 + u < N) IO<Sin, C, V>::load(pin + (int64_t)(i0 + u) * M, blk[u]);
     };
     auto run_fwd = [&](C (&blk)[U][V], int i0) {
+      const int n = (N - i0) < U ? (N - i0) : U;
+      fwd_block<BW, ADJ, C, V, U>(cf, i0, n, blk, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (i0 + u < N) {
-          fwd_step<BW, ADJ, C, V>(cf, i0 + u, blk[u], r1, r2);
-          IO<Sout, C, V>::store(pout + (int64_t)(i0 + u) * M, blk[u]);
-        }
+        if (u < n) IO<Sout, C, V>::store(pout + (int64_t)(i0 + u) * M, blk[u]);
     };
     auto load_bwd = [&](C (&blk)[U][V], int top) {
 #pragma unroll
@@ -234,12 +293,11 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
         if (top - u >= 0) IO<Sout, C, V>::load(pout + (int64_t)(top - u) * M, blk[u]);
     };
     auto run_bwd = [&](C (&blk)[U][V], int top) {
+      const int n = (top + 1) < U ? (top + 1) : U;
+      bwd_block<BW, ADJ, C, V, U>(cf, top, n, blk, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (top - u >= 0) {
-          bwd_step<BW, ADJ, C, V>(cf, top - u, blk[u], r1, r2);
-          IO<Sout, C, V>::store(pout + (int64_t)(top - u) * M, blk[u]);
-        }
+        if (u < n) IO<Sout, C, V>::store(pout + (int64_t)(top - u) * M, blk[u]);
     };
 
     // forward sweep
@@ -278,6 +336,8 @@ template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, 
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
   static_assert(V * sizeof(Sout) == 16, "output lane row must be 16 bytes");
+  constexpr int U = 4;  // rows per block; D is a multiple of U
+  static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
@@ -292,46 +352,60 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     C r1[V], r2[V];
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
-    // forward sweep: rows 0..D-1 requested up front, row i + D after row i
+    // forward sweep: rows 0..D-1 requested up front (one copy group per
+    // row), then each block of U rows is consumed and its slots refilled
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
       if (r < N) copy_row<Sin, V>(ring_s + r * pitch, pin + (int64_t)r * M);
       cp_commit();
     }
-    int slot = 0;
 #pragma unroll 1
-    for (int i = 0; i < N; i++) {
-      cp_wait<D - 1>();
-      unsigned char* sp = ring + (size_t)slot * pitch;
-      C f[V];
-      IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(sp), f);
-      fwd_step<BW, ADJ, C, V>(cf, i, f, r1, r2);
-      if (i + D < N) {
-        IO<Sout, C, V>::store(pout + (int64_t)i * M, f);
-        copy_row<Sin, V>(ring_s + slot * pitch, pin + (int64_t)(i + D) * M);
-      } else {
-        IO<Sout, C, V>::store(reinterpret_cast<Sout*>(sp), f);  // tail stays on chip
+    for (int i0 = 0; i0 < N; i0 += U) {
+      cp_wait<D - U>();
+      const int n = (N - i0) < U ? (N - i0) : U;
+      const int s0 = i0 % D;
+      C f[U][V];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
+      fwd_block<BW, ADJ, C, V, U>(cf, i0, n, f, r1, r2);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int i = i0 + u;
+        if (u < n) {
+          if (i + D < N) {
+            IO<Sout, C, V>::store(pout + (int64_t)i * M, f[u]);
+            copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pin + (int64_t)(i + D) * M);
+          } else {
+            IO<Sout, C, V>::store(reinterpret_cast<Sout*>(ring + (size_t)(s0 + u) * pitch), f[u]);  // tail on chip
+          }
+        }
+        cp_commit();
       }
-      cp_commit();
-      slot = (slot + 1 == D) ? 0 : slot + 1;
     }
     // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
     // into the slot row i frees
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
     const int tail = N - D;
-    slot = (N - 1) % D;
 #pragma unroll 1
-    for (int i = N - 1; i >= 0; i--) {
-      if (i < tail) cp_wait<D - 1>();
-      unsigned char* sp = ring + (size_t)slot * pitch;
-      C f[V];
-      IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(sp), f);
-      bwd_step<BW, ADJ, C, V>(cf, i, f, r1, r2);
-      IO<Sout, C, V>::store(pout + (int64_t)i * M, f);
-      if (i - D >= 0) copy_row<Sout, V>(ring_s + slot * pitch, pout + (int64_t)(i - D) * M);
-      cp_commit();
-      slot = (slot == 0) ? D - 1 : slot - 1;
+    for (int top = N - 1; top >= 0; top -= U) {
+      const int n = (top + 1) < U ? (top + 1) : U;
+      if (top - (n - 1) < tail) cp_wait<D - U>();
+      C f[U][V];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
+      bwd_block<BW, ADJ, C, V, U>(cf, top, n, f, r1, r2);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int i = top - u;
+        if (u < n) {
+          IO<Sout, C, V>::store(pout + (int64_t)i * M, f[u]);
+          if (i - D >= 0) copy_row<Sout, V>(ring_s + (i % D) * pitch, pout + (int64_t)(i - D) * M);
+        }
+        cp_commit();
+      }
     }
     cp_wait<0>();
   }

@@ -24,6 +24,7 @@
 namespace bs {
 
 constexpr int kTmaRows = 32;         // rows per chunk = box height
+constexpr int kTmaU = 8;             // rows per register block (divides kTmaRows)
 constexpr int kTmaMaxChunks = 128;   // N <= 4096
 constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
 
@@ -128,12 +129,16 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       const int i0 = c * kTmaRows;
       const int rows = (N - i0) < kTmaRows ? (N - i0) : kTmaRows;
       if (lane < T) {
-#pragma unroll 4
-        for (int q = 0; q < rows; q++) {
-          const int i = i0 + q;
-          float f[1] = {widen<Sin>(land[(size_t)i * T + lane])};
-          fwd_step<BW, ADJ, float, 1>(cf, i, f, r1, r2);
-          d[(size_t)i * T + lane] = f[0];
+#pragma unroll 1
+        for (int q0 = 0; q0 < rows; q0 += kTmaU) {
+          const int n = (rows - q0) < kTmaU ? (rows - q0) : kTmaU;
+          float f[kTmaU][1];
+#pragma unroll
+          for (int u = 0; u < kTmaU; u++) f[u][0] = widen<Sin>(land[(size_t)(i0 + q0 + u) * T + lane]);
+          fwd_block<BW, ADJ, float, 1, kTmaU>(cf, i0 + q0, n, f, r1, r2);
+#pragma unroll
+          for (int u = 0; u < kTmaU; u++)
+            if (u < n) d[(size_t)(i0 + q0 + u) * T + lane] = f[u][0];
         }
       }
     }
@@ -152,12 +157,16 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       const int i0 = c * kTmaRows;
       const int rows = (N - i0) < kTmaRows ? (N - i0) : kTmaRows;
       if (lane < T) {
-#pragma unroll 4
-        for (int q = rows - 1; q >= 0; q--) {
-          const int i = i0 + q;
-          float f[1] = {d[(size_t)i * T + lane]};
-          bwd_step<BW, ADJ, float, 1>(cf, i, f, r1, r2);
-          d[(size_t)i * T + lane] = f[0];
+#pragma unroll 1
+        for (int top = i0 + rows - 1; top >= i0; top -= kTmaU) {
+          const int n = (top - i0 + 1) < kTmaU ? (top - i0 + 1) : kTmaU;
+          float f[kTmaU][1];
+#pragma unroll
+          for (int u = 0; u < kTmaU; u++) f[u][0] = d[(size_t)(u < n ? top - u : top) * T + lane];
+          bwd_block<BW, ADJ, float, 1, kTmaU>(cf, top, n, f, r1, r2);
+#pragma unroll
+          for (int u = 0; u < kTmaU; u++)
+            if (u < n) d[(size_t)(top - u) * T + lane] = f[u][0];
         }
       }
       fence_proxy_async();  // make the writes visible to the store's async proxy
