@@ -229,12 +229,15 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    (default 0: as many as shared memory and threads allow).
  *  BS_OPT_SWEEP_KERNEL: 0 (default) lets FP32-arithmetic interleaved solves
  *    use the on-chip kernel (forward values kept in shared memory, rows moved
- *    by TMA) where the shape qualifies; 1 forces the streaming kernels. */
+ *    by TMA) where the shape qualifies; 1 forces the streaming kernels.
+ *  BS_OPT_TMA_AHEAD: row chunks (32 rows each) the on-chip kernel keeps in
+ *    flight ahead of its forward sweep (default 0: 4). */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
   BS_OPT_SWEEP_KERNEL = 2,
-  BS_OPT_COUNT = 3
+  BS_OPT_TMA_AHEAD = 3,
+  BS_OPT_COUNT = 4
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

@@ -37,11 +37,17 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
 }
 
 // FP32 B (4-byte lane rows in pass 1), 8-byte slots in passes 2 and 3; ring of
-// D slots of 8 bytes per lane.
+// D slots of 8 bytes per lane.  Rows move in blocks of kRU: a block's ring
+// reads and coefficient loads are issued before its arithmetic, the chains
+// (the sweeps) run row by row, and the block's residuals -- independent of
+// each other once X0 is known -- interleave.
+constexpr int kRU = 4;
+
 template <int BW, int D, bool SMEM>
 __global__ void __launch_bounds__(128)
 k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int steps) {
   constexpr int W = 2 * BW + 1;
+  static_assert(D % kRU == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RefineCoefs<BW> cf = cg;
   size_t coef_bytes = 0;
@@ -90,28 +96,38 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
         if (r < N) cp_async4(ring_s + r * pitch, pb + (int64_t)r * M);
         cp_commit();
       }
-      int slot = 0;
 #pragma unroll 1
-      for (int i = 0; i < N; i++) {
-        cp_wait<D - 1>();
-        const float b = *reinterpret_cast<const float*>(ring + (size_t)slot * pitch);
-        if (i + D < N) cp_async4(ring_s + slot * pitch, pb + (int64_t)(i + D) * M);
-        cp_commit();
-        const float w = refine_fwd<BW>(cf, i, b, w1, w2);
-        ps[(int64_t)i * M] = make_float2(w, b);
-        slot = (slot + 1 == D) ? 0 : slot + 1;
+      for (int i0 = 0; i0 < N; i0 += kRU) {
+        cp_wait<D - kRU>();
+        const int n = (N - i0) < kRU ? (N - i0) : kRU;
+        const int s0 = i0 % D;
+        float b[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          if (u < n && i0 + u + D < N) cp_async4(ring_s + (s0 + u) * pitch, pb + (int64_t)(i0 + u + D) * M);
+          cp_commit();
+        }
+        float w[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) w[u] = refine_fwd<BW>(cf, i0 + u, b[u], w1, w2);
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) ps[(int64_t)(i0 + u) * M] = make_float2(w[u], b[u]);
       }
       cp_wait<0>();
     }
 
     // ---- pass 2: X0 = U^{-1} w; r = B - A X0; z = U'^{-1} r; slot <- {X0, z}
     {
-      float xw[W];  // X0 of rows i .. i+2BW (rows >= N are 0)
-      float bw[BW + 1];  // B of rows i .. i+BW
+      float xw[W + kRU];  // X0 of rows top-kRU+1 .. top+2BW (index q -> row top-kRU+1+q)
+      float bw[BW + kRU];
 #pragma unroll
-      for (int k = 0; k < W; k++) xw[k] = 0.f;
+      for (int k = 0; k < W + kRU; k++) xw[k] = 0.f;
 #pragma unroll
-      for (int k = 0; k <= BW; k++) bw[k] = 0.f;
+      for (int k = 0; k < BW + kRU; k++) bw[k] = 0.f;
       float z1 = 0.f, z2 = 0.f;
 #pragma unroll 1
       for (int r = 0; r < D; r++) {
@@ -119,34 +135,87 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
         if (row >= 0) cp_async8(ring_s + r * pitch, ps + (int64_t)row * M);
         cp_commit();
       }
-      int slot = 0;
+      // blocks of rows top, top-1, .., top-kRU+1 (rows < 0 read as 0)
 #pragma unroll 1
-      for (int i = N - 1; i >= -BW; i--) {
-        float x0 = 0.f, b = 0.f;
-        if (i >= 0) {
-          cp_wait<D - 1>();
-          const float2 wb = *reinterpret_cast<const float2*>(ring + (size_t)slot * pitch);
-          if (i - D >= 0) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i - D) * M);
-          cp_commit();
-          slot = (slot + 1 == D) ? 0 : slot + 1;
-          x0 = refine_bwd<BW>(cf, i, wb.x, xw);
-          b = wb.y;
+      for (int top = N - 1; top >= -BW; top -= kRU) {
+        // window shift: rows top+1 .. top+2BW move to the high end
+#pragma unroll
+        for (int k = W + kRU - 1; k >= kRU; k--) xw[k] = xw[k - kRU];
+#pragma unroll
+        for (int k = BW + kRU - 1; k >= kRU; k--) bw[k] = bw[k - kRU];
+        float wv[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          wv[u] = 0.f;
+          bw[kRU - 1 - u] = 0.f;
         }
+        if (top >= 0) {
+          cp_wait<D - kRU>();
+          const int s0 = (N - 1 - top) % D;
 #pragma unroll
-        for (int k = W - 1; k > 0; k--) xw[k] = xw[k - 1];
-        xw[0] = x0;
+          for (int u = 0; u < kRU; u++) {
+            if (top - u >= 0) {
+              const float2 wb = *reinterpret_cast<const float2*>(ring + (size_t)(s0 + u) * pitch);
+              wv[u] = wb.x;
+              bw[kRU - 1 - u] = wb.y;
+            }
+          }
 #pragma unroll
-        for (int k = BW; k > 0; k--) bw[k] = bw[k - 1];
-        bw[0] = b;
-        const int q = i + BW;  // row whose neighbourhood x0_{q-BW..q+BW} is now complete
-        if (q < N) {
-          if (steps == 0) {
-            px[(int64_t)q * M] = (double)xw[BW];
-          } else {
-            const float z = refine_resid_z<BW>(cf, q, bw[BW], xw, z1, z2);
-            ps[(int64_t)q * M] = make_float2(xw[BW], z);
+          for (int u = 0; u < kRU; u++) {
+            const int i = top - u;
+            if (i >= 0 && i - D >= 0) cp_async8(ring_s + (s0 + u) * pitch, ps + (int64_t)(i - D) * M);
+            cp_commit();
           }
         }
+        // X0 chain, rows top down (row top-u sits at xw[kRU-1-u])
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          const int i = top - u;
+          float x0 = 0.f;
+          if (i >= 0) {
+            const float nx[2] = {xw[kRU - u], xw[kRU - u + 1]};
+            x0 = refine_bwd<BW>(cf, i, wv[u], nx);
+          }
+          xw[kRU - 1 - u] = x0;
+        }
+        // residuals of rows q = top-u+BW (neighbourhood complete), then the z chain
+        float zr[kRU];
+
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          const int q = top - u + BW;
+          zr[u] = 0.f;
+          if (q < N && q >= 0) {
+            float x[W];
+#pragma unroll
+            for (int k = 0; k < W; k++) x[k] = xw[kRU - 1 - u + k];
+            float ah[W], al[W];
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+              ah[k] = cf.ahi[k][q];
+              al[k] = cf.alo[k][q];
+            }
+            zr[u] = residual_row<W>(bw[kRU - 1 - u + BW], x, ah, al);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          const int q = top - u + BW;
+          if (q < N && q >= 0) {
+            if (steps == 0) {
+              px[(int64_t)q * M] = (double)xw[kRU - 1 - u + BW];
+            } else {
+              float z = zr[u] * cf.ul[0][q];
+              if (BW == 2) z = fmaf(-cf.ul[2][q], z2, z);
+              z = fmaf(-cf.ul[1][q], z1, z);
+              z2 = z1;
+              z1 = z;
+              ps[(int64_t)q * M] = make_float2(xw[kRU - 1 - u + BW], z);
+            }
+
+          }
+        }
+
       }
       cp_wait<0>();
     }
@@ -160,15 +229,26 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
         if (r < N) cp_async8(ring_s + r * pitch, ps + (int64_t)r * M);
         cp_commit();
       }
-      int slot = 0;
 #pragma unroll 1
-      for (int i = 0; i < N; i++) {
-        cp_wait<D - 1>();
-        const float2 xz = *reinterpret_cast<const float2*>(ring + (size_t)slot * pitch);
-        if (i + D < N) cp_async8(ring_s + slot * pitch, ps + (int64_t)(i + D) * M);
-        cp_commit();
-        slot = (slot + 1 == D) ? 0 : slot + 1;
-        px[(int64_t)i * M] = refine_out<BW>(cf, i, xz.x, xz.y, d1, d2);
+      for (int i0 = 0; i0 < N; i0 += kRU) {
+        cp_wait<D - kRU>();
+        const int n = (N - i0) < kRU ? (N - i0) : kRU;
+        const int s0 = i0 % D;
+        float2 xz[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) xz[u] = *reinterpret_cast<const float2*>(ring + (size_t)(s0 + u) * pitch);
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          if (u < n && i0 + u + D < N) cp_async8(ring_s + (s0 + u) * pitch, ps + (int64_t)(i0 + u + D) * M);
+          cp_commit();
+        }
+        double xo[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) xo[u] = refine_out<BW>(cf, i0 + u, xz[u].x, xz[u].y, d1, d2);
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) px[(int64_t)(i0 + u) * M] = xo[u];
       }
       cp_wait<0>();
     }

@@ -81,6 +81,19 @@ __device__ __forceinline__ float refine_resid_z(const RefineCoefs<BW>& cf, int q
   return z;
 }
 
+// Exact FP32 -> FP64 widening with integer operations (the FP64 pipe, which
+// also executes conversions on GB300, stays free): for normal numbers the
+// exponent is rebiased and the mantissa shifted; zero, subnormals, inf and
+// NaN take the conversion instruction.
+__device__ __forceinline__ double widen_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  const uint32_t lo = b << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // pass 3: second sweep of A = U' L' at row i and the FP64 sum X0 + d
 template <int BW>
 __device__ __forceinline__ double refine_out(const RefineCoefs<BW>& cf, int i, float x0, float z, float& d1, float& d2) {
@@ -89,7 +102,7 @@ __device__ __forceinline__ double refine_out(const RefineCoefs<BW>& cf, int i, f
   d = fmaf(-cf.ul[3][i], d1, d);
   d2 = d1;
   d1 = d;
-  return (double)x0 + (double)d;
+  return widen_exact(x0) + widen_exact(d);
 }
 
 }  // namespace bs

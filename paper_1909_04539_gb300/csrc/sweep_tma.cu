@@ -23,6 +23,8 @@
 
 namespace bs {
 
+int64_t option(int o);
+
 constexpr int kTmaRows = 32;         // rows per chunk = box height
 constexpr int kTmaU = 8;             // rows per register block (divides kTmaRows)
 constexpr int kTmaMaxChunks = 128;   // N <= 4096
@@ -86,7 +88,7 @@ __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) {
 template <int BW, bool ADJ, bool SMEM, typename Sin, int T>
 __global__ void __launch_bounds__(32)
 k_sweep_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, Coefs<float> cf_g,
-            int N, int64_t M) {
+            int N, int64_t M, int ahead) {
   constexpr bool kStage = !std::is_same<Sin, float>::value;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar[kTmaMaxChunks];
@@ -112,18 +114,20 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     const int j0 = (int)(t * T);
     fence_proxy_async();  // earlier reads of this smem precede the async writes below
     __syncwarp();
+    auto issue = [&](int c) {
+      mbar_expect_tx(mbar0 + 8 * c, chunk_in);
+      tma_load_2d(smem_u32(land + (size_t)c * kTmaRows * T), &tin, j0, c * kTmaRows, mbar0 + 8 * c);
+    };
     if (lane == 0) {
       bulk_wait_read0();  // the previous tile's stores have read their rows
-      for (int c = 0; c < nch; c++) {
-        mbar_expect_tx(mbar0 + 8 * c, chunk_in);
-        tma_load_2d(smem_u32(land + (size_t)c * kTmaRows * T), &tin, j0, c * kTmaRows, mbar0 + 8 * c);
-      }
+      for (int c = 0; c < nch && c < ahead; c++) issue(c);
     }
     __syncwarp();
     // forward sweep, chunk by chunk as the rows land
     float r1[1] = {0.f}, r2[1] = {0.f};
     int c = 0;
     for (; c < nch; c++) {
+      if (lane == 0 && c + ahead < nch) issue(c + ahead);  // keep `ahead` chunks in flight
       const bool ok = mbar_wait_bounded(mbar0 + 8 * c, parity);
       if (!__all_sync(0xffffffffu, ok)) break;
       const int i0 = c * kTmaRows;
@@ -145,7 +149,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     if (c < nch) {  // a load never completed: record, drain what we started, leave
       if (lane == 0) {
         atomicExch(&g_device_status, 1);
-        for (int q = c; q < nch; q++) mbar_wait_bounded(mbar0 + 8 * q, parity);
+        for (int q = c; q < nch && q < c + ahead + 1; q++) mbar_wait_bounded(mbar0 + 8 * q, parity);
         bulk_wait0();
       }
       __syncwarp();
@@ -257,14 +261,16 @@ static int try_launch(const SweepPlan& p, int N, const Sin* in, float* out, int6
   int64_t grid = (int64_t)di.sms * per;
   const int64_t tiles = (M + T - 1) / T;
   if (grid > tiles) grid = tiles;
-  void (*k)(const CUtensorMap, const CUtensorMap, Coefs<float>, int, int64_t);
+  void (*k)(const CUtensorMap, const CUtensorMap, Coefs<float>, int, int64_t, int);
   if (T == 32)
     k = sc ? k_sweep_tma<BW, ADJ, true, Sin, 32> : k_sweep_tma<BW, ADJ, false, Sin, 32>;
   else
     k = sc ? k_sweep_tma<BW, ADJ, true, Sin, 16> : k_sweep_tma<BW, ADJ, false, Sin, 16>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) {
-    k<<<(int)grid, 32, bytes, st>>>(mi, mo, cf, N, M);
+    int ahead = (int)option(BS_OPT_TMA_AHEAD);
+    if (ahead <= 0) ahead = 4;
+    k<<<(int)grid, 32, bytes, st>>>(mi, mo, cf, N, M, ahead);
     e = cudaGetLastError();
   }
   *err = e;
