@@ -284,6 +284,7 @@ def run_ours(args):
     # end to end through the public API with host buffers
     e2e = run_e2e(bs, f, N, M, st, args, world)
     serving = None if args.no_serving else run_serving(bs)
+    others, other_samples = run_other_configs(bs, st, hbm)
 
     clocks = clk.summary()
     line = {
@@ -301,11 +302,12 @@ def run_ours(args):
         "roofline": roof,
         "e2e": e2e,
         "serving": serving,
+        "other_workloads": others,
         "gpu_launches": 4 * args.steps,  # f64 solve, refine solve, adjoint, band gradient
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, errs = cpu_baseline(args, bands, sample)
+        cb, errs = cpu_baseline(args, bands, sample, other_samples)
         line["cpu_baseline"] = cb
         line["rel_err_vs_oracle"] = errs
     if rank == 0:
@@ -403,6 +405,70 @@ def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=400, load=0.7, budget=24 <
     }
 
 
+def run_other_configs(bs, st, hbm):
+    """The other workloads, each timed alone (median of CUDA-event timings;
+    operands larger than L2 except the small random case): sampled results
+    are kept for the oracle comparison of the CPU-baseline leg."""
+    import torch
+    import synth
+
+    out, samples = {}, {}
+    # random tridiagonal, N=64, M=1024, FP64 (launch-bound, L2-resident)
+    bands, Bh = synth.random_tri_case(64, 1024, 0)
+    f = bs.Factor(bands)
+    B0 = torch.tensor(Bh, device="cuda")
+    X = B0.clone()
+    ms = time_alone(lambda: (X.copy_(B0), bs.solve(f, X)), st, reps=200) - \
+        time_alone(lambda: X.copy_(B0), st, reps=200)
+    X.copy_(B0)
+    bs.solve(f, X)
+    out["random_tri_N64_M1024_f64"] = {"us_per_solve": ms * 1e3, "unknowns_per_s": 64 * 1024 / (ms * 1e-3)}
+    samples["random_tri"] = (bands, Bh, X.cpu().numpy(), None)
+    # spline [1,4,1]/6, N=1024, M=2^20: FP64 plain vs FP32-stored + refinement
+    N, M = 1024, 1 << 20
+    bands = synth.spline_bands(N)
+    f = bs.Factor(bands)
+    B32 = synth.spline_rhs(N, M, 0, "cuda")
+    B64 = B32.double()
+    X64 = B64.clone()
+    XR = torch.empty_like(B64)
+    t64 = time_alone(lambda: bs.solve(f, X64), st, reps=10)
+    tr = time_alone(lambda: bs.solve_refine(f, B32, XR), st, reps=10)
+    X64.copy_(B64)
+    bs.solve(f, X64)
+    bs.solve_refine(f, B32, XR)
+    cols = np.random.default_rng(11).choice(M, 256, replace=False)
+    samples["spline"] = (bands, B64[:, cols].cpu().numpy(), X64[:, cols].cpu().numpy(), XR[:, cols].cpu().numpy())
+    nm = N * M
+    out["spline_N1024_M1048576"] = {
+        "f64_solve": {"ms": t64, "unknowns_per_s": nm / (t64 * 1e-3), "hbm_gbs": 16 * nm / (t64 * 1e-3) / 1e9},
+        "refine_solve": {"ms": tr, "unknowns_per_s": nm / (tr * 1e-3), "hbm_gbs": 12 * nm / (tr * 1e-3) / 1e9,
+                         "hbm_frac_of_measured": 12 * nm / (tr * 1e-3) / 1e9 / hbm},
+        "refine_over_f64_speedup": t64 / tr}
+    del B32, B64, X64, XR
+    torch.cuda.empty_cache()
+    # ADI 4096^2, r = 0.5: half-steps on both axes, forward and adjoint, FP64 and FP32
+    n, r = 4096, 0.5
+    f = bs.Factor(synth.adi_bands(n, r))
+    adi = {}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        u = synth.adi_field(n, 0, "cuda", dt)
+        o = torch.empty_like(u)
+        for axis in (0, 1):
+            for adj in (False, True):
+                t = time_alone(lambda: bs.adi_halfstep(f, u, r, axis, out=o, adjoint=adj), st, reps=10)
+                es = 8 if dt == torch.float64 else 4
+                adi[f"{name}_axis{axis}{'_adjoint' if adj else ''}"] = {
+                    "ms": t, "unknowns_per_s": n * n / (t * 1e-3), "hbm_gbs": 2 * es * n * n / (t * 1e-3) / 1e9}
+        if dt == torch.float64:
+            half = bs.adi_halfstep(f, u, r, 0)
+            full = bs.adi_halfstep(f, half, r, 1)
+            rows = np.random.default_rng(12).choice(n, 8, replace=False)
+            samples["adi"] = (r, u.cpu().numpy(), full.cpu().numpy(), rows)
+    out["adi_4096x4096"] = adi
+    return out, samples
+
+
 def time_alone(fn, st, reps=50, warm=3) -> float:
     """Median per-call milliseconds of fn on stream st (CUDA events)."""
     import torch
@@ -476,7 +542,7 @@ def _oracle_step(oracle, bands, B, G):
     return X
 
 
-def cpu_baseline(args, bands, sample, target_s: float = 12.0):
+def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0):
     """The oracle, as it stands, timed on a bounded column sample of the
     workload (the very columns the GPU solved first), which also gives the
     GPU's error against it."""
@@ -494,6 +560,17 @@ def cpu_baseline(args, bands, sample, target_s: float = 12.0):
             "refine_solve": float(np.linalg.norm(sample["XR"] - XR) / np.linalg.norm(XR)),
             "tolerance": {"f64_solve": 1e-12, "refine_solve": 1e-12, "f32_solve": 2e-5},
             "systems_checked": int(m0)}
+    for name, smp in (other_samples or {}).items():
+        if name == "adi":
+            r, u, full, rows = smp
+            ref = oracle.adi_halfstep(oracle.adi_halfstep(u, r, 0), r, 1)
+            errs["adi_4096_full_step_f64"] = float(np.linalg.norm(full - ref) / np.linalg.norm(ref))
+        else:
+            b, Bs, X64s, XRs = smp
+            ref = oracle.solve(b, Bs)
+            errs[f"{name}_f64_solve"] = float(np.linalg.norm(X64s - ref) / np.linalg.norm(ref))
+            if XRs is not None:
+                errs[f"{name}_refine_solve"] = float(np.linalg.norm(XRs - ref) / np.linalg.norm(ref))
     # timing: the oracle step on a column block of the same batch, grown
     # until one step takes at least a quarter of target_s, then repeated to ~target_s
     Ball = sample["B_all"]

@@ -227,9 +227,12 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    on the device runs at once).
  *  BS_OPT_BLOCKS_PER_SM: cap on resident CTAs per SM of the persistent grids
  *    (default 0: as many as shared memory and threads allow).
- *  BS_OPT_SWEEP_KERNEL: 0 (default) lets FP32-arithmetic interleaved solves
- *    use the on-chip kernel (forward values kept in shared memory, rows moved
- *    by TMA) where the shape qualifies; 1 forces the streaming kernels.
+ *  BS_OPT_SWEEP_KERNEL: 0 (default) and 1 use the streaming kernels; 2 lets
+ *    FP32-arithmetic interleaved solves use the on-chip kernel (forward values
+ *    kept in shared memory, rows moved by TMA) where the shape qualifies.  The
+ *    on-chip kernel moves only the compulsory bytes but fits ~100 systems per
+ *    SM at N = 512, too few to hide latency; it is slower on the workloads
+ *    measured so far and kept as an option.
  *  BS_OPT_TMA_AHEAD: row chunks (32 rows each) the on-chip kernel keeps in
  *    flight ahead of its forward sweep (default 0: 4). */
 typedef enum {

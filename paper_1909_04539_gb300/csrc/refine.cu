@@ -284,13 +284,15 @@ static cudaError_t launch_refine_bw(bs_handle h, const float* B, double* X, int6
   if (per_sm > 2048 / tpb) per_sm = 2048 / tpb;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)d.sms * per_sm;
-  // Bound the systems in flight so that their 8-byte slots (N per system)
-  // stay in L2 between the passes: by default half of L2.
-  int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
-  if (budget <= 0) budget = (int64_t)d.l2_bytes / 2;
-  int64_t cap = budget / ((int64_t)tpb * N * 8);
-  if (cap < d.sms) cap = d.sms;
-  if (grid > cap) grid = cap;
+  // Optional bound on the systems in flight (their 8-byte slots, N per
+  // system, between the passes); off by default: the kernel is bound by
+  // latency and wants every system in flight.
+  const int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
+  if (budget > 0) {
+    int64_t cap = budget / ((int64_t)tpb * N * 8);
+    if (cap < d.sms) cap = d.sms;
+    if (grid > cap) grid = cap;
+  }
   const int64_t need = (M + tpb - 1) / tpb;
   if (grid > need) grid = need;
   cudaError_t e;

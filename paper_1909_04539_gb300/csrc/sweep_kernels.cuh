@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace bs {
@@ -61,6 +63,17 @@ struct IO<float, float, 4> {
   }
   static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct IO<float, float, 2> {
+  static __device__ __forceinline__ void load(const float* p, float (&o)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
   }
 };
 template <>
@@ -335,7 +348,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
-  static_assert(V * sizeof(Sout) == 16, "output lane row must be 16 bytes");
+  static_assert(V * sizeof(Sout) == 16 || V * sizeof(Sout) == 8, "output lane row must be 8 or 16 bytes");
   constexpr int U = 4;  // rows per block; D is a multiple of U
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -354,11 +367,14 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
     // forward sweep: rows 0..D-1 requested up front (one copy group per
     // row), then each block of U rows is consumed and its slots refilled
+    const Sin* pnext = pin;  // next row to request
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
-      if (r < N) copy_row<Sin, V>(ring_s + r * pitch, pin + (int64_t)r * M);
+      if (r < N) copy_row<Sin, V>(ring_s + r * pitch, pnext);
+      pnext += M;
       cp_commit();
     }
+    Sout* prow = pout;  // output row i0
 #pragma unroll 1
     for (int i0 = 0; i0 < N; i0 += U) {
       cp_wait<D - U>();
@@ -374,12 +390,14 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
         const int i = i0 + u;
         if (u < n) {
           if (i + D < N) {
-            IO<Sout, C, V>::store(pout + (int64_t)i * M, f[u]);
-            copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pin + (int64_t)(i + D) * M);
+            IO<Sout, C, V>::store(prow, f[u]);
+            copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pnext);
           } else {
             IO<Sout, C, V>::store(reinterpret_cast<Sout*>(ring + (size_t)(s0 + u) * pitch), f[u]);  // tail on chip
           }
         }
+        prow += M;
+        pnext += M;
         cp_commit();
       }
     }
@@ -388,6 +406,8 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
     const int tail = N - D;
+    prow = pout + (int64_t)(N - 1) * M;               // output row `top`
+    const Sout* pback = pout + (int64_t)(N - 1 - D) * M;  // row top - D, requested next
 #pragma unroll 1
     for (int top = N - 1; top >= 0; top -= U) {
       const int n = (top + 1) < U ? (top + 1) : U;
@@ -401,9 +421,11 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       for (int u = 0; u < U; u++) {
         const int i = top - u;
         if (u < n) {
-          IO<Sout, C, V>::store(pout + (int64_t)i * M, f[u]);
-          if (i - D >= 0) copy_row<Sout, V>(ring_s + (i % D) * pitch, pout + (int64_t)(i - D) * M);
+          IO<Sout, C, V>::store(prow, f[u]);
+          if (i - D >= 0) copy_row<Sout, V>(ring_s + (i % D) * pitch, pback);
         }
+        prow -= M;
+        pback -= M;
         cp_commit();
       }
     }
@@ -572,9 +594,18 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
   const Coefs<C> cf = coefs_of<C>(base, N);
   const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
                    (reinterpret_cast<uintptr_t>(out) % (VEC * sizeof(Sout)) == 0);
-#define BS_DISPATCH(BWV, ADJV)                                                          \
-  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, C, Sin, Sout>(cf, N, in, out, M, st); \
-  if (vec) return launch_il<BWV, ADJV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);        \
+  // FP32 with few systems per SM: half-width vectors (8-byte lane rows) give
+  // twice the warps to hide the latency of the recurrences
+  constexpr bool kHalf = std::is_same<Sin, float>::value && VEC == 4;
+  const bool half = kHalf && (M % 2 == 0) && (reinterpret_cast<uintptr_t>(in) % 8 == 0) &&
+                    (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
+                    (M / VEC < (int64_t)device_info().sms * 32 * 8);
+#define BS_DISPATCH(BWV, ADJV)                                                                       \
+  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, C, Sin, Sout>(cf, N, in, out, M, st);          \
+  if constexpr (kHalf) {                                                                             \
+    if (half) return launch_il<BWV, ADJV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, st);     \
+  }                                                                                                  \
+  if (vec) return launch_il<BWV, ADJV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);                      \
   return launch_il<BWV, ADJV, C, Sin, Sout, 1>(cf, N, in, out, M, st);
   if (p.bw == 1) {
     if (!adjoint) { BS_DISPATCH(1, false) } else { BS_DISPATCH(1, true) }
