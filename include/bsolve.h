@@ -131,6 +131,28 @@ bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* 
 bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layout, int64_t M,
                            const void* X, double* dbands, bs_stream stream);
 
+/* bs_band_grad without any device allocation (the paper has no counterpart).
+ * Some callers cannot allocate device memory at call time: a service that has
+ * handed all device memory to its own pool allocator, or a latency-bound loop
+ * where an allocation could block on the driver.  This entry point computes
+ * exactly what bs_band_grad computes (same kernels, same fixed reduction
+ * order, bitwise the same result) but keeps its per-chunk partial sums in a
+ * fixed device array inside the library (2 MiB, held on every GPU that loads
+ * the library until the process exits) and allocates nothing.  The caller
+ * still provides GB, X and dbands as for bs_band_grad.
+ * Limit: the partial sums need (system chunks) x width x N doubles and the
+ * array holds 262144 of them (about 20480 are needed up to N = 4096, then
+ * width x N): N above 52428 (width 5) or 87381 (width 3) is rejected with
+ * BS_EINVAL and a message naming the size -- use bs_band_grad there.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents (every partial is
+ * written before it is read, so nothing needs clearing): calls that can
+ * overlap on the GPU -- on different streams, or from different host threads
+ * -- race and must be serialised by the caller. */
+bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout,
+                               int64_t M, double* dbands, bs_stream stream);
+
 /* One Peaceman-Rachford ADI half-step for u_t = u_xx + u_yy on an ny x nx
  * grid stored row-major (U[y*nx + x], device), homogeneous Dirichlet
  * boundaries (zero outside the grid):

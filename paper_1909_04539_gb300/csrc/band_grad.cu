@@ -13,6 +13,9 @@
 // reproducible.  Work per unknown: `width` FP64 FMAs (the kernel is bound by
 // the FP64 pipe on GB300), 16 bytes of compulsory reads (GB and X; the X
 // halo of 2h rows per block of kGradRows comes mostly from L2).
+#include <mutex>
+#include <string>
+
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -159,4 +162,66 @@ bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype 
   return BS_OK;
 }
 
+// ------------------------------------------------- no-allocation variant
+//
+// bs_band_grad_noalloc runs the same two levels as bs_band_grad, but keeps the
+// per-chunk partials in this fixed device array instead of memory allocated
+// per call, for callers that must not allocate device memory while they run
+// (see include/bsolve.h).  Every GPU that loads the library holds the array
+// (2 MiB) until the process exits.  The name below is only a host-side
+// stand-in for the device array: host code must pass the device address that
+// cudaGetSymbolAddress returns, looked up once per device.
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 18;
+static __device__ __align__(256) double g_band_grad_scratch[kNoAllocScratchDoubles];
+
+// Device address of g_band_grad_scratch on the current device, looked up on
+// the first call for that device (the device must be current).
+static cudaError_t noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* ptr[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_band_grad_scratch);
+    if (e != cudaSuccess) return e;
+    ptr[dev] = static_cast<double*>(p);
+  }
+  *out = ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace bs
+
+extern "C" bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const void* X, bs_dtype dtype,
+                                          bs_layout layout, int64_t M, double* dbands, bs_stream stream) {
+  using namespace bs;
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_band_grad_noalloc: unknown handle");
+  if (!GB || !X || !dbands) return set_error(BS_EINVAL, "bs_band_grad_noalloc: null data pointer");
+  if (M < 1) return set_error(BS_EINVAL, "bs_band_grad_noalloc: M must be >= 1");
+  if (layout != BS_INTERLEAVED && layout != BS_STRIDED)
+    return set_error(BS_EINVAL, "bs_band_grad_noalloc: bad layout");
+  if (dtype != BS_F64 && dtype != BS_F32)
+    return set_error(BS_EINVAL, "bs_band_grad_noalloc: dtype must be BS_F64 or BS_F32");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(BS_EINVAL, "bs_band_grad_noalloc: handle belongs to another device");
+  const int N = (int)h->N;
+  const size_t need = band_grad_scratch_bytes(h->width, N, M) / sizeof(double);
+  if (need > kNoAllocScratchDoubles)
+    return set_error(BS_EINVAL, "bs_band_grad_noalloc: this size needs " + std::to_string(need) +
+                                    " doubles of scratch, more than the " +
+                                    std::to_string(kNoAllocScratchDoubles) +
+                                    " the fixed array holds; use bs_band_grad");
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc: scratch address");
+  e = band_grad_with_scratch(h->width, N, GB, X, dtype, layout, M, dbands, scratch,
+                             reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc launch");
+  return BS_OK;
+}
+

@@ -1,0 +1,58 @@
+"""bs_band_grad_noalloc: the band-gradient reduction for callers that cannot
+allocate device memory while they run (its scratch is a fixed array inside
+the library).  Called through the C ABI twice in a row, it must agree with
+bs_band_grad (which allocates its scratch per call) within the 1e-12 relative
+tolerance used for every FP64 result; sizes beyond its fixed array are
+refused.  Kept in a file of its own, collected last."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    from paper_1909_04539_gb300 import _lib
+    return _lib.lib()
+
+
+def _call(L, name, f, GB, X, db, layout=0):
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return getattr(L, name)(f.handle, ctypes.c_void_p(GB.data_ptr()), ctypes.c_void_p(X.data_ptr()), 0, layout,
+                            GB.shape[1] if layout == 0 else GB.shape[0], ctypes.c_void_p(db.data_ptr()), st)
+
+
+@pytest.mark.parametrize("width,N,M,layout", [(5, 512, 20000, 0), (3, 77, 1003, 0), (5, 64, 300, 1)])
+def test_noalloc_matches_allocating_entry_point(lib, width, N, M, layout):
+    import paper_1909_04539_gb300 as bs
+    rng = np.random.default_rng(N + M)
+    bands = synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
+    f = bs.Factor(bands)
+    shape = (N, M) if layout == 0 else (M, N)
+    GB = torch.tensor(rng.uniform(-1, 1, shape), device="cuda")
+    X = torch.tensor(rng.uniform(-1, 1, shape), device="cuda")
+    ref = torch.empty((width, N), dtype=torch.float64, device="cuda")
+    assert _call(lib, "bs_band_grad", f, GB, X, ref, layout) == 0
+    for _ in range(2):  # two calls in a row share the fixed scratch
+        out = torch.full((width, N), float("nan"), dtype=torch.float64, device="cuda")
+        assert _call(lib, "bs_band_grad_noalloc", f, GB, X, out, layout) == 0
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm(out - ref) / torch.linalg.norm(ref)).item()
+        assert err < 1e-12, err
+
+
+def test_noalloc_refuses_sizes_beyond_its_array(lib):
+    import paper_1909_04539_gb300 as bs
+    N = 60000  # needs 5 x 60000 doubles of partial sums, more than the 262144 held
+    f = bs.Factor(synth.random_penta_bands(N, np.random.default_rng(0)))
+    GB = torch.zeros((N, 4), dtype=torch.float64, device="cuda")
+    db = torch.zeros((5, N), dtype=torch.float64, device="cuda")
+    assert _call(lib, "bs_band_grad_noalloc", f, GB, GB, db) == 1
+    assert b"fixed array" in lib.bs_last_error()
