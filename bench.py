@@ -281,6 +281,14 @@ def run_ours(args):
     f32_alone["hbm_frac_of_measured"] = f32_alone["hbm_gbs"] / hbm
     del X32
 
+    # the three-pass refinement on the system residual (not part of the step)
+    XS = torch.empty_like(XR)
+    ms_sys = time_alone(lambda: bs.solve_refine(f, B32, XS, mode=bs.REFINE_SYSTEM), st, reps=30)
+    refine_system_alone = {"ms": ms_sys, "unknowns_per_s": nm / (ms_sys * 1e-3),
+                           "hbm_gbs": 12 * nm / (ms_sys * 1e-3) / 1e9,
+                           "rel_residual": rel_residual(bands, B32.double(), XS)}
+    del XS
+
     # end to end through the public API with host buffers
     e2e = run_e2e(bs, f, N, M, st, args, world)
     serving = None if args.no_serving else run_serving(bs)
@@ -296,6 +304,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (systems partitioned, no collective)"},
         "rel_residual": resid,
         "f32_solve_alone": f32_alone,
+        "refine_system_alone": refine_system_alone,
         "hbm_gbs_step": (sum(p["bytes"] for p in paths.values())) / (ms_step * 1e-3) / 1e9,
         "paths": {n: {k: (round(v, 6) if isinstance(v, float) else v) for k, v in p.items()}
                   for n, p in paths.items()},

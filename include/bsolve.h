@@ -101,20 +101,27 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
 /* Mixed-precision solve (FP32 storage, FP64 result): X = A^{-1} B with B
  * stored in FP32 (float[N*M], device, read only) and X written in FP64
  * (double[N*M], device).  The sweeps run in FP32; with refine_steps = 1 one
- * step of iterative refinement follows, with the residual r = B - A X0 of
- * the FP32 solution X0 evaluated to FP64 accuracy (FP64 bands split into
- * FP32 pairs, error-free products and sums) and the correction added in
- * FP64.  The correction solve uses the reversed elimination A = U' L',
- * factorised once with the handle, so the whole solve is three passes over
- * each system in one kernel.  refine_steps = 0 returns the FP32 solution
- * widened to FP64.  X doubles as the workspace of the passes.  Only
- * BS_INTERLEAVED and b_dtype BS_F32 are implemented (BS_EUNSUPPORTED
- * otherwise); refine_steps > 1 is BS_EUNSUPPORTED.  B and X must not
- * overlap.  Returns BS_ESINGULAR if the reversed elimination of A met a bad
- * pivot when the handle was built (plain solves still work then).
+ * step of iterative refinement follows, with residuals evaluated to FP64
+ * accuracy in FP32 arithmetic (FP64 coefficients split into FP32 pairs,
+ * error-free products and sums) and the correction added in FP64:
+ *   mode BS_REFINE_FACTOR (default, two passes per system): each triangular
+ *     factor of A = L U is solved in FP32 and corrected once with its own
+ *     residual -- B - L w on the way up, y - U x on the way down;
+ *   mode BS_REFINE_SYSTEM (three passes): the residual of the whole system,
+ *     r = B - A X0, of the FP32 solution X0 drives one correction solve
+ *     through the reversed elimination A = U' L' (factorised once with the
+ *     handle) so that its first sweep follows the backward sweep of X0.
+ * Both reach ~1e-15 relative error on well-conditioned bands.
+ * refine_steps = 0 returns the FP32 solution widened to FP64 (mode ignored).
+ * X doubles as the workspace of the passes.  Only BS_INTERLEAVED and b_dtype
+ * BS_F32 are implemented (BS_EUNSUPPORTED otherwise); refine_steps > 1 is
+ * BS_EUNSUPPORTED.  B and X must not overlap.  BS_REFINE_SYSTEM returns
+ * BS_ESINGULAR if the reversed elimination of A met a bad pivot when the
+ * handle was built (the other solves still work then).
  * Not in the paper: the paper's solvers work in a single precision. */
+typedef enum { BS_REFINE_FACTOR = 0, BS_REFINE_SYSTEM = 1 } bs_refine_mode;
 bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
-                          int64_t M, int refine_steps, bs_stream stream);
+                          int64_t M, int refine_steps, bs_refine_mode mode, bs_stream stream);
 
 /* Adjoint solve: G <- A^{-T} G, in place, reusing the same factorisation
  * (A^T = R^T L^T, a forward sweep with R^T then a backward sweep with L^T).
@@ -196,7 +203,8 @@ bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtyp
  *                              plain FP64 solve (as bs_solve); arena N*M*8 B.
  *   mode BS_SERVE_F32_REFINE : B float[N*M], X double[N*M]; mixed-precision
  *                              solve with one refinement step (as
- *                              bs_solve_refine); arena N*M*12 B.
+ *                              bs_solve_refine, BS_REFINE_FACTOR); arena
+ *                              N*M*12 B.
  * Layout is interleaved.  The worker admits queued requests in arrival order
  * while their arena bytes fit, puts every newly admitted request into one
  * batch and runs the batch on one of `n_streams` streams: host-to-device

@@ -20,7 +20,7 @@ SIGNATURES = {
     "bs_lhs_bytes": (i64, [i32, i64, i32]),
     "bs_solve": (i32, [vp, vp, i32, i32, i64, vp]),
     "bs_solve_bf16": (i32, [vp, vp, vp, i32, i64, vp]),
-    "bs_solve_refine": (i32, [vp, vp, i32, vp, i32, i64, i32, vp]),
+    "bs_solve_refine": (i32, [vp, vp, i32, vp, i32, i64, i32, i32, vp]),
     "bs_solve_adjoint": (i32, [vp, vp, i32, i32, i64, vp, vp, vp]),
     "bs_adi_halfstep": (i32, [vp, vp, vp, i32, i64, i64, ctypes.c_double, i32, i32, vp]),
     "bs_band_grad": (i32, [vp, vp, vp, i32, i32, i64, vp, vp]),

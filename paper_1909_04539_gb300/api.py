@@ -135,11 +135,17 @@ def solve_bf16(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, layout
     return X
 
 
+REFINE_FACTOR = 0
+REFINE_SYSTEM = 1
+
+
 def solve_refine(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, refine_steps: int = 1,
-                 layout: str = "interleaved", stream=None) -> torch.Tensor:
+                 layout: str = "interleaved", stream=None, mode: int = REFINE_FACTOR) -> torch.Tensor:
     """FP32-stored B (float32), FP32 sweeps plus ``refine_steps`` (0 or 1)
-    steps of iterative refinement with an FP64-accurate residual; returns the
-    FP64 solution X (also used as workspace)."""
+    steps of iterative refinement with FP64-accurate residuals (``mode``:
+    REFINE_FACTOR per triangular factor, two passes; REFINE_SYSTEM on
+    r = B - A X0, three passes); returns the FP64 solution X (also used as
+    workspace)."""
     M = _batch(f, B, layout, "B")
     if B.dtype != torch.float32:
         raise ValueError("B must be float32")
@@ -150,7 +156,7 @@ def solve_refine(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, refi
         raise ValueError("X must be float64 with B's shape")
     check(lib().bs_solve_refine(f.handle, ctypes.c_void_p(B.data_ptr()), _DTYPE[B.dtype],
                                 ctypes.c_void_p(X.data_ptr()), _LAYOUT[layout], M, int(refine_steps),
-                                _stream(stream)), "bs_solve_refine")
+                                int(mode), _stream(stream)), "bs_solve_refine")
     return X
 
 

@@ -76,12 +76,14 @@ bool bad(double v) { return v == 0.0 || !std::isfinite(v); }
 // (p_1 = b_1), chat_i = c_i / p_i, with c_N taken as 0.  Returns the row of
 // the first bad pivot (1-based) or 0.
 int64_t tri_factor(const double* a, const double* b, const double* c, int64_t N,
-                   std::vector<double>& r, std::vector<double>& chat) {
+                   std::vector<double>& r, std::vector<double>& chat, std::vector<double>* piv = nullptr) {
   r.assign(N, 0.0);
   chat.assign(N, 0.0);
+  if (piv) piv->assign(N, 0.0);
   for (int64_t i = 0; i < N; i++) {
     const double p = (i == 0) ? b[0] : b[i] - a[i] * chat[i - 1];
     if (bad(p)) return i + 1;
+    if (piv) (*piv)[i] = p;
     r[i] = 1.0 / p;
     chat[i] = (i + 1 < N) ? c[i] * r[i] : 0.0;
   }
@@ -120,11 +122,12 @@ int64_t penta_factor(const double* const* bd, int64_t N, std::vector<double>& al
 
 // Sweep coefficients of the primal (A^{-1}) and adjoint (A^{-T}) solves.
 // Returns the 1-based row of a bad pivot, or 0.
-int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, HostPlan& Q) {
+int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, HostPlan& Q,
+                   std::vector<double>* entries = nullptr) {
   auto C = [&](HostPlan& p, int k, int64_t i) -> double& { return p.c[(size_t)k * N + i]; };
   if (width == 3) {
-    std::vector<double> r, chat;
-    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat);
+    std::vector<double> r, chat, piv;
+    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat, &piv);
     if (bad_row) return bad_row;
     // primal: dhat_i = r_i d_i - (a_i r_i) dhat_{i-1};  x_i = dhat_i - chat_i x_{i+1}
     P.bw = 1;
@@ -146,6 +149,14 @@ int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, H
       C(Q, C_L1, i) = (i > 0) ? chat[i - 1] : 0.0;
       C(Q, C_T, i) = r[i];
       C(Q, C_U1, i) = (i + 1 < N) ? bd[0][i + 1] * r[i] : 0.0;
+    }
+    if (entries) {  // A = L U: L = (a_i sub, p_i diag), U = (1, chat_i super)
+      entries->assign((size_t)5 * N, 0.0);
+      for (int64_t i = 0; i < N; i++) {
+        (*entries)[0 * N + i] = piv[i];
+        (*entries)[1 * N + i] = (i > 0) ? bd[0][i] : 0.0;
+        (*entries)[3 * N + i] = (i + 1 < N) ? chat[i] : 0.0;
+      }
     }
     return 0;
   }
@@ -181,6 +192,16 @@ int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, H
     C(Q, C_U1, i) = (i + 1 < N) ? be[i + 1] * ia : 0.0;
     C(Q, C_U2, i) = (i + 2 < N) ? ep[i + 2] * ia : 0.0;
   }
+  if (entries) {  // A = L R: L = (eps_i, beta_i, alpha_i), R = (1, gamma_i, delta_i)
+    entries->assign((size_t)5 * N, 0.0);
+    for (int64_t i = 0; i < N; i++) {
+      (*entries)[0 * N + i] = al[i];
+      (*entries)[1 * N + i] = (i >= 1) ? be[i] : 0.0;
+      (*entries)[2 * N + i] = (i >= 2) ? ep[i] : 0.0;
+      (*entries)[3 * N + i] = (i + 1 < N) ? ga[i] : 0.0;
+      (*entries)[4 * N + i] = (i + 2 < N) ? de[i] : 0.0;
+    }
+  }
   return 0;
 }
 
@@ -193,6 +214,8 @@ void free_handle(bs_handle h) {
   if (h->bands64) cudaFree(h->bands64);
   if (h->bands_hi) cudaFree(h->bands_hi);
   if (h->bands_lo) cudaFree(h->bands_lo);
+  if (h->lu_hi) cudaFree(h->lu_hi);
+  if (h->lu_lo) cudaFree(h->lu_lo);
   delete h;
 }
 
@@ -235,7 +258,8 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   HostPlan hp[3];
   bool has_ul = false;
   for (auto& p : hp) p.c.assign((size_t)C_COUNT * N, 0.0);
-  int64_t bad_row = make_plans(bd, width, N, hp[0], hp[1]);
+  std::vector<double> entries;
+  int64_t bad_row = make_plans(bd, width, N, hp[0], hp[1], &entries);
   if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
   {
     // Reversed matrix J A J (J the row reversal): band k of row i is band
@@ -296,6 +320,18 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
     if (e == cudaSuccess)
       e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
     bytes += (sizeof(double) + sizeof(float)) * hp[p].c.size();
+  }
+  {
+    std::vector<float> ehi(entries.size()), elo(entries.size());
+    for (size_t q = 0; q < entries.size(); q++) {
+      ehi[q] = (float)entries[q];
+      elo[q] = (float)(entries[q] - (double)ehi[q]);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_hi, sizeof(float) * ehi.size());
+    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_lo, sizeof(float) * elo.size());
+    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_hi, ehi.data(), sizeof(float) * ehi.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_lo, elo.data(), sizeof(float) * elo.size(), cudaMemcpyHostToDevice);
+    bytes += 2 * sizeof(float) * ehi.size();
   }
   if (e == cudaSuccess) e = cudaMalloc(&hd->bands64, sizeof(double) * b64.size());
   if (e == cudaSuccess) e = cudaMalloc(&hd->bands_hi, sizeof(float) * bhi.size());

@@ -51,65 +51,44 @@ __device__ void lane_solve_f64(const GReq& q, int64_t j) {
 
 template <int BW>
 __device__ void lane_solve_refine(const GReq& q, int64_t j) {
-  constexpr int W = 2 * BW + 1;
-  const RefineCoefs<BW> cf = make_refine_coefs<BW>(q.c32, q.ul32, q.bhi, q.blo, q.N);
+  constexpr int U = 4;  // the block of the standalone kernel: same arithmetic
+  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(q.c32, q.lu_hi, q.lu_lo, q.N);
   const int N = q.N;
   const int64_t M = q.M;
   const float* pb = static_cast<const float*>(q.B) + j;
   double* px = q.X + j;
   float2* ps = reinterpret_cast<float2*>(q.X) + j;
-  {  // pass 1
-    float w1 = 0.f, w2 = 0.f;
+  {
+    float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += kGroupU) {
-      float b[kGroupU];
+    for (int i0 = 0; i0 < N; i0 += U) {
+      const int n = (N - i0) < U ? (N - i0) : U;
+      float b[U], w[U], d[U];
 #pragma unroll
-      for (int u = 0; u < kGroupU; u++)
-        if (i0 + u < N) b[u] = pb[(int64_t)(i0 + u) * M];
+      for (int u = 0; u < U; u++) b[u] = (u < n) ? pb[(int64_t)(i0 + u) * M] : 0.f;
+      frefine_pass1<BW, U>(cf, i0, n, b, w, d, w1, w2, d1, d2);
 #pragma unroll
-      for (int u = 0; u < kGroupU; u++)
-        if (i0 + u < N) ps[(int64_t)(i0 + u) * M] = make_float2(refine_fwd<BW>(cf, i0 + u, b[u], w1, w2), b[u]);
+      for (int u = 0; u < U; u++)
+        if (u < n) ps[(int64_t)(i0 + u) * M] = make_float2(w[u], d[u]);
     }
   }
-  {  // pass 2
-    float xw[W], bw[BW + 1];
-#pragma unroll
-    for (int k = 0; k < W; k++) xw[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k <= BW; k++) bw[k] = 0.f;
-    float z1 = 0.f, z2 = 0.f;
+  {
+    float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
 #pragma unroll 1
-    for (int i = N - 1; i >= -BW; i--) {
-      float x0 = 0.f, b = 0.f;
-      if (i >= 0) {
-        const float2 wb = ps[(int64_t)i * M];
-        x0 = refine_bwd<BW>(cf, i, wb.x, xw);
-        b = wb.y;
+    for (int top = N - 1; top >= 0; top -= U) {
+      const int n = (top + 1) < U ? (top + 1) : U;
+      float w[U], dl[U];
+      double xo[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const float2 v = (u < n) ? ps[(int64_t)(top - u) * M] : make_float2(0.f, 0.f);
+        w[u] = v.x;
+        dl[u] = v.y;
       }
+      frefine_pass2<BW, U>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
 #pragma unroll
-      for (int k = W - 1; k > 0; k--) xw[k] = xw[k - 1];
-      xw[0] = x0;
-#pragma unroll
-      for (int k = BW; k > 0; k--) bw[k] = bw[k - 1];
-      bw[0] = b;
-      const int qrow = i + BW;
-      if (qrow < N) {
-        const float z = refine_resid_z<BW>(cf, qrow, bw[BW], xw, z1, z2);
-        ps[(int64_t)qrow * M] = make_float2(xw[BW], z);
-      }
-    }
-  }
-  {  // pass 3
-    float d1 = 0.f, d2 = 0.f;
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += kGroupU) {
-      float2 xz[kGroupU];
-#pragma unroll
-      for (int u = 0; u < kGroupU; u++)
-        if (i0 + u < N) xz[u] = ps[(int64_t)(i0 + u) * M];
-#pragma unroll
-      for (int u = 0; u < kGroupU; u++)
-        if (i0 + u < N) px[(int64_t)(i0 + u) * M] = refine_out<BW>(cf, i0 + u, xz[u].x, xz[u].y, d1, d2);
+      for (int u = 0; u < U; u++)
+        if (u < n) px[(int64_t)(top - u) * M] = xo[u];
     }
   }
 }

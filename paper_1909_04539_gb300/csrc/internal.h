@@ -60,6 +60,13 @@ struct bs_factor_s {
   double* bands64;         // device, width * N, entries outside the matrix zeroed
   float* bands_hi;         // device, width * N: FP32 rounding of the bands
   float* bands_lo;         // device, width * N: FP32 rounding of (band - hi)
+  // Entries of the factors A = L U (tri) / A = L R (penta), 5 * N each:
+  // [0] L diagonal (pivot / alpha), [1] L first sub-diagonal (a / beta),
+  // [2] L second sub-diagonal (0 / eps), [3] U first super-diagonal
+  // (chat / gamma), [4] U second super-diagonal (0 / delta); FP64 values
+  // split into FP32 high and low parts.
+  float* lu_hi;
+  float* lu_lo;
   size_t device_bytes;
   bool has_ul;             // plan[2] is valid (reversed elimination met no bad pivot)
 };
@@ -80,7 +87,7 @@ const DeviceInfo& device_info();
 // Launchers
 bs_status launch_sweep(const SweepPlan& p, int64_t N, const void* in, void* out, bs_dtype in_t,
                        bs_dtype out_t, bs_layout layout, int64_t M, cudaStream_t st);
-bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps,
+bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, int mode,
                         cudaStream_t st);
 bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout,
                            int64_t M, double* dbands, cudaStream_t st);

@@ -255,6 +255,150 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
   }
 }
 
+// Factor-wise refinement, two passes (see refine_math.cuh).  Pass 1 streams B
+// up through a ring of 4-byte rows and leaves (w, delta) in the 8-byte slots
+// of X; pass 2 streams the slots down through a ring and writes the FP64
+// solution over them.  Rows move in blocks of kRU.
+template <int BW, int D, bool SMEM>
+__global__ void __launch_bounds__(128)
+k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M) {
+  static_assert(D % kRU == 0, "ring depth must be a multiple of the block");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FRefineCoefs<BW> cf = cg;
+  size_t coef_bytes = 0;
+  if (SMEM) {
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    int off = 0;
+    auto stage = [&](const float*& p) {
+      float* dst = sm + off;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = p[i];
+      p = dst;
+      off += N;
+    };
+    stage(cf.sw[0]);
+    stage(cf.sw[1]);
+    if (BW == 2) stage(cf.sw[2]);
+    stage(cf.sw[3]);
+    if (BW == 2) stage(cf.sw[4]);
+    for (int k = 0; k <= BW; k++) {
+      stage(cf.Lh[k]);
+      stage(cf.Ll[k]);
+    }
+    for (int k = 0; k < BW; k++) {
+      stage(cf.Uh[k]);
+      stage(cf.Ul[k]);
+    }
+    coef_bytes = align_up((size_t)off * sizeof(float), 16);
+    __syncthreads();
+  }
+  unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 8;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * 8;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    const float* pb = B + j;
+    double* px = X + j;
+    float2* ps = reinterpret_cast<float2*>(X) + j;
+
+    // ---- pass 1 (rows up): slot <- (w, delta)
+    {
+      float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        if (r < N) cp_async4(ring_s + r * pitch, pb + (int64_t)r * M);
+        cp_commit();
+      }
+#pragma unroll 1
+      for (int i0 = 0; i0 < N; i0 += kRU) {
+        cp_wait<D - kRU>();
+        const int n = (N - i0) < kRU ? (N - i0) : kRU;
+        const int s0 = i0 % D;
+        float b[kRU], w[kRU], d[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          if (u < n && i0 + u + D < N) cp_async4(ring_s + (s0 + u) * pitch, pb + (int64_t)(i0 + u + D) * M);
+          cp_commit();
+        }
+        frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) ps[(int64_t)(i0 + u) * M] = make_float2(w[u], d[u]);
+      }
+      cp_wait<0>();
+    }
+    // ---- pass 2 (rows down): X
+    {
+      float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        const int row = N - 1 - r;
+        if (row >= 0) cp_async8(ring_s + r * pitch, ps + (int64_t)row * M);
+        cp_commit();
+      }
+#pragma unroll 1
+      for (int top = N - 1; top >= 0; top -= kRU) {
+        cp_wait<D - kRU>();
+        const int n = (top + 1) < kRU ? (top + 1) : kRU;
+        const int s0 = (N - 1 - top) % D;
+        float w[kRU], dl[kRU];
+        double xo[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          const float2 v = *reinterpret_cast<const float2*>(ring + (size_t)(s0 + u) * pitch);
+          w[u] = v.x;
+          dl[u] = v.y;
+        }
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+          const int i = top - u;
+          if (u < n && i - D >= 0) cp_async8(ring_s + (s0 + u) * pitch, ps + (int64_t)(i - D) * M);
+          cp_commit();
+        }
+        frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
+#pragma unroll
+        for (int u = 0; u < kRU; u++)
+          if (u < n) px[(int64_t)(top - u) * M] = xo[u];
+      }
+      cp_wait<0>();
+    }
+  }
+}
+
+template <int BW>
+static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* X, int64_t M, cudaStream_t st) {
+  constexpr int D = 16;
+  const int N = (int)h->N;
+  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(h->plan[0].c32, h->lu_hi, h->lu_lo, N);
+  const DeviceInfo& d = device_info();
+  int tpb = 128;
+  while (tpb > 32 && M < (int64_t)2 * d.sms * tpb) tpb /= 2;
+  const size_t coef = align_up((size_t)frefine_arrays<BW>() * N * sizeof(float), 16);
+  const size_t ring = (size_t)tpb * D * 8;
+  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
+  const bool smem = coef + ring <= limit;
+  const size_t bytes = (smem ? coef : 0) + ring;
+  int per_sm = (int)((228 * 1024) / (bytes + 1024));
+  if (per_sm > 2048 / tpb) per_sm = 2048 / tpb;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)d.sms * per_sm;
+  const int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
+  if (budget > 0) {
+    int64_t cap = budget / ((int64_t)tpb * N * 8);
+    if (cap < d.sms) cap = d.sms;
+    if (grid > cap) grid = cap;
+  }
+  const int64_t need = (M + tpb - 1) / tpb;
+  if (grid > need) grid = need;
+  auto k = smem ? k_refine_factor<BW, D, true> : k_refine_factor<BW, D, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k<<<(int)grid, tpb, bytes, st>>>(cf, N, B, X, M);
+  return cudaGetLastError();
+}
+
 template <int BW>
 static cudaError_t launch_refine_bw(bs_handle h, const float* B, double* X, int64_t M, int steps, cudaStream_t st) {
   constexpr int D = 16;
@@ -310,10 +454,16 @@ static cudaError_t launch_refine_bw(bs_handle h, const float* B, double* X, int6
   return cudaGetLastError();
 }
 
-bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, cudaStream_t st) {
+bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, int mode,
+                        cudaStream_t st) {
   if (b_t != BS_F32) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: B must be BS_F32");
-  cudaError_t e = h->width == 3 ? launch_refine_bw<1>(h, (const float*)B, X, M, steps, st)
-                                : launch_refine_bw<2>(h, (const float*)B, X, M, steps, st);
+  cudaError_t e;
+  if (steps == 1 && mode == BS_REFINE_FACTOR)
+    e = h->width == 3 ? launch_refine_factor_bw<1>(h, (const float*)B, X, M, st)
+                      : launch_refine_factor_bw<2>(h, (const float*)B, X, M, st);
+  else
+    e = h->width == 3 ? launch_refine_bw<1>(h, (const float*)B, X, M, steps, st)
+                      : launch_refine_bw<2>(h, (const float*)B, X, M, steps, st);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve_refine launch");
   return BS_OK;
 }
@@ -321,7 +471,7 @@ bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int
 }  // namespace bs
 
 extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
-                                     int64_t M, int refine_steps, bs_stream stream) {
+                                     int64_t M, int refine_steps, bs_refine_mode mode, bs_stream stream) {
   using namespace bs;
   if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_solve_refine: unknown handle");
   if (!B || !X) return set_error(BS_EINVAL, "bs_solve_refine: null data pointer");
@@ -330,7 +480,9 @@ extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtyp
     return set_error(BS_EUNSUPPORTED, "bs_solve_refine: only the interleaved layout is implemented");
   if (refine_steps < 0 || refine_steps > 1)
     return set_error(BS_EUNSUPPORTED, "bs_solve_refine: refine_steps must be 0 or 1");
-  if (refine_steps > 0 && !h->has_ul)
+  if (mode != BS_REFINE_FACTOR && mode != BS_REFINE_SYSTEM)
+    return set_error(BS_EINVAL, "bs_solve_refine: bad refinement mode");
+  if (refine_steps > 0 && mode == BS_REFINE_SYSTEM && !h->has_ul)
     return set_error(BS_ESINGULAR, "bs_solve_refine: the reversed elimination of this matrix met a bad pivot");
   if (reinterpret_cast<uintptr_t>(X) % 8 || reinterpret_cast<uintptr_t>(B) % 4)
     return set_error(BS_EINVAL, "bs_solve_refine: misaligned pointer");
@@ -341,5 +493,5 @@ extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtyp
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != h->device) return set_error(BS_EINVAL, "bs_solve_refine: handle belongs to another device");
-  return launch_refine(h, B, b_dtype, X, M, refine_steps, reinterpret_cast<cudaStream_t>(stream));
+  return launch_refine(h, B, b_dtype, X, M, refine_steps, (int)mode, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -129,3 +129,180 @@ __host__ __device__ __forceinline__ RefineCoefs<BW> make_refine_coefs(const floa
 }
 
 }  // namespace bs
+
+// ---------------------------------------------------------------------------
+// Factor-wise refinement (two passes): each triangular sweep of A = L U is
+// solved in FP32 and corrected once with the residual of that triangular
+// system evaluated to FP64 accuracy:
+//   rows up  : w = L^{-1} B (FP32);  rho = B - L w;  delta = L^{-1} rho (FP32)
+//              -> y = w + delta  (kept as the pair, 8 bytes per row)
+//   rows down: x = U^{-1} fl32(y) (FP32);  sigma = y - U x;  eps = U^{-1} sigma
+//              -> X = x + eps in FP64
+// L and U are the FP64 factors (their entries split into FP32 hi/lo pairs),
+// so X solves L U X = B to ~1e-15 relative for well-conditioned bands.
+
+namespace bs {
+
+template <int BW>
+struct FRefineCoefs {
+  const float* sw[5];  // FP32 sweep coefficients s, l1, l2, u1, u2 of A = L U
+  const float* Lh[3];  // L entries (diagonal, first, second sub-diagonal), high parts
+  const float* Ll[3];  //   ... low parts
+  const float* Uh[2];  // U entries (first, second super-diagonal), high parts
+  const float* Ul[2];  //   ... low parts
+};
+
+template <int BW>
+__host__ __device__ constexpr int frefine_arrays() {
+  return (1 + 2 * BW) + 2 * (BW + 1) + 2 * BW;
+}
+
+// lu = FP32 primal plan (C_COUNT * N); ehi/elo = factor entries (5 * N).
+template <int BW>
+__host__ __device__ __forceinline__ FRefineCoefs<BW> make_frefine_coefs(const float* lu, const float* ehi,
+                                                                       const float* elo, int64_t n) {
+  FRefineCoefs<BW> cf{};
+  const int idx[5] = {C_S, C_L1, C_L2, C_U1, C_U2};
+  for (int k = 0; k < 5; k++) cf.sw[k] = lu + idx[k] * n;
+  for (int k = 0; k < 3; k++) {
+    cf.Lh[k] = ehi + k * n;
+    cf.Ll[k] = elo + k * n;
+  }
+  for (int k = 0; k < 2; k++) {
+    cf.Uh[k] = ehi + (3 + k) * n;
+    cf.Ul[k] = elo + (3 + k) * n;
+  }
+  return cf;
+}
+
+// Rows i0 .. i0+n-1 of the first pass.  b: the FP32 inputs; on exit w, d
+// hold the pairs (w, delta) to keep.  (w1, w2), (d1, d2): the two previous
+// rows of each recurrence.
+template <int BW, int U>
+__device__ __forceinline__ void frefine_pass1(const FRefineCoefs<BW>& cf, int i0, int n, const float (&b)[U],
+                                              float (&w)[U], float (&d)[U], float& w1, float& w2, float& d1,
+                                              float& d2) {
+  constexpr int W = BW + 1;
+  float s[U], l1[U], l2[U], wp1[U], wp2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (u < n) ? i0 + u : i0;
+    s[u] = cf.sw[0][i];
+    l1[u] = cf.sw[1][i];
+    l2[u] = (BW == 2) ? cf.sw[2][i] : 0.f;
+  }
+  // forward sweep of w (the chain)
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    wp1[u] = w1;
+    wp2[u] = w2;
+    if (u < n) {
+      float x = b[u] * s[u];
+      if (BW == 2) x = fmaf(-l2[u], w2, x);
+      x = fmaf(-l1[u], w1, x);
+      w[u] = x;
+      w2 = w1;
+      w1 = x;
+    }
+  }
+  // residuals of the rows (independent of each other)
+  float rho[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    rho[u] = 0.f;
+    if (u < n) {
+      const int i = i0 + u;
+      float x[W], ah[W], al[W];
+      x[0] = w[u];
+      ah[0] = cf.Lh[0][i];
+      al[0] = cf.Ll[0][i];
+      x[1] = wp1[u];
+      ah[1] = cf.Lh[1][i];
+      al[1] = cf.Ll[1][i];
+      if (BW == 2) {
+        x[W - 1] = wp2[u];
+        ah[W - 1] = cf.Lh[2][i];
+        al[W - 1] = cf.Ll[2][i];
+      }
+      rho[u] = residual_row<W>(b[u], x, ah, al);
+    }
+  }
+  // forward sweep of the correction
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+      float x = rho[u] * s[u];
+      if (BW == 2) x = fmaf(-l2[u], d2, x);
+      x = fmaf(-l1[u], d1, x);
+      d[u] = x;
+      d2 = d1;
+      d1 = x;
+    }
+  }
+}
+
+// Rows top, top-1, .., top-n+1 of the second pass: (w, dl) the kept pairs;
+// returns the FP64 solution in X.  (x1, x2), (e1, e2): the two rows below.
+template <int BW, int U>
+__device__ __forceinline__ void frefine_pass2(const FRefineCoefs<BW>& cf, int top, int n, const float (&w)[U],
+                                              const float (&dl)[U], double (&X)[U], float& x1, float& x2,
+                                              float& e1, float& e2) {
+  constexpr int W = BW + 1;
+  float u1[U], u2[U], x[U], xn1[U], xn2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (u < n) ? top - u : top;
+    u1[u] = cf.sw[3][i];
+    u2[u] = (BW == 2) ? cf.sw[4][i] : 0.f;
+  }
+  // backward sweep of x on the rounded pair (the chain)
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    xn1[u] = x1;
+    xn2[u] = x2;
+    if (u < n) {
+      float v = __fadd_rn(w[u], dl[u]);
+      if (BW == 2) v = fmaf(-u2[u], x2, v);
+      v = fmaf(-u1[u], x1, v);
+      x[u] = v;
+      x2 = x1;
+      x1 = v;
+    }
+  }
+  // residuals sigma = (w + dl) - U x of the rows
+  float sig[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    sig[u] = 0.f;
+    if (u < n) {
+      const int i = top - u;
+      float xs[W], ah[W], al[W];
+      xs[0] = x[u];
+      ah[0] = 1.f;
+      al[0] = 0.f;
+      xs[1] = xn1[u];
+      ah[1] = cf.Uh[0][i];
+      al[1] = cf.Ul[0][i];
+      if (BW == 2) {
+        xs[W - 1] = xn2[u];
+        ah[W - 1] = cf.Uh[1][i];
+        al[W - 1] = cf.Ul[1][i];
+      }
+      sig[u] = __fadd_rn(residual_row<W>(w[u], xs, ah, al), dl[u]);
+    }
+  }
+  // backward sweep of the correction and the FP64 sum
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+      float v = sig[u];
+      if (BW == 2) v = fmaf(-u2[u], e2, v);
+      v = fmaf(-u1[u], e1, v);
+      e2 = e1;
+      e1 = v;
+      X[u] = widen_exact(x[u]) + widen_exact(v);
+    }
+  }
+}
+
+}  // namespace bs

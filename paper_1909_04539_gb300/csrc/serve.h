@@ -11,9 +11,8 @@ enum { SERVE_F64 = 0, SERVE_F32_REFINE = 1 };
 struct GReq {
   const double* c64;  // primal sweep coefficients, FP64 (C_COUNT * N)
   const float* c32;   // primal sweep coefficients, FP32
-  const float* ul32;  // reversed-elimination coefficients, FP32
-  const float* bhi;   // bands, FP32 high parts (width * N)
-  const float* blo;   // bands, FP32 low parts
+  const float* lu_hi; // entries of the factors L, U: FP32 high parts (5 * N)
+  const float* lu_lo; //   ... low parts
   void* B;            // SERVE_F64: double, solved in place; SERVE_F32_REFINE: float input
   double* X;          // SERVE_F32_REFINE: FP64 output (SERVE_F64: equals B)
   int64_t M;

@@ -182,9 +182,8 @@ cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<int64_t>& ids)
     GReq g{};
     g.c64 = h->plan[0].c64;
     g.c32 = h->plan[0].c32;
-    g.ul32 = h->plan[2].c32;
-    g.bhi = h->bands_hi;
-    g.blo = h->bands_lo;
+    g.lu_hi = h->lu_hi;
+    g.lu_lo = h->lu_lo;
     g.M = r.M;
     g.N = (int)h->N;
     g.width = h->width;
@@ -368,8 +367,6 @@ bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* h
   if (h->device != s->device) return set_error(BS_EINVAL, "bs_server_submit: handle on another device");
   if (!host_B || !host_X) return set_error(BS_EINVAL, "bs_server_submit: null buffer");
   if (mode != SERVE_F64 && mode != SERVE_F32_REFINE) return set_error(BS_EINVAL, "bs_server_submit: bad mode");
-  if (mode == SERVE_F32_REFINE && !h->has_ul)
-    return set_error(BS_ESINGULAR, "bs_server_submit: the reversed elimination of this matrix met a bad pivot");
   if (M < 1 || M > (int64_t)kGroupMaxTiles * 32) return set_error(BS_EINVAL, "bs_server_submit: M out of range");
   const size_t bytes = req_bytes(h->width, h->N, mode, M);
   std::lock_guard<std::mutex> lk(s->mu);

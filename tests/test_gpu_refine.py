@@ -29,13 +29,14 @@ def _bands(width, N, seed):
     return synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["factor", "system"])
 @pytest.mark.parametrize("width,N,M", [(3, 2, 1), (3, 3, 5), (3, 64, 1024), (3, 100, 333), (3, 1024, 257),
                                        (5, 4, 1), (5, 5, 7), (5, 37, 33), (5, 512, 1000), (5, 130, 4099)])
-def test_refine_random(bs, width, N, M):
+def test_refine_random(bs, width, N, M, mode):
     bands = _bands(width, N, N + M)
     B = torch.tensor(np.random.default_rng(M).uniform(-1, 1, (N, M)), dtype=torch.float32, device="cuda")
     f = bs.Factor(bands)
-    X = bs.solve_refine(f, B, refine_steps=1)
+    X = bs.solve_refine(f, B, refine_steps=1, mode=mode)
     X0 = bs.solve_refine(f, B, refine_steps=0)
     torch.cuda.synchronize()
     ref = oracle.solve(bands, B.double().cpu().numpy())
@@ -43,14 +44,15 @@ def test_refine_random(bs, width, N, M):
     assert rel_l2(X0.cpu().numpy(), ref) < 2e-5
 
 
-def test_refine_clamped_hyperdiffusion_full_size(bs):
+@pytest.mark.parametrize("mode", [0, 1], ids=["factor", "system"])
+def test_refine_clamped_hyperdiffusion_full_size(bs, mode):
     """Penta I + 0.1 D4 clamped, N=512, M=65536, RHS ~ N(0,1) stored in FP32:
     512 sampled systems against the oracle, every system via the residual."""
     N, M = 512, 65536
     bands = synth.clamped_hyperdiffusion_bands(N, 0.1)
     f = bs.Factor(bands)
     B = synth.normal_rhs(N, M, 0, "cuda").float()
-    X = bs.solve_refine(f, B)
+    X = bs.solve_refine(f, B, mode=mode)
     torch.cuda.synchronize()
     cols = np.union1d(np.random.default_rng(4).choice(M, 512, replace=False), [0, M - 1])
     ref = oracle.solve(bands, B[:, cols].double().cpu().numpy())
@@ -63,7 +65,8 @@ def test_refine_clamped_hyperdiffusion_full_size(bs):
     assert (torch.linalg.norm(R) / torch.linalg.norm(B.double())).item() < 1e-13
 
 
-def test_refine_spline_sampled(bs):
+@pytest.mark.parametrize("mode", [0, 1], ids=["factor", "system"])
+def test_refine_spline_sampled(bs, mode):
     """Tri [1,4,1]/6 natural spline, N=1024, spline RHS stored in FP32 (a
     2^16-system slice of the 2^20-system workload; the full size runs in the
     benchmark of that workload)."""
@@ -71,7 +74,7 @@ def test_refine_spline_sampled(bs):
     bands = synth.spline_bands(N)
     f = bs.Factor(bands)
     B = synth.spline_rhs(N, M, 0, "cuda")
-    X = bs.solve_refine(f, B)
+    X = bs.solve_refine(f, B, mode=mode)
     torch.cuda.synchronize()
     cols = np.random.default_rng(5).choice(M, 256, replace=False)
     ref = oracle.solve(bands, B[:, cols].double().cpu().numpy())
@@ -83,5 +86,7 @@ def test_refine_rejects_bad_arguments(bs):
     B = torch.zeros(16, 8, dtype=torch.float32, device="cuda")
     with pytest.raises(bs.BsolveError):
         bs.solve_refine(f, B, refine_steps=2)
+    with pytest.raises(bs.BsolveError):
+        bs.solve_refine(f, B, mode=7)
     with pytest.raises(ValueError):
         bs.solve_refine(f, B.double())
