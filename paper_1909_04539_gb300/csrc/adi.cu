@@ -29,46 +29,64 @@ __global__ void __launch_bounds__(kSweepThreads)
 k_adi_il(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  constexpr int U = 8;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
     const C* pu = u + j;
     C* po = out + j;
     const bool has_l = j > 0, has_r = j + 1 < M;
     C r1[1] = {C(0)}, r2[1] = {C(0)};
-    constexpr int U = 8;
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += U) {
+    // explicit operator on load: rows i0 .. i0+U-1 of this column and its two
+    // neighbours; a block of loads is issued before the previous block is swept
+    auto load_rhs = [&](C (&f)[U][1], int i0) {
       C c[U], l[U], rr[U];
 #pragma unroll
-      for (int q = 0; q < U; q++)
-        if (i0 + q < N) {
-          const int64_t o = (int64_t)(i0 + q) * M;
-          c[q] = pu[o];
-          l[q] = has_l ? pu[o - 1] : C(0);
-          rr[q] = has_r ? pu[o + 1] : C(0);
-        }
+      for (int q = 0; q < U; q++) {
+        const int i = i0 + q < N ? i0 + q : N - 1;
+        const int64_t o = (int64_t)i * M;
+        c[q] = pu[o];
+        l[q] = has_l ? pu[o - 1] : C(0);
+        rr[q] = has_r ? pu[o + 1] : C(0);
+      }
+#pragma unroll
+      for (int q = 0; q < U; q++) f[q][0] = c[q] + r * (l[q] - C(2) * c[q] + rr[q]);
+    };
+    C fa[U][1], fb[U][1];
+    load_rhs(fa, 0);
+#pragma unroll 1
+    for (int i0 = 0; i0 < N; i0 += U) {
+      const bool more = i0 + U < N;
+      if (more) load_rhs(fb, i0 + U);
+      const int n = (N - i0) < U ? (N - i0) : U;
+      fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, fa, r1, r2);
 #pragma unroll
       for (int q = 0; q < U; q++)
-        if (i0 + q < N) {
-          C f[1] = {c[q] + r * (l[q] - C(2) * c[q] + rr[q])};
-          fwd_step<BW, ADJ, C, 1>(cf, i0 + q, f, r1, r2);
-          po[(int64_t)(i0 + q) * M] = f[0];
-        }
+        if (q < n) po[(int64_t)(i0 + q) * M] = fa[q][0];
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < U; q++) fa[q][0] = fb[q][0];
+      }
     }
     r1[0] = r2[0] = C(0);
+    // backward: blocks of rows top .. top-U+1, the next block loaded ahead
+    auto load_w = [&](C (&f)[U][1], int top) {
+#pragma unroll
+      for (int q = 0; q < U; q++) f[q][0] = po[(int64_t)(top - q >= 0 ? top - q : 0) * M];
+    };
+    load_w(fa, N - 1);
 #pragma unroll 1
     for (int top = N - 1; top >= 0; top -= U) {
-      C w[U];
+      const bool more = top - U >= 0;
+      if (more) load_w(fb, top - U);
+      const int n = (top + 1) < U ? (top + 1) : U;
+      bwd_block<BW, ADJ, C, 1, U>(cf, top, n, fa, r1, r2);
 #pragma unroll
       for (int q = 0; q < U; q++)
-        if (top - q >= 0) w[q] = po[(int64_t)(top - q) * M];
+        if (q < n) po[(int64_t)(top - q) * M] = fa[q][0];
+      if (more) {
 #pragma unroll
-      for (int q = 0; q < U; q++)
-        if (top - q >= 0) {
-          C f[1] = {w[q]};
-          bwd_step<BW, ADJ, C, 1>(cf, top - q, f, r1, r2);
-          po[(int64_t)(top - q) * M] = f[0];
-        }
+        for (int q = 0; q < U; q++) fa[q][0] = fb[q][0];
+      }
     }
   }
 }
@@ -86,6 +104,7 @@ k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kWarps = kSweepThreads / 32;
+  constexpr int U = 8;
   C* tin = smc + (SMEM ? coef_arrays<BW>() * N : 0) + warp * kAdiWarpTile;
   C* tout = tin + kStRows * kAdiTile;
   const int64_t nwg = (M + 31) / 32;
@@ -94,41 +113,69 @@ k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
     const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
     const bool mine = lane < nsys;
     C r1[1] = {C(0)}, r2[1] = {C(0)};
-    // forward sweep with the explicit operator applied on load
+    // Lane `lane` holds row c0 + lane of systems j0-1 .. j0+32 of a chunk in
+    // registers; the next chunk's row is loaded while this one is swept.
+    C pre[34];
+    auto load_chunk = [&](int c0) {
+      const bool ok = c0 + lane < N;
+#pragma unroll
+      for (int s = 0; s < 34; s++) {
+        const int64_t jj = j0 + s - 1;
+        pre[s] = (ok && jj >= 0 && jj < M && s - 1 < nsys + 1) ? u[jj * (int64_t)N + c0 + lane] : C(0);
+      }
+    };
+    load_chunk(0);
     for (int c0 = 0; c0 < N; c0 += kStRows) {
       const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
-      // input tile column s + 1 holds system j0 + s, s = -1 .. nsys
-      if (lane < rows)
-        for (int s = -1; s <= nsys; s++) {
-          const int64_t jj = j0 + s;
-          tin[lane * kAdiTile + s + 1] = (jj >= 0 && jj < M) ? u[jj * (int64_t)N + c0 + lane] : C(0);
-        }
+#pragma unroll
+      for (int s = 0; s < 34; s++) tin[lane * kAdiTile + s] = pre[s];
       __syncwarp();
+      if (c0 + kStRows < N) load_chunk(c0 + kStRows);
       if (mine)
-        for (int q = 0; q < rows; q++) {
-          const C* t = tin + q * kAdiTile + lane;
-          C f[1] = {t[1] + r * (t[0] - C(2) * t[1] + t[2])};
-          fwd_step<BW, ADJ, C, 1>(cf, c0 + q, f, r1, r2);
-          tout[q * kStPad + lane] = f[0];
+        for (int q0 = 0; q0 < rows; q0 += U) {
+          const int n = (rows - q0) < U ? (rows - q0) : U;
+          C f[U][1];
+#pragma unroll
+          for (int q = 0; q < U; q++) {
+            const C* t = tin + (q0 + q) * kAdiTile + lane;
+            f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
+          }
+          fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
+#pragma unroll
+          for (int q = 0; q < U; q++)
+            if (q < n) tout[(q0 + q) * kStPad + lane] = f[q][0];
         }
       __syncwarp();
       if (lane < rows)
         for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
       __syncwarp();
     }
-    // backward sweep, chunks in decreasing order, through the output tile
+    // backward sweep, chunks in decreasing order, the next chunk loaded ahead
     r1[0] = r2[0] = C(0);
     const int last = ((N - 1) / kStRows) * kStRows;
+    C pw[32];
+    auto load_back = [&](int c0) {
+      const bool ok = c0 + lane < N;
+#pragma unroll
+      for (int s = 0; s < 32; s++) pw[s] = (ok && s < nsys) ? out[(j0 + s) * (int64_t)N + c0 + lane] : C(0);
+    };
+    load_back(last);
     for (int c0 = last; c0 >= 0; c0 -= kStRows) {
       const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
-      if (lane < rows)
-        for (int s = 0; s < nsys; s++) tout[lane * kStPad + s] = out[(j0 + s) * (int64_t)N + c0 + lane];
+#pragma unroll
+      for (int s = 0; s < 32; s++) tout[lane * kStPad + s] = pw[s];
       __syncwarp();
+      if (c0 - kStRows >= 0) load_back(c0 - kStRows);
       if (mine)
-        for (int q = rows - 1; q >= 0; q--) {
-          C f[1] = {tout[q * kStPad + lane]};
-          bwd_step<BW, ADJ, C, 1>(cf, c0 + q, f, r1, r2);
-          tout[q * kStPad + lane] = f[0];
+        for (int top = rows - 1; top >= 0; top -= U) {
+          const int n = (top + 1) < U ? (top + 1) : U;
+          C f[U][1];
+#pragma unroll
+          for (int q = 0; q < U; q++) f[q][0] = tout[(q < n ? top - q : top) * kStPad + lane];
+          bwd_block<BW, ADJ, C, 1, U>(cf, c0 + top, n, f, r1, r2);
+#pragma unroll
+          for (int q = 0; q < U; q++)
+            if (q < n) tout[(top - q) * kStPad + lane] = f[q][0];
         }
       __syncwarp();
       if (lane < rows)
