@@ -47,8 +47,13 @@ NOMINAL_HBM_GBS = 8000.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # step's kernels from one ncu capture of this workload, valid only while the
-# kernel sources hash to the value they had at capture time (see profiles/).
-NCU_TRAFFIC = {}
+# kernel sources hash to the value they had at capture time.
+NCU_TRAFFIC = {
+    # one --set full capture of the kernel inside this benchmark's step
+    "band_grad_f64": {"bytes": 537621248 + 3447296, "sha": "beac1e924fa6a1d3"},
+    # likewise (the accuracy-check launch, same kernel and batch)
+    "f64_solve": {"bytes": 472660224 + 432845056, "sha": "b63f557d662de20f"},
+}
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
     "adjoint_f64": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],

@@ -91,6 +91,123 @@ k_adi_il(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
   }
 }
 
+// Deep-pipelined variant of the y-implicit half-step: one warp owns 32
+// consecutive columns (systems), each lane streams its column's rows through
+// a ring of D slots in shared memory (cp.async), so D rows per lane are in
+// flight -- with 4096 grid lines there is less than one warp per SM, so depth
+// has to come from each lane.  The explicit operator needs the neighbouring
+// columns' values: inside the warp they come from the adjacent lanes by
+// shuffle, the two outer neighbours are copied by lanes 0 and 31 into a second
+// half of their slots.  The forward values go to `out` and come back through
+// the same ring for the backward sweep.
+template <int BW, bool ADJ, bool SMEM, typename C, int D>
+__global__ void __launch_bounds__(kSweepThreads)
+k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+  constexpr int U = 4;
+  static_assert(D % U == 0, "ring depth must be a multiple of the block");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+  const int lane = threadIdx.x & 31;
+  // slot layout per lane: [own value | outer neighbour], 2 * sizeof(C) bytes
+  constexpr int kSlot = 2 * sizeof(C);
+  unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * kSlot;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * kSlot;
+  const int64_t nwarps_total = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t ngroups = (M + 31) / 32;
+  auto cp = [&](uint32_t dst, const C* src) {
+    if constexpr (sizeof(C) == 8)
+      cp_async8(dst, src);
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+  };
+  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); wg < ngroups; wg += nwarps_total) {
+    const int64_t j = wg * 32 + lane;
+    const bool valid = j < M;
+    // the column this lane copies into the second half of its slot, if any
+    const int64_t jn = lane == 0 ? j - 1 : (lane == 31 ? j + 1 : -1);
+    const bool has_n = (lane == 0 || lane == 31) && jn >= 0 && jn < M;
+    const C* pu = u + (valid ? j : 0);
+    const C* pn = u + (has_n ? jn : 0);
+    C* po = out + (valid ? j : 0);
+    auto request = [&](int slot, int row) {
+      if (valid) cp(ring_s + slot * pitch, pu + (int64_t)row * M);
+      if (has_n) cp(ring_s + slot * pitch + sizeof(C), pn + (int64_t)row * M);
+    };
+    C r1[1] = {C(0)}, r2[1] = {C(0)};
+#pragma unroll 1
+    for (int q = 0; q < D; q++) {
+      if (q < N) request(q, q);
+      cp_commit();
+    }
+#pragma unroll 1
+    for (int i0 = 0; i0 < N; i0 += U) {
+      cp_wait<D - U>();
+      __syncwarp();
+      const int n = (N - i0) < U ? (N - i0) : U;
+      const int s0 = i0 % D;
+      C f[U][1];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const C* sl = reinterpret_cast<const C*>(ring + (size_t)(s0 + q) * pitch);
+        const C c = valid ? sl[0] : C(0);
+        const C outer = has_n ? sl[1] : C(0);
+        C left = __shfl_up_sync(0xffffffffu, c, 1);
+        C right = __shfl_down_sync(0xffffffffu, c, 1);
+        if (lane == 0) left = outer;
+        if (lane == 31) right = outer;
+        f[q][0] = c + r * (left - C(2) * c + right);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        if (q < n && i0 + q + D < N) request(s0 + q, i0 + q + D);
+        cp_commit();
+      }
+      if (valid) {
+        fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, f, r1, r2);
+#pragma unroll
+        for (int q = 0; q < U; q++)
+          if (q < n) po[(int64_t)(i0 + q) * M] = f[q][0];
+      }
+    }
+    cp_wait<0>();
+    __syncwarp();
+    // backward sweep: the lane's own forward values come back through the ring
+    r1[0] = r2[0] = C(0);
+#pragma unroll 1
+    for (int q = 0; q < D; q++) {
+      const int row = N - 1 - q;
+      if (row >= 0 && valid) cp(ring_s + q * pitch, po + (int64_t)row * M);
+      cp_commit();
+    }
+#pragma unroll 1
+    for (int top = N - 1; top >= 0; top -= U) {
+      cp_wait<D - U>();
+      const int n = (top + 1) < U ? (top + 1) : U;
+      const int s0 = (N - 1 - top) % D;
+      C f[U][1];
+#pragma unroll
+      for (int q = 0; q < U; q++) f[q][0] = *reinterpret_cast<const C*>(ring + (size_t)(s0 + q) * pitch);
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int row = top - q - D;
+        if (q < n && row >= 0 && valid) cp(ring_s + (s0 + q) * pitch, po + (int64_t)row * M);
+        cp_commit();
+      }
+      if (valid) {
+        bwd_block<BW, ADJ, C, 1, U>(cf, top, n, f, r1, r2);
+#pragma unroll
+        for (int q = 0; q < U; q++)
+          if (q < n) po[(int64_t)(top - q) * M] = f[q][0];
+      }
+    }
+    cp_wait<0>();
+    __syncwarp();
+  }
+}
+
 // ----------------------------------------------------- implicit along x
 
 constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
@@ -185,6 +302,127 @@ k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
   }
 }
 
+// Deep-pipelined x-implicit half-step: one-warp CTAs, each owning 32 rows of
+// the grid (systems).  Chunks of 32 grid columns (rows of the systems) move
+// through a ring of K tiles in shared memory by cp.async -- each lane copies
+// its row of the chunk for the 34 systems it touches (its 32 plus one
+// neighbour each side) -- so K chunks are in flight while one is swept.  The
+// forward values leave through an output tile with coalesced stores and come
+// back through the same ring for the backward sweep.
+template <int BW, bool ADJ, bool SMEM, typename C, int K>
+__global__ void __launch_bounds__(32)
+k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+  constexpr int U = 8;
+  constexpr int kTile = kStRows * kAdiTile;  // one ring tile (input layout)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smc = reinterpret_cast<C*>(smem_raw);
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+  const int lane = threadIdx.x;
+  C* ringt = smc + (SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) / sizeof(C) : 0);
+  C* tout = ringt + K * kTile;
+  auto cp = [&](C* dst, const C* src) {
+    const uint32_t d = smem_u32(dst);
+    if constexpr (sizeof(C) == 8)
+      cp_async8(d, src);
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  };
+  const int nch = (N + kStRows - 1) / kStRows;
+  for (int64_t wg = blockIdx.x; wg * 32 < M; wg += gridDim.x) {
+    const int64_t j0 = wg * 32;
+    const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
+    const bool mine = lane < nsys;
+    // forward: chunk c lands in tile c % K; tile column s + 1 = system j0 + s
+    auto request_in = [&](int c) {
+      C* t = ringt + (c % K) * kTile + lane * kAdiTile;
+      const int row = c * kStRows + lane;
+      if (row < N)
+        for (int s = -1; s <= nsys; s++) {
+          const int64_t jj = j0 + s;
+          if (jj >= 0 && jj < M) cp(t + s + 1, u + jj * (int64_t)N + row);
+          else t[s + 1] = C(0);
+        }
+    };
+#pragma unroll 1
+    for (int c = 0; c < K; c++) {
+      if (c < nch) request_in(c);
+      cp_commit();
+    }
+    C r1[1] = {C(0)}, r2[1] = {C(0)};
+#pragma unroll 1
+    for (int c = 0; c < nch; c++) {
+      cp_wait<K - 1>();
+      __syncwarp();
+      const int c0 = c * kStRows;
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      const C* tin = ringt + (c % K) * kTile;
+      if (mine)
+        for (int q0 = 0; q0 < rows; q0 += U) {
+          const int n = (rows - q0) < U ? (rows - q0) : U;
+          C f[U][1];
+#pragma unroll
+          for (int q = 0; q < U; q++) {
+            const C* t = tin + (q0 + q) * kAdiTile + lane;
+            f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
+          }
+          fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
+#pragma unroll
+          for (int q = 0; q < U; q++)
+            if (q < n) tout[(q0 + q) * kStPad + lane] = f[q][0];
+        }
+      __syncwarp();
+      if (c + K < nch) request_in(c + K);  // the tile just swept is free again
+      cp_commit();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
+      __syncwarp();
+    }
+    cp_wait<0>();
+    __syncwarp();
+    // backward: chunks in decreasing order through the ring (output layout)
+    auto request_back = [&](int c) {
+      C* t = ringt + (c % K) * kTile + lane * kStPad;
+      const int row = c * kStRows + lane;
+      if (row < N)
+        for (int s = 0; s < nsys; s++) cp(t + s, out + (j0 + s) * (int64_t)N + row);
+    };
+#pragma unroll 1
+    for (int q = 0; q < K; q++) {
+      const int c = nch - 1 - q;
+      if (c >= 0) request_back(c);
+      cp_commit();
+    }
+    r1[0] = r2[0] = C(0);
+#pragma unroll 1
+    for (int c = nch - 1; c >= 0; c--) {
+      cp_wait<K - 1>();
+      __syncwarp();
+      const int c0 = c * kStRows;
+      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      C* tw = ringt + (c % K) * kTile;
+      if (mine)
+        for (int top = rows - 1; top >= 0; top -= U) {
+          const int n = (top + 1) < U ? (top + 1) : U;
+          C f[U][1];
+#pragma unroll
+          for (int q = 0; q < U; q++) f[q][0] = tw[(q < n ? top - q : top) * kStPad + lane];
+          bwd_block<BW, ADJ, C, 1, U>(cf, c0 + top, n, f, r1, r2);
+#pragma unroll
+          for (int q = 0; q < U; q++)
+            if (q < n) tw[(top - q) * kStPad + lane] = f[q][0];
+        }
+      __syncwarp();
+      if (lane < rows)
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tw[lane * kStPad + s];
+      __syncwarp();
+      if (c - K >= 0) request_back(c - K);
+      cp_commit();
+    }
+    cp_wait<0>();
+    __syncwarp();
+  }
+}
+
 template <int BW, bool ADJ, typename C>
 static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int64_t M, C r, int axis,
                               cudaStream_t st) {
@@ -195,21 +433,23 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     base = reinterpret_cast<const C*>(p.c32);
   const Coefs<C> cf = coefs_of<C>(base, N);
   if (axis == 1) {
-    const LaunchShape sh = sweep_shape(BW, N, M, sizeof(C), sizeof(C), 1, 0, 0, 0);
-    auto k = sh.smem_coefs ? k_adi_il<BW, ADJ, true, C> : k_adi_il<BW, ADJ, false, C>;
-    if (sh.smem_coefs) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-      if (e != cudaSuccess) return e;
-    }
-    k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, N, u, out, M, r);
-  } else {
-    const size_t tiles = (size_t)(kSweepThreads / 32) * kAdiWarpTile * sizeof(C);
+    constexpr int D = 64;
     const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, 0, tiles, kSweepThreads);
-    auto k = sh.smem_coefs ? k_adi_st<BW, ADJ, true, C> : k_adi_st<BW, ADJ, false, C>;
+    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
+    const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
+    auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, u, out, M, r);
+  } else {
+    constexpr int K = 8;
+    const size_t tiles = ((size_t)K * kStRows * kAdiTile + (size_t)kStRows * kStPad) * sizeof(C);
+    const int64_t threads = ((M + 31) / 32) * 32;
+    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, 0, tiles, 32);
+    auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K> : k_adi_st2<BW, ADJ, false, C, K>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
-    k<<<sh.grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, u, out, M, r);
+    k<<<sh.grid, 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r);
   }
   return cudaGetLastError();
 }

@@ -81,16 +81,34 @@ __device__ __forceinline__ float refine_resid_z(const RefineCoefs<BW>& cf, int q
   return z;
 }
 
-// Exact FP32 -> FP64 widening with integer operations (the FP64 pipe, which
-// also executes conversions on GB300, stays free): for normal numbers the
-// exponent is rebiased and the mantissa shifted; zero, subnormals, inf and
-// NaN take the conversion instruction.
+// Exact FP32 -> FP64 widening with integer operations only: on GB300 the
+// conversion instruction runs on the slow FP64 pipe, and a conditional
+// conversion for the rare cases is if-converted into every call.  Normal
+// numbers rebias the exponent and shift the mantissa; zero keeps its sign;
+// subnormals are normalised with a leading-zero count; inf and NaN map to
+// exponent 2047.
 __device__ __forceinline__ double widen_exact(float f) {
   const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u;
   const uint32_t e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  const uint32_t lo = b << 29;
+  const uint32_t m = b & 0x7fffffu;
+  // normal: exponent e - 127 + 1023, mantissa m << 29
+  uint32_t hi = sign | ((e + 896u) << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  // subnormal: m * 2^-149 = 1.f * 2^(p - 149), p = index of the top set bit
+  const int p = 31 - __clz((int)(m | 1u));
+  const uint32_t shifted = (m << (23 - p)) & 0x7fffffu;  // drop the leading 1
+  const uint32_t hs = sign | ((uint32_t)(p + 874) << 20) | (shifted >> 3);
+  const uint32_t ls = shifted << 29;
+  const bool sub = (e == 0u) & (m != 0u);
+  hi = sub ? hs : hi;
+  lo = sub ? ls : lo;
+  const bool zero = (e == 0u) & (m == 0u);
+  hi = zero ? sign : hi;
+  lo = zero ? 0u : lo;
+  const bool special = e == 0xffu;  // inf / NaN
+  hi = special ? (sign | 0x7ff00000u | (m >> 3)) : hi;
+  lo = special ? (m << 29) : lo;
   return __hiloint2double((int)hi, (int)lo);
 }
 
