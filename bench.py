@@ -351,7 +351,7 @@ def run_ours(args):
         "e2e": e2e,
         "serving": serving,
         "other_workloads": others,
-        "gpu_launches": 4 * args.steps,  # f64 solve, refine solve, adjoint, band gradient
+        "gpu_launches": 5 * args.steps,  # f64 solve, refine solve, adjoint, band gradient (two kernels)
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -487,12 +487,28 @@ def run_other_configs(bs, st, hbm):
     bs.solve_refine(f, B32, XR)
     cols = np.random.default_rng(11).choice(M, 256, replace=False)
     samples["spline"] = (bands, B64[:, cols].cpu().numpy(), X64[:, cols].cpu().numpy(), XR[:, cols].cpu().numpy())
+    # the same right-hand sides with the periodic spline matrix (cyclic
+    # [1,4,1]/6, Sherman-Morrison fused into the sweeps), FP64 and FP32
+    pbands = synth.toeplitz_bands(N, (1 / 6, 4 / 6, 1 / 6))
+    fp = bs.Factor(pbands, periodic=True)
+    XP = B64.clone()
+    tp = time_alone(lambda: bs.solve(fp, XP), st, reps=10)
+    XP32 = B32.clone()
+    tp32 = time_alone(lambda: bs.solve(fp, XP32), st, reps=10)
+    XP.copy_(B64)
+    bs.solve(fp, XP)
+    samples["periodic_spline"] = (pbands, B64[:, cols].cpu().numpy(), XP[:, cols].cpu().numpy(), None)
+    del XP, XP32
     nm = N * M
     out["spline_N1024_M1048576"] = {
         "f64_solve": {"ms": t64, "unknowns_per_s": nm / (t64 * 1e-3), "hbm_gbs": 16 * nm / (t64 * 1e-3) / 1e9},
         "refine_solve": {"ms": tr, "unknowns_per_s": nm / (tr * 1e-3), "hbm_gbs": 12 * nm / (tr * 1e-3) / 1e9,
                          "hbm_frac_of_measured": 12 * nm / (tr * 1e-3) / 1e9 / hbm},
-        "refine_over_f64_speedup": t64 / tr}
+        "refine_over_f64_speedup": t64 / tr,
+        "periodic_f64_solve": {"ms": tp, "unknowns_per_s": nm / (tp * 1e-3), "hbm_gbs": 16 * nm / (tp * 1e-3) / 1e9,
+                               "over_plain_f64": tp / t64},
+        "periodic_f32_solve": {"ms": tp32, "unknowns_per_s": nm / (tp32 * 1e-3),
+                               "hbm_gbs": 8 * nm / (tp32 * 1e-3) / 1e9}}
     del B32, B64, X64, XR
     torch.cuda.empty_cache()
     # ADI 4096^2, r = 0.5: half-steps on both axes, forward and adjoint, FP64 and FP32
@@ -615,7 +631,7 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
             errs["adi_4096_full_step_f64"] = float(np.linalg.norm(full - ref) / np.linalg.norm(ref))
         else:
             b, Bs, X64s, XRs = smp
-            ref = oracle.solve(b, Bs)
+            ref = oracle.periodic_tri_solve_bands(b, Bs) if name.startswith("periodic") else oracle.solve(b, Bs)
             errs[f"{name}_f64_solve"] = float(np.linalg.norm(X64s - ref) / np.linalg.norm(ref))
             if XRs is not None:
                 errs[f"{name}_refine_solve"] = float(np.linalg.norm(XRs - ref) / np.linalg.norm(ref))

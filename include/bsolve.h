@@ -70,6 +70,25 @@ typedef enum { BS_INTERLEAVED = 0, BS_STRIDED = 1 } bs_layout;
  * until bs_destroy. */
 bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out);
 
+/* Factorise a periodic (cyclic) tridiagonal LHS, Sec. 3.3: row i has a_i at
+ * column i-1, b_i on the diagonal and c_i at column i+1, columns taken
+ * modulo N, so a_1 (band 0, row 0) sits in the top-right corner and c_N
+ * (band 2, row N-1) in the bottom-left one; the paper's case is constant
+ * a, b, c.  bands: host pointer, 3 x N doubles.  N >= 3.
+ * The matrix is split as A = A' + u v^T with gamma = -b_1,
+ * u = (gamma, 0, .., 0, c_N), v = (1, 0, .., 0, a_1 / gamma), A' tridiagonal
+ * with A'_11 = 2 b_1 and A'_NN = b_N - c_N a_1 / gamma.  A' is factorised as
+ * bs_factor does, and z = A'^{-1} u and q = A'^{-T} v are formed once on the
+ * host in FP64, so that every later solve applies x = y - (q.d)/(1 + v.z) z
+ * (y = A'^{-1} d) inside its own two sweeps with no extra pass; the adjoint
+ * applies the transposed correction the same way.  Returns BS_ESINGULAR for
+ * b_1 == 0, a bad pivot of A', or 1 + v.z == 0 or non-finite.
+ * The handle works with bs_solve, bs_solve_bf16, bs_solve_adjoint and the
+ * band gradients (whose output then includes the two corner entries);
+ * bs_solve_refine, bs_adi_halfstep and the server return BS_EUNSUPPORTED for
+ * it.  Blocking; the handle owns its device memory until bs_destroy. */
+bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out);
+
 /* Release a handle's device memory.  The caller must ensure no solve using it
  * is still running (synchronise its streams first).  NULL is a no-op. */
 bs_status bs_destroy(bs_handle h);
@@ -183,7 +202,9 @@ bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_dtype dtype,
 /* Band-gradient reduction alone, for a caller that already holds
  * GB = A^{-T} (dL/dX) (e.g. from bs_solve_adjoint without X):
  *   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - width/2, j]
- * (0 for entries outside the matrix), reduced in a fixed order (rows x
+ * (0 for entries outside the matrix; for a bs_factor_periodic handle the
+ * column index is taken modulo N and every entry is defined, the corners
+ * being dbands[0] (a_1) and dbands[3N-1] (c_N)), reduced in a fixed order (rows x
  * chunks of systems, then chunks in order), bitwise reproducible.  GB and X:
  * device, same dtype (BS_F64 or BS_F32) and layout; dbands: device
  * double[width*N], overwritten.  Uses stream-ordered scratch as

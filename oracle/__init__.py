@@ -43,6 +43,9 @@ def _load(path: str) -> ctypes.CDLL:
     L.oracle_band_grad.restype = None
     L.oracle_periodic_tri_solve.argtypes = [i64, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, dp, i64, i64, i64]
+    L.oracle_periodic_tri_solve_bands.argtypes = [i64, dp, dp, i64, i64, i64]
+    L.oracle_band_grad_periodic.argtypes = [i64, dp, dp, i64, i64, i64, dp]
+    L.oracle_band_grad_periodic.restype = None
     L.oracle_adi_halfstep.argtypes = [i64, i64, ctypes.c_double, dp, dp, i32]
     L.oracle_num_threads.argtypes = []
     L.oracle_set_threads.argtypes = [i32]
@@ -189,6 +192,40 @@ def periodic_tri_solve(a: float, b: float, c: float, B, layout: str = "interleav
     if st != 0:
         raise OracleError(f"periodic solve failed (status {st})")
     return X
+
+
+def periodic_tri_solve_bands(bands, B, layout: str = "interleaved"):
+    """Periodic tridiagonal solve via Sherman-Morrison (Sec. 3.3), general
+    bands: row i has a_i at column i-1 and c_i at column i+1 modulo N."""
+    b = _bands(bands)
+    X = np.array(B, dtype=np.float64, order="C", copy=True)
+    N, M, rs, ss = _strides(X, layout)
+    st = lib().oracle_periodic_tri_solve_bands(N, _p(b), _p(X), M, rs, ss)
+    if st != 0:
+        raise OracleError(f"periodic solve failed (status {st})")
+    return X
+
+
+def periodic_transpose_bands(bands) -> np.ndarray:
+    """Bands of A^T for a periodic tridiagonal A: row i of A^T has c_{i-1}
+    at column i-1 and a_{i+1} at column i+1 (indices modulo N)."""
+    b = np.asarray(bands, dtype=np.float64)
+    return np.stack([np.roll(b[2], 1), b[1], np.roll(b[0], -1)])
+
+
+def periodic_solve_adjoint(bands, G, layout: str = "interleaved"):
+    """A^{-T} G for a periodic tridiagonal A: the periodic solve of A^T."""
+    return periodic_tri_solve_bands(periodic_transpose_bands(bands), G, layout)
+
+
+def band_grad_periodic(GB, X, layout: str = "interleaved") -> np.ndarray:
+    """-(GB) X^T on the 3N entries of a periodic tridiagonal matrix."""
+    GB = np.ascontiguousarray(GB, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    N, M, rs, ss = _strides(X, layout)
+    out = np.zeros((3, N))
+    lib().oracle_band_grad_periodic(N, _p(GB), _p(X), M, rs, ss, _p(out))
+    return out
 
 
 def adi_halfstep(u, r: float, implicit_axis: int) -> np.ndarray:

@@ -279,44 +279,80 @@ void oracle_band_grad(int width, int64_t N, const double* GB, const double* X,
     }
 }
 
+/* The same for a periodic tridiagonal A (columns modulo N): every one of
+ * the 3N band entries is a matrix entry, the corners being a_1 (k = 0, i = 0,
+ * column N-1) and c_N (k = 2, i = N-1, column 0). */
+void oracle_band_grad_periodic(int64_t N, const double* GB, const double* X,
+                               int64_t M, int64_t rs, int64_t ss, double* dbands) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < N; i++)
+    for (int k = 0; k < 3; k++) {
+      int64_t col = (i + k - 1 + N) % N;
+      double s = 0.0;
+      for (int64_t j = 0; j < M; j++) s += EL(GB, i, j) * EL(X, col, j);
+      dbands[(int64_t)k * N + i] = -s;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Periodic tridiagonal via Sherman-Morrison (Sec. 3.3)                */
 /* ------------------------------------------------------------------ */
 
-/* Constant-coefficient periodic tridiagonal A (b on the diagonal, a below,
- * c above, a in the top-right corner and c in the bottom-left) written as
- * A = A' + u v^T with u = (-b, 0, .., 0, c)^T, v = (1, 0, .., 0, -a/b)^T.
- * A' is tridiagonal with corners removed, A'_11 = 2b and A'_NN = b + a c / b.
- * Solve A' y = d, A' z = u, then x = y - (v.y)/(1 + v.z) z.
- * (The paper prints the corners of A' still present and the second solve as
- * A' x = u; the reading used here is the one for which A = A' + u v^T.) */
-int oracle_periodic_tri_solve(int64_t N, double a, double b, double c, double* X,
-                              int64_t M, int64_t rs, int64_t ss) {
+/* Periodic tridiagonal A: row i has a_i at column i-1, b_i on the diagonal
+ * and c_i at column i+1, columns taken modulo N (so a_1 sits in the top-right
+ * corner and c_N in the bottom-left one; Sec. 3.3 has constant a, b, c).
+ * Written as A = A' + u v^T with g = -b_1, u = (g, 0, .., 0, c_N)^T and
+ * v = (1, 0, .., 0, a_1 / g)^T, so that A' is tridiagonal with its corners
+ * removed, A'_11 = b_1 - g = 2 b_1 and A'_NN = b_N - c_N a_1 / g.  Solve
+ * A' y = d and A' z = u, then x = y - (v.y)/(1 + v.z) z.  For constant
+ * coefficients this is the paper's u = (-b, 0, .., c), v = (1, 0, .., -a/b).
+ * (The paper prints A' with the corners still present and the second solve
+ * as A' x = u; the reading used here is the one for which A = A' + u v^T.) */
+int oracle_periodic_tri_solve_bands(int64_t N, const double* pb, double* X, int64_t M, int64_t rs, int64_t ss) {
+  const double* a = pb;
+  const double* b = pb + N;
+  const double* c = pb + 2 * N;
   double* bands = (double*)calloc(3 * N, sizeof(double));
   double* z = (double*)calloc(N, sizeof(double));
   int st;
+  const double g = -b[0];
   for (int64_t i = 0; i < N; i++) {
-    bands[i] = (i > 0) ? a : 0.0;
-    bands[N + i] = b;
-    bands[2 * N + i] = (i < N - 1) ? c : 0.0;
+    bands[i] = (i > 0) ? a[i] : 0.0;
+    bands[N + i] = b[i];
+    bands[2 * N + i] = (i < N - 1) ? c[i] : 0.0;
   }
-  bands[N + 0] = 2.0 * b;
-  bands[N + N - 1] = b + a * c / b;
-  z[0] = -b;
-  z[N - 1] = c;
+  bands[N + 0] = b[0] - g;
+  bands[N + N - 1] = b[N - 1] - c[N - 1] * a[0] / g;
+  z[0] = g;
+  z[N - 1] = c[N - 1];
   st = oracle_tri_solve(N, bands, z, 1, 1, 1);
   if (st == 0) st = oracle_tri_solve(N, bands, X, M, rs, ss);
   if (st == 0) {
-    double vz = z[0] - (a / b) * z[N - 1];
+    const double vz = z[0] + (a[0] / g) * z[N - 1];
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < M; j++) {
-      double vy = EL(X, 0, j) - (a / b) * EL(X, N - 1, j);
+      double vy = EL(X, 0, j) + (a[0] / g) * EL(X, N - 1, j);
       double s = vy / (1.0 + vz);
       for (int64_t i = 0; i < N; i++) EL(X, i, j) = EL(X, i, j) - s * z[i];
     }
   }
   free(bands);
   free(z);
+  return st;
+}
+
+/* The paper's constant-coefficient case (Sec. 3.3). */
+int oracle_periodic_tri_solve(int64_t N, double a, double b, double c, double* X, int64_t M, int64_t rs,
+                              int64_t ss) {
+  double* pb = (double*)malloc(sizeof(double) * 3 * N);
+  int st;
+  for (int64_t i = 0; i < N; i++) {
+    pb[i] = a;
+    pb[N + i] = b;
+    pb[2 * N + i] = c;
+  }
+  st = oracle_periodic_tri_solve_bands(N, pb, X, M, rs, ss);
+  free(pb);
   return st;
 }
 

@@ -15,6 +15,7 @@ i32, i64, vp, dp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER
 # name -> (restype, argtypes); kept in the order of include/*.h
 SIGNATURES = {
     "bs_factor": (i32, [dp, i32, i64, ctypes.POINTER(vp)]),
+    "bs_factor_periodic": (i32, [dp, i64, ctypes.POINTER(vp)]),
     "bs_destroy": (i32, [vp]),
     "bs_handle_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)]),
     "bs_lhs_bytes": (i64, [i32, i64, i32]),

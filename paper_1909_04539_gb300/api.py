@@ -53,23 +53,31 @@ class Factor:
     """One factorised shared LHS resident on a device (``bs_factor``).
 
     ``bands``: (width, N) float64 array-like, width 3 (a, b, c) or 5
-    (a, b, c, d, e), row-aligned as in the paper."""
+    (a, b, c, d, e), row-aligned as in the paper.  ``periodic=True`` (width 3
+    only, ``bs_factor_periodic``): cyclic tridiagonal, a_1 is the top-right
+    corner entry and c_N the bottom-left one."""
 
-    def __init__(self, bands, device=None):
+    def __init__(self, bands, device=None, periodic: bool = False):
         if isinstance(bands, torch.Tensor):
             bands = bands.detach().to("cpu", torch.float64).numpy()
         b = np.ascontiguousarray(np.asarray(bands, dtype=np.float64))
         if b.ndim != 2:
             raise ValueError("bands must be a (width, N) array")
         self.width, self.N = int(b.shape[0]), int(b.shape[1])
+        self.periodic = bool(periodic)
+        if self.periodic and self.width != 3:
+            raise ValueError("a periodic factor is tridiagonal (width 3)")
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if dev.type != "cuda":
             raise ValueError("Factor lives on a CUDA device")
         self.device = dev
         h = ctypes.c_void_p()
+        bp = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         with torch.cuda.device(dev):
-            check(lib().bs_factor(b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.width, self.N,
-                                  ctypes.byref(h)), "bs_factor")
+            if self.periodic:
+                check(lib().bs_factor_periodic(bp, self.N, ctypes.byref(h)), "bs_factor_periodic")
+            else:
+                check(lib().bs_factor(bp, self.width, self.N, ctypes.byref(h)), "bs_factor")
         self._h = h
 
     @property
@@ -239,15 +247,16 @@ class ADIHalfStepFn(torch.autograd.Function):
 class SolveFn(torch.autograd.Function):
     """X = A^{-1} B with gradients for B and for the band entries of A.
 
-    ``SolveFn.apply(bands, B, factor=None, layout="interleaved")``: bands is a
-    (width, N) float64 tensor (its values define A; pass ``factor`` to reuse
-    an existing factorisation of the same bands).  The backward pass is the
-    hand-written adjoint: one transposed solve with the same factors plus the
-    band-gradient reduction over the batch."""
+    ``SolveFn.apply(bands, B, factor=None, layout="interleaved", periodic=False)``:
+    bands is a (width, N) float64 tensor (its values define A; pass ``factor``
+    to reuse an existing factorisation of the same bands; ``periodic`` makes A
+    cyclic tridiagonal, whose band gradient includes the two corners).  The
+    backward pass is the hand-written adjoint: one transposed solve with the
+    same factors plus the band-gradient reduction over the batch."""
 
     @staticmethod
-    def forward(ctx, bands, B, factor=None, layout="interleaved"):
-        f = factor if factor is not None else Factor(bands.detach(), device=B.device)
+    def forward(ctx, bands, B, factor=None, layout="interleaved", periodic=False):
+        f = factor if factor is not None else Factor(bands.detach(), device=B.device, periodic=periodic)
         X = solve(f, B.detach().clone().contiguous(), layout)
         ctx.factor = f
         ctx.layout = layout
@@ -266,4 +275,4 @@ class SolveFn(torch.autograd.Function):
         else:
             solve_adjoint(ctx.factor, GB, ctx.layout)
             db = None
-        return db, (GB if ctx.needs_input_grad[1] else None), None, None
+        return db, (GB if ctx.needs_input_grad[1] else None), None, None, None

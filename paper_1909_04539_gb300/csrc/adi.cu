@@ -471,6 +471,7 @@ extern "C" bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_d
                                      double r, int implicit_axis, int adjoint, bs_stream stream) {
   using namespace bs;
   if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_adi_halfstep: unknown handle");
+  if (h->periodic) return set_error(BS_EUNSUPPORTED, "bs_adi_halfstep: not available for a periodic handle");
   if (!U || !out) return set_error(BS_EINVAL, "bs_adi_halfstep: null data pointer");
   if (ny < 1 || nx < 1) return set_error(BS_EINVAL, "bs_adi_halfstep: empty grid");
   if (implicit_axis != 0 && implicit_axis != 1) return set_error(BS_EINVAL, "bs_adi_halfstep: axis must be 0 or 1");

@@ -51,8 +51,8 @@ size_t band_grad_scratch_bytes(int width, int N, int64_t M) {
 }
 
 // Level 1.  blockIdx.x = row block, blockIdx.y = chunk.  partial layout:
-// [chunk][band][row].
-template <typename T, int W>
+// [chunk][band][row].  PER: periodic matrix, X rows taken modulo N.
+template <typename T, int W, bool PER>
 __global__ void __launch_bounds__(kGradThreads)
 k_band_grad_partial(int N, int64_t M, int64_t chunk, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
                     int64_t ss, double* __restrict__ partial) {
@@ -73,7 +73,12 @@ k_band_grad_partial(int N, int64_t M, int64_t chunk, const T* __restrict__ GB, c
 #pragma unroll
     for (int q = 0; q < NX; q++) {
       const int row = i0 - H + q;
-      x[q] = (row >= 0 && row < N) ? (double)X[row * rs + j * ss] : 0.0;
+      if constexpr (PER) {
+        const int pr = ((row % N) + N) % N;
+        x[q] = (double)X[pr * rs + j * ss];
+      } else {
+        x[q] = (row >= 0 && row < N) ? (double)X[row * rs + j * ss] : 0.0;
+      }
     }
 #pragma unroll
     for (int r = 0; r < kGradRows; r++) {
@@ -106,8 +111,9 @@ k_band_grad_partial(int N, int64_t M, int64_t chunk, const T* __restrict__ GB, c
   }
 }
 
-// Level 2: dbands[k*N + i] = -(sum over chunks, in order); 0 outside the matrix.
-__global__ void k_band_grad_finish(int W, int N, int chunks, const double* __restrict__ partial,
+// Level 2: dbands[k*N + i] = -(sum over chunks, in order); 0 outside the
+// matrix (a periodic matrix has no entries outside).
+__global__ void k_band_grad_finish(int W, int N, int chunks, int periodic, const double* __restrict__ partial,
                                    double* __restrict__ dbands) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)W * N) return;
@@ -115,35 +121,43 @@ __global__ void k_band_grad_finish(int W, int N, int chunks, const double* __res
   const int col = i + k - W / 2;
   double s = 0.0;
   for (int c = 0; c < chunks; c++) s += partial[(int64_t)c * W * N + t];
-  dbands[t] = (col >= 0 && col < N) ? -s : 0.0;
+  dbands[t] = (periodic || (col >= 0 && col < N)) ? -s : 0.0;
 }
 
 // Both levels with caller-provided scratch of band_grad_scratch_bytes().
-cudaError_t band_grad_with_scratch(int width, int N, const void* GB, const void* X, bs_dtype t, bs_layout layout,
-                                   int64_t M, double* dbands, double* scratch, cudaStream_t st) {
+cudaError_t band_grad_with_scratch(int width, int N, bool periodic, const void* GB, const void* X, bs_dtype t,
+                                   bs_layout layout, int64_t M, double* dbands, double* scratch, cudaStream_t st) {
   const int64_t rs = layout == BS_INTERLEAVED ? M : 1;
   const int64_t ss = layout == BS_INTERLEAVED ? 1 : N;
   const GradShape g = grad_shape(N, M);
   const dim3 grid(g.row_blocks, g.chunks);
-  if (t == BS_F64) {
+  if (periodic) {  // width 3 only
+    if (t == BS_F64)
+      k_band_grad_partial<double, 3, true><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
+                                                                           (const double*)X, rs, ss, scratch);
+    else
+      k_band_grad_partial<float, 3, true><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
+                                                                          (const float*)X, rs, ss, scratch);
+  } else if (t == BS_F64) {
     if (width == 3)
-      k_band_grad_partial<double, 3><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
+      k_band_grad_partial<double, 3, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
                                                                      (const double*)X, rs, ss, scratch);
     else
-      k_band_grad_partial<double, 5><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
+      k_band_grad_partial<double, 5, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
                                                                      (const double*)X, rs, ss, scratch);
   } else {
     if (width == 3)
-      k_band_grad_partial<float, 3><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
+      k_band_grad_partial<float, 3, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
                                                                     (const float*)X, rs, ss, scratch);
     else
-      k_band_grad_partial<float, 5><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
+      k_band_grad_partial<float, 5, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
                                                                     (const float*)X, rs, ss, scratch);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)width * N;
-  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, g.chunks, scratch, dbands);
+  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, g.chunks, periodic ? 1 : 0, scratch,
+                                                             dbands);
   return cudaGetLastError();
 }
 
@@ -155,7 +169,7 @@ bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype 
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, st);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(BS_ENOMEM, "band gradient: scratch")
                                                               : cuda_error(e, "band gradient scratch");
-  e = band_grad_with_scratch(h->width, N, GB, X, t, layout, M, dbands, scratch, st);
+  e = band_grad_with_scratch(h->width, N, h->periodic, GB, X, t, layout, M, dbands, scratch, st);
   const cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_error(e, "band gradient launch");
   if (e2 != cudaSuccess) return cuda_error(e2, "band gradient scratch release");
@@ -219,7 +233,7 @@ extern "C" bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const voi
   double* scratch = nullptr;
   cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc: scratch address");
-  e = band_grad_with_scratch(h->width, N, GB, X, dtype, layout, M, dbands, scratch,
+  e = band_grad_with_scratch(h->width, N, h->periodic, GB, X, dtype, layout, M, dbands, scratch,
                              reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc launch");
   return BS_OK;

@@ -66,7 +66,7 @@ namespace {
 // Host copies of one plan before upload: C_COUNT arrays of N.
 struct HostPlan {
   int bw = 1;
-  bool fwd_scale = false, bwd_scale = false;
+  bool fwd_scale = false, bwd_scale = false, periodic = false;
   std::vector<double> c;
 };
 
@@ -219,6 +219,96 @@ void free_handle(bs_handle h) {
   delete h;
 }
 
+// Applies one host plan to a single right-hand side in FP64 (the same
+// recurrence pair the kernels run), in place.
+void apply_plan(const HostPlan& p, int64_t N, std::vector<double>& x) {
+  auto C = [&](int k, int64_t i) { return p.c[(size_t)k * N + i]; };
+  for (int64_t i = 0; i < N; i++) {
+    double w = p.fwd_scale ? C(C_S, i) * x[i] : x[i];
+    if (i >= 1) w -= C(C_L1, i) * x[i - 1];
+    if (p.bw == 2 && i >= 2) w -= C(C_L2, i) * x[i - 2];
+    x[i] = w;
+  }
+  for (int64_t i = N - 1; i >= 0; i--) {
+    double v = p.bwd_scale ? C(C_T, i) * x[i] : x[i];
+    if (i + 1 < N) v -= C(C_U1, i) * x[i + 1];
+    if (p.bw == 2 && i + 2 < N) v -= C(C_U2, i) * x[i + 2];
+    x[i] = v;
+  }
+}
+
+// Copies the host plans, factor entries and bands (b64, width * N) of one
+// LHS to the current device and registers the handle.
+bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool periodic,
+                        const std::vector<double>& entries, const std::vector<double>& b64, bs_handle* out) {
+  std::vector<float> bhi(b64.size()), blo(b64.size());
+  for (size_t q = 0; q < b64.size(); q++) {
+    const float hi = (float)b64[q];
+    bhi[q] = hi;
+    blo[q] = (float)(b64[q] - (double)hi);
+  }
+  bs_handle hd = new (std::nothrow) bs_factor_s();
+  if (!hd) return set_error(BS_ENOMEM, "factor: host allocation failed");
+  std::memset(hd, 0, sizeof(*hd));
+  hd->width = width;
+  hd->N = N;
+  cudaGetDevice(&hd->device);
+  size_t bytes = 0;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 3 && e == cudaSuccess; p++) {
+    SweepPlan& sp = hd->plan[p];
+    sp.bw = hp[p].bw;
+    sp.fwd_scale = hp[p].fwd_scale;
+    sp.bwd_scale = hp[p].bwd_scale;
+    sp.periodic = hp[p].periodic;
+    std::vector<float> c32(hp[p].c.size());
+    for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp[p].c[q];
+    e = cudaMalloc(&sp.c64, sizeof(double) * hp[p].c.size());
+    if (e == cudaSuccess) e = cudaMalloc(&sp.c32, sizeof(float) * c32.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sp.c64, hp[p].c.data(), sizeof(double) * hp[p].c.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
+    bytes += (sizeof(double) + sizeof(float)) * hp[p].c.size();
+  }
+  {
+    std::vector<float> ehi(entries.size()), elo(entries.size());
+    for (size_t q = 0; q < entries.size(); q++) {
+      ehi[q] = (float)entries[q];
+      elo[q] = (float)(entries[q] - (double)ehi[q]);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_hi, sizeof(float) * ehi.size());
+    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_lo, sizeof(float) * elo.size());
+    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_hi, ehi.data(), sizeof(float) * ehi.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_lo, elo.data(), sizeof(float) * elo.size(), cudaMemcpyHostToDevice);
+    bytes += 2 * sizeof(float) * ehi.size();
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands64, sizeof(double) * b64.size());
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_hi, sizeof(float) * bhi.size());
+  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_lo, sizeof(float) * blo.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands64, b64.data(), sizeof(double) * b64.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands_hi, bhi.data(), sizeof(float) * bhi.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hd->bands_lo, blo.data(), sizeof(float) * blo.size(), cudaMemcpyHostToDevice);
+  bytes += (sizeof(double) + 2 * sizeof(float)) * b64.size();
+  if (e != cudaSuccess) {
+    free_handle(hd);
+    if (e == cudaErrorMemoryAllocation) return set_error(BS_ENOMEM, "factor: cudaMalloc failed");
+    return cuda_error(e, "factor upload");
+  }
+  hd->device_bytes = bytes;
+  hd->has_ul = has_ul;
+  hd->periodic = periodic;
+  {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    g_handles.insert(hd);
+  }
+  *out = hd;
+  return BS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -284,78 +374,77 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
       for (int64_t i = 0; i < N; i++) hp[2].c[(size_t)k * N + i] = rp.c[(size_t)k * N + (N - 1 - i)];
   }
 
-  // Bands with the outside entries zeroed, and their FP32 hi/lo split.
+  // Bands with the outside entries zeroed.
   std::vector<double> b64((size_t)width * N, 0.0);
-  std::vector<float> bhi((size_t)width * N), blo((size_t)width * N);
   const int h = width / 2;
   for (int k = 0; k < width; k++)
     for (int64_t i = 0; i < N; i++) {
       const int64_t col = i + k - h;
-      const double v = (col >= 0 && col < N) ? bd[k][i] : 0.0;
-      b64[(size_t)k * N + i] = v;
-      const float hi = (float)v;
-      bhi[(size_t)k * N + i] = hi;
-      blo[(size_t)k * N + i] = (float)(v - (double)hi);
+      b64[(size_t)k * N + i] = (col >= 0 && col < N) ? bd[k][i] : 0.0;
     }
+  return upload_handle(width, N, hp, has_ul, false, entries, b64, out);
+}
 
-  bs_handle hd = new (std::nothrow) bs_factor_s();
-  if (!hd) return set_error(BS_ENOMEM, "bs_factor: host allocation failed");
-  std::memset(hd, 0, sizeof(*hd));
-  hd->width = width;
-  hd->N = N;
-  cudaGetDevice(&hd->device);
-  size_t bytes = 0;
-  cudaError_t e = cudaSuccess;
-  for (int p = 0; p < 3 && e == cudaSuccess; p++) {
-    SweepPlan& sp = hd->plan[p];
-    sp.bw = hp[p].bw;
-    sp.fwd_scale = hp[p].fwd_scale;
-    sp.bwd_scale = hp[p].bwd_scale;
-    std::vector<float> c32(hp[p].c.size());
-    for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp[p].c[q];
-    e = cudaMalloc(&sp.c64, sizeof(double) * hp[p].c.size());
-    if (e == cudaSuccess) e = cudaMalloc(&sp.c32, sizeof(float) * c32.size());
-    if (e == cudaSuccess)
-      e = cudaMemcpy(sp.c64, hp[p].c.data(), sizeof(double) * hp[p].c.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
-    bytes += (sizeof(double) + sizeof(float)) * hp[p].c.size();
+bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out) {
+  if (!out) return set_error(BS_EINVAL, "bs_factor_periodic: out is NULL");
+  *out = nullptr;
+  if (!bands) return set_error(BS_EINVAL, "bs_factor_periodic: bands is NULL");
+  if (N < 3) return set_error(BS_EINVAL, "bs_factor_periodic: N must be >= 3");
+  if (N > (int64_t)1 << 28) return set_error(BS_EINVAL, "bs_factor_periodic: N too large");
+  const double* a = bands;
+  const double* b = bands + N;
+  const double* c = bands + 2 * N;
+  // Sherman-Morrison split (Sec. 3.3): A = A' + u v^T, gamma = -b_1,
+  // u = (gamma, 0, .., 0, c_N), v = (1, 0, .., 0, a_1 / gamma).
+  const double gam = -b[0];
+  if (bad(gam)) return set_error(BS_ESINGULAR, "bs_factor_periodic: b_1 must be non-zero");
+  const double v_last = a[0] / gam;
+  std::vector<double> mod((size_t)3 * N);
+  for (int64_t i = 0; i < N; i++) {
+    mod[i] = (i > 0) ? a[i] : 0.0;
+    mod[N + i] = b[i];
+    mod[2 * N + i] = (i + 1 < N) ? c[i] : 0.0;
   }
-  {
-    std::vector<float> ehi(entries.size()), elo(entries.size());
-    for (size_t q = 0; q < entries.size(); q++) {
-      ehi[q] = (float)entries[q];
-      elo[q] = (float)(entries[q] - (double)ehi[q]);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_hi, sizeof(float) * ehi.size());
-    if (e == cudaSuccess) e = cudaMalloc(&hd->lu_lo, sizeof(float) * elo.size());
-    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_hi, ehi.data(), sizeof(float) * ehi.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(hd->lu_lo, elo.data(), sizeof(float) * elo.size(), cudaMemcpyHostToDevice);
-    bytes += 2 * sizeof(float) * ehi.size();
+  mod[N] = b[0] - gam;
+  mod[N + N - 1] = b[N - 1] - c[N - 1] * v_last;
+  const double* bd[3] = {mod.data(), mod.data() + N, mod.data() + 2 * N};
+
+  HostPlan hp[3];
+  for (auto& p : hp) p.c.assign((size_t)C_COUNT * N, 0.0);
+  std::vector<double> entries;
+  const int64_t bad_row = make_plans(bd, 3, N, hp[0], hp[1], &entries);
+  if (bad_row)
+    return set_error(BS_ESINGULAR, "bs_factor_periodic: bad pivot of the corner-free matrix at row " +
+                                       std::to_string(bad_row));
+  // z = A'^{-1} u and q = A'^{-T} v, in FP64 with the plans themselves.
+  std::vector<double> z(N, 0.0), q(N, 0.0);
+  z[0] = gam;
+  z[N - 1] = c[N - 1];
+  q[0] = 1.0;
+  q[N - 1] = v_last;
+  apply_plan(hp[0], N, z);
+  apply_plan(hp[1], N, q);
+  const double vz = z[0] + v_last * z[N - 1];
+  const double den = 1.0 + vz;
+  // 1 + v.z is zero exactly when A is singular; within a few rounding errors
+  // of zero no digit of the correction can be trusted either.
+  if (bad(den) || std::fabs(den) <= 4.0 * (double)N * 2.220446049250313e-16 * (1.0 + std::fabs(vz)))
+    return set_error(BS_ESINGULAR, "bs_factor_periodic: 1 + v.z is zero to rounding (the periodic matrix is singular)");
+  // primal: sigma = q.d (= v.y), x = y - sigma z / den;
+  // adjoint of A = A' + u v^T: sigma = z.g (= u.(A'^{-T} g)), x = y - sigma q / den
+  for (int64_t i = 0; i < N; i++) {
+    hp[0].c[(size_t)C_PW * N + i] = q[i];
+    hp[0].c[(size_t)C_PC * N + i] = z[i] / den;
+    hp[1].c[(size_t)C_PW * N + i] = z[i];
+    hp[1].c[(size_t)C_PC * N + i] = q[i] / den;
   }
-  if (e == cudaSuccess) e = cudaMalloc(&hd->bands64, sizeof(double) * b64.size());
-  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_hi, sizeof(float) * bhi.size());
-  if (e == cudaSuccess) e = cudaMalloc(&hd->bands_lo, sizeof(float) * blo.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(hd->bands64, b64.data(), sizeof(double) * b64.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(hd->bands_hi, bhi.data(), sizeof(float) * bhi.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(hd->bands_lo, blo.data(), sizeof(float) * blo.size(), cudaMemcpyHostToDevice);
-  bytes += (sizeof(double) + 2 * sizeof(float)) * b64.size();
-  if (e != cudaSuccess) {
-    free_handle(hd);
-    if (e == cudaErrorMemoryAllocation) return set_error(BS_ENOMEM, "bs_factor: cudaMalloc failed");
-    return cuda_error(e, "bs_factor");
-  }
-  hd->device_bytes = bytes;
-  hd->has_ul = has_ul;
-  {
-    std::lock_guard<std::mutex> lk(g_handles_mu);
-    g_handles.insert(hd);
-  }
-  *out = hd;
-  return BS_OK;
+  hp[0].periodic = hp[1].periodic = true;
+  hp[2] = hp[0];  // no reversed elimination for the periodic case (never read)
+  hp[2].periodic = true;
+
+  // The periodic bands themselves, corners included.
+  std::vector<double> b64(bands, bands + 3 * N);
+  return upload_handle(3, N, hp, false, true, entries, b64, out);
 }
 
 bs_status bs_destroy(bs_handle h) {

@@ -22,7 +22,11 @@ namespace bs {
 //   backward: x_i = t_i w_i - u1_i x_{i+1} - u2_i x_{i+2}          (i = N-1..0)
 // with s == 1 or t == 1 where the flags say so, l2 == u2 == 0 for width 3,
 // and every coefficient that would reach outside the matrix stored as 0.
-enum { C_S = 0, C_L1, C_L2, C_T, C_U1, C_U2, C_COUNT };
+// A periodic (cyclic tridiagonal) plan adds the Sherman-Morrison rank-one
+// correction (Sec. 3.3) in the same two passes: the forward pass also sums
+// sigma = sum_i pw_i f_i over the raw right-hand side, and the backward pass
+// writes x_i - sigma pc_i while the recurrence carries the uncorrected x_i.
+enum { C_S = 0, C_L1, C_L2, C_T, C_U1, C_U2, C_PW, C_PC, C_COUNT };
 
 template <typename C>
 struct Coefs {
@@ -32,20 +36,23 @@ struct Coefs {
   const C* t;
   const C* u1;
   const C* u2;
+  const C* pw;  // periodic plans only
+  const C* pc;
 };
 
 struct SweepPlan {
   int bw;          // band half-width: 1 (tri) or 2 (penta)
   bool fwd_scale;  // s present
   bool bwd_scale;  // t present
+  bool periodic;   // pw / pc present (Sherman-Morrison correction)
   double* c64;     // device, C_COUNT * N
   float* c32;      // device, C_COUNT * N
 };
 
 template <typename C>
 BS_HD inline Coefs<C> coefs_of(const C* base, int64_t N) {
-  return Coefs<C>{base + C_S * N, base + C_L1 * N, base + C_L2 * N,
-                  base + C_T * N, base + C_U1 * N, base + C_U2 * N};
+  return Coefs<C>{base + C_S * N,  base + C_L1 * N, base + C_L2 * N, base + C_T * N,
+                  base + C_U1 * N, base + C_U2 * N, base + C_PW * N, base + C_PC * N};
 }
 
 }  // namespace bs
@@ -69,6 +76,8 @@ struct bs_factor_s {
   float* lu_lo;
   size_t device_bytes;
   bool has_ul;             // plan[2] is valid (reversed elimination met no bad pivot)
+  bool periodic;           // cyclic tridiagonal (bs_factor_periodic): bands64 holds the
+                           // corner entries a_1 (band 0, row 0) and c_N (band 2, row N-1)
 };
 
 namespace bs {

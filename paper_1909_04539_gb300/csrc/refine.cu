@@ -474,6 +474,7 @@ extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtyp
                                      int64_t M, int refine_steps, bs_refine_mode mode, bs_stream stream) {
   using namespace bs;
   if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_solve_refine: unknown handle");
+  if (h->periodic) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: not available for a periodic handle");
   if (!B || !X) return set_error(BS_EINVAL, "bs_solve_refine: null data pointer");
   if (M < 1) return set_error(BS_EINVAL, "bs_solve_refine: M must be >= 1");
   if (layout != BS_INTERLEAVED)

@@ -364,6 +364,7 @@ bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* h
                            int64_t* request_id) {
   if (!s || !request_id) return set_error(BS_EINVAL, "bs_server_submit: null argument");
   if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_server_submit: unknown handle");
+  if (h->periodic) return set_error(BS_EUNSUPPORTED, "bs_server_submit: not available for a periodic handle");
   if (h->device != s->device) return set_error(BS_EINVAL, "bs_server_submit: handle on another device");
   if (!host_B || !host_X) return set_error(BS_EINVAL, "bs_server_submit: null buffer");
   if (mode != SERVE_F64 && mode != SERVE_F32_REFINE) return set_error(BS_EINVAL, "bs_server_submit: bad mode");

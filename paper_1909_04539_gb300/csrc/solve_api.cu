@@ -15,7 +15,8 @@ static int64_t g_opt[BS_OPT_COUNT] = {0};
 int64_t option(int o) { return (o >= 0 && o < BS_OPT_COUNT) ? g_opt[o] : 0; }
 
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
-                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb) {
+                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
+                        int extra_coef_arrays) {
   const DeviceInfo& d = device_info();
   LaunchShape sh{};
   if (tpb <= 0) {
@@ -23,7 +24,7 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
     while (tpb > 32 && threads_needed < (int64_t)2 * d.sms * tpb) tpb /= 2;
   }
   sh.threads = tpb;
-  const size_t coef_bytes = align_up((size_t)(1 + 2 * bw) * N * coef_elem, 16);
+  const size_t coef_bytes = align_up((size_t)(1 + 2 * bw + extra_coef_arrays) * N * coef_elem, 16);
   const size_t extra = extra_smem_fixed + extra_smem_per_thread * (size_t)tpb;
   const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
   sh.smem_coefs = coef_bytes + extra <= limit;

@@ -9,7 +9,7 @@ int64_t option(int o);
 
 cudaError_t sweep_f32(const SweepPlan& p, bool adjoint, int N, const void* in, void* out,
                         bs_layout layout, int64_t M, cudaStream_t st) {
-  if (layout == BS_INTERLEAVED && option(BS_OPT_SWEEP_KERNEL) == 2) {
+  if (layout == BS_INTERLEAVED && !p.periodic && option(BS_OPT_SWEEP_KERNEL) == 2) {
     cudaError_t e = cudaSuccess;
     if (sweep_tma<float>(p, adjoint, N, reinterpret_cast<const float*>(in), reinterpret_cast<float*>(out), M, st, &e))
       return e;

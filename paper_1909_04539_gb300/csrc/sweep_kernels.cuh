@@ -102,9 +102,9 @@ struct IO<__nv_bfloat16, float, 1> {
 
 // ------------------------------------------------------- coefficient staging
 
-// Copies the coefficient arrays a sweep of kind (BW, ADJ) uses into shared
-// memory (when SMEM) and returns pointers to wherever they live.
-template <int BW, bool ADJ, bool SMEM, typename C>
+// Copies the coefficient arrays a sweep of kind (BW, ADJ, PER) uses into
+// shared memory (when SMEM) and returns pointers to wherever they live.
+template <int BW, bool ADJ, bool SMEM, typename C, bool PER = false>
 __device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
   if (SMEM) {
     int off = 0;
@@ -120,14 +120,45 @@ __device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
     if (ADJ) stage(cf.t);
     stage(cf.u1);
     if (BW == 2) stage(cf.u2);
+    if (PER) {
+      stage(cf.pw);
+      stage(cf.pc);
+    }
     __syncthreads();
   }
   return cf;
 }
 
-template <int BW>
+template <int BW, bool PER = false>
 __host__ __device__ constexpr int coef_arrays() {
-  return 1 + 2 * BW;  // scale + BW lower + BW upper
+  return 1 + 2 * BW + (PER ? 2 : 0);  // scale + BW lower + BW upper (+ pw, pc)
+}
+
+// Periodic correction terms (Sherman-Morrison, Sec. 3.3) of one block of U
+// rows: before the forward block, sig += pw_i f_i over the raw inputs; after
+// the backward block, f_i -= sig pc_i (the recurrence state keeps the
+// uncorrected values).
+template <typename C, int V, int U>
+__device__ __forceinline__ void per_dot(const Coefs<C>& cf, int i0, int n, const C (&f)[U][V], C (&sig)[V]) {
+  C pw[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) pw[u] = cf.pw[(u < n) ? i0 + u : i0];
+#pragma unroll
+  for (int u = 0; u < U; u++)
+    if (u < n)
+#pragma unroll
+      for (int v = 0; v < V; v++) sig[v] = fma(pw[u], f[u][v], sig[v]);
+}
+template <typename C, int V, int U>
+__device__ __forceinline__ void per_fix(const Coefs<C>& cf, int top, int n, C (&f)[U][V], const C (&sig)[V]) {
+  C pc[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) pc[u] = cf.pc[(u < n) ? top - u : top];
+#pragma unroll
+  for (int u = 0; u < U; u++)
+    if (u < n)
+#pragma unroll
+      for (int v = 0; v < V; v++) f[u][v] = fma(-sig[v], pc[u], f[u][v]);
 }
 
 // One forward step for V systems at row i (f holds the input on entry and
@@ -275,18 +306,20 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // Rows are moved in blocks of U with a two-block register pipeline: the loads
 // of the next block are issued before the current block is computed, so each
 // thread keeps up to 2*U*V loads in flight.
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const int64_t ngroups = M / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
     const Sin* pin = in + g * V;
     Sout* pout = out + g * V;
     C a[U][V], b[U][V];
-    C r1[V], r2[V];
+    C r1[V], r2[V], sig[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) sig[v] = C(0);
 
     auto load_fwd = [&](C (&blk)[U][V], int i0) {
 #pragma unroll
@@ -295,6 +328,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     };
     auto run_fwd = [&](C (&blk)[U][V], int i0) {
       const int n = (N - i0) < U ? (N - i0) : U;
+      if constexpr (PER) per_dot<C, V, U>(cf, i0, n, blk, sig);
       fwd_block<BW, ADJ, C, V, U>(cf, i0, n, blk, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
@@ -308,6 +342,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     auto run_bwd = [&](C (&blk)[U][V], int top) {
       const int n = (top + 1) < U ? (top + 1) : U;
       bwd_block<BW, ADJ, C, V, U>(cf, top, n, blk, r1, r2);
+      if constexpr (PER) per_fix<C, V, U>(cf, top, n, blk, sig);
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::store(pout + (int64_t)(top - u) * M, blk[u]);
@@ -345,15 +380,15 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 // of the last D rows stay in the ring, so the backward sweep starts without
 // reloading them; the earlier ones go to the output buffer and are streamed
 // back through the same ring.
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
   static_assert(V * sizeof(Sout) == 16 || V * sizeof(Sout) == 8, "output lane row must be 8 or 16 bytes");
   constexpr int U = 4;  // rows per block; D is a multiple of U
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER>() * N * sizeof(C), 16) : 0;
   unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
   const uint32_t ring_s = smem_u32(ring);
   const uint32_t pitch = blockDim.x * 16;
@@ -362,9 +397,9 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
     const Sin* pin = in + g * V;
     Sout* pout = out + g * V;
-    C r1[V], r2[V];
+    C r1[V], r2[V], sig[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = sig[v] = C(0);
     // forward sweep: rows 0..D-1 requested up front (one copy group per
     // row), then each block of U rows is consumed and its slots refilled
     const Sin* pnext = pin;  // next row to request
@@ -384,6 +419,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
+      if constexpr (PER) per_dot<C, V, U>(cf, i0, n, f, sig);
       fwd_block<BW, ADJ, C, V, U>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++) {
@@ -417,6 +453,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
       bwd_block<BW, ADJ, C, V, U>(cf, top, n, f, r1, r2);
+      if constexpr (PER) per_fix<C, V, U>(cf, top, n, f, sig);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int i = top - u;
@@ -443,21 +480,21 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 constexpr int kStRows = 32;
 constexpr int kStPad = 33;
 
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smc = reinterpret_cast<C*>(smem_raw);
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, smc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kWarps = kSweepThreads / 32;
-  C* tile = smc + (SMEM ? coef_arrays<BW>() * N : 0) + warp * kStRows * kStPad;
+  C* tile = smc + (SMEM ? coef_arrays<BW, PER>() * N : 0) + warp * kStRows * kStPad;
   const int64_t nwg = (M + 31) / 32;
   for (int64_t wg = (int64_t)blockIdx.x * kWarps + warp; wg < nwg; wg += (int64_t)gridDim.x * kWarps) {
     const int64_t j0 = wg * 32;
     const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
     const bool mine = lane < nsys;
-    C r1[1] = {C(0)}, r2[1] = {C(0)};
+    C r1[1] = {C(0)}, r2[1] = {C(0)}, sig[1] = {C(0)};
     // forward sweep, chunks of rows in increasing order
     for (int c0 = 0; c0 < N; c0 += kStRows) {
       const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
@@ -471,6 +508,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (mine)
         for (int r = 0; r < rows; r++) {
           C f[1] = {tile[r * kStPad + lane]};
+          if constexpr (PER) sig[0] = fma(cf.pw[c0 + r], f[0], sig[0]);
           fwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
           tile[r * kStPad + lane] = f[0];
         }
@@ -498,6 +536,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
         for (int r = rows - 1; r >= 0; r--) {
           C f[1] = {tile[r * kStPad + lane]};
           bwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
+          if constexpr (PER) f[0] = fma(-sig[0], cf.pc[c0 + r], f[0]);
           tile[r * kStPad + lane] = f[0];
         }
       __syncwarp();
@@ -527,56 +566,59 @@ struct LaunchShape {
 // coefficients (ring slots); extra_smem_fixed: per CTA (transpose tiles).
 // tpb = 0 lets the policy pick 32, 64 or 128 threads per CTA so that small
 // batches still spread over every SM.
+// extra_coef_arrays: coefficient arrays staged beyond the 1 + 2 bw of a plain
+// sweep (2 for the periodic correction).
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
-                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb);
+                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
+                        int extra_coef_arrays = 0);
 
-template <int BW, bool ADJ, typename C, typename Sin, typename Sout, int V>
+template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout, int V>
 cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
   constexpr int U = 8;
   const int64_t groups = M / V;
   if constexpr (V > 1) {
     // pipelined kernel: ring of kRingRows 16-byte slots per lane
     constexpr int D = 16;
-    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, D * 16, 0, 0);
+    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
     const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
     if (sh.smem_coefs) {
-      auto k = k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D>;
+      auto k = k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
     } else {
-      auto k = k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D>;
+      auto k = k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
     }
     return cudaGetLastError();
   } else {
-    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, 0, 0, 0);
+    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, 0, 0, 0, PER ? 2 : 0);
     if (sh.smem_coefs) {
-      auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U>;
+      auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
       if (e != cudaSuccess) return e;
       k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, N, in, out, M);
     } else {
-      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U><<<sh.grid, sh.threads, 0, st>>>(cf, N, in, out, M);
+      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U, PER><<<sh.grid, sh.threads, 0, st>>>(cf, N, in, out, M);
     }
     return cudaGetLastError();
   }
 }
 
-template <int BW, bool ADJ, typename C, typename Sin, typename Sout>
+template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout>
 cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
   const int64_t threads = ((M + 31) / 32) * 32;
   const size_t tiles = (size_t)(kSweepThreads / 32) * kStRows * kStPad * sizeof(C);
-  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads);
+  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads, PER ? 2 : 0);
   if (sh.smem_coefs) {
-    auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout>;
+    auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout, PER>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
     k<<<sh.grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, in, out, M);
   } else {
-    k_sweep_st<BW, ADJ, false, C, Sin, Sout><<<sh.grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M);
+    k_sweep_st<BW, ADJ, false, C, Sin, Sout, PER><<<sh.grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M);
   }
   return cudaGetLastError();
 }
@@ -600,17 +642,19 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
   const bool half = kHalf && (M % 2 == 0) && (reinterpret_cast<uintptr_t>(in) % 8 == 0) &&
                     (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
                     (M / VEC < (int64_t)device_info().sms * 32 * 8);
-#define BS_DISPATCH(BWV, ADJV)                                                                       \
-  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, C, Sin, Sout>(cf, N, in, out, M, st);          \
-  if constexpr (kHalf) {                                                                             \
-    if (half) return launch_il<BWV, ADJV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, st);     \
-  }                                                                                                  \
-  if (vec) return launch_il<BWV, ADJV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);                      \
-  return launch_il<BWV, ADJV, C, Sin, Sout, 1>(cf, N, in, out, M, st);
-  if (p.bw == 1) {
-    if (!adjoint) { BS_DISPATCH(1, false) } else { BS_DISPATCH(1, true) }
+#define BS_DISPATCH(BWV, ADJV, PERV)                                                                  \
+  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, st);      \
+  if constexpr (kHalf) {                                                                              \
+    if (half) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, st); \
+  }                                                                                                   \
+  if (vec) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);                \
+  return launch_il<BWV, ADJV, PERV, C, Sin, Sout, 1>(cf, N, in, out, M, st);
+  if (p.bw == 1 && p.periodic) {
+    if (!adjoint) { BS_DISPATCH(1, false, true) } else { BS_DISPATCH(1, true, true) }
+  } else if (p.bw == 1) {
+    if (!adjoint) { BS_DISPATCH(1, false, false) } else { BS_DISPATCH(1, true, false) }
   } else {
-    if (!adjoint) { BS_DISPATCH(2, false) } else { BS_DISPATCH(2, true) }
+    if (!adjoint) { BS_DISPATCH(2, false, false) } else { BS_DISPATCH(2, true, false) }
   }
 #undef BS_DISPATCH
 }

@@ -49,6 +49,17 @@ def random_tri_bands(N: int, rng: np.random.Generator) -> np.ndarray:
     return np.stack([a, b, c])
 
 
+def random_periodic_bands(N: int, rng: np.random.Generator) -> np.ndarray:
+    """Periodic tridiagonal bands: a, c ~ U(-1,1) then u ~ U(1,2) for all N
+    rows, b = |a| + |c| + u; a_1 and c_N are kept (they are the corner
+    entries of the cyclic matrix)."""
+    a = rng.uniform(-1.0, 1.0, N)
+    c = rng.uniform(-1.0, 1.0, N)
+    u = rng.uniform(1.0, 2.0, N)
+    b = np.abs(a) + np.abs(c) + u
+    return np.stack([a, b, c])
+
+
 def random_penta_bands(N: int, rng: np.random.Generator) -> np.ndarray:
     """Off-diagonals a, b, d, e ~ U(-1,1), then u ~ U(1,2); outside entries
     zeroed; diagonal c = sum of |off-diagonals| + u (strictly dominant)."""

@@ -31,6 +31,17 @@ def periodic_tri(N: int, a: float, b: float, c: float) -> np.ndarray:
     return A
 
 
+def periodic_from_bands(bands: np.ndarray) -> np.ndarray:
+    """Full cyclic tridiagonal matrix: band k of row i at column
+    (i + k - 1) mod N (N >= 3)."""
+    _, N = bands.shape
+    A = np.zeros((N, N))
+    for i in range(N):
+        for k in range(3):
+            A[i, (i + k - 1) % N] = bands[k, i]
+    return A
+
+
 def to_layout(X_nm: np.ndarray, layout: str) -> np.ndarray:
     """(N, M) interleaved block to the requested storage."""
     return np.ascontiguousarray(X_nm if layout == "interleaved" else X_nm.T)

@@ -15,7 +15,7 @@ import scipy.linalg
 
 import oracle
 import synth
-from tests.dense import (dense_from_bands, from_layout, periodic_tri, rel_l2,
+from tests.dense import (dense_from_bands, from_layout, periodic_from_bands, periodic_tri, rel_l2,
                          second_difference, to_layout)
 
 LAYOUTS = ("interleaved", "strided")
@@ -186,6 +186,58 @@ def pin_periodic(N, a, b, c, seed=9):
         assert rel_l2(x, v / (b + 2 * a * math.cos(2 * math.pi * k / N))) < 1e-13
 
 
+def pin_periodic_bands(N, seed=13):
+    """General periodic bands (a_1 and c_N in the corners) against a dense
+    solve of the periodic matrix."""
+    rng = np.random.default_rng(seed)
+    a, c = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    b = np.abs(a) + np.abs(c) + rng.uniform(1, 2, N)
+    A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    A[0, N - 1] = a[0]
+    A[N - 1, 0] = c[N - 1]
+    B = rng.uniform(-1, 1, (N, 3))
+    X = oracle.periodic_tri_solve_bands(np.stack([a, b, c]), B)
+    assert rel_l2(X, np.linalg.solve(A, B)) < 1e-13
+
+
+def pin_periodic_adjoint(N, layout, seed=15):
+    """Periodic A^{-T} G against a dense solve with the transposed cyclic
+    matrix, and the dot-product identity <A^{-T} g, b> = <g, A^{-1} b>."""
+    rng = np.random.default_rng(seed)
+    bands = synth.random_periodic_bands(N, rng)
+    G = rng.uniform(-1, 1, (N, 4))
+    Bm = rng.uniform(-1, 1, (N, 4))
+    A = periodic_from_bands(bands)
+    Y = from_layout(oracle.periodic_solve_adjoint(bands, to_layout(G, layout), layout), layout)
+    assert rel_l2(Y, np.linalg.solve(A.T, G)) < 1e-13
+    X = oracle.periodic_tri_solve_bands(bands, Bm)
+    assert np.allclose(np.sum(Y * Bm, axis=0), np.sum(G * X, axis=0), rtol=1e-13, atol=1e-13)
+
+
+def pin_periodic_band_grad(N=5, M=3, seed=16):
+    """Band gradient of L = sum(G * A^{-1} B) for a cyclic A, every entry
+    (corners included) against -(A^{-T} G) X^T and central differences."""
+    rng = np.random.default_rng(seed)
+    bands = synth.random_periodic_bands(N, rng)
+    B = rng.uniform(-1, 1, (N, M))
+    G = rng.uniform(-1, 1, (N, M))
+    A = periodic_from_bands(bands)
+    X = oracle.periodic_tri_solve_bands(bands, B)
+    GB = oracle.periodic_solve_adjoint(bands, G)
+    db = oracle.band_grad_periodic(GB, X)
+    dA = -np.linalg.solve(A.T, G) @ np.linalg.solve(A, B).T
+    eps = 1e-6
+    for k in range(3):
+        for i in range(N):
+            col = (i + k - 1) % N
+            assert abs(db[k, i] - dA[i, col]) < 1e-12 * (1 + abs(dA[i, col]))
+            Ap, Am = A.copy(), A.copy()
+            Ap[i, col] += eps
+            Am[i, col] -= eps
+            fd = (np.sum(G * np.linalg.solve(Ap, B)) - np.sum(G * np.linalg.solve(Am, B))) / (2 * eps)
+            assert abs(db[k, i] - fd) < 1e-7 * (1 + abs(fd)), (k, i)
+
+
 def pin_adi(ny, nx, r, seed=10):
     """ADI half-steps against the dense Kronecker operators:
     axis 0: (I - r Dxx) out = (I + r Dyy) u; axis 1: (I - r Dyy) out = (I + r Dxx) u."""
@@ -229,6 +281,12 @@ def all_pins():
         ("penta_factor_identity_min", lambda: pin_penta_factor_identity(4)),
         ("periodic_sym", lambda: pin_periodic(32, -0.4, 1.8, -0.4)),
         ("periodic_nonsym", lambda: pin_periodic(17, 0.3, 2.0, -0.6)),
+        ("periodic_bands", lambda: pin_periodic_bands(23)),
+        ("periodic_bands_min", lambda: pin_periodic_bands(3, 14)),
+        ("periodic_adjoint_il", lambda: pin_periodic_adjoint(19, "interleaved")),
+        ("periodic_adjoint_st", lambda: pin_periodic_adjoint(3, "strided", 17)),
+        ("periodic_band_grad", lambda: pin_periodic_band_grad()),
+        ("periodic_band_grad_min", lambda: pin_periodic_band_grad(3, 2, 18)),
         ("adi_rect", lambda: pin_adi(5, 7, 0.5)),
     ]
     return out

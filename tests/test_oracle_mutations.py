@@ -30,8 +30,12 @@ MUTATIONS = [
     ("band_grad_sign", "dbands[(int64_t)k * N + i] = -s;", "dbands[(int64_t)k * N + i] = s;", 0),
     ("band_grad_index", "s += EL(GB, i, j) * EL(X, col, j);", "s += EL(GB, i, j) * EL(X, i, j);", 0),
     ("residual_sign", "EL(R, i, j) = EL(B, i, j) - s;", "EL(R, i, j) = EL(B, i, j) + s;", 0),
-    ("periodic_corner", "bands[N + N - 1] = b + a * c / b;", "bands[N + N - 1] = b;", 0),
-    ("periodic_vz_sign", "double vz = z[0] - (a / b) * z[N - 1];", "double vz = z[0] + (a / b) * z[N - 1];", 0),
+    ("periodic_corner", "bands[N + N - 1] = b[N - 1] - c[N - 1] * a[0] / g;", "bands[N + N - 1] = b[N - 1];", 0),
+    ("periodic_vz_sign", "const double vz = z[0] + (a[0] / g) * z[N - 1];",
+     "const double vz = z[0] - (a[0] / g) * z[N - 1];", 0),
+    ("periodic_u_corner", "z[N - 1] = c[N - 1];", "z[N - 1] = a[0];", 0),
+    ("periodic_grad_col", "int64_t col = (i + k - 1 + N) % N;", "int64_t col = (i + k + N) % N;", 0),
+    ("periodic_grad_sign", "dbands[(int64_t)k * N + i] = -s;\n    }\n}\n\n/* -----", "dbands[(int64_t)k * N + i] = s;\n    }\n}\n\n/* -----", 0),
     ("adi_explicit_sign", "out[y * nx + x] = c0 + r * (lo - 2.0 * c0 + hi);",
      "out[y * nx + x] = c0 - r * (lo - 2.0 * c0 + hi);", 0),
     ("adi_lhs_diag", "bands[n_row + i] = 1.0 + 2.0 * r;", "bands[n_row + i] = 1.0 + r;", 0),
