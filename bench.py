@@ -489,7 +489,7 @@ def run_other_configs(bs, st, hbm):
     samples["spline"] = (bands, B64[:, cols].cpu().numpy(), X64[:, cols].cpu().numpy(), XR[:, cols].cpu().numpy())
     # the same right-hand sides with the periodic spline matrix (cyclic
     # [1,4,1]/6, Sherman-Morrison fused into the sweeps), FP64 and FP32
-    pbands = synth.toeplitz_bands(N, (1 / 6, 4 / 6, 1 / 6))
+    pbands = synth.periodic_toeplitz_bands(N, (1 / 6, 4 / 6, 1 / 6))
     fp = bs.Factor(pbands, periodic=True)
     XP = B64.clone()
     tp = time_alone(lambda: bs.solve(fp, XP), st, reps=10)

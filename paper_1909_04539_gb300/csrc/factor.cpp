@@ -67,6 +67,7 @@ namespace {
 struct HostPlan {
   int bw = 1;
   bool fwd_scale = false, bwd_scale = false, periodic = false;
+  int per_lo = 0, per_hi = 0;
   std::vector<double> c;
 };
 
@@ -261,6 +262,8 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
     sp.fwd_scale = hp[p].fwd_scale;
     sp.bwd_scale = hp[p].bwd_scale;
     sp.periodic = hp[p].periodic;
+    sp.per_lo = hp[p].per_lo;
+    sp.per_hi = hp[p].per_hi;
     std::vector<float> c32(hp[p].c.size());
     for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp[p].c[q];
     e = cudaMalloc(&sp.c64, sizeof(double) * hp[p].c.size());
@@ -430,6 +433,30 @@ bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out) {
   // of zero no digit of the correction can be trusted either.
   if (bad(den) || std::fabs(den) <= 4.0 * (double)N * 2.220446049250313e-16 * (1.0 + std::fabs(vz)))
     return set_error(BS_ESINGULAR, "bs_factor_periodic: 1 + v.z is zero to rounding (the periodic matrix is singular)");
+  // For a diagonally dominant A', q and z decay geometrically away from the
+  // first and last rows.  Entries below 2^-60 max / N change sigma, or any
+  // x_i, by less than 2^-60 of max|q| max|d| (resp. max|z|), far below FP64
+  // rounding; they are set to zero, and the middle range of rows where both
+  // are zero is recorded so that the kernels skip its correction terms.
+  double qmax = 0.0, zmax = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    qmax = std::fmax(qmax, std::fabs(q[i]));
+    zmax = std::fmax(zmax, std::fabs(z[i]));
+  }
+  const double tq = qmax * 0x1p-60 / (double)N, tz = zmax * 0x1p-60 / (double)N;
+  int64_t lo = 0, hi = N;
+  for (int64_t i = 0; i < N; i++) {
+    const bool active = std::fabs(q[i]) > tq || std::fabs(z[i]) > tz;
+    if (!active) {
+      q[i] = 0.0;
+      z[i] = 0.0;
+    }
+  }
+  for (int64_t i = 0; i < N / 2; i++)
+    if (q[i] != 0.0 || z[i] != 0.0) lo = i + 1;
+  for (int64_t i = N - 1; i >= N / 2; i--)
+    if (q[i] != 0.0 || z[i] != 0.0) hi = i;
+  if (lo > hi) lo = hi;
   // primal: sigma = q.d (= v.y), x = y - sigma z / den;
   // adjoint of A = A' + u v^T: sigma = z.g (= u.(A'^{-T} g)), x = y - sigma q / den
   for (int64_t i = 0; i < N; i++) {
@@ -439,6 +466,8 @@ bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out) {
     hp[1].c[(size_t)C_PC * N + i] = q[i] / den;
   }
   hp[0].periodic = hp[1].periodic = true;
+  hp[0].per_lo = hp[1].per_lo = (int)lo;
+  hp[0].per_hi = hp[1].per_hi = (int)hi;
   hp[2] = hp[0];  // no reversed elimination for the periodic case (never read)
   hp[2].periodic = true;
 

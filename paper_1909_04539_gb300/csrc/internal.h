@@ -38,6 +38,8 @@ struct Coefs {
   const C* u2;
   const C* pw;  // periodic plans only
   const C* pc;
+  int per_lo;   // rows per_lo <= i < per_hi have pw_i == pc_i == 0, so a
+  int per_hi;   // block of rows inside that range skips the correction
 };
 
 struct SweepPlan {
@@ -45,6 +47,7 @@ struct SweepPlan {
   bool fwd_scale;  // s present
   bool bwd_scale;  // t present
   bool periodic;   // pw / pc present (Sherman-Morrison correction)
+  int per_lo, per_hi;  // rows without correction terms (see Coefs)
   double* c64;     // device, C_COUNT * N
   float* c32;      // device, C_COUNT * N
 };
@@ -52,7 +55,7 @@ struct SweepPlan {
 template <typename C>
 BS_HD inline Coefs<C> coefs_of(const C* base, int64_t N) {
   return Coefs<C>{base + C_S * N,  base + C_L1 * N, base + C_L2 * N, base + C_T * N,
-                  base + C_U1 * N, base + C_U2 * N, base + C_PW * N, base + C_PC * N};
+                  base + C_U1 * N, base + C_U2 * N, base + C_PW * N, base + C_PC * N, 0, 0};
 }
 
 }  // namespace bs

@@ -137,7 +137,8 @@ __host__ __device__ constexpr int coef_arrays() {
 // Periodic correction terms (Sherman-Morrison, Sec. 3.3) of one block of U
 // rows: before the forward block, sig += pw_i f_i over the raw inputs; after
 // the backward block, f_i -= sig pc_i (the recurrence state keeps the
-// uncorrected values).
+// uncorrected values).  Callers skip blocks that lie entirely inside
+// [per_lo, per_hi), where both arrays are zero.
 template <typename C, int V, int U>
 __device__ __forceinline__ void per_dot(const Coefs<C>& cf, int i0, int n, const C (&f)[U][V], C (&sig)[V]) {
   C pw[U];
@@ -328,7 +329,8 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     };
     auto run_fwd = [&](C (&blk)[U][V], int i0) {
       const int n = (N - i0) < U ? (N - i0) : U;
-      if constexpr (PER) per_dot<C, V, U>(cf, i0, n, blk, sig);
+      if constexpr (PER)
+        if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, blk, sig);
       fwd_block<BW, ADJ, C, V, U>(cf, i0, n, blk, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
@@ -342,7 +344,8 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
     auto run_bwd = [&](C (&blk)[U][V], int top) {
       const int n = (top + 1) < U ? (top + 1) : U;
       bwd_block<BW, ADJ, C, V, U>(cf, top, n, blk, r1, r2);
-      if constexpr (PER) per_fix<C, V, U>(cf, top, n, blk, sig);
+      if constexpr (PER)
+        if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, blk, sig);
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::store(pout + (int64_t)(top - u) * M, blk[u]);
@@ -419,7 +422,8 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
-      if constexpr (PER) per_dot<C, V, U>(cf, i0, n, f, sig);
+      if constexpr (PER)
+        if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
       fwd_block<BW, ADJ, C, V, U>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++) {
@@ -453,7 +457,8 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
       bwd_block<BW, ADJ, C, V, U>(cf, top, n, f, r1, r2);
-      if constexpr (PER) per_fix<C, V, U>(cf, top, n, f, sig);
+      if constexpr (PER)
+        if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, f, sig);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int i = top - u;
@@ -508,7 +513,8 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (mine)
         for (int r = 0; r < rows; r++) {
           C f[1] = {tile[r * kStPad + lane]};
-          if constexpr (PER) sig[0] = fma(cf.pw[c0 + r], f[0], sig[0]);
+          if constexpr (PER)
+            if (c0 + r < cf.per_lo || c0 + r >= cf.per_hi) sig[0] = fma(cf.pw[c0 + r], f[0], sig[0]);
           fwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
           tile[r * kStPad + lane] = f[0];
         }
@@ -536,7 +542,8 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
         for (int r = rows - 1; r >= 0; r--) {
           C f[1] = {tile[r * kStPad + lane]};
           bwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
-          if constexpr (PER) f[0] = fma(-sig[0], cf.pc[c0 + r], f[0]);
+          if constexpr (PER)
+            if (c0 + r < cf.per_lo || c0 + r >= cf.per_hi) f[0] = fma(-sig[0], cf.pc[c0 + r], f[0]);
           tile[r * kStPad + lane] = f[0];
         }
       __syncwarp();
@@ -633,7 +640,9 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
     base = reinterpret_cast<const C*>(p.c64);
   else
     base = reinterpret_cast<const C*>(p.c32);
-  const Coefs<C> cf = coefs_of<C>(base, N);
+  Coefs<C> cf = coefs_of<C>(base, N);
+  cf.per_lo = p.per_lo;
+  cf.per_hi = p.per_hi;
   const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
                    (reinterpret_cast<uintptr_t>(out) % (VEC * sizeof(Sout)) == 0);
   // FP32 with few systems per SM: half-width vectors (8-byte lane rows) give

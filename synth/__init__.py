@@ -91,6 +91,13 @@ def toeplitz_bands(N: int, diagonals) -> np.ndarray:
     return out
 
 
+def periodic_toeplitz_bands(N: int, diagonals) -> np.ndarray:
+    """Constant cyclic tridiagonal bands (a, b, c) on every row, a_1 and c_N
+    included (they are the corner entries of the periodic matrix)."""
+    a, b, c = diagonals
+    return np.stack([np.full(N, float(a)), np.full(N, float(b)), np.full(N, float(c))])
+
+
 def clamped_hyperdiffusion_bands(N: int = 512, s: float = 0.1, clamped: bool = True) -> np.ndarray:
     """A = I + s D4, D4 the [1, -4, 6, -4, 1] stencil.  With ``clamped`` the
     first and last two rows are identity rows (Dirichlet-clamped values);

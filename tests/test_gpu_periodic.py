@@ -81,7 +81,7 @@ def test_paper_constant_case(bs, N, M):
     rng = np.random.default_rng(N + M)
     for a, b, c in ((-0.5, 2.0, -0.5), (0.3, 2.0, -0.6)):
         Bh = rng.uniform(-1, 1, (N, M))
-        f = bs.Factor(synth.toeplitz_bands(N, (a, b, c)), periodic=True)
+        f = bs.Factor(synth.periodic_toeplitz_bands(N, (a, b, c)), periodic=True)
         B = torch.tensor(Bh, device="cuda")
         bs.solve(f, B)
         assert rel_l2(B.cpu().numpy(), oracle.periodic_tri_solve(a, b, c, Bh)) < TOL64
@@ -166,6 +166,23 @@ def test_periodic_factor_errors(bs):
     with pytest.raises(RuntimeError, match="N must be"):
         bs.Factor(bands[:, :2], periodic=True)
     # a singular cyclic matrix: every row sums to zero (a + b + c = 0)
-    sing = synth.toeplitz_bands(8, (-1.0, 2.0, -1.0))
+    sing = synth.periodic_toeplitz_bands(8, (-1.0, 2.0, -1.0))
     with pytest.raises(RuntimeError, match="singular|pivot"):
         bs.Factor(sing, periodic=True)
+
+
+@pytest.mark.parametrize("b", [2.05, 2.6])
+def test_periodic_weak_dominance(bs, b):
+    """Cyclic (-1, b, -1) with N = 4096: the correction vectors decay slowly
+    (ratio ~0.8 for b = 2.05), so hundreds of rows at each end carry
+    correction terms and the rest skip them; FP64 parity with the oracle."""
+    N, M = 4096, 130
+    rng = np.random.default_rng(int(b * 100))
+    Bh = rng.uniform(-1, 1, (N, M))
+    f = bs.Factor(synth.periodic_toeplitz_bands(N, (-1.0, b, -1.0)), periodic=True)
+    for layout in ("interleaved", "strided"):
+        B_in = Bh if layout == "interleaved" else np.ascontiguousarray(Bh.T)
+        B = torch.tensor(B_in, device="cuda")
+        bs.solve(f, B, layout)
+        ref = oracle.periodic_tri_solve(-1.0, b, -1.0, B_in, layout)
+        assert rel_l2(B.cpu().numpy(), ref) < TOL64, layout
