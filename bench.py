@@ -53,6 +53,7 @@ NCU_TRAFFIC = {
     "band_grad_f64": {"bytes": 537621248 + 3447296, "sha": "beac1e924fa6a1d3"},
     # likewise (the accuracy-check launch, same kernel and batch)
     "f64_solve": {"bytes": 472660224 + 432845056, "sha": "b63f557d662de20f"},
+    "refine_solve": {"bytes": 356136704 + 439495168, "sha": "50e6f54d16641a56"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],

@@ -162,14 +162,15 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  * handed all device memory to its own pool allocator, or a latency-bound loop
  * where an allocation could block on the driver.  This entry point computes
  * exactly what bs_band_grad computes (same kernels, same fixed reduction
- * order, bitwise the same result) but keeps its per-chunk partial sums in a
- * fixed device array inside the library (2 MiB, held on every GPU that loads
- * the library until the process exits) and allocates nothing.  The caller
- * still provides GB, X and dbands as for bs_band_grad.
- * Limit: the partial sums need (system chunks) x width x N doubles and the
- * array holds 262144 of them (about 20480 are needed up to N = 4096, then
- * width x N): N above 52428 (width 5) or 87381 (width 3) is rejected with
- * BS_EINVAL and a message naming the size -- use bs_band_grad there.
+ * order, bitwise the same result) but keeps its partial sums in a fixed
+ * device array inside the library (2 MiB, held on every GPU that loads the
+ * library until the process exits) and allocates nothing.  The caller still
+ * provides GB, X and dbands as for bs_band_grad.
+ * Limit: the partial sums need about (N / 8 + 2 G) x 8 x width doubles
+ * (G = the reduction's CTA count, SMs x resident CTAs per SM: 152 on GB300)
+ * and the array holds 262144 of them: on GB300 N above about 50000 (width 5)
+ * or 84000 (width 3) is rejected with BS_EINVAL and a message naming the
+ * size -- use bs_band_grad there.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls
  * share the one array and it keeps the last call's contents (every partial is
@@ -204,8 +205,9 @@ bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_dtype dtype,
  *   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - width/2, j]
  * (0 for entries outside the matrix; for a bs_factor_periodic handle the
  * column index is taken modulo N and every entry is defined, the corners
- * being dbands[0] (a_1) and dbands[3N-1] (c_N)), reduced in a fixed order (rows x
- * chunks of systems, then chunks in order), bitwise reproducible.  GB and X:
+ * being dbands[0] (a_1) and dbands[3N-1] (c_N)), reduced in a fixed order
+ * (equal contiguous ranges of (row block, system) per CTA, then the CTAs'
+ * partials in CTA order), bitwise reproducible on a given device.  GB and X:
  * device, same dtype (BS_F64 or BS_F32) and layout; dbands: device
  * double[width*N], overwritten.  Uses stream-ordered scratch as
  * bs_solve_adjoint does. */

@@ -4,124 +4,207 @@
 // dL/dA = -GB X^T; the entries on the bands are
 //   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - h, j],   h = width / 2.
 // Two levels, fixed order, no atomics:
-//   1. a 2D grid of CTAs, each owning kGradRows rows and one chunk of the
-//      systems, accumulates its products in FP64 (threads stride over the
-//      chunk's systems; warp shuffles and a shared-memory tree combine the
-//      threads) and writes one partial per (chunk, band, row) to scratch;
-//   2. one thread per (band, row) adds the chunks' partials in chunk order.
-// The grid shape is a function of N and M only, so the result is bitwise
-// reproducible.  Work per unknown: `width` FP64 FMAs (the kernel is bound by
-// the FP64 pipe on GB300), 16 bytes of compulsory reads (GB and X; the X
-// halo of 2h rows per block of kGradRows comes mostly from L2).
+//   1. the work space (row blocks of kGradRows rows) x (systems), taken in
+//      row-block-major order, is cut into G equal contiguous ranges, one per
+//      CTA of a grid that fills the device exactly once (G = SMs x resident
+//      CTAs per SM, so no partial last wave).  A CTA walks its range as at
+//      most a few segments (one per row block it touches); for each segment
+//      its threads stride over the systems accumulating in FP64, a warp
+//      reduce-scatter (shuffles) and a shared-memory pass across the warps
+//      combine them, and one partial per (CTA, segment, band, row) goes to
+//      scratch;
+//   2. one thread per (band, row) adds the partials of the CTAs that touched
+//      its row block, in CTA order.
+// The decomposition is a function of N, M and G only, so the result is
+// bitwise reproducible on a given device.  Work per unknown: `width` FP64
+// FMAs (the kernel is bound by the FP64 pipe on GB300), 16 bytes of
+// compulsory reads (GB and X; the X halo of 2h rows per row block comes
+// from L2).
 #include <mutex>
 #include <string>
 
+#include "refine_math.cuh"
 #include "sweep_kernels.cuh"
 
 namespace bs {
 
 constexpr int kGradThreads = 256;
 constexpr int kGradRows = 8;
-constexpr int kGradTargetCtas = 512;
-constexpr int64_t kGradMinChunk = 1024;  // systems per chunk at least
 
 struct GradShape {
-  int row_blocks;
-  int chunks;
-  int64_t chunk;  // systems per chunk (multiple of 2)
+  int R;      // row blocks
+  int G;      // CTAs
+  int S;      // most segments (row blocks) one CTA can touch
+  int64_t M;  // systems
 };
+
+// CTA c owns the positions [range_lo(c), range_lo(c + 1)) of the R*M work
+// space (position p = row block p / M, system p % M).
+__host__ __device__ __forceinline__ int64_t range_lo(int64_t c, int64_t total, int64_t G) { return c * total / G; }
+
+static int grad_ctas_per_sm();
 
 GradShape grad_shape(int N, int64_t M) {
   GradShape g{};
-  g.row_blocks = (N + kGradRows - 1) / kGradRows;
-  int64_t c = (kGradTargetCtas + g.row_blocks - 1) / g.row_blocks;
-  const int64_t cmax = (M + kGradMinChunk - 1) / kGradMinChunk;
-  if (c > cmax) c = cmax;
-  if (c < 1) c = 1;
-  int64_t chunk = (M + c - 1) / c;
-  chunk = (chunk + 1) / 2 * 2;
-  g.chunks = (int)((M + chunk - 1) / chunk);
-  g.chunk = chunk;
+  g.R = (N + kGradRows - 1) / kGradRows;
+  g.M = M;
+  g.G = device_info().sms * grad_ctas_per_sm();
+  const int64_t total = (int64_t)g.R * M;
+  // a range of ceil(total / G) positions touches at most this many row blocks
+  const int64_t per = (total + g.G - 1) / g.G;
+  g.S = (int)((per + M - 1) / M) + 1;
+  if (g.S > g.R) g.S = g.R;
   return g;
 }
 
 size_t band_grad_scratch_bytes(int width, int N, int64_t M) {
   const GradShape g = grad_shape(N, M);
-  return (size_t)g.chunks * width * N * sizeof(double);
+  return (size_t)g.G * g.S * width * kGradRows * sizeof(double);
 }
 
-// Level 1.  blockIdx.x = row block, blockIdx.y = chunk.  partial layout:
-// [chunk][band][row].  PER: periodic matrix, X rows taken modulo N.
+template <typename T>
+__device__ __forceinline__ double load_wide(const T* p) {
+  if constexpr (sizeof(T) == 8)
+    return *p;
+  else
+    return widen_exact(*p);  // integer-only widening: keeps the FP64 pipe for the FMAs
+}
+
+// Level 1.  partial layout: [CTA][segment][band][row in block].
+// PER: periodic matrix, X rows taken modulo N.
 template <typename T, int W, bool PER>
 __global__ void __launch_bounds__(kGradThreads)
-k_band_grad_partial(int N, int64_t M, int64_t chunk, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
+k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
                     int64_t ss, double* __restrict__ partial) {
   constexpr int H = W / 2;
   constexpr int NX = kGradRows + 2 * H;
-  __shared__ double red[kGradThreads / 32][kGradRows * W];
-  const int i0 = blockIdx.x * kGradRows;
-  const int64_t jlo = (int64_t)blockIdx.y * chunk;
-  const int64_t jhi = (jlo + chunk) < M ? (jlo + chunk) : M;
-  double acc[kGradRows][W];
+  constexpr int NV = kGradRows * W;  // accumulators per thread
+  static_assert(NV <= 64, "reduce-scatter holds at most 64 values per lane");
+  __shared__ double red[kGradThreads / 32][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t total = (int64_t)R * M;
+  const int64_t lo = range_lo(blockIdx.x, total, gridDim.x);
+  const int64_t hi = range_lo(blockIdx.x + 1, total, gridDim.x);
+  const int rb0 = (int)(lo / M);
+  for (int64_t p = lo; p < hi;) {
+    const int rb = (int)(p / M);
+    const int64_t seg_end = hi < (int64_t)(rb + 1) * M ? hi : (int64_t)(rb + 1) * M;
+    const int64_t jlo = p - (int64_t)rb * M, jhi = seg_end - (int64_t)rb * M;
+    const int i0 = rb * kGradRows;
+    double acc[NV];
 #pragma unroll
-  for (int r = 0; r < kGradRows; r++)
+    for (int v = 0; v < NV; v++) acc[v] = 0.0;
+    for (int64_t j = jlo + threadIdx.x; j < jhi; j += kGradThreads) {
+      double x[NX], g[kGradRows];
 #pragma unroll
-    for (int k = 0; k < W; k++) acc[r][k] = 0.0;
-
-  for (int64_t j = jlo + threadIdx.x; j < jhi; j += kGradThreads) {
-    double x[NX], g[kGradRows];
+      for (int q = 0; q < NX; q++) {
+        const int row = i0 - H + q;
+        if constexpr (PER) {
+          const int pr = ((row % N) + N) % N;
+          x[q] = load_wide(X + pr * rs + j * ss);
+        } else {
+          x[q] = (row >= 0 && row < N) ? load_wide(X + row * rs + j * ss) : 0.0;
+        }
+      }
 #pragma unroll
-    for (int q = 0; q < NX; q++) {
-      const int row = i0 - H + q;
-      if constexpr (PER) {
-        const int pr = ((row % N) + N) % N;
-        x[q] = (double)X[pr * rs + j * ss];
-      } else {
-        x[q] = (row >= 0 && row < N) ? (double)X[row * rs + j * ss] : 0.0;
+      for (int r = 0; r < kGradRows; r++) {
+        const int row = i0 + r;
+        g[r] = (row < N) ? load_wide(GB + row * rs + j * ss) : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < kGradRows; r++)
+#pragma unroll
+        for (int k = 0; k < W; k++) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
+    }
+    // Warp reduce-scatter over the NV values (padded to 64): at each level a
+    // lane keeps one half, sends the other to its partner and adds what it
+    // receives, so that lane l ends with the warp sums of values 2l, 2l + 1.
+    double w32[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+      const double a = (i < NV) ? acc[i < NV ? i : 0] : 0.0;
+      const double b = (i + 32 < NV) ? acc[i + 32 < NV ? i + 32 : 0] : 0.0;
+      const bool up = lane & 16;
+      const double keep = up ? b : a, send = up ? a : b;
+      w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int o = 8, n = 16; o >= 1; o >>= 1, n >>= 1) {
+#pragma unroll
+      for (int i = 0; i < n; i++) {
+        const bool up = lane & o;
+        const double keep = up ? w32[i + n] : w32[i], send = up ? w32[i] : w32[i + n];
+        w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
     }
+    red[warp][2 * lane] = w32[0];
+    red[warp][2 * lane + 1] = w32[1];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double t = 0.0;
 #pragma unroll
-    for (int r = 0; r < kGradRows; r++) {
-      const int row = i0 + r;
-      g[r] = (row < N) ? (double)GB[row * rs + j * ss] : 0.0;
+      for (int w = 0; w < kGradThreads / 32; w++) t += red[w][threadIdx.x];
+      partial[((int64_t)blockIdx.x * S + (rb - rb0)) * NV + threadIdx.x] = t;
     }
-#pragma unroll
-    for (int r = 0; r < kGradRows; r++)
-#pragma unroll
-      for (int k = 0; k < W; k++) acc[r][k] = fma(g[r], x[r + k], acc[r][k]);
-  }
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int r = 0; r < kGradRows; r++)
-#pragma unroll
-    for (int k = 0; k < W; k++) {
-      double v = acc[r][k];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) red[warp][r * W + k] = v;
-    }
-  __syncthreads();
-  if (threadIdx.x < kGradRows * W) {
-    const int r = threadIdx.x / W, k = threadIdx.x % W;
-    double s = 0.0;
-    for (int w = 0; w < kGradThreads / 32; w++) s += red[w][threadIdx.x];
-    const int row = i0 + r;
-    if (row < N) partial[((int64_t)blockIdx.y * W + k) * N + row] = s;
+    __syncthreads();
+    p = seg_end;
   }
 }
 
-// Level 2: dbands[k*N + i] = -(sum over chunks, in order); 0 outside the
-// matrix (a periodic matrix has no entries outside).
-__global__ void k_band_grad_finish(int W, int N, int chunks, int periodic, const double* __restrict__ partial,
-                                   double* __restrict__ dbands) {
+// Level 2: dbands[k*N + i] = -(sum over the CTAs that touched row block
+// i / kGradRows, in CTA order); 0 outside the matrix (a periodic matrix has no
+// entries outside).
+__global__ void k_band_grad_finish(int W, int N, int64_t M, int R, int G, int S, int periodic,
+                                   const double* __restrict__ partial, double* __restrict__ dbands) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)W * N) return;
   const int k = (int)(t / N), i = (int)(t % N);
+  const int rb = i / kGradRows, r = i % kGradRows;
   const int col = i + k - W / 2;
+  const int64_t total = (int64_t)R * M;
+  const int64_t b_lo = (int64_t)rb * M, b_hi = b_lo + M;
+  // first CTA whose range can reach row block rb
+  int64_t c = b_lo * G / total - 1;
+  if (c < 0) c = 0;
   double s = 0.0;
-  for (int c = 0; c < chunks; c++) s += partial[(int64_t)c * W * N + t];
+  for (; c < G; c++) {
+    const int64_t lo = range_lo(c, total, G), hi = range_lo(c + 1, total, G);
+    if (lo >= b_hi) break;
+    if (hi <= b_lo || lo == hi) continue;
+    const int seg = rb - (int)(lo / M);
+    s += partial[((c * S) + seg) * (int64_t)(W * kGradRows) + k * kGradRows + r];
+  }
   dbands[t] = (periodic || (col >= 0 && col < N)) ? -s : 0.0;
+}
+
+template <typename T, int W, bool PER>
+static int ctas_per_sm_of() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_band_grad_partial<T, W, PER>, kGradThreads, 0) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
+  return n;
+}
+
+// Resident CTAs per SM of the partial kernel (the smallest over its
+// instantiations, so that every variant uses the same decomposition).
+static int grad_ctas_per_sm() {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cached[dev]) {
+    int n = ctas_per_sm_of<double, 5, false>();
+    const int m[] = {ctas_per_sm_of<double, 3, false>(), ctas_per_sm_of<double, 3, true>(),
+                     ctas_per_sm_of<float, 5, false>(), ctas_per_sm_of<float, 3, false>(),
+                     ctas_per_sm_of<float, 3, true>()};
+    for (int v : m) n = v < n ? v : n;
+    cached[dev] = n;
+  }
+  return cached[dev];
 }
 
 // Both levels with caller-provided scratch of band_grad_scratch_bytes().
@@ -130,33 +213,30 @@ cudaError_t band_grad_with_scratch(int width, int N, bool periodic, const void* 
   const int64_t rs = layout == BS_INTERLEAVED ? M : 1;
   const int64_t ss = layout == BS_INTERLEAVED ? 1 : N;
   const GradShape g = grad_shape(N, M);
-  const dim3 grid(g.row_blocks, g.chunks);
+#define BS_GRAD(TT, WW, PP)                                                                         \
+  k_band_grad_partial<TT, WW, PP><<<g.G, kGradThreads, 0, st>>>(N, M, g.R, g.S, (const TT*)GB, (const TT*)X, \
+                                                                rs, ss, scratch)
   if (periodic) {  // width 3 only
     if (t == BS_F64)
-      k_band_grad_partial<double, 3, true><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
-                                                                           (const double*)X, rs, ss, scratch);
+      BS_GRAD(double, 3, true);
     else
-      k_band_grad_partial<float, 3, true><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
-                                                                          (const float*)X, rs, ss, scratch);
+      BS_GRAD(float, 3, true);
   } else if (t == BS_F64) {
     if (width == 3)
-      k_band_grad_partial<double, 3, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
-                                                                     (const double*)X, rs, ss, scratch);
+      BS_GRAD(double, 3, false);
     else
-      k_band_grad_partial<double, 5, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const double*)GB,
-                                                                     (const double*)X, rs, ss, scratch);
+      BS_GRAD(double, 5, false);
   } else {
     if (width == 3)
-      k_band_grad_partial<float, 3, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
-                                                                    (const float*)X, rs, ss, scratch);
+      BS_GRAD(float, 3, false);
     else
-      k_band_grad_partial<float, 5, false><<<grid, kGradThreads, 0, st>>>(N, M, g.chunk, (const float*)GB,
-                                                                    (const float*)X, rs, ss, scratch);
+      BS_GRAD(float, 5, false);
   }
+#undef BS_GRAD
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)width * N;
-  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, g.chunks, periodic ? 1 : 0, scratch,
+  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, M, g.R, g.G, g.S, periodic ? 1 : 0, scratch,
                                                              dbands);
   return cudaGetLastError();
 }
