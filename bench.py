@@ -50,9 +50,10 @@ NOMINAL_HBM_GBS = 8000.0
 # kernel sources hash to the value they had at capture time.
 NCU_TRAFFIC = {
     # one --set full capture of the kernel inside this benchmark's step
-    "band_grad_f64": {"bytes": 537621248 + 3447296, "sha": "beac1e924fa6a1d3"},
+    "band_grad_f64": {"bytes": 669353728 + 3254784, "sha": "c7b197ac3fc4ac2c"},
     # likewise (the accuracy-check launch, same kernel and batch)
-    "f64_solve": {"bytes": 472660224 + 432845056, "sha": "b63f557d662de20f"},
+    "f64_solve": {"bytes": 472688128 + 432523264, "sha": "5fc8ddccf0627042"},
+    "adjoint_f64": {"bytes": 459128576 + 426641664, "sha": "5fc8ddccf0627042"},
     "refine_solve": {"bytes": 356136704 + 439495168, "sha": "50e6f54d16641a56"},
 }
 KERNEL_SOURCES = {
