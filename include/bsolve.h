@@ -287,13 +287,27 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    SM at N = 512, too few to hide latency; it is slower on the workloads
  *    measured so far and kept as an option.
  *  BS_OPT_TMA_AHEAD: row chunks (32 rows each) the on-chip kernel keeps in
- *    flight ahead of its forward sweep (default 0: 4). */
+ *    flight ahead of its forward sweep (default 0: 4).
+ *  BS_OPT_PARTITION: row-partitioned solves of a tridiagonal handle (not in
+ *    the paper; for batches too small to fill the GPU one thread per
+ *    system).  bs_factor prepares, for width 3 and N >= 256 when the matrix's
+ *    spikes decay within a quarter of a block, a split of the rows into P
+ *    blocks (P <= 32, blocks of >= 192 rows) for A and for A^T.  A solve then
+ *    runs one thread per (system, block) on the matrix without the couplings
+ *    across block edges, solves a pentadiagonal system of 2 (P - 1) block-edge
+ *    values per system (factorised once with the handle), and corrects the
+ *    rows near the block edges; the result is the same as the unpartitioned
+ *    solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
+ *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 128
+ *    vector groups of systems per SM; 1: never; 2: whenever the handle has
+ *    one. */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
   BS_OPT_SWEEP_KERNEL = 2,
   BS_OPT_TMA_AHEAD = 3,
-  BS_OPT_COUNT = 4
+  BS_OPT_PARTITION = 4,
+  BS_OPT_COUNT = 5
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

@@ -20,6 +20,8 @@ _LAYOUT = {"interleaved": 0, "strided": 1}
 OPT_INFLIGHT_BYTES = 0
 OPT_BLOCKS_PER_SM = 1
 OPT_SWEEP_KERNEL = 2
+OPT_TMA_AHEAD = 3
+OPT_PARTITION = 4
 
 
 def device_status(reset: bool = False) -> int:

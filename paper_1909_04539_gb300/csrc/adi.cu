@@ -24,74 +24,7 @@ namespace bs {
 
 // ----------------------------------------------------- implicit along y
 
-template <int BW, bool ADJ, bool SMEM, typename C>
-__global__ void __launch_bounds__(kSweepThreads)
-k_adi_il(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  constexpr int U = 8;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const C* pu = u + j;
-    C* po = out + j;
-    const bool has_l = j > 0, has_r = j + 1 < M;
-    C r1[1] = {C(0)}, r2[1] = {C(0)};
-    // explicit operator on load: rows i0 .. i0+U-1 of this column and its two
-    // neighbours; a block of loads is issued before the previous block is swept
-    auto load_rhs = [&](C (&f)[U][1], int i0) {
-      C c[U], l[U], rr[U];
-#pragma unroll
-      for (int q = 0; q < U; q++) {
-        const int i = i0 + q < N ? i0 + q : N - 1;
-        const int64_t o = (int64_t)i * M;
-        c[q] = pu[o];
-        l[q] = has_l ? pu[o - 1] : C(0);
-        rr[q] = has_r ? pu[o + 1] : C(0);
-      }
-#pragma unroll
-      for (int q = 0; q < U; q++) f[q][0] = c[q] + r * (l[q] - C(2) * c[q] + rr[q]);
-    };
-    C fa[U][1], fb[U][1];
-    load_rhs(fa, 0);
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += U) {
-      const bool more = i0 + U < N;
-      if (more) load_rhs(fb, i0 + U);
-      const int n = (N - i0) < U ? (N - i0) : U;
-      fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, fa, r1, r2);
-#pragma unroll
-      for (int q = 0; q < U; q++)
-        if (q < n) po[(int64_t)(i0 + q) * M] = fa[q][0];
-      if (more) {
-#pragma unroll
-        for (int q = 0; q < U; q++) fa[q][0] = fb[q][0];
-      }
-    }
-    r1[0] = r2[0] = C(0);
-    // backward: blocks of rows top .. top-U+1, the next block loaded ahead
-    auto load_w = [&](C (&f)[U][1], int top) {
-#pragma unroll
-      for (int q = 0; q < U; q++) f[q][0] = po[(int64_t)(top - q >= 0 ? top - q : 0) * M];
-    };
-    load_w(fa, N - 1);
-#pragma unroll 1
-    for (int top = N - 1; top >= 0; top -= U) {
-      const bool more = top - U >= 0;
-      if (more) load_w(fb, top - U);
-      const int n = (top + 1) < U ? (top + 1) : U;
-      bwd_block<BW, ADJ, C, 1, U>(cf, top, n, fa, r1, r2);
-#pragma unroll
-      for (int q = 0; q < U; q++)
-        if (q < n) po[(int64_t)(top - q) * M] = fa[q][0];
-      if (more) {
-#pragma unroll
-        for (int q = 0; q < U; q++) fa[q][0] = fb[q][0];
-      }
-    }
-  }
-}
-
-// Deep-pipelined variant of the y-implicit half-step: one warp owns 32
+// Y-implicit half-step: one warp owns 32
 // consecutive columns (systems), each lane streams its column's rows through
 // a ring of D slots in shared memory (cp.async), so D rows per lane are in
 // flight -- with 4096 grid lines there is less than one warp per SM, so depth
@@ -102,10 +35,17 @@ k_adi_il(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
 // the same ring for the backward sweep.
 template <int BW, bool ADJ, bool SMEM, typename C, int D>
 __global__ void __launch_bounds__(kSweepThreads)
-k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r, int L) {
   constexpr int U = 4;
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise)
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    u += (int64_t)r0 * M;
+    out += (int64_t)r0 * M;
+  }
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
   const int lane = threadIdx.x & 31;
@@ -211,98 +151,8 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
 // ----------------------------------------------------- implicit along x
 
 constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
-constexpr int kAdiWarpTile = kStRows * kAdiTile + kStRows * kStPad;  // input tile + output tile
 
-template <int BW, bool ADJ, bool SMEM, typename C>
-__global__ void __launch_bounds__(kSweepThreads)
-k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* smc = reinterpret_cast<C*>(smem_raw);
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kWarps = kSweepThreads / 32;
-  constexpr int U = 8;
-  C* tin = smc + (SMEM ? coef_arrays<BW>() * N : 0) + warp * kAdiWarpTile;
-  C* tout = tin + kStRows * kAdiTile;
-  const int64_t nwg = (M + 31) / 32;
-  for (int64_t wg = (int64_t)blockIdx.x * kWarps + warp; wg < nwg; wg += (int64_t)gridDim.x * kWarps) {
-    const int64_t j0 = wg * 32;
-    const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
-    const bool mine = lane < nsys;
-    C r1[1] = {C(0)}, r2[1] = {C(0)};
-    // Lane `lane` holds row c0 + lane of systems j0-1 .. j0+32 of a chunk in
-    // registers; the next chunk's row is loaded while this one is swept.
-    C pre[34];
-    auto load_chunk = [&](int c0) {
-      const bool ok = c0 + lane < N;
-#pragma unroll
-      for (int s = 0; s < 34; s++) {
-        const int64_t jj = j0 + s - 1;
-        pre[s] = (ok && jj >= 0 && jj < M && s - 1 < nsys + 1) ? u[jj * (int64_t)N + c0 + lane] : C(0);
-      }
-    };
-    load_chunk(0);
-    for (int c0 = 0; c0 < N; c0 += kStRows) {
-      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
-#pragma unroll
-      for (int s = 0; s < 34; s++) tin[lane * kAdiTile + s] = pre[s];
-      __syncwarp();
-      if (c0 + kStRows < N) load_chunk(c0 + kStRows);
-      if (mine)
-        for (int q0 = 0; q0 < rows; q0 += U) {
-          const int n = (rows - q0) < U ? (rows - q0) : U;
-          C f[U][1];
-#pragma unroll
-          for (int q = 0; q < U; q++) {
-            const C* t = tin + (q0 + q) * kAdiTile + lane;
-            f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
-          }
-          fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
-#pragma unroll
-          for (int q = 0; q < U; q++)
-            if (q < n) tout[(q0 + q) * kStPad + lane] = f[q][0];
-        }
-      __syncwarp();
-      if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
-      __syncwarp();
-    }
-    // backward sweep, chunks in decreasing order, the next chunk loaded ahead
-    r1[0] = r2[0] = C(0);
-    const int last = ((N - 1) / kStRows) * kStRows;
-    C pw[32];
-    auto load_back = [&](int c0) {
-      const bool ok = c0 + lane < N;
-#pragma unroll
-      for (int s = 0; s < 32; s++) pw[s] = (ok && s < nsys) ? out[(j0 + s) * (int64_t)N + c0 + lane] : C(0);
-    };
-    load_back(last);
-    for (int c0 = last; c0 >= 0; c0 -= kStRows) {
-      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
-#pragma unroll
-      for (int s = 0; s < 32; s++) tout[lane * kStPad + s] = pw[s];
-      __syncwarp();
-      if (c0 - kStRows >= 0) load_back(c0 - kStRows);
-      if (mine)
-        for (int top = rows - 1; top >= 0; top -= U) {
-          const int n = (top + 1) < U ? (top + 1) : U;
-          C f[U][1];
-#pragma unroll
-          for (int q = 0; q < U; q++) f[q][0] = tout[(q < n ? top - q : top) * kStPad + lane];
-          bwd_block<BW, ADJ, C, 1, U>(cf, c0 + top, n, f, r1, r2);
-#pragma unroll
-          for (int q = 0; q < U; q++)
-            if (q < n) tout[(top - q) * kStPad + lane] = f[q][0];
-        }
-      __syncwarp();
-      if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
-      __syncwarp();
-    }
-  }
-}
-
-// Deep-pipelined x-implicit half-step: one-warp CTAs, each owning 32 rows of
+// X-implicit half-step: one-warp CTAs, each owning 32 rows of
 // the grid (systems).  Chunks of 32 grid columns (rows of the systems) move
 // through a ring of K tiles in shared memory by cp.async -- each lane copies
 // its row of the chunk for the 34 systems it touches (its 32 plus one
@@ -311,10 +161,17 @@ k_adi_st(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int
 // back through the same ring for the backward sweep.
 template <int BW, bool ADJ, bool SMEM, typename C, int K>
 __global__ void __launch_bounds__(32)
-k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r) {
+k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r, int64_t ld, int L) {
   constexpr int U = 8;
   constexpr int kTile = kStRows * kAdiTile;  // one ring tile (input layout)
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise); ld = system stride
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    u += r0;
+    out += r0;
+  }
   C* smc = reinterpret_cast<C*>(smem_raw);
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
   const int lane = threadIdx.x;
@@ -339,7 +196,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       if (row < N)
         for (int s = -1; s <= nsys; s++) {
           const int64_t jj = j0 + s;
-          if (jj >= 0 && jj < M) cp(t + s + 1, u + jj * (int64_t)N + row);
+          if (jj >= 0 && jj < M) cp(t + s + 1, u + jj * ld + row);
           else t[s + 1] = C(0);
         }
     };
@@ -374,7 +231,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       if (c + K < nch) request_in(c + K);  // the tile just swept is free again
       cp_commit();
       if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tout[lane * kStPad + s];
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tout[lane * kStPad + s];
       __syncwarp();
     }
     cp_wait<0>();
@@ -384,7 +241,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       C* t = ringt + (c % K) * kTile + lane * kStPad;
       const int row = c * kStRows + lane;
       if (row < N)
-        for (int s = 0; s < nsys; s++) cp(t + s, out + (j0 + s) * (int64_t)N + row);
+        for (int s = 0; s < nsys; s++) cp(t + s, out + (j0 + s) * ld + row);
     };
 #pragma unroll 1
     for (int q = 0; q < K; q++) {
@@ -413,7 +270,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         }
       __syncwarp();
       if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * (int64_t)N + c0 + lane] = tw[lane * kStPad + s];
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tw[lane * kStPad + s];
       __syncwarp();
       if (c - K >= 0) request_back(c - K);
       cp_commit();
@@ -424,7 +281,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
 }
 
 template <int BW, bool ADJ, typename C>
-static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int64_t M, C r, int axis,
+static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int64_t M, C r, int axis, int L, int P,
                               cudaStream_t st) {
   const C* base;
   if constexpr (sizeof(C) == 8)
@@ -435,34 +292,52 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   if (axis == 1) {
     constexpr int D = 64;
     const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
+    const LaunchShape sh =
+        sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
     const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
     auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, u, out, M, r);
+    k<<<dim3((sh.grid + P - 1) / P, P), sh.threads, bytes, st>>>(cf, N, u, out, M, r, L);
   } else {
     constexpr int K = 8;
     const size_t tiles = ((size_t)K * kStRows * kAdiTile + (size_t)kStRows * kStPad) * sizeof(C);
     const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(C), 1, 0, tiles, 32);
+    const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32);
     auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K> : k_adi_st2<BW, ADJ, false, C, K>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
-    k<<<sh.grid, 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r);
+    k<<<dim3((sh.grid + P - 1) / P, P), 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
   }
   return cudaGetLastError();
 }
 
+bool use_partition(bs_handle h, int64_t M, int vec);
+bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
+                       cudaStream_t st);
+
 template <typename C>
-static cudaError_t dispatch_adi(bs_handle h, int N, const C* u, C* out, int64_t M, C r, int axis, bool adj,
-                                cudaStream_t st) {
+static bs_status dispatch_adi(bs_handle h, int N, const C* u, C* out, int64_t M, C r, int axis, bool adj,
+                              cudaStream_t st) {
+  cudaError_t e;
+  if (use_partition(h, M, 1)) {
+    // row-partitioned: the primal-form plan of the block-diagonal part of
+    // A (or A^T), then the block-edge correction on `out`
+    const PartPlan& pp = h->part[adj ? 1 : 0];
+    e = launch_adi<1, false, C>(pp.blk, N, u, out, M, r, axis, pp.L, pp.P, st);
+    if (e != cudaSuccess) return cuda_error(e, "bs_adi_halfstep launch");
+    return part_correct(pp, N, out, sizeof(C) == 8 ? BS_F64 : BS_F32, axis == 1 ? BS_INTERLEAVED : BS_STRIDED, M,
+                        st);
+  }
   const SweepPlan& p = h->plan[adj ? 1 : 0];
   if (h->width == 3)
-    return adj ? launch_adi<1, true, C>(p, N, u, out, M, r, axis, st)
-               : launch_adi<1, false, C>(p, N, u, out, M, r, axis, st);
-  return adj ? launch_adi<2, true, C>(p, N, u, out, M, r, axis, st)
-             : launch_adi<2, false, C>(p, N, u, out, M, r, axis, st);
+    e = adj ? launch_adi<1, true, C>(p, N, u, out, M, r, axis, N, 1, st)
+            : launch_adi<1, false, C>(p, N, u, out, M, r, axis, N, 1, st);
+  else
+    e = adj ? launch_adi<2, true, C>(p, N, u, out, M, r, axis, N, 1, st)
+            : launch_adi<2, false, C>(p, N, u, out, M, r, axis, N, 1, st);
+  if (e != cudaSuccess) return cuda_error(e, "bs_adi_halfstep launch");
+  return BS_OK;
 }
 
 }  // namespace bs
@@ -490,11 +365,7 @@ extern "C" bs_status bs_adi_halfstep(bs_handle h, const void* U, void* out, bs_d
   cudaGetDevice(&dev);
   if (dev != h->device) return set_error(BS_EINVAL, "bs_adi_halfstep: handle belongs to another device");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e;
   if (dtype == BS_F64)
-    e = dispatch_adi<double>(h, (int)N, (const double*)U, (double*)out, M, r, implicit_axis, adjoint != 0, st);
-  else
-    e = dispatch_adi<float>(h, (int)N, (const float*)U, (float*)out, M, (float)r, implicit_axis, adjoint != 0, st);
-  if (e != cudaSuccess) return cuda_error(e, "bs_adi_halfstep launch");
-  return BS_OK;
+    return dispatch_adi<double>(h, (int)N, (const double*)U, (double*)out, M, r, implicit_axis, adjoint != 0, st);
+  return dispatch_adi<float>(h, (int)N, (const float*)U, (float*)out, M, (float)r, implicit_axis, adjoint != 0, st);
 }

@@ -7,6 +7,7 @@
 // by pivots are replaced by stored reciprocals so the sweeps contain no
 // divides; every coefficient is a plain FP64 expression of the paper's
 // factors, rounded once more to FP32 for the reduced-precision sweeps.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -217,6 +218,14 @@ void free_handle(bs_handle h) {
   if (h->bands_lo) cudaFree(h->bands_lo);
   if (h->lu_hi) cudaFree(h->lu_hi);
   if (h->lu_lo) cudaFree(h->lu_lo);
+  for (auto& pp : h->part) {
+    for (SweepPlan* sp : {&pp.blk, &pp.red}) {
+      if (sp->c64) cudaFree(sp->c64);
+      if (sp->c32) cudaFree(sp->c32);
+    }
+    if (pp.spk64) cudaFree(pp.spk64);
+    if (pp.spk32) cudaFree(pp.spk32);
+  }
   delete h;
 }
 
@@ -238,10 +247,137 @@ void apply_plan(const HostPlan& p, int64_t N, std::vector<double>& x) {
   }
 }
 
+// Host side of a row partition (see PartPlan) for the tridiagonal matrix with
+// bands a, b, c (outside entries ignored).
+struct HostPart {
+  int P = 0, L = 0, R = 0, kv = 0, kw = 0;
+  HostPlan blk, red;
+  std::vector<double> spk;  // 2N: V then W
+};
+
+// Rows per block at least this many; blocks at most kPartMax.
+constexpr int kPartMinRows = 192;
+constexpr int kPartMax = 32;
+
+bool make_partition(const double* a, const double* b, const double* c, int64_t N, HostPart& hp) {
+  int P = 1;
+  while (P * 2 <= kPartMax && (int64_t)P * 2 * kPartMinRows <= N) P *= 2;
+  if (P < 4) return false;
+  const int64_t L = (N + P - 1) / P;
+  P = (int)((N + L - 1) / L);
+  if (P < 4) return false;
+  auto top = [&](int k) { return (int64_t)k * L; };
+  auto bot = [&](int k) { return std::min<int64_t>(N, (int64_t)(k + 1) * L) - 1; };
+  // block-diagonal matrix: the couplings across block edges removed
+  std::vector<double> mod((size_t)3 * N);
+  for (int64_t i = 0; i < N; i++) {
+    mod[i] = (i > 0) ? a[i] : 0.0;
+    mod[N + i] = b[i];
+    mod[2 * N + i] = (i + 1 < N) ? c[i] : 0.0;
+  }
+  for (int k = 0; k < P; k++) {
+    if (k > 0) mod[top(k)] = 0.0;
+    if (k < P - 1) mod[2 * N + bot(k)] = 0.0;
+  }
+  const double* bd[3] = {mod.data(), mod.data() + N, mod.data() + 2 * N};
+  HostPlan bq;
+  hp.blk.c.assign((size_t)C_COUNT * N, 0.0);
+  bq.c.assign((size_t)C_COUNT * N, 0.0);
+  if (make_plans(bd, 3, N, hp.blk, bq)) return false;
+  // spikes: V = A_blk^{-1} (sum_k a_top(k) e_top(k)), W likewise with c_bot(k)
+  std::vector<double> V(N, 0.0), W(N, 0.0);
+  for (int k = 1; k < P; k++) V[top(k)] = a[top(k)];
+  for (int k = 0; k < P - 1; k++) W[bot(k)] = c[bot(k)];
+  apply_plan(hp.blk, N, V);
+  apply_plan(hp.blk, N, W);
+  double vmax = 0.0, wmax = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    vmax = std::fmax(vmax, std::fabs(V[i]));
+    wmax = std::fmax(wmax, std::fabs(W[i]));
+  }
+  // each x_i gets at most two correction terms: entries below 2^-60 of the
+  // maximum change no result above rounding
+  const double tv = vmax * 0x1p-60, tw = wmax * 0x1p-60;
+  int64_t kv = 0, kw = 0;
+  for (int k = 0; k < P; k++)
+    for (int64_t i = top(k); i <= bot(k); i++) {
+      if (std::fabs(V[i]) <= tv) V[i] = 0.0;
+      if (std::fabs(W[i]) <= tw) W[i] = 0.0;
+      if (V[i] != 0.0) kv = std::max<int64_t>(kv, i - top(k) + 1);
+      if (W[i] != 0.0) kw = std::max<int64_t>(kw, bot(k) - i + 1);
+    }
+  // the correction is meant to touch a small part of each block
+  if (kv + kw > L / 2) return false;
+  // reduced system, unknowns (x_bot(b), x_top(b+1)) for b = 0..P-2,
+  // bands at columns -2..+2 of each row
+  const int R = 2 * (P - 1);
+  std::vector<double> rb((size_t)5 * R, 0.0);
+  for (int q = 0; q < P - 1; q++) {
+    const int r0 = 2 * q, r1 = 2 * q + 1;
+    rb[0 * R + r0] = V[bot(q)];      // x_bot(q-1), column r0 - 2
+    rb[2 * R + r0] = 1.0;
+    rb[3 * R + r0] = W[bot(q)];      // x_top(q+1), column r0 + 1
+    rb[1 * R + r1] = V[top(q + 1)];  // x_bot(q), column r1 - 1
+    rb[2 * R + r1] = 1.0;
+    rb[4 * R + r1] = W[top(q + 1)];  // x_top(q+2), column r1 + 2
+  }
+  const double* rbd[5] = {rb.data(), rb.data() + R, rb.data() + 2 * R, rb.data() + 3 * R, rb.data() + 4 * R};
+  HostPlan rq;
+  hp.red.c.assign((size_t)C_COUNT * R, 0.0);
+  rq.c.assign((size_t)C_COUNT * R, 0.0);
+  if (make_plans(rbd, 5, R, hp.red, rq)) return false;
+  hp.P = P;
+  hp.L = (int)L;
+  hp.R = R;
+  hp.kv = (int)kv;
+  hp.kw = (int)kw;
+  hp.spk.resize((size_t)2 * N);
+  std::copy(V.begin(), V.end(), hp.spk.begin());
+  std::copy(W.begin(), W.end(), hp.spk.begin() + N);
+  return true;
+}
+
+cudaError_t upload_plan(const HostPlan& hp, SweepPlan& sp, size_t& bytes) {
+  sp.bw = hp.bw;
+  sp.fwd_scale = hp.fwd_scale;
+  sp.bwd_scale = hp.bwd_scale;
+  sp.periodic = hp.periodic;
+  sp.per_lo = hp.per_lo;
+  sp.per_hi = hp.per_hi;
+  std::vector<float> c32(hp.c.size());
+  for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp.c[q];
+  cudaError_t e = cudaMalloc(&sp.c64, sizeof(double) * hp.c.size());
+  if (e == cudaSuccess) e = cudaMalloc(&sp.c32, sizeof(float) * c32.size());
+  if (e == cudaSuccess) e = cudaMemcpy(sp.c64, hp.c.data(), sizeof(double) * hp.c.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
+  bytes += (sizeof(double) + sizeof(float)) * hp.c.size();
+  return e;
+}
+
+cudaError_t upload_part(const HostPart& hp, PartPlan& pp, size_t& bytes) {
+  pp.P = hp.P;
+  pp.L = hp.L;
+  pp.R = hp.R;
+  pp.kv = hp.kv;
+  pp.kw = hp.kw;
+  cudaError_t e = upload_plan(hp.blk, pp.blk, bytes);
+  if (e == cudaSuccess) e = upload_plan(hp.red, pp.red, bytes);
+  std::vector<float> s32(hp.spk.size());
+  for (size_t q = 0; q < s32.size(); q++) s32[q] = (float)hp.spk[q];
+  if (e == cudaSuccess) e = cudaMalloc(&pp.spk64, sizeof(double) * hp.spk.size());
+  if (e == cudaSuccess) e = cudaMalloc(&pp.spk32, sizeof(float) * s32.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pp.spk64, hp.spk.data(), sizeof(double) * hp.spk.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pp.spk32, s32.data(), sizeof(float) * s32.size(), cudaMemcpyHostToDevice);
+  bytes += (sizeof(double) + sizeof(float)) * hp.spk.size();
+  return e;
+}
+
 // Copies the host plans, factor entries and bands (b64, width * N) of one
 // LHS to the current device and registers the handle.
 bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool periodic,
-                        const std::vector<double>& entries, const std::vector<double>& b64, bs_handle* out) {
+                        const std::vector<double>& entries, const std::vector<double>& b64, bs_handle* out,
+                        const HostPart* parts = nullptr) {
   std::vector<float> bhi(b64.size()), blo(b64.size());
   for (size_t q = 0; q < b64.size(); q++) {
     const float hi = (float)b64[q];
@@ -256,23 +392,10 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   cudaGetDevice(&hd->device);
   size_t bytes = 0;
   cudaError_t e = cudaSuccess;
-  for (int p = 0; p < 3 && e == cudaSuccess; p++) {
-    SweepPlan& sp = hd->plan[p];
-    sp.bw = hp[p].bw;
-    sp.fwd_scale = hp[p].fwd_scale;
-    sp.bwd_scale = hp[p].bwd_scale;
-    sp.periodic = hp[p].periodic;
-    sp.per_lo = hp[p].per_lo;
-    sp.per_hi = hp[p].per_hi;
-    std::vector<float> c32(hp[p].c.size());
-    for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp[p].c[q];
-    e = cudaMalloc(&sp.c64, sizeof(double) * hp[p].c.size());
-    if (e == cudaSuccess) e = cudaMalloc(&sp.c32, sizeof(float) * c32.size());
-    if (e == cudaSuccess)
-      e = cudaMemcpy(sp.c64, hp[p].c.data(), sizeof(double) * hp[p].c.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(sp.c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice);
-    bytes += (sizeof(double) + sizeof(float)) * hp[p].c.size();
+  for (int p = 0; p < 3 && e == cudaSuccess; p++) e = upload_plan(hp[p], hd->plan[p], bytes);
+  if (parts) {
+    for (int p = 0; p < 2 && e == cudaSuccess; p++) e = upload_part(parts[p], hd->part[p], bytes);
+    hd->has_part = true;
   }
   {
     std::vector<float> ehi(entries.size()), elo(entries.size());
@@ -385,7 +508,18 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
       const int64_t col = i + k - h;
       b64[(size_t)k * N + i] = (col >= 0 && col < N) ? bd[k][i] : 0.0;
     }
-  return upload_handle(width, N, hp, has_ul, false, entries, b64, out);
+  // row partitions of A and of A^T for small batches (tridiagonal only)
+  HostPart parts[2];
+  bool has_part = false;
+  if (width == 3) {
+    std::vector<double> at(N, 0.0), ct(N, 0.0);  // bands of A^T: c_{i-1}, b_i, a_{i+1}
+    for (int64_t i = 0; i < N; i++) {
+      at[i] = (i > 0) ? bd[2][i - 1] : 0.0;
+      ct[i] = (i + 1 < N) ? bd[0][i + 1] : 0.0;
+    }
+    has_part = make_partition(bd[0], bd[1], bd[2], N, parts[0]) && make_partition(at.data(), bd[1], ct.data(), N, parts[1]);
+  }
+  return upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
 }
 
 bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out) {

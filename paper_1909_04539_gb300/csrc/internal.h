@@ -60,6 +60,28 @@ BS_HD inline Coefs<C> coefs_of(const C* base, int64_t N) {
 
 }  // namespace bs
 
+namespace bs {
+// Row-partitioned solve of a tridiagonal matrix for batches too small to fill
+// the GPU one thread per system (e.g. the 4096 lines of an ADI half-step).
+// Rows are cut into P blocks of L rows (the last may be shorter).  With
+// A_blk = A with the couplings between blocks removed, y = A_blk^{-1} d is
+// solved with one thread per (system, block); then
+//   x = y - V x_{top-1} - W x_{bot+1}   inside each block,
+// V = A_k^{-1} (a_top e_1), W = A_k^{-1} (c_bot e_L) the block's spikes (one
+// copy: the LHS is shared).  The values at the block ends follow from a
+// pentadiagonal reduced system of R = 2 (P - 1) unknowns
+// (x_bot of block b, x_top of block b + 1), factorised once, and the
+// correction touches only the first kv and last kw rows of a block (spike
+// entries below 2^-60 of their maximum / N are zero).
+struct PartPlan {
+  int P, L, R, kv, kw;
+  SweepPlan blk;   // block-diagonal plan, C_COUNT x N
+  double* spk64;   // 2 x N: V then W
+  float* spk32;
+  SweepPlan red;   // reduced system, C_COUNT x R (pentadiagonal)
+};
+}  // namespace bs
+
 struct bs_factor_s {
   int width;
   int64_t N;
@@ -79,6 +101,8 @@ struct bs_factor_s {
   float* lu_lo;
   size_t device_bytes;
   bool has_ul;             // plan[2] is valid (reversed elimination met no bad pivot)
+  bool has_part;           // part[] valid (tridiagonal, N large enough, spikes decay)
+  bs::PartPlan part[2];    // [0] for A, [1] for A^T
   bool periodic;           // cyclic tridiagonal (bs_factor_periodic): bands64 holds the
                            // corner entries a_1 (band 0, row 0) and c_N (band 2, row N-1)
 };

@@ -6,9 +6,13 @@
 
 namespace bs {
 
-cudaError_t sweep_f64(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
-cudaError_t sweep_f32(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
-cudaError_t sweep_bf16(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t);
+// L, P: row blocks of a partitioned solve (0, 1: none)
+cudaError_t sweep_f64(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t, int L = 0,
+                      int P = 1);
+cudaError_t sweep_f32(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t, int L = 0,
+                      int P = 1);
+cudaError_t sweep_bf16(const SweepPlan&, bool, int, const void*, void*, bs_layout, int64_t, cudaStream_t, int L = 0,
+                       int P = 1);
 
 static int64_t g_opt[BS_OPT_COUNT] = {0};
 
@@ -53,6 +57,18 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
   return sh;
 }
 
+bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
+                       cudaStream_t st);
+
+// Whether a solve of M systems (vector width vec) runs row-partitioned.
+bool use_partition(bs_handle h, int64_t M, int vec) {
+  if (!h->has_part || h->periodic) return false;
+  const int64_t o = option(BS_OPT_PARTITION);
+  if (o == 1) return false;
+  if (o == 2) return true;
+  return M / vec < (int64_t)device_info().sms * 128;
+}
+
 static bs_status check_common(bs_handle h, const void* B, bs_layout layout, int64_t M, const char* fn) {
   if (!valid_handle(h)) return set_error(BS_EINVAL, std::string(fn) + ": unknown handle");
   if (!B) return set_error(BS_EINVAL, std::string(fn) + ": null data pointer");
@@ -87,13 +103,17 @@ bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64
   cudaError_t e;
   const int N = (int)h->N;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (dtype == BS_F64)
-    e = sweep_f64(h->plan[0], false, N, B, B, layout, M, st);
-  else if (dtype == BS_F32)
-    e = sweep_f32(h->plan[0], false, N, B, B, layout, M, st);
-  else
+  if (dtype != BS_F64 && dtype != BS_F32)
     return set_error(BS_EINVAL, "bs_solve: dtype must be BS_F64 or BS_F32 (BF16 input: bs_solve_bf16)");
+  const bool part = use_partition(h, M, dtype == BS_F64 ? 2 : 4);
+  const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
+  const int L = part ? h->part[0].L : 0, P = part ? h->part[0].P : 1;
+  if (dtype == BS_F64)
+    e = sweep_f64(p, false, N, B, B, layout, M, st, L, P);
+  else
+    e = sweep_f32(p, false, N, B, B, layout, M, st, L, P);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve launch");
+  if (part) return part_correct(h->part[0], N, B, dtype, layout, M, st);
   return BS_OK;
 }
 
@@ -105,8 +125,13 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
   const char* x0 = reinterpret_cast<const char*>(X);
   const size_t nm = (size_t)h->N * (size_t)M;
   if (b0 < x0 + nm * 4 && x0 < b0 + nm * 2) return set_error(BS_EINVAL, "bs_solve_bf16: B and X overlap");
-  cudaError_t e = sweep_bf16(h->plan[0], false, (int)h->N, B, X, layout, M, reinterpret_cast<cudaStream_t>(stream));
+  const bool part = use_partition(h, M, 4);
+  const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = sweep_bf16(p, false, (int)h->N, B, X, layout, M, st, part ? h->part[0].L : 0,
+                             part ? h->part[0].P : 1);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve_bf16 launch");
+  if (part) return part_correct(h->part[0], (int)h->N, X, BS_F32, layout, M, st);
   return BS_OK;
 }
 
@@ -119,13 +144,20 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
   const int N = (int)h->N;
+  if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_solve_adjoint: dtype must be BS_F64 or BS_F32");
+  // partitioned: the primal-form plan of A^T's block-diagonal part
+  const bool part = use_partition(h, M, dtype == BS_F64 ? 2 : 4);
+  const SweepPlan& p = part ? h->part[1].blk : h->plan[1];
+  const int L = part ? h->part[1].L : 0, P = part ? h->part[1].P : 1;
   if (dtype == BS_F64)
-    e = sweep_f64(h->plan[1], true, N, G, G, layout, M, st);
-  else if (dtype == BS_F32)
-    e = sweep_f32(h->plan[1], true, N, G, G, layout, M, st);
+    e = sweep_f64(p, !part, N, G, G, layout, M, st, L, P);
   else
-    return set_error(BS_EINVAL, "bs_solve_adjoint: dtype must be BS_F64 or BS_F32");
+    e = sweep_f32(p, !part, N, G, G, layout, M, st, L, P);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve_adjoint launch");
+  if (part) {
+    const bs_status ps = part_correct(h->part[1], N, G, dtype, layout, M, st);
+    if (ps != BS_OK) return ps;
+  }
   if (X) return launch_band_grad(h, G, X, dtype, layout, M, dbands, st);
   return BS_OK;
 }

@@ -8,14 +8,14 @@ int sweep_tma(const SweepPlan&, bool, int, const Sin*, float*, int64_t, cudaStre
 int64_t option(int o);
 
 cudaError_t sweep_bf16(const SweepPlan& p, bool adjoint, int N, const void* in, void* out,
-                        bs_layout layout, int64_t M, cudaStream_t st) {
-  if (layout == BS_INTERLEAVED && !p.periodic && option(BS_OPT_SWEEP_KERNEL) == 2) {
+                        bs_layout layout, int64_t M, cudaStream_t st, int L, int P) {
+  if (layout == BS_INTERLEAVED && !p.periodic && P == 1 && option(BS_OPT_SWEEP_KERNEL) == 2) {
     cudaError_t e = cudaSuccess;
     if (sweep_tma<__nv_bfloat16>(p, adjoint, N, reinterpret_cast<const __nv_bfloat16*>(in), reinterpret_cast<float*>(out), M, st, &e))
       return e;
   }
   return dispatch_sweep<float, __nv_bfloat16, float, 4>(p, adjoint, N, reinterpret_cast<const __nv_bfloat16*>(in),
-                                                reinterpret_cast<float*>(out), layout, M, st);
+                                                reinterpret_cast<float*>(out), layout, M, st, L, P);
 }
 
 }  // namespace bs

@@ -134,6 +134,23 @@ __host__ __device__ constexpr int coef_arrays() {
   return 1 + 2 * BW + (PER ? 2 : 0);  // scale + BW lower + BW upper (+ pw, pc)
 }
 
+// Coefficients of rows r0, r0 + 1, ... (the row block of a partitioned
+// launch) as a plan of its own.
+template <typename C>
+__host__ __device__ __forceinline__ Coefs<C> shift_coefs(Coefs<C> c, int r0) {
+  c.s += r0;
+  c.l1 += r0;
+  c.l2 += r0;
+  c.t += r0;
+  c.u1 += r0;
+  c.u2 += r0;
+  c.pw += r0;
+  c.pc += r0;
+  c.per_lo -= r0;
+  c.per_hi -= r0;
+  return c;
+}
+
 // Periodic correction terms (Sherman-Morrison, Sec. 3.3) of one block of U
 // rows: before the forward block, sig += pw_i f_i over the raw inputs; after
 // the backward block, f_i -= sig pc_i (the recurrence state keeps the
@@ -309,8 +326,15 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // thread keeps up to 2*U*V loads in flight.
 template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
-k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise)
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    in += (int64_t)r0 * M;
+    out += (int64_t)r0 * M;
+  }
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const int64_t ngroups = M / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -385,11 +409,18 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
 // back through the same ring.
 template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
-k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
   static_assert(V * sizeof(Sout) == 16 || V * sizeof(Sout) == 8, "output lane row must be 8 or 16 bytes");
   constexpr int U = 4;  // rows per block; D is a multiple of U
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise)
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    in += (int64_t)r0 * M;
+    out += (int64_t)r0 * M;
+  }
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER>() * N * sizeof(C), 16) : 0;
   unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
@@ -487,8 +518,15 @@ constexpr int kStPad = 33;
 
 template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, bool PER>
 __global__ void __launch_bounds__(kSweepThreads)
-k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
+k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int64_t ld, int L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise); ld = system stride
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    in += r0;
+    out += r0;
+  }
   C* smc = reinterpret_cast<C*>(smem_raw);
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, smc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -506,7 +544,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (lane < rows)
         for (int s = 0; s < nsys; s++) {
           C v[1];
-          IO<Sin, C, 1>::load(in + (j0 + s) * (int64_t)N + c0 + lane, v);
+          IO<Sin, C, 1>::load(in + (j0 + s) * ld + c0 + lane, v);
           tile[lane * kStPad + s] = v[0];
         }
       __syncwarp();
@@ -522,7 +560,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (lane < rows)
         for (int s = 0; s < nsys; s++) {
           const C v[1] = {tile[lane * kStPad + s]};
-          IO<Sout, C, 1>::store(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+          IO<Sout, C, 1>::store(out + (j0 + s) * ld + c0 + lane, v);
         }
       __syncwarp();
     }
@@ -534,7 +572,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (lane < rows)
         for (int s = 0; s < nsys; s++) {
           C v[1];
-          IO<Sout, C, 1>::load(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+          IO<Sout, C, 1>::load(out + (j0 + s) * ld + c0 + lane, v);
           tile[lane * kStPad + s] = v[0];
         }
       __syncwarp();
@@ -550,7 +588,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M) {
       if (lane < rows)
         for (int s = 0; s < nsys; s++) {
           const C v[1] = {tile[lane * kStPad + s]};
-          IO<Sout, C, 1>::store(out + (j0 + s) * (int64_t)N + c0 + lane, v);
+          IO<Sout, C, 1>::store(out + (j0 + s) * ld + c0 + lane, v);
         }
       __syncwarp();
     }
@@ -579,53 +617,58 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
                         int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
                         int extra_coef_arrays = 0);
 
+// L, P: rows per block and blocks of a partitioned launch (L = N, P = 1
+// otherwise); grid.y = P.
 template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout, int V>
-cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
+cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
   constexpr int U = 8;
   const int64_t groups = M / V;
   if constexpr (V > 1) {
     // pipelined kernel: ring of kRingRows 16-byte slots per lane
     constexpr int D = 16;
-    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
+    const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
     const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
+    const dim3 grid((sh.grid + P - 1) / P, P);
     if (sh.smem_coefs) {
       auto k = k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
-      k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
+      k<<<grid, sh.threads, bytes, st>>>(cf, N, in, out, M, L);
     } else {
       auto k = k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
-      k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
+      k<<<grid, sh.threads, bytes, st>>>(cf, N, in, out, M, L);
     }
     return cudaGetLastError();
   } else {
-    const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(Sout), V, 0, 0, 0, PER ? 2 : 0);
+    const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, 0, 0, 0, PER ? 2 : 0);
+    const dim3 grid((sh.grid + P - 1) / P, P);
     if (sh.smem_coefs) {
       auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
       if (e != cudaSuccess) return e;
-      k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, N, in, out, M);
+      k<<<grid, sh.threads, sh.smem, st>>>(cf, N, in, out, M, L);
     } else {
-      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U, PER><<<sh.grid, sh.threads, 0, st>>>(cf, N, in, out, M);
+      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U, PER><<<grid, sh.threads, 0, st>>>(cf, N, in, out, M, L);
     }
     return cudaGetLastError();
   }
 }
 
 template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout>
-cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
+cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
   const int64_t threads = ((M + 31) / 32) * 32;
   const size_t tiles = (size_t)(kSweepThreads / 32) * kStRows * kStPad * sizeof(C);
-  LaunchShape sh = sweep_shape(BW, N, threads, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads, PER ? 2 : 0);
+  LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads, PER ? 2 : 0);
+  const dim3 grid((sh.grid + P - 1) / P, P);
   if (sh.smem_coefs) {
     auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout, PER>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
-    k<<<sh.grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, in, out, M);
+    k<<<grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, in, out, M, (int64_t)N, L);
   } else {
-    k_sweep_st<BW, ADJ, false, C, Sin, Sout, PER><<<sh.grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M);
+    k_sweep_st<BW, ADJ, false, C, Sin, Sout, PER><<<grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M, (int64_t)N, L);
   }
   return cudaGetLastError();
 }
@@ -634,7 +677,8 @@ cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, c
 // storage/compute type combination.
 template <typename C, typename Sin, typename Sout, int VEC>
 cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* in, Sout* out,
-                           bs_layout layout, int64_t M, cudaStream_t st) {
+                           bs_layout layout, int64_t M, cudaStream_t st, int L = 0, int P = 1) {
+  if (L <= 0) L = N;
   const C* base;
   if constexpr (sizeof(C) == 8)
     base = reinterpret_cast<const C*>(p.c64);
@@ -650,14 +694,14 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
   constexpr bool kHalf = std::is_same<Sin, float>::value && VEC == 4;
   const bool half = kHalf && (M % 2 == 0) && (reinterpret_cast<uintptr_t>(in) % 8 == 0) &&
                     (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
-                    (M / VEC < (int64_t)device_info().sms * 32 * 8);
-#define BS_DISPATCH(BWV, ADJV, PERV)                                                                  \
-  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, st);      \
-  if constexpr (kHalf) {                                                                              \
-    if (half) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, st); \
-  }                                                                                                   \
-  if (vec) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, VEC>(cf, N, in, out, M, st);                \
-  return launch_il<BWV, ADJV, PERV, C, Sin, Sout, 1>(cf, N, in, out, M, st);
+                    (M / VEC * P < (int64_t)device_info().sms * 32 * 8);
+#define BS_DISPATCH(BWV, ADJV, PERV)                                                                        \
+  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, L, P, st);      \
+  if constexpr (kHalf) {                                                                                    \
+    if (half) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, L, P, st); \
+  }                                                                                                         \
+  if (vec) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, VEC>(cf, N, in, out, M, L, P, st);                \
+  return launch_il<BWV, ADJV, PERV, C, Sin, Sout, 1>(cf, N, in, out, M, L, P, st);
   if (p.bw == 1 && p.periodic) {
     if (!adjoint) { BS_DISPATCH(1, false, true) } else { BS_DISPATCH(1, true, true) }
   } else if (p.bw == 1) {

@@ -1,0 +1,155 @@
+"""GPU parity of the row-partitioned tridiagonal solves (blocks of rows per
+thread, a reduced system for the block-edge values, a correction near the
+edges) against the CPU FP64 oracle, through the C ABI.  The partition is
+forced with OPT_PARTITION = 2 (it is otherwise used automatically for small
+batches); tolerances as for the plain solves: FP64 1e-12 relative L2, FP32
+and BF16-stored 2e-5.  The partitioned and unpartitioned FP64 results must
+also agree to 1e-13."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    yield m
+    m.set_option(m.OPT_PARTITION, 0)
+
+
+def _run(bs, f, Bh, dtype, layout, mode):
+    bs.set_option(bs.OPT_PARTITION, mode)
+    try:
+        B = torch.tensor(Bh, dtype=dtype, device="cuda")
+        bs.solve(f, B, layout)
+        torch.cuda.synchronize()
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+    return B.double().cpu().numpy()
+
+
+SHAPES = [(768, 1), (768, 7), (1000, 64), (4096, 130), (5000, 33), (4096, 2048)]
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("N,M", SHAPES)
+def test_partitioned_fp64(bs, N, M, layout):
+    rng = np.random.default_rng(N + 3 * M)
+    bands = synth.random_tri_bands(N, rng)
+    B = rng.uniform(-1, 1, (N, M))
+    Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
+    f = bs.Factor(bands)
+    Xp = _run(bs, f, Bh, torch.float64, layout, 2)
+    Xu = _run(bs, f, Bh, torch.float64, layout, 1)
+    ref = oracle.solve(bands, Bh, layout)
+    assert rel_l2(Xp, ref) < TOL64
+    assert rel_l2(Xp, Xu) < 1e-13
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("N,M", [(768, 5), (4096, 130), (5000, 1024)])
+def test_partitioned_fp32(bs, N, M, layout):
+    rng = np.random.default_rng(N + 5 * M)
+    bands = synth.random_tri_bands(N, rng)
+    B = rng.uniform(-1, 1, (N, M)).astype(np.float32).astype(np.float64)
+    Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
+    f = bs.Factor(bands)
+    X = _run(bs, f, Bh, torch.float32, layout, 2)
+    assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL32
+
+
+def test_partitioned_bf16(bs):
+    N, M = 4096, 260
+    rng = np.random.default_rng(21)
+    bands = synth.random_tri_bands(N, rng)
+    f = bs.Factor(bands)
+    B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.bfloat16, device="cuda")
+    bs.set_option(bs.OPT_PARTITION, 2)
+    try:
+        X = bs.solve_bf16(f, B)
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+    ref = oracle.solve(bands, B.double().cpu().numpy())
+    assert rel_l2(X.double().cpu().numpy(), ref) < TOL32
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+def test_partitioned_adjoint_and_band_grad(bs, layout, dtype, tol):
+    """Non-symmetric bands, so A^T's partition differs from A's."""
+    N, M = 2000, 300
+    rng = np.random.default_rng(31)
+    bands = synth.random_tri_bands(N, rng)
+    B = rng.uniform(-1, 1, (N, M))
+    Gm = rng.uniform(-1, 1, (N, M))
+    if dtype == torch.float32:
+        B = B.astype(np.float32).astype(np.float64)
+        Gm = Gm.astype(np.float32).astype(np.float64)
+    tr = (lambda A: A) if layout == "interleaved" else (lambda A: np.ascontiguousarray(A.T))
+    f = bs.Factor(bands)
+    bs.set_option(bs.OPT_PARTITION, 2)
+    try:
+        X = torch.tensor(tr(B), dtype=dtype, device="cuda")
+        bs.solve(f, X, layout)
+        G = torch.tensor(tr(Gm), dtype=dtype, device="cuda")
+        G, db = bs.solve_adjoint(f, G, layout, X=X)
+        torch.cuda.synchronize()
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+    assert rel_l2(X.double().cpu().numpy(), oracle.solve(bands, tr(B), layout)) < tol
+    GB_ref = oracle.solve_adjoint(bands, tr(Gm), layout)
+    assert rel_l2(G.double().cpu().numpy(), GB_ref) < tol
+    db_ref = oracle.band_grad(3, G.double().cpu().numpy(), X.double().cpu().numpy(), layout)
+    err = np.max(np.abs(db.cpu().numpy() - db_ref)) / np.max(np.abs(db_ref))
+    assert err < (1e-13 if dtype == torch.float64 else 1e-6)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_partitioned_adi(bs, axis, adjoint, dtype, tol):
+    """ADI half-steps on a 1024 x 1024 grid (the implicit axis splits into 4
+    blocks of 256 rows), forward and adjoint, against the oracle's half-step
+    (the ADI operator is symmetric, so the adjoint half-step equals the
+    oracle's half-step applied in the transposed order of operators)."""
+    n, r = 1024, 0.5
+    u = synth.adi_field(n, 5, "cpu", torch.float64).numpy()
+    if dtype == torch.float32:
+        u = u.astype(np.float32).astype(np.float64)
+    f = bs.Factor(synth.adi_bands(n, r))
+    ut = torch.tensor(u, dtype=dtype, device="cuda")
+    outs = {}
+    for mode in (2, 1):
+        bs.set_option(bs.OPT_PARTITION, mode)
+        try:
+            outs[mode] = bs.adi_halfstep(f, ut, r, axis, adjoint=adjoint).double().cpu().numpy()
+        finally:
+            bs.set_option(bs.OPT_PARTITION, 0)
+    if not adjoint:
+        ref = oracle.adi_halfstep(u, r, axis)
+        assert rel_l2(outs[2], ref) < tol
+    assert rel_l2(outs[2], outs[1]) < (1e-13 if dtype == torch.float64 else 1e-5)
+
+
+def test_no_partition_without_decay(bs):
+    """A tridiagonal matrix whose spikes do not decay within a block gets no
+    partition; forcing the option then falls back to the plain solve."""
+    N, M = 4096, 64
+    bands = synth.toeplitz_bands(N, (-1.0, 2.0001, -1.0))
+    rng = np.random.default_rng(41)
+    Bh = rng.uniform(-1, 1, (N, M))
+    f = bs.Factor(bands)
+    X = _run(bs, f, Bh, torch.float64, "interleaved", 2)
+    Xu = _run(bs, f, Bh, torch.float64, "interleaved", 1)
+    assert np.array_equal(X, Xu)
+    assert rel_l2(X, oracle.solve(bands, Bh)) < 1e-9  # condition number ~1e7
