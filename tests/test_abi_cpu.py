@@ -70,3 +70,17 @@ def test_set_option(L):
     assert L.bs_set_option(0, 0) == 0
     assert L.bs_set_option(99, 1) == 1
     assert L.bs_set_option(0, -5) == 1
+
+
+def test_option_constants_match_header():
+    """The binding's OPT_* values are the header's bs_option values."""
+    import re
+
+    import paper_1909_04539_gb300 as bs
+
+    hdr = open(os.path.join(ROOT, "include", "bsolve.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"BS_OPT_(\w+)\s*=\s*(\d+)", hdr))
+    for name, val in enum.items():
+        if name == "COUNT":
+            continue
+        assert getattr(bs, "OPT_" + name) == val, name
