@@ -47,6 +47,7 @@ def _load(path: str) -> ctypes.CDLL:
     L.oracle_band_grad_periodic.argtypes = [i64, dp, dp, i64, i64, i64, dp]
     L.oracle_band_grad_periodic.restype = None
     L.oracle_adi_halfstep.argtypes = [i64, i64, ctypes.c_double, dp, dp, i32]
+    L.oracle_cn_steps.argtypes = [i32, i64, dp, i32, dp, i64, i64, i64, i32]
     L.oracle_num_threads.argtypes = []
     L.oracle_set_threads.argtypes = [i32]
     L.oracle_set_threads.restype = None
@@ -226,6 +227,19 @@ def band_grad_periodic(GB, X, layout: str = "interleaved") -> np.ndarray:
     out = np.zeros((3, N))
     lib().oracle_band_grad_periodic(N, _p(GB), _p(X), M, rs, ss, _p(out))
     return out
+
+
+def cn_steps(bands, C, steps: int = 1, periodic: bool = False, layout: str = "interleaved") -> np.ndarray:
+    """``steps`` Crank-Nicolson steps C <- A^{-1} (2I - A) C (the paper's
+    diffusion and hyperdiffusion benchmarks); ``periodic``: A is the periodic
+    tridiagonal matrix of ``bands``."""
+    b = _bands(bands)
+    X = np.array(C, dtype=np.float64, order="C", copy=True)
+    N, M, rs, ss = _strides(X, layout)
+    st = lib().oracle_cn_steps(b.shape[0], N, _p(b), int(bool(periodic)), _p(X), M, rs, ss, int(steps))
+    if st != 0:
+        raise OracleError(f"CN step failed (status {st})")
+    return X
 
 
 def adi_halfstep(u, r: float, implicit_axis: int) -> np.ndarray:

@@ -357,6 +357,47 @@ int oracle_periodic_tri_solve(int64_t N, double a, double b, double c, double* X
 }
 
 /* ------------------------------------------------------------------ */
+/* Crank-Nicolson time steps (the paper's benchmark problems, Sec. 3.2  */
+/* and Sec. 4.2)                                                       */
+/* ------------------------------------------------------------------ */
+
+/* The CN scheme for C_t = L C writes A C^{n+1} = B C^n with
+ * A = I - (dt/2) L and B = I + (dt/2) L, so that B = 2I - A: for the
+ * diffusion benchmark A = (-s, 1 + 2s, -s) and B = (s, 1 - 2s, s); for the
+ * hyperdiffusion benchmark A = (s, -4s, 1 + 6s, -4s, s) and
+ * B = (-s, 4s, 1 - 6s, 4s, -s).  One step: F = 2 C - A C, then solve
+ * A C = F (periodic != 0: A is the periodic tridiagonal matrix of Sec. 3.3,
+ * columns modulo N; else A is banded).  Repeated `steps` times in place. */
+int oracle_cn_steps(int width, int64_t N, const double* bands, int periodic, double* X, int64_t M, int64_t rs,
+                    int64_t ss, int steps) {
+  int h = width / 2;
+  int st = 0;
+  double* F = (double*)malloc(sizeof(double) * N * M);
+  for (int n = 0; n < steps && st == 0; n++) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < M; j++)
+      for (int64_t i = 0; i < N; i++) {
+        double s = 0.0;
+        for (int k = 0; k < width; k++) {
+          int64_t col = i + k - h;
+          if (periodic) col = (col + N) % N;
+          if (col >= 0 && col < N) s += bands[(int64_t)k * N + i] * EL(X, col, j);
+        }
+        F[i * M + j] = 2.0 * EL(X, i, j) - s;
+      }
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < M; j++)
+      for (int64_t i = 0; i < N; i++) EL(X, i, j) = F[i * M + j];
+    if (periodic)
+      st = oracle_periodic_tri_solve_bands(N, bands, X, M, rs, ss);
+    else
+      st = oracle_solve(width, N, bands, X, M, rs, ss);
+  }
+  free(F);
+  return st;
+}
+
+/* ------------------------------------------------------------------ */
 /* 2D ADI (Peaceman-Rachford) half-step for u_t = u_xx + u_yy           */
 /* ------------------------------------------------------------------ */
 

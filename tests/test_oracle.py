@@ -238,6 +238,48 @@ def pin_periodic_band_grad(N=5, M=3, seed=16):
             assert abs(db[k, i] - fd) < 1e-7 * (1 + abs(fd)), (k, i)
 
 
+def pin_cn_tri(N, s, K):
+    """K Crank-Nicolson steps of the diffusion benchmark matrix
+    A = (-s, 1 + 2s, -s) with zero boundary values: sine modes
+    sin(i k pi/(N+1)) are multiplied by g^K, g = (1 - 2s(1 - cos t))/(1 + 2s(1 - cos t)),
+    t = k pi/(N+1)."""
+    bands = synth.toeplitz_bands(N, (-s, 1 + 2 * s, -s))
+    i = np.arange(1, N + 1)
+    th = np.array([1, 2, 7, N // 2, N]) * math.pi / (N + 1)
+    V = np.sin(np.outer(i, th))
+    g = (1 - 2 * s * (1 - np.cos(th))) / (1 + 2 * s * (1 - np.cos(th)))
+    assert rel_l2(oracle.cn_steps(bands, V, K), V * g[None, :] ** K) < 1e-12
+
+
+def pin_cn_penta(N, s, K):
+    """K CN steps with A = I + s D2^2 (interior (s, -4s, 1 + 6s, -4s, s) as in
+    the hyperdiffusion benchmark, corner diagonals 1 + 5s): sine modes are
+    multiplied by g^K, g = (1 - s m^2)/(1 + s m^2), m = 2 - 2 cos t."""
+    bands = synth.toeplitz_bands(N, (s, -4 * s, 1 + 6 * s, -4 * s, s))
+    bands[2, 0] = bands[2, N - 1] = 1 + 5 * s
+    i = np.arange(1, N + 1)
+    th = np.array([1, 3, N // 3, N]) * math.pi / (N + 1)
+    V = np.sin(np.outer(i, th))
+    m2 = (2 - 2 * np.cos(th)) ** 2
+    g = (1 - s * m2) / (1 + s * m2)
+    assert rel_l2(oracle.cn_steps(bands, V, K), V * g[None, :] ** K) < 1e-12
+
+
+def pin_cn_periodic(N, s, K, layout="interleaved"):
+    """K CN steps of the periodic diffusion benchmark (Sec. 3.2 scheme on a
+    periodic domain): Fourier modes cos/sin(2 pi k i / N) are multiplied by
+    g^K, g = (1 - 2s(1 - cos t))/(1 + 2s(1 - cos t)), t = 2 pi k / N."""
+    bands = synth.periodic_toeplitz_bands(N, (-s, 1 + 2 * s, -s))
+    i = np.arange(N)
+    ks = np.array([0, 1, 3, N // 2])
+    th = 2 * math.pi * ks / N
+    V = np.concatenate([np.cos(np.outer(i, th)), np.sin(np.outer(i, th[1:3]))], axis=1)
+    g = (1 - 2 * s * (1 - np.cos(th))) / (1 + 2 * s * (1 - np.cos(th)))
+    gg = np.concatenate([g, g[1:3]])
+    X = from_layout(oracle.cn_steps(bands, to_layout(V, layout), K, periodic=True, layout=layout), layout)
+    assert rel_l2(X, V * gg[None, :] ** K) < 1e-12
+
+
 def pin_adi(ny, nx, r, seed=10):
     """ADI half-steps against the dense Kronecker operators:
     axis 0: (I - r Dxx) out = (I + r Dyy) u; axis 1: (I - r Dyy) out = (I + r Dxx) u."""
@@ -288,6 +330,10 @@ def all_pins():
         ("periodic_band_grad", lambda: pin_periodic_band_grad()),
         ("periodic_band_grad_min", lambda: pin_periodic_band_grad(3, 2, 18)),
         ("adi_rect", lambda: pin_adi(5, 7, 0.5)),
+        ("cn_tri", lambda: pin_cn_tri(40, 0.7, 5)),
+        ("cn_penta", lambda: pin_cn_penta(30, 0.3, 4)),
+        ("cn_periodic", lambda: pin_cn_periodic(24, 0.9, 6)),
+        ("cn_periodic_strided", lambda: pin_cn_periodic(9, 0.4, 3, "strided")),
     ]
     return out
 

@@ -36,6 +36,8 @@ MUTATIONS = [
     ("periodic_u_corner", "z[N - 1] = c[N - 1];", "z[N - 1] = a[0];", 0),
     ("periodic_grad_col", "int64_t col = (i + k - 1 + N) % N;", "int64_t col = (i + k + N) % N;", 0),
     ("periodic_grad_sign", "dbands[(int64_t)k * N + i] = -s;\n    }\n}\n\n/* -----", "dbands[(int64_t)k * N + i] = s;\n    }\n}\n\n/* -----", 0),
+    ("cn_explicit_op", "F[i * M + j] = 2.0 * EL(X, i, j) - s;", "F[i * M + j] = EL(X, i, j) - s;", 0),
+    ("cn_no_wrap", "if (periodic) col = (col + N) % N;", "", 0),
     ("adi_explicit_sign", "out[y * nx + x] = c0 + r * (lo - 2.0 * c0 + hi);",
      "out[y * nx + x] = c0 - r * (lo - 2.0 * c0 + hi);", 0),
     ("adi_lhs_diag", "bands[n_row + i] = 1.0 + 2.0 * r;", "bands[n_row + i] = 1.0 + r;", 0),
