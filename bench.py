@@ -532,6 +532,27 @@ def run_other_configs(bs, st, hbm):
             rows = np.random.default_rng(12).choice(n, 8, replace=False)
             samples["adi"] = (r, u.cpu().numpy(), full.cpu().numpy(), rows)
     out["adi_4096x4096"] = adi
+    # the paper's benchmark problems as Crank-Nicolson time stepping (explicit
+    # side fused into the sweep): periodic diffusion (-s, 1 + 2s, -s), N = 1024,
+    # and hyperdiffusion (s, -4s, 1 + 6s, -4s, s), N = 512; M = 65536, 10 steps
+    cn = {}
+    for name, N, bands, per in (
+            ("periodic_diffusion_N1024", 1024, synth.periodic_toeplitz_bands(1024, (-0.5, 2.0, -0.5)), True),
+            ("hyperdiffusion_N512", 512, synth.toeplitz_bands(512, (0.1, -0.4, 1.6, -0.4, 0.1)), False)):
+        f = bs.Factor(bands, periodic=per)
+        M, K = 65536, 10
+        for dt, dname, es in ((torch.float64, "f64", 8), (torch.float32, "f32", 4)):
+            C = synth.uniform_rhs(N, M, 3, "cuda", dt)
+            if dt == torch.float64:
+                cols = np.random.default_rng(13).choice(M, 64, replace=False)
+                C0 = C[:, cols].cpu().numpy()
+                bs.cn_steps(f, C, 2)
+                samples[f"cn_{name}"] = (bands, per, C0, C[:, cols].cpu().numpy())
+            t = time_alone(lambda: bs.cn_steps(f, C, K), st, reps=5) / K
+            cn[f"{name}_{dname}"] = {"ms_per_step": t, "unknowns_per_s": N * M / (t * 1e-3),
+                                     "hbm_gbs": 2 * es * N * M / (t * 1e-3) / 1e9}
+            del C
+    out["cn_steps_M65536"] = cn
     return out, samples
 
 
@@ -631,6 +652,10 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
             r, u, full, rows = smp
             ref = oracle.adi_halfstep(oracle.adi_halfstep(u, r, 0), r, 1)
             errs["adi_4096_full_step_f64"] = float(np.linalg.norm(full - ref) / np.linalg.norm(ref))
+        elif name.startswith("cn_"):
+            b, per, C0, C2 = smp
+            ref = oracle.cn_steps(b, C0, 2, periodic=per)
+            errs[f"{name}_2_steps_f64"] = float(np.linalg.norm(C2 - ref) / np.linalg.norm(ref))
         else:
             b, Bs, X64s, XRs = smp
             ref = oracle.periodic_tri_solve_bands(b, Bs) if name.startswith("periodic") else oracle.solve(b, Bs)

@@ -180,6 +180,20 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
 bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const void* X, bs_dtype dtype, bs_layout layout,
                                int64_t M, double* dbands, bs_stream stream);
 
+/* `steps` Crank-Nicolson time steps of the batch C (device, interleaved,
+ * N x M, dtype BS_F64 or BS_F32), in place: C <- A^{-1} (2I - A) C, where A
+ * is the handle's matrix.  For C_t = L C the scheme's LHS is A = I - (dt/2) L
+ * and its explicit side is I + (dt/2) L = 2I - A, so the handle alone defines
+ * the step: the paper's benchmarks are the periodic diffusion equation
+ * (A = (-s, 1 + 2s, -s) from bs_factor_periodic, Sec. 3.2-3.3) and the
+ * hyperdiffusion equation (A = (s, -4s, 1 + 6s, -4s, s), Sec. 4.2).  The
+ * explicit side is applied while the forward sweep reads the rows (no
+ * separate stencil pass); for a periodic handle it wraps around and the
+ * Sherman-Morrison correction is fused as in bs_solve.  One kernel launch
+ * per step, stream-ordered.  BS_EUNSUPPORTED for the strided layout. */
+bs_status bs_cn_steps(bs_handle h, void* C, bs_dtype dtype, bs_layout layout, int64_t M, int steps,
+                      bs_stream stream);
+
 /* One Peaceman-Rachford ADI half-step for u_t = u_xx + u_yy on an ny x nx
  * grid stored row-major (U[y*nx + x], device), homogeneous Dirichlet
  * boundaries (zero outside the grid):

@@ -24,6 +24,7 @@ SIGNATURES = {
     "bs_solve_refine": (i32, [vp, vp, i32, vp, i32, i64, i32, i32, vp]),
     "bs_solve_adjoint": (i32, [vp, vp, i32, i32, i64, vp, vp, vp]),
     "bs_adi_halfstep": (i32, [vp, vp, vp, i32, i64, i64, ctypes.c_double, i32, i32, vp]),
+    "bs_cn_steps": (i32, [vp, vp, i32, i32, i64, i32, vp]),
     "bs_band_grad": (i32, [vp, vp, vp, i32, i32, i64, vp, vp]),
     "bs_band_grad_noalloc": (i32, [vp, vp, vp, i32, i32, i64, vp, vp]),
     "bs_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(vp)]),

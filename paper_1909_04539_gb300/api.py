@@ -209,6 +209,17 @@ def band_grad(f: Factor, GB: torch.Tensor, X: torch.Tensor, layout: str = "inter
     return dbands
 
 
+def cn_steps(f: Factor, C: torch.Tensor, steps: int = 1, layout: str = "interleaved", stream=None) -> torch.Tensor:
+    """``steps`` Crank-Nicolson steps in place, C <- A^{-1} (2I - A) C (A the
+    factor's matrix: the scheme's LHS I - (dt/2) L); float64 or float32."""
+    M = _batch(f, C, layout, "C")
+    if C.dtype not in (torch.float64, torch.float32):
+        raise ValueError("C must be float64 or float32")
+    check(lib().bs_cn_steps(f.handle, ctypes.c_void_p(C.data_ptr()), _DTYPE[C.dtype], _LAYOUT[layout], M,
+                            int(steps), _stream(stream)), "bs_cn_steps")
+    return C
+
+
 def adi_halfstep(f: Factor, u: torch.Tensor, r: float, implicit_axis: int, out: torch.Tensor | None = None,
                  adjoint: bool = False, stream=None) -> torch.Tensor:
     """One Peaceman-Rachford half-step on the (ny, nx) field u (row-major,

@@ -18,6 +18,8 @@
 //   (interleaved, M = nx).  Implicit along x: system j = row y, row i = x, at
 //   u[j * nx + i] (system-contiguous); a warp moves 32 rows of 34 systems (its
 //   32 plus one neighbour each side) through a shared-memory tile.
+#include <type_traits>
+
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -289,18 +291,27 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   else
     base = reinterpret_cast<const C*>(p.c32);
   const Coefs<C> cf = coefs_of<C>(base, N);
+  // Ring depth: with one thread per grid line (P = 1) there is less than one
+  // warp per SM and the depth must come from each lane (64 rows, 8 chunks);
+  // a partitioned launch has P times the threads, and shallow rings leave
+  // room for more resident CTAs.
   if (axis == 1) {
-    constexpr int D = 64;
-    const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh =
-        sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
-    const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
-    auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    k<<<dim3((sh.grid + P - 1) / P, P), sh.threads, bytes, st>>>(cf, N, u, out, M, r, L);
-  } else {
-    constexpr int K = 8;
+    auto go = [&](auto dtag) -> cudaError_t {
+      constexpr int D = decltype(dtag)::value;
+      const int64_t threads = ((M + 31) / 32) * 32;
+      const LaunchShape sh =
+          sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
+      const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
+      auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      k<<<dim3((sh.grid + P - 1) / P, P), sh.threads, bytes, st>>>(cf, N, u, out, M, r, L);
+      return cudaGetLastError();
+    };
+    return P > 1 ? go(std::integral_constant<int, 16>{}) : go(std::integral_constant<int, 64>{});
+  }
+  auto go = [&](auto ktag) -> cudaError_t {
+    constexpr int K = decltype(ktag)::value;
     const size_t tiles = ((size_t)K * kStRows * kAdiTile + (size_t)kStRows * kStPad) * sizeof(C);
     const int64_t threads = ((M + 31) / 32) * 32;
     const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32);
@@ -308,8 +319,9 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
     k<<<dim3((sh.grid + P - 1) / P, P), 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
-  }
-  return cudaGetLastError();
+    return cudaGetLastError();
+  };
+  return P > 1 ? go(std::integral_constant<int, 3>{}) : go(std::integral_constant<int, 8>{});
 }
 
 bool use_partition(bs_handle h, int64_t M, int vec);

@@ -1,0 +1,224 @@
+// Crank-Nicolson time steps C <- A^{-1} (2I - A) C on an interleaved batch,
+// in place: the paper's benchmark problems (the periodic diffusion equation,
+// Sec. 3.2-3.3, and the hyperdiffusion equation, Sec. 4.2) advance every
+// system with A C^{n+1} = B C^n, where A = I - (dt/2) L is the shared LHS and
+// B = I + (dt/2) L = 2I - A.  The paper forms the right-hand side with a
+// separate stencil library pass; here the explicit side is applied to the
+// rows as the forward sweep reads them (each thread keeps the rows it needs
+// around row i in registers), so a step reads C once and writes it once plus
+// the forward values' round trip of the ordinary solve.
+//
+// Per thread: V neighbouring systems, rows moved in blocks of U with a
+// two-block register pipeline (as the plain V = 1 kernel).  The explicit
+// bands e = 2I - A are formed once per CTA in shared memory (or read from
+// the handle's bands in global memory for large N).  For a periodic handle
+// the explicit side wraps around (rows 0 and N-1 are kept from the start of
+// the step, before they are overwritten) and the Sherman-Morrison correction
+// of the solve is applied as in the plain periodic sweeps.
+#include "sweep_kernels.cuh"
+
+namespace bs {
+
+template <int BW, bool PER, bool SMEM, typename C, int V, int U>
+__global__ void __launch_bounds__(kSweepThreads)
+k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
+  constexpr int W = 2 * BW + 1;
+  static_assert(U >= BW, "a block must cover the look-ahead rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const Coefs<C> cf = stage_coefs<BW, false, SMEM, C, PER>(cf_g, N, sm);
+  // explicit bands e_k(i) = [k == BW] * 2 - band_k(i)
+  const C* eb;
+  C* esm = sm + (SMEM ? coef_arrays<BW, PER>() * N : 0);
+  if (SMEM) {
+    for (int t = threadIdx.x; t < W * N; t += blockDim.x) esm[t] = ((t / N) == BW ? C(2) : C(0)) - bands[t];
+    __syncthreads();
+    eb = esm;
+  } else {
+    eb = bands;  // e computed on the fly below
+  }
+  auto e_at = [&](int k, int i) -> C {
+    if (SMEM) return eb[k * N + i];
+    return (k == BW ? C(2) : C(0)) - eb[k * N + i];
+  };
+  const int64_t ngroups = M / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    C* px = X + g * V;
+    auto load = [&](C (&o)[V], int row) { IO<C, C, V>::load(px + (int64_t)row * M, o); };
+    C head[BW][V], prev[BW][V];
+#pragma unroll
+    for (int q = 0; q < BW; q++)
+#pragma unroll
+      for (int v = 0; v < V; v++) head[q][v] = prev[q][v] = C(0);
+    if (PER) {  // rows 0..BW-1 and N-BW..N-1 before the step overwrites them
+#pragma unroll
+      for (int q = 0; q < BW; q++) {
+        load(head[q], q);
+        load(prev[q], N - BW + q);
+      }
+    }
+    C cur[U][V], nxt[U][V], r1[V], r2[V], sig[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = sig[v] = C(0);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (u < N) load(cur[u], u);
+    for (int i0 = 0; i0 < N; i0 += U) {
+      const int n = (N - i0) < U ? (N - i0) : U;
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (i0 + U + u < N) load(nxt[u], i0 + U + u);
+      // window of raw rows i0 - BW .. i0 + U - 1 + BW (all indexes static):
+      // rows past N are the wrapped rows 0.. (periodic) or zero
+      C win[U + 2 * BW][V];
+#pragma unroll
+      for (int q = 0; q < BW; q++)
+#pragma unroll
+        for (int v = 0; v < V; v++) win[q][v] = prev[q][v];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        C w[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) w[v] = cur[u][v];
+        if (u >= n) {  // row i0 + u >= N: the wrapped row u - n
+#pragma unroll
+          for (int v = 0; v < V; v++) w[v] = C(0);
+          if (PER) {
+#pragma unroll
+            for (int q = 0; q < BW; q++)
+              if (u - n == q)
+#pragma unroll
+                for (int v = 0; v < V; v++) w[v] = head[q][v];
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) win[BW + u][v] = w[v];
+      }
+#pragma unroll
+      for (int q = 0; q < BW; q++) {
+        const bool in = i0 + U + q < N;
+#pragma unroll
+        for (int v = 0; v < V; v++) win[BW + U + q][v] = in ? nxt[q][v] : (PER ? head[q][v] : C(0));
+      }
+      // F = e applied to the window
+      C f[U][V];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (u < n) {
+          const int i = i0 + u;
+          C e[W];
+#pragma unroll
+          for (int k = 0; k < W; k++) e[k] = e_at(k, i);
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            C sacc = e[0] * win[u][v];
+#pragma unroll
+            for (int k = 1; k < W; k++) sacc = fma(e[k], win[u + k][v], sacc);
+            f[u][v] = sacc;
+          }
+        }
+      }
+      // raw rows i0 + n - BW .. i0 + n - 1 become the previous rows
+      if (n == U) {
+#pragma unroll
+        for (int q = 0; q < BW; q++)
+#pragma unroll
+          for (int v = 0; v < V; v++) prev[q][v] = cur[U - BW + q][v];
+      }
+      if constexpr (PER)
+        if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
+      fwd_block<BW, false, C, V, U>(cf, i0, n, f, r1, r2);
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (u < n) IO<C, C, V>::store(px + (int64_t)(i0 + u) * M, f[u]);
+#pragma unroll
+      for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int v = 0; v < V; v++) cur[u][v] = nxt[u][v];
+    }
+    // backward sweep over the forward values, as in the plain solve
+#pragma unroll
+    for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
+    for (int top = N - 1; top >= 0; top -= U) {
+      const int n = (top + 1) < U ? (top + 1) : U;
+      C b[U][V];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (u < n) load(b[u], top - u);
+      bwd_block<BW, false, C, V, U>(cf, top, n, b, r1, r2);
+      if constexpr (PER)
+        if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, b, sig);
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (u < n) IO<C, C, V>::store(px + (int64_t)(top - u) * M, b[u]);
+    }
+  }
+}
+
+template <int BW, bool PER, typename C, int V>
+static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, int64_t M, cudaStream_t st) {
+  constexpr int U = 8;
+  const C* base;
+  if constexpr (sizeof(C) == 8)
+    base = reinterpret_cast<const C*>(p.c64);
+  else
+    base = reinterpret_cast<const C*>(p.c32);
+  Coefs<C> cf = coefs_of<C>(base, N);
+  cf.per_lo = p.per_lo;
+  cf.per_hi = p.per_hi;
+  const int64_t groups = M / V;
+  // the explicit bands add 2 BW + 1 arrays to the staged coefficients
+  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(C), V, 0, 0, 0, (PER ? 2 : 0) + 2 * BW + 1);
+  if (sh.smem_coefs) {
+    auto k = k_cn_il<BW, PER, true, C, V, U>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    k<<<sh.grid, sh.threads, sh.smem, st>>>(cf, bands, N, X, M);
+  } else {
+    k_cn_il<BW, PER, false, C, V, U><<<sh.grid, sh.threads, 0, st>>>(cf, bands, N, X, M);
+  }
+  return cudaGetLastError();
+}
+
+template <typename C, int VEC>
+static cudaError_t cn_dispatch(bs_handle h, C* X, int64_t M, cudaStream_t st) {
+  const SweepPlan& p = h->plan[0];
+  const int N = (int)h->N;
+  const C* bands;
+  if constexpr (sizeof(C) == 8)
+    bands = reinterpret_cast<const C*>(h->bands64);
+  else
+    bands = reinterpret_cast<const C*>(h->bands_hi);
+  const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(X) % (VEC * sizeof(C)) == 0);
+  if (h->periodic)
+    return vec ? launch_cn<1, true, C, VEC>(p, bands, N, X, M, st) : launch_cn<1, true, C, 1>(p, bands, N, X, M, st);
+  if (h->width == 3)
+    return vec ? launch_cn<1, false, C, VEC>(p, bands, N, X, M, st)
+               : launch_cn<1, false, C, 1>(p, bands, N, X, M, st);
+  return vec ? launch_cn<2, false, C, VEC>(p, bands, N, X, M, st) : launch_cn<2, false, C, 1>(p, bands, N, X, M, st);
+}
+
+}  // namespace bs
+
+extern "C" bs_status bs_cn_steps(bs_handle h, void* C, bs_dtype dtype, bs_layout layout, int64_t M, int steps,
+                                 bs_stream stream) {
+  using namespace bs;
+  if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_cn_steps: unknown handle");
+  if (!C) return set_error(BS_EINVAL, "bs_cn_steps: null data pointer");
+  if (M < 1) return set_error(BS_EINVAL, "bs_cn_steps: M must be >= 1");
+  if (steps < 0) return set_error(BS_EINVAL, "bs_cn_steps: steps must be >= 0");
+  if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_cn_steps: dtype must be BS_F64 or BS_F32");
+  if (layout != BS_INTERLEAVED)
+    return set_error(BS_EUNSUPPORTED, "bs_cn_steps: only the interleaved layout is implemented");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(BS_EINVAL, "bs_cn_steps: handle belongs to another device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int n = 0; n < steps; n++) {
+    const cudaError_t e = dtype == BS_F64 ? cn_dispatch<double, 2>(h, static_cast<double*>(C), M, st)
+                                          : cn_dispatch<float, 4>(h, static_cast<float*>(C), M, st);
+    if (e != cudaSuccess) return cuda_error(e, "bs_cn_steps launch");
+  }
+  return BS_OK;
+}

@@ -1,0 +1,93 @@
+"""GPU parity of the fused Crank-Nicolson steps C <- A^{-1} (2I - A) C (the
+explicit side formed inside the forward sweep) against the oracle's
+definition (explicit product, then solve), through the C ABI.  Tolerances
+(relative L2 after the stated number of steps): FP64 1e-12; FP32 2e-5 for
+the oracle run on the FP32-rounded start (the schemes are stable, so the
+FP32 rounding of each step does not grow)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    return m
+
+
+def _run(bs, f, C0, dtype, steps):
+    C = torch.tensor(C0, dtype=dtype, device="cuda")
+    bs.cn_steps(f, C, steps)
+    torch.cuda.synchronize()
+    return C.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("N,M,sigma,steps", [(3, 1, 0.3, 2), (5, 6, 2.0, 3), (64, 1000, 0.25, 5),
+                                             (257, 1030, 5.0, 3), (1024, 4096, 1.0, 2)])
+def test_periodic_diffusion(bs, N, M, sigma, steps, dtype, tol):
+    """The paper's benchmark (Sec. 3.2-3.3): periodic (-s, 1 + 2s, -s)."""
+    bands = synth.periodic_toeplitz_bands(N, (-sigma, 1 + 2 * sigma, -sigma))
+    rng = np.random.default_rng(N + M)
+    C0 = rng.uniform(-1, 1, (N, M))
+    if dtype == torch.float32:
+        C0 = C0.astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands, periodic=True)
+    X = _run(bs, f, C0, dtype, steps)
+    assert rel_l2(X, oracle.cn_steps(bands, C0, steps, periodic=True)) < tol
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("N,M,steps", [(4, 1, 1), (5, 7, 2), (64, 512, 3), (513, 2050, 2)])
+def test_hyperdiffusion_penta(bs, N, M, steps, dtype, tol):
+    """The paper's second benchmark (Sec. 4.2) with zero boundary values:
+    (s, -4s, 1 + 6s, -4s, s)."""
+    s = 0.4
+    bands = synth.toeplitz_bands(N, (s, -4 * s, 1 + 6 * s, -4 * s, s))
+    rng = np.random.default_rng(3 * N + M)
+    C0 = rng.uniform(-1, 1, (N, M))
+    if dtype == torch.float32:
+        C0 = C0.astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    X = _run(bs, f, C0, dtype, steps)
+    assert rel_l2(X, oracle.cn_steps(bands, C0, steps)) < tol
+
+
+@pytest.mark.parametrize("N,M", [(2, 3), (100, 33), (1000, 64)])
+def test_diffusion_tri_random_bands(bs, N, M):
+    """Non-constant tridiagonal bands (any handle defines a step)."""
+    rng = np.random.default_rng(N * M)
+    bands = synth.random_tri_bands(N, rng)
+    C0 = rng.uniform(-1, 1, (N, M))
+    f = bs.Factor(bands)
+    X = _run(bs, f, C0, torch.float64, 3)
+    assert rel_l2(X, oracle.cn_steps(bands, C0, 3)) < TOL64
+
+
+def test_clamped_hyperdiffusion_matrix(bs):
+    bands = synth.clamped_hyperdiffusion_bands(512, 0.1)
+    rng = np.random.default_rng(5)
+    C0 = rng.uniform(-1, 1, (512, 2048))
+    f = bs.Factor(bands)
+    X = _run(bs, f, C0, torch.float64, 4)
+    assert rel_l2(X, oracle.cn_steps(bands, C0, 4)) < TOL64
+
+
+def test_zero_steps_and_errors(bs):
+    bands = synth.periodic_toeplitz_bands(16, (-0.5, 2.0, -0.5))
+    f = bs.Factor(bands, periodic=True)
+    C0 = np.random.default_rng(1).uniform(-1, 1, (16, 8))
+    assert np.array_equal(_run(bs, f, C0, torch.float64, 0), C0)
+    C = torch.zeros(8, 16, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError, match="interleaved"):
+        bs.cn_steps(f, C, 1, layout="strided")
