@@ -574,48 +574,99 @@ def time_alone(fn, st, reps=50, warm=3) -> float:
 
 def run_e2e(bs, f, N, M, st, args, world):
     """Same three solves through the public API with pinned host buffers:
-    each step copies its inputs host->device and its results back."""
+    each step copies its inputs host->device and its results back.  Steps
+    are pipelined the way a user streaming batches would run them: two sets
+    of device buffers, the host->device copies of step k+1 and the
+    device->host copies of step k-1 on their own streams while step k
+    computes (ordered by events).  The same steps run one after another on
+    one stream are reported beside it."""
     import torch
 
     steps = max(1, min(args.steps, 10))
     hB = torch.empty((N, M), dtype=torch.float64, pin_memory=True).normal_()
     hB32 = hB.float().pin_memory()
-    oXR = torch.empty_like(hB).pin_memory()
-    dXR = torch.empty((N, M), dtype=torch.float64, device="cuda")
     hG = torch.empty((N, M), dtype=torch.float64, pin_memory=True).uniform_(-1, 1)
-    oX = torch.empty_like(hB).pin_memory()
-    oG = torch.empty_like(hG).pin_memory()
-    odb = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
-    dB = torch.empty((N, M), dtype=torch.float64, device="cuda")
-    dB32 = torch.empty((N, M), dtype=torch.float32, device="cuda")
-    dG = torch.empty((N, M), dtype=torch.float64, device="cuda")
 
-    def one():
-        dB.copy_(hB, non_blocking=True)
-        dB32.copy_(hB32, non_blocking=True)
-        dG.copy_(hG, non_blocking=True)
-        bs.solve(f, dB)
-        bs.solve_refine(f, dB32, dXR)
-        _, db = bs.solve_adjoint(f, dG, X=dB)
-        oX.copy_(dB, non_blocking=True)
-        oXR.copy_(dXR, non_blocking=True)
-        oG.copy_(dG, non_blocking=True)
-        odb.copy_(db, non_blocking=True)
+    class Set:
+        def __init__(self):
+            self.dB = torch.empty((N, M), dtype=torch.float64, device="cuda")
+            self.dB32 = torch.empty((N, M), dtype=torch.float32, device="cuda")
+            self.dG = torch.empty((N, M), dtype=torch.float64, device="cuda")
+            self.dXR = torch.empty((N, M), dtype=torch.float64, device="cuda")
+            self.db = torch.empty((5, N), dtype=torch.float64, device="cuda")
+            self.oX = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
+            self.oXR = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
+            self.oG = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
+            self.odb = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
+            self.h2d = torch.cuda.Event()
+            self.comp = torch.cuda.Event()
+            self.d2h = torch.cuda.Event()
 
-    one()
+    sets = [Set(), Set()]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d(S, stream):
+        with torch.cuda.stream(stream):
+            S.dB.copy_(hB, non_blocking=True)
+            S.dB32.copy_(hB32, non_blocking=True)
+            S.dG.copy_(hG, non_blocking=True)
+
+    def compute(S, stream):
+        bs.solve(f, S.dB, stream=stream)
+        bs.solve_refine(f, S.dB32, S.dXR, stream=stream)
+        bs.solve_adjoint(f, S.dG, X=S.dB, dbands=S.db, stream=stream)
+
+    def d2h(S, stream):
+        with torch.cuda.stream(stream):
+            S.oX.copy_(S.dB, non_blocking=True)
+            S.oXR.copy_(S.dXR, non_blocking=True)
+            S.oG.copy_(S.dG, non_blocking=True)
+            S.odb.copy_(S.db, non_blocking=True)
+
+    def serial_step():
+        S = sets[0]
+        h2d(S, st)
+        compute(S, st)
+        d2h(S, st)
+
+    def pipelined(n):
+        for k in range(n):
+            S = sets[k % 2]
+            s_in.wait_event(S.d2h)   # step k-2 has read this set back
+            h2d(S, s_in)
+            S.h2d.record(s_in)
+            st.wait_event(S.h2d)
+            compute(S, st)
+            S.comp.record(st)
+            s_out.wait_event(S.comp)
+            d2h(S, s_out)
+            S.d2h.record(s_out)
+
+    serial_step()
+    pipelined(2)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    # serial
     t0.record(st)
     for _ in range(steps):
-        one()
+        serial_step()
     t1.record(st)
     torch.cuda.synchronize()
+    ms_serial = t0.elapsed_time(t1) / steps
+    # pipelined: from the first input copy to the last result copy
+    t0.record(s_in)
+    pipelined(steps)
+    t1.record(s_out)
+    torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
-    h2d = N * M * (8 + 4 + 8)
-    d2h = N * M * (8 + 8 + 8) + 5 * N * 8
-    return {"value": 3 * N * M * world / (ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": steps}
+    h2d_b = N * M * (8 + 4 + 8)
+    d2h_b = N * M * (8 + 8 + 8) + 5 * N * 8
+    return {"value": 3 * N * M * world / (ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": h2d_b,
+            "d2h_bytes_per_step": d2h_b, "ms_per_step": ms, "steps": steps,
+            "pipelining": "two buffer sets; copies in, compute and copies out on three streams",
+            "serial_ms_per_step": ms_serial,
+            "h2d_gbs": h2d_b / (ms * 1e-3) / 1e9, "d2h_gbs": d2h_b / (ms * 1e-3) / 1e9}
 
 
 # ------------------------------------------------------------------ CPU oracle

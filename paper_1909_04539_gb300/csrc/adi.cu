@@ -321,7 +321,7 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     k<<<dim3((sh.grid + P - 1) / P, P), 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
     return cudaGetLastError();
   };
-  return P > 1 ? go(std::integral_constant<int, 3>{}) : go(std::integral_constant<int, 8>{});
+  return P > 1 ? go(std::integral_constant<int, 2>{}) : go(std::integral_constant<int, 8>{});
 }
 
 bool use_partition(bs_handle h, int64_t M, int vec);

@@ -94,8 +94,11 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
     double acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) acc[v] = 0.0;
-    for (int64_t j = jlo + threadIdx.x; j < jhi; j += kGradThreads) {
-      double x[NX], g[kGradRows];
+    // rows i0 - H .. i0 + kGradRows - 1 + H of X and i0 .. of GB for system
+    // j; the next system's rows are requested before the current ones are
+    // used (two register sets), so each thread keeps one load batch in flight
+    // while its FMAs run
+    auto fetch = [&](int64_t j, double (&x)[NX], double (&g)[kGradRows]) {
 #pragma unroll
       for (int q = 0; q < NX; q++) {
         const int row = i0 - H + q;
@@ -111,10 +114,23 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
         const int row = i0 + r;
         g[r] = (row < N) ? load_wide(GB + row * rs + j * ss) : 0.0;
       }
+    };
+    auto accumulate = [&](const double (&x)[NX], const double (&g)[kGradRows]) {
 #pragma unroll
       for (int r = 0; r < kGradRows; r++)
 #pragma unroll
         for (int k = 0; k < W; k++) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
+    };
+    double xa[NX], ga[kGradRows], xb[NX], gb[kGradRows];
+    int64_t j = jlo + threadIdx.x;
+    if (j < jhi) fetch(j, xa, ga);
+    for (; j < jhi; j += 2 * kGradThreads) {
+      const int64_t j1 = j + kGradThreads;
+      if (j1 < jhi) fetch(j1, xb, gb);
+      accumulate(xa, ga);
+      if (j1 >= jhi) break;
+      if (j1 + kGradThreads < jhi) fetch(j1 + kGradThreads, xa, ga);
+      accumulate(xb, gb);
     }
     // Warp reduce-scatter over the NV values (padded to 64): at each level a
     // lane keeps one half, sends the other to its partner and adds what it

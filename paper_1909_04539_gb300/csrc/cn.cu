@@ -15,6 +15,8 @@
 // the explicit side wraps around (rows 0 and N-1 are kept from the start of
 // the step, before they are overwritten) and the Sherman-Morrison correction
 // of the solve is applied as in the plain periodic sweeps.
+#include <type_traits>
+
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -137,21 +139,31 @@ k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
 #pragma unroll
         for (int v = 0; v < V; v++) cur[u][v] = nxt[u][v];
     }
-    // backward sweep over the forward values, as in the plain solve
+    // backward sweep over the forward values, as in the plain solve, with the
+    // next block's loads issued before the current block is computed
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
-    for (int top = N - 1; top >= 0; top -= U) {
+    auto load_bwd = [&](C (&blk)[U][V], int top) {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (top - u >= 0) load(blk[u], top - u);
+    };
+    auto run_bwd = [&](C (&blk)[U][V], int top) {
       const int n = (top + 1) < U ? (top + 1) : U;
-      C b[U][V];
-#pragma unroll
-      for (int u = 0; u < U; u++)
-        if (u < n) load(b[u], top - u);
-      bwd_block<BW, false, C, V, U>(cf, top, n, b, r1, r2);
+      bwd_block<BW, false, C, V, U>(cf, top, n, blk, r1, r2);
       if constexpr (PER)
-        if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, b, sig);
+        if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, blk, sig);
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (u < n) IO<C, C, V>::store(px + (int64_t)(top - u) * M, b[u]);
+        if (u < n) IO<C, C, V>::store(px + (int64_t)(top - u) * M, blk[u]);
+    };
+    load_bwd(cur, N - 1);
+    for (int top = N - 1; top >= 0; top -= 2 * U) {
+      if (top - U >= 0) load_bwd(nxt, top - U);
+      run_bwd(cur, top);
+      if (top - U < 0) break;
+      if (top - 2 * U >= 0) load_bwd(cur, top - 2 * U);
+      run_bwd(nxt, top - U);
     }
   }
 }
@@ -190,13 +202,28 @@ static cudaError_t cn_dispatch(bs_handle h, C* X, int64_t M, cudaStream_t st) {
     bands = reinterpret_cast<const C*>(h->bands64);
   else
     bands = reinterpret_cast<const C*>(h->bands_hi);
-  const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(X) % (VEC * sizeof(C)) == 0);
-  if (h->periodic)
-    return vec ? launch_cn<1, true, C, VEC>(p, bands, N, X, M, st) : launch_cn<1, true, C, 1>(p, bands, N, X, M, st);
-  if (h->width == 3)
-    return vec ? launch_cn<1, false, C, VEC>(p, bands, N, X, M, st)
-               : launch_cn<1, false, C, 1>(p, bands, N, X, M, st);
-  return vec ? launch_cn<2, false, C, VEC>(p, bands, N, X, M, st) : launch_cn<2, false, C, 1>(p, bands, N, X, M, st);
+  // systems per thread: the widest vector that still gives every SM at
+  // least 256 threads (the FP64 pipe and the loads need the warps more than
+  // the wide loads)
+  const int64_t want = (int64_t)device_info().sms * 256;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(X);
+  int v = 1;
+  if (M % VEC == 0 && a % (VEC * sizeof(C)) == 0 && M / VEC >= want)
+    v = VEC;
+  else if (M % 2 == 0 && a % (2 * sizeof(C)) == 0 && M / 2 >= want)
+    v = 2;
+  auto go = [&](auto bwt, auto pert) -> cudaError_t {
+    constexpr int BW = decltype(bwt)::value;
+    constexpr bool PER = decltype(pert)::value;
+    if (v == VEC) return launch_cn<BW, PER, C, VEC>(p, bands, N, X, M, st);
+    if (v == 2) return launch_cn<BW, PER, C, 2>(p, bands, N, X, M, st);
+    return launch_cn<BW, PER, C, 1>(p, bands, N, X, M, st);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  if (h->periodic) return go(I1{}, std::true_type{});
+  if (h->width == 3) return go(I1{}, std::false_type{});
+  return go(I2{}, std::false_type{});
 }
 
 }  // namespace bs
