@@ -60,7 +60,7 @@ KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
     "adjoint_f64": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
     "refine_solve": ["refine.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
-    "band_grad_f64": ["band_grad.cu", "sweep_kernels.cuh", "internal.h"],
+    "band_grad_f64": ["band_grad.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
 }
 
 

@@ -83,32 +83,36 @@ __device__ __forceinline__ float refine_resid_z(const RefineCoefs<BW>& cf, int q
 
 // Exact FP32 -> FP64 widening with integer operations only: on GB300 the
 // conversion instruction runs on the slow FP64 pipe, and a conditional
-// conversion for the rare cases is if-converted into every call.  Normal
-// numbers rebias the exponent and shift the mantissa; zero keeps its sign;
-// subnormals are normalised with a leading-zero count; inf and NaN map to
-// exponent 2047.
+// conversion for the rare cases is if-converted into every call.  A normal
+// number keeps its sign, its exponent is rebiased by 1023 - 127 = 896 and its
+// mantissa moves to the top of the 52-bit field: five integer operations.
+// Zero keeps its sign; a subnormal is normalised with a leading-zero count;
+// inf and NaN map to exponent 2047.  Those cases are rare, so they run behind
+// a branch that the warp takes only if one of its active lanes needs it.
 __device__ __forceinline__ double widen_exact(float f) {
   const uint32_t b = __float_as_uint(f);
-  const uint32_t sign = b & 0x80000000u;
   const uint32_t e = (b >> 23) & 0xffu;
-  const uint32_t m = b & 0x7fffffu;
-  // normal: exponent e - 127 + 1023, mantissa m << 29
-  uint32_t hi = sign | ((e + 896u) << 20) | (m >> 3);
-  uint32_t lo = m << 29;
-  // subnormal: m * 2^-149 = 1.f * 2^(p - 149), p = index of the top set bit
-  const int p = 31 - __clz((int)(m | 1u));
-  const uint32_t shifted = (m << (23 - p)) & 0x7fffffu;  // drop the leading 1
-  const uint32_t hs = sign | ((uint32_t)(p + 874) << 20) | (shifted >> 3);
-  const uint32_t ls = shifted << 29;
-  const bool sub = (e == 0u) & (m != 0u);
-  hi = sub ? hs : hi;
-  lo = sub ? ls : lo;
-  const bool zero = (e == 0u) & (m == 0u);
-  hi = zero ? sign : hi;
-  lo = zero ? 0u : lo;
-  const bool special = e == 0xffu;  // inf / NaN
-  hi = special ? (sign | 0x7ff00000u | (m >> 3)) : hi;
-  lo = special ? (m << 29) : lo;
+  uint32_t hi = (((b & 0x7fffffffu) >> 3) + (896u << 20)) | (b & 0x80000000u);
+  uint32_t lo = b << 29;
+  const bool normal = (e - 1u) < 254u;
+  if (__any_sync(__activemask(), !normal)) {
+    if (!normal) {
+      const uint32_t sign = b & 0x80000000u;
+      const uint32_t m = b & 0x7fffffu;
+      if (e == 0xffu) {  // inf / NaN
+        hi = sign | 0x7ff00000u | (m >> 3);
+        lo = m << 29;
+      } else if (m == 0u) {  // zero
+        hi = sign;
+        lo = 0u;
+      } else {  // subnormal: m * 2^-149 = 1.f * 2^(p - 149), p = index of the top set bit
+        const int p = 31 - __clz((int)m);
+        const uint32_t shifted = (m << (23 - p)) & 0x7fffffu;  // drop the leading 1
+        hi = sign | ((uint32_t)(p + 874) << 20) | (shifted >> 3);
+        lo = shifted << 29;
+      }
+    }
+  }
   return __hiloint2double((int)hi, (int)lo);
 }
 

@@ -90,3 +90,25 @@ def test_refine_rejects_bad_arguments(bs):
         bs.solve_refine(f, B, mode=7)
     with pytest.raises(ValueError):
         bs.solve_refine(f, B.double())
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["factor", "system"])
+def test_refine_zero_tiny_and_huge_columns(bs, mode):
+    """Columns that are all zero must come back as exact (signed) zeros; a
+    column scaled to 1e-20 and one scaled to 1e30 keep the relative accuracy
+    (the FP64 result is assembled from FP32 parts by exact integer widening,
+    whose zero and special-value cases run behind a rare branch)."""
+    N, M = 300, 64
+    bands = _bands(3, N, 4)
+    rng = np.random.default_rng(9)
+    Bh = rng.uniform(-1, 1, (N, M)).astype(np.float32)
+    Bh[:, 3] = 0.0
+    Bh[:, 5] = -0.0
+    Bh[:, 7] *= np.float32(1e-20)
+    Bh[:, 9] *= np.float32(1e30)
+    f = bs.Factor(bands)
+    X = bs.solve_refine(f, torch.tensor(Bh, device="cuda"), mode=mode).cpu().numpy()
+    assert np.all(X[:, 3] == 0.0) and np.all(X[:, 5] == 0.0)
+    ref = oracle.solve(bands, Bh.astype(np.float64))
+    for j in (0, 7, 9):
+        assert rel_l2(X[:, j], ref[:, j]) < 1e-12, j
