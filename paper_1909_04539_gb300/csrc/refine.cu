@@ -301,14 +301,18 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
     double* px = X + j;
     float2* ps = reinterpret_cast<float2*>(X) + j;
 
-    // ---- pass 1 (rows up): slot <- (w, delta)
+    // ---- pass 1 (rows up): slot <- (w, delta).  Row addresses advance by
+    // pointer increments (no 64-bit multiply per row).
     {
       float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
+      const float* pnext = pb;  // next row to request
 #pragma unroll 1
       for (int r = 0; r < D; r++) {
-        if (r < N) cp_async4(ring_s + r * pitch, pb + (int64_t)r * M);
+        if (r < N) cp_async4(ring_s + r * pitch, pnext);
+        pnext += M;
         cp_commit();
       }
+      float2* prow = ps;  // slot of row i0
 #pragma unroll 1
       for (int i0 = 0; i0 < N; i0 += kRU) {
         cp_wait<D - kRU>();
@@ -319,25 +323,30 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
         for (int u = 0; u < kRU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          if (u < n && i0 + u + D < N) cp_async4(ring_s + (s0 + u) * pitch, pb + (int64_t)(i0 + u + D) * M);
+          if (u < n && i0 + u + D < N) cp_async4(ring_s + (s0 + u) * pitch, pnext);
+          pnext += M;
           cp_commit();
         }
         frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
 #pragma unroll
-        for (int u = 0; u < kRU; u++)
-          if (u < n) ps[(int64_t)(i0 + u) * M] = make_float2(w[u], d[u]);
+        for (int u = 0; u < kRU; u++) {
+          if (u < n) *prow = make_float2(w[u], d[u]);
+          prow += M;
+        }
       }
       cp_wait<0>();
     }
     // ---- pass 2 (rows down): X
     {
       float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
+      const float2* pback = ps + (int64_t)(N - 1) * M;  // next slot row to request
 #pragma unroll 1
       for (int r = 0; r < D; r++) {
-        const int row = N - 1 - r;
-        if (row >= 0) cp_async8(ring_s + r * pitch, ps + (int64_t)row * M);
+        if (N - 1 - r >= 0) cp_async8(ring_s + r * pitch, pback);
+        pback -= M;
         cp_commit();
       }
+      double* pout = px + (int64_t)(N - 1) * M;  // output row `top`
 #pragma unroll 1
       for (int top = N - 1; top >= 0; top -= kRU) {
         cp_wait<D - kRU>();
@@ -353,14 +362,16 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
         }
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          const int i = top - u;
-          if (u < n && i - D >= 0) cp_async8(ring_s + (s0 + u) * pitch, ps + (int64_t)(i - D) * M);
+          if (u < n && top - u - D >= 0) cp_async8(ring_s + (s0 + u) * pitch, pback);
+          pback -= M;
           cp_commit();
         }
         frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
 #pragma unroll
-        for (int u = 0; u < kRU; u++)
-          if (u < n) px[(int64_t)(top - u) * M] = xo[u];
+        for (int u = 0; u < kRU; u++) {
+          if (u < n) *pout = xo[u];
+          pout -= M;
+        }
       }
       cp_wait<0>();
     }

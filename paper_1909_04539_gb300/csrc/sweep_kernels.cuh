@@ -624,8 +624,9 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
   constexpr int U = 8;
   const int64_t groups = M / V;
   if constexpr (V > 1) {
-    // pipelined kernel: ring of kRingRows 16-byte slots per lane
-    constexpr int D = 16;
+    // pipelined kernel: ring of D 16-byte slots per lane; the FP32 sweeps are
+    // bound by memory latency, so they keep twice the rows in flight
+    constexpr int D = sizeof(C) == 4 ? 32 : 16;
     const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
     const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
     const dim3 grid((sh.grid + P - 1) / P, P);
