@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
     # likewise (the accuracy-check launch, same kernel and batch)
     "f64_solve": {"bytes": 472688128 + 432523264, "sha": "5fc8ddccf0627042"},
     "adjoint_f64": {"bytes": 459128576 + 426641664, "sha": "5fc8ddccf0627042"},
-    "refine_solve": {"bytes": 356136704 + 439495168, "sha": "50e6f54d16641a56"},
+    "refine_solve": {"bytes": 352089088 + 436296448, "sha": "df305083846c0b9f"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
