@@ -623,7 +623,7 @@ template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout, i
 cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
   constexpr int U = 8;
   const int64_t groups = M / V;
-  if constexpr (V > 1) {
+  if constexpr (V > 1 || sizeof(Sout) == 8) {
     // pipelined kernel: ring of D 16-byte slots per lane; the FP32 sweeps are
     // bound by memory latency, so they keep twice the rows in flight
     constexpr int D = sizeof(C) == 4 ? 32 : 16;
@@ -688,14 +688,16 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
   Coefs<C> cf = coefs_of<C>(base, N);
   cf.per_lo = p.per_lo;
   cf.per_hi = p.per_hi;
-  const bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
+  bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
                    (reinterpret_cast<uintptr_t>(out) % (VEC * sizeof(Sout)) == 0);
   // FP32 with few systems per SM: half-width vectors (8-byte lane rows) give
   // twice the warps to hide the latency of the recurrences
   constexpr bool kHalf = std::is_same<Sin, float>::value && VEC == 4;
+  const bool few = M / VEC * P < (int64_t)device_info().sms * 32 * 8;
   const bool half = kHalf && (M % 2 == 0) && (reinterpret_cast<uintptr_t>(in) % 8 == 0) &&
-                    (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
-                    (M / VEC * P < (int64_t)device_info().sms * 32 * 8);
+                    (reinterpret_cast<uintptr_t>(out) % 8 == 0) && few;
+  // FP64 with few systems per SM: one system per thread (twice the warps)
+  if (std::is_same<Sin, double>::value && few) vec = false;
 #define BS_DISPATCH(BWV, ADJV, PERV)                                                                        \
   if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, L, P, st);      \
   if constexpr (kHalf) {                                                                                    \
