@@ -159,8 +159,8 @@ constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padd
 // through a ring of K tiles in shared memory by cp.async -- each lane copies
 // its row of the chunk for the 34 systems it touches (its 32 plus one
 // neighbour each side) -- so K chunks are in flight while one is swept.  The
-// forward values leave through an output tile with coalesced stores and come
-// back through the same ring for the backward sweep.
+// forward values overwrite the swept tile, leave from it with coalesced
+// stores and come back through the same ring for the backward sweep.
 template <int BW, bool ADJ, bool SMEM, typename C, int K>
 __global__ void __launch_bounds__(32)
 k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r, int64_t ld, int L) {
@@ -178,7 +178,6 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
   const int lane = threadIdx.x;
   C* ringt = smc + (SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) / sizeof(C) : 0);
-  C* tout = ringt + K * kTile;
   auto cp = [&](C* dst, const C* src) {
     const uint32_t d = smem_u32(dst);
     if constexpr (sizeof(C) == 8)
@@ -214,27 +213,33 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       __syncwarp();
       const int c0 = c * kStRows;
       const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
-      const C* tin = ringt + (c % K) * kTile;
-      if (mine)
-        for (int q0 = 0; q0 < rows; q0 += U) {
-          const int n = (rows - q0) < U ? (rows - q0) : U;
-          C f[U][1];
+      // the forward values overwrite the tile's own entries (each block of U
+      // rows is read by every lane before any lane writes it)
+      C* tin = ringt + (c % K) * kTile;
+      for (int q0 = 0; q0 < rows; q0 += U) {
+        const int n = (rows - q0) < U ? (rows - q0) : U;
+        C f[U][1];
+        if (mine) {
 #pragma unroll
           for (int q = 0; q < U; q++) {
             const C* t = tin + (q0 + q) * kAdiTile + lane;
             f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
           }
+        }
+        __syncwarp();
+        if (mine) {
           fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
 #pragma unroll
           for (int q = 0; q < U; q++)
-            if (q < n) tout[(q0 + q) * kStPad + lane] = f[q][0];
+            if (q < n) tin[(q0 + q) * kAdiTile + lane + 1] = f[q][0];
         }
+      }
       __syncwarp();
-      if (c + K < nch) request_in(c + K);  // the tile just swept is free again
-      cp_commit();
       if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tout[lane * kStPad + s];
+        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tin[lane * kAdiTile + s + 1];
       __syncwarp();
+      if (c + K < nch) request_in(c + K);  // the tile is free again
+      cp_commit();
     }
     cp_wait<0>();
     __syncwarp();
@@ -312,7 +317,7 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   }
   auto go = [&](auto ktag) -> cudaError_t {
     constexpr int K = decltype(ktag)::value;
-    const size_t tiles = ((size_t)K * kStRows * kAdiTile + (size_t)kStRows * kStPad) * sizeof(C);
+    const size_t tiles = (size_t)K * kStRows * kAdiTile * sizeof(C);
     const int64_t threads = ((M + 31) / 32) * 32;
     const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32);
     auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K> : k_adi_st2<BW, ADJ, false, C, K>;
