@@ -26,30 +26,54 @@ __device__ __forceinline__ int part_top(int b, int L) { return b * L; }
 __device__ __forceinline__ int part_bot(int b, int L, int N) { return ((b + 1) * L < N ? (b + 1) * L : N) - 1; }
 
 // Step 2: one thread per system.  bt (R x M, row q of the reduced system at
-// bt[q * M + j]) receives the forward values, then the solution.
+// bt[q * M + j]) receives the forward values, then the solution.  Rows are
+// taken in groups of 8 whose loads are all issued before the group's
+// recurrence runs, so a thread waits for memory once per group.
 template <typename C>
 __global__ void __launch_bounds__(kPartThreads)
 k_part_reduced(Coefs<C> rc, int R, int L, int N, const C* __restrict__ X, int64_t rs, int64_t ss, int64_t M,
                C* __restrict__ bt) {
+  constexpr int G = 8;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
     C w1 = C(0), w2 = C(0);
-    for (int q = 0; q < R; q++) {
-      const int row = (q & 1) ? part_top(q / 2 + 1, L) : part_bot(q / 2, L, N);
-      C w = rc.s[q] * X[row * rs + j * ss];
-      w = fma(-rc.l2[q], w2, w);
-      w = fma(-rc.l1[q], w1, w);
-      w2 = w1;
-      w1 = w;
-      bt[q * M + j] = w;
+    for (int q0 = 0; q0 < R; q0 += G) {
+      C z[G];
+#pragma unroll
+      for (int u = 0; u < G; u++) {
+        const int q = q0 + u;
+        const int row = (q & 1) ? part_top(q / 2 + 1, L) : part_bot(q / 2, L, N);
+        z[u] = q < R ? X[row * rs + j * ss] : C(0);
+      }
+#pragma unroll
+      for (int u = 0; u < G; u++) {
+        const int q = q0 + u;
+        if (q < R) {
+          C w = rc.s[q] * z[u];
+          w = fma(-rc.l2[q], w2, w);
+          w = fma(-rc.l1[q], w1, w);
+          w2 = w1;
+          w1 = w;
+          bt[q * M + j] = w;
+        }
+      }
     }
     C x1 = C(0), x2 = C(0);
-    for (int q = R - 1; q >= 0; q--) {
-      C x = bt[q * M + j];
-      x = fma(-rc.u2[q], x2, x);
-      x = fma(-rc.u1[q], x1, x);
-      x2 = x1;
-      x1 = x;
-      bt[q * M + j] = x;
+    for (int q0 = R - 1; q0 >= 0; q0 -= G) {
+      C z[G];
+#pragma unroll
+      for (int u = 0; u < G; u++) z[u] = (q0 - u >= 0) ? bt[(q0 - u) * M + j] : C(0);
+#pragma unroll
+      for (int u = 0; u < G; u++) {
+        const int q = q0 - u;
+        if (q >= 0) {
+          C x = z[u];
+          x = fma(-rc.u2[q], x2, x);
+          x = fma(-rc.u1[q], x1, x);
+          x2 = x1;
+          x1 = x;
+          bt[q * M + j] = x;
+        }
+      }
     }
   }
 }
