@@ -50,10 +50,10 @@ NOMINAL_HBM_GBS = 8000.0
 # kernel sources hash to the value they had at capture time.
 NCU_TRAFFIC = {
     # one --set full capture of the kernel inside this benchmark's step
-    "band_grad_f64": {"bytes": 669353728 + 3254784, "sha": "c7b197ac3fc4ac2c"},
+    "band_grad_f64": {"bytes": 669718784 + 3322880, "sha": "cef8753477e7867f"},
     # likewise (the accuracy-check launch, same kernel and batch)
-    "f64_solve": {"bytes": 472688128 + 432523264, "sha": "5fc8ddccf0627042"},
-    "adjoint_f64": {"bytes": 459128576 + 426641664, "sha": "5fc8ddccf0627042"},
+    "f64_solve": {"bytes": 472481536 + 432248064, "sha": "5afb4b8a49d041db"},
+    "adjoint_f64": {"bytes": 471471104 + 432331008, "sha": "5afb4b8a49d041db"},
     "refine_solve": {"bytes": 352089088 + 436296448, "sha": "df305083846c0b9f"},
 }
 KERNEL_SOURCES = {
