@@ -41,7 +41,8 @@ N_ROWS, M_SYS, S_HYPER = 512, 65536, 0.1
 METRIC = "unknowns/s & HBM GB/s vs 8 TB/s at stated rel err; serving p50/p99 latency"
 WORKLOAD = ("penta A=I+0.1*D4 clamped, N=512, M=65536 RHS ~ N(0,1) per GPU, interleaved; "
             "step = FP64 solve + FP32-stored solve with one FP64-accurate refinement step + "
-            "FP64 adjoint solve + band-gradient reduction")
+            "FP64 adjoint solve + band-gradient reduction (FP64 solve, adjoint and band gradient in "
+            "order on a high-priority stream; the mixed-precision solve beside them on a low-priority one)")
 NOMINAL_HBM_GBS = 8000.0
 
 
@@ -235,19 +236,35 @@ def run_ours(args):
     del Xchk, X32chk, XRchk, B32d
 
     names = ["f64_solve", "refine_solve", "adjoint_f64", "band_grad_f64"]
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    # per step and path: a start and an end event on the path's own stream
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
+          for _ in range(args.steps)]
+    # The mixed-precision solve is independent of the FP64 chain (solve,
+    # adjoint, band gradient, which need the FP64 pipe) and mostly uses the
+    # FP32 and integer pipes, so it runs on a low-priority stream beside the
+    # chain, which runs in order on a high-priority stream.
+    lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+    s_chain = torch.cuda.Stream(priority=hi)
+    s_ref = torch.cuda.Stream(priority=lo)
+    fork = [torch.cuda.Event() for _ in range(2)]
+
+    def timed(e, q, stream, fn):
+        if e: e[q][0].record(stream)
+        fn()
+        if e: e[q][1].record(stream)
 
     def step(k=None):
         e = ev[k] if k is not None else None
-        if e: e[0].record(st)
-        bs.solve(f, X64)
-        if e: e[1].record(st)
-        bs.solve_refine(f, B32, XR)
-        if e: e[2].record(st)
-        bs.solve_adjoint(f, G)
-        if e: e[3].record(st)
-        bs.band_grad(f, G, X64, dbands=db)
-        if e: e[4].record(st)
+        fk = fork[(k or 0) % 2]
+        fk.record(st)
+        s_chain.wait_event(fk)
+        s_ref.wait_event(fk)
+        timed(e, 0, s_chain, lambda: bs.solve(f, X64, stream=s_chain))
+        timed(e, 2, s_chain, lambda: bs.solve_adjoint(f, G, stream=s_chain))
+        timed(e, 3, s_chain, lambda: bs.band_grad(f, G, X64, dbands=db, stream=s_chain))
+        timed(e, 1, s_ref, lambda: bs.solve_refine(f, B32, XR, stream=s_ref))
+        st.wait_stream(s_chain)
+        st.wait_stream(s_ref)
 
     for _ in range(args.warmup):
         step()
@@ -271,10 +288,20 @@ def run_ours(args):
     per = {n: 0.0 for n in names}
     for k in range(args.steps):
         for q, n in enumerate(names):
-            per[n] += ev[k][q].elapsed_time(ev[k][q + 1]) / args.steps
+            per[n] += ev[k][q][0].elapsed_time(ev[k][q][1]) / args.steps
     ms_step = ms / args.steps
     units_step = 3 * N * M  # three solves of N*M unknowns each: FP64, mixed precision, adjoint
     value = job_value(units_step, world, ms_step)
+
+    # Each kernel of the step timed alone right after the timed region (same
+    # data and streams; the in-step durations of the concurrent kernels share
+    # the SMs, so the per-kernel rooflines use these)
+    alone = {
+        "f64_solve": time_alone(lambda: bs.solve(f, X64, stream=s_chain), s_chain, reps=20),
+        "refine_solve": time_alone(lambda: bs.solve_refine(f, B32, XR, stream=s_ref), s_ref, reps=20),
+        "adjoint_f64": time_alone(lambda: bs.solve_adjoint(f, G, stream=s_chain), s_chain, reps=20),
+        "band_grad_f64": time_alone(lambda: bs.band_grad(f, G, X64, dbands=db, stream=s_chain), s_chain, reps=20),
+    }
 
     peaks, peak_src = _peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -290,8 +317,9 @@ def run_ours(args):
     }
     for n, p in paths.items():
         p["ncu_dram_bytes"] = ncu_traffic(n)
-        t = per[n] * 1e-3
-        p["ms"] = round(per[n], 5)
+        t = alone[n] * 1e-3
+        p["ms"] = round(alone[n], 5)
+        p["in_step_ms"] = round(per[n], 5)
         p["unknowns_per_s"] = nm / t
         p["hbm_gbs"] = p["bytes"] / t / 1e9
         p["hbm_frac_of_measured"] = p["hbm_gbs"] / hbm
@@ -299,12 +327,17 @@ def run_ours(args):
         if "dp_instr" in p:
             p["fp64_tflops"] = p["flops"] / t / 1e12
             p["fp64_instr_frac_of_measured"] = p["dp_instr"] / t / fp64_fma
-    dom = max(paths, key=lambda n: per[n])
+    # the dominant kernel: the longest one timed alone
+    paths["refine_solve"]["stream"] = "low priority, concurrent with the FP64 chain"
+    dom = max(paths, key=lambda n: alone[n])
     dp = paths[dom]
     if dp["bound"] == "alu":
         roof = {"bound": "alu", "kernel": dom, "achieved": dp["fp64_tflops"], "peak": fp64_tflops,
                 "unit": "TFLOP/s", "frac": dp["fp64_tflops"] / fp64_tflops, "traffic": ncu_traffic(dom),
                 "algorithmic_bytes": dp["bytes"],
+                "timing": "the kernel timed alone (median of 20 launches, CUDA events on its stream) right "
+                          "after the timed region; inside the timed region the FP64 chain shares the SMs "
+                          "with the concurrent mixed-precision solve (paths[...].in_step_ms)",
                 "peak_source": "FP64 FMA rate measured live by bs_measure_fp64_rate (FMA = 2 flop)",
                 "algorithmic": {"f64_solve": "9 FP64 flop per unknown (forward MUL + 2 FMA, backward 2 FMA)",
                                 "adjoint_f64": "9 FP64 flop per unknown",

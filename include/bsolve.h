@@ -108,7 +108,11 @@ int64_t bs_lhs_bytes(int width, int64_t N, int elem_bytes);
  *   dtype BS_F32: B is float[N*M], FP32 arithmetic.
  *   dtype BS_BF16: not in place -- use bs_solve_bf16.
  * The intermediate forward-sweep values are kept in B itself between the two
- * sweeps.  M >= 1. */
+ * sweeps.  M >= 1.  A tridiagonal handle may solve a small batch
+ * row-partitioned (see BS_OPT_PARTITION): the result is the same to
+ * rounding, and the call then also allocates 2 (P - 1) x M values of
+ * stream-ordered scratch for the block-edge system.  A periodic handle
+ * (bs_factor_periodic) solves the cyclic system. */
 bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64_t M,
                    bs_stream stream);
 
