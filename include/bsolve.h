@@ -108,10 +108,10 @@ int64_t bs_lhs_bytes(int width, int64_t N, int elem_bytes);
  *   dtype BS_F32: B is float[N*M], FP32 arithmetic.
  *   dtype BS_BF16: not in place -- use bs_solve_bf16.
  * The intermediate forward-sweep values are kept in B itself between the two
- * sweeps.  M >= 1.  A tridiagonal handle may solve a small batch
- * row-partitioned (see BS_OPT_PARTITION): the result is the same to
- * rounding, and the call then also allocates 2 (P - 1) x M values of
- * stream-ordered scratch for the block-edge system.  A periodic handle
+ * sweeps.  M >= 1.  A small batch may be solved row-partitioned (see
+ * BS_OPT_PARTITION): the result is the same to rounding, and the call then
+ * also allocates 2h (P - 1) x M values of stream-ordered scratch for the
+ * block-edge system.  A periodic handle
  * (bs_factor_periodic) solves the cyclic system. */
 bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64_t M,
                    bs_stream stream);
@@ -306,16 +306,16 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    measured so far and kept as an option.
  *  BS_OPT_TMA_AHEAD: row chunks (32 rows each) the on-chip kernel keeps in
  *    flight ahead of its forward sweep (default 0: 4).
- *  BS_OPT_PARTITION: row-partitioned solves of a tridiagonal handle (not in
- *    the paper; for batches too small to fill the GPU one thread per
- *    system).  bs_factor prepares, for width 3 and N >= 256 when the matrix's
- *    spikes decay within a quarter of a block, a split of the rows into P
- *    blocks (P <= 32, blocks of >= 192 rows) for A and for A^T.  A solve then
- *    runs one thread per (system, block) on the matrix without the couplings
- *    across block edges, solves a pentadiagonal system of 2 (P - 1) block-edge
- *    values per system (factorised once with the handle), and corrects the
- *    rows near the block edges; the result is the same as the unpartitioned
- *    solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
+ *  BS_OPT_PARTITION: row-partitioned solves (not in the paper; for batches
+ *    too small to fill the GPU one thread per system).  bs_factor prepares,
+ *    for N >= 384 when the matrix's spikes decay within a quarter of a block,
+ *    a split of the rows into P blocks (2 <= P <= 32, blocks of >= 192 rows)
+ *    for A and for A^T.  A solve then runs one thread per (system, block) on
+ *    the matrix without its entries that couple different blocks, solves a
+ *    banded system of the 2h (P - 1) block-edge values per system (h = 1
+ *    tridiagonal, 2 pentadiagonal; its LU computed once with the handle), and
+ *    corrects the rows near the block edges; the result is the same as the
+ *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
  *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 128
  *    vector groups of systems per SM; 1: never; 2: whenever the handle has
  *    one. */

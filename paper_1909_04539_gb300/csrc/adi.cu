@@ -341,7 +341,8 @@ static bs_status dispatch_adi(bs_handle h, int N, const C* u, C* out, int64_t M,
     // row-partitioned: the primal-form plan of the block-diagonal part of
     // A (or A^T), then the block-edge correction on `out`
     const PartPlan& pp = h->part[adj ? 1 : 0];
-    e = launch_adi<1, false, C>(pp.blk, N, u, out, M, r, axis, pp.L, pp.P, st);
+    e = h->width == 3 ? launch_adi<1, false, C>(pp.blk, N, u, out, M, r, axis, pp.L, pp.P, st)
+                      : launch_adi<2, false, C>(pp.blk, N, u, out, M, r, axis, pp.L, pp.P, st);
     if (e != cudaSuccess) return cuda_error(e, "bs_adi_halfstep launch");
     return part_correct(pp, N, out, sizeof(C) == 8 ? BS_F64 : BS_F32, axis == 1 ? BS_INTERLEAVED : BS_STRIDED, M,
                         st);

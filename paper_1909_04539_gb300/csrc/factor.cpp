@@ -219,12 +219,10 @@ void free_handle(bs_handle h) {
   if (h->lu_hi) cudaFree(h->lu_hi);
   if (h->lu_lo) cudaFree(h->lu_lo);
   for (auto& pp : h->part) {
-    for (SweepPlan* sp : {&pp.blk, &pp.red}) {
-      if (sp->c64) cudaFree(sp->c64);
-      if (sp->c32) cudaFree(sp->c32);
-    }
-    if (pp.spk64) cudaFree(pp.spk64);
-    if (pp.spk32) cudaFree(pp.spk32);
+    if (pp.blk.c64) cudaFree(pp.blk.c64);
+    if (pp.blk.c32) cudaFree(pp.blk.c32);
+    for (void* ptr : {(void*)pp.spk64, (void*)pp.spk32, (void*)pp.red64, (void*)pp.red32})
+      if (ptr) cudaFree(ptr);
   }
   delete h;
 }
@@ -247,93 +245,145 @@ void apply_plan(const HostPlan& p, int64_t N, std::vector<double>& x) {
   }
 }
 
-// Host side of a row partition (see PartPlan) for the tridiagonal matrix with
-// bands a, b, c (outside entries ignored).
+// Host side of a row partition (see PartPlan) of the banded matrix with
+// half-width h = width / 2 given by its bands (outside entries ignored).
 struct HostPart {
-  int P = 0, L = 0, R = 0, kv = 0, kw = 0;
-  HostPlan blk, red;
-  std::vector<double> spk;  // 2N: V then W
+  int P = 0, L = 0, R = 0, kv = 0, kw = 0, h = 0, p = 0, q = 0;
+  HostPlan blk;
+  std::vector<double> spk;  // 2h x N: V_1 .. V_h, then W_1 .. W_h
+  std::vector<double> red;  // (p + q + 1) x R: reduced-system LU (see PartPlan)
 };
 
 // Rows per block at least this many; blocks at most kPartMax.
 constexpr int kPartMinRows = 192;
 constexpr int kPartMax = 32;
+constexpr int kPartMaxBand = 8;  // bandwidth limit of the reduced system
 
-bool make_partition(const double* a, const double* b, const double* c, int64_t N, HostPart& hp) {
+bool make_partition(const double* const* bd, int width, int64_t N, HostPart& hp) {
+  const int h = width / 2;
   int P = 1;
   while (P * 2 <= kPartMax && (int64_t)P * 2 * kPartMinRows <= N) P *= 2;
-  if (P < 4) return false;
+  if (P < 2) return false;
   const int64_t L = (N + P - 1) / P;
   P = (int)((N + L - 1) / L);
-  if (P < 4) return false;
+  if (P < 2) return false;
   auto top = [&](int k) { return (int64_t)k * L; };
   auto bot = [&](int k) { return std::min<int64_t>(N, (int64_t)(k + 1) * L) - 1; };
-  // block-diagonal matrix: the couplings across block edges removed
-  std::vector<double> mod((size_t)3 * N);
-  for (int64_t i = 0; i < N; i++) {
-    mod[i] = (i > 0) ? a[i] : 0.0;
-    mod[N + i] = b[i];
-    mod[2 * N + i] = (i + 1 < N) ? c[i] : 0.0;
-  }
-  for (int k = 0; k < P; k++) {
-    if (k > 0) mod[top(k)] = 0.0;
-    if (k < P - 1) mod[2 * N + bot(k)] = 0.0;
-  }
-  const double* bd[3] = {mod.data(), mod.data() + N, mod.data() + 2 * N};
+  auto blk_of = [&](int64_t i) { return (int)(i / L); };
+  // band k of row i as a matrix entry at column i + k - h (0 outside)
+  auto band = [&](int k, int64_t i) -> double {
+    const int64_t col = i + k - h;
+    return (col >= 0 && col < N) ? bd[k][i] : 0.0;
+  };
+  // block-diagonal matrix: every entry whose row and column lie in
+  // different blocks removed
+  std::vector<double> mod((size_t)width * N);
+  for (int k = 0; k < width; k++)
+    for (int64_t i = 0; i < N; i++) {
+      const int64_t col = i + k - h;
+      const bool inside = col >= 0 && col < N && blk_of(col) == blk_of(i);
+      mod[(size_t)k * N + i] = inside ? bd[k][i] : 0.0;
+    }
+  const double* mbd[5];
+  for (int k = 0; k < width; k++) mbd[k] = mod.data() + (size_t)k * N;
   HostPlan bq;
   hp.blk.c.assign((size_t)C_COUNT * N, 0.0);
   bq.c.assign((size_t)C_COUNT * N, 0.0);
-  if (make_plans(bd, 3, N, hp.blk, bq)) return false;
-  // spikes: V = A_blk^{-1} (sum_k a_top(k) e_top(k)), W likewise with c_bot(k)
-  std::vector<double> V(N, 0.0), W(N, 0.0);
-  for (int k = 1; k < P; k++) V[top(k)] = a[top(k)];
-  for (int k = 0; k < P - 1; k++) W[bot(k)] = c[bot(k)];
-  apply_plan(hp.blk, N, V);
-  apply_plan(hp.blk, N, W);
-  double vmax = 0.0, wmax = 0.0;
-  for (int64_t i = 0; i < N; i++) {
-    vmax = std::fmax(vmax, std::fabs(V[i]));
-    wmax = std::fmax(wmax, std::fabs(W[i]));
-  }
-  // each x_i gets at most two correction terms: entries below 2^-60 of the
-  // maximum change no result above rounding
-  const double tv = vmax * 0x1p-60, tw = wmax * 0x1p-60;
-  int64_t kv = 0, kw = 0;
-  for (int k = 0; k < P; k++)
-    for (int64_t i = top(k); i <= bot(k); i++) {
-      if (std::fabs(V[i]) <= tv) V[i] = 0.0;
-      if (std::fabs(W[i]) <= tw) W[i] = 0.0;
-      if (V[i] != 0.0) kv = std::max<int64_t>(kv, i - top(k) + 1);
-      if (W[i] != 0.0) kw = std::max<int64_t>(kw, bot(k) - i + 1);
+  if (make_plans(mbd, width, N, hp.blk, bq)) return false;
+  // spikes: V_m = A_blk^{-1} (the removed entries of column top - m, every
+  // block), W_m likewise for column bot + m
+  std::vector<std::vector<double>> V(h, std::vector<double>(N, 0.0)), W(h, std::vector<double>(N, 0.0));
+  for (int m = 1; m <= h; m++) {
+    for (int b = 0; b < P; b++) {
+      for (int64_t i = top(b); i < std::min<int64_t>(N, top(b) + h); i++) {
+        const int k = (int)(top(b) - m - i + h);
+        if (b > 0 && k >= 0 && k < width) V[m - 1][i] += band(k, i);
+      }
+      for (int64_t i = std::max<int64_t>(0, bot(b) - h + 1); i <= bot(b); i++) {
+        const int k = (int)(bot(b) + m - i + h);
+        if (b < P - 1 && k >= 0 && k < width) W[m - 1][i] += band(k, i);
+      }
     }
+    apply_plan(hp.blk, N, V[m - 1]);
+    apply_plan(hp.blk, N, W[m - 1]);
+  }
+  // entries below 2^-60 of a spike's maximum are dropped (each x_i gets at
+  // most 2h such terms, so nothing changes above rounding)
+  int64_t kv = 0, kw = 0;
+  for (auto* set : {&V, &W})
+    for (auto& vec : *set) {
+      double mx = 0.0;
+      for (double v : vec) mx = std::fmax(mx, std::fabs(v));
+      for (double& v : vec)
+        if (std::fabs(v) <= mx * 0x1p-60) v = 0.0;
+    }
+  for (int b = 0; b < P; b++)
+    for (int64_t i = top(b); i <= bot(b); i++)
+      for (int m = 0; m < h; m++) {
+        if (V[m][i] != 0.0) kv = std::max<int64_t>(kv, i - top(b) + 1);
+        if (W[m][i] != 0.0) kw = std::max<int64_t>(kw, bot(b) - i + 1);
+      }
   // the correction is meant to touch a small part of each block
   if (kv + kw > L / 2) return false;
-  // reduced system, unknowns (x_bot(b), x_top(b+1)) for b = 0..P-2,
-  // bands at columns -2..+2 of each row
-  const int R = 2 * (P - 1);
-  std::vector<double> rb((size_t)5 * R, 0.0);
-  for (int q = 0; q < P - 1; q++) {
-    const int r0 = 2 * q, r1 = 2 * q + 1;
-    rb[0 * R + r0] = V[bot(q)];      // x_bot(q-1), column r0 - 2
-    rb[2 * R + r0] = 1.0;
-    rb[3 * R + r0] = W[bot(q)];      // x_top(q+1), column r0 + 1
-    rb[1 * R + r1] = V[top(q + 1)];  // x_bot(q), column r1 - 1
-    rb[2 * R + r1] = 1.0;
-    rb[4 * R + r1] = W[top(q + 1)];  // x_top(q+2), column r1 + 2
+  // Reduced system: per block edge b the unknowns x at rows bot(b)-h+1 ..
+  // bot(b) and top(b+1) .. top(b+1)+h-1 (in row order), z index 2h b + t.
+  // Row r of block k: x_r + sum_m V_m(r) x_{top(k)-m} + sum_m W_m(r) x_{bot(k)+m} = y_r.
+  const int R = 2 * h * (P - 1);
+  auto zrow = [&](int zi) -> int64_t {
+    const int b = zi / (2 * h), t = zi % (2 * h);
+    return t < h ? bot(b) - h + 1 + t : top(b + 1) + (t - h);
+  };
+  std::vector<double> A((size_t)R * R, 0.0);
+  for (int zi = 0; zi < R; zi++) {
+    const int64_t r = zrow(zi);
+    const int k = blk_of(r);
+    A[(size_t)zi * R + zi] = 1.0;
+    for (int m = 1; m <= h; m++) {
+      if (k >= 1) A[(size_t)zi * R + (2 * h * (k - 1) + h - m)] += V[m - 1][r];
+      if (k <= P - 2) A[(size_t)zi * R + (2 * h * k + h + m - 1)] += W[m - 1][r];
+    }
   }
-  const double* rbd[5] = {rb.data(), rb.data() + R, rb.data() + 2 * R, rb.data() + 3 * R, rb.data() + 4 * R};
-  HostPlan rq;
-  hp.red.c.assign((size_t)C_COUNT * R, 0.0);
-  rq.c.assign((size_t)C_COUNT * R, 0.0);
-  if (make_plans(rbd, 5, R, hp.red, rq)) return false;
+  int pl = 0, qu = 0;  // lower and upper bandwidth
+  for (int i = 0; i < R; i++)
+    for (int j = 0; j < R; j++)
+      if (A[(size_t)i * R + j] != 0.0) {
+        pl = std::max(pl, i - j);
+        qu = std::max(qu, j - i);
+      }
+  if (pl > kPartMaxBand || qu > kPartMaxBand) return false;
+  // LU without pivoting (the fill stays inside the band)
+  for (int c = 0; c < R; c++) {
+    const double piv = A[(size_t)c * R + c];
+    if (bad(piv)) return false;
+    for (int i = c + 1; i <= std::min(R - 1, c + pl); i++) {
+      const double l = A[(size_t)i * R + c] / piv;
+      A[(size_t)i * R + c] = l;
+      for (int j = c + 1; j <= std::min(R - 1, c + qu); j++) A[(size_t)i * R + j] -= l * A[(size_t)c * R + j];
+    }
+  }
+  // layout: [0, p): L multipliers of columns i-1 .. i-p; [p]: 1 / U_ii;
+  // [p+1, p+q+1): U entries of columns i+1 .. i+q
+  hp.red.assign((size_t)(pl + qu + 1) * R, 0.0);
+  for (int i = 0; i < R; i++) {
+    for (int k = 1; k <= pl; k++)
+      if (i - k >= 0) hp.red[(size_t)(k - 1) * R + i] = A[(size_t)i * R + (i - k)];
+    hp.red[(size_t)pl * R + i] = 1.0 / A[(size_t)i * R + i];
+    for (int k = 1; k <= qu; k++)
+      if (i + k < R) hp.red[(size_t)(pl + k) * R + i] = A[(size_t)i * R + (i + k)];
+  }
   hp.P = P;
   hp.L = (int)L;
   hp.R = R;
   hp.kv = (int)kv;
   hp.kw = (int)kw;
-  hp.spk.resize((size_t)2 * N);
-  std::copy(V.begin(), V.end(), hp.spk.begin());
-  std::copy(W.begin(), W.end(), hp.spk.begin() + N);
+  hp.h = h;
+  hp.p = pl;
+  hp.q = qu;
+  hp.spk.assign((size_t)2 * h * N, 0.0);
+  for (int m = 0; m < h; m++) {
+    std::copy(V[m].begin(), V[m].end(), hp.spk.begin() + (size_t)m * N);
+    std::copy(W[m].begin(), W[m].end(), hp.spk.begin() + (size_t)(h + m) * N);
+  }
   return true;
 }
 
@@ -360,16 +410,21 @@ cudaError_t upload_part(const HostPart& hp, PartPlan& pp, size_t& bytes) {
   pp.R = hp.R;
   pp.kv = hp.kv;
   pp.kw = hp.kw;
+  pp.h = hp.h;
+  pp.p = hp.p;
+  pp.q = hp.q;
   cudaError_t e = upload_plan(hp.blk, pp.blk, bytes);
-  if (e == cudaSuccess) e = upload_plan(hp.red, pp.red, bytes);
-  std::vector<float> s32(hp.spk.size());
-  for (size_t q = 0; q < s32.size(); q++) s32[q] = (float)hp.spk[q];
-  if (e == cudaSuccess) e = cudaMalloc(&pp.spk64, sizeof(double) * hp.spk.size());
-  if (e == cudaSuccess) e = cudaMalloc(&pp.spk32, sizeof(float) * s32.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(pp.spk64, hp.spk.data(), sizeof(double) * hp.spk.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(pp.spk32, s32.data(), sizeof(float) * s32.size(), cudaMemcpyHostToDevice);
-  bytes += (sizeof(double) + sizeof(float)) * hp.spk.size();
+  auto up = [&](const std::vector<double>& v, double** d64, float** d32) {
+    std::vector<float> v32(v.size());
+    for (size_t i = 0; i < v.size(); i++) v32[i] = (float)v[i];
+    if (e == cudaSuccess) e = cudaMalloc(d64, sizeof(double) * v.size());
+    if (e == cudaSuccess) e = cudaMalloc(d32, sizeof(float) * v.size());
+    if (e == cudaSuccess) e = cudaMemcpy(*d64, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(*d32, v32.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice);
+    bytes += (sizeof(double) + sizeof(float)) * v.size();
+  };
+  up(hp.spk, &pp.spk64, &pp.spk32);
+  up(hp.red, &pp.red64, &pp.red32);
   return e;
 }
 
@@ -508,17 +563,17 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
       const int64_t col = i + k - h;
       b64[(size_t)k * N + i] = (col >= 0 && col < N) ? bd[k][i] : 0.0;
     }
-  // row partitions of A and of A^T for small batches (tridiagonal only)
+  // row partitions of A and of A^T for small batches
   HostPart parts[2];
-  bool has_part = false;
-  if (width == 3) {
-    std::vector<double> at(N, 0.0), ct(N, 0.0);  // bands of A^T: c_{i-1}, b_i, a_{i+1}
+  std::vector<double> tb((size_t)width * N, 0.0);  // bands of A^T: band k of row i = band w-1-k of row i+k-h
+  for (int k = 0; k < width; k++)
     for (int64_t i = 0; i < N; i++) {
-      at[i] = (i > 0) ? bd[2][i - 1] : 0.0;
-      ct[i] = (i + 1 < N) ? bd[0][i + 1] : 0.0;
+      const int64_t r = i + k - h;
+      if (r >= 0 && r < N) tb[(size_t)k * N + i] = bd[width - 1 - k][r];
     }
-    has_part = make_partition(bd[0], bd[1], bd[2], N, parts[0]) && make_partition(at.data(), bd[1], ct.data(), N, parts[1]);
-  }
+  const double* tbd[5];
+  for (int k = 0; k < width; k++) tbd[k] = tb.data() + (size_t)k * N;
+  const bool has_part = make_partition(bd, width, N, parts[0]) && make_partition(tbd, width, N, parts[1]);
   return upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
 }
 

@@ -61,24 +61,26 @@ BS_HD inline Coefs<C> coefs_of(const C* base, int64_t N) {
 }  // namespace bs
 
 namespace bs {
-// Row-partitioned solve of a tridiagonal matrix for batches too small to fill
-// the GPU one thread per system (e.g. the 4096 lines of an ADI half-step).
-// Rows are cut into P blocks of L rows (the last may be shorter).  With
-// A_blk = A with the couplings between blocks removed, y = A_blk^{-1} d is
-// solved with one thread per (system, block); then
-//   x = y - V x_{top-1} - W x_{bot+1}   inside each block,
-// V = A_k^{-1} (a_top e_1), W = A_k^{-1} (c_bot e_L) the block's spikes (one
-// copy: the LHS is shared).  The values at the block ends follow from a
-// pentadiagonal reduced system of R = 2 (P - 1) unknowns
-// (x_bot of block b, x_top of block b + 1), factorised once, and the
+// Row-partitioned solve of a banded matrix (half-width h = 1 or 2) for
+// batches too small to fill the GPU one thread per system (e.g. the 4096
+// lines of an ADI half-step).  Rows are cut into P blocks of L rows (the last
+// may be shorter).  With A_blk = A without its entries that couple different
+// blocks, y = A_blk^{-1} d is solved with one thread per (system, block);
+// then inside block k
+//   x = y - sum_m V_m x_{top-m} - sum_m W_m x_{bot+m}     (m = 1 .. h),
+// V_m, W_m the block's spikes (one copy: the LHS is shared).  The 2h values
+// at each block edge, z = (x_{bot(0)-h+1} .. x_{bot(0)}, x_{top(1)} ..
+// x_{top(1)+h-1}, ...), R = 2h (P - 1) of them, solve a banded reduced system
+// factorised once (LU without pivoting, lower bandwidth p, upper q), and the
 // correction touches only the first kv and last kw rows of a block (spike
-// entries below 2^-60 of their maximum / N are zero).
+// entries below 2^-60 of their maximum are zero).
 struct PartPlan {
-  int P, L, R, kv, kw;
+  int P, L, R, kv, kw, h, p, q;
   SweepPlan blk;   // block-diagonal plan, C_COUNT x N
-  double* spk64;   // 2 x N: V then W
+  double* spk64;   // 2h x N: V_1 .. V_h, then W_1 .. W_h
   float* spk32;
-  SweepPlan red;   // reduced system, C_COUNT x R (pentadiagonal)
+  double* red64;   // (p + q + 1) x R: row i of the LU at [k * R + i]: k < p the
+  float* red32;    // multiplier of column i-1-k, k = p 1 / U_ii, k > p U_{i, i+k-p}
 };
 }  // namespace bs
 

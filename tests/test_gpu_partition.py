@@ -1,6 +1,7 @@
-"""GPU parity of the row-partitioned tridiagonal solves (blocks of rows per
-thread, a reduced system for the block-edge values, a correction near the
-edges) against the CPU FP64 oracle, through the C ABI.  The partition is
+"""GPU parity of the row-partitioned solves, tridiagonal and pentadiagonal
+(blocks of rows per thread, a banded reduced system for the block-edge
+values, a correction near the edges) against the CPU FP64 oracle, through the
+C ABI.  The partition is
 forced with OPT_PARTITION = 2 (it is otherwise used automatically for small
 batches); tolerances as for the plain solves: FP64 1e-12 relative L2, FP32
 and BF16-stored 2e-5.  The partitioned and unpartitioned FP64 results must
@@ -38,14 +39,19 @@ def _run(bs, f, Bh, dtype, layout, mode):
     return B.double().cpu().numpy()
 
 
-SHAPES = [(768, 1), (768, 7), (1000, 64), (4096, 130), (5000, 33), (4096, 2048)]
+SHAPES = [(3, 400, 3), (3, 768, 1), (3, 768, 7), (3, 1000, 64), (3, 4096, 130), (3, 5000, 33), (3, 4096, 2048),
+          (5, 384, 5), (5, 512, 64), (5, 777, 33), (5, 4096, 300)]
+
+
+def _bands(width, N, rng):
+    return synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
 
 
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
-@pytest.mark.parametrize("N,M", SHAPES)
-def test_partitioned_fp64(bs, N, M, layout):
+@pytest.mark.parametrize("width,N,M", SHAPES)
+def test_partitioned_fp64(bs, width, N, M, layout):
     rng = np.random.default_rng(N + 3 * M)
-    bands = synth.random_tri_bands(N, rng)
+    bands = _bands(width, N, rng)
     B = rng.uniform(-1, 1, (N, M))
     Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
     f = bs.Factor(bands)
@@ -57,10 +63,10 @@ def test_partitioned_fp64(bs, N, M, layout):
 
 
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
-@pytest.mark.parametrize("N,M", [(768, 5), (4096, 130), (5000, 1024)])
-def test_partitioned_fp32(bs, N, M, layout):
+@pytest.mark.parametrize("width,N,M", [(3, 768, 5), (3, 4096, 130), (3, 5000, 1024), (5, 512, 4096), (5, 2000, 77)])
+def test_partitioned_fp32(bs, width, N, M, layout):
     rng = np.random.default_rng(N + 5 * M)
-    bands = synth.random_tri_bands(N, rng)
+    bands = _bands(width, N, rng)
     B = rng.uniform(-1, 1, (N, M)).astype(np.float32).astype(np.float64)
     Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
     f = bs.Factor(bands)
@@ -85,11 +91,12 @@ def test_partitioned_bf16(bs):
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
-def test_partitioned_adjoint_and_band_grad(bs, layout, dtype, tol):
+@pytest.mark.parametrize("width", [3, 5])
+def test_partitioned_adjoint_and_band_grad(bs, width, layout, dtype, tol):
     """Non-symmetric bands, so A^T's partition differs from A's."""
     N, M = 2000, 300
     rng = np.random.default_rng(31)
-    bands = synth.random_tri_bands(N, rng)
+    bands = _bands(width, N, rng)
     B = rng.uniform(-1, 1, (N, M))
     Gm = rng.uniform(-1, 1, (N, M))
     if dtype == torch.float32:
@@ -109,7 +116,7 @@ def test_partitioned_adjoint_and_band_grad(bs, layout, dtype, tol):
     assert rel_l2(X.double().cpu().numpy(), oracle.solve(bands, tr(B), layout)) < tol
     GB_ref = oracle.solve_adjoint(bands, tr(Gm), layout)
     assert rel_l2(G.double().cpu().numpy(), GB_ref) < tol
-    db_ref = oracle.band_grad(3, G.double().cpu().numpy(), X.double().cpu().numpy(), layout)
+    db_ref = oracle.band_grad(width, G.double().cpu().numpy(), X.double().cpu().numpy(), layout)
     err = np.max(np.abs(db.cpu().numpy() - db_ref)) / np.max(np.abs(db_ref))
     assert err < (1e-13 if dtype == torch.float64 else 1e-6)
 
@@ -153,3 +160,38 @@ def test_no_partition_without_decay(bs):
     Xu = _run(bs, f, Bh, torch.float64, "interleaved", 1)
     assert np.array_equal(X, Xu)
     assert rel_l2(X, oracle.solve(bands, Bh)) < 1e-9  # condition number ~1e7
+
+
+def test_partitioned_clamped_hyperdiffusion_fp32(bs):
+    """The clamped I + 0.1 D4 matrix at N = 512 splits into two blocks; the
+    FP32 solve of 65536 systems runs partitioned by default."""
+    N, M = 512, 65536
+    bands = synth.clamped_hyperdiffusion_bands(N, 0.1)
+    f = bs.Factor(bands)
+    B = synth.normal_rhs(N, M, 3, "cuda").float()
+    cols = np.random.default_rng(2).choice(M, 128, replace=False)
+    Bs = B[:, cols].double().cpu().numpy()
+    X = B.clone()
+    bs.solve(f, X)
+    Xu = _run(bs, f, B.cpu().numpy(), torch.float32, "interleaved", 1)
+    ref = oracle.solve(bands, Bs)
+    assert rel_l2(X[:, cols].double().cpu().numpy(), ref) < TOL32
+    assert rel_l2(X.double().cpu().numpy(), Xu) < 1e-6
+
+
+def test_partitioned_penta_adi(bs):
+    """An ADI half-step whose implicit operator is pentadiagonal (I + s D2^2
+    along the implicit axis) runs partitioned; same result as unpartitioned."""
+    n = 1024
+    s = 0.3
+    bands = synth.toeplitz_bands(n, (s, -4 * s, 1 + 6 * s, -4 * s, s))
+    f = bs.Factor(bands)
+    u = synth.adi_field(n, 7, "cuda", torch.float64)
+    outs = {}
+    for mode in (2, 1):
+        bs.set_option(bs.OPT_PARTITION, mode)
+        try:
+            outs[mode] = bs.adi_halfstep(f, u, 0.5, 1).cpu().numpy()
+        finally:
+            bs.set_option(bs.OPT_PARTITION, 0)
+    assert rel_l2(outs[2], outs[1]) < 1e-13
