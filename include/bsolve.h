@@ -254,7 +254,7 @@ bs_status bs_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype dtyp
  * Batches overlap across streams; requests arriving meanwhile join the next
  * batch as soon as memory and a stream are free.  A request's result is
  * bitwise the same whatever else shares its batch (one lane per system, the
- * arithmetic of the standalone solves).
+ * arithmetic of the standalone one-thread-per-system solves).
  * Request states: 0 queued, 1 running, 2 done, 3 cancelled, 4 failed.
  * Latency = host submission to host-observed completion.
  * ---------------------------------------------------------------------- */

@@ -1,7 +1,8 @@
 """Request server: results against the oracle and bitwise against the direct
-solves, the same whether a request runs alone or in a mix, admission under a
-small HBM budget, and host-side failure handling (oversized request,
-cancellation, a request that fails at admission, wait time-outs)."""
+(unpartitioned) solves, the same whether a request runs alone or in a mix,
+admission under a small HBM budget, and host-side failure handling
+(oversized request, cancellation, a request that fails at admission, wait
+time-outs)."""
 import numpy as np
 import pytest
 import torch
@@ -63,13 +64,18 @@ def test_mix_equals_alone_and_direct(bs, serve):
         r2 = srv.submit(facs[k], B2, X2, mode)
         assert srv.wait(r2, 60) == "done"
         assert torch.equal(X, X2), "result depends on the batch"
-        # bitwise equal to the direct API, and right against the oracle
-        if mode == 0:
-            D = B.cuda()
-            bs.solve(facs[k], D)
-        else:
-            D = bs.solve_refine(facs[k], B.cuda())
-        torch.cuda.synchronize()
+        # bitwise equal to the direct API's one-thread-per-system solve (a
+        # small direct batch may otherwise run row-partitioned, equal to
+        # rounding), and right against the oracle
+        bs.set_option(bs.OPT_PARTITION, 1)
+        try:
+            if mode == 0:
+                D = bs.solve(facs[k], B.cuda())
+            else:
+                D = bs.solve_refine(facs[k], B.cuda())
+            torch.cuda.synchronize()
+        finally:
+            bs.set_option(bs.OPT_PARTITION, 0)
         assert torch.equal(D.cpu(), X)  # same per-system arithmetic as the direct solves
         ref = oracle.solve(specs[k].bands, B.double().numpy())
         assert rel_l2(X.numpy(), ref) < 1e-12
