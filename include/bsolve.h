@@ -316,9 +316,8 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    tridiagonal, 2 pentadiagonal; its LU computed once with the handle), and
  *    corrects the rows near the block edges; the result is the same as the
  *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
- *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 128
- *    vector groups of systems per SM; 1: never; 2: whenever the handle has
- *    one. */
+ *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 256
+ *    systems per SM; 1: never; 2: whenever the handle has one. */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,

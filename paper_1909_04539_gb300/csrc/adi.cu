@@ -329,7 +329,7 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   return P > 1 ? go(std::integral_constant<int, 2>{}) : go(std::integral_constant<int, 8>{});
 }
 
-bool use_partition(bs_handle h, int64_t M, int vec);
+bool use_partition(bs_handle h, int64_t M);
 bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
                        cudaStream_t st);
 
@@ -337,7 +337,7 @@ template <typename C>
 static bs_status dispatch_adi(bs_handle h, int N, const C* u, C* out, int64_t M, C r, int axis, bool adj,
                               cudaStream_t st) {
   cudaError_t e;
-  if (use_partition(h, M, 1)) {
+  if (use_partition(h, M)) {
     // row-partitioned: the primal-form plan of the block-diagonal part of
     // A (or A^T), then the block-edge correction on `out`
     const PartPlan& pp = h->part[adj ? 1 : 0];

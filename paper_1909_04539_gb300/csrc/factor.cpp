@@ -257,7 +257,6 @@ struct HostPart {
 // Rows per block at least this many; blocks at most kPartMax.
 constexpr int kPartMinRows = 192;
 constexpr int kPartMax = 32;
-constexpr int kPartMaxBand = 8;  // bandwidth limit of the reduced system
 
 bool make_partition(const double* const* bd, int width, int64_t N, HostPart& hp) {
   const int h = width / 2;
@@ -350,7 +349,7 @@ bool make_partition(const double* const* bd, int width, int64_t N, HostPart& hp)
         pl = std::max(pl, i - j);
         qu = std::max(qu, j - i);
       }
-  if (pl > kPartMaxBand || qu > kPartMaxBand) return false;
+  if (pl > 3 * h - 1 || qu > 3 * h - 1) return false;  // the kernels' fixed band limit
   // LU without pivoting (the fill stays inside the band)
   for (int c = 0; c < R; c++) {
     const double piv = A[(size_t)c * R + c];

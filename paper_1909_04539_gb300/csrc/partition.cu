@@ -20,7 +20,14 @@
 namespace bs {
 
 constexpr int kPartThreads = 256;
-constexpr int kPartBand = 8;  // largest bandwidth of the reduced system's LU
+
+// Largest bandwidth of the reduced system's LU for half-width H: the unknowns
+// of one block edge couple to those of the neighbouring edges, at most
+// 3H - 1 positions away (2 for tridiagonal, 5 for pentadiagonal matrices).
+template <int H>
+__host__ __device__ constexpr int part_band() {
+  return 3 * H - 1;
+}
 
 __device__ __forceinline__ int part_top(int b, int L) { return b * L; }
 __device__ __forceinline__ int part_bot(int b, int L, int N) { return ((b + 1) * L < N ? (b + 1) * L : N) - 1; }
@@ -41,6 +48,7 @@ __global__ void __launch_bounds__(kPartThreads)
 k_part_reduced(const C* __restrict__ lu, int R, int p, int q, int L, int N, const C* __restrict__ X, int64_t rs,
                int64_t ss, int64_t M, C* __restrict__ bt) {
   constexpr int G = 8;
+  constexpr int kPartBand = part_band<H>();
   const C* dinv = lu + (int64_t)p * R;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
     C win[kPartBand];  // win[k] = the value k + 1 rows back

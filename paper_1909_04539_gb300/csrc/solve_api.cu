@@ -60,13 +60,15 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
 bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
                        cudaStream_t st);
 
-// Whether a solve of M systems (vector width vec) runs row-partitioned.
-bool use_partition(bs_handle h, int64_t M, int vec) {
+// Whether a solve of M systems runs row-partitioned: by default when the
+// batch has fewer than 256 systems per SM (measured: 65536 systems of N = 512
+// already keep every SM busy, 4096 lines of an ADI step do not).
+bool use_partition(bs_handle h, int64_t M) {
   if (!h->has_part || h->periodic) return false;
   const int64_t o = option(BS_OPT_PARTITION);
   if (o == 1) return false;
   if (o == 2) return true;
-  return M / vec < (int64_t)device_info().sms * 128;
+  return M < (int64_t)device_info().sms * 256;
 }
 
 static bs_status check_common(bs_handle h, const void* B, bs_layout layout, int64_t M, const char* fn) {
@@ -105,7 +107,7 @@ bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (dtype != BS_F64 && dtype != BS_F32)
     return set_error(BS_EINVAL, "bs_solve: dtype must be BS_F64 or BS_F32 (BF16 input: bs_solve_bf16)");
-  const bool part = use_partition(h, M, dtype == BS_F64 ? 2 : 4);
+  const bool part = use_partition(h, M);
   const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   const int L = part ? h->part[0].L : 0, P = part ? h->part[0].P : 1;
   if (dtype == BS_F64)
@@ -125,7 +127,7 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
   const char* x0 = reinterpret_cast<const char*>(X);
   const size_t nm = (size_t)h->N * (size_t)M;
   if (b0 < x0 + nm * 4 && x0 < b0 + nm * 2) return set_error(BS_EINVAL, "bs_solve_bf16: B and X overlap");
-  const bool part = use_partition(h, M, 4);
+  const bool part = use_partition(h, M);
   const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = sweep_bf16(p, false, (int)h->N, B, X, layout, M, st, part ? h->part[0].L : 0,
@@ -146,7 +148,7 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
   const int N = (int)h->N;
   if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_solve_adjoint: dtype must be BS_F64 or BS_F32");
   // partitioned: the primal-form plan of A^T's block-diagonal part
-  const bool part = use_partition(h, M, dtype == BS_F64 ? 2 : 4);
+  const bool part = use_partition(h, M);
   const SweepPlan& p = part ? h->part[1].blk : h->plan[1];
   const int L = part ? h->part[1].L : 0, P = part ? h->part[1].P : 1;
   if (dtype == BS_F64)

@@ -625,23 +625,24 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
   const int64_t groups = M / V;
   if constexpr (V > 1 || sizeof(Sout) == 8) {
     // pipelined kernel: ring of D 16-byte slots per lane; the FP32 sweeps are
-    // bound by memory latency, so they keep twice the rows in flight
-    constexpr int D = sizeof(C) == 4 ? 32 : 16;
-    const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
-    const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
-    const dim3 grid((sh.grid + P - 1) / P, P);
-    if (sh.smem_coefs) {
-      auto k = k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER>;
+    // bound by memory latency, so they keep twice the rows in flight -- but a
+    // partitioned launch has the threads, and shallow rings let more CTAs fit
+    auto go = [&](auto dtag) -> cudaError_t {
+      constexpr int D = decltype(dtag)::value;
+      const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
+      const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
+      const dim3 grid((sh.grid + P - 1) / P, P);
+      auto k = sh.smem_coefs ? k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER>
+                             : k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       k<<<grid, sh.threads, bytes, st>>>(cf, N, in, out, M, L);
-    } else {
-      auto k = k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER>;
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (e != cudaSuccess) return e;
-      k<<<grid, sh.threads, bytes, st>>>(cf, N, in, out, M, L);
+      return cudaGetLastError();
+    };
+    if constexpr (sizeof(C) == 4) {
+      if (P == 1) return go(std::integral_constant<int, 32>{});
     }
-    return cudaGetLastError();
+    return go(std::integral_constant<int, 16>{});
   } else {
     const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, 0, 0, 0, PER ? 2 : 0);
     const dim3 grid((sh.grid + P - 1) / P, P);

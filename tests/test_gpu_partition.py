@@ -164,19 +164,18 @@ def test_no_partition_without_decay(bs):
 
 def test_partitioned_clamped_hyperdiffusion_fp32(bs):
     """The clamped I + 0.1 D4 matrix at N = 512 splits into two blocks; the
-    FP32 solve of 65536 systems runs partitioned by default."""
+    partitioned FP32 solve of 65536 systems against the oracle (sampled) and
+    the unpartitioned one."""
     N, M = 512, 65536
     bands = synth.clamped_hyperdiffusion_bands(N, 0.1)
     f = bs.Factor(bands)
-    B = synth.normal_rhs(N, M, 3, "cuda").float()
+    B = synth.normal_rhs(N, M, 3, "cuda").float().cpu().numpy()
     cols = np.random.default_rng(2).choice(M, 128, replace=False)
-    Bs = B[:, cols].double().cpu().numpy()
-    X = B.clone()
-    bs.solve(f, X)
-    Xu = _run(bs, f, B.cpu().numpy(), torch.float32, "interleaved", 1)
-    ref = oracle.solve(bands, Bs)
-    assert rel_l2(X[:, cols].double().cpu().numpy(), ref) < TOL32
-    assert rel_l2(X.double().cpu().numpy(), Xu) < 1e-6
+    X = _run(bs, f, B, torch.float32, "interleaved", 2)
+    Xu = _run(bs, f, B, torch.float32, "interleaved", 1)
+    ref = oracle.solve(bands, B[:, cols].astype(np.float64))
+    assert rel_l2(X[:, cols], ref) < TOL32
+    assert rel_l2(X, Xu) < 1e-6
 
 
 def test_partitioned_penta_adi(bs):
