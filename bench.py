@@ -50,12 +50,12 @@ NOMINAL_HBM_GBS = 8000.0
 # step's kernels from one ncu capture of this workload, valid only while the
 # kernel sources hash to the value they had at capture time.
 NCU_TRAFFIC = {
-    # one --set full capture of the kernel inside this benchmark's step
-    "band_grad_f64": {"bytes": 669718784 + 3322880, "sha": "cef8753477e7867f"},
-    # likewise (the accuracy-check launch, same kernel and batch)
-    "f64_solve": {"bytes": 472481536 + 432248064, "sha": "5afb4b8a49d041db"},
-    "adjoint_f64": {"bytes": 471471104 + 432331008, "sha": "5afb4b8a49d041db"},
-    "refine_solve": {"bytes": 352089088 + 436296448, "sha": "df305083846c0b9f"},
+    # one capture of the kernel inside this benchmark's step (the first
+    # launch of each: the accuracy-check solves or the first warm-up step)
+    "band_grad_f64": {"bytes": 669884160 + 2746368, "sha": "e0b2725bd9320463"},
+    "f64_solve": {"bytes": 472539904 + 431898880, "sha": "ed771da74998cc8c"},
+    "adjoint_f64": {"bytes": 471562752 + 432265984, "sha": "ed771da74998cc8c"},
+    "refine_solve": {"bytes": 352071424 + 435869696, "sha": "9ff4c0c01e27ba27"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
