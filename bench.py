@@ -517,6 +517,9 @@ def run_other_configs(bs, st, hbm):
     XR = torch.empty_like(B64)
     t64 = time_alone(lambda: bs.solve(f, X64), st, reps=10)
     tr = time_alone(lambda: bs.solve_refine(f, B32, XR), st, reps=10)
+    X32 = B32.clone()
+    t32 = time_alone(lambda: bs.solve(f, X32), st, reps=10)
+    del X32
     X64.copy_(B64)
     bs.solve(f, X64)
     bs.solve_refine(f, B32, XR)
@@ -540,6 +543,8 @@ def run_other_configs(bs, st, hbm):
         "refine_solve": {"ms": tr, "unknowns_per_s": nm / (tr * 1e-3), "hbm_gbs": 12 * nm / (tr * 1e-3) / 1e9,
                          "hbm_frac_of_measured": 12 * nm / (tr * 1e-3) / 1e9 / hbm},
         "refine_over_f64_speedup": t64 / tr,
+        "f32_solve": {"ms": t32, "unknowns_per_s": nm / (t32 * 1e-3), "hbm_gbs": 8 * nm / (t32 * 1e-3) / 1e9,
+                      "hbm_frac_of_measured": 8 * nm / (t32 * 1e-3) / 1e9 / hbm},
         "periodic_f64_solve": {"ms": tp, "unknowns_per_s": nm / (tp * 1e-3), "hbm_gbs": 16 * nm / (tp * 1e-3) / 1e9,
                                "over_plain_f64": tp / t64},
         "periodic_f32_solve": {"ms": tp32, "unknowns_per_s": nm / (tp32 * 1e-3),
