@@ -506,156 +506,6 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
   }
 }
 
-// Interleaved layout, checkpointed variant for FP32 sweeps of large batches,
-// which are bound by DRAM bandwidth: instead of spilling every forward value
-// (4 bytes written and read back per unknown), each lane keeps only the
-// forward recurrence's state at every K-th row, in shared memory.  The
-// backward sweep walks the segments of K rows from the bottom up; for each it
-// streams the segment's input rows again, recomputes their forward values
-// into registers from the checkpoint, and runs the backward recurrence over
-// them.  Traffic per unknown: input read twice and output written once
-// (12 bytes instead of 16); the forward arithmetic runs twice.  Rows of both
-// passes arrive through a per-lane cp.async ring of D slots, requested in the
-// order they are consumed.
-template <int BW, bool ADJ, bool SMEM, typename C, int V, int K, int D, bool PER>
-__global__ void __launch_bounds__(kSweepThreads)
-k_sweep_ck(Coefs<C> cf_g, int N, const C* in, C* out, int64_t M) {
-  constexpr int U = 4;
-  static_assert(K % U == 0 && D % U == 0, "segments and ring hold whole blocks");
-  static_assert(V * sizeof(C) == 8 || V * sizeof(C) == 16, "lane row must be 8 or 16 bytes");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER>() * N * sizeof(C), 16) : 0;
-  unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
-  const uint32_t ring_s = smem_u32(ring);
-  const uint32_t pitch = blockDim.x * 16;
-  // checkpoints: state (w_{i-1}, w_{i-2}) at the first row of segments 1..S-1
-  const int S = (N + K - 1) / K;
-  C* ck = reinterpret_cast<C*>(smem_raw + coef_bytes + (size_t)blockDim.x * D * 16) + (size_t)threadIdx.x * 2 * V;
-  const size_t ck_stride = (size_t)blockDim.x * 2 * V;
-  const int64_t ngroups = M / V;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  auto slot = [&](int pos) { return reinterpret_cast<const C*>(ring + (size_t)(pos % D) * pitch); };
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
-    const C* pin = in + g * V;
-    C* pout = out + g * V;
-    C r1[V], r2[V], sig[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) r1[v] = r2[v] = sig[v] = C(0);
-    // ---- pass A: forward sweep, checkpoints only
-    const C* pnext = pin;
-#pragma unroll 1
-    for (int r = 0; r < D; r++) {
-      if (r < N) copy_row<C, V>(ring_s + r * pitch, pnext);
-      pnext += M;
-      cp_commit();
-    }
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += U) {
-      cp_wait<D - U>();
-      const int n = (N - i0) < U ? (N - i0) : U;
-      C f[U][V];
-#pragma unroll
-      for (int u = 0; u < U; u++)
-        if (u < n) IO<C, C, V>::load(slot(i0 + u), f[u]);
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (u < n && i0 + u + D < N) copy_row<C, V>(ring_s + ((i0 + u) % D) * pitch, pnext);
-        pnext += M;
-        cp_commit();
-      }
-      if constexpr (PER)
-        if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
-      fwd_block<BW, ADJ, C, V, U>(cf, i0, n, f, r1, r2);
-      if ((i0 + U) % K == 0 && i0 + U < N) {
-        C* c = ck + (size_t)((i0 + U) / K - 1) * ck_stride;
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-          c[v] = r1[v];
-          c[V + v] = r2[v];
-        }
-      }
-    }
-    cp_wait<0>();
-    // ---- pass B: segments bottom-up; rows of each segment requested in
-    // increasing order, segment after segment
-    int req_seg = S - 1, req_off = 0;
-    const C* preq = pin + (int64_t)(S - 1) * K * M;
-    auto request = [&](int pos) {
-      if (req_seg >= 0) {
-        copy_row<C, V>(ring_s + (pos % D) * pitch, preq);
-        preq += M;
-        const int len = (N - req_seg * K) < K ? (N - req_seg * K) : K;
-        if (++req_off == len) {
-          --req_seg;
-          req_off = 0;
-          preq = pin + (int64_t)req_seg * K * M;
-        }
-      }
-      cp_commit();
-    };
-#pragma unroll 1
-    for (int r = 0; r < D; r++) request(r);
-    int pos = 0;  // consumption position
-    C x1[V], x2[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) x1[v] = x2[v] = C(0);
-#pragma unroll 1
-    for (int sg = S - 1; sg >= 0; sg--) {
-      const int r0 = sg * K;
-      const int len = (N - r0) < K ? (N - r0) : K;
-      C w1[V], w2[V];
-      if (sg == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v++) w1[v] = w2[v] = C(0);
-      } else {
-        const C* c = ck + (size_t)(sg - 1) * ck_stride;
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-          w1[v] = c[v];
-          w2[v] = c[V + v];
-        }
-      }
-      C w[K][V];
-#pragma unroll
-      for (int b0 = 0; b0 < K; b0 += U) {
-        if (b0 < len) {
-          cp_wait<D - U>();
-          const int n = (len - b0) < U ? (len - b0) : U;
-          C f[U][V];
-#pragma unroll
-          for (int u = 0; u < U; u++)
-            if (u < n) IO<C, C, V>::load(slot(pos + u), f[u]);
-          // one request (one copy group) per consumed position keeps the
-          // k-th request in slot k % D
-#pragma unroll
-          for (int u = 0; u < U; u++)
-            if (u < n) request(pos + u + D);
-          pos += n;
-          fwd_block<BW, ADJ, C, V, U>(cf, r0 + b0, n, f, w1, w2);
-#pragma unroll
-          for (int u = 0; u < U; u++)
-#pragma unroll
-            for (int v = 0; v < V; v++) w[b0 + u][v] = f[u][v];
-        }
-      }
-#pragma unroll
-      for (int t = K - 1; t >= 0; t--) {
-        if (t < len) {
-          C f1[1][V];
-#pragma unroll
-          for (int v = 0; v < V; v++) f1[0][v] = w[t][v];
-          bwd_block<BW, ADJ, C, V, 1>(cf, r0 + t, 1, f1, x1, x2);
-          if constexpr (PER)
-            if (r0 + t < cf.per_lo || r0 + t >= cf.per_hi) per_fix<C, V, 1>(cf, r0 + t, 1, f1, sig);
-          IO<C, C, V>::store(pout + (int64_t)(r0 + t) * M, f1[0]);
-        }
-      }
-    }
-    cp_wait<0>();
-  }
-}
-
 // ------------------------------------------------------ strided layout
 
 // Row i of system j at [j*N + i] (system-contiguous).  Each warp owns 32
@@ -763,8 +613,6 @@ struct LaunchShape {
 // batches still spread over every SM.
 // extra_coef_arrays: coefficient arrays staged beyond the 1 + 2 bw of a plain
 // sweep (2 for the periodic correction).
-int64_t option(int o);
-
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
                         int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
                         int extra_coef_arrays = 0);
@@ -810,23 +658,6 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
   }
 }
 
-// Checkpointed FP32 sweep (k_sweep_ck): two systems per thread, segments of
-// 32 rows, 16-row rings.
-constexpr int kCkRows = 32;
-template <int BW, bool ADJ, bool PER>
-cudaError_t launch_ck(Coefs<float> cf, int N, const float* in, float* out, int64_t M, cudaStream_t st) {
-  constexpr int V = 2, K = kCkRows, D = 16;
-  const int S = (N + K - 1) / K;
-  const size_t per_thread = (size_t)D * 16 + (size_t)(S - 1) * 2 * V * sizeof(float);
-  const LaunchShape sh = sweep_shape(BW, N, M / V, sizeof(float), sizeof(float), V, per_thread, 0, 0, PER ? 2 : 0);
-  const size_t bytes = sh.smem + (size_t)sh.threads * per_thread;
-  auto k = sh.smem_coefs ? k_sweep_ck<BW, ADJ, true, float, V, K, D, PER> : k_sweep_ck<BW, ADJ, false, float, V, K, D, PER>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  k<<<sh.grid, sh.threads, bytes, st>>>(cf, N, in, out, M);
-  return cudaGetLastError();
-}
-
 template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout>
 cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
   const int64_t threads = ((M + 31) / 32) * 32;
@@ -868,16 +699,8 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
                     (reinterpret_cast<uintptr_t>(out) % 8 == 0) && few;
   // FP64 with few systems per SM: one system per thread (twice the warps)
   if (std::is_same<Sin, double>::value && few) vec = false;
-  // large FP32 batches: the checkpointed sweep (no spill of the forward values)
-  const bool ck = std::is_same<Sin, float>::value && std::is_same<Sout, float>::value && layout == BS_INTERLEAVED &&
-                  P == 1 && option(BS_OPT_SWEEP_KERNEL) == 0 && !few && N >= 2 * kCkRows && (M % 2 == 0) &&
-                  (reinterpret_cast<uintptr_t>(in) % 8 == 0) && (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
-                  (size_t)((N + kCkRows - 1) / kCkRows - 1) * 16 <= 1024;
 #define BS_DISPATCH(BWV, ADJV, PERV)                                                                        \
   if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, L, P, st);      \
-  if constexpr (std::is_same<Sin, float>::value && std::is_same<Sout, float>::value) {                      \
-    if (ck) return launch_ck<BWV, ADJV, PERV>(cf, N, in, out, M, st);                                      \
-  }                                                                                                         \
   if constexpr (kHalf) {                                                                                    \
     if (half) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, L, P, st); \
   }                                                                                                         \

@@ -206,39 +206,3 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
         X, Y, Xb = outs[kern]
         assert rel_l2(X, ref) < TOL32 and rel_l2(Y, refa) < TOL32 and rel_l2(Xb, refb) < TOL32
     assert bs.device_status() == 0
-
-
-@pytest.mark.parametrize("width,N,periodic", [(3, 64, False), (3, 1001, False), (5, 100, False), (5, 2048, False),
-                                              (3, 1024, True)])
-@pytest.mark.parametrize("adjoint", [False, True])
-def test_fp32_checkpointed_sweep(bs, width, N, periodic, adjoint):
-    """Large FP32 batches run the checkpointed sweep (forward values
-    recomputed per segment of 32 rows instead of spilled): the same
-    arithmetic per row as the streaming kernel, so bitwise equal to it
-    (OPT_SWEEP_KERNEL = 1), and against the oracle on sampled systems."""
-    M = 1 << 18
-    rng = np.random.default_rng(N + width)
-    if periodic:
-        bands = synth.random_periodic_bands(N, rng)
-    else:
-        bands = _bands(width, N, N * 3 + width)
-    f = bs.Factor(bands, periodic=periodic)
-    B = synth.uniform_rhs(N, M, N, "cuda", torch.float32)
-    cols = np.sort(rng.choice(M, 32, replace=False))
-    Bs = B[:, cols].double().cpu().numpy()
-    run = (lambda T: bs.solve_adjoint(f, T)) if adjoint else (lambda T: bs.solve(f, T))
-    X = B.clone()
-    run(X)
-    bs.set_option(bs.OPT_SWEEP_KERNEL, 1)
-    try:
-        Xs = B.clone()
-        run(Xs)
-        torch.cuda.synchronize()
-    finally:
-        bs.set_option(bs.OPT_SWEEP_KERNEL, 0)
-    assert torch.equal(X, Xs)
-    if periodic:
-        ref = oracle.periodic_solve_adjoint(bands, Bs) if adjoint else oracle.periodic_tri_solve_bands(bands, Bs)
-    else:
-        ref = oracle.solve_adjoint(bands, Bs) if adjoint else oracle.solve(bands, Bs)
-    assert rel_l2(X[:, cols].double().cpu().numpy(), ref) < TOL32
