@@ -264,31 +264,17 @@ __global__ void __launch_bounds__(128)
 k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M) {
   static_assert(D % kRU == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FRefineCoefs<BW> cf = cg;
+  const FRefineCoefs<BW> cf = cg;
+  // with SMEM, every row's coefficients packed into one record per pass
+  FRefineRecs<BW> rc{};
   size_t coef_bytes = 0;
   if (SMEM) {
-    float* sm = reinterpret_cast<float*>(smem_raw);
-    int off = 0;
-    auto stage = [&](const float*& p) {
-      float* dst = sm + off;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = p[i];
-      p = dst;
-      off += N;
-    };
-    stage(cf.sw[0]);
-    stage(cf.sw[1]);
-    if (BW == 2) stage(cf.sw[2]);
-    stage(cf.sw[3]);
-    if (BW == 2) stage(cf.sw[4]);
-    for (int k = 0; k <= BW; k++) {
-      stage(cf.Lh[k]);
-      stage(cf.Ll[k]);
-    }
-    for (int k = 0; k < BW; k++) {
-      stage(cf.Uh[k]);
-      stage(cf.Ul[k]);
-    }
-    coef_bytes = align_up((size_t)off * sizeof(float), 16);
+    float4* r1 = reinterpret_cast<float4*>(smem_raw);
+    float4* r2 = r1 + (size_t)N * FRefineRecs<BW>::R1;
+    pack_frefine_recs<BW>(cf, N, threadIdx.x, blockDim.x, r1, r2);
+    rc.r1 = r1;
+    rc.r2 = r2;
+    coef_bytes = (size_t)N * (FRefineRecs<BW>::R1 + FRefineRecs<BW>::R2) * sizeof(float4);
     __syncthreads();
   }
   unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 8;
@@ -327,7 +313,10 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
           pnext += M;
           cp_commit();
         }
-        frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
+        if constexpr (SMEM)
+          frefine_pass1<BW, kRU>(rc, i0, n, b, w, d, w1, w2, d1, d2);
+        else
+          frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
           if (u < n) *prow = make_float2(w[u], d[u]);
@@ -366,7 +355,10 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
           pback -= M;
           cp_commit();
         }
-        frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
+        if constexpr (SMEM)
+          frefine_pass2<BW, kRU>(rc, top, n, w, dl, xo, x1, x2, e1, e2);
+        else
+          frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
           if (u < n) *pout = xo[u];
@@ -386,7 +378,7 @@ static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* 
   const DeviceInfo& d = device_info();
   int tpb = 128;
   while (tpb > 32 && M < (int64_t)2 * d.sms * tpb) tpb /= 2;
-  const size_t coef = align_up((size_t)frefine_arrays<BW>() * N * sizeof(float), 16);
+  const size_t coef = (size_t)N * (FRefineRecs<BW>::R1 + FRefineRecs<BW>::R2) * sizeof(float4);
   const size_t ring = (size_t)tpb * D * 8;
   const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
   const bool smem = coef + ring <= limit;

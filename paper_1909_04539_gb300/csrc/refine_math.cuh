@@ -174,11 +174,6 @@ struct FRefineCoefs {
   const float* Ul[2];  //   ... low parts
 };
 
-template <int BW>
-__host__ __device__ constexpr int frefine_arrays() {
-  return (1 + 2 * BW) + 2 * (BW + 1) + 2 * BW;
-}
-
 // lu = FP32 primal plan (C_COUNT * N); ehi/elo = factor entries (5 * N).
 template <int BW>
 __host__ __device__ __forceinline__ FRefineCoefs<BW> make_frefine_coefs(const float* lu, const float* ehi,
@@ -197,31 +192,133 @@ __host__ __device__ __forceinline__ FRefineCoefs<BW> make_frefine_coefs(const fl
   return cf;
 }
 
+// Coefficients of one row as the two passes use them.
+template <int BW>
+struct FRow1 {  // pass 1: sweep s, l1, l2 and the L entries (diagonal, sub-diagonals), hi/lo
+  float s, l1, l2;
+  float ah[BW + 1], al[BW + 1];
+};
+template <int BW>
+struct FRow2 {  // pass 2: sweep u1, u2 and the U super-diagonal entries, hi/lo
+  float u1, u2;
+  float ah[BW], al[BW];
+};
+
+__device__ __forceinline__ float4 f4_zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// The same coefficients packed per row in shared memory (records of FRecs1
+// and FRecs2 float4s), so that a row's set arrives in one or a few 128-bit
+// loads instead of one load per value.  Layout of a pass-1 record:
+// BW = 1: (s, l1, Lh0, Ll0), (Lh1, Ll1, -, -); BW = 2: (s, l1, l2, Lh0),
+// (Ll0, Lh1, Ll1, Lh2), (Ll2, -, -, -).  Pass-2 record: BW = 1:
+// (u1, Uh0, Ul0, -); BW = 2: (u1, u2, Uh0, Ul0), (Uh1, Ul1, -, -).
+template <int BW>
+struct FRefineRecs {
+  static constexpr int R1 = BW == 1 ? 2 : 3;
+  static constexpr int R2 = BW == 1 ? 1 : 2;
+  const float4* r1;  // N * R1
+  const float4* r2;  // N * R2
+};
+
+template <int BW>
+__device__ __forceinline__ FRow1<BW> frow1(const FRefineCoefs<BW>& cf, int i) {
+  FRow1<BW> c;
+  c.s = cf.sw[0][i];
+  c.l1 = cf.sw[1][i];
+  c.l2 = (BW == 2) ? cf.sw[2][i] : 0.f;
+#pragma unroll
+  for (int k = 0; k <= BW; k++) {
+    c.ah[k] = cf.Lh[k][i];
+    c.al[k] = cf.Ll[k][i];
+  }
+  return c;
+}
+template <int BW>
+__device__ __forceinline__ FRow2<BW> frow2(const FRefineCoefs<BW>& cf, int i) {
+  FRow2<BW> c;
+  c.u1 = cf.sw[3][i];
+  c.u2 = (BW == 2) ? cf.sw[4][i] : 0.f;
+#pragma unroll
+  for (int k = 0; k < BW; k++) {
+    c.ah[k] = cf.Uh[k][i];
+    c.al[k] = cf.Ul[k][i];
+  }
+  return c;
+}
+template <int BW>
+__device__ __forceinline__ FRow1<BW> frow1(const FRefineRecs<BW>& rc, int i) {
+  FRow1<BW> c;
+  const float4* p = rc.r1 + (size_t)i * FRefineRecs<BW>::R1;
+  if constexpr (BW == 1) {
+    const float4 a = p[0], b = p[1];
+    c.s = a.x, c.l1 = a.y, c.l2 = 0.f;
+    c.ah[0] = a.z, c.al[0] = a.w, c.ah[1] = b.x, c.al[1] = b.y;
+  } else {
+    const float4 a = p[0], b = p[1], d = p[2];
+    c.s = a.x, c.l1 = a.y, c.l2 = a.z;
+    c.ah[0] = a.w, c.al[0] = b.x, c.ah[1] = b.y, c.al[1] = b.z, c.ah[2] = b.w, c.al[2] = d.x;
+  }
+  return c;
+}
+template <int BW>
+__device__ __forceinline__ FRow2<BW> frow2(const FRefineRecs<BW>& rc, int i) {
+  FRow2<BW> c;
+  const float4* p = rc.r2 + (size_t)i * FRefineRecs<BW>::R2;
+  if constexpr (BW == 1) {
+    const float4 a = p[0];
+    c.u1 = a.x, c.u2 = 0.f, c.ah[0] = a.y, c.al[0] = a.z;
+  } else {
+    const float4 a = p[0], b = p[1];
+    c.u1 = a.x, c.u2 = a.y, c.ah[0] = a.z, c.al[0] = a.w, c.ah[1] = b.x, c.al[1] = b.y;
+  }
+  return c;
+}
+
+// Writes the packed records of rows [i_begin, N) with stride `step` (for a
+// CTA-wide staging loop), reading the per-array coefficients of cf.
+template <int BW>
+__device__ __forceinline__ void pack_frefine_recs(const FRefineCoefs<BW>& cf, int N, int i_begin, int step,
+                                                  float4* r1, float4* r2) {
+  for (int i = i_begin; i < N; i += step) {
+    const FRow1<BW> a = frow1<BW>(cf, i);
+    const FRow2<BW> b = frow2<BW>(cf, i);
+    float4* p1 = r1 + (size_t)i * FRefineRecs<BW>::R1;
+    float4* p2 = r2 + (size_t)i * FRefineRecs<BW>::R2;
+    if constexpr (BW == 1) {
+      p1[0] = make_float4(a.s, a.l1, a.ah[0], a.al[0]);
+      p1[1] = make_float4(a.ah[1], a.al[1], 0.f, 0.f);
+      p2[0] = make_float4(b.u1, b.ah[0], b.al[0], 0.f);
+    } else {
+      p1[0] = make_float4(a.s, a.l1, a.l2, a.ah[0]);
+      p1[1] = make_float4(a.al[0], a.ah[1], a.al[1], a.ah[2]);
+      p1[2] = make_float4(a.al[2], 0.f, 0.f, 0.f);
+      p2[0] = make_float4(b.u1, b.u2, b.ah[0], b.al[0]);
+      p2[1] = make_float4(b.ah[1], b.al[1], 0.f, 0.f);
+    }
+  }
+}
+
 // Rows i0 .. i0+n-1 of the first pass.  b: the FP32 inputs; on exit w, d
 // hold the pairs (w, delta) to keep.  (w1, w2), (d1, d2): the two previous
-// rows of each recurrence.
-template <int BW, int U>
-__device__ __forceinline__ void frefine_pass1(const FRefineCoefs<BW>& cf, int i0, int n, const float (&b)[U],
-                                              float (&w)[U], float (&d)[U], float& w1, float& w2, float& d1,
-                                              float& d2) {
+// rows of each recurrence.  Acc: FRefineCoefs or FRefineRecs (the same
+// values, so the same result).
+template <int BW, int U, typename Acc>
+__device__ __forceinline__ void frefine_pass1(const Acc& cf, int i0, int n, const float (&b)[U], float (&w)[U],
+                                              float (&d)[U], float& w1, float& w2, float& d1, float& d2) {
   constexpr int W = BW + 1;
-  float s[U], l1[U], l2[U], wp1[U], wp2[U];
+  FRow1<BW> c[U];
 #pragma unroll
-  for (int u = 0; u < U; u++) {
-    const int i = (u < n) ? i0 + u : i0;
-    s[u] = cf.sw[0][i];
-    l1[u] = cf.sw[1][i];
-    l2[u] = (BW == 2) ? cf.sw[2][i] : 0.f;
-  }
+  for (int u = 0; u < U; u++) c[u] = frow1<BW>(cf, (u < n) ? i0 + u : i0);
+  float wp1[U], wp2[U];
   // forward sweep of w (the chain)
 #pragma unroll
   for (int u = 0; u < U; u++) {
     wp1[u] = w1;
     wp2[u] = w2;
     if (u < n) {
-      float x = b[u] * s[u];
-      if (BW == 2) x = fmaf(-l2[u], w2, x);
-      x = fmaf(-l1[u], w1, x);
+      float x = b[u] * c[u].s;
+      if (BW == 2) x = fmaf(-c[u].l2, w2, x);
+      x = fmaf(-c[u].l1, w1, x);
       w[u] = x;
       w2 = w1;
       w1 = x;
@@ -233,29 +330,20 @@ __device__ __forceinline__ void frefine_pass1(const FRefineCoefs<BW>& cf, int i0
   for (int u = 0; u < U; u++) {
     rho[u] = 0.f;
     if (u < n) {
-      const int i = i0 + u;
-      float x[W], ah[W], al[W];
+      float x[W];
       x[0] = w[u];
-      ah[0] = cf.Lh[0][i];
-      al[0] = cf.Ll[0][i];
       x[1] = wp1[u];
-      ah[1] = cf.Lh[1][i];
-      al[1] = cf.Ll[1][i];
-      if (BW == 2) {
-        x[W - 1] = wp2[u];
-        ah[W - 1] = cf.Lh[2][i];
-        al[W - 1] = cf.Ll[2][i];
-      }
-      rho[u] = residual_row<W>(b[u], x, ah, al);
+      if (BW == 2) x[W - 1] = wp2[u];
+      rho[u] = residual_row<W>(b[u], x, c[u].ah, c[u].al);
     }
   }
   // forward sweep of the correction
 #pragma unroll
   for (int u = 0; u < U; u++) {
     if (u < n) {
-      float x = rho[u] * s[u];
-      if (BW == 2) x = fmaf(-l2[u], d2, x);
-      x = fmaf(-l1[u], d1, x);
+      float x = rho[u] * c[u].s;
+      if (BW == 2) x = fmaf(-c[u].l2, d2, x);
+      x = fmaf(-c[u].l1, d1, x);
       d[u] = x;
       d2 = d1;
       d1 = x;
@@ -265,18 +353,15 @@ __device__ __forceinline__ void frefine_pass1(const FRefineCoefs<BW>& cf, int i0
 
 // Rows top, top-1, .., top-n+1 of the second pass: (w, dl) the kept pairs;
 // returns the FP64 solution in X.  (x1, x2), (e1, e2): the two rows below.
-template <int BW, int U>
-__device__ __forceinline__ void frefine_pass2(const FRefineCoefs<BW>& cf, int top, int n, const float (&w)[U],
+template <int BW, int U, typename Acc>
+__device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, const float (&w)[U],
                                               const float (&dl)[U], double (&X)[U], float& x1, float& x2,
                                               float& e1, float& e2) {
   constexpr int W = BW + 1;
-  float u1[U], u2[U], x[U], xn1[U], xn2[U];
+  FRow2<BW> c[U];
 #pragma unroll
-  for (int u = 0; u < U; u++) {
-    const int i = (u < n) ? top - u : top;
-    u1[u] = cf.sw[3][i];
-    u2[u] = (BW == 2) ? cf.sw[4][i] : 0.f;
-  }
+  for (int u = 0; u < U; u++) c[u] = frow2<BW>(cf, (u < n) ? top - u : top);
+  float x[U], xn1[U], xn2[U];
   // backward sweep of x on the rounded pair (the chain)
 #pragma unroll
   for (int u = 0; u < U; u++) {
@@ -284,8 +369,8 @@ __device__ __forceinline__ void frefine_pass2(const FRefineCoefs<BW>& cf, int to
     xn2[u] = x2;
     if (u < n) {
       float v = __fadd_rn(w[u], dl[u]);
-      if (BW == 2) v = fmaf(-u2[u], x2, v);
-      v = fmaf(-u1[u], x1, v);
+      if (BW == 2) v = fmaf(-c[u].u2, x2, v);
+      v = fmaf(-c[u].u1, x1, v);
       x[u] = v;
       x2 = x1;
       x1 = v;
@@ -297,18 +382,17 @@ __device__ __forceinline__ void frefine_pass2(const FRefineCoefs<BW>& cf, int to
   for (int u = 0; u < U; u++) {
     sig[u] = 0.f;
     if (u < n) {
-      const int i = top - u;
       float xs[W], ah[W], al[W];
       xs[0] = x[u];
       ah[0] = 1.f;
       al[0] = 0.f;
       xs[1] = xn1[u];
-      ah[1] = cf.Uh[0][i];
-      al[1] = cf.Ul[0][i];
+      ah[1] = c[u].ah[0];
+      al[1] = c[u].al[0];
       if (BW == 2) {
         xs[W - 1] = xn2[u];
-        ah[W - 1] = cf.Uh[1][i];
-        al[W - 1] = cf.Ul[1][i];
+        ah[W - 1] = c[u].ah[1];
+        al[W - 1] = c[u].al[1];
       }
       sig[u] = __fadd_rn(residual_row<W>(w[u], xs, ah, al), dl[u]);
     }
@@ -318,8 +402,8 @@ __device__ __forceinline__ void frefine_pass2(const FRefineCoefs<BW>& cf, int to
   for (int u = 0; u < U; u++) {
     if (u < n) {
       float v = sig[u];
-      if (BW == 2) v = fmaf(-u2[u], e2, v);
-      v = fmaf(-u1[u], e1, v);
+      if (BW == 2) v = fmaf(-c[u].u2, e2, v);
+      v = fmaf(-c[u].u1, e1, v);
       e2 = e1;
       e1 = v;
       X[u] = widen_exact(x[u]) + widen_exact(v);
