@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 669884160 + 2746368, "sha": "e0b2725bd9320463"},
+    "band_grad_f64": {"bytes": 669860608 + 3034112, "sha": "a8007f3a8ab0586e"},
     "f64_solve": {"bytes": 472539904 + 431898880, "sha": "ed771da74998cc8c"},
     "adjoint_f64": {"bytes": 471562752 + 432265984, "sha": "ed771da74998cc8c"},
-    "refine_solve": {"bytes": 352071424 + 435869696, "sha": "9ff4c0c01e27ba27"},
+    "refine_solve": {"bytes": 355813120 + 439578368, "sha": "5a03e81291d28e9d"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
