@@ -354,6 +354,13 @@ def run_ours(args):
                  "hbm_gbs": 8 * nm / (f32_alone * 1e-3) / 1e9}
     f32_alone["hbm_frac_of_measured"] = f32_alone["hbm_gbs"] / hbm
     del X32
+    # BF16-stored B, FP32 arithmetic, FP32 X (not part of the step): 6 B per unknown
+    B16 = B0.to(torch.bfloat16)
+    Xb = torch.empty((N, M), dtype=torch.float32, device="cuda")
+    t16 = time_alone(lambda: bs.solve_bf16(f, B16, Xb), st, reps=50)
+    bf16_alone = {"ms": t16, "unknowns_per_s": nm / (t16 * 1e-3), "hbm_gbs": 6 * nm / (t16 * 1e-3) / 1e9}
+    bf16_alone["hbm_frac_of_measured"] = bf16_alone["hbm_gbs"] / hbm
+    del B16, Xb
 
     # the three-pass refinement on the system residual (not part of the step)
     XS = torch.empty_like(XR)
@@ -378,6 +385,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (systems partitioned, no collective)"},
         "rel_residual": resid,
         "f32_solve_alone": f32_alone,
+        "bf16_solve_alone": bf16_alone,
         "refine_system_alone": refine_system_alone,
         "hbm_gbs_step": (sum(p["bytes"] for p in paths.values())) / (ms_step * 1e-3) / 1e9,
         "paths": {n: {k: (round(v, 6) if isinstance(v, float) else v) for k, v in p.items()}
@@ -570,6 +578,29 @@ def run_other_configs(bs, st, hbm):
             rows = np.random.default_rng(12).choice(n, 8, replace=False)
             samples["adi"] = (r, u.cpu().numpy(), full.cpu().numpy(), rows)
     out["adi_4096x4096"] = adi
+    # a small batch of long tridiagonal systems (N = 4096, M = 4096, FP64):
+    # row-partitioned (the default below 256 systems per SM) against one
+    # thread per system
+    N4, M4 = 4096, 4096
+    rng4 = np.random.default_rng(21)
+    b4 = synth.random_tri_bands(N4, rng4)
+    f4 = bs.Factor(b4)
+    B4 = synth.uniform_rhs(N4, M4, 21, "cuda")
+    X4 = B4.clone()
+    tp = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - \
+        time_alone(lambda: X4.copy_(B4), st, reps=20)
+    bs.set_option(bs.OPT_PARTITION, 1)
+    tu = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - \
+        time_alone(lambda: X4.copy_(B4), st, reps=20)
+    bs.set_option(bs.OPT_PARTITION, 0)
+    out["tri_N4096_M4096_f64"] = {"partitioned_ms": tp, "one_thread_per_system_ms": tu,
+                                  "unknowns_per_s": N4 * M4 / (tp * 1e-3), "speedup": tu / tp}
+    X4.copy_(B4)
+    bs.solve(f4, X4)
+    cols4 = np.random.default_rng(22).choice(M4, 16, replace=False)
+    samples["tri_N4096"] = (b4, B4[:, cols4].cpu().numpy(), X4[:, cols4].cpu().numpy(), None)
+    del B4, X4, f4
+
     # the paper's benchmark problems as Crank-Nicolson time stepping (explicit
     # side fused into the sweep): periodic diffusion (-s, 1 + 2s, -s), N = 1024,
     # and hyperdiffusion (s, -4s, 1 + 6s, -4s, s), N = 512; M = 65536, 10 steps
