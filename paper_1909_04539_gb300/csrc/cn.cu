@@ -21,8 +21,10 @@
 
 namespace bs {
 
+constexpr int kCnThreads = 256;
+
 template <int BW, bool PER, bool SMEM, typename C, int V, int U>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kCnThreads)
 k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
   constexpr int W = 2 * BW + 1;
   static_assert(U >= BW, "a block must cover the look-ahead rows");
@@ -181,7 +183,10 @@ static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, in
   cf.per_hi = p.per_hi;
   const int64_t groups = M / V;
   // the explicit bands add 2 BW + 1 arrays to the staged coefficients
-  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(C), V, 0, 0, 0, (PER ? 2 : 0) + 2 * BW + 1);
+  // 256-thread CTAs when the batch fills the device: the staged coefficient
+  // and explicit-band arrays are shared by twice the threads
+  const int tpb = groups >= (int64_t)device_info().sms * kCnThreads ? kCnThreads : 0;
+  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(C), V, 0, 0, tpb, (PER ? 2 : 0) + 2 * BW + 1);
   if (sh.smem_coefs) {
     auto k = k_cn_il<BW, PER, true, C, V, U>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
