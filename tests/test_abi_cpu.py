@@ -84,3 +84,23 @@ def test_option_constants_match_header():
         if name == "COUNT":
             continue
         assert getattr(bs, "OPT_" + name) == val, name
+
+
+def test_newer_entry_points_reject_bad_arguments(L):
+    """Argument errors of the periodic factorisation and of the entry points
+    that take a handle are reported before any device work."""
+    h = ctypes.c_void_p()
+    bands = (ctypes.c_double * 9)()
+    assert L.bs_factor_periodic(None, 3, ctypes.byref(h)) == 1
+    assert L.bs_factor_periodic(bands, 2, ctypes.byref(h)) == 1
+    assert b"N must be" in L.bs_last_error()
+    assert L.bs_factor_periodic(bands, 3, None) == 1
+    bogus = ctypes.c_void_p(0x1234)
+    p = ctypes.c_void_p(0x1000)
+    assert L.bs_cn_steps(bogus, p, 0, 0, 4, 1, None) == 1
+    assert L.bs_adi_halfstep(bogus, p, p, 0, 8, 8, ctypes.c_double(0.5), 0, 0, None) == 1
+    assert L.bs_solve_refine(bogus, p, 1, p, 0, 4, 1, 0, None) == 1
+    assert L.bs_band_grad(bogus, p, p, 0, 0, 4, p, None) == 1
+    assert L.bs_band_grad_noalloc(bogus, p, p, 0, 0, 4, p, None) == 1
+    assert L.bs_solve_bf16(bogus, p, p, 0, 4, None) == 1
+    assert b"unknown handle" in L.bs_last_error()
