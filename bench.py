@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 669860608 + 3034112, "sha": "a8007f3a8ab0586e"},
-    "f64_solve": {"bytes": 472539904 + 431898880, "sha": "ed771da74998cc8c"},
-    "adjoint_f64": {"bytes": 471562752 + 432265984, "sha": "ed771da74998cc8c"},
-    "refine_solve": {"bytes": 355813120 + 439578368, "sha": "5a03e81291d28e9d"},
+    "band_grad_f64": {"bytes": 669723136 + 90624, "sha": "1b07e7a5e77a241f"},
+    "f64_solve": {"bytes": 472629760 + 431598336, "sha": "d0e98d4b994c940f"},
+    "adjoint_f64": {"bytes": 471430144 + 429337856, "sha": "d0e98d4b994c940f"},
+    "refine_solve": {"bytes": 355862016 + 436320512, "sha": "0187d1373f265810"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
@@ -601,6 +601,35 @@ def run_other_configs(bs, st, hbm):
     samples["tri_N4096"] = (b4, B4[:, cols4].cpu().numpy(), X4[:, cols4].cpu().numpy(), None)
     del B4, X4, f4
 
+    # uniform pentadiagonal matrix (the outermost sub-diagonal one scalar,
+    # Sec. 4.1 cuPentUniformBatch): hyperdiffusion (s, -4s, 1 + 6s, -4s, s),
+    # N = 512, M = 65536; the FP32-arithmetic sweeps with the scalar against
+    # the general ones (FP64 solves always take the general sweeps)
+    uni = {}
+    Nu, Mu = 512, 65536
+    bu = synth.toeplitz_bands(Nu, (0.1, -0.4, 1.6, -0.4, 0.1))
+    fu = bs.Factor(bu)
+    B32 = synth.normal_rhs(Nu, Mu, 4, "cuda", torch.float32)
+    X32 = B32.clone()
+    B16 = B32.bfloat16()
+    tcopy = time_alone(lambda: X32.copy_(B32), st, reps=20)
+    for dname, fn, tc in (("f32", lambda: (X32.copy_(B32), bs.solve(fu, X32)), tcopy),
+                          ("bf16_storage", lambda: bs.solve_bf16(fu, B16, X32), 0.0)):
+        row = {}
+        for opt, key in ((0, "uniform_ms"), (1, "general_ms")):
+            bs.set_option(bs.OPT_UNIFORM, opt)
+            row[key] = time_alone(fn, st, reps=20) - tc
+        bs.set_option(bs.OPT_UNIFORM, 0)
+        row["unknowns_per_s"] = Nu * Mu / (row["uniform_ms"] * 1e-3)
+        uni[dname] = row
+    X32.copy_(B32)
+    bs.solve(fu, X32)
+    colsu = np.random.default_rng(23).choice(Mu, 64, replace=False)
+    Bs = B32[:, colsu].double().cpu().numpy()
+    samples["uniform_penta_f32"] = (bu, Bs, X32[:, colsu].double().cpu().numpy(), None)
+    out["uniform_penta_N512_M65536"] = uni
+    del B32, X32, B16, fu
+
     # the paper's benchmark problems as Crank-Nicolson time stepping (explicit
     # side fused into the sweep): periodic diffusion (-s, 1 + 2s, -s), N = 1024,
     # and hyperdiffusion (s, -4s, 1 + 6s, -4s, s), N = 512; M = 65536, 10 steps
@@ -779,7 +808,8 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
         else:
             b, Bs, X64s, XRs = smp
             ref = oracle.periodic_tri_solve_bands(b, Bs) if name.startswith("periodic") else oracle.solve(b, Bs)
-            errs[f"{name}_f64_solve"] = float(np.linalg.norm(X64s - ref) / np.linalg.norm(ref))
+            key = f"{name}_solve" if name.endswith("_f32") else f"{name}_f64_solve"
+            errs[key] = float(np.linalg.norm(X64s - ref) / np.linalg.norm(ref))
             if XRs is not None:
                 errs[f"{name}_refine_solve"] = float(np.linalg.norm(XRs - ref) / np.linalg.norm(ref))
     # timing: the oracle step on a column block of the same batch, grown

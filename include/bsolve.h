@@ -67,7 +67,8 @@ typedef enum { BS_INTERLEAVED = 0, BS_STRIDED = 1 } bs_layout;
  * diagonal dominance or symmetric positive definiteness, Sec. 4.3): a zero
  * or non-finite pivot returns BS_ESINGULAR and *out stays NULL.
  * Blocking (synchronous device copies).  The handle owns its device memory
- * until bs_destroy. */
+ * until bs_destroy.  A width-5 matrix whose outermost sub-diagonal entries
+ * a_3 .. a_N (1-based) are all equal is marked uniform (see BS_OPT_UNIFORM). */
 bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out);
 
 /* Factorise a periodic (cyclic) tridiagonal LHS, Sec. 3.3: row i has a_i at
@@ -317,14 +318,25 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    corrects the rows near the block edges; the result is the same as the
  *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
  *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 256
- *    systems per SM; 1: never; 2: whenever the handle has one. */
+ *    systems per SM; 1: never; 2: whenever the handle has one.
+ *  BS_OPT_UNIFORM: uniform pentadiagonal solves (Sec. 4.1, cuPentUniformBatch).
+ *    bs_factor marks a pentadiagonal handle uniform when every in-range entry
+ *    of its outermost sub-diagonal (a_i, i = 3..N, 1-based) is the same value
+ *    eps; the unpartitioned FP32-arithmetic sweeps of bs_solve (BS_F32),
+ *    bs_solve_bf16 and bs_solve_adjoint (BS_F32) then read eps as a scalar
+ *    instead of a coefficient array (one array fewer staged and read per
+ *    row; the same number of operations, in a different order, so results
+ *    differ from the general sweeps by rounding only).  FP64 solves keep the
+ *    general sweeps, which are faster there.  0 (default): used for uniform
+ *    handles; 1: never. */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
   BS_OPT_SWEEP_KERNEL = 2,
   BS_OPT_TMA_AHEAD = 3,
   BS_OPT_PARTITION = 4,
-  BS_OPT_COUNT = 5
+  BS_OPT_UNIFORM = 5,
+  BS_OPT_COUNT = 6
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

@@ -22,6 +22,7 @@ OPT_BLOCKS_PER_SM = 1
 OPT_SWEEP_KERNEL = 2
 OPT_TMA_AHEAD = 3
 OPT_PARTITION = 4
+OPT_UNIFORM = 5
 
 
 def device_status(reset: bool = False) -> int:

@@ -69,6 +69,8 @@ struct HostPlan {
   int bw = 1;
   bool fwd_scale = false, bwd_scale = false, periodic = false;
   int per_lo = 0, per_hi = 0;
+  bool uniform = false;  // see SweepPlan
+  double eps = 0.0;
   std::vector<double> c;
 };
 
@@ -393,6 +395,8 @@ cudaError_t upload_plan(const HostPlan& hp, SweepPlan& sp, size_t& bytes) {
   sp.periodic = hp.periodic;
   sp.per_lo = hp.per_lo;
   sp.per_hi = hp.per_hi;
+  sp.uniform = hp.uniform;
+  sp.eps = hp.eps;
   std::vector<float> c32(hp.c.size());
   for (size_t q = 0; q < c32.size(); q++) c32[q] = (float)hp.c[q];
   cudaError_t e = cudaMalloc(&sp.c64, sizeof(double) * hp.c.size());
@@ -531,6 +535,19 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   std::vector<double> entries;
   int64_t bad_row = make_plans(bd, width, N, hp[0], hp[1], &entries);
   if (bad_row) return set_error(BS_ESINGULAR, "bs_factor: bad pivot at row " + std::to_string(bad_row));
+  if (width == 5) {
+    // uniform outermost sub-diagonal (Sec. 4.1, cuPentUniformBatch): a_i for
+    // the in-range rows i >= 2 (0-based) all equal; then eps_i = a_i is one
+    // scalar in the primal forward and the adjoint backward sweep
+    bool uni = true;
+    for (int64_t i = 3; i < N && uni; i++) uni = bd[0][i] == bd[0][2];
+    if (uni && std::isfinite(bd[0][2])) {
+      for (int p = 0; p < 2; p++) {
+        hp[p].uniform = true;
+        hp[p].eps = bd[0][2];
+      }
+    }
+  }
   {
     // Reversed matrix J A J (J the row reversal): band k of row i is band
     // (width-1-k) of row N-1-i.  Its primal plan, read back in original row

@@ -40,6 +40,7 @@ struct Coefs {
   const C* pc;
   int per_lo;   // rows per_lo <= i < per_hi have pw_i == pc_i == 0, so a
   int per_hi;   // block of rows inside that range skips the correction
+  C eps;        // uniform pentadiagonal plans: the outermost sub-diagonal entry
 };
 
 struct SweepPlan {
@@ -48,6 +49,8 @@ struct SweepPlan {
   bool bwd_scale;  // t present
   bool periodic;   // pw / pc present (Sherman-Morrison correction)
   int per_lo, per_hi;  // rows without correction terms (see Coefs)
+  bool uniform;    // pentadiagonal with every a_i (i >= 3, 1-based) equal to eps
+  double eps;
   double* c64;     // device, C_COUNT * N
   float* c32;      // device, C_COUNT * N
 };
@@ -121,6 +124,7 @@ struct DeviceInfo {
   int smem_optin;
 };
 const DeviceInfo& device_info();
+int64_t option(int o);
 
 // Launchers
 bs_status launch_sweep(const SweepPlan& p, int64_t N, const void* in, void* out, bs_dtype in_t,

@@ -30,7 +30,6 @@
 
 namespace bs {
 
-int64_t option(int o);
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");

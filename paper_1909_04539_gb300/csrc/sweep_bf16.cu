@@ -5,7 +5,6 @@ namespace bs {
 
 template <typename Sin>
 int sweep_tma(const SweepPlan&, bool, int, const Sin*, float*, int64_t, cudaStream_t, cudaError_t*);
-int64_t option(int o);
 
 cudaError_t sweep_bf16(const SweepPlan& p, bool adjoint, int N, const void* in, void* out,
                         bs_layout layout, int64_t M, cudaStream_t st, int L, int P) {

@@ -17,6 +17,12 @@
 //   backward: x_i = t_i w_i - u1_i x_{i+1} - u2_i x_{i+2}
 // where the primal has t == 1 and the adjoint s == 1 (ADJ).  Each step's
 // dependency on the previous row goes through a single FMA.
+//
+// Uniform pentadiagonal matrices (every entry of the outermost sub-diagonal
+// equal, Sec. 4.1's cuPentUniformBatch) keep that entry as one scalar eps
+// (UNI): the primal forward step is w_i = s_i (f_i - eps w_{i-2}) - l1_i
+// w_{i-1} and the adjoint backward step x_i = t_i (w_i - eps x_{i+2}) - u1_i
+// x_{i+1}, so one coefficient array fewer is staged and read per row.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -104,7 +110,7 @@ struct IO<__nv_bfloat16, float, 1> {
 
 // Copies the coefficient arrays a sweep of kind (BW, ADJ, PER) uses into
 // shared memory (when SMEM) and returns pointers to wherever they live.
-template <int BW, bool ADJ, bool SMEM, typename C, bool PER = false>
+template <int BW, bool ADJ, bool SMEM, typename C, bool PER = false, bool UNI = false>
 __device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
   if (SMEM) {
     int off = 0;
@@ -116,10 +122,10 @@ __device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
     };
     if (!ADJ) stage(cf.s);
     stage(cf.l1);
-    if (BW == 2) stage(cf.l2);
+    if (BW == 2 && !(UNI && !ADJ)) stage(cf.l2);
     if (ADJ) stage(cf.t);
     stage(cf.u1);
-    if (BW == 2) stage(cf.u2);
+    if (BW == 2 && !(UNI && ADJ)) stage(cf.u2);
     if (PER) {
       stage(cf.pw);
       stage(cf.pc);
@@ -129,9 +135,10 @@ __device__ __forceinline__ Coefs<C> stage_coefs(Coefs<C> cf, int N, C* sm) {
   return cf;
 }
 
-template <int BW, bool PER = false>
+template <int BW, bool PER = false, bool UNI = false>
 __host__ __device__ constexpr int coef_arrays() {
-  return 1 + 2 * BW + (PER ? 2 : 0);  // scale + BW lower + BW upper (+ pw, pc)
+  // scale + BW lower + BW upper (+ pw, pc) (- the scalar eps's array)
+  return 1 + 2 * BW + (PER ? 2 : 0) - ((UNI && BW == 2) ? 1 : 0);
 }
 
 // Coefficients of rows r0, r0 + 1, ... (the row block of a partitioned
@@ -181,16 +188,22 @@ __device__ __forceinline__ void per_fix(const Coefs<C>& cf, int top, int n, C (&
 
 // One forward step for V systems at row i (f holds the input on entry and
 // the forward value on exit).
-template <int BW, bool ADJ, typename C, int V>
+template <int BW, bool ADJ, typename C, int V, bool UNI = false>
 __device__ __forceinline__ void fwd_step(const Coefs<C>& cf, int i, C (&f)[V], C (&w1)[V], C (&w2)[V]) {
+  constexpr bool kUni = UNI && !ADJ && BW == 2;
   const C l1 = cf.l1[i];
   C s = C(1), l2 = C(0);
   if (!ADJ) s = cf.s[i];
-  if (BW == 2) l2 = cf.l2[i];
+  if (BW == 2 && !kUni) l2 = cf.l2[i];
 #pragma unroll
   for (int v = 0; v < V; v++) {
-    C w = ADJ ? f[v] : f[v] * s;
-    if (BW == 2) w = fma(-l2, w2[v], w);
+    C w;
+    if (kUni) {
+      w = fma(-cf.eps, w2[v], f[v]) * s;
+    } else {
+      w = ADJ ? f[v] : f[v] * s;
+      if (BW == 2) w = fma(-l2, w2[v], w);
+    }
     w = fma(-l1, w1[v], w);
     if (BW == 2) w2[v] = w1[v];
     w1[v] = w;
@@ -199,16 +212,22 @@ __device__ __forceinline__ void fwd_step(const Coefs<C>& cf, int i, C (&f)[V], C
 }
 
 // One backward step for V systems at row i (f holds w_i on entry, x_i on exit).
-template <int BW, bool ADJ, typename C, int V>
+template <int BW, bool ADJ, typename C, int V, bool UNI = false>
 __device__ __forceinline__ void bwd_step(const Coefs<C>& cf, int i, C (&f)[V], C (&x1)[V], C (&x2)[V]) {
+  constexpr bool kUni = UNI && ADJ && BW == 2;
   const C u1 = cf.u1[i];
   C t = C(1), u2 = C(0);
   if (ADJ) t = cf.t[i];
-  if (BW == 2) u2 = cf.u2[i];
+  if (BW == 2 && !kUni) u2 = cf.u2[i];
 #pragma unroll
   for (int v = 0; v < V; v++) {
-    C x = ADJ ? f[v] * t : f[v];
-    if (BW == 2) x = fma(-u2, x2[v], x);
+    C x;
+    if (kUni) {
+      x = fma(-cf.eps, x2[v], f[v]) * t;
+    } else {
+      x = ADJ ? f[v] * t : f[v];
+      if (BW == 2) x = fma(-u2, x2[v], x);
+    }
     x = fma(-u1, x1[v], x);
     if (BW == 2) x2[v] = x1[v];
     x1[v] = x;
@@ -221,24 +240,30 @@ __device__ __forceinline__ void bwd_step(const Coefs<C>& cf, int i, C (&f)[V], C
 // they do not wait behind the caller's stores of the previous block (which
 // the compiler must assume may alias them).  Per row and system the
 // arithmetic is exactly that of fwd_step / bwd_step.
-template <int BW, bool ADJ, typename C, int V, int U>
+template <int BW, bool ADJ, typename C, int V, int U, bool UNI = false>
 __device__ __forceinline__ void fwd_block(const Coefs<C>& cf, int i0, int n, C (&f)[U][V], C (&w1)[V],
                                           C (&w2)[V]) {
+  constexpr bool kUni = UNI && !ADJ && BW == 2;
   C s[U], l1[U], l2[U];
 #pragma unroll
   for (int u = 0; u < U; u++) {
     const int i = (u < n) ? i0 + u : i0;
     l1[u] = cf.l1[i];
     s[u] = ADJ ? C(1) : cf.s[i];
-    l2[u] = (BW == 2) ? cf.l2[i] : C(0);
+    l2[u] = (BW == 2 && !kUni) ? cf.l2[i] : C(0);
   }
 #pragma unroll
   for (int u = 0; u < U; u++) {
     if (u < n) {
 #pragma unroll
       for (int v = 0; v < V; v++) {
-        C w = ADJ ? f[u][v] : f[u][v] * s[u];
-        if (BW == 2) w = fma(-l2[u], w2[v], w);
+        C w;
+        if (kUni) {
+          w = fma(-cf.eps, w2[v], f[u][v]) * s[u];
+        } else {
+          w = ADJ ? f[u][v] : f[u][v] * s[u];
+          if (BW == 2) w = fma(-l2[u], w2[v], w);
+        }
         w = fma(-l1[u], w1[v], w);
         if (BW == 2) w2[v] = w1[v];
         w1[v] = w;
@@ -249,24 +274,30 @@ __device__ __forceinline__ void fwd_block(const Coefs<C>& cf, int i0, int n, C (
 }
 
 // Backward block: rows top, top-1, ..., top-n+1 held in f[0..n-1].
-template <int BW, bool ADJ, typename C, int V, int U>
+template <int BW, bool ADJ, typename C, int V, int U, bool UNI = false>
 __device__ __forceinline__ void bwd_block(const Coefs<C>& cf, int top, int n, C (&f)[U][V], C (&x1)[V],
                                           C (&x2)[V]) {
+  constexpr bool kUni = UNI && ADJ && BW == 2;
   C t[U], u1[U], u2[U];
 #pragma unroll
   for (int u = 0; u < U; u++) {
     const int i = (u < n) ? top - u : top;
     u1[u] = cf.u1[i];
     t[u] = ADJ ? cf.t[i] : C(1);
-    u2[u] = (BW == 2) ? cf.u2[i] : C(0);
+    u2[u] = (BW == 2 && !kUni) ? cf.u2[i] : C(0);
   }
 #pragma unroll
   for (int u = 0; u < U; u++) {
     if (u < n) {
 #pragma unroll
       for (int v = 0; v < V; v++) {
-        C x = ADJ ? f[u][v] * t[u] : f[u][v];
-        if (BW == 2) x = fma(-u2[u], x2[v], x);
+        C x;
+        if (kUni) {
+          x = fma(-cf.eps, x2[v], f[u][v]) * t[u];
+        } else {
+          x = ADJ ? f[u][v] * t[u] : f[u][v];
+          if (BW == 2) x = fma(-u2[u], x2[v], x);
+        }
         x = fma(-u1[u], x1[v], x);
         if (BW == 2) x2[v] = x1[v];
         x1[v] = x;
@@ -324,7 +355,7 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // Rows are moved in blocks of U with a two-block register pipeline: the loads
 // of the next block are issued before the current block is computed, so each
 // thread keeps up to 2*U*V loads in flight.
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U, bool PER>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int U, bool PER, bool UNI>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -335,7 +366,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
     in += (int64_t)r0 * M;
     out += (int64_t)r0 * M;
   }
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER, UNI>(cf_g, N, reinterpret_cast<C*>(smem_raw));
   const int64_t ngroups = M / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -355,7 +386,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
       const int n = (N - i0) < U ? (N - i0) : U;
       if constexpr (PER)
         if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, blk, sig);
-      fwd_block<BW, ADJ, C, V, U>(cf, i0, n, blk, r1, r2);
+      fwd_block<BW, ADJ, C, V, U, UNI>(cf, i0, n, blk, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::store(pout + (int64_t)(i0 + u) * M, blk[u]);
@@ -367,7 +398,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
     };
     auto run_bwd = [&](C (&blk)[U][V], int top) {
       const int n = (top + 1) < U ? (top + 1) : U;
-      bwd_block<BW, ADJ, C, V, U>(cf, top, n, blk, r1, r2);
+      bwd_block<BW, ADJ, C, V, U, UNI>(cf, top, n, blk, r1, r2);
       if constexpr (PER)
         if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, blk, sig);
 #pragma unroll
@@ -407,7 +438,7 @@ k_sweep_il(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 // of the last D rows stay in the ring, so the backward sweep starts without
 // reloading them; the earlier ones go to the output buffer and are streamed
 // back through the same ring.
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D, bool PER>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, int V, int D, bool PER, bool UNI>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
   static_assert(V * sizeof(Sout) == 16 || V * sizeof(Sout) == 8, "output lane row must be 8 or 16 bytes");
@@ -421,8 +452,8 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
     in += (int64_t)r0 * M;
     out += (int64_t)r0 * M;
   }
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER>() * N * sizeof(C), 16) : 0;
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER, UNI>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER, UNI>() * N * sizeof(C), 16) : 0;
   unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
   const uint32_t ring_s = smem_u32(ring);
   const uint32_t pitch = blockDim.x * 16;
@@ -455,7 +486,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
         if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
       if constexpr (PER)
         if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
-      fwd_block<BW, ADJ, C, V, U>(cf, i0, n, f, r1, r2);
+      fwd_block<BW, ADJ, C, V, U, UNI>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int i = i0 + u;
@@ -487,7 +518,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
-      bwd_block<BW, ADJ, C, V, U>(cf, top, n, f, r1, r2);
+      bwd_block<BW, ADJ, C, V, U, UNI>(cf, top, n, f, r1, r2);
       if constexpr (PER)
         if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, f, sig);
 #pragma unroll
@@ -516,7 +547,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 constexpr int kStRows = 32;
 constexpr int kStPad = 33;
 
-template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, bool PER>
+template <int BW, bool ADJ, bool SMEM, typename C, typename Sin, typename Sout, bool PER, bool UNI>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int64_t ld, int L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -528,10 +559,10 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int64_t ld
     out += r0;
   }
   C* smc = reinterpret_cast<C*>(smem_raw);
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER>(cf_g, N, smc);
+  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER, UNI>(cf_g, N, smc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kWarps = kSweepThreads / 32;
-  C* tile = smc + (SMEM ? coef_arrays<BW, PER>() * N : 0) + warp * kStRows * kStPad;
+  C* tile = smc + (SMEM ? coef_arrays<BW, PER, UNI>() * N : 0) + warp * kStRows * kStPad;
   const int64_t nwg = (M + 31) / 32;
   for (int64_t wg = (int64_t)blockIdx.x * kWarps + warp; wg < nwg; wg += (int64_t)gridDim.x * kWarps) {
     const int64_t j0 = wg * 32;
@@ -553,7 +584,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int64_t ld
           C f[1] = {tile[r * kStPad + lane]};
           if constexpr (PER)
             if (c0 + r < cf.per_lo || c0 + r >= cf.per_hi) sig[0] = fma(cf.pw[c0 + r], f[0], sig[0]);
-          fwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
+          fwd_step<BW, ADJ, C, 1, UNI>(cf, c0 + r, f, r1, r2);
           tile[r * kStPad + lane] = f[0];
         }
       __syncwarp();
@@ -579,7 +610,7 @@ k_sweep_st(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int64_t ld
       if (mine)
         for (int r = rows - 1; r >= 0; r--) {
           C f[1] = {tile[r * kStPad + lane]};
-          bwd_step<BW, ADJ, C, 1>(cf, c0 + r, f, r1, r2);
+          bwd_step<BW, ADJ, C, 1, UNI>(cf, c0 + r, f, r1, r2);
           if constexpr (PER)
             if (c0 + r < cf.per_lo || c0 + r >= cf.per_hi) f[0] = fma(-sig[0], cf.pc[c0 + r], f[0]);
           tile[r * kStPad + lane] = f[0];
@@ -619,9 +650,10 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
 
 // L, P: rows per block and blocks of a partitioned launch (L = N, P = 1
 // otherwise); grid.y = P.
-template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout, int V>
+template <int BW, bool ADJ, bool PER, bool UNI, typename C, typename Sin, typename Sout, int V>
 cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
   constexpr int U = 8;
+  constexpr int kExtra = coef_arrays<BW, PER, UNI>() - coef_arrays<BW>();  // arrays beyond 1 + 2 BW
   const int64_t groups = M / V;
   if constexpr (V > 1 || sizeof(Sout) == 8) {
     // pipelined kernel: ring of D 16-byte slots per lane; the FP32 sweeps are
@@ -629,11 +661,11 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
     // partitioned launch has the threads, and shallow rings let more CTAs fit
     auto go = [&](auto dtag) -> cudaError_t {
       constexpr int D = decltype(dtag)::value;
-      const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, PER ? 2 : 0);
+      const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, kExtra);
       const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
       const dim3 grid((sh.grid + P - 1) / P, P);
-      auto k = sh.smem_coefs ? k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER>
-                             : k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER>;
+      auto k = sh.smem_coefs ? k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER, UNI>
+                             : k_sweep_il2<BW, ADJ, false, C, Sin, Sout, V, D, PER, UNI>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       k<<<grid, sh.threads, bytes, st>>>(cf, N, in, out, M, L);
@@ -644,33 +676,34 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
     }
     return go(std::integral_constant<int, 16>{});
   } else {
-    const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, 0, 0, 0, PER ? 2 : 0);
+    const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, 0, 0, 0, kExtra);
     const dim3 grid((sh.grid + P - 1) / P, P);
     if (sh.smem_coefs) {
-      auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U, PER>;
+      auto k = k_sweep_il<BW, ADJ, true, C, Sin, Sout, V, U, PER, UNI>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
       if (e != cudaSuccess) return e;
       k<<<grid, sh.threads, sh.smem, st>>>(cf, N, in, out, M, L);
     } else {
-      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U, PER><<<grid, sh.threads, 0, st>>>(cf, N, in, out, M, L);
+      k_sweep_il<BW, ADJ, false, C, Sin, Sout, V, U, PER, UNI><<<grid, sh.threads, 0, st>>>(cf, N, in, out, M, L);
     }
     return cudaGetLastError();
   }
 }
 
-template <int BW, bool ADJ, bool PER, typename C, typename Sin, typename Sout>
+template <int BW, bool ADJ, bool PER, bool UNI, typename C, typename Sin, typename Sout>
 cudaError_t launch_st(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, int L, int P, cudaStream_t st) {
+  constexpr int kExtra = coef_arrays<BW, PER, UNI>() - coef_arrays<BW>();
   const int64_t threads = ((M + 31) / 32) * 32;
   const size_t tiles = (size_t)(kSweepThreads / 32) * kStRows * kStPad * sizeof(C);
-  LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads, PER ? 2 : 0);
+  LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(Sout), 1, 0, tiles, kSweepThreads, kExtra);
   const dim3 grid((sh.grid + P - 1) / P, P);
   if (sh.smem_coefs) {
-    auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout, PER>;
+    auto k = k_sweep_st<BW, ADJ, true, C, Sin, Sout, PER, UNI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
     k<<<grid, kSweepThreads, sh.smem + tiles, st>>>(cf, N, in, out, M, (int64_t)N, L);
   } else {
-    k_sweep_st<BW, ADJ, false, C, Sin, Sout, PER><<<grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M, (int64_t)N, L);
+    k_sweep_st<BW, ADJ, false, C, Sin, Sout, PER, UNI><<<grid, kSweepThreads, tiles, st>>>(cf, N, in, out, M, (int64_t)N, L);
   }
   return cudaGetLastError();
 }
@@ -689,6 +722,7 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
   Coefs<C> cf = coefs_of<C>(base, N);
   cf.per_lo = p.per_lo;
   cf.per_hi = p.per_hi;
+  cf.eps = (C)p.eps;
   bool vec = (M % VEC == 0) && (reinterpret_cast<uintptr_t>(in) % (VEC * sizeof(Sin)) == 0) &&
                    (reinterpret_cast<uintptr_t>(out) % (VEC * sizeof(Sout)) == 0);
   // FP32 with few systems per SM: half-width vectors (8-byte lane rows) give
@@ -699,19 +733,28 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
                     (reinterpret_cast<uintptr_t>(out) % 8 == 0) && few;
   // FP64 with few systems per SM: one system per thread (twice the warps)
   if (std::is_same<Sin, double>::value && few) vec = false;
-#define BS_DISPATCH(BWV, ADJV, PERV)                                                                        \
-  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, C, Sin, Sout>(cf, N, in, out, M, L, P, st);      \
-  if constexpr (kHalf) {                                                                                    \
-    if (half) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, L, P, st); \
-  }                                                                                                         \
-  if (vec) return launch_il<BWV, ADJV, PERV, C, Sin, Sout, VEC>(cf, N, in, out, M, L, P, st);                \
-  return launch_il<BWV, ADJV, PERV, C, Sin, Sout, 1>(cf, N, in, out, M, L, P, st);
+#define BS_DISPATCH(BWV, ADJV, PERV, UNIV)                                                                    \
+  if (layout == BS_STRIDED) return launch_st<BWV, ADJV, PERV, UNIV, C, Sin, Sout>(cf, N, in, out, M, L, P, st); \
+  if constexpr (kHalf) {                                                                                      \
+    if (half)                                                                                                 \
+      return launch_il<BWV, ADJV, PERV, UNIV, C, Sin, Sout, (kHalf ? 2 : VEC)>(cf, N, in, out, M, L, P, st);  \
+  }                                                                                                           \
+  if (vec) return launch_il<BWV, ADJV, PERV, UNIV, C, Sin, Sout, VEC>(cf, N, in, out, M, L, P, st);            \
+  return launch_il<BWV, ADJV, PERV, UNIV, C, Sin, Sout, 1>(cf, N, in, out, M, L, P, st);
   if (p.bw == 1 && p.periodic) {
-    if (!adjoint) { BS_DISPATCH(1, false, true) } else { BS_DISPATCH(1, true, true) }
+    if (!adjoint) { BS_DISPATCH(1, false, true, false) } else { BS_DISPATCH(1, true, true, false) }
   } else if (p.bw == 1) {
-    if (!adjoint) { BS_DISPATCH(1, false, false) } else { BS_DISPATCH(1, true, false) }
+    if (!adjoint) { BS_DISPATCH(1, false, false, false) } else { BS_DISPATCH(1, true, false, false) }
+  } else if (sizeof(C) == 4 && p.uniform && option(BS_OPT_UNIFORM) != 1) {
+    // FP32 arithmetic only: measured at N = 512, M = 65536 the scalar form is
+    // 2 % (FP32) and 6 % (BF16 storage) faster, but 3 % slower in FP64, whose
+    // sweeps are bound by the FP64 pipe: the w_{i-2} link of its recurrence
+    // takes three dependent operations per two rows instead of two
+    if constexpr (sizeof(C) == 4) {
+      if (!adjoint) { BS_DISPATCH(2, false, false, true) } else { BS_DISPATCH(2, true, false, true) }
+    }
   } else {
-    if (!adjoint) { BS_DISPATCH(2, false, false) } else { BS_DISPATCH(2, true, false) }
+    if (!adjoint) { BS_DISPATCH(2, false, false, false) } else { BS_DISPATCH(2, true, false, false) }
   }
 #undef BS_DISPATCH
 }

@@ -23,7 +23,6 @@
 
 namespace bs {
 
-int64_t option(int o);
 
 constexpr int kTmaRows = 32;         // rows per chunk = box height
 constexpr int kTmaU = 8;             // rows per register block (divides kTmaRows)

@@ -76,6 +76,23 @@ def random_penta_bands(N: int, rng: np.random.Generator) -> np.ndarray:
     return np.stack([a, b, c, d, e])
 
 
+def uniform_penta_bands(N: int, rng: np.random.Generator, a: float = 0.25) -> np.ndarray:
+    """Pentadiagonal bands whose outermost sub-diagonal is the constant a (the
+    uniform case of Sec. 4.1); b, d, e ~ U(-1,1) and u ~ U(1,2) per row in that
+    order, outside entries zeroed, diagonal c = sum of |off-diagonals| + u."""
+    b = rng.uniform(-1.0, 1.0, N)
+    d = rng.uniform(-1.0, 1.0, N)
+    e = rng.uniform(-1.0, 1.0, N)
+    u = rng.uniform(1.0, 2.0, N)
+    av = np.full(N, float(a))
+    av[:2] = 0.0
+    b[0] = 0.0
+    d[N - 1] = 0.0
+    e[N - 2:] = 0.0
+    c = np.abs(av) + np.abs(b) + np.abs(d) + np.abs(e) + u
+    return np.stack([av, b, c, d, e])
+
+
 def toeplitz_bands(N: int, diagonals) -> np.ndarray:
     """Constant bands (e.g. (-r, 1+2r, -r)), outside entries zeroed."""
     w = len(diagonals)
