@@ -155,17 +155,21 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
 constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
 
 // X-implicit half-step: one-warp CTAs, each owning 32 rows of
-// the grid (systems).  Chunks of 32 grid columns (rows of the systems) move
-// through a ring of K tiles in shared memory by cp.async -- each lane copies
-// its row of the chunk for the 34 systems it touches (its 32 plus one
-// neighbour each side) -- so K chunks are in flight while one is swept.  The
+// the grid (systems).  Chunks of R grid columns (rows of the systems) move
+// through a ring of K tiles in shared memory by cp.async -- the lanes with
+// lane % R == q copy row q of the chunk for the 34 systems the warp touches
+// (its 32 plus one neighbour each side), 32 / R lanes sharing a row -- so K
+// chunks are in flight while one is swept.  The
 // forward values overwrite the swept tile, leave from it with coalesced
 // stores and come back through the same ring for the backward sweep.
-template <int BW, bool ADJ, bool SMEM, typename C, int K>
+template <int BW, bool ADJ, bool SMEM, typename C, int K, int R>
 __global__ void __launch_bounds__(32)
 k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r, int64_t ld, int L) {
+  static_assert(R == 16 || R == 32, "chunk rows");
+  static_assert(kStPad <= kAdiTile, "backward tiles reuse the ring");
   constexpr int U = 8;
-  constexpr int kTile = kStRows * kAdiTile;  // one ring tile (input layout)
+  constexpr int kTile = R * kAdiTile;  // one ring tile (input layout)
+  constexpr int kParts = 32 / R;       // lanes per chunk row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {  // row block of a partitioned launch (blockIdx.y; L = N otherwise); ld = system stride
     const int r0 = blockIdx.y * L;
@@ -177,6 +181,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
   C* smc = reinterpret_cast<C*>(smem_raw);
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
   const int lane = threadIdx.x;
+  const int crow = lane % R, cph = lane / R;  // chunk row and system phase of this lane's copies
   C* ringt = smc + (SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) / sizeof(C) : 0);
   auto cp = [&](C* dst, const C* src) {
     const uint32_t d = smem_u32(dst);
@@ -185,17 +190,17 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     else
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
   };
-  const int nch = (N + kStRows - 1) / kStRows;
+  const int nch = (N + R - 1) / R;
   for (int64_t wg = blockIdx.x; wg * 32 < M; wg += gridDim.x) {
     const int64_t j0 = wg * 32;
     const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
     const bool mine = lane < nsys;
     // forward: chunk c lands in tile c % K; tile column s + 1 = system j0 + s
     auto request_in = [&](int c) {
-      C* t = ringt + (c % K) * kTile + lane * kAdiTile;
-      const int row = c * kStRows + lane;
+      C* t = ringt + (c % K) * kTile + crow * kAdiTile;
+      const int row = c * R + crow;
       if (row < N)
-        for (int s = -1; s <= nsys; s++) {
+        for (int s = -1 + cph; s <= nsys; s += kParts) {
           const int64_t jj = j0 + s;
           if (jj >= 0 && jj < M) cp(t + s + 1, u + jj * ld + row);
           else t[s + 1] = C(0);
@@ -211,8 +216,8 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     for (int c = 0; c < nch; c++) {
       cp_wait<K - 1>();
       __syncwarp();
-      const int c0 = c * kStRows;
-      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      const int c0 = c * R;
+      const int rows = (N - c0) < R ? (N - c0) : R;
       // the forward values overwrite the tile's own entries (each block of U
       // rows is read by every lane before any lane writes it)
       C* tin = ringt + (c % K) * kTile;
@@ -235,8 +240,8 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         }
       }
       __syncwarp();
-      if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tin[lane * kAdiTile + s + 1];
+      if (crow < rows)
+        for (int s = cph; s < nsys; s += kParts) out[(j0 + s) * ld + c0 + crow] = tin[crow * kAdiTile + s + 1];
       __syncwarp();
       if (c + K < nch) request_in(c + K);  // the tile is free again
       cp_commit();
@@ -245,10 +250,10 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     __syncwarp();
     // backward: chunks in decreasing order through the ring (output layout)
     auto request_back = [&](int c) {
-      C* t = ringt + (c % K) * kTile + lane * kStPad;
-      const int row = c * kStRows + lane;
+      C* t = ringt + (c % K) * kTile + crow * kStPad;
+      const int row = c * R + crow;
       if (row < N)
-        for (int s = 0; s < nsys; s++) cp(t + s, out + (j0 + s) * ld + row);
+        for (int s = cph; s < nsys; s += kParts) cp(t + s, out + (j0 + s) * ld + row);
     };
 #pragma unroll 1
     for (int q = 0; q < K; q++) {
@@ -261,8 +266,8 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     for (int c = nch - 1; c >= 0; c--) {
       cp_wait<K - 1>();
       __syncwarp();
-      const int c0 = c * kStRows;
-      const int rows = (N - c0) < kStRows ? (N - c0) : kStRows;
+      const int c0 = c * R;
+      const int rows = (N - c0) < R ? (N - c0) : R;
       C* tw = ringt + (c % K) * kTile;
       if (mine)
         for (int top = rows - 1; top >= 0; top -= U) {
@@ -276,8 +281,8 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
             if (q < n) tw[(top - q) * kStPad + lane] = f[q][0];
         }
       __syncwarp();
-      if (lane < rows)
-        for (int s = 0; s < nsys; s++) out[(j0 + s) * ld + c0 + lane] = tw[lane * kStPad + s];
+      if (crow < rows)
+        for (int s = cph; s < nsys; s += kParts) out[(j0 + s) * ld + c0 + crow] = tw[crow * kStPad + s];
       __syncwarp();
       if (c - K >= 0) request_back(c - K);
       cp_commit();
@@ -315,18 +320,27 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     };
     return P > 1 ? go(std::integral_constant<int, 16>{}) : go(std::integral_constant<int, 64>{});
   }
-  auto go = [&](auto ktag) -> cudaError_t {
+  auto go = [&](auto ktag, auto rtag) -> cudaError_t {
     constexpr int K = decltype(ktag)::value;
-    const size_t tiles = (size_t)K * kStRows * kAdiTile * sizeof(C);
+    constexpr int R = decltype(rtag)::value;
+    const size_t tiles = (size_t)K * R * kAdiTile * sizeof(C);
     const int64_t threads = ((M + 31) / 32) * 32;
     const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32);
-    auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K> : k_adi_st2<BW, ADJ, false, C, K>;
+    auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K, R> : k_adi_st2<BW, ADJ, false, C, K, R>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
     k<<<dim3((sh.grid + P - 1) / P, P), 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
     return cudaGetLastError();
   };
-  return P > 1 ? go(std::integral_constant<int, 2>{}) : go(std::integral_constant<int, 8>{});
+  if (P == 1) return go(std::integral_constant<int, 8>{}, std::integral_constant<int, 32>{});
+  // partitioned: two chunks in flight.  FP64 takes 16-row chunks (half the
+  // shared memory per warp, so about twice the resident warps for the FP64
+  // pipe: 0.313 against 0.342 ms per 4096^2 half-step); FP32, bound by
+  // latency, keeps 32-row chunks (0.113 against 0.129 ms with 16 rows)
+  if constexpr (sizeof(C) == 8)
+    return go(std::integral_constant<int, 2>{}, std::integral_constant<int, 16>{});
+  else
+    return go(std::integral_constant<int, 2>{}, std::integral_constant<int, 32>{});
 }
 
 bool use_partition(bs_handle h, int64_t M);

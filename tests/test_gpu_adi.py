@@ -26,7 +26,7 @@ def _factor(bs, n, r):
 
 
 @pytest.mark.parametrize("axis", [0, 1])
-@pytest.mark.parametrize("ny,nx", [(1, 1), (3, 5), (33, 17), (100, 64), (70, 257)])
+@pytest.mark.parametrize("ny,nx", [(1, 1), (3, 5), (33, 17), (100, 64), (70, 257), (1000, 777), (777, 1000)])
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
 def test_adi_halfstep(bs, axis, ny, nx, dtype, tol):
     r = 0.5
