@@ -504,16 +504,26 @@ def run_other_configs(bs, st, hbm):
     import synth
 
     out, samples = {}, {}
-    # random tridiagonal, N=64, M=1024, FP64 (launch-bound, L2-resident)
+    # random tridiagonal, N=64, M=1024, FP64 (L2-resident; the default path is
+    # the two-ended sweep).  Device time per solve from a CUDA graph of 100
+    # (copy + solve) minus 100 copies; a plain launch loop is bound by the
+    # host's launch rate instead, reported beside it
     bands, Bh = synth.random_tri_case(64, 1024, 0)
     f = bs.Factor(bands)
     B0 = torch.tensor(Bh, device="cuda")
     X = B0.clone()
-    ms = time_alone(lambda: (X.copy_(B0), bs.solve(f, X)), st, reps=200) - \
+    tcopy = time_graph(lambda: X.copy_(B0))
+    us = (time_graph(lambda: (X.copy_(B0), bs.solve(f, X))) - tcopy) * 1e3
+    bs.set_option(bs.OPT_TWISTED, 1)
+    us1 = (time_graph(lambda: (X.copy_(B0), bs.solve(f, X))) - tcopy) * 1e3
+    bs.set_option(bs.OPT_TWISTED, 0)
+    loop = time_alone(lambda: (X.copy_(B0), bs.solve(f, X)), st, reps=200) - \
         time_alone(lambda: X.copy_(B0), st, reps=200)
     X.copy_(B0)
     bs.solve(f, X)
-    out["random_tri_N64_M1024_f64"] = {"us_per_solve": ms * 1e3, "unknowns_per_s": 64 * 1024 / (ms * 1e-3)}
+    out["random_tri_N64_M1024_f64"] = {"us_per_solve": us, "unknowns_per_s": 64 * 1024 / (us * 1e-6),
+                                       "one_thread_per_system_us": us1,
+                                       "us_per_call_launch_loop": loop * 1e3}
     samples["random_tri"] = (bands, Bh, X.cpu().numpy(), None)
     # spline [1,4,1]/6, N=1024, M=2^20: FP64 plain vs FP32-stored + refinement
     N, M = 1024, 1 << 20
@@ -587,13 +597,16 @@ def run_other_configs(bs, st, hbm):
     f4 = bs.Factor(b4)
     B4 = synth.uniform_rhs(N4, M4, 21, "cuda")
     X4 = B4.clone()
-    tp = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - \
-        time_alone(lambda: X4.copy_(B4), st, reps=20)
+    tc4 = time_alone(lambda: X4.copy_(B4), st, reps=20)
+    tp = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - tc4
     bs.set_option(bs.OPT_PARTITION, 1)
-    tu = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - \
-        time_alone(lambda: X4.copy_(B4), st, reps=20)
+    bs.set_option(bs.OPT_TWISTED, 2)
+    tt = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - tc4
+    bs.set_option(bs.OPT_TWISTED, 1)
+    tu = time_alone(lambda: (X4.copy_(B4), bs.solve(f4, X4)), st, reps=20) - tc4
     bs.set_option(bs.OPT_PARTITION, 0)
-    out["tri_N4096_M4096_f64"] = {"partitioned_ms": tp, "one_thread_per_system_ms": tu,
+    bs.set_option(bs.OPT_TWISTED, 0)
+    out["tri_N4096_M4096_f64"] = {"partitioned_ms": tp, "two_ended_ms": tt, "one_thread_per_system_ms": tu,
                                   "unknowns_per_s": N4 * M4 / (tp * 1e-3), "speedup": tu / tp}
     X4.copy_(B4)
     bs.solve(f4, X4)
@@ -652,6 +665,36 @@ def run_other_configs(bs, st, hbm):
             del C
     out["cn_steps_M65536"] = cn
     return out, samples
+
+
+def time_graph(fn, reps=100) -> float:
+    """Per-call milliseconds of fn replayed from a CUDA graph of `reps` calls
+    (the best of three replays): device time without the host's launch
+    cost."""
+    import torch
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(reps):
+                fn()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()  # the replay runs on the current stream
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / reps)
+    return best
 
 
 def time_alone(fn, st, reps=50, warm=3) -> float:

@@ -328,7 +328,19 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    row; the same number of operations, in a different order, so results
  *    differ from the general sweeps by rounding only).  FP64 solves keep the
  *    general sweeps, which are faster there.  0 (default): used for uniform
- *    handles; 1: never. */
+ *    handles; 1: never.
+ *  BS_OPT_TWISTED: two-ended tridiagonal solves for small batches (not in the
+ *    paper).  bs_factor also prepares, for a tridiagonal matrix whose
+ *    row-reversed elimination (A = U' L') meets no bad pivot, the meeting
+ *    row k = N / 2 of a solve in which two threads share a system: one
+ *    eliminates rows 1 .. k top-down with A = L U, the other rows N .. k + 2
+ *    bottom-up with A = U' L' (1-based), both meet at row k + 1 and
+ *    back-substitute outward -- half the dependent steps per system.  The
+ *    result equals the one-thread solve to rounding.  0 (default): used by
+ *    bs_solve (BS_F64, BS_F32; interleaved layout) when a batch has at most
+ *    128 systems per SM and would not be row-partitioned into more than two
+ *    blocks (BS_OPT_PARTITION 2 keeps the partition); 1: never; 2: whenever
+ *    the handle allows (interleaved, not partitioned). */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
@@ -336,7 +348,8 @@ typedef enum {
   BS_OPT_TMA_AHEAD = 3,
   BS_OPT_PARTITION = 4,
   BS_OPT_UNIFORM = 5,
-  BS_OPT_COUNT = 6
+  BS_OPT_TWISTED = 6,
+  BS_OPT_COUNT = 7
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

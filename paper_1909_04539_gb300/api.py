@@ -23,6 +23,7 @@ OPT_SWEEP_KERNEL = 2
 OPT_TMA_AHEAD = 3
 OPT_PARTITION = 4
 OPT_UNIFORM = 5
+OPT_TWISTED = 6
 
 
 def device_status(reset: bool = False) -> int:

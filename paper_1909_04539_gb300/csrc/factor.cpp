@@ -590,7 +590,25 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   const double* tbd[5];
   for (int k = 0; k < width; k++) tbd[k] = tb.data() + (size_t)k * N;
   const bool has_part = make_partition(bd, width, N, parts[0]) && make_partition(tbd, width, N, parts[1]);
-  return upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
+  const bs_status st = upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
+  if (st == BS_OK && width == 3 && has_ul) {
+    // meeting row of the two-ended sweeps: g_k = b_k - a_k chat_{k-1} -
+    // c_k chat'_{k+1}, chat from A = L U (plan 0), chat' from A = U' L' (plan 2)
+    const int64_t k = N / 2;
+    const double a = b64[k];                            // band 0, row k (k >= 1)
+    const double c = b64[(size_t)2 * N + k];            // band 2, row k (0 for k = N - 1)
+    const double ch = hp[0].c[(size_t)C_U1 * N + k - 1];
+    const double chr = (k + 1 < N) ? hp[2].c[(size_t)C_U1 * N + k + 1] : 0.0;
+    const double g = b64[(size_t)N + k] - a * ch - c * chr;
+    if (!bad(g)) {
+      (*out)->has_twist = true;
+      (*out)->twist_k = (int)k;
+      (*out)->twist[0] = a;
+      (*out)->twist[1] = c;
+      (*out)->twist[2] = 1.0 / g;
+    }
+  }
+  return st;
 }
 
 bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out) {

@@ -106,10 +106,13 @@ struct bs_factor_s {
   float* lu_lo;
   size_t device_bytes;
   bool has_ul;             // plan[2] is valid (reversed elimination met no bad pivot)
-  bool has_part;           // part[] valid (tridiagonal, N large enough, spikes decay)
+  bool has_part;           // part[] valid (N large enough, spikes decay)
   bs::PartPlan part[2];    // [0] for A, [1] for A^T
   bool periodic;           // cyclic tridiagonal (bs_factor_periodic): bands64 holds the
                            // corner entries a_1 (band 0, row 0) and c_N (band 2, row N-1)
+  bool has_twist;          // tridiagonal with plan[2]: two-ended sweeps meeting at row
+  int twist_k;             // twist_k = N / 2, with a_k, c_k and 1 / g_k in twist[]
+  double twist[3];
 };
 
 namespace bs {

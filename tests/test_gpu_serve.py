@@ -65,9 +65,10 @@ def test_mix_equals_alone_and_direct(bs, serve):
         assert srv.wait(r2, 60) == "done"
         assert torch.equal(X, X2), "result depends on the batch"
         # bitwise equal to the direct API's one-thread-per-system solve (a
-        # small direct batch may otherwise run row-partitioned, equal to
-        # rounding), and right against the oracle
+        # small direct batch may otherwise run row-partitioned or two-ended,
+        # equal to rounding), and right against the oracle
         bs.set_option(bs.OPT_PARTITION, 1)
+        bs.set_option(bs.OPT_TWISTED, 1)
         try:
             if mode == 0:
                 D = bs.solve(facs[k], B.cuda())
@@ -76,6 +77,7 @@ def test_mix_equals_alone_and_direct(bs, serve):
             torch.cuda.synchronize()
         finally:
             bs.set_option(bs.OPT_PARTITION, 0)
+            bs.set_option(bs.OPT_TWISTED, 0)
         assert torch.equal(D.cpu(), X)  # same per-system arithmetic as the direct solves
         ref = oracle.solve(specs[k].bands, B.double().numpy())
         assert rel_l2(X.numpy(), ref) < 1e-12

@@ -189,6 +189,7 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
     Bh = np.random.default_rng(M).uniform(-1, 1, (N, M))
     f = bs.Factor(bands)
     outs = {}
+    bs.set_option(api.OPT_TWISTED, 1)  # small tridiagonal batches: not the two-ended sweep
     for kern in (2, 1):
         bs.set_option(api.OPT_SWEEP_KERNEL, kern)
         X = torch.tensor(Bh, dtype=torch.float32, device="cuda")
@@ -199,6 +200,7 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
         torch.cuda.synchronize()
         outs[kern] = (X.double().cpu().numpy(), Y.double().cpu().numpy(), Xb.double().cpu().numpy())
     bs.set_option(api.OPT_SWEEP_KERNEL, 0)
+    bs.set_option(api.OPT_TWISTED, 0)
     B32 = Bh.astype(np.float32).astype(np.float64)
     Bb = torch.tensor(Bh, dtype=torch.bfloat16).double().numpy()
     ref, refa, refb = oracle.solve(bands, B32), oracle.solve_adjoint(bands, B32), oracle.solve(bands, Bb)

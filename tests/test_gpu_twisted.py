@@ -1,0 +1,113 @@
+"""GPU parity of the two-ended tridiagonal solves (two threads per system
+meeting at row N/2; used for small batches) against the CPU FP64 oracle,
+through the C ABI.  Tolerances as for the one-thread sweeps: FP64 1e-12
+relative L2, FP32 2e-5; the two-ended and one-thread FP64 results agree to
+1e-13 (same arithmetic per row, another elimination order)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.dense import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_1909_04539_gb300 import build
+    build.build()
+    import paper_1909_04539_gb300 as m
+    yield m
+    m.set_option(m.OPT_TWISTED, 0)
+    m.set_option(m.OPT_PARTITION, 0)
+
+
+def _solve(bs, f, Bh, dtype, twisted, layout="interleaved"):
+    bs.set_option(bs.OPT_TWISTED, twisted)
+    bs.set_option(bs.OPT_PARTITION, 1)
+    try:
+        B = torch.tensor(Bh, dtype=dtype, device="cuda")
+        bs.solve(f, B, layout)
+        torch.cuda.synchronize()
+    finally:
+        bs.set_option(bs.OPT_TWISTED, 0)
+        bs.set_option(bs.OPT_PARTITION, 0)
+    return B.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 16, 17, 64, 257, 1000])
+@pytest.mark.parametrize("M", [1, 2, 7, 33, 1024])
+def test_twisted_fp64(bs, N, M):
+    rng = np.random.default_rng(N * 7919 + M)
+    bands = synth.random_tri_bands(N, rng)
+    Bh = rng.uniform(-1, 1, (N, M))
+    f = bs.Factor(bands)
+    Xt = _solve(bs, f, Bh, torch.float64, 2)
+    X1 = _solve(bs, f, Bh, torch.float64, 1)
+    ref = oracle.solve(bands, Bh)
+    assert rel_l2(Xt, ref) < TOL64
+    assert rel_l2(Xt, X1) < 1e-13
+
+
+@pytest.mark.parametrize("N,M", [(2, 3), (5, 1), (64, 1024), (333, 130), (1024, 4099)])
+def test_twisted_fp32(bs, N, M):
+    rng = np.random.default_rng(N + 31 * M)
+    bands = synth.random_tri_bands(N, rng)
+    Bh = rng.uniform(-1, 1, (N, M)).astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    X = _solve(bs, f, Bh, torch.float32, 2)
+    assert rel_l2(X, oracle.solve(bands, Bh)) < TOL32
+
+
+@pytest.mark.parametrize("name", ["adi", "spline", "toeplitz_weak"])
+def test_twisted_structured_bands(bs, name):
+    """Toeplitz matrices (ADI I - 0.5 d2, the [1,4,1]/6 spline, and a barely
+    dominant (-1, 2.01, -1)) at N = 512, 1000 systems."""
+    N, M = 512, 1000
+    bands = {"adi": synth.adi_bands(N, 0.5), "spline": synth.spline_bands(N),
+             "toeplitz_weak": synth.toeplitz_bands(N, (-1.0, 2.01, -1.0))}[name]
+    rng = np.random.default_rng(17)
+    Bh = rng.uniform(-1, 1, (N, M))
+    f = bs.Factor(bands)
+    Xt = _solve(bs, f, Bh, torch.float64, 2)
+    X1 = _solve(bs, f, Bh, torch.float64, 1)
+    ref = oracle.solve(bands, Bh)
+    tol = 1e-11 if name == "toeplitz_weak" else TOL64  # condition number ~4e3
+    assert rel_l2(Xt, ref) < tol
+    assert rel_l2(Xt, X1) < 1e-12
+
+
+def test_default_choice(bs):
+    """Small tridiagonal batches take the two-ended sweep by default (not
+    bitwise the one-thread result, right against the oracle); large ones,
+    the strided layout and pentadiagonal handles do not."""
+    rng = np.random.default_rng(5)
+    bands = synth.random_tri_bands(64, rng)
+    f = bs.Factor(bands)
+    Bh = rng.uniform(-1, 1, (64, 1024))
+    X0 = _solve(bs, f, Bh, torch.float64, 0)
+    X1 = _solve(bs, f, Bh, torch.float64, 1)
+    assert not np.array_equal(X0, X1)
+    assert rel_l2(X0, oracle.solve(bands, Bh)) < TOL64
+    Bs = np.ascontiguousarray(Bh.T)
+    assert np.array_equal(_solve(bs, f, Bs, torch.float64, 0, "strided"),
+                          _solve(bs, f, Bs, torch.float64, 1, "strided"))
+    Bl = rng.uniform(-1, 1, (64, 65536))
+    assert np.array_equal(_solve(bs, f, Bl, torch.float64, 0), _solve(bs, f, Bl, torch.float64, 1))
+    pb = synth.random_penta_bands(64, rng)
+    fp = bs.Factor(pb)
+    assert np.array_equal(_solve(bs, fp, Bh, torch.float64, 0), _solve(bs, fp, Bh, torch.float64, 2))
+
+
+def test_periodic_handle_not_twisted(bs):
+    pb = synth.random_periodic_bands(40, np.random.default_rng(8))
+    f = bs.Factor(pb, periodic=True)
+    Bh = np.random.default_rng(9).uniform(-1, 1, (40, 64))
+    X2 = _solve(bs, f, Bh, torch.float64, 2)
+    X1 = _solve(bs, f, Bh, torch.float64, 1)
+    assert np.array_equal(X2, X1)
+    assert rel_l2(X2, oracle.periodic_tri_solve_bands(pb, Bh)) < TOL64
