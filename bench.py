@@ -504,6 +504,24 @@ def run_other_configs(bs, st, hbm):
     import synth
 
     out, samples = {}, {}
+    # one-off factorisation (host FP64 elimination, reversed elimination,
+    # row partitions, uploads): host wall time, median of 5, kept out of
+    # every throughput figure
+    fac = {}
+    for name, bands, per in (("penta_clamped_N512", synth.clamped_hyperdiffusion_bands(512, 0.1), False),
+                             ("tri_spline_N1024", synth.spline_bands(1024), False),
+                             ("tri_adi_N4096", synth.adi_bands(4096, 0.5), False),
+                             ("periodic_tri_N1024", synth.periodic_toeplitz_bands(1024, (-0.5, 2.0, -0.5)), True)):
+        ts = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ff = bs.Factor(bands, periodic=per)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+            ff.close()
+        fac[f"{name}_ms"] = statistics.median(ts)
+    out["factor"] = fac
     # random tridiagonal, N=64, M=1024, FP64 (L2-resident; the default path is
     # the two-ended sweep).  Device time per solve from a CUDA graph of 100
     # (copy + solve) minus 100 copies; a plain launch loop is bound by the
