@@ -318,7 +318,9 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    corrects the rows near the block edges; the result is the same as the
  *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
  *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 256
- *    systems per SM; 1: never; 2: whenever the handle has one.
+ *    systems per SM (except that bs_solve takes the two-ended sweep of
+ *    BS_OPT_TWISTED instead of a two-block partition of a tridiagonal
+ *    matrix); 1: never; 2: whenever the handle has one.
  *  BS_OPT_UNIFORM: uniform pentadiagonal solves (Sec. 4.1, cuPentUniformBatch).
  *    bs_factor marks a pentadiagonal handle uniform when every in-range entry
  *    of its outermost sub-diagonal (a_i, i = 3..N, 1-based) is the same value
