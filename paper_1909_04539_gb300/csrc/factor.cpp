@@ -220,6 +220,10 @@ void free_handle(bs_handle h) {
   if (h->bands_lo) cudaFree(h->bands_lo);
   if (h->lu_hi) cudaFree(h->lu_hi);
   if (h->lu_lo) cudaFree(h->lu_lo);
+  for (auto& p : h->tplan) {
+    if (p.c64) cudaFree(p.c64);
+    if (p.c32) cudaFree(p.c32);
+  }
   for (auto& pp : h->part) {
     if (pp.blk.c64) cudaFree(pp.blk.c64);
     if (pp.blk.c32) cudaFree(pp.blk.c32);
@@ -493,6 +497,50 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   return BS_OK;
 }
 
+// Primal plan, in original row order, of the row-reversed matrix J A J:
+// A = U' L' with its first sweep over decreasing rows.  Returns false on a
+// bad pivot.
+bool reversed_plan(const double* const* bd, int width, int64_t N, HostPlan& out) {
+  std::vector<double> rev((size_t)width * N);
+  const double* rbd[5];
+  for (int k = 0; k < width; k++) {
+    for (int64_t i = 0; i < N; i++) rev[(size_t)k * N + i] = bd[width - 1 - k][N - 1 - i];
+    rbd[k] = rev.data() + (size_t)k * N;
+  }
+  HostPlan rp, ra;
+  rp.c.assign((size_t)C_COUNT * N, 0.0);
+  ra.c.assign((size_t)C_COUNT * N, 0.0);
+  const bool ok = make_plans(rbd, width, N, rp, ra) == 0;
+  out.bw = rp.bw;
+  out.fwd_scale = rp.fwd_scale;
+  out.bwd_scale = rp.bwd_scale;
+  out.c.assign((size_t)C_COUNT * N, 0.0);
+  for (int k = 0; k < C_COUNT; k++)
+    for (int64_t i = 0; i < N; i++) out.c[(size_t)k * N + i] = rp.c[(size_t)k * N + (N - 1 - i)];
+  return ok;
+}
+
+// Meeting row k = N / 2 of the two-ended sweeps of a tridiagonal matrix with
+// zeroed out-of-range bands bz (3 x N), given its plans top (A = L U) and bot
+// (A = U' L'): g_k = b_k - a_k chat_{k-1} - c_k chat'_{k+1}.  False if g_k is
+// zero or not finite.
+bool twist_row(const std::vector<double>& bz, const HostPlan& top, const HostPlan& bot, int64_t N,
+               bs::TwistPlan& t) {
+  const int64_t k = N / 2;
+  const double a = bz[k];                   // band 0, row k (k >= 1)
+  const double c = bz[(size_t)2 * N + k];   // band 2, row k (0 for k = N - 1)
+  const double ch = top.c[(size_t)C_U1 * N + k - 1];
+  const double chr = (k + 1 < N) ? bot.c[(size_t)C_U1 * N + k + 1] : 0.0;
+  const double g = bz[(size_t)N + k] - a * ch - c * chr;
+  if (bad(g)) return false;
+  t.ok = true;
+  t.k = (int)k;
+  t.a = a;
+  t.c = c;
+  t.g = 1.0 / g;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -548,28 +596,11 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
       }
     }
   }
-  {
-    // Reversed matrix J A J (J the row reversal): band k of row i is band
-    // (width-1-k) of row N-1-i.  Its primal plan, read back in original row
-    // order, solves A = U' L' with a first sweep over decreasing rows.
-    std::vector<double> rev((size_t)width * N);
-    const double* rbd[5];
-    for (int k = 0; k < width; k++) {
-      for (int64_t i = 0; i < N; i++) rev[(size_t)k * N + i] = bd[width - 1 - k][N - 1 - i];
-      rbd[k] = rev.data() + (size_t)k * N;
-    }
-    HostPlan rp, ra;
-    rp.c.assign((size_t)C_COUNT * N, 0.0);
-    ra.c.assign((size_t)C_COUNT * N, 0.0);
-    // A matrix whose reversed elimination meets a bad pivot still gets a
-    // handle; only the refined solve (which needs U' L') is then refused.
-    has_ul = make_plans(rbd, width, N, rp, ra) == 0;
-    hp[2].bw = rp.bw;
-    hp[2].fwd_scale = rp.fwd_scale;
-    hp[2].bwd_scale = rp.bwd_scale;
-    for (int k = 0; k < C_COUNT; k++)
-      for (int64_t i = 0; i < N; i++) hp[2].c[(size_t)k * N + i] = rp.c[(size_t)k * N + (N - 1 - i)];
-  }
+  // Reversed matrix J A J (J the row reversal): band k of row i is band
+  // (width-1-k) of row N-1-i.  A matrix whose reversed elimination meets a
+  // bad pivot still gets a handle; only the refined solve (which needs
+  // U' L') and the two-ended sweeps are then refused.
+  has_ul = reversed_plan(bd, width, N, hp[2]);
 
   // Bands with the outside entries zeroed.
   std::vector<double> b64((size_t)width * N, 0.0);
@@ -591,22 +622,32 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   for (int k = 0; k < width; k++) tbd[k] = tb.data() + (size_t)k * N;
   const bool has_part = make_partition(bd, width, N, parts[0]) && make_partition(tbd, width, N, parts[1]);
   const bs_status st = upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
-  if (st == BS_OK && width == 3 && has_ul) {
-    // meeting row of the two-ended sweeps: g_k = b_k - a_k chat_{k-1} -
-    // c_k chat'_{k+1}, chat from A = L U (plan 0), chat' from A = U' L' (plan 2)
-    const int64_t k = N / 2;
-    const double a = b64[k];                            // band 0, row k (k >= 1)
-    const double c = b64[(size_t)2 * N + k];            // band 2, row k (0 for k = N - 1)
-    const double ch = hp[0].c[(size_t)C_U1 * N + k - 1];
-    const double chr = (k + 1 < N) ? hp[2].c[(size_t)C_U1 * N + k + 1] : 0.0;
-    const double g = b64[(size_t)N + k] - a * ch - c * chr;
-    if (!bad(g)) {
-      (*out)->has_twist = true;
-      (*out)->twist_k = (int)k;
-      (*out)->twist[0] = a;
-      (*out)->twist[1] = c;
-      (*out)->twist[2] = 1.0 / g;
+  if (st != BS_OK || width != 3) return st;
+  // two-ended sweeps (small batches): for A with plans 0 and 2; for A^T with
+  // its own two plans, uploaded here
+  bs_handle hd = *out;
+  if (has_ul && twist_row(b64, hp[0], hp[2], N, hd->twist[0])) {
+    hd->twist[0].top = &hd->plan[0];
+    hd->twist[0].bot = &hd->plan[2];
+  }
+  HostPlan tt[2], tq;
+  tt[0].c.assign((size_t)C_COUNT * N, 0.0);
+  tq.c.assign((size_t)C_COUNT * N, 0.0);
+  bs::TwistPlan ta{};
+  if (make_plans(tbd, 3, N, tt[0], tq) == 0 && reversed_plan(tbd, 3, N, tt[1]) &&
+      twist_row(tb, tt[0], tt[1], N, ta)) {
+    size_t bytes = 0;
+    cudaError_t e = upload_plan(tt[0], hd->tplan[0], bytes);
+    if (e == cudaSuccess) e = upload_plan(tt[1], hd->tplan[1], bytes);
+    hd->device_bytes += bytes;
+    if (e != cudaSuccess) {
+      bs_destroy(hd);
+      *out = nullptr;
+      return cuda_error(e, "bs_factor: upload");
     }
+    hd->twist[1] = ta;
+    hd->twist[1].top = &hd->tplan[0];
+    hd->twist[1].bot = &hd->tplan[1];
   }
   return st;
 }

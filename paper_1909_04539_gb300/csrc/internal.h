@@ -87,6 +87,20 @@ struct PartPlan {
 };
 }  // namespace bs
 
+namespace bs {
+// Two-ended tridiagonal sweeps (small batches): the even lane of a pair
+// eliminates rows 0 .. k-1 top-down with `top` (A = L U), the odd lane rows
+// N-1 .. k+1 bottom-up with `bot` (A = U' L', coefficients in original row
+// order); they meet at row k with x_k = (f_k - a w_{k-1} - c z_{k+1}) * g.
+struct TwistPlan {
+  bool ok;
+  int k;
+  double a, c, g;          // a_k, c_k of the matrix solved, g = 1 / (b_k - a_k chat_{k-1} - c_k chat'_{k+1})
+  const SweepPlan* top;
+  const SweepPlan* bot;
+};
+}  // namespace bs
+
 struct bs_factor_s {
   int width;
   int64_t N;
@@ -110,9 +124,9 @@ struct bs_factor_s {
   bs::PartPlan part[2];    // [0] for A, [1] for A^T
   bool periodic;           // cyclic tridiagonal (bs_factor_periodic): bands64 holds the
                            // corner entries a_1 (band 0, row 0) and c_N (band 2, row N-1)
-  bool has_twist;          // tridiagonal with plan[2]: two-ended sweeps meeting at row
-  int twist_k;             // twist_k = N / 2, with a_k, c_k and 1 / g_k in twist[]
-  double twist[3];
+  bs::TwistPlan twist[2];  // two-ended tridiagonal sweeps: [0] for A (plan[0], plan[2]),
+                           // [1] for A^T (tplan[])
+  bs::SweepPlan tplan[2];  // A^T = L U and A^T = U' L' (primal form, original row order)
 };
 
 namespace bs {

@@ -59,8 +59,16 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
 
 bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
                        cudaStream_t st);
-bool use_twisted(bs_handle h, bs_layout layout, int64_t M);
-cudaError_t sweep_twisted(bs_handle h, const void* in, void* out, bs_dtype t, int64_t M, cudaStream_t st);
+bool use_twisted(bs_handle h, int which, bs_layout layout, int64_t M);
+cudaError_t sweep_twisted(bs_handle h, int which, const void* in, void* out, bs_dtype t, int64_t M,
+                          cudaStream_t st);
+
+// The two-ended sweep also beats a partition into two blocks (measured
+// N = 400, 512: 1.1-1.3x); from four blocks on the partition is faster.
+static bool take_twisted(bs_handle h, int which, bs_layout layout, int64_t M, bool part) {
+  return use_twisted(h, which, layout, M) &&
+         (!part || (h->part[which].P <= 2 && option(BS_OPT_PARTITION) != 2));
+}
 
 // Whether a solve of M systems runs row-partitioned: by default when the
 // batch has fewer than 256 systems per SM (measured: 65536 systems of N = 512
@@ -110,11 +118,8 @@ bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64
   if (dtype != BS_F64 && dtype != BS_F32)
     return set_error(BS_EINVAL, "bs_solve: dtype must be BS_F64 or BS_F32 (BF16 input: bs_solve_bf16)");
   const bool part = use_partition(h, M);
-  // the two-ended sweep also beats a partition into two blocks (measured
-  // N = 400, 512: 1.1-1.3x); from four blocks on the partition is faster
-  if (use_twisted(h, layout, M) &&
-      (!part || (h->part[0].P <= 2 && option(BS_OPT_PARTITION) != 2))) {
-    e = sweep_twisted(h, B, B, dtype, M, st);
+  if (take_twisted(h, 0, layout, M, part)) {
+    e = sweep_twisted(h, 0, B, B, dtype, M, st);
     if (e != cudaSuccess) return cuda_error(e, "bs_solve launch");
     return BS_OK;
   }
@@ -159,6 +164,12 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
   if (dtype != BS_F64 && dtype != BS_F32) return set_error(BS_EINVAL, "bs_solve_adjoint: dtype must be BS_F64 or BS_F32");
   // partitioned: the primal-form plan of A^T's block-diagonal part
   const bool part = use_partition(h, M);
+  if (take_twisted(h, 1, layout, M, part)) {
+    e = sweep_twisted(h, 1, G, G, dtype, M, st);
+    if (e != cudaSuccess) return cuda_error(e, "bs_solve_adjoint launch");
+    if (X) return launch_band_grad(h, G, X, dtype, layout, M, dbands, st);
+    return BS_OK;
+  }
   const SweepPlan& p = part ? h->part[1].blk : h->plan[1];
   const int L = part ? h->part[1].L : 0, P = part ? h->part[1].P : 1;
   if (dtype == BS_F64)

@@ -131,10 +131,10 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
 }
 
 template <typename C>
-static cudaError_t launch_tw(const bs_factor_s& hd, int N, const C* in, C* out, int64_t M, cudaStream_t st) {
+static cudaError_t launch_tw(const TwistPlan& tp, int N, const C* in, C* out, int64_t M, cudaStream_t st) {
   TwistArgs<C> ta{};
   for (int q = 0; q < 2; q++) {
-    const SweepPlan& p = hd.plan[q == 0 ? 0 : 2];
+    const SweepPlan& p = q == 0 ? *tp.top : *tp.bot;
     const C* base;
     if constexpr (sizeof(C) == 8)
       base = reinterpret_cast<const C*>(p.c64);
@@ -145,10 +145,10 @@ static cudaError_t launch_tw(const bs_factor_s& hd, int N, const C* in, C* out, 
     ta.l1[q] = cf.l1;
     ta.u1[q] = cf.u1;
   }
-  ta.k = hd.twist_k;
-  ta.a = (C)hd.twist[0];
-  ta.c = (C)hd.twist[1];
-  ta.g = (C)hd.twist[2];
+  ta.k = tp.k;
+  ta.a = (C)tp.a;
+  ta.c = (C)tp.c;
+  ta.g = (C)tp.g;
   const int64_t threads = 2 * M;
   int64_t grid = (threads + kTwThreads - 1) / kTwThreads;
   const int64_t cap = (int64_t)device_info().sms * (2048 / kTwThreads);
@@ -157,25 +157,28 @@ static cudaError_t launch_tw(const bs_factor_s& hd, int N, const C* in, C* out, 
   return cudaGetLastError();
 }
 
-// Whether bs_solve takes the two-ended sweep: tridiagonal, not periodic, the
-// handle has a meeting row, interleaved layout, and at most 128 systems per
-// SM; BS_OPT_TWISTED 1 never, 2 whenever the handle allows.  Measured on
-// GB300 (N = 64 .. 2048, FP64 and FP32): 1.8-2.3x faster than one thread per
-// system up to 64 systems per SM, 1.2-1.6x at 128, slower from 256 on, where
-// the one-thread sweeps already keep the SMs busy.
-bool use_twisted(bs_handle h, bs_layout layout, int64_t M) {
-  if (h->width != 3 || h->periodic || !h->has_twist || layout != BS_INTERLEAVED) return false;
+// Whether a solve with A (which = 0) or A^T (which = 1) takes the two-ended
+// sweep: tridiagonal, not periodic, the handle has a meeting row for that
+// matrix, interleaved layout, and at most 128 systems per SM; BS_OPT_TWISTED
+// 1 never, 2 whenever the handle allows.  Measured on GB300 (N = 64 .. 2048,
+// FP64 and FP32): 1.8-2.3x faster than one thread per system up to 64
+// systems per SM, 1.2-1.6x at 128, slower from 256 on, where the one-thread
+// sweeps already keep the SMs busy.
+bool use_twisted(bs_handle h, int which, bs_layout layout, int64_t M) {
+  if (h->width != 3 || h->periodic || !h->twist[which].ok || layout != BS_INTERLEAVED) return false;
   const int64_t o = option(BS_OPT_TWISTED);
   if (o == 1) return false;
   if (o == 2) return true;
   return M <= (int64_t)device_info().sms * 128;
 }
 
-cudaError_t sweep_twisted(bs_handle h, const void* in, void* out, bs_dtype t, int64_t M, cudaStream_t st) {
+cudaError_t sweep_twisted(bs_handle h, int which, const void* in, void* out, bs_dtype t, int64_t M,
+                          cudaStream_t st) {
   const int N = (int)h->N;
+  const TwistPlan& tp = h->twist[which];
   if (t == BS_F64)
-    return launch_tw<double>(*h, N, static_cast<const double*>(in), static_cast<double*>(out), M, st);
-  return launch_tw<float>(*h, N, static_cast<const float*>(in), static_cast<float*>(out), M, st);
+    return launch_tw<double>(tp, N, static_cast<const double*>(in), static_cast<double*>(out), M, st);
+  return launch_tw<float>(tp, N, static_cast<const float*>(in), static_cast<float*>(out), M, st);
 }
 
 }  // namespace bs

@@ -111,3 +111,40 @@ def test_periodic_handle_not_twisted(bs):
     X1 = _solve(bs, f, Bh, torch.float64, 1)
     assert np.array_equal(X2, X1)
     assert rel_l2(X2, oracle.periodic_tri_solve_bands(pb, Bh)) < TOL64
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("N,M", [(2, 5), (3, 1), (64, 1024), (333, 77), (1000, 130)])
+def test_twisted_adjoint_and_band_grad(bs, N, M, dtype, tol):
+    """A^{-T} G by the two-ended sweep of A^T (non-symmetric bands, so A^T's
+    plans differ from A's), then the band gradient."""
+    rng = np.random.default_rng(3 * N + M)
+    bands = synth.random_tri_bands(N, rng)
+    Bh = rng.uniform(-1, 1, (N, M))
+    Gh = rng.uniform(-1, 1, (N, M))
+    if dtype == torch.float32:
+        Bh = Bh.astype(np.float32).astype(np.float64)
+        Gh = Gh.astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    res = {}
+    for tw in (2, 1):
+        bs.set_option(bs.OPT_TWISTED, tw)
+        bs.set_option(bs.OPT_PARTITION, 1)
+        try:
+            X = torch.tensor(Bh, dtype=dtype, device="cuda")
+            bs.solve(f, X)
+            G = torch.tensor(Gh, dtype=dtype, device="cuda")
+            G, db = bs.solve_adjoint(f, G, X=X)
+            torch.cuda.synchronize()
+        finally:
+            bs.set_option(bs.OPT_TWISTED, 0)
+            bs.set_option(bs.OPT_PARTITION, 0)
+        res[tw] = (X.double().cpu().numpy(), G.double().cpu().numpy(), db.cpu().numpy())
+    X, GB, db = res[2]
+    GB_ref = oracle.solve_adjoint(bands, Gh)
+    assert rel_l2(GB, GB_ref) < tol
+    assert rel_l2(X, oracle.solve(bands, Bh)) < tol
+    db_ref = oracle.band_grad(3, GB, X)
+    assert np.max(np.abs(db - db_ref)) / np.max(np.abs(db_ref)) < (1e-13 if dtype == torch.float64 else 1e-6)
+    if dtype == torch.float64:
+        assert rel_l2(GB, res[1][1]) < 1e-13
