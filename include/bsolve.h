@@ -319,8 +319,8 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
  *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 256
  *    systems per SM (except that bs_solve and bs_solve_adjoint take the
- *    two-ended sweep of BS_OPT_TWISTED instead of a two-block partition of a
- *    tridiagonal matrix); 1: never; 2: whenever the handle has one.
+ *    two-ended sweep of BS_OPT_TWISTED instead of a two-block partition);
+ *    1: never; 2: whenever the handle has one.
  *  BS_OPT_UNIFORM: uniform pentadiagonal solves (Sec. 4.1, cuPentUniformBatch).
  *    bs_factor marks a pentadiagonal handle uniform when every in-range entry
  *    of its outermost sub-diagonal (a_i, i = 3..N, 1-based) is the same value
@@ -331,14 +331,15 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    differ from the general sweeps by rounding only).  FP64 solves keep the
  *    general sweeps, which are faster there.  0 (default): used for uniform
  *    handles; 1: never.
- *  BS_OPT_TWISTED: two-ended tridiagonal solves for small batches (not in the
- *    paper).  bs_factor also prepares, for a tridiagonal matrix (and for its
- *    transpose) whose row-reversed elimination (A = U' L') meets no bad
- *    pivot, the meeting row k = N / 2 of a solve in which two threads share
- *    a system: one eliminates rows 1 .. k top-down with A = L U, the other
- *    rows N .. k + 2 bottom-up with A = U' L' (1-based), both meet at row
- *    k + 1 and back-substitute outward -- half the dependent steps per
- *    system.  The result equals the one-thread solve to rounding.
+ *  BS_OPT_TWISTED: two-ended solves for small batches (not in the paper).
+ *    bs_factor also prepares, for a matrix (and for its transpose) whose
+ *    row-reversed elimination (A = U' L') meets no bad pivot, the meeting
+ *    rows of a solve in which two threads share a system: one eliminates
+ *    the top rows with A = L U / L R, the other the bottom rows with
+ *    A = U' L'; the meeting rows (one in the middle of a tridiagonal
+ *    system, two of a pentadiagonal one) are solved from both, and each
+ *    thread back-substitutes outward -- half the dependent steps per system.
+ *    The result equals the one-thread solve to rounding.
  *    0 (default): used by bs_solve and bs_solve_adjoint (BS_F64, BS_F32;
  *    interleaved layout) when a batch has at most 128 systems per SM and
  *    would not be row-partitioned into more than two blocks

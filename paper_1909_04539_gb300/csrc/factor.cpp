@@ -520,24 +520,59 @@ bool reversed_plan(const double* const* bd, int width, int64_t N, HostPlan& out)
   return ok;
 }
 
-// Meeting row k = N / 2 of the two-ended sweeps of a tridiagonal matrix with
-// zeroed out-of-range bands bz (3 x N), given its plans top (A = L U) and bot
-// (A = U' L'): g_k = b_k - a_k chat_{k-1} - c_k chat'_{k+1}.  False if g_k is
-// zero or not finite.
-bool twist_row(const std::vector<double>& bz, const HostPlan& top, const HostPlan& bot, int64_t N,
-               bs::TwistPlan& t) {
-  const int64_t k = N / 2;
-  const double a = bz[k];                   // band 0, row k (k >= 1)
-  const double c = bz[(size_t)2 * N + k];   // band 2, row k (0 for k = N - 1)
-  const double ch = top.c[(size_t)C_U1 * N + k - 1];
-  const double chr = (k + 1 < N) ? bot.c[(size_t)C_U1 * N + k + 1] : 0.0;
-  const double g = bz[(size_t)N + k] - a * ch - c * chr;
-  if (bad(g)) return false;
+// Meeting rows of the two-ended sweeps (see bs::TwistPlan) of a matrix with
+// zeroed out-of-range bands bz (width x N), given its plans top (A = L U /
+// L R) and bot (A = U' L').  False if the meeting system is singular or not
+// finite.
+bool twist_rows(const std::vector<double>& bz, int width, const HostPlan& top, const HostPlan& bot, int64_t N,
+                bs::TwistPlan& t) {
+  auto band = [&](int q, int64_t i) { return (i >= 0 && i < N) ? bz[(size_t)q * N + i] : 0.0; };
+  auto cf = [&](const HostPlan& p, int q, int64_t i) { return (i >= 0 && i < N) ? p.c[(size_t)q * N + i] : 0.0; };
+  std::memset(t.m, 0, sizeof(t.m));
+  if (width == 3) {
+    // g_k = b_k - a_k chat_{k-1} - c_k chat'_{k+1}
+    const int64_t k = N / 2;
+    const double a = band(0, k), c = band(2, k);
+    const double g = band(1, k) - a * cf(top, C_U1, k - 1) - c * cf(bot, C_U1, k + 1);
+    if (bad(g)) return false;
+    t.k = (int)k;
+    t.m[0] = -a;
+    t.m[1] = -c;
+    t.m[2] = 1.0 / g;
+  } else {
+    // rows k, k+1 with x_{k-1}, x_{k-2} (top back-substitution) and x_{k+2},
+    // x_{k+3} (bottom) as affine functions of x_k, x_{k+1}
+    const int64_t k = (N - 2) / 2;
+    const double g1 = cf(top, C_U1, k - 1), g2 = cf(top, C_U1, k - 2);
+    const double d1 = cf(top, C_U2, k - 1), d2 = cf(top, C_U2, k - 2);
+    const double v1 = cf(bot, C_U1, k + 2), v3 = cf(bot, C_U1, k + 3);
+    const double y1 = cf(bot, C_U2, k + 2), y3 = cf(bot, C_U2, k + 3);
+    const double p2k = g2 * g1 - d2, p2m = g2 * d1;  // x_{k-2}
+    const double p1k = -g1, p1m = -d1;               // x_{k-1}
+    const double q2k = -y1, q2m = -v1;               // x_{k+2}
+    const double q3k = -v3 * q2k, q3m = -v3 * q2m - y3;  // x_{k+3}
+    const double ak = band(0, k), bk = band(1, k), ck = band(2, k), dk = band(3, k), ek = band(4, k);
+    const double a1 = band(0, k + 1), b1 = band(1, k + 1), c1 = band(2, k + 1), d1b = band(3, k + 1),
+                 e1 = band(4, k + 1);
+    const double m00 = ck + ak * p2k + bk * p1k + ek * q2k, m01 = dk + ak * p2m + bk * p1m + ek * q2m;
+    const double m10 = b1 + a1 * p1k + d1b * q2k + e1 * q3k, m11 = c1 + a1 * p1m + d1b * q2m + e1 * q3m;
+    const double det = m00 * m11 - m01 * m10;
+    if (bad(det)) return false;
+    t.k = (int)k;
+    t.m[0] = -ak;
+    t.m[1] = ak * g2 - bk;
+    t.m[2] = -ek;
+    t.m[3] = -a1;
+    t.m[4] = e1 * v3 - d1b;
+    t.m[5] = -e1;
+    t.m[6] = m11 / det;
+    t.m[7] = -m01 / det;
+    t.m[8] = -m10 / det;
+    t.m[9] = m00 / det;
+    for (double v : t.m)
+      if (!std::isfinite(v)) return false;
+  }
   t.ok = true;
-  t.k = (int)k;
-  t.a = a;
-  t.c = c;
-  t.g = 1.0 / g;
   return true;
 }
 
@@ -622,11 +657,11 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   for (int k = 0; k < width; k++) tbd[k] = tb.data() + (size_t)k * N;
   const bool has_part = make_partition(bd, width, N, parts[0]) && make_partition(tbd, width, N, parts[1]);
   const bs_status st = upload_handle(width, N, hp, has_ul, false, entries, b64, out, has_part ? parts : nullptr);
-  if (st != BS_OK || width != 3) return st;
+  if (st != BS_OK) return st;
   // two-ended sweeps (small batches): for A with plans 0 and 2; for A^T with
   // its own two plans, uploaded here
   bs_handle hd = *out;
-  if (has_ul && twist_row(b64, hp[0], hp[2], N, hd->twist[0])) {
+  if (has_ul && twist_rows(b64, width, hp[0], hp[2], N, hd->twist[0])) {
     hd->twist[0].top = &hd->plan[0];
     hd->twist[0].bot = &hd->plan[2];
   }
@@ -634,8 +669,8 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out) {
   tt[0].c.assign((size_t)C_COUNT * N, 0.0);
   tq.c.assign((size_t)C_COUNT * N, 0.0);
   bs::TwistPlan ta{};
-  if (make_plans(tbd, 3, N, tt[0], tq) == 0 && reversed_plan(tbd, 3, N, tt[1]) &&
-      twist_row(tb, tt[0], tt[1], N, ta)) {
+  if (make_plans(tbd, width, N, tt[0], tq) == 0 && reversed_plan(tbd, width, N, tt[1]) &&
+      twist_rows(tb, width, tt[0], tt[1], N, ta)) {
     size_t bytes = 0;
     cudaError_t e = upload_plan(tt[0], hd->tplan[0], bytes);
     if (e == cudaSuccess) e = upload_plan(tt[1], hd->tplan[1], bytes);

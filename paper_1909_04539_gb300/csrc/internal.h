@@ -88,14 +88,20 @@ struct PartPlan {
 }  // namespace bs
 
 namespace bs {
-// Two-ended tridiagonal sweeps (small batches): the even lane of a pair
-// eliminates rows 0 .. k-1 top-down with `top` (A = L U), the odd lane rows
-// N-1 .. k+1 bottom-up with `bot` (A = U' L', coefficients in original row
-// order); they meet at row k with x_k = (f_k - a w_{k-1} - c z_{k+1}) * g.
+// Two-ended sweeps (small batches): the even lane of a pair eliminates rows
+// 0 .. k-1 top-down with `top` (A = L U / L R), the odd lane rows N-1 .. k+h
+// bottom-up with `bot` (A = U' L', coefficients in original row order), h
+// the band half-width; the meeting rows k .. k+h-1 follow from their last
+// forward values w_{k-1}, w_{k-2} and z_{k+h}, z_{k+h+1} with the weights m:
+//   h = 1: x_k = (f_k + m0 w_{k-1} + m1 z_{k+1}) m2
+//          (m0 = -a_k, m1 = -c_k, m2 = 1 / (b_k - a_k chat_{k-1} - c_k chat'_{k+1}))
+//   h = 2: r0 = f_k + m0 w_{k-2} + m1 w_{k-1} + m2 z_{k+2},
+//          r1 = f_{k+1} + m3 w_{k-1} + m4 z_{k+2} + m5 z_{k+3},
+//          (x_k, x_{k+1}) = (m6 r0 + m7 r1, m8 r0 + m9 r1).
 struct TwistPlan {
   bool ok;
   int k;
-  double a, c, g;          // a_k, c_k of the matrix solved, g = 1 / (b_k - a_k chat_{k-1} - c_k chat'_{k+1})
+  double m[10];
   const SweepPlan* top;
   const SweepPlan* bot;
 };

@@ -1,4 +1,4 @@
-// Two-ended ("twisted") tridiagonal solves for small batches.
+// Two-ended ("twisted") banded solves for small batches.
 //
 // With one thread per system (Sec. 2) a batch too small to fill the GPU takes
 // as long as one system's chain of 2N dependent steps (forward, then
@@ -6,17 +6,24 @@
 // the number of active lanes, so that time does not shrink with the batch:
 // N = 64 takes ~14 us for 1 system as for 9728.  Here two threads share a
 // system and the chain halves.  The even lane eliminates rows 0 .. k-1
-// top-down with the factorisation A = L U of Sec. 3.1 (w_i = s_i f_i -
-// l1_i w_{i-1}); the odd lane eliminates rows N-1 .. k+1 bottom-up with the
-// factorisation of the row-reversed matrix, A = U' L' (z_i = s'_i f_i -
-// l1'_i z_{i+1}).  At row k = N / 2 the two meet:
-//   x_k = (f_k - a_k w_{k-1} - c_k z_{k+1}) / g_k,
-//   g_k = b_k - a_k chat_{k-1} - c_k chat'_{k+1},
-// (row k of A with x_{k-1} = w_{k-1} - chat_{k-1} x_k and x_{k+1} = z_{k+1} -
-// chat'_{k+1} x_k substituted), and each lane back-substitutes its half
-// outward: x_i = w_i - chat_i x_{i+1} above, x_i = z_i - chat'_i x_{i-1}
-// below.  N + 1 dependent steps instead of 2N, the same FP64 operations per
-// row as the one-thread sweeps.
+// top-down with the factorisation of Sec. 3.1 / 4.1 (A = L U, A = L R:
+// w_i = s_i f_i - l1_i w_{i-1} - l2_i w_{i-2}); the odd lane eliminates rows
+// N-1 .. k+h bottom-up with the factorisation of the row-reversed matrix,
+// A = U' L' (z_i = s'_i f_i - l1'_i z_{i+1} - l2'_i z_{i+2}), h the band
+// half-width.  The h meeting rows k .. k+h-1 are then solved from the two
+// lanes' last forward values:
+//   tridiagonal:   x_k = (f_k - a_k w_{k-1} - c_k z_{k+1}) / g_k,
+//                  g_k = b_k - a_k chat_{k-1} - c_k chat'_{k+1}
+//   (row k of A with x_{k-1} = w_{k-1} - chat_{k-1} x_k and x_{k+1} = z_{k+1}
+//   - chat'_{k+1} x_k substituted);
+//   pentadiagonal: rows k and k+1 with x_{k-2}, x_{k-1} (from the top lane's
+//   back-substitution) and x_{k+2}, x_{k+3} (bottom lane) written as affine
+//   functions of x_k, x_{k+1}: a 2x2 system whose inverse and right-hand
+//   side weights are formed with the handle.
+// Each lane then back-substitutes its part outward: x_i = w_i - u1_i x_{i+1}
+// - u2_i x_{i+2} above, x_i = z_i - u1'_i x_{i-1} - u2'_i x_{i-2} below.
+// About N + 2h dependent steps instead of 2N, and per row the same FP64
+// operations as the one-thread sweeps.
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -25,32 +32,38 @@ constexpr int kTwThreads = 64;
 
 template <typename C>
 struct TwistArgs {
-  const C* s[2];   // [0] top half: plan of A = L U; [1] bottom half: plan of A = U' L'
+  const C* s[2];   // [0] top part: plan of A = L U / L R; [1] bottom part: plan of A = U' L'
   const C* l1[2];  // (each indexed by matrix row)
+  const C* l2[2];
   const C* u1[2];
-  int k;           // meeting row
-  C a, c, g;       // a_k, c_k and 1 / g_k
+  const C* u2[2];
+  int k;           // first meeting row
+  C m[10];         // meeting-row weights (TwistPlan::m)
 };
 
-// Even lane (h = 0): rows 0, 1, .., k-1 forward, then k-1, .., 0 backward.
-// Odd lane (h = 1): rows N-1, .., k+1 forward, then k+1, .., N-1 backward.
-template <typename C, int U>
+// Even lane (t = 0): rows 0, 1, .., k-1 forward, then k-1, .., 0 backward.
+// Odd lane (t = 1): rows N-1, .., k+BW forward, then k+BW, .., N-1 backward.
+template <typename C, int BW, int U>
 __global__ void __launch_bounds__(kTwThreads)
 k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == out allowed
-  const int h = threadIdx.x & 1;
+  const int t = threadIdx.x & 1;
   const int k = ta.k;
-  const int n = h ? N - 1 - k : k;       // rows this lane eliminates
-  const int r0 = h ? N - 1 : 0;          // its first row
-  const int dr = h ? -1 : 1;             // row step of its forward sweep
-  const C* __restrict__ S = h ? ta.s[1] : ta.s[0];  // selects, not a dynamic index into the parameters
-  const C* __restrict__ L1 = h ? ta.l1[1] : ta.l1[0];
-  const C* __restrict__ U1 = h ? ta.u1[1] : ta.u1[0];
+  const int n = t ? N - k - BW : k;      // rows this lane eliminates
+  const int r0 = t ? N - 1 : 0;          // its first row
+  const int dr = t ? -1 : 1;             // row step of its forward sweep
+  // selects, not a dynamic index into the kernel parameters
+  const C* __restrict__ S = t ? ta.s[1] : ta.s[0];
+  const C* __restrict__ L1 = t ? ta.l1[1] : ta.l1[0];
+  const C* __restrict__ L2 = t ? ta.l2[1] : ta.l2[0];
+  const C* __restrict__ U1 = t ? ta.u1[1] : ta.u1[0];
+  const C* __restrict__ U2 = t ? ta.u2[1] : ta.u2[0];
+  const unsigned pair = 3u << ((threadIdx.x & 31) & ~1u);
   const int64_t pairs = ((int64_t)gridDim.x * blockDim.x) >> 1;
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1; j < M; j += pairs) {
-    const int64_t dp = h ? -M : M;       // pointer step of the forward sweep
+    const int64_t dp = t ? -M : M;       // pointer step of the forward sweep
     // forward sweep over this lane's n rows, U rows per block, the next
     // block's inputs requested before the current block is computed
-    C w = C(0);
+    C w1 = C(0), w2 = C(0);  // the last and second-to-last forward values
     {
       const C* pin = in + (int64_t)r0 * M + j;
       C* pout = out + (int64_t)r0 * M + j;
@@ -61,17 +74,22 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
           if (q0 + u < n) f[u] = pin[(int64_t)(q0 + u) * dp];
       };
       auto run = [&](C (&f)[U], int q0) {
-        C sv[U], lv[U];
+        C sv[U], lv[U], lw[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const int i = r0 + dr * (q0 + u < n ? q0 + u : q0);
           sv[u] = __ldg(S + i);
           lv[u] = __ldg(L1 + i);
+          lw[u] = BW == 2 ? __ldg(L2 + i) : C(0);
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
           if (q0 + u < n) {
-            w = fma(-lv[u], w, f[u] * sv[u]);
+            C w = f[u] * sv[u];
+            if (BW == 2) w = fma(-lw[u], w2, w);
+            w = fma(-lv[u], w1, w);
+            w2 = w1;
+            w1 = w;
             pout[(int64_t)(q0 + u) * dp] = w;
           }
       };
@@ -84,22 +102,39 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
         run(fb, q0 + U);
       }
     }
-    // meeting row, read and written by the even lane only: it receives
-    // z_{k+1} (0 when k = N - 1) from the odd lane and hands x_k back.  The
-    // shuffles name exactly the two lanes of the pair, whose loops above may
-    // have run different trip counts.
-    const unsigned pair = 3u << ((threadIdx.x & 31) & ~1u);
-    const C zk = __shfl_xor_sync(pair, w, 1);
-    C x = C(0);
-    if (!h) {
-      x = fma(-ta.c, zk, fma(-ta.a, w, in[(int64_t)k * M + j])) * ta.g;
-      out[(int64_t)k * M + j] = x;
+    // meeting rows, read and written by the even lane only: it receives the
+    // odd lane's last forward values (0 where that lane has fewer rows) and
+    // hands the meeting rows' solution back.  The shuffles name exactly the
+    // two lanes of the pair, whose loops above may have run different trip
+    // counts.
+    const C z1 = __shfl_xor_sync(pair, w1, 1);
+    const C z2 = __shfl_xor_sync(pair, w2, 1);
+    C x1 = C(0), x2 = C(0);  // backward state: the nearest and next solved rows
+    if (t == 0) {
+      const C* m = ta.m;
+      if constexpr (BW == 1) {
+        x1 = fma(m[1], z1, fma(m[0], w1, in[(int64_t)k * M + j])) * m[2];
+        out[(int64_t)k * M + j] = x1;
+      } else {
+        const C r0v = fma(m[2], z1, fma(m[1], w1, fma(m[0], w2, in[(int64_t)k * M + j])));
+        const C r1v = fma(m[5], z2, fma(m[4], z1, fma(m[3], w1, in[(int64_t)(k + 1) * M + j])));
+        x1 = fma(m[7], r1v, m[6] * r0v);  // x_k
+        x2 = fma(m[9], r1v, m[8] * r0v);  // x_{k+1}
+        out[(int64_t)k * M + j] = x1;
+        out[(int64_t)(k + 1) * M + j] = x2;
+      }
     }
-    const C xe = __shfl_xor_sync(pair, x, 1);
-    if (h) x = xe;
-    // backward sweep outward from row k over the same n rows
     {
-      const int rb = k - dr;  // first row: k - 1 (even) or k + 1 (odd)
+      const C e1 = __shfl_xor_sync(pair, x1, 1);
+      const C e2 = __shfl_xor_sync(pair, x2, 1);
+      if (t) {  // below the meeting rows the nearest solved row is the last one
+        x1 = BW == 2 ? e2 : e1;
+        x2 = BW == 2 ? e1 : C(0);
+      }
+    }
+    // backward sweep outward from the meeting rows over the same n rows
+    {
+      const int rb = t ? k + BW : k - 1;  // first row
       C* pb = out + (int64_t)rb * M + j;
       C fa[U], fb[U];
       auto load = [&](C (&f)[U], int q0) {
@@ -108,13 +143,21 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
           if (q0 + u < n) f[u] = pb[-(int64_t)(q0 + u) * dp];
       };
       auto run = [&](C (&f)[U], int q0) {
-        C uv[U];
+        C uv[U], uw[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) uv[u] = __ldg(U1 + rb - dr * (q0 + u < n ? q0 + u : q0));
+        for (int u = 0; u < U; u++) {
+          const int i = rb - dr * (q0 + u < n ? q0 + u : q0);
+          uv[u] = __ldg(U1 + i);
+          uw[u] = BW == 2 ? __ldg(U2 + i) : C(0);
+        }
 #pragma unroll
         for (int u = 0; u < U; u++)
           if (q0 + u < n) {
-            x = fma(-uv[u], x, f[u]);
+            C x = f[u];
+            if (BW == 2) x = fma(-uw[u], x2, x);
+            x = fma(-uv[u], x1, x);
+            x2 = x1;
+            x1 = x;
             pb[-(int64_t)(q0 + u) * dp] = x;
           }
       };
@@ -131,7 +174,7 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
 }
 
 template <typename C>
-static cudaError_t launch_tw(const TwistPlan& tp, int N, const C* in, C* out, int64_t M, cudaStream_t st) {
+static cudaError_t launch_tw(const TwistPlan& tp, int bw, int N, const C* in, C* out, int64_t M, cudaStream_t st) {
   TwistArgs<C> ta{};
   for (int q = 0; q < 2; q++) {
     const SweepPlan& p = q == 0 ? *tp.top : *tp.bot;
@@ -143,29 +186,32 @@ static cudaError_t launch_tw(const TwistPlan& tp, int N, const C* in, C* out, in
     const Coefs<C> cf = coefs_of<C>(base, N);
     ta.s[q] = cf.s;
     ta.l1[q] = cf.l1;
+    ta.l2[q] = cf.l2;
     ta.u1[q] = cf.u1;
+    ta.u2[q] = cf.u2;
   }
   ta.k = tp.k;
-  ta.a = (C)tp.a;
-  ta.c = (C)tp.c;
-  ta.g = (C)tp.g;
+  for (int q = 0; q < 10; q++) ta.m[q] = (C)tp.m[q];
   const int64_t threads = 2 * M;
   int64_t grid = (threads + kTwThreads - 1) / kTwThreads;
   const int64_t cap = (int64_t)device_info().sms * (2048 / kTwThreads);
   if (grid > cap) grid = cap;
-  k_sweep_tw<C, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
+  if (bw == 1)
+    k_sweep_tw<C, 1, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
+  else
+    k_sweep_tw<C, 2, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
   return cudaGetLastError();
 }
 
 // Whether a solve with A (which = 0) or A^T (which = 1) takes the two-ended
-// sweep: tridiagonal, not periodic, the handle has a meeting row for that
-// matrix, interleaved layout, and at most 128 systems per SM; BS_OPT_TWISTED
-// 1 never, 2 whenever the handle allows.  Measured on GB300 (N = 64 .. 2048,
-// FP64 and FP32): 1.8-2.3x faster than one thread per system up to 64
-// systems per SM, 1.2-1.6x at 128, slower from 256 on, where the one-thread
-// sweeps already keep the SMs busy.
+// sweep: not periodic, the handle has meeting rows for that matrix,
+// interleaved layout, and at most 128 systems per SM; BS_OPT_TWISTED 1
+// never, 2 whenever the handle allows.  Measured on GB300 (tridiagonal,
+// N = 64 .. 2048, FP64 and FP32): 1.8-2.3x faster than one thread per system
+// up to 64 systems per SM, 1.2-1.6x at 128, slower from 256 on, where the
+// one-thread sweeps already keep the SMs busy.
 bool use_twisted(bs_handle h, int which, bs_layout layout, int64_t M) {
-  if (h->width != 3 || h->periodic || !h->twist[which].ok || layout != BS_INTERLEAVED) return false;
+  if (h->periodic || !h->twist[which].ok || layout != BS_INTERLEAVED) return false;
   const int64_t o = option(BS_OPT_TWISTED);
   if (o == 1) return false;
   if (o == 2) return true;
@@ -175,10 +221,11 @@ bool use_twisted(bs_handle h, int which, bs_layout layout, int64_t M) {
 cudaError_t sweep_twisted(bs_handle h, int which, const void* in, void* out, bs_dtype t, int64_t M,
                           cudaStream_t st) {
   const int N = (int)h->N;
+  const int bw = h->width / 2;
   const TwistPlan& tp = h->twist[which];
   if (t == BS_F64)
-    return launch_tw<double>(tp, N, static_cast<const double*>(in), static_cast<double*>(out), M, st);
-  return launch_tw<float>(tp, N, static_cast<const float*>(in), static_cast<float*>(out), M, st);
+    return launch_tw<double>(tp, bw, N, static_cast<const double*>(in), static_cast<double*>(out), M, st);
+  return launch_tw<float>(tp, bw, N, static_cast<const float*>(in), static_cast<float*>(out), M, st);
 }
 
 }  // namespace bs

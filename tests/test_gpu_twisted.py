@@ -1,8 +1,9 @@
-"""GPU parity of the two-ended tridiagonal solves (two threads per system
-meeting at row N/2; used for small batches) against the CPU FP64 oracle,
-through the C ABI.  Tolerances as for the one-thread sweeps: FP64 1e-12
-relative L2, FP32 2e-5; the two-ended and one-thread FP64 results agree to
-1e-13 (same arithmetic per row, another elimination order)."""
+"""GPU parity of the two-ended tridiagonal and pentadiagonal solves (two
+threads per system meeting in the middle; used for small batches) against
+the CPU FP64 oracle, through the C ABI.  Tolerances as for the one-thread
+sweeps: FP64 1e-12 relative L2, FP32 2e-5; the two-ended and one-thread FP64
+results agree to 1e-13 (same arithmetic per row, another elimination
+order)."""
 import numpy as np
 import pytest
 import torch
@@ -39,11 +40,17 @@ def _solve(bs, f, Bh, dtype, twisted, layout="interleaved"):
     return B.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5, 16, 17, 64, 257, 1000])
+def _bands(width, N, rng):
+    return synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
+
+
+@pytest.mark.parametrize("width,N", [(3, 2), (3, 3), (3, 4), (3, 5), (3, 16), (3, 17), (3, 64), (3, 257),
+                                     (3, 1000), (5, 4), (5, 5), (5, 6), (5, 7), (5, 16), (5, 33), (5, 64),
+                                     (5, 255), (5, 1000)])
 @pytest.mark.parametrize("M", [1, 2, 7, 33, 1024])
-def test_twisted_fp64(bs, N, M):
-    rng = np.random.default_rng(N * 7919 + M)
-    bands = synth.random_tri_bands(N, rng)
+def test_twisted_fp64(bs, width, N, M):
+    rng = np.random.default_rng(N * 7919 + M + width)
+    bands = _bands(width, N, rng)
     Bh = rng.uniform(-1, 1, (N, M))
     f = bs.Factor(bands)
     Xt = _solve(bs, f, Bh, torch.float64, 2)
@@ -53,23 +60,27 @@ def test_twisted_fp64(bs, N, M):
     assert rel_l2(Xt, X1) < 1e-13
 
 
-@pytest.mark.parametrize("N,M", [(2, 3), (5, 1), (64, 1024), (333, 130), (1024, 4099)])
-def test_twisted_fp32(bs, N, M):
-    rng = np.random.default_rng(N + 31 * M)
-    bands = synth.random_tri_bands(N, rng)
+@pytest.mark.parametrize("width,N,M", [(3, 2, 3), (3, 5, 1), (3, 64, 1024), (3, 333, 130), (3, 1024, 4099),
+                                       (5, 4, 3), (5, 9, 1), (5, 64, 1024), (5, 333, 130), (5, 1024, 4099)])
+def test_twisted_fp32(bs, width, N, M):
+    rng = np.random.default_rng(N + 31 * M + width)
+    bands = _bands(width, N, rng)
     Bh = rng.uniform(-1, 1, (N, M)).astype(np.float32).astype(np.float64)
     f = bs.Factor(bands)
     X = _solve(bs, f, Bh, torch.float32, 2)
     assert rel_l2(X, oracle.solve(bands, Bh)) < TOL32
 
 
-@pytest.mark.parametrize("name", ["adi", "spline", "toeplitz_weak"])
+@pytest.mark.parametrize("name", ["adi", "spline", "toeplitz_weak", "clamped_hyper", "hyper"])
 def test_twisted_structured_bands(bs, name):
-    """Toeplitz matrices (ADI I - 0.5 d2, the [1,4,1]/6 spline, and a barely
-    dominant (-1, 2.01, -1)) at N = 512, 1000 systems."""
+    """Toeplitz-like matrices (ADI I - 0.5 d2, the [1,4,1]/6 spline, a barely
+    dominant (-1, 2.01, -1), the clamped I + 0.1 D4 and I + 0.4 D4) at
+    N = 512, 1000 systems."""
     N, M = 512, 1000
     bands = {"adi": synth.adi_bands(N, 0.5), "spline": synth.spline_bands(N),
-             "toeplitz_weak": synth.toeplitz_bands(N, (-1.0, 2.01, -1.0))}[name]
+             "toeplitz_weak": synth.toeplitz_bands(N, (-1.0, 2.01, -1.0)),
+             "clamped_hyper": synth.clamped_hyperdiffusion_bands(N, 0.1),
+             "hyper": synth.toeplitz_bands(N, (0.4, -1.6, 3.4, -1.6, 0.4))}[name]
     rng = np.random.default_rng(17)
     Bh = rng.uniform(-1, 1, (N, M))
     f = bs.Factor(bands)
@@ -81,12 +92,13 @@ def test_twisted_structured_bands(bs, name):
     assert rel_l2(Xt, X1) < 1e-12
 
 
-def test_default_choice(bs):
-    """Small tridiagonal batches take the two-ended sweep by default (not
-    bitwise the one-thread result, right against the oracle); large ones,
-    the strided layout and pentadiagonal handles do not."""
+@pytest.mark.parametrize("width", [3, 5])
+def test_default_choice(bs, width):
+    """Small batches take the two-ended sweep by default (not bitwise the
+    one-thread result, right against the oracle); large ones and the strided
+    layout do not."""
     rng = np.random.default_rng(5)
-    bands = synth.random_tri_bands(64, rng)
+    bands = _bands(width, 64, rng)
     f = bs.Factor(bands)
     Bh = rng.uniform(-1, 1, (64, 1024))
     X0 = _solve(bs, f, Bh, torch.float64, 0)
@@ -98,9 +110,6 @@ def test_default_choice(bs):
                           _solve(bs, f, Bs, torch.float64, 1, "strided"))
     Bl = rng.uniform(-1, 1, (64, 65536))
     assert np.array_equal(_solve(bs, f, Bl, torch.float64, 0), _solve(bs, f, Bl, torch.float64, 1))
-    pb = synth.random_penta_bands(64, rng)
-    fp = bs.Factor(pb)
-    assert np.array_equal(_solve(bs, fp, Bh, torch.float64, 0), _solve(bs, fp, Bh, torch.float64, 2))
 
 
 def test_periodic_handle_not_twisted(bs):
@@ -114,12 +123,13 @@ def test_periodic_handle_not_twisted(bs):
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
-@pytest.mark.parametrize("N,M", [(2, 5), (3, 1), (64, 1024), (333, 77), (1000, 130)])
-def test_twisted_adjoint_and_band_grad(bs, N, M, dtype, tol):
+@pytest.mark.parametrize("width,N,M", [(3, 2, 5), (3, 3, 1), (3, 64, 1024), (3, 333, 77), (3, 1000, 130),
+                                       (5, 4, 5), (5, 7, 1), (5, 64, 1024), (5, 333, 77), (5, 1000, 130)])
+def test_twisted_adjoint_and_band_grad(bs, width, N, M, dtype, tol):
     """A^{-T} G by the two-ended sweep of A^T (non-symmetric bands, so A^T's
     plans differ from A's), then the band gradient."""
-    rng = np.random.default_rng(3 * N + M)
-    bands = synth.random_tri_bands(N, rng)
+    rng = np.random.default_rng(3 * N + M + width)
+    bands = _bands(width, N, rng)
     Bh = rng.uniform(-1, 1, (N, M))
     Gh = rng.uniform(-1, 1, (N, M))
     if dtype == torch.float32:
@@ -144,7 +154,7 @@ def test_twisted_adjoint_and_band_grad(bs, N, M, dtype, tol):
     GB_ref = oracle.solve_adjoint(bands, Gh)
     assert rel_l2(GB, GB_ref) < tol
     assert rel_l2(X, oracle.solve(bands, Bh)) < tol
-    db_ref = oracle.band_grad(3, GB, X)
+    db_ref = oracle.band_grad(width, GB, X)
     assert np.max(np.abs(db - db_ref)) / np.max(np.abs(db_ref)) < (1e-13 if dtype == torch.float64 else 1e-6)
     if dtype == torch.float64:
         assert rel_l2(GB, res[1][1]) < 1e-13

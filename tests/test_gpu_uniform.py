@@ -27,6 +27,7 @@ def bs():
     yield m
     m.set_option(m.OPT_UNIFORM, 0)
     m.set_option(m.OPT_PARTITION, 0)
+    m.set_option(m.OPT_TWISTED, 0)
 
 
 def _bands(kind, N, rng):
@@ -37,8 +38,11 @@ def _bands(kind, N, rng):
 
 
 def _solve(bs, f, Bh, dtype, layout, uniform_opt):
+    """The one-thread sweeps (no partition, no two-ended sweep), with the
+    scalar-eps form allowed (0) or not (1)."""
     bs.set_option(bs.OPT_UNIFORM, uniform_opt)
     bs.set_option(bs.OPT_PARTITION, 1)
+    bs.set_option(bs.OPT_TWISTED, 1)
     try:
         B = torch.tensor(Bh, dtype=dtype, device="cuda")
         bs.solve(f, B, layout)
@@ -46,6 +50,7 @@ def _solve(bs, f, Bh, dtype, layout, uniform_opt):
     finally:
         bs.set_option(bs.OPT_UNIFORM, 0)
         bs.set_option(bs.OPT_PARTITION, 0)
+        bs.set_option(bs.OPT_TWISTED, 0)
     return B.double().cpu().numpy()
 
 
@@ -112,6 +117,7 @@ def test_uniform_adjoint_and_band_grad(bs, layout, dtype, tol):
     tr = (lambda A: A) if layout == "interleaved" else (lambda A: np.ascontiguousarray(A.T))
     f = bs.Factor(bands)
     bs.set_option(bs.OPT_PARTITION, 1)
+    bs.set_option(bs.OPT_TWISTED, 1)
     try:
         X = torch.tensor(tr(B), dtype=dtype, device="cuda")
         bs.solve(f, X, layout)
@@ -120,6 +126,7 @@ def test_uniform_adjoint_and_band_grad(bs, layout, dtype, tol):
         torch.cuda.synchronize()
     finally:
         bs.set_option(bs.OPT_PARTITION, 0)
+        bs.set_option(bs.OPT_TWISTED, 0)
     GB_ref = oracle.solve_adjoint(bands, tr(Gm), layout)
     assert rel_l2(G.double().cpu().numpy(), GB_ref) < tol
     db_ref = oracle.band_grad(5, G.double().cpu().numpy(), X.double().cpu().numpy(), layout)
