@@ -318,8 +318,9 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    corrects the rows near the block edges; the result is the same as the
  *    unpartitioned solve's to rounding.  0 (default): used by bs_solve, bs_solve_bf16,
  *    bs_solve_adjoint and bs_adi_halfstep when the batch has fewer than 256
- *    systems per SM (except that bs_solve and bs_solve_adjoint take the
- *    two-ended sweep of BS_OPT_TWISTED instead of a two-block partition);
+ *    systems per SM (except that bs_solve, bs_solve_bf16 and bs_solve_adjoint
+ *    take the two-ended sweep of BS_OPT_TWISTED instead of a two-block
+ *    partition);
  *    1: never; 2: whenever the handle has one.
  *  BS_OPT_UNIFORM: uniform pentadiagonal solves (Sec. 4.1, cuPentUniformBatch).
  *    bs_factor marks a pentadiagonal handle uniform when every in-range entry
@@ -340,8 +341,8 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    system, two of a pentadiagonal one) are solved from both, and each
  *    thread back-substitutes outward -- half the dependent steps per system.
  *    The result equals the one-thread solve to rounding.
- *    0 (default): used by bs_solve and bs_solve_adjoint (BS_F64, BS_F32;
- *    interleaved layout) when a batch has at most 128 systems per SM and
+ *    0 (default): used by bs_solve, bs_solve_bf16 and bs_solve_adjoint
+ *    (interleaved layout) when a batch has at most 128 systems per SM and
  *    would not be row-partitioned into more than two blocks
  *    (BS_OPT_PARTITION 2 keeps the partition); 1: never; 2: whenever the
  *    handle allows (interleaved, not partitioned). */

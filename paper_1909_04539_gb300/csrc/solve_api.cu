@@ -143,8 +143,13 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
   const size_t nm = (size_t)h->N * (size_t)M;
   if (b0 < x0 + nm * 4 && x0 < b0 + nm * 2) return set_error(BS_EINVAL, "bs_solve_bf16: B and X overlap");
   const bool part = use_partition(h, M);
-  const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (take_twisted(h, 0, layout, M, part)) {
+    const cudaError_t e = sweep_twisted(h, 0, B, X, BS_BF16, M, st);
+    if (e != cudaSuccess) return cuda_error(e, "bs_solve_bf16 launch");
+    return BS_OK;
+  }
+  const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   cudaError_t e = sweep_bf16(p, false, (int)h->N, B, X, layout, M, st, part ? h->part[0].L : 0,
                              part ? h->part[0].P : 1);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve_bf16 launch");

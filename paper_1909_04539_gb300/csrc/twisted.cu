@@ -41,11 +41,20 @@ struct TwistArgs {
   C m[10];         // meeting-row weights (TwistPlan::m)
 };
 
+// One input value widened to the compute type (BF16 storage: exact in FP32).
+template <typename C, typename Sin>
+__device__ __forceinline__ C tw_load(const Sin* p) {
+  if constexpr (std::is_same<Sin, __nv_bfloat16>::value)
+    return bf16_bits_to_float(*reinterpret_cast<const unsigned short*>(p));
+  else
+    return *p;
+}
+
 // Even lane (t = 0): rows 0, 1, .., k-1 forward, then k-1, .., 0 backward.
 // Odd lane (t = 1): rows N-1, .., k+BW forward, then k+BW, .., N-1 backward.
-template <typename C, int BW, int U>
+template <typename C, typename Sin, int BW, int U>
 __global__ void __launch_bounds__(kTwThreads)
-k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == out allowed
+k_sweep_tw(TwistArgs<C> ta, int N, const Sin* in, C* out, int64_t M) {  // in == out allowed
   const int t = threadIdx.x & 1;
   const int k = ta.k;
   const int n = t ? N - k - BW : k;      // rows this lane eliminates
@@ -65,13 +74,13 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
     // block's inputs requested before the current block is computed
     C w1 = C(0), w2 = C(0);  // the last and second-to-last forward values
     {
-      const C* pin = in + (int64_t)r0 * M + j;
+      const Sin* pin = in + (int64_t)r0 * M + j;
       C* pout = out + (int64_t)r0 * M + j;
       C fa[U], fb[U];
       auto load = [&](C (&f)[U], int q0) {
 #pragma unroll
         for (int u = 0; u < U; u++)
-          if (q0 + u < n) f[u] = pin[(int64_t)(q0 + u) * dp];
+          if (q0 + u < n) f[u] = tw_load<C>(pin + (int64_t)(q0 + u) * dp);
       };
       auto run = [&](C (&f)[U], int q0) {
         C sv[U], lv[U], lw[U];
@@ -113,11 +122,11 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
     if (t == 0) {
       const C* m = ta.m;
       if constexpr (BW == 1) {
-        x1 = fma(m[1], z1, fma(m[0], w1, in[(int64_t)k * M + j])) * m[2];
+        x1 = fma(m[1], z1, fma(m[0], w1, tw_load<C>(in + (int64_t)k * M + j))) * m[2];
         out[(int64_t)k * M + j] = x1;
       } else {
-        const C r0v = fma(m[2], z1, fma(m[1], w1, fma(m[0], w2, in[(int64_t)k * M + j])));
-        const C r1v = fma(m[5], z2, fma(m[4], z1, fma(m[3], w1, in[(int64_t)(k + 1) * M + j])));
+        const C r0v = fma(m[2], z1, fma(m[1], w1, fma(m[0], w2, tw_load<C>(in + (int64_t)k * M + j))));
+        const C r1v = fma(m[5], z2, fma(m[4], z1, fma(m[3], w1, tw_load<C>(in + (int64_t)(k + 1) * M + j))));
         x1 = fma(m[7], r1v, m[6] * r0v);  // x_k
         x2 = fma(m[9], r1v, m[8] * r0v);  // x_{k+1}
         out[(int64_t)k * M + j] = x1;
@@ -173,8 +182,8 @@ k_sweep_tw(TwistArgs<C> ta, int N, const C* in, C* out, int64_t M) {  // in == o
   }
 }
 
-template <typename C>
-static cudaError_t launch_tw(const TwistPlan& tp, int bw, int N, const C* in, C* out, int64_t M, cudaStream_t st) {
+template <typename C, typename Sin>
+static cudaError_t launch_tw(const TwistPlan& tp, int bw, int N, const Sin* in, C* out, int64_t M, cudaStream_t st) {
   TwistArgs<C> ta{};
   for (int q = 0; q < 2; q++) {
     const SweepPlan& p = q == 0 ? *tp.top : *tp.bot;
@@ -197,9 +206,9 @@ static cudaError_t launch_tw(const TwistPlan& tp, int bw, int N, const C* in, C*
   const int64_t cap = (int64_t)device_info().sms * (2048 / kTwThreads);
   if (grid > cap) grid = cap;
   if (bw == 1)
-    k_sweep_tw<C, 1, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
+    k_sweep_tw<C, Sin, 1, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
   else
-    k_sweep_tw<C, 2, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
+    k_sweep_tw<C, Sin, 2, 8><<<(int)grid, kTwThreads, 0, st>>>(ta, N, in, out, M);
   return cudaGetLastError();
 }
 
@@ -218,6 +227,7 @@ bool use_twisted(bs_handle h, int which, bs_layout layout, int64_t M) {
   return M <= (int64_t)device_info().sms * 128;
 }
 
+// t: storage type of `in` (BS_BF16: FP32 arithmetic and output).
 cudaError_t sweep_twisted(bs_handle h, int which, const void* in, void* out, bs_dtype t, int64_t M,
                           cudaStream_t st) {
   const int N = (int)h->N;
@@ -225,6 +235,8 @@ cudaError_t sweep_twisted(bs_handle h, int which, const void* in, void* out, bs_
   const TwistPlan& tp = h->twist[which];
   if (t == BS_F64)
     return launch_tw<double>(tp, bw, N, static_cast<const double*>(in), static_cast<double*>(out), M, st);
+  if (t == BS_BF16)
+    return launch_tw<float>(tp, bw, N, static_cast<const __nv_bfloat16*>(in), static_cast<float*>(out), M, st);
   return launch_tw<float>(tp, bw, N, static_cast<const float*>(in), static_cast<float*>(out), M, st);
 }
 

@@ -158,3 +158,25 @@ def test_twisted_adjoint_and_band_grad(bs, width, N, M, dtype, tol):
     assert np.max(np.abs(db - db_ref)) / np.max(np.abs(db_ref)) < (1e-13 if dtype == torch.float64 else 1e-6)
     if dtype == torch.float64:
         assert rel_l2(GB, res[1][1]) < 1e-13
+
+
+@pytest.mark.parametrize("width,N,M", [(3, 64, 1024), (3, 5, 3), (5, 64, 1000), (5, 300, 77)])
+def test_twisted_bf16_storage(bs, width, N, M):
+    """BF16-stored right-hand sides, FP32 arithmetic and output: two-ended
+    against the oracle on the BF16 values and against the one-thread sweep."""
+    rng = np.random.default_rng(N + M + width)
+    bands = _bands(width, N, rng)
+    f = bs.Factor(bands)
+    B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.bfloat16, device="cuda")
+    out = {}
+    for tw in (2, 1):
+        bs.set_option(bs.OPT_TWISTED, tw)
+        bs.set_option(bs.OPT_PARTITION, 1)
+        try:
+            out[tw] = bs.solve_bf16(f, B).double().cpu().numpy()
+        finally:
+            bs.set_option(bs.OPT_TWISTED, 0)
+            bs.set_option(bs.OPT_PARTITION, 0)
+    ref = oracle.solve(bands, B.double().cpu().numpy())
+    assert rel_l2(out[2], ref) < TOL32
+    assert rel_l2(out[2], out[1]) < TOL32

@@ -95,10 +95,12 @@ def test_uniform_bf16(bs):
     f = bs.Factor(bands)
     B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.bfloat16, device="cuda")
     bs.set_option(bs.OPT_PARTITION, 1)
+    bs.set_option(bs.OPT_TWISTED, 1)
     try:
         X = bs.solve_bf16(f, B)
     finally:
         bs.set_option(bs.OPT_PARTITION, 0)
+        bs.set_option(bs.OPT_TWISTED, 0)
     ref = oracle.solve(bands, B.double().cpu().numpy())
     assert rel_l2(X.double().cpu().numpy(), ref) < TOL32
 
