@@ -735,71 +735,84 @@ def run_e2e(bs, f, N, M, st, args, world):
     """Same three solves through the public API with pinned host buffers:
     each step copies its inputs host->device and its results back.  Steps
     are pipelined the way a user streaming batches would run them: two sets
-    of device buffers, the host->device copies of step k+1 and the
-    device->host copies of step k-1 on their own streams while step k
-    computes (ordered by events).  The same steps run one after another on
-    one stream are reported beside it."""
+    of device input buffers and two of output buffers, the host->device
+    copies of step k+1 and the device->host copies of step k-1 on their own
+    streams while step k computes (ordered by events).  A step first copies
+    its in-place operands (B, G) from its input set to its output set on the
+    device, so the next step's inputs may arrive while this step's results
+    are still being read back.  The same steps run one after another on one
+    stream are reported beside it."""
     import torch
 
-    steps = max(1, min(args.steps, 10))
+    steps = max(1, min(args.steps, 50))
     hB = torch.empty((N, M), dtype=torch.float64, pin_memory=True).normal_()
     hB32 = hB.float().pin_memory()
     hG = torch.empty((N, M), dtype=torch.float64, pin_memory=True).uniform_(-1, 1)
 
-    class Set:
+    class Inputs:
         def __init__(self):
             self.dB = torch.empty((N, M), dtype=torch.float64, device="cuda")
             self.dB32 = torch.empty((N, M), dtype=torch.float32, device="cuda")
             self.dG = torch.empty((N, M), dtype=torch.float64, device="cuda")
+            self.h2d = torch.cuda.Event()
+            self.used = torch.cuda.Event()   # the step's compute has read them
+
+    class Outputs:
+        def __init__(self):
+            self.dX = torch.empty((N, M), dtype=torch.float64, device="cuda")
             self.dXR = torch.empty((N, M), dtype=torch.float64, device="cuda")
+            self.dGB = torch.empty((N, M), dtype=torch.float64, device="cuda")
             self.db = torch.empty((5, N), dtype=torch.float64, device="cuda")
             self.oX = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
             self.oXR = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
             self.oG = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
             self.odb = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
-            self.h2d = torch.cuda.Event()
             self.comp = torch.cuda.Event()
             self.d2h = torch.cuda.Event()
 
-    sets = [Set(), Set()]
+    ins, outs = [Inputs(), Inputs()], [Outputs(), Outputs()]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def h2d(S, stream):
+    def h2d(I, stream):
         with torch.cuda.stream(stream):
-            S.dB.copy_(hB, non_blocking=True)
-            S.dB32.copy_(hB32, non_blocking=True)
-            S.dG.copy_(hG, non_blocking=True)
+            I.dB.copy_(hB, non_blocking=True)
+            I.dB32.copy_(hB32, non_blocking=True)
+            I.dG.copy_(hG, non_blocking=True)
 
-    def compute(S, stream):
-        bs.solve(f, S.dB, stream=stream)
-        bs.solve_refine(f, S.dB32, S.dXR, stream=stream)
-        bs.solve_adjoint(f, S.dG, X=S.dB, dbands=S.db, stream=stream)
-
-    def d2h(S, stream):
+    def compute(I, O, stream):
         with torch.cuda.stream(stream):
-            S.oX.copy_(S.dB, non_blocking=True)
-            S.oXR.copy_(S.dXR, non_blocking=True)
-            S.oG.copy_(S.dG, non_blocking=True)
-            S.odb.copy_(S.db, non_blocking=True)
+            O.dX.copy_(I.dB)
+            O.dGB.copy_(I.dG)
+        bs.solve_refine(f, I.dB32, O.dXR, stream=stream)
+        I.used.record(stream)
+        bs.solve(f, O.dX, stream=stream)
+        bs.solve_adjoint(f, O.dGB, X=O.dX, dbands=O.db, stream=stream)
+
+    def d2h(O, stream):
+        with torch.cuda.stream(stream):
+            O.oX.copy_(O.dX, non_blocking=True)
+            O.oXR.copy_(O.dXR, non_blocking=True)
+            O.oG.copy_(O.dGB, non_blocking=True)
+            O.odb.copy_(O.db, non_blocking=True)
 
     def serial_step():
-        S = sets[0]
-        h2d(S, st)
-        compute(S, st)
-        d2h(S, st)
+        h2d(ins[0], st)
+        compute(ins[0], outs[0], st)
+        d2h(outs[0], st)
 
     def pipelined(n):
         for k in range(n):
-            S = sets[k % 2]
-            s_in.wait_event(S.d2h)   # step k-2 has read this set back
-            h2d(S, s_in)
-            S.h2d.record(s_in)
-            st.wait_event(S.h2d)
-            compute(S, st)
-            S.comp.record(st)
-            s_out.wait_event(S.comp)
-            d2h(S, s_out)
-            S.d2h.record(s_out)
+            I, O = ins[k % 2], outs[k % 2]
+            s_in.wait_event(I.used)    # step k-2 has read this input set
+            h2d(I, s_in)
+            I.h2d.record(s_in)
+            st.wait_event(I.h2d)
+            st.wait_event(O.d2h)       # step k-2's results have left this output set
+            compute(I, O, st)
+            O.comp.record(st)
+            s_out.wait_event(O.comp)
+            d2h(O, s_out)
+            O.d2h.record(s_out)
 
     serial_step()
     pipelined(2)
@@ -823,7 +836,8 @@ def run_e2e(bs, f, N, M, st, args, world):
     d2h_b = N * M * (8 + 8 + 8) + 5 * N * 8
     return {"value": 3 * N * M * world / (ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": h2d_b,
             "d2h_bytes_per_step": d2h_b, "ms_per_step": ms, "steps": steps,
-            "pipelining": "two buffer sets; copies in, compute and copies out on three streams",
+            "pipelining": "two input and two output buffer sets; copies in, compute and copies out on three "
+                          "streams",
             "serial_ms_per_step": ms_serial,
             "h2d_gbs": h2d_b / (ms * 1e-3) / 1e9, "d2h_gbs": d2h_b / (ms * 1e-3) / 1e9}
 
