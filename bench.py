@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 669723136 + 90624, "sha": "1b07e7a5e77a241f"},
-    "f64_solve": {"bytes": 472629760 + 431598336, "sha": "d0e98d4b994c940f"},
-    "adjoint_f64": {"bytes": 471430144 + 429337856, "sha": "d0e98d4b994c940f"},
-    "refine_solve": {"bytes": 355862016 + 436320512, "sha": "0187d1373f265810"},
+    "band_grad_f64": {"bytes": 669530368 + 146688, "sha": "1a2951d51f28157b"},
+    "f64_solve": {"bytes": 472502784 + 431980800, "sha": "d6ca4e038623dc4b"},
+    "adjoint_f64": {"bytes": 471336192 + 429259776, "sha": "d6ca4e038623dc4b"},
+    "refine_solve": {"bytes": 355809536 + 436237824, "sha": "a35db471ba624c39"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
