@@ -407,7 +407,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=400, load=0.7, budget=24 << 30, seed=0):
+def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=10000, load=0.7, budget=24 << 30, seed=0):
     """Serving workload: 256 resident LHS (tri/penta 50/50, N log-uniform in
     [64, 4096], diagonally dominant), requests with M log-uniform in
     [1, 65536], FP64 or FP32-stored + refinement 50/50, RHS ~ U(-1,1) in pinned
