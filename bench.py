@@ -407,21 +407,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=10000, load=0.7, budget=24 << 30, seed=0):
+def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=10000, load=0.7, sweep=(0.1, 0.3, 0.5, 0.9, 1.1),
+                n_sweep=1000, budget=24 << 30, seed=0):
     """Serving workload: 256 resident LHS (tri/penta 50/50, N log-uniform in
     [64, 4096], diagonally dominant), requests with M log-uniform in
     [1, 65536], FP64 or FP32-stored + refinement 50/50, RHS ~ U(-1,1) in pinned
     host memory, results copied back to host memory.  First a closed burst
     (all requests queued at once) gives the saturation rate, then a Poisson
     stream at `load` times that rate gives p50/p99 latency (submission to
-    host-observed completion) at sustained load."""
+    host-observed completion) at sustained load over `n_poisson` requests;
+    shorter streams at the `sweep` loads give the latency-throughput curve."""
     import torch
     import synth
     from paper_1909_04539_gb300 import serve as sv
 
     specs = [synth.serving_lhs(i) for i in range(n_lhs)]
     facs = [bs.Factor(sp.bands) for sp in specs]
-    reqs = synth.serving_requests(n_burst + n_poisson, rate_hz=1.0, n_lhs=n_lhs, seed=seed)
+    n_total = n_burst + n_poisson + n_sweep * len(sweep)
+    reqs = synth.serving_requests(n_total, rate_hz=1.0, n_lhs=n_lhs, seed=seed)
     max_nm = max(specs[r.lhs_id].N * r.M for r in reqs)
     g = torch.Generator().manual_seed(seed)
     pool = (torch.rand(max_nm + 4096, dtype=torch.float64, generator=g) * 2 - 1).pin_memory()
@@ -456,40 +459,54 @@ def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=10000, load=0.7, budget=24
     sat_rps = n_burst / t_burst
     for i in ids:
         srv.release(i)
+
+    def poisson(stream, ld, gap_seed):
+        """Poisson arrivals at ld * saturation; latency percentiles."""
+        rate = ld * sat_rps
+        gaps = np.random.default_rng(gap_seed).exponential(1.0 / rate, len(stream))
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for r, gap in zip(stream, gaps):
+            t_next += gap
+            while True:
+                d = t_next - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.0005))
+            B, X = views(r)
+            ids.append(srv.submit(facs[r.lhs_id], B, X, sv.F32_REFINE if r.refine else sv.F64))
+        lat = []
+        for i in ids:
+            srv.wait(i, 600)
+            lat.append(srv.poll(i)[1])
+        t_stream = time.perf_counter() - t0
+        for i in ids:
+            srv.release(i)
+        lat_ms = np.array(lat) * 1e3
+        unk = sum(specs[r.lhs_id].N * r.M for r in stream)
+        return {"offered_requests_per_s": rate, "load_of_saturation": ld, "requests": len(stream),
+                "achieved_requests_per_s": len(stream) / t_stream, "unknowns_per_s": unk / t_stream,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean())}
+
     # sustained: Poisson at load * saturation
-    rate = load * sat_rps
-    stream = reqs[n_burst:]
-    gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, len(stream))
-    ids = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for r, gap in zip(stream, gaps):
-        t_next += gap
-        while True:
-            d = t_next - time.perf_counter()
-            if d <= 0:
-                break
-            time.sleep(min(d, 0.0005))
-        B, X = views(r)
-        ids.append(srv.submit(facs[r.lhs_id], B, X, sv.F32_REFINE if r.refine else sv.F64))
-    lat = []
-    for i in ids:
-        srv.wait(i, 600)
-        lat.append(srv.poll(i)[1])
-    t_stream = time.perf_counter() - t0
+    pos = n_burst
+    sustained = poisson(reqs[pos:pos + n_poisson], load, seed + 2)
+    pos += n_poisson
+    curve = []
+    for q, ld in enumerate(sweep):
+        curve.append(poisson(reqs[pos:pos + n_sweep], ld, seed + 3 + q))
+        pos += n_sweep
     st = srv.stats()
     srv.close()
-    lat_ms = np.array(lat) * 1e3
-    unk_stream = sum(specs[r.lhs_id].N * r.M for r in stream)
     return {
         "workload": "256 resident LHS (tri/penta, N log-uniform [64,4096]); M log-uniform [1,65536]; "
                     "FP64 or FP32+refine 50/50; host (pinned) RHS in, host results out; Poisson arrivals",
         "saturation": {"requests_per_s": sat_rps, "unknowns_per_s": unk_burst / t_burst,
                        "host_device_gbs": bytes_burst / t_burst / 1e9, "requests": n_burst},
-        "sustained": {"offered_requests_per_s": rate, "load_of_saturation": load, "requests": len(stream),
-                      "achieved_requests_per_s": len(stream) / t_stream, "unknowns_per_s": unk_stream / t_stream,
-                      "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                      "mean_ms": float(lat_ms.mean())},
+        "sustained": sustained,
+        "load_sweep": curve,
         "server": {"hbm_budget_bytes": budget, "streams": 4, "batches": st["batches"],
                    "max_batch_requests": st["max_batch_requests"],
                    "max_concurrent_batches": st["max_concurrent_batches"]},
