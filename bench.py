@@ -924,9 +924,20 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
         _oracle_step(oracle, bands, Bs, G)
     dt = (time.perf_counter() - t) / reps
     m0 = m
-    cb = {"value": 3 * N * m0 / dt, "unit": "unknowns/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores_used = oracle.num_threads()
+    # the same step on one core, on a block sized for about 3 s
+    oracle.set_threads(1)
+    m1 = int(min(m0, max(256, m0 * 3.0 / max(dt * cores_used, 1e-6))))
+    B1, G1 = np.ascontiguousarray(Bs[:, :m1]), np.ascontiguousarray(G[:, :m1])
+    t = time.perf_counter()
+    _oracle_step(oracle, bands, B1, G1)
+    dt1 = time.perf_counter() - t
+    oracle.set_threads(cores)
+    cb = {"value": 3 * N * m0 / dt, "unit": "unknowns/s", "cores": cores_used, "kind": "oracle",
           "sample": f"{reps} repetitions of one step (FP64 solve, FP64 solve, adjoint + band gradient) on "
-                    f"the first {m0} of the {M_SYS} systems, {dt * reps:.1f} s in total"}
+                    f"the first {m0} of the {M_SYS} systems, {dt * reps:.1f} s in total",
+          "value_1_core": 3 * N * m1 / dt1,
+          "sample_1_core": f"one step on the first {m1} systems, one thread, {dt1:.1f} s"}
     return cb, errs
 
 
