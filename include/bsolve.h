@@ -329,9 +329,12 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    bs_solve_bf16 and bs_solve_adjoint (BS_F32) then read eps as a scalar
  *    instead of a coefficient array (one array fewer staged and read per
  *    row; the same number of operations, in a different order, so results
- *    differ from the general sweeps by rounding only).  FP64 solves keep the
- *    general sweeps, which are faster there.  0 (default): used for uniform
- *    handles; 1: never.
+ *    differ from the general sweeps by rounding only).  On GB300 the general
+ *    FP32 sweeps read each row's coefficients as one packed record, so the
+ *    scalar saves no load and its longer dependency chain makes it equal or
+ *    slower (FP64 solves, bound by the FP64 pipe, are 3 % slower with it);
+ *    it is therefore used only on request.  0 (default) and 1: the general
+ *    sweeps; 2: the scalar form for uniform handles (FP32 arithmetic).
  *  BS_OPT_TWISTED: two-ended solves for small batches (not in the paper).
  *    bs_factor also prepares, for a matrix (and for its transpose) whose
  *    row-reversed elimination (A = U' L') meets no bad pivot, the meeting

@@ -307,6 +307,77 @@ __device__ __forceinline__ void bwd_block(const Coefs<C>& cf, int top, int n, C 
   }
 }
 
+// FP32 sweeps whose coefficients are staged in shared memory keep each row's
+// forward (s, l1, l2) and backward (t, u1, u2) coefficients in one 16-byte
+// record each: one 128-bit shared load per row and sweep instead of one load
+// per coefficient array (the FP32 sweeps are bound by instruction issue).
+// The arithmetic is that of fwd_block / bwd_block.
+template <int BW, bool ADJ, bool UNI>
+__device__ __forceinline__ void stage_records(const Coefs<float>& cf, int N, float4* fr, float4* br) {
+  constexpr bool kUniF = UNI && !ADJ && BW == 2, kUniB = UNI && ADJ && BW == 2;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    fr[i] = make_float4(ADJ ? 1.f : cf.s[i], cf.l1[i], (BW == 2 && !kUniF) ? cf.l2[i] : 0.f, 0.f);
+    br[i] = make_float4(ADJ ? cf.t[i] : 1.f, cf.u1[i], (BW == 2 && !kUniB) ? cf.u2[i] : 0.f, 0.f);
+  }
+  __syncthreads();
+}
+
+template <int BW, bool ADJ, int V, int U, bool UNI>
+__device__ __forceinline__ void fwd_block_rec(const float4* fr, float eps, int i0, int n, float (&f)[U][V],
+                                              float (&w1)[V], float (&w2)[V]) {
+  constexpr bool kUni = UNI && !ADJ && BW == 2;
+  float4 r[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) r[u] = fr[(u < n) ? i0 + u : i0];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        float w;
+        if (kUni) {
+          w = fmaf(-eps, w2[v], f[u][v]) * r[u].x;
+        } else {
+          w = ADJ ? f[u][v] : f[u][v] * r[u].x;
+          if (BW == 2) w = fmaf(-r[u].z, w2[v], w);
+        }
+        w = fmaf(-r[u].y, w1[v], w);
+        if (BW == 2) w2[v] = w1[v];
+        w1[v] = w;
+        f[u][v] = w;
+      }
+    }
+  }
+}
+
+template <int BW, bool ADJ, int V, int U, bool UNI>
+__device__ __forceinline__ void bwd_block_rec(const float4* br, float eps, int top, int n, float (&f)[U][V],
+                                              float (&x1)[V], float (&x2)[V]) {
+  constexpr bool kUni = UNI && ADJ && BW == 2;
+  float4 r[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) r[u] = br[(u < n) ? top - u : top];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        float x;
+        if (kUni) {
+          x = fmaf(-eps, x2[v], f[u][v]) * r[u].x;
+        } else {
+          x = ADJ ? f[u][v] * r[u].x : f[u][v];
+          if (BW == 2) x = fmaf(-r[u].z, x2[v], x);
+        }
+        x = fmaf(-r[u].y, x1[v], x);
+        if (BW == 2) x2[v] = x1[v];
+        x1[v] = x;
+        f[u][v] = x;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------ async row copies
 
 // Per-lane rings of rows in shared memory, filled with cp.async.  Each lane
@@ -452,8 +523,19 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
     in += (int64_t)r0 * M;
     out += (int64_t)r0 * M;
   }
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM, C, PER, UNI>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER, UNI>() * N * sizeof(C), 16) : 0;
+  // FP32 with staged coefficients: per-row records (stage_records)
+  constexpr bool REC = SMEM && std::is_same<C, float>::value && !PER;
+  const float4* fr = reinterpret_cast<const float4*>(smem_raw);
+  const float4* br = fr + N;
+  Coefs<C> cf = cf_g;
+  size_t coef_bytes;
+  if constexpr (REC) {
+    stage_records<BW, ADJ, UNI>(cf_g, N, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + N);
+    coef_bytes = (size_t)N * 2 * sizeof(float4);
+  } else {
+    cf = stage_coefs<BW, ADJ, SMEM, C, PER, UNI>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+    coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW, PER, UNI>() * N * sizeof(C), 16) : 0;
+  }
   unsigned char* ring = smem_raw + coef_bytes + (size_t)threadIdx.x * 16;
   const uint32_t ring_s = smem_u32(ring);
   const uint32_t pitch = blockDim.x * 16;
@@ -486,7 +568,10 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
         if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
       if constexpr (PER)
         if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
-      fwd_block<BW, ADJ, C, V, U, UNI>(cf, i0, n, f, r1, r2);
+      if constexpr (REC)
+        fwd_block_rec<BW, ADJ, V, U, UNI>(fr, cf.eps, i0, n, f, r1, r2);
+      else
+        fwd_block<BW, ADJ, C, V, U, UNI>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int i = i0 + u;
@@ -518,7 +603,10 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
-      bwd_block<BW, ADJ, C, V, U, UNI>(cf, top, n, f, r1, r2);
+      if constexpr (REC)
+        bwd_block_rec<BW, ADJ, V, U, UNI>(br, cf.eps, top, n, f, r1, r2);
+      else
+        bwd_block<BW, ADJ, C, V, U, UNI>(cf, top, n, f, r1, r2);
       if constexpr (PER)
         if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, f, sig);
 #pragma unroll
@@ -659,9 +747,11 @@ cudaError_t launch_il(Coefs<C> cf, int N, const Sin* in, Sout* out, int64_t M, i
     // pipelined kernel: ring of D 16-byte slots per lane; the FP32 sweeps are
     // bound by memory latency, so they keep twice the rows in flight -- but a
     // partitioned launch has the threads, and shallow rings let more CTAs fit
+    // FP32 without the periodic terms stages 8 values per row (two records)
+    constexpr int kExtra2 = (sizeof(C) == 4 && !PER) ? 8 - coef_arrays<BW>() : kExtra;
     auto go = [&](auto dtag) -> cudaError_t {
       constexpr int D = decltype(dtag)::value;
-      const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, kExtra);
+      const LaunchShape sh = sweep_shape(BW, L, groups * P, sizeof(C), sizeof(Sout), V, D * 16, 0, 0, kExtra2);
       const size_t bytes = sh.smem + (size_t)sh.threads * D * 16;
       const dim3 grid((sh.grid + P - 1) / P, P);
       auto k = sh.smem_coefs ? k_sweep_il2<BW, ADJ, true, C, Sin, Sout, V, D, PER, UNI>
@@ -745,11 +835,12 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
     if (!adjoint) { BS_DISPATCH(1, false, true, false) } else { BS_DISPATCH(1, true, true, false) }
   } else if (p.bw == 1) {
     if (!adjoint) { BS_DISPATCH(1, false, false, false) } else { BS_DISPATCH(1, true, false, false) }
-  } else if (sizeof(C) == 4 && p.uniform && option(BS_OPT_UNIFORM) != 1) {
-    // FP32 arithmetic only: measured at N = 512, M = 65536 the scalar form is
-    // 2 % (FP32) and 6 % (BF16 storage) faster, but 3 % slower in FP64, whose
-    // sweeps are bound by the FP64 pipe: the w_{i-2} link of its recurrence
-    // takes three dependent operations per two rows instead of two
+  } else if (sizeof(C) == 4 && p.uniform && option(BS_OPT_UNIFORM) == 2) {
+    // on request only, FP32 arithmetic only: with the per-row coefficient
+    // records the scalar saves no load and its w_{i-2} link takes three
+    // dependent operations per two rows instead of two (measured equal or
+    // slower except BF16 storage at N >= 8192, 3 % faster); in FP64, bound
+    // by the FP64 pipe, 3 % slower
     if constexpr (sizeof(C) == 4) {
       if (!adjoint) { BS_DISPATCH(2, false, false, true) } else { BS_DISPATCH(2, true, false, true) }
     }

@@ -1,8 +1,8 @@
 """GPU parity of uniform pentadiagonal matrices (Sec. 4.1,
 cuPentUniformBatch: the outermost sub-diagonal a_i = eps for every in-range
-row) against the CPU FP64 oracle, through the C ABI.  The FP32-arithmetic
-sweeps read eps as one scalar; FP64 solves keep the general sweeps (bitwise
-equal with the option on and off).  Tolerances as for the general sweeps:
+row) against the CPU FP64 oracle, through the C ABI.  With BS_OPT_UNIFORM = 2
+the FP32-arithmetic sweeps read eps as one scalar; FP64 solves keep the
+general sweeps (bitwise equal with the option on and off).  Tolerances as for the general sweeps:
 FP64 1e-12 relative L2, FP32 and BF16-stored 2e-5; the scalar and general
 FP32 sweeps differ in operation order only (agree to 1e-6).  A matrix with
 one differing a_i takes the general sweeps in every precision."""
@@ -39,7 +39,7 @@ def _bands(kind, N, rng):
 
 def _solve(bs, f, Bh, dtype, layout, uniform_opt):
     """The one-thread sweeps (no partition, no two-ended sweep), with the
-    scalar-eps form allowed (0) or not (1)."""
+    scalar-eps form requested (2) or not (1)."""
     bs.set_option(bs.OPT_UNIFORM, uniform_opt)
     bs.set_option(bs.OPT_PARTITION, 1)
     bs.set_option(bs.OPT_TWISTED, 1)
@@ -66,7 +66,7 @@ def test_uniform_fp64(bs, N, M, kind, layout):
     B = rng.uniform(-1, 1, (N, M))
     Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
     f = bs.Factor(bands)
-    Xu = _solve(bs, f, Bh, torch.float64, layout, 0)
+    Xu = _solve(bs, f, Bh, torch.float64, layout, 2)
     Xg = _solve(bs, f, Bh, torch.float64, layout, 1)
     assert rel_l2(Xu, oracle.solve(bands, Bh, layout)) < TOL64
     assert np.array_equal(Xu, Xg)  # FP64: the general sweeps either way
@@ -80,7 +80,7 @@ def test_uniform_fp32(bs, N, M, layout):
     B = rng.uniform(-1, 1, (N, M)).astype(np.float32).astype(np.float64)
     Bh = B if layout == "interleaved" else np.ascontiguousarray(B.T)
     f = bs.Factor(bands)
-    X = _solve(bs, f, Bh, torch.float32, layout, 0)
+    X = _solve(bs, f, Bh, torch.float32, layout, 2)
     Xg = _solve(bs, f, Bh, torch.float32, layout, 1)
     assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL32
     assert rel_l2(X, Xg) < 1e-6
@@ -96,11 +96,13 @@ def test_uniform_bf16(bs):
     B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.bfloat16, device="cuda")
     bs.set_option(bs.OPT_PARTITION, 1)
     bs.set_option(bs.OPT_TWISTED, 1)
+    bs.set_option(bs.OPT_UNIFORM, 2)
     try:
         X = bs.solve_bf16(f, B)
     finally:
         bs.set_option(bs.OPT_PARTITION, 0)
         bs.set_option(bs.OPT_TWISTED, 0)
+        bs.set_option(bs.OPT_UNIFORM, 0)
     ref = oracle.solve(bands, B.double().cpu().numpy())
     assert rel_l2(X.double().cpu().numpy(), ref) < TOL32
 
@@ -120,6 +122,7 @@ def test_uniform_adjoint_and_band_grad(bs, layout, dtype, tol):
     f = bs.Factor(bands)
     bs.set_option(bs.OPT_PARTITION, 1)
     bs.set_option(bs.OPT_TWISTED, 1)
+    bs.set_option(bs.OPT_UNIFORM, 2)
     try:
         X = torch.tensor(tr(B), dtype=dtype, device="cuda")
         bs.solve(f, X, layout)
@@ -129,6 +132,7 @@ def test_uniform_adjoint_and_band_grad(bs, layout, dtype, tol):
     finally:
         bs.set_option(bs.OPT_PARTITION, 0)
         bs.set_option(bs.OPT_TWISTED, 0)
+        bs.set_option(bs.OPT_UNIFORM, 0)
     GB_ref = oracle.solve_adjoint(bands, tr(Gm), layout)
     assert rel_l2(G.double().cpu().numpy(), GB_ref) < tol
     db_ref = oracle.band_grad(5, G.double().cpu().numpy(), X.double().cpu().numpy(), layout)
@@ -137,8 +141,8 @@ def test_uniform_adjoint_and_band_grad(bs, layout, dtype, tol):
 
 
 def test_non_uniform_takes_general_sweeps(bs):
-    """One differing a_i: the handle is not uniform, so the option changes
-    nothing."""
+    """One differing a_i: the handle is not uniform, so requesting the scalar
+    form changes nothing."""
     N, M = 256, 1024
     rng = np.random.default_rng(3)
     bands = synth.uniform_penta_bands(N, rng)
@@ -146,7 +150,7 @@ def test_non_uniform_takes_general_sweeps(bs):
     bands[2, 100] += 0.125
     Bh = rng.uniform(-1, 1, (N, M))
     f = bs.Factor(bands)
-    X0 = _solve(bs, f, Bh, torch.float32, "interleaved", 0)
+    X0 = _solve(bs, f, Bh, torch.float32, "interleaved", 2)
     X1 = _solve(bs, f, Bh, torch.float32, "interleaved", 1)
     assert np.array_equal(X0, X1)
     assert rel_l2(X0, oracle.solve(bands, Bh)) < TOL32
