@@ -11,7 +11,9 @@
 // Per thread: V neighbouring systems, rows moved in blocks of U with a
 // two-block register pipeline (as the plain V = 1 kernel).  The explicit
 // bands e = 2I - A are formed once per CTA in shared memory (or read from
-// the handle's bands in global memory for large N).  For a periodic handle
+// the handle's bands in global memory for large N); in FP32 the sweep
+// coefficients and the explicit bands are staged as per-row 16-byte records
+// (one 128-bit load per row and use, as in the FP32 sweeps).  For a periodic handle
 // the explicit side wraps around (rows 0 and N-1 are kept from the start of
 // the step, before they are overwritten) and the Sherman-Morrison correction
 // of the solve is applied as in the plain periodic sweeps.
@@ -30,20 +32,39 @@ k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
   static_assert(U >= BW, "a block must cover the look-ahead rows");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  const Coefs<C> cf = stage_coefs<BW, false, SMEM, C, PER>(cf_g, N, sm);
+  // FP32 with staged coefficients: records fr (forward), br (backward) and
+  // er (explicit bands, one or two per row); pw, pc stay in global memory
+  constexpr bool REC = SMEM && std::is_same<C, float>::value;
+  constexpr int ER = BW == 1 ? 1 : 2;
+  const float4* fr = reinterpret_cast<const float4*>(smem_raw);
+  const float4* br = fr + N;
+  const float4* er = br + N;
+  Coefs<C> cf = cf_g;
   // explicit bands e_k(i) = [k == BW] * 2 - band_k(i)
-  const C* eb;
-  C* esm = sm + (SMEM ? coef_arrays<BW, PER>() * N : 0);
-  if (SMEM) {
-    for (int t = threadIdx.x; t < W * N; t += blockDim.x) esm[t] = ((t / N) == BW ? C(2) : C(0)) - bands[t];
+  const C* eb = bands;
+  if constexpr (REC) {
+    float4* w4 = reinterpret_cast<float4*>(smem_raw);
+    stage_records<BW, false, false>(cf_g, N, w4, w4 + N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < W; k++) e[k] = (k == BW ? 2.f : 0.f) - (float)bands[(size_t)k * N + i];
+      w4[2 * N + (size_t)i * ER] = make_float4(e[0], e[1], e[2], e[3]);
+      if (ER == 2) w4[2 * N + (size_t)i * ER + 1] = make_float4(e[4], e[5], e[6], e[7]);
+    }
     __syncthreads();
-    eb = esm;
   } else {
-    eb = bands;  // e computed on the fly below
+    cf = stage_coefs<BW, false, SMEM, C, PER>(cf_g, N, sm);
+    C* esm = sm + (SMEM ? coef_arrays<BW, PER>() * N : 0);
+    if (SMEM) {
+      for (int t = threadIdx.x; t < W * N; t += blockDim.x) esm[t] = ((t / N) == BW ? C(2) : C(0)) - bands[t];
+      __syncthreads();
+      eb = esm;
+    }
   }
   auto e_at = [&](int k, int i) -> C {
     if (SMEM) return eb[k * N + i];
-    return (k == BW ? C(2) : C(0)) - eb[k * N + i];
+    return (k == BW ? C(2) : C(0)) - eb[k * N + i];  // e computed on the fly
   };
   const int64_t ngroups = M / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -112,8 +133,16 @@ k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
         if (u < n) {
           const int i = i0 + u;
           C e[W];
+          if constexpr (REC) {
+            const float4 a = er[(size_t)i * ER];
+            const float ev[8] = {a.x, a.y, a.z, a.w, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int k = 0; k < W; k++) e[k] = e_at(k, i);
+            for (int k = 0; k < W && k < 4; k++) e[k] = ev[k];
+            if constexpr (ER == 2) e[4] = er[(size_t)i * ER + 1].x;
+          } else {
+#pragma unroll
+            for (int k = 0; k < W; k++) e[k] = e_at(k, i);
+          }
 #pragma unroll
           for (int v = 0; v < V; v++) {
             C sacc = e[0] * win[u][v];
@@ -132,7 +161,10 @@ k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
       }
       if constexpr (PER)
         if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
-      fwd_block<BW, false, C, V, U>(cf, i0, n, f, r1, r2);
+      if constexpr (REC)
+        fwd_block_rec<BW, false, V, U, false>(fr, 0.f, i0, n, f, r1, r2);
+      else
+        fwd_block<BW, false, C, V, U>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++)
         if (u < n) IO<C, C, V>::store(px + (int64_t)(i0 + u) * M, f[u]);
@@ -152,7 +184,10 @@ k_cn_il(Coefs<C> cf_g, const C* __restrict__ bands, int N, C* X, int64_t M) {
     };
     auto run_bwd = [&](C (&blk)[U][V], int top) {
       const int n = (top + 1) < U ? (top + 1) : U;
-      bwd_block<BW, false, C, V, U>(cf, top, n, blk, r1, r2);
+      if constexpr (REC)
+        bwd_block_rec<BW, false, V, U, false>(br, 0.f, top, n, blk, r1, r2);
+      else
+        bwd_block<BW, false, C, V, U>(cf, top, n, blk, r1, r2);
       if constexpr (PER)
         if (top + 1 - n < cf.per_lo || top + 1 > cf.per_hi) per_fix<C, V, U>(cf, top, n, blk, sig);
 #pragma unroll
@@ -186,7 +221,9 @@ static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, in
   // 256-thread CTAs when the batch fills the device: the staged coefficient
   // and explicit-band arrays are shared by twice the threads
   const int tpb = groups >= (int64_t)device_info().sms * kCnThreads ? kCnThreads : 0;
-  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(C), V, 0, 0, tpb, (PER ? 2 : 0) + 2 * BW + 1);
+  // FP32: records of 16 bytes, 2 + (1 or 2) per row
+  constexpr int kExtra = sizeof(C) == 4 ? 4 * (2 + (BW == 1 ? 1 : 2)) - (1 + 2 * BW) : (PER ? 2 : 0) + 2 * BW + 1;
+  const LaunchShape sh = sweep_shape(BW, N, groups, sizeof(C), sizeof(C), V, 0, 0, tpb, kExtra);
   if (sh.smem_coefs) {
     auto k = k_cn_il<BW, PER, true, C, V, U>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
