@@ -48,8 +48,20 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     u += (int64_t)r0 * M;
     out += (int64_t)r0 * M;
   }
-  const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-  const size_t coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+  // FP32 with staged coefficients: one 16-byte record per row and sweep
+  // (stage_records)
+  constexpr bool REC = SMEM && std::is_same<C, float>::value;
+  const float4* fr = reinterpret_cast<const float4*>(smem_raw);
+  const float4* br = fr + N;
+  Coefs<C> cf = cf_g;
+  size_t coef_bytes;
+  if constexpr (REC) {
+    stage_records<BW, ADJ, false>(cf_g, N, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + N);
+    coef_bytes = (size_t)N * 2 * sizeof(float4);
+  } else {
+    cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
+    coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+  }
   const int lane = threadIdx.x & 31;
   // slot layout per lane: [own value | outer neighbour], 2 * sizeof(C) bytes
   constexpr int kSlot = 2 * sizeof(C);
@@ -108,7 +120,10 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         cp_commit();
       }
       if (valid) {
-        fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, f, r1, r2);
+        if constexpr (REC)
+          fwd_block_rec<BW, ADJ, 1, U, false>(fr, 0.f, i0, n, f, r1, r2);
+        else
+          fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, f, r1, r2);
 #pragma unroll
         for (int q = 0; q < U; q++)
           if (q < n) po[(int64_t)(i0 + q) * M] = f[q][0];
@@ -139,7 +154,10 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         cp_commit();
       }
       if (valid) {
-        bwd_block<BW, ADJ, C, 1, U>(cf, top, n, f, r1, r2);
+        if constexpr (REC)
+          bwd_block_rec<BW, ADJ, 1, U, false>(br, 0.f, top, n, f, r1, r2);
+        else
+          bwd_block<BW, ADJ, C, 1, U>(cf, top, n, f, r1, r2);
 #pragma unroll
         for (int q = 0; q < U; q++)
           if (q < n) po[(int64_t)(top - q) * M] = f[q][0];
@@ -305,12 +323,17 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   // warp per SM and the depth must come from each lane (64 rows, 8 chunks);
   // a partitioned launch has P times the threads, and shallow rings leave
   // room for more resident CTAs.
+  // FP32 along y stages two 16-byte records per row (8 values) instead of
+  // 1 + 2 BW arrays (k_adi_il2; 0.115 -> 0.108 ms per 4096^2 half-step).  The
+  // one-warp CTAs along x keep the arrays: records there cost resident CTAs
+  // (0.113 -> 0.121 ms).
+  constexpr int kRecExtra = sizeof(C) == 4 ? 8 - coef_arrays<BW>() : 0;
   if (axis == 1) {
     auto go = [&](auto dtag) -> cudaError_t {
       constexpr int D = decltype(dtag)::value;
       const int64_t threads = ((M + 31) / 32) * 32;
       const LaunchShape sh =
-          sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0);
+          sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0, kRecExtra);
       const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
       auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
