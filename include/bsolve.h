@@ -135,15 +135,22 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
  *     r = B - A X0, of the FP32 solution X0 drives one correction solve
  *     through the reversed elimination A = U' L' (factorised once with the
  *     handle) so that its first sweep follows the backward sweep of X0.
- * Both reach ~1e-15 relative error on well-conditioned bands.
- * refine_steps = 0 returns the FP32 solution widened to FP64 (mode ignored).
+ *   mode BS_REFINE_AUTO: BS_REFINE_FACTOR, except for batches with fewer
+ *     than 256 systems per SM, whose FP32 passes are bound by their chains
+ *     of dependent rows: those are
+ *     solved as an FP64 solve of B widened exactly to FP64 in X (as bs_solve
+ *     does it, row-partitioned or two-ended), which is faster there and
+ *     exact to FP64 rounding (not in the paper).
+ * Both refinement modes reach ~1e-15 relative error on well-conditioned
+ * bands.  refine_steps = 0 returns the FP32 solution widened to FP64 (mode
+ * ignored).
  * X doubles as the workspace of the passes.  Only BS_INTERLEAVED and b_dtype
  * BS_F32 are implemented (BS_EUNSUPPORTED otherwise); refine_steps > 1 is
  * BS_EUNSUPPORTED.  B and X must not overlap.  BS_REFINE_SYSTEM returns
  * BS_ESINGULAR if the reversed elimination of A met a bad pivot when the
  * handle was built (the other solves still work then).
  * Not in the paper: the paper's solvers work in a single precision. */
-typedef enum { BS_REFINE_FACTOR = 0, BS_REFINE_SYSTEM = 1 } bs_refine_mode;
+typedef enum { BS_REFINE_FACTOR = 0, BS_REFINE_SYSTEM = 1, BS_REFINE_AUTO = 2 } bs_refine_mode;
 bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
                           int64_t M, int refine_steps, bs_refine_mode mode, bs_stream stream);
 

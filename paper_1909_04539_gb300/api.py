@@ -149,15 +149,17 @@ def solve_bf16(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, layout
 
 REFINE_FACTOR = 0
 REFINE_SYSTEM = 1
+REFINE_AUTO = 2
 
 
 def solve_refine(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, refine_steps: int = 1,
-                 layout: str = "interleaved", stream=None, mode: int = REFINE_FACTOR) -> torch.Tensor:
+                 layout: str = "interleaved", stream=None, mode: int = REFINE_AUTO) -> torch.Tensor:
     """FP32-stored B (float32), FP32 sweeps plus ``refine_steps`` (0 or 1)
     steps of iterative refinement with FP64-accurate residuals (``mode``:
     REFINE_FACTOR per triangular factor, two passes; REFINE_SYSTEM on
-    r = B - A X0, three passes); returns the FP64 solution X (also used as
-    workspace)."""
+    r = B - A X0, three passes; REFINE_AUTO as REFINE_FACTOR, but small
+    batches solved in FP64 from the widened input); returns the FP64
+    solution X (also used as workspace)."""
     M = _batch(f, B, layout, "B")
     if B.dtype != torch.float32:
         raise ValueError("B must be float32")

@@ -456,9 +456,37 @@ static cudaError_t launch_refine_bw(bs_handle h, const float* B, double* X, int6
   return cudaGetLastError();
 }
 
+// X = B widened exactly to FP64 (integer operations, no FP64 pipe).
+__global__ void __launch_bounds__(256) k_widen(const float* __restrict__ B, double* __restrict__ X, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = widen_exact(B[i]);
+}
+
+// BS_REFINE_AUTO: below 256 systems per SM the one-thread FP32 passes are
+// bound by their chains of dependent rows, and an FP64 solve of the widened
+// input -- row-partitioned or two-ended as bs_solve picks -- is faster and
+// exact to FP64 rounding.  Measured (refine / widen + FP64 solve): N = 512
+// penta M = 1024: 127 / 77 us, M = 16384: 134 / 120 us, M = 65536: 252 /
+// 350 us; N = 1024 tri M = 1024: 226 / 66 us, M = 16384: 235 / 178 us,
+// M = 65536: 543 / 635 us (the widening pass then costs 0.16 ms).
+static bool refine_direct(int64_t M) { return M < (int64_t)device_info().sms * 256; }
+
 bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, int mode,
                         cudaStream_t st) {
   if (b_t != BS_F32) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: B must be BS_F32");
+  if (mode == BS_REFINE_AUTO) {
+    if (steps == 1 && refine_direct(M)) {
+      const int64_t n = h->N * M;
+      int64_t g = (n + 255) / 256;
+      const int64_t cap = (int64_t)device_info().sms * 8;
+      if (g > cap) g = cap;
+      k_widen<<<(int)g, 256, 0, st>>>(static_cast<const float*>(B), X, n);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_error(e, "bs_solve_refine launch");
+      return bs_solve(h, X, BS_F64, BS_INTERLEAVED, M, reinterpret_cast<bs_stream>(st));
+    }
+    mode = BS_REFINE_FACTOR;
+  }
   cudaError_t e;
   if (steps == 1 && mode == BS_REFINE_FACTOR)
     e = h->width == 3 ? launch_refine_factor_bw<1>(h, (const float*)B, X, M, st)
@@ -483,7 +511,7 @@ extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtyp
     return set_error(BS_EUNSUPPORTED, "bs_solve_refine: only the interleaved layout is implemented");
   if (refine_steps < 0 || refine_steps > 1)
     return set_error(BS_EUNSUPPORTED, "bs_solve_refine: refine_steps must be 0 or 1");
-  if (mode != BS_REFINE_FACTOR && mode != BS_REFINE_SYSTEM)
+  if (mode != BS_REFINE_FACTOR && mode != BS_REFINE_SYSTEM && mode != BS_REFINE_AUTO)
     return set_error(BS_EINVAL, "bs_solve_refine: bad refinement mode");
   if (refine_steps > 0 && mode == BS_REFINE_SYSTEM && !h->has_ul)
     return set_error(BS_ESINGULAR, "bs_solve_refine: the reversed elimination of this matrix met a bad pivot");

@@ -112,3 +112,35 @@ def test_refine_zero_tiny_and_huge_columns(bs, mode):
     ref = oracle.solve(bands, Bh.astype(np.float64))
     for j in (0, 7, 9):
         assert rel_l2(X[:, j], ref[:, j]) < 1e-12, j
+
+
+@pytest.mark.parametrize("width,N,M", [(3, 64, 1024), (5, 512, 1000), (3, 1024, 4096), (5, 37, 9)])
+def test_refine_auto_small_batch_is_fp64_solve(bs, width, N, M):
+    """REFINE_AUTO on a small batch: B widened exactly to FP64 and solved in
+    FP64 (bitwise the FP64 solve of the widened input), right against the
+    oracle to FP64 rounding."""
+    rng = np.random.default_rng(N + M)
+    bands = synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
+    f = bs.Factor(bands)
+    B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.float32, device="cuda")
+    X = bs.solve_refine(f, B, mode=bs.REFINE_AUTO)
+    X64 = B.double()
+    bs.solve(f, X64)
+    torch.cuda.synchronize()
+    assert torch.equal(X, X64)
+    ref = oracle.solve(bands, B.double().cpu().numpy())
+    assert rel_l2(X.cpu().numpy(), ref) < 1e-12
+
+
+def test_refine_auto_large_batch_is_factor_mode(bs):
+    """Above the small-batch threshold REFINE_AUTO is the factor-wise
+    refinement, bit for bit."""
+    N, M = 64, 65536
+    rng = np.random.default_rng(3)
+    bands = synth.random_tri_bands(N, rng)
+    f = bs.Factor(bands)
+    B = torch.tensor(rng.uniform(-1, 1, (N, M)), dtype=torch.float32, device="cuda")
+    Xa = bs.solve_refine(f, B, mode=bs.REFINE_AUTO)
+    Xf = bs.solve_refine(f, B, mode=bs.REFINE_FACTOR)
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xf)

@@ -73,7 +73,7 @@ def test_mix_equals_alone_and_direct(bs, serve):
             if mode == 0:
                 D = bs.solve(facs[k], B.cuda())
             else:
-                D = bs.solve_refine(facs[k], B.cuda())
+                D = bs.solve_refine(facs[k], B.cuda(), mode=bs.REFINE_FACTOR)
             torch.cuda.synchronize()
         finally:
             bs.set_option(bs.OPT_PARTITION, 0)
