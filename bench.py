@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 669821696 + 237824, "sha": "b1b8227fa2e9e117"},
-    "f64_solve": {"bytes": 472463872 + 431912960, "sha": "f7d9e63bfed6f25a"},
-    "adjoint_f64": {"bytes": 471305472 + 429300736, "sha": "f7d9e63bfed6f25a"},
-    "refine_solve": {"bytes": 355816960 + 436172032, "sha": "0151df7e2bb70002"},
+    "band_grad_f64": {"bytes": 669666816 + 152064, "sha": "b1b8227fa2e9e117"},
+    "f64_solve": {"bytes": 472359424 + 431979264, "sha": "f7d9e63bfed6f25a"},
+    "adjoint_f64": {"bytes": 471199744 + 429270528, "sha": "f7d9e63bfed6f25a"},
+    "refine_solve": {"bytes": 355822848 + 436277248, "sha": "6527b50c8c99cfd7"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
