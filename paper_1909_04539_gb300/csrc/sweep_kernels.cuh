@@ -548,18 +548,20 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = sig[v] = C(0);
     // forward sweep: rows 0..D-1 requested up front (one copy group per
-    // row), then each block of U rows is consumed and its slots refilled
+    // block of U rows), then each block is consumed and its slots refilled
+    // with one new group; the group a block waits for was committed D / U
+    // groups earlier
     const Sin* pnext = pin;  // next row to request
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
       if (r < N) copy_row<Sin, V>(ring_s + r * pitch, pnext);
       pnext += M;
-      cp_commit();
+      if ((r + 1) % U == 0) cp_commit();
     }
     Sout* prow = pout;  // output row i0
 #pragma unroll 1
     for (int i0 = 0; i0 < N; i0 += U) {
-      cp_wait<D - U>();
+      cp_wait<D / U - 1>();
       const int n = (N - i0) < U ? (N - i0) : U;
       const int s0 = i0 % D;
       C f[U][V];
@@ -585,11 +587,13 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
         }
         prow += M;
         pnext += M;
-        cp_commit();
       }
+      cp_commit();
     }
     // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
-    // into the slot row i frees
+    // into the slot row i frees (one group per block, as above; blocks are
+    // aligned to N - 1 and D is a multiple of U, so the rows a block needs
+    // were requested together, D / U blocks earlier)
 #pragma unroll
     for (int v = 0; v < V; v++) r1[v] = r2[v] = C(0);
     const int tail = N - D;
@@ -598,7 +602,7 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 #pragma unroll 1
     for (int top = N - 1; top >= 0; top -= U) {
       const int n = (top + 1) < U ? (top + 1) : U;
-      if (top - (n - 1) < tail) cp_wait<D - U>();
+      if (top - (n - 1) < tail) cp_wait<D / U - 1>();
       C f[U][V];
 #pragma unroll
       for (int u = 0; u < U; u++)
@@ -618,8 +622,8 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
         }
         prow -= M;
         pback -= M;
-        cp_commit();
       }
+      cp_commit();
     }
     cp_wait<0>();
   }
