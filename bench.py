@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 863664384 + 179712, "sha": "e65f66c977152dc9"},
-    "f64_solve": {"bytes": 472359424 + 431979264, "sha": "f7d9e63bfed6f25a"},
-    "adjoint_f64": {"bytes": 471199744 + 429270528, "sha": "f7d9e63bfed6f25a"},
-    "refine_solve": {"bytes": 355822848 + 436277248, "sha": "6527b50c8c99cfd7"},
+    "band_grad_f64": {"bytes": 863921152 + 165632, "sha": "8f193dc9c0c61583"},
+    "f64_solve": {"bytes": 472388864 + 431877888, "sha": "0c04615c0d2c1943"},
+    "adjoint_f64": {"bytes": 472751104 + 430187520, "sha": "0c04615c0d2c1943"},
+    "refine_solve": {"bytes": 355728384 + 436071936, "sha": "45524936f5f3b6d7"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
