@@ -559,15 +559,17 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
       if ((r + 1) % U == 0) cp_commit();
     }
     Sout* prow = pout;  // output row i0
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += U) {
+    // one block of U rows; FULL: all U rows exist and each refills its slot
+    // (no per-row guards), otherwise the guarded general case
+    auto fwd = [&](auto full_tag, int i0) {
+      constexpr bool FULL = decltype(full_tag)::value;
       cp_wait<D / U - 1>();
-      const int n = (N - i0) < U ? (N - i0) : U;
+      const int n = FULL ? U : ((N - i0) < U ? (N - i0) : U);
       const int s0 = i0 % D;
       C f[U][V];
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
+        if (FULL || u < n) IO<Sin, C, V>::load(reinterpret_cast<const Sin*>(ring + (size_t)(s0 + u) * pitch), f[u]);
       if constexpr (PER)
         if (i0 < cf.per_lo || i0 + n > cf.per_hi) per_dot<C, V, U>(cf, i0, n, f, sig);
       if constexpr (REC)
@@ -576,20 +578,30 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
         fwd_block<BW, ADJ, C, V, U, UNI>(cf, i0, n, f, r1, r2);
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const int i = i0 + u;
-        if (u < n) {
-          if (i + D < N) {
-            IO<Sout, C, V>::store(prow, f[u]);
-            copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pnext);
-          } else {
-            IO<Sout, C, V>::store(reinterpret_cast<Sout*>(ring + (size_t)(s0 + u) * pitch), f[u]);  // tail on chip
+        if constexpr (FULL) {
+          IO<Sout, C, V>::store(prow, f[u]);
+          copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pnext);
+        } else {
+          const int i = i0 + u;
+          if (u < n) {
+            if (i + D < N) {
+              IO<Sout, C, V>::store(prow, f[u]);
+              copy_row<Sin, V>(ring_s + (s0 + u) * pitch, pnext);
+            } else {
+              IO<Sout, C, V>::store(reinterpret_cast<Sout*>(ring + (size_t)(s0 + u) * pitch), f[u]);  // tail on chip
+            }
           }
         }
         prow += M;
         pnext += M;
       }
       cp_commit();
-    }
+    };
+    int i0 = 0;
+#pragma unroll 1
+    for (; i0 + U + D <= N; i0 += U) fwd(std::true_type{}, i0);
+#pragma unroll 1
+    for (; i0 < N; i0 += U) fwd(std::false_type{}, i0);
     // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
     // into the slot row i frees (one group per block, as above; blocks are
     // aligned to N - 1 and D is a multiple of U, so the rows a block needs
@@ -599,14 +611,18 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
     const int tail = N - D;
     prow = pout + (int64_t)(N - 1) * M;               // output row `top`
     const Sout* pback = pout + (int64_t)(N - 1 - D) * M;  // row top - D, requested next
-#pragma unroll 1
-    for (int top = N - 1; top >= 0; top -= U) {
-      const int n = (top + 1) < U ? (top + 1) : U;
-      if (top - (n - 1) < tail) cp_wait<D / U - 1>();
+    // FULL: all U rows exist and each requests row i - D.  Its wait is also
+    // taken on the first blocks, whose rows are on chip: fewer than D / U
+    // groups are pending then, so it does not block.
+    auto bwd = [&](auto full_tag, int top) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      const int n = FULL ? U : ((top + 1) < U ? (top + 1) : U);
+      if (FULL || top - (n - 1) < tail) cp_wait<D / U - 1>();
       C f[U][V];
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (u < n) IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
+        if (FULL || u < n)
+          IO<Sout, C, V>::load(reinterpret_cast<const Sout*>(ring + (size_t)((top - u) % D) * pitch), f[u]);
       if constexpr (REC)
         bwd_block_rec<BW, ADJ, V, U, UNI>(br, cf.eps, top, n, f, r1, r2);
       else
@@ -616,15 +632,25 @@ k_sweep_il2(Coefs<C> cf_g, int N, const Sin* in, Sout* out, int64_t M, int L) {
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int i = top - u;
-        if (u < n) {
+        if constexpr (FULL) {
           IO<Sout, C, V>::store(prow, f[u]);
-          if (i - D >= 0) copy_row<Sout, V>(ring_s + (i % D) * pitch, pback);
+          copy_row<Sout, V>(ring_s + (i % D) * pitch, pback);
+        } else {
+          if (u < n) {
+            IO<Sout, C, V>::store(prow, f[u]);
+            if (i - D >= 0) copy_row<Sout, V>(ring_s + (i % D) * pitch, pback);
+          }
         }
         prow -= M;
         pback -= M;
       }
       cp_commit();
-    }
+    };
+    int top = N - 1;
+#pragma unroll 1
+    for (; top >= D + U - 1; top -= U) bwd(std::true_type{}, top);
+#pragma unroll 1
+    for (; top >= 0; top -= U) bwd(std::false_type{}, top);
     cp_wait<0>();
   }
 }
