@@ -287,7 +287,10 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
     float2* ps = reinterpret_cast<float2*>(X) + j;
 
     // ---- pass 1 (rows up): slot <- (w, delta).  Row addresses advance by
-    // pointer increments (no 64-bit multiply per row).
+    // pointer increments (no 64-bit multiply per row).  One copy group per
+    // block of kRU rows (a block waits for the group committed D / kRU
+    // groups earlier); FULL blocks -- all kRU rows exist and each refills its
+    // slot -- run without per-row guards.
     {
       float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
       const float* pnext = pb;  // next row to request
@@ -295,33 +298,38 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
       for (int r = 0; r < D; r++) {
         if (r < N) cp_async4(ring_s + r * pitch, pnext);
         pnext += M;
-        cp_commit();
+        if ((r + 1) % kRU == 0) cp_commit();
       }
       float2* prow = ps;  // slot of row i0
-#pragma unroll 1
-      for (int i0 = 0; i0 < N; i0 += kRU) {
-        cp_wait<D - kRU>();
-        const int n = (N - i0) < kRU ? (N - i0) : kRU;
+      auto pass1 = [&](auto full_tag, int i0) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        cp_wait<D / kRU - 1>();
+        const int n = FULL ? kRU : ((N - i0) < kRU ? (N - i0) : kRU);
         const int s0 = i0 % D;
         float b[kRU], w[kRU], d[kRU];
 #pragma unroll
         for (int u = 0; u < kRU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          if (u < n && i0 + u + D < N) cp_async4(ring_s + (s0 + u) * pitch, pnext);
+          if (FULL || (u < n && i0 + u + D < N)) cp_async4(ring_s + (s0 + u) * pitch, pnext);
           pnext += M;
-          cp_commit();
         }
+        cp_commit();
         if constexpr (SMEM)
           frefine_pass1<BW, kRU>(rc, i0, n, b, w, d, w1, w2, d1, d2);
         else
           frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          if (u < n) *prow = make_float2(w[u], d[u]);
+          if (FULL || u < n) *prow = make_float2(w[u], d[u]);
           prow += M;
         }
-      }
+      };
+      int i0 = 0;
+#pragma unroll 1
+      for (; i0 + kRU + D <= N; i0 += kRU) pass1(std::true_type{}, i0);
+#pragma unroll 1
+      for (; i0 < N; i0 += kRU) pass1(std::false_type{}, i0);
       cp_wait<0>();
     }
     // ---- pass 2 (rows down): X
@@ -332,13 +340,13 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
       for (int r = 0; r < D; r++) {
         if (N - 1 - r >= 0) cp_async8(ring_s + r * pitch, pback);
         pback -= M;
-        cp_commit();
+        if ((r + 1) % kRU == 0) cp_commit();
       }
       double* pout = px + (int64_t)(N - 1) * M;  // output row `top`
-#pragma unroll 1
-      for (int top = N - 1; top >= 0; top -= kRU) {
-        cp_wait<D - kRU>();
-        const int n = (top + 1) < kRU ? (top + 1) : kRU;
+      auto pass2 = [&](auto full_tag, int top) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        cp_wait<D / kRU - 1>();
+        const int n = FULL ? kRU : ((top + 1) < kRU ? (top + 1) : kRU);
         const int s0 = (N - 1 - top) % D;
         float w[kRU], dl[kRU];
         double xo[kRU];
@@ -350,20 +358,25 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
         }
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          if (u < n && top - u - D >= 0) cp_async8(ring_s + (s0 + u) * pitch, pback);
+          if (FULL || (u < n && top - u - D >= 0)) cp_async8(ring_s + (s0 + u) * pitch, pback);
           pback -= M;
-          cp_commit();
         }
+        cp_commit();
         if constexpr (SMEM)
           frefine_pass2<BW, kRU>(rc, top, n, w, dl, xo, x1, x2, e1, e2);
         else
           frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
 #pragma unroll
         for (int u = 0; u < kRU; u++) {
-          if (u < n) *pout = xo[u];
+          if (FULL || u < n) *pout = xo[u];
           pout -= M;
         }
-      }
+      };
+      int top = N - 1;
+#pragma unroll 1
+      for (; top >= D + kRU - 1; top -= kRU) pass2(std::true_type{}, top);
+#pragma unroll 1
+      for (; top >= 0; top -= kRU) pass2(std::false_type{}, top);
       cp_wait<0>();
     }
   }
