@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 863921152 + 165632, "sha": "8f193dc9c0c61583"},
-    "f64_solve": {"bytes": 472388864 + 431877888, "sha": "0c04615c0d2c1943"},
-    "adjoint_f64": {"bytes": 472751104 + 430187520, "sha": "0c04615c0d2c1943"},
-    "refine_solve": {"bytes": 355728384 + 436071936, "sha": "45524936f5f3b6d7"},
+    "band_grad_f64": {"bytes": 864131072 + 92928, "sha": "0a29990a87f74cb2"},
+    "f64_solve": {"bytes": 472630528 + 432050944, "sha": "c1c38219756d9d7b"},
+    "adjoint_f64": {"bytes": 471394304 + 429535488, "sha": "c1c38219756d9d7b"},
+    "refine_solve": {"bytes": 356244480 + 437019392, "sha": "2ce32cf91bc411ad"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
