@@ -24,6 +24,60 @@
 
 namespace bs {
 
+// FP64 primal plans with staged coefficients fold the forward sweep's row
+// scale s_i into the explicit operator: s_i (c + r (left - 2c + right)) =
+// e0_i c + e1_i (left + right) with e0_i = s_i (1 - 2r), e1_i = s_i r, staged
+// once per CTA as one 16-byte pair per row (ahead of the plan's arrays, so a
+// row still takes two shared loads in the tridiagonal case).  Per unknown
+// that is one ADD, one MUL and one FMA before the unscaled forward
+// recurrence, against two FMAs, an ADD and the scale's MUL: one FP64
+// instruction fewer, and the FP64 half-steps are bound by the FP64 pipe.
+// (FP32 half-steps are bound by latency and keep the plain form.)
+__device__ __forceinline__ void fuse_explicit(const double* s, double2* pr, int N, double r) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double si = s[i];
+    pr[i] = make_double2(si * (1.0 - 2.0 * r), si * r);
+  }
+  __syncthreads();
+}
+
+// Forward block of the fused step: f[u] holds the centre value c and nb[u]
+// the sum of the two neighbours of row i0 + u on entry, the forward value
+// w = e0 c + e1 nb - l2 w2 - l1 w1 on exit.  All coefficient loads are issued
+// first, as in fwd_block.
+template <int BW, int U>
+__device__ __forceinline__ void adi_fwd_fused(const Coefs<double>& cf, const double2* pr, int i0, int n,
+                                              double (&f)[U][1], const double (&nb)[U], double (&w1)[1],
+                                              double (&w2)[1]) {
+  double2 e[U];
+  double l1[U], l2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (u < n) ? i0 + u : i0;
+    e[u] = pr[i];
+    l1[u] = cf.l1[i];
+    l2[u] = BW == 2 ? cf.l2[i] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (u < n) {
+      double w = fma(e[u].y, nb[u], e[u].x * f[u][0]);
+      if (BW == 2) w = fma(-l2[u], w2[0], w);
+      w = fma(-l1[u], w1[0], w);
+      if (BW == 2) w2[0] = w1[0];
+      w1[0] = w;
+      f[u][0] = w;
+    }
+  }
+}
+
+// Shared elements (of C) ahead of the plan's staged arrays: the (e0, e1)
+// pairs of a fused launch.
+template <typename C, bool FUSE>
+__host__ __device__ constexpr size_t fuse_elems(int N) {
+  return FUSE ? (size_t)N * 2 : 0;
+}
+
 // ----------------------------------------------------- implicit along y
 
 // Y-implicit half-step: one warp owns 32
@@ -53,14 +107,18 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
   constexpr bool REC = SMEM && std::is_same<C, float>::value;
   const float4* fr = reinterpret_cast<const float4*>(smem_raw);
   const float4* br = fr + N;
+  constexpr bool FUSE = SMEM && !ADJ && sizeof(C) == 8;
   Coefs<C> cf = cf_g;
+  const double2* pr = reinterpret_cast<const double2*>(smem_raw);
   size_t coef_bytes;
   if constexpr (REC) {
     stage_records<BW, ADJ, false>(cf_g, N, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + N);
     coef_bytes = (size_t)N * 2 * sizeof(float4);
   } else {
-    cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, reinterpret_cast<C*>(smem_raw));
-    coef_bytes = SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) : 0;
+    C* smc = reinterpret_cast<C*>(smem_raw) + fuse_elems<C, FUSE>(N);
+    cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+    if constexpr (FUSE) fuse_explicit(cf.s, reinterpret_cast<double2*>(smem_raw), N, r);
+    coef_bytes = SMEM ? align_up((fuse_elems<C, FUSE>(N) + (size_t)coef_arrays<BW>() * N) * sizeof(C), 16) : 0;
   }
   const int lane = threadIdx.x & 31;
   // slot layout per lane: [own value | outer neighbour], 2 * sizeof(C) bytes
@@ -101,7 +159,7 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       __syncwarp();
       const int n = (N - i0) < U ? (N - i0) : U;
       const int s0 = i0 % D;
-      C f[U][1];
+      C f[U][1], nb[U];
 #pragma unroll
       for (int q = 0; q < U; q++) {
         const C* sl = reinterpret_cast<const C*>(ring + (size_t)(s0 + q) * pitch);
@@ -111,7 +169,12 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         C right = __shfl_down_sync(0xffffffffu, c, 1);
         if (lane == 0) left = outer;
         if (lane == 31) right = outer;
-        f[q][0] = c + r * (left - C(2) * c + right);
+        if constexpr (FUSE) {
+          f[q][0] = c;
+          nb[q] = left + right;
+        } else {
+          f[q][0] = c + r * (left - C(2) * c + right);
+        }
       }
       __syncwarp();
 #pragma unroll
@@ -120,7 +183,9 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
         cp_commit();
       }
       if (valid) {
-        if constexpr (REC)
+        if constexpr (FUSE)
+          adi_fwd_fused<BW, U>(cf, pr, i0, n, f, nb, r1, r2);
+        else if constexpr (REC)
           fwd_block_rec<BW, ADJ, 1, U, false>(fr, 0.f, i0, n, f, r1, r2);
         else
           fwd_block<BW, ADJ, C, 1, U>(cf, i0, n, f, r1, r2);
@@ -196,11 +261,16 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
     u += r0;
     out += r0;
   }
-  C* smc = reinterpret_cast<C*>(smem_raw);
+  constexpr bool FUSE = SMEM && !ADJ && sizeof(C) == 8;
+  const double2* pr = reinterpret_cast<const double2*>(smem_raw);
+  C* smc = reinterpret_cast<C*>(smem_raw) + fuse_elems<C, FUSE>(N);
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
+  if constexpr (FUSE) fuse_explicit(cf.s, reinterpret_cast<double2*>(smem_raw), N, r);
   const int lane = threadIdx.x;
   const int crow = lane % R, cph = lane / R;  // chunk row and system phase of this lane's copies
-  C* ringt = smc + (SMEM ? align_up((size_t)coef_arrays<BW>() * N * sizeof(C), 16) / sizeof(C) : 0);
+  C* ringt = reinterpret_cast<C*>(smem_raw) +
+             (SMEM ? align_up((fuse_elems<C, FUSE>(N) + (size_t)coef_arrays<BW>() * N) * sizeof(C), 16) / sizeof(C)
+                   : 0);
   auto cp = [&](C* dst, const C* src) {
     const uint32_t d = smem_u32(dst);
     if constexpr (sizeof(C) == 8)
@@ -241,17 +311,25 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       C* tin = ringt + (c % K) * kTile;
       for (int q0 = 0; q0 < rows; q0 += U) {
         const int n = (rows - q0) < U ? (rows - q0) : U;
-        C f[U][1];
+        C f[U][1], nb[U];
         if (mine) {
 #pragma unroll
           for (int q = 0; q < U; q++) {
             const C* t = tin + (q0 + q) * kAdiTile + lane;
-            f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
+            if constexpr (FUSE) {
+              f[q][0] = t[1];
+              nb[q] = t[0] + t[2];
+            } else {
+              f[q][0] = t[1] + r * (t[0] - C(2) * t[1] + t[2]);
+            }
           }
         }
         __syncwarp();
         if (mine) {
-          fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
+          if constexpr (FUSE)
+            adi_fwd_fused<BW, U>(cf, pr, c0 + q0, n, f, nb, r1, r2);
+          else
+            fwd_block<BW, ADJ, C, 1, U>(cf, c0 + q0, n, f, r1, r2);
 #pragma unroll
           for (int q = 0; q < U; q++)
             if (q < n) tin[(q0 + q) * kAdiTile + lane + 1] = f[q][0];
@@ -327,7 +405,9 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   // 1 + 2 BW arrays (k_adi_il2; 0.115 -> 0.108 ms per 4096^2 half-step).  The
   // one-warp CTAs along x keep the arrays: records there cost resident CTAs
   // (0.113 -> 0.121 ms).
-  constexpr int kRecExtra = sizeof(C) == 4 ? 8 - coef_arrays<BW>() : 0;
+  // FP64 primal plans stage the (e0, e1) pairs beside the arrays (fuse_explicit).
+  constexpr int kFuseExtra = (sizeof(C) == 8 && !ADJ) ? 2 : 0;
+  constexpr int kRecExtra = sizeof(C) == 4 ? 8 - coef_arrays<BW>() : kFuseExtra;
   if (axis == 1) {
     auto go = [&](auto dtag) -> cudaError_t {
       constexpr int D = decltype(dtag)::value;
@@ -348,7 +428,7 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     constexpr int R = decltype(rtag)::value;
     const size_t tiles = (size_t)K * R * kAdiTile * sizeof(C);
     const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32);
+    const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32, kFuseExtra);
     auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K, R> : k_adi_st2<BW, ADJ, false, C, K, R>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
     if (e != cudaSuccess) return e;
