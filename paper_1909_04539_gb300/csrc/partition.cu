@@ -12,7 +12,8 @@
 // Step 2 (k_part_reduced) solves, per system, the banded reduced system for
 // the 2h values at each block edge (rows bot(b)-h+1 .. bot(b), top(b+1) ..
 // top(b+1)+h-1), whose LU is computed once with the handle.  Step 3
-// (k_part_fix) applies the correction to the rows where a spike is non-zero:
+// (k_part_fix_il / k_part_fix_st for the two layouts) applies the correction
+// to the rows where a spike is non-zero:
 // the first kv and the last kw rows of each block (spike entries below 2^-60
 // of their maximum are zero, which changes no result above rounding).
 #include "sweep_kernels.cuh"
