@@ -52,14 +52,14 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 864131072 + 92928, "sha": "0a29990a87f74cb2"},
-    "f64_solve": {"bytes": 472630528 + 432050944, "sha": "c1c38219756d9d7b"},
-    "adjoint_f64": {"bytes": 471394304 + 429535488, "sha": "c1c38219756d9d7b"},
-    "refine_solve": {"bytes": 356244480 + 437019392, "sha": "2ce32cf91bc411ad"},
+    "band_grad_f64": {"bytes": 864354560 + 83456, "sha": "7ba2374f98630563"},
+    "f64_solve": {"bytes": 472626432 + 432110592, "sha": "39127f130240d1c5"},
+    "adjoint_f64": {"bytes": 471495424 + 429850368, "sha": "39127f130240d1c5"},
+    "refine_solve": {"bytes": 356485376 + 437087488, "sha": "f8df3951d185c4cf"},
 }
 KERNEL_SOURCES = {
-    "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
-    "adjoint_f64": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h"],
+    "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h", "solve_api.cu"],
+    "adjoint_f64": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h", "solve_api.cu"],
     "refine_solve": ["refine.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
     "band_grad_f64": ["band_grad.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
 }

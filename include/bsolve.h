@@ -355,7 +355,11 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    (interleaved layout) when a batch has at most 128 systems per SM and
  *    would not be row-partitioned into more than two blocks
  *    (BS_OPT_PARTITION 2 keeps the partition); 1: never; 2: whenever the
- *    handle allows (interleaved, not partitioned). */
+ *    handle allows (interleaved, not partitioned).
+ *  BS_OPT_CTA_THREADS: threads per CTA of the streaming sweep and ADI
+ *    kernels that size their CTAs by policy.  0 (default): the policy (128,
+ *    halved while the batch would give fewer than two CTAs per SM, down to
+ *    32); 32, 64 or 128: that size.  Other values are rejected (BS_EINVAL). */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
@@ -364,7 +368,8 @@ typedef enum {
   BS_OPT_PARTITION = 4,
   BS_OPT_UNIFORM = 5,
   BS_OPT_TWISTED = 6,
-  BS_OPT_COUNT = 7
+  BS_OPT_CTA_THREADS = 7,
+  BS_OPT_COUNT = 8
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

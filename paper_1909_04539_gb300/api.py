@@ -24,6 +24,7 @@ OPT_TMA_AHEAD = 3
 OPT_PARTITION = 4
 OPT_UNIFORM = 5
 OPT_TWISTED = 6
+OPT_CTA_THREADS = 7
 
 
 def device_status(reset: bool = False) -> int:

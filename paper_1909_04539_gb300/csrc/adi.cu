@@ -413,7 +413,7 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
       constexpr int D = decltype(dtag)::value;
       const int64_t threads = ((M + 31) / 32) * 32;
       const LaunchShape sh =
-          sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0, kRecExtra);
+          sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, (size_t)D * 2 * sizeof(C), 0, 0, kRecExtra, P > 1);
       const size_t bytes = sh.smem + (size_t)sh.threads * D * 2 * sizeof(C);
       auto k = sh.smem_coefs ? k_adi_il2<BW, ADJ, true, C, D> : k_adi_il2<BW, ADJ, false, C, D>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

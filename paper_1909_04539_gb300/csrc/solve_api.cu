@@ -1,4 +1,5 @@
 // C-ABI entry points of the solves and the launch-shape policy.
+#include <algorithm>
 #include <climits>
 #include <string>
 
@@ -18,15 +19,12 @@ static int64_t g_opt[BS_OPT_COUNT] = {0};
 
 int64_t option(int o) { return (o >= 0 && o < BS_OPT_COUNT) ? g_opt[o] : 0; }
 
-LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
-                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
-                        int extra_coef_arrays) {
+// The shape of one launch for a given CTA size.
+static LaunchShape shape_for(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
+                             int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
+                             int extra_coef_arrays) {
   const DeviceInfo& d = device_info();
   LaunchShape sh{};
-  if (tpb <= 0) {
-    tpb = 128;
-    while (tpb > 32 && threads_needed < (int64_t)2 * d.sms * tpb) tpb /= 2;
-  }
   sh.threads = tpb;
   const size_t coef_bytes = align_up((size_t)(1 + 2 * bw + extra_coef_arrays) * N * coef_elem, 16);
   const size_t extra = extra_smem_fixed + extra_smem_per_thread * (size_t)tpb;
@@ -55,6 +53,69 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
   if (grid < 1) grid = 1;
   sh.grid = (int)grid;
   return sh;
+}
+
+// Estimated time of an FP64 sweep launch, in units of one warp's share of
+// the FP64 pipe, on its busiest SM.  CTAs go to SMs in turn and each takes
+// groups of systems c, c + grid, ... of the persistent loop, so the busiest
+// SM runs its ceil(grid / sms) CTAs for q = blocks / grid rounds and its
+// share of the rem = blocks % grid remainder in one more.  A round with k
+// warps on the SM costs max(k, kLone): below ~5.5 warps the FP64 pipe is no
+// longer the bound and a round costs what a nearly lone warp's dependent
+// chain takes (fitted to the penta N = 512, M = 65536 solve, the 4096-line
+// ADI half-step and the partitioned tri N = 4096, M = 4096 solve at 32, 64
+// and 128 threads: the short second rounds of a grid that holds only part of
+// the batch were 9-20 % slower, one round with 7 warps per SM instead of
+// 3-4 CTAs of 4 was 5-8 % faster).
+static double fp64_round_cost(const LaunchShape& sh, int64_t threads_needed, int sms) {
+  constexpr double kLone = 5.5;
+  const int64_t blocks = (threads_needed + sh.threads - 1) / sh.threads;
+  const int64_t grid = sh.grid;
+  const double w = sh.threads / 32.0;
+  const int64_t q = blocks / grid, rem = blocks % grid;
+  auto round = [&](int64_t ctas) { return std::max((double)ctas * w, kLone); };
+  double c = (double)q * round((grid + sms - 1) / sms);
+  if (rem > 0) c += round((rem + sms - 1) / sms);
+  return c;
+}
+
+LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
+                        int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
+                        int extra_coef_arrays, bool balance) {
+  const DeviceInfo& d = device_info();
+  auto shape = [&](int t) {
+    return shape_for(bw, N, threads_needed, coef_elem, spill_elem, per_thread_systems, extra_smem_per_thread,
+                     extra_smem_fixed, t, extra_coef_arrays);
+  };
+  if (tpb > 0) return shape(tpb);
+  if (option(BS_OPT_CTA_THREADS) > 0) return shape((int)option(BS_OPT_CTA_THREADS));
+  // Policy: 128 threads, halved while the batch would give fewer than two
+  // CTAs per SM.  With `balance` (row-partitioned ADI half-steps), FP64 sweeps,
+  // bound by the FP64 pipe, then take the CTA size whose rounds load the
+  // busiest SM least (fp64_round_cost), if it is strictly better; the larger
+  // CTA on a tie (4096^2 FP64 y-implicit half-step: 0.231 -> 0.215 ms).
+  // Solves keep the plain policy: on the penta N = 512, M = 65536 batch
+  // 32-thread CTAs made the FP64 solve 5 % faster alone, but they fill every
+  // SM's shared memory, and a mixed-precision solve on another stream could
+  // no longer run beside it (that step: 1.107 -> 1.235 ms); partitioned
+  // solves (tri N = 4096, M = 4096: 0.145 -> 0.138 ms alone) share the
+  // server's streams the same way.
+  tpb = 128;
+  while (tpb > 32 && threads_needed < (int64_t)2 * d.sms * tpb) tpb /= 2;
+  LaunchShape best = shape(tpb);
+  if (balance && coef_elem == 8 && spill_elem == 8) {
+    double best_cost = fp64_round_cost(best, threads_needed, d.sms);
+    for (int t = 128; t >= 32; t /= 2) {
+      if (t == tpb) continue;
+      const LaunchShape sh = shape(t);
+      const double c = fp64_round_cost(sh, threads_needed, d.sms);
+      if (c < best_cost * 0.97) {
+        best = sh;
+        best_cost = c;
+      }
+    }
+  }
+  return best;
 }
 
 bs_status part_correct(const PartPlan& pp, int N, void* X, bs_dtype t, bs_layout layout, int64_t M,
@@ -105,6 +166,8 @@ extern "C" {
 bs_status bs_set_option(int opt, int64_t value) {
   if (opt < 0 || opt >= BS_OPT_COUNT) return set_error(BS_EINVAL, "bs_set_option: unknown option");
   if (value < 0) return set_error(BS_EINVAL, "bs_set_option: negative value");
+  if (opt == BS_OPT_CTA_THREADS && value != 0 && value != 32 && value != 64 && value != 128)
+    return set_error(BS_EINVAL, "bs_set_option: BS_OPT_CTA_THREADS must be 0, 32, 64 or 128");
   g_opt[opt] = value;
   return BS_OK;
 }

@@ -768,10 +768,13 @@ struct LaunchShape {
 // tpb = 0 lets the policy pick 32, 64 or 128 threads per CTA so that small
 // batches still spread over every SM.
 // extra_coef_arrays: coefficient arrays staged beyond the 1 + 2 bw of a plain
-// sweep (2 for the periodic correction).
+// sweep (2 for the periodic correction).  balance: pick the CTA size of an
+// FP64 launch by the load of the busiest SM (the row-partitioned ADI
+// half-steps; solves keep the plain policy, since concurrent solves on other
+// streams lose the SMs whose shared memory a balanced grid fills).
 LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem, size_t spill_elem,
                         int per_thread_systems, size_t extra_smem_per_thread, size_t extra_smem_fixed, int tpb,
-                        int extra_coef_arrays = 0);
+                        int extra_coef_arrays = 0, bool balance = false);
 
 // L, P: rows per block and blocks of a partitioned launch (L = N, P = 1
 // otherwise); grid.y = P.
@@ -885,6 +888,7 @@ cudaError_t dispatch_sweep(const SweepPlan& p, bool adjoint, int N, const Sin* i
     if (!adjoint) { BS_DISPATCH(2, false, false, false) } else { BS_DISPATCH(2, true, false, false) }
   }
 #undef BS_DISPATCH
+  return cudaErrorNotSupported;  // not reached: every branch above returns
 }
 
 }  // namespace bs

@@ -70,6 +70,12 @@ def test_set_option(L):
     assert L.bs_set_option(0, 0) == 0
     assert L.bs_set_option(99, 1) == 1
     assert L.bs_set_option(0, -5) == 1
+    # BS_OPT_CTA_THREADS takes 0, 32, 64 or 128 only
+    for v in (32, 64, 128, 0):
+        assert L.bs_set_option(7, v) == 0
+    for v in (1, 48, 256):
+        assert L.bs_set_option(7, v) == 1
+    assert L.bs_set_option(7, 0) == 0
 
 
 def test_option_constants_match_header():

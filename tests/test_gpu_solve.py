@@ -208,3 +208,24 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
         X, Y, Xb = outs[kern]
         assert rel_l2(X, ref) < TOL32 and rel_l2(Y, refa) < TOL32 and rel_l2(Xb, refb) < TOL32
     assert bs.device_status() == 0
+
+
+@pytest.mark.parametrize("cta", [32, 64, 128])
+@pytest.mark.parametrize("width,N,M,dtype", [(5, 512, 4100, torch.float64), (3, 257, 1027, torch.float32),
+                                              (3, 1000, 3000, torch.float64)])
+def test_cta_threads_option(bs, width, N, M, dtype, cta):
+    """Every CTA size of BS_OPT_CTA_THREADS gives the oracle's solution (the
+    last shape is row-partitioned)."""
+    bands = _bands(width, N, 11)
+    Bh = _rhs(N, M, 11, "interleaved")
+    if dtype == torch.float32:
+        Bh = Bh.astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    bs.set_option(bs.OPT_CTA_THREADS, cta)
+    try:
+        X = torch.tensor(Bh, dtype=dtype, device="cuda")
+        bs.solve(f, X)
+        torch.cuda.synchronize()
+    finally:
+        bs.set_option(bs.OPT_CTA_THREADS, 0)
+    assert rel_l2(X.double().cpu().numpy(), oracle.solve(bands, Bh)) < (TOL64 if dtype == torch.float64 else TOL32)
