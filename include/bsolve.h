@@ -359,7 +359,9 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *  BS_OPT_CTA_THREADS: threads per CTA of the streaming sweep and ADI
  *    kernels that size their CTAs by policy.  0 (default): the policy (128,
  *    halved while the batch would give fewer than two CTAs per SM, down to
- *    32); 32, 64 or 128: that size.  Other values are rejected (BS_EINVAL). */
+ *    32; row-partitioned FP64 ADI half-steps then take whichever of 32, 64
+ *    and 128 loads the busiest SM least); 32, 64 or 128: that size.  Other
+ *    values are rejected (BS_EINVAL).  The result does not depend on it. */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,

@@ -72,9 +72,10 @@ k_part_reduced(const C* __restrict__ lu_g, int R, int p, int q, int L, int N, co
     const int64_t j = j0 + lane;
     const bool valid = j < M;
     if (valid)
-      for (int i = 0; i < R; i++) part_cp(smem_u32(zt + i * kPartRedThreads + lane), X + part_zrow<H>(i, L, N) * rs + j * ss);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      for (int i = 0; i < R; i++)
+        part_cp(smem_u32(zt + i * kPartRedThreads + lane), X + part_zrow<H>(i, L, N) * rs + j * ss);
+    cp_commit();
+    cp_wait<0>();
     __syncwarp();  // also orders the lu staging before its first use
     if (valid) {
       C win[kPartBand];  // win[k] = the value k + 1 rows back
