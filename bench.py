@@ -48,7 +48,8 @@ NOMINAL_HBM_GBS = 8000.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # step's kernels from one ncu capture of this workload, valid only while the
-# kernel sources hash to the value they had at capture time.
+# kernel sources (for the sweeps also the launch policy in solve_api.cu, which
+# sets their grid) hash to the value they had at capture time.
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
