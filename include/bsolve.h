@@ -360,8 +360,49 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    kernels that size their CTAs by policy.  0 (default): the policy (128,
  *    halved while the batch would give fewer than two CTAs per SM, down to
  *    32; row-partitioned FP64 ADI half-steps then take whichever of 32, 64
- *    and 128 loads the busiest SM least); 32, 64 or 128: that size.  Other
- *    values are rejected (BS_EINVAL).  The result does not depend on it. */
+ *    and 128 loads the busiest SM least); 32, 64 or 128: that size; a
+ *    multiple of 64 up to 512: that size for the windowed sweeps
+ *    (BS_OPT_WINDOW), 128 for the other kernels.  Other values are rejected
+ *    (BS_EINVAL).  The result does not depend on it.
+ *  BS_OPT_F64_PAIRS: arithmetic of the FP64 (BS_F64) solves of bs_solve and
+ *    bs_solve_adjoint that run one thread per system (not row-partitioned,
+ *    not two-ended), interleaved layout, non-periodic handle (not in the
+ *    paper).  GB300 issues FP64 instructions at ~1/66 of the FP32 rate, so
+ *    these sweeps carry every value as an unevaluated sum of two FP32 numbers
+ *    (48 significant bits) formed with error-free products and sums, and
+ *    convert the FP64 data with integer operations: FP64 in, FP64 out,
+ *    relative error a few units of 2^-48 (about 1e-14) against the exact
+ *    solution of the FP64 data instead of ~1e-16.  bs_factor admits a matrix
+ *    for it when every sweep coefficient has magnitude in [2^-100, 2^100)
+ *    (or is 0) and the sweeps' gains are at most 2^24 (intermediates at most
+ *    2^24 times the largest input); other handles always take native FP64.
+ *    A warp of systems that meets an input outside the pairs' range (nonzero
+ *    |x| < 2^-72 or >= 2^101, inf, NaN) continues those systems in native
+ *    FP64 from that row on.  0 (default): pairs where admitted, two systems
+ *    per thread when the batch has at least 2 x 256 systems per SM (else
+ *    one); 1: native FP64 always; 2: pairs with one system per thread; 3:
+ *    pairs with two systems per thread (even M and 16-byte aligned data).
+ *  BS_OPT_WINDOW: windowed sweeps that keep the forward-sweep values on chip
+ *    (not in the paper).  For the matrices the method targets, a backward
+ *    sweep started from zero at some row instead of from the true solution
+ *    there agrees with the true one, a few tens of rows above it, to 2^-50
+ *    of the system's largest value (2^-28 for FP32 arithmetic): bs_factor
+ *    measures that distance Lw for A and A^T.  A windowed sweep then solves
+ *    each system in blocks of rows held in shared memory: the backward sweep
+ *    of a block starts from zero at the block's end and writes the rows more
+ *    than Lw above it; the next block's backward sweep passes through the
+ *    block's last Lw rows again and writes them.  B is read once and X
+ *    written once, instead of the forward values also going to memory and
+ *    back, at the price of Lw extra backward steps per block; the result
+ *    differs from the two-sweep solve by at most 2^-50 (2^-28) of the
+ *    system's largest value per row.  Used by the one-thread-per-system
+ *    interleaved solves of bs_solve and bs_solve_adjoint (BS_F32) and by
+ *    bs_solve_bf16 (even M) when the handle has a window (non-periodic,
+ *    decay within 28 rows for FP32 arithmetic; 52 rows for pairs).  The FP64
+ *    solves in pairs are bound by instruction issue, where the extra backward
+ *    steps cost more than the round trip of the forward values through
+ *    memory saves, so they use windows only on request.  0 (default): FP32
+ *    arithmetic where available; 1: never; 2: FP32 and pair arithmetic. */
 typedef enum {
   BS_OPT_INFLIGHT_BYTES = 0,
   BS_OPT_BLOCKS_PER_SM = 1,
@@ -371,7 +412,9 @@ typedef enum {
   BS_OPT_UNIFORM = 5,
   BS_OPT_TWISTED = 6,
   BS_OPT_CTA_THREADS = 7,
-  BS_OPT_COUNT = 8
+  BS_OPT_F64_PAIRS = 8,
+  BS_OPT_WINDOW = 9,
+  BS_OPT_COUNT = 10
 } bs_option;
 bs_status bs_set_option(int opt, int64_t value);
 

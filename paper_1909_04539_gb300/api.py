@@ -25,6 +25,8 @@ OPT_PARTITION = 4
 OPT_UNIFORM = 5
 OPT_TWISTED = 6
 OPT_CTA_THREADS = 7
+OPT_F64_PAIRS = 8
+OPT_WINDOW = 9
 
 
 def device_status(reset: bool = False) -> int:

@@ -214,6 +214,8 @@ void free_handle(bs_handle h) {
   for (auto& p : h->plan) {
     if (p.c64) cudaFree(p.c64);
     if (p.c32) cudaFree(p.c32);
+    if (p.dfrec) cudaFree(p.dfrec);
+    if (p.rec32) cudaFree(p.rec32);
   }
   if (h->bands64) cudaFree(h->bands64);
   if (h->bands_hi) cudaFree(h->bands_hi);
@@ -392,6 +394,126 @@ bool make_partition(const double* const* bd, int width, int64_t N, HostPart& hp)
   return true;
 }
 
+// Records of the FP32-pair sweeps (sweep_df.cu) of a primal (fwd_scale) or
+// adjoint (bwd_scale) plan: each coefficient c as the pair (fl32(c),
+// fl32(c - fl32(c))), per row and sweep the pairs present -- (s), l1, (l2)
+// forward, (t), u1, (u2) backward -- the first two in a float4, the third in a
+// float2 (layout of SweepPlan::dfrec).  Returns whether pair arithmetic is
+// safe for the plan: every coefficient is zero or of magnitude in
+// [2^-100, 2^100), and the sweep gains bound every intermediate by 2^24 times
+// the largest input, so that inputs below 2^101 keep every value below 2^125.
+// The gains follow the recurrences on magnitudes: with |f_i| <= 1,
+// |w_i| <= W_i = |s_i| + |l1_i| W_{i-1} + |l2_i| W_{i-2} and
+// |x_i| <= X_i = |t_i| W_i + |u1_i| X_{i+1} + |u2_i| X_{i+2}.
+bool make_df_records(const HostPlan& hp, int64_t N, std::vector<float>& rec) {
+  auto C = [&](int k, int64_t i) { return hp.c[(size_t)k * N + i]; };
+  bool ok = true;
+  auto pair = [&](double c, float& h, float& l) {
+    const double a = std::fabs(c);
+    if (!std::isfinite(c) || (c != 0.0 && (a < std::ldexp(1.0, -100) || a >= std::ldexp(1.0, 100)))) ok = false;
+    h = (float)c;
+    l = (float)(c - (double)h);
+  };
+  rec.assign((size_t)12 * N, 0.f);
+  float* f4 = rec.data();
+  float* b4 = f4 + 4 * N;
+  float* f2 = b4 + 4 * N;
+  float* b2 = f2 + 2 * N;
+  const bool adj = hp.bwd_scale;
+  for (int64_t i = 0; i < N; i++) {
+    float v[6] = {0, 0, 0, 0, 0, 0};
+    int n = 0;
+    if (!adj) pair(C(C_S, i), v[0], v[1]), n = 2;
+    pair(C(C_L1, i), v[n], v[n + 1]);
+    n += 2;
+    if (hp.bw == 2) pair(C(C_L2, i), v[n], v[n + 1]);
+    for (int q = 0; q < 4; q++) f4[4 * i + q] = v[q];
+    f2[2 * i] = v[4], f2[2 * i + 1] = v[5];
+    for (float& x : v) x = 0.f;
+    n = 0;
+    if (adj) pair(C(C_T, i), v[0], v[1]), n = 2;
+    pair(C(C_U1, i), v[n], v[n + 1]);
+    n += 2;
+    if (hp.bw == 2) pair(C(C_U2, i), v[n], v[n + 1]);
+    for (int q = 0; q < 4; q++) b4[4 * i + q] = v[q];
+    b2[2 * i] = v[4], b2[2 * i + 1] = v[5];
+  }
+  std::vector<double> W(N), X(N);
+  double g = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    double w = adj ? 1.0 : std::fabs(C(C_S, i));
+    if (i >= 1) w += std::fabs(C(C_L1, i)) * W[i - 1];
+    if (i >= 2) w += std::fabs(C(C_L2, i)) * W[i - 2];
+    W[i] = w;
+    g = std::max(g, w);
+  }
+  for (int64_t i = N - 1; i >= 0; i--) {
+    double x = (adj ? std::fabs(C(C_T, i)) : 1.0) * W[i];
+    if (i + 1 < N) x += std::fabs(C(C_U1, i)) * X[i + 1];
+    if (i + 2 < N) x += std::fabs(C(C_U2, i)) * X[i + 2];
+    X[i] = x;
+    g = std::max(g, x);
+  }
+  return ok && std::isfinite(g) && g <= std::ldexp(1.0, 24);
+}
+
+// Window lengths of the windowed sweeps (sweep_win.cu) of one plan.  A
+// backward sweep started from zero at row e instead of from the true x_e,
+// x_{e+1} is off at row j < e by psi1_j x_e + psi2_j x_{e+1}, where psi1,
+// psi2 follow the homogeneous recurrence psi_j = -u1_j psi_{j+1} - u2_j
+// psi_{j+2} from (1, 0) and (0, 1).  The window for a threshold is the
+// largest, over every e, distance e - j at which |psi1_j| + |psi2_j| is still
+// above it, for rows up to `cap` above e; 0 if the responses are above it
+// anywhere between cap and 2 cap rows above some e (no decay within reach).
+// The window is measured for every e, so it holds for any block size.
+void make_windows(const HostPlan& hp, int64_t N, int cap32, int capdf, int& w32, int& wdf) {
+  w32 = wdf = 0;
+  if (N > ((int64_t)1 << 20) || hp.periodic) return;
+  auto C = [&](int k, int64_t i) { return hp.c[(size_t)k * N + i]; };
+  const double t32 = std::ldexp(1.0, -28), tdf = std::ldexp(1.0, -50);
+  const int cap = std::max(cap32, capdf);
+  int m32 = 0, mdf = 0;
+  bool ok32 = true, okdf = true;
+  std::vector<double> a(2 * cap + 3), b(2 * cap + 3);
+  for (int64_t e = 1; e < N && (ok32 || okdf); e++) {
+    // a[d], b[d]: responses at row e - d (d = 0: row e, d = -1: row e + 1)
+    double a1 = 1.0, a2 = 0.0, b1 = 0.0, b2 = 1.0;  // values at rows j + 1, j + 2
+    for (int d = 1; d <= 2 * cap && e - d >= 0; d++) {
+      const int64_t j = e - d;
+      const double u1 = C(C_U1, j), u2 = hp.bw == 2 ? C(C_U2, j) : 0.0;
+      const double an = -u1 * a1 - u2 * a2, bn = -u1 * b1 - u2 * b2;
+      a2 = a1, a1 = an, b2 = b1, b1 = bn;
+      const double r = std::fabs(an) + (hp.bw == 2 ? std::fabs(bn) : 0.0);
+      if (r > t32) {
+        if (d > cap32) ok32 = false;
+        m32 = std::max(m32, d);
+      }
+      if (r > tdf) {
+        if (d > capdf) okdf = false;
+        mdf = std::max(mdf, d);
+      }
+    }
+  }
+  w32 = ok32 ? std::max(m32, 1) : 0;
+  wdf = okdf ? std::max(mdf, 1) : 0;
+}
+
+// FP32 records of the windowed FP32 sweeps (layout of SweepPlan::rec32).
+void make_rec32(const HostPlan& hp, int64_t N, std::vector<float>& rec) {
+  auto C = [&](int k, int64_t i) { return (float)hp.c[(size_t)k * N + i]; };
+  rec.assign((size_t)8 * N, 0.f);
+  for (int64_t i = 0; i < N; i++) {
+    float* f = rec.data() + 4 * i;
+    float* b = rec.data() + 4 * N + 4 * i;
+    f[0] = hp.fwd_scale ? C(C_S, i) : 1.f;
+    f[1] = C(C_L1, i);
+    f[2] = hp.bw == 2 ? C(C_L2, i) : 0.f;
+    b[0] = hp.bwd_scale ? C(C_T, i) : 1.f;
+    b[1] = C(C_U1, i);
+    b[2] = hp.bw == 2 ? C(C_U2, i) : 0.f;
+  }
+}
+
 cudaError_t upload_plan(const HostPlan& hp, SweepPlan& sp, size_t& bytes) {
   sp.bw = hp.bw;
   sp.fwd_scale = hp.fwd_scale;
@@ -455,6 +577,21 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   size_t bytes = 0;
   cudaError_t e = cudaSuccess;
   for (int p = 0; p < 3 && e == cudaSuccess; p++) e = upload_plan(hp[p], hd->plan[p], bytes);
+  // FP32-pair sweep records of the primal and adjoint plans (not periodic)
+  for (int p = 0; p < 2 && e == cudaSuccess && !periodic; p++) {
+    std::vector<float> rec;
+    hd->plan[p].df_ok = make_df_records(hp[p], N, rec);
+    e = cudaMalloc(&hd->plan[p].dfrec, sizeof(float) * rec.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(hd->plan[p].dfrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice);
+    bytes += sizeof(float) * rec.size();
+    make_rec32(hp[p], N, rec);
+    if (e == cudaSuccess) e = cudaMalloc(&hd->plan[p].rec32, sizeof(float) * rec.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(hd->plan[p].rec32, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice);
+    bytes += sizeof(float) * rec.size();
+    make_windows(hp[p], N, win_rows(false), win_rows(true), hd->plan[p].win32, hd->plan[p].win_df);
+  }
   if (parts) {
     for (int p = 0; p < 2 && e == cudaSuccess; p++) e = upload_part(parts[p], hd->part[p], bytes);
     hd->has_part = true;

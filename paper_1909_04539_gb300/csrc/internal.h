@@ -53,6 +53,19 @@ struct SweepPlan {
   double eps;
   double* c64;     // device, C_COUNT * N
   float* c32;      // device, C_COUNT * N
+  // FP32-pair sweeps (sweep_df.cu) of primal and adjoint plans: per row the
+  // coefficient pairs of each sweep packed as float4 + float2 (device, 48 N
+  // bytes: forward float4 x N, backward float4 x N, forward float2 x N,
+  // backward float2 x N); df_ok: the plan's sweep gains keep pair arithmetic
+  // inside the FP32 range for inputs below 2^101 (see make_df_records)
+  float* dfrec;
+  bool df_ok;
+  // Windowed sweeps (sweep_win.cu): FP32 records, per row forward
+  // (s, l1, l2, 0) and backward (t, u1, u2, 0) as float4 (device, 32 N
+  // bytes); win32 / win_df: rows after which a backward sweep started from
+  // zero is within 2^-28 / 2^-50 of the true one (0: not windowed)
+  float* rec32;
+  int win32, win_df;
 };
 
 template <typename C>
@@ -156,5 +169,12 @@ bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int
                         cudaStream_t st);
 bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout,
                            int64_t M, double* dbands, cudaStream_t st);
+bool df_eligible(const SweepPlan& p, bs_layout layout);
+cudaError_t sweep_df(const SweepPlan& p, bool adjoint, int N, double* X, int64_t M, cudaStream_t st);
+cudaError_t sweep_win_df(const SweepPlan& p, bool adjoint, int N, double* X, int64_t M, cudaStream_t st);
+template <typename Sin>
+cudaError_t sweep_win32(const SweepPlan& p, bool adjoint, int N, const Sin* in, float* out, int64_t M,
+                        cudaStream_t st);
+int win_rows(bool pairs);
 
 }  // namespace bs

@@ -88,7 +88,7 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
                      extra_smem_fixed, t, extra_coef_arrays);
   };
   if (tpb > 0) return shape(tpb);
-  if (option(BS_OPT_CTA_THREADS) > 0) return shape((int)option(BS_OPT_CTA_THREADS));
+  if (option(BS_OPT_CTA_THREADS) > 0) return shape((int)std::min<int64_t>(option(BS_OPT_CTA_THREADS), 128));
   // Policy: 128 threads, halved while the batch would give fewer than two
   // CTAs per SM.  With `balance` (row-partitioned ADI half-steps), FP64 sweeps,
   // bound by the FP64 pipe, then take the CTA size whose rounds load the
@@ -142,6 +142,29 @@ bool use_partition(bs_handle h, int64_t M) {
   return M < (int64_t)device_info().sms * 256;
 }
 
+// One-thread-per-system interleaved solve of plan p (primal or adjoint) on
+// the windowed or pair sweeps where they apply; returns false if neither
+// applies (the caller runs the streaming kernels).
+static bool fast_sweep(const SweepPlan& p, bool adjoint, int N, void* B, bs_dtype dtype, bs_layout layout,
+                       int64_t M, cudaStream_t st, cudaError_t* e) {
+  if (layout != BS_INTERLEAVED || p.periodic) return false;
+  const bool win = option(BS_OPT_WINDOW) != 1;
+  if (dtype == BS_F64 && df_eligible(p, layout)) {
+    // pairs: the two-sweep kernel unless windows are asked for (the pair
+    // arithmetic is bound by instruction issue, and the windowed sweep's extra
+    // backward steps cost more than the forward values' round trip through
+    // memory: penta N = 512, M = 65536 0.256 - 0.31 ms against 0.19 ms)
+    *e = (option(BS_OPT_WINDOW) == 2 && p.win_df > 0) ? sweep_win_df(p, adjoint, N, static_cast<double*>(B), M, st)
+                                                       : sweep_df(p, adjoint, N, static_cast<double*>(B), M, st);
+    return true;
+  }
+  if (dtype == BS_F32 && win && p.win32 > 0 && p.rec32) {
+    *e = sweep_win32<float>(p, adjoint, N, static_cast<const float*>(B), static_cast<float*>(B), M, st);
+    return true;
+  }
+  return false;
+}
+
 static bs_status check_common(bs_handle h, const void* B, bs_layout layout, int64_t M, const char* fn) {
   if (!valid_handle(h)) return set_error(BS_EINVAL, std::string(fn) + ": unknown handle");
   if (!B) return set_error(BS_EINVAL, std::string(fn) + ": null data pointer");
@@ -166,8 +189,10 @@ extern "C" {
 bs_status bs_set_option(int opt, int64_t value) {
   if (opt < 0 || opt >= BS_OPT_COUNT) return set_error(BS_EINVAL, "bs_set_option: unknown option");
   if (value < 0) return set_error(BS_EINVAL, "bs_set_option: negative value");
-  if (opt == BS_OPT_CTA_THREADS && value != 0 && value != 32 && value != 64 && value != 128)
-    return set_error(BS_EINVAL, "bs_set_option: BS_OPT_CTA_THREADS must be 0, 32, 64 or 128");
+  if (opt == BS_OPT_CTA_THREADS && value != 0 && value != 32 && !(value % 64 == 0 && value <= 512))
+    return set_error(BS_EINVAL, "bs_set_option: BS_OPT_CTA_THREADS must be 0, 32 or a multiple of 64 up to 512");
+  if (opt == BS_OPT_F64_PAIRS && value > 3) return set_error(BS_EINVAL, "bs_set_option: BS_OPT_F64_PAIRS must be 0..3");
+  if (opt == BS_OPT_WINDOW && value > 2) return set_error(BS_EINVAL, "bs_set_option: BS_OPT_WINDOW must be 0, 1 or 2");
   g_opt[opt] = value;
   return BS_OK;
 }
@@ -188,7 +213,9 @@ bs_status bs_solve(bs_handle h, void* B, bs_dtype dtype, bs_layout layout, int64
   }
   const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   const int L = part ? h->part[0].L : 0, P = part ? h->part[0].P : 1;
-  if (dtype == BS_F64)
+  if (!part && fast_sweep(p, false, N, B, dtype, layout, M, st, &e))
+    ;
+  else if (dtype == BS_F64)
     e = sweep_f64(p, false, N, B, B, layout, M, st, L, P);
   else
     e = sweep_f32(p, false, N, B, B, layout, M, st, L, P);
@@ -213,8 +240,12 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
     return BS_OK;
   }
   const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
-  cudaError_t e = sweep_bf16(p, false, (int)h->N, B, X, layout, M, st, part ? h->part[0].L : 0,
-                             part ? h->part[0].P : 1);
+  cudaError_t e;
+  if (!part && layout == BS_INTERLEAVED && !p.periodic && option(BS_OPT_WINDOW) != 1 && p.win32 > 0 && p.rec32 &&
+      M % 2 == 0 && reinterpret_cast<uintptr_t>(B) % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 8 == 0)
+    e = sweep_win32<__nv_bfloat16>(p, false, (int)h->N, static_cast<const __nv_bfloat16*>(B), X, M, st);
+  else
+    e = sweep_bf16(p, false, (int)h->N, B, X, layout, M, st, part ? h->part[0].L : 0, part ? h->part[0].P : 1);
   if (e != cudaSuccess) return cuda_error(e, "bs_solve_bf16 launch");
   if (part) return part_correct(h->part[0], (int)h->N, X, BS_F32, layout, M, st);
   return BS_OK;
@@ -240,7 +271,9 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
   }
   const SweepPlan& p = part ? h->part[1].blk : h->plan[1];
   const int L = part ? h->part[1].L : 0, P = part ? h->part[1].P : 1;
-  if (dtype == BS_F64)
+  if (!part && fast_sweep(p, true, N, G, dtype, layout, M, st, &e))
+    ;
+  else if (dtype == BS_F64)
     e = sweep_f64(p, !part, N, G, G, layout, M, st, L, P);
   else
     e = sweep_f32(p, !part, N, G, G, layout, M, st, L, P);

@@ -55,3 +55,24 @@ def rel_l2(x, ref) -> float:
     x = np.asarray(x, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def sys_rel_err(x, ref, layout: str = "interleaved") -> float:
+    """Largest relative L2 error of one system, max_j |x_j - ref_j| / |ref_j|
+    over the systems j (columns of an interleaved (N, M) block, rows of a
+    strided (M, N) one); a system whose reference is zero must be exactly
+    zero."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if layout != "interleaved":
+        x, ref = x.T, ref.T
+    # scaled by each system's largest entry, so that norms of systems near
+    # the ends of the FP64 range neither overflow nor underflow
+    sc = np.max(np.abs(ref), axis=0)
+    sc = np.where(sc > 0, sc, 1.0)
+    num = np.linalg.norm((x - ref) / sc, axis=0)
+    den = np.linalg.norm(ref / sc, axis=0)
+    zero = den == 0
+    if np.any(num[zero] != 0):
+        return float("inf")
+    return float(np.max(num[~zero] / den[~zero])) if np.any(~zero) else 0.0

@@ -70,12 +70,19 @@ def test_set_option(L):
     assert L.bs_set_option(0, 0) == 0
     assert L.bs_set_option(99, 1) == 1
     assert L.bs_set_option(0, -5) == 1
-    # BS_OPT_CTA_THREADS takes 0, 32, 64 or 128 only
-    for v in (32, 64, 128, 0):
+    # BS_OPT_CTA_THREADS takes 0, 32 or a multiple of 64 up to 512
+    for v in (32, 64, 128, 192, 448, 512, 0):
         assert L.bs_set_option(7, v) == 0
-    for v in (1, 48, 256):
+    for v in (1, 48, 96, 576):
         assert L.bs_set_option(7, v) == 1
     assert L.bs_set_option(7, 0) == 0
+    # BS_OPT_F64_PAIRS 0..3, BS_OPT_WINDOW 0..2
+    for opt, good, bad in ((8, (0, 1, 2, 3), (4,)), (9, (0, 1, 2), (3,))):
+        for v in good:
+            assert L.bs_set_option(opt, v) == 0
+        for v in bad:
+            assert L.bs_set_option(opt, v) == 1
+        assert L.bs_set_option(opt, 0) == 0
 
 
 def test_option_constants_match_header():

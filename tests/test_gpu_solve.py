@@ -210,12 +210,13 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
     assert bs.device_status() == 0
 
 
-@pytest.mark.parametrize("cta", [32, 64, 128])
+@pytest.mark.parametrize("cta", [32, 64, 128, 256, 448])
 @pytest.mark.parametrize("width,N,M,dtype", [(5, 512, 4100, torch.float64), (3, 257, 1027, torch.float32),
                                               (3, 1000, 3000, torch.float64)])
 def test_cta_threads_option(bs, width, N, M, dtype, cta):
     """Every CTA size of BS_OPT_CTA_THREADS gives the oracle's solution (the
-    last shape is row-partitioned)."""
+    last shape is row-partitioned; sizes above 128 reach the windowed sweeps
+    only)."""
     bands = _bands(width, N, 11)
     Bh = _rhs(N, M, 11, "interleaved")
     if dtype == torch.float32:
