@@ -54,13 +54,13 @@ NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
     "band_grad_f64": {"bytes": 864354560 + 83456, "sha": "7ba2374f98630563"},
-    "f64_solve": {"bytes": 472626432 + 432110592, "sha": "39127f130240d1c5"},
-    "adjoint_f64": {"bytes": 471495424 + 429850368, "sha": "39127f130240d1c5"},
+    "f64_solve": {"bytes": None, "sha": ""},
+    "adjoint_f64": {"bytes": None, "sha": ""},
     "refine_solve": {"bytes": 356485376 + 437087488, "sha": "f8df3951d185c4cf"},
 }
 KERNEL_SOURCES = {
-    "f64_solve": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h", "solve_api.cu"],
-    "adjoint_f64": ["sweep_kernels.cuh", "sweep_f64.cu", "internal.h", "solve_api.cu"],
+    "f64_solve": ["sweep_df.cu", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
+    "adjoint_f64": ["sweep_df.cu", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
     "refine_solve": ["refine.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
     "band_grad_f64": ["band_grad.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
 }
@@ -306,55 +306,63 @@ def run_ours(args):
 
     peaks, peak_src = _peaks()
     hbm = float(peaks["hbm_gbs"])
-    fp64_fma = bs.measure_fp64_rate()
-    fp64_tflops = 2 * fp64_fma / 1e12
+    # FP64 FMA ceiling from unit counts and clocks: 2 FP64 FMA per clock per
+    # SM (1.25 TFLOP/s nominal at the 2.07 GHz maximum SM clock of 152 SMs);
+    # the device's rate measured by bs_measure_fp64_rate is reported beside it
+    dev = torch.cuda.get_device_properties(0)
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_fma_derived = 2.0 * dev.multi_processor_count * sm_max_mhz * 1e6
+    fp64_fma_live = [bs.measure_fp64_rate() for _ in range(5)]
+    fp64_fma_live = statistics.median(fp64_fma_live)
     nm = N * M
-    # algorithmic bytes and flops per launch (pentadiagonal)
+    # algorithmic bytes and FP64 work per launch (pentadiagonal); "arith" is
+    # what each path computes in
     paths = {
-        "f64_solve": {"bytes": 16 * nm, "flops": 9 * nm, "dp_instr": 5 * nm, "bound": "alu"},
-        "refine_solve": {"bytes": 12 * nm, "bound": "hbm"},
-        "adjoint_f64": {"bytes": 16 * nm, "flops": 9 * nm, "dp_instr": 5 * nm, "bound": "alu"},
-        "band_grad_f64": {"bytes": 16 * nm, "flops": 10 * nm, "dp_instr": 5 * nm, "bound": "alu"},
+        "f64_solve": {"bytes": 16 * nm, "arith": "fp32 pairs (FP64 data in and out)"},
+        "refine_solve": {"bytes": 12 * nm, "arith": "fp32 sweeps + error-free fp32 residuals, fp64 sum"},
+        "adjoint_f64": {"bytes": 16 * nm, "arith": "fp32 pairs (FP64 data in and out)"},
+        "band_grad_f64": {"bytes": 16 * nm, "arith": "fp64 (5 FMA per unknown)", "dp_fma": 5 * nm},
     }
     for n, p in paths.items():
         p["ncu_dram_bytes"] = ncu_traffic(n)
-        t = alone[n] * 1e-3
+        t_alone = alone[n] * 1e-3
+        t_step = per[n] * 1e-3
         p["ms"] = round(alone[n], 5)
         p["in_step_ms"] = round(per[n], 5)
-        p["unknowns_per_s"] = nm / t
-        p["hbm_gbs"] = p["bytes"] / t / 1e9
+        p["unknowns_per_s"] = nm / t_alone
+        p["hbm_gbs"] = p["bytes"] / t_alone / 1e9
         p["hbm_frac_of_measured"] = p["hbm_gbs"] / hbm
         p["hbm_frac_of_8tbs"] = p["hbm_gbs"] / NOMINAL_HBM_GBS
-        if "dp_instr" in p:
-            p["fp64_tflops"] = p["flops"] / t / 1e12
-            p["fp64_instr_frac_of_measured"] = p["dp_instr"] / t / fp64_fma
-    # the dominant kernel: the longest one timed alone
+        p["in_step_hbm_frac_of_measured"] = p["bytes"] / t_step / 1e9 / hbm
+        if "dp_fma" in p:
+            p["fp64_fma_per_s"] = p["dp_fma"] / t_alone
+            p["fp64_frac_of_derived_peak"] = p["fp64_fma_per_s"] / fp64_fma_derived
+            p["fp64_frac_of_live_rate"] = p["fp64_fma_per_s"] / fp64_fma_live
     paths["refine_solve"]["stream"] = "low priority, concurrent with the FP64 chain"
-    dom = max(paths, key=lambda n: alone[n])
+    # the dominant kernel: the longest share of the FP64 chain, which sets the
+    # step time (the mixed-precision solve runs beside it on a low-priority
+    # stream, its in-step duration stretched by that sharing)
+    dom = max(("f64_solve", "adjoint_f64", "band_grad_f64"), key=lambda n: per[n])
     dp = paths[dom]
-    if dp["bound"] == "alu":
-        # The FP64 pipe issues one instruction (MUL or FMA alike) per slot, so
-        # the ceiling is the FP64 instruction rate; the flop view (a MUL is
-        # one flop, an FMA two) is reported beside it.
-        t_dom = alone[dom] * 1e-3
-        ach = dp["dp_instr"] / t_dom / 1e9
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_fma / 1e9,
-                "unit": "G FP64 instructions/s", "frac": ach * 1e9 / fp64_fma, "traffic": ncu_traffic(dom),
-                "algorithmic_bytes": dp["bytes"],
-                "achieved_tflops": dp["fp64_tflops"], "peak_tflops": fp64_tflops,
-                "frac_of_flops": dp["fp64_tflops"] / fp64_tflops,
-                "timing": "the kernel timed alone (median of 20 launches, CUDA events on its stream) right "
-                          "after the timed region; inside the timed region the FP64 chain shares the SMs "
-                          "with the concurrent mixed-precision solve (paths[...].in_step_ms)",
-                "peak_source": "FP64 FMA instruction rate measured live by bs_measure_fp64_rate",
-                "algorithmic": {"f64_solve": "5 FP64 instructions per unknown (forward MUL + 2 FMA, backward "
-                                             "2 FMA) = 9 flop",
-                                "adjoint_f64": "5 FP64 instructions per unknown = 9 flop",
-                                "band_grad_f64": "5 FP64 FMA per unknown = 10 flop"}[dom]}
-    else:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": dp["hbm_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": dp["hbm_gbs"] / hbm, "traffic": ncu_traffic(dom), "algorithmic_bytes": dp["bytes"],
-                "peak_source": peak_src}
+    t_dom = per[dom] * 1e-3
+    ach = dp["bytes"] / t_dom / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": ncu_traffic(dom), "algorithmic_bytes": dp["bytes"],
+            "timing": "algorithmic bytes / mean in-step duration (CUDA events on the kernel's stream over the "
+                      "timed region)",
+            "peak_source": peak_src,
+            "alone": {"ms": dp["ms"], "frac": dp["hbm_frac_of_measured"]},
+            "arith": dp["arith"]}
+    if "dp_fma" in dp:
+        roof["fp64_pipe"] = {
+            "bound_by": "FP64 FMA pipe (5 FMA per unknown)",
+            "achieved_fma_per_s": dp["dp_fma"] / t_dom,
+            "peak_fma_per_s": fp64_fma_derived,
+            "peak_source": "derived: 2 FP64 FMA / clock / SM x SMs x max SM clock (1.25 TFLOP/s nominal)",
+            "frac": dp["dp_fma"] / t_dom / fp64_fma_derived,
+            "live_rate_fma_per_s": fp64_fma_live,
+            "live_rate_source": "self-measured: bs_measure_fp64_rate, median of 5 launches, clocks in 'clocks'",
+            "frac_of_live_rate": dp["dp_fma"] / t_dom / fp64_fma_live}
 
     # the plain FP32 solve (not part of the step): timed alone, error reported
     X32 = B0.float()
@@ -388,8 +396,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32-pair/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "width": 5, "layout": "interleaved",
+                   "arithmetic": "FP64 data; the FP64 solve and adjoint in FP32 pairs (48 significant bits, "
+                                 "error-free transformations), the band gradient in FP64, the mixed-precision "
+                                 "solve in FP32 with error-free residuals",
                    "l2": "no flush: FP64 operands (256 MiB) exceed L2; the FP32 input is re-read after >1 GiB of other traffic",
                    "parallelism": f"replicas x{world} (systems partitioned, no collective)"},
         "rel_residual": resid,
@@ -893,10 +904,17 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
     m0 = B.shape[1]
     X = oracle.solve(bands, B)
     XR = oracle.solve(bands, sample["B32"])
+    X32ref = oracle.solve(bands, sample["B32"])
     errs = {"f64_solve": float(np.linalg.norm(sample["X64"] - X) / np.linalg.norm(X)),
-            "f32_solve": float(np.linalg.norm(sample["X32"] - X) / np.linalg.norm(X)),
+            "f32_solve": float(np.linalg.norm(sample["X32"] - X32ref) / np.linalg.norm(X32ref)),
             "refine_solve": float(np.linalg.norm(sample["XR"] - XR) / np.linalg.norm(XR)),
-            "tolerance": {"f64_solve": 1e-12, "refine_solve": 1e-12, "f32_solve": 2e-5},
+            "f64_solve_max_system": max_system_err(sample["X64"], X),
+            "f32_solve_max_system": max_system_err(sample["X32"], X32ref),
+            "refine_solve_max_system": max_system_err(sample["XR"], XR),
+            "f32_solve_vs_fp64_input": float(np.linalg.norm(sample["X32"] - X) / np.linalg.norm(X)),
+            "tolerance": {"f64_solve": 1e-12, "refine_solve": 1e-12, "f32_solve": 2e-6},
+            "metric": "relative L2 over the sampled systems, and the largest relative L2 of one system "
+                      "(_max_system); the FP32 solve against the oracle's solve of the FP32-rounded input",
             "systems_checked": int(m0)}
     for name, smp in (other_samples or {}).items():
         if name == "adi":
@@ -912,8 +930,10 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
             ref = oracle.periodic_tri_solve_bands(b, Bs) if name.startswith("periodic") else oracle.solve(b, Bs)
             key = f"{name}_solve" if name.endswith("_f32") else f"{name}_f64_solve"
             errs[key] = float(np.linalg.norm(X64s - ref) / np.linalg.norm(ref))
+            errs[key + "_max_system"] = max_system_err(X64s, ref)
             if XRs is not None:
                 errs[f"{name}_refine_solve"] = float(np.linalg.norm(XRs - ref) / np.linalg.norm(ref))
+                errs[f"{name}_refine_solve_max_system"] = max_system_err(XRs, ref)
     # timing: the oracle step on a column block of the same batch, grown
     # until one step takes at least a quarter of target_s, then repeated to ~target_s
     Ball = sample["B_all"]
@@ -949,6 +969,15 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
           "value_1_core": 3 * N * m1 / dt1,
           "sample_1_core": f"one step on the first {m1} systems, one thread, {dt1:.1f} s"}
     return cb, errs
+
+
+def max_system_err(x, ref) -> float:
+    """Largest relative L2 error of one system (columns of an (N, m) block)."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.linalg.norm(ref, axis=0)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.linalg.norm(x - ref, axis=0) / den))
 
 
 def rel_residual(bands, B, X) -> float:

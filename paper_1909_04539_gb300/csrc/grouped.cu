@@ -1,10 +1,11 @@
 // Grouped persistent solve: one launch runs every request of a serving batch.
 // Each warp takes 32-system tiles from the work list (static stride over all
 // warps of the grid) and runs, lane by lane, exactly the per-system arithmetic
-// of the standalone solves (the same sweep and refinement helpers), so a
-// system's result does not depend on what else is in the batch.  The work
-// list (count included) is read from device memory, so one captured CUDA
-// graph (work-list copy + this launch) serves every batch.
+// of the standalone solves (the same sweep, pair-arithmetic and refinement
+// helpers), so a system's result does not depend on what else is in the
+// batch.  The work list (count included) is read from device memory, so one
+// captured CUDA graph (work-list copy + this launch) serves every batch.
+#include "df_sweep.cuh"
 #include "refine_math.cuh"
 #include "serve.h"
 
@@ -46,6 +47,48 @@ __device__ void lane_solve_f64(const GReq& q, int64_t j) {
         bwd_step<BW, false, double, 1>(cf, top - u, f[u], r1, r2);
         x[(int64_t)(top - u) * M] = f[u][0];
       }
+  }
+}
+
+// FP64 data in FP32 pairs: the row groups of the two-sweep kernel
+// (df_sweep.cuh), the forward values kept in place in B
+template <int BW>
+__device__ void lane_solve_pairs(const GReq& q, int64_t j) {
+  constexpr int U = 4;  // the block of the standalone kernel: the same switch rows
+  const DfRecs rc = df_recs_of(q.dfrec, q.N);
+  const Coefs<double> c64 = coefs_of<double>(q.c64, q.N);
+  double* x = static_cast<double*>(q.B) + j;
+  const int N = q.N;
+  const int64_t M = q.M;
+  DfState<1> st;
+  st.reset_values();
+  st.f64 = false;
+  st.rsw = N;
+#pragma unroll 1
+  for (int i0 = 0; i0 < N; i0 += U) {
+    const int n = (N - i0) < U ? (N - i0) : U;
+    double f[U][1];
+    uint2 w[U][1];
+#pragma unroll
+    for (int u = 0; u < U; u++) f[u][0] = (u < n) ? x[(int64_t)(i0 + u) * M] : 0.0;
+    df_fwd_group<BW, false, 1, U, false>(rc, c64, i0, n, f, w, st);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (u < n) *reinterpret_cast<uint2*>(x + (int64_t)(i0 + u) * M) = w[u][0];
+  }
+  st.reset_values();
+#pragma unroll 1
+  for (int top = N - 1; top >= 0; top -= U) {
+    const int n = (top + 1) < U ? (top + 1) : U;
+    uint2 w[U][1];
+    double xo[U][1];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      w[u][0] = (u < n) ? *reinterpret_cast<const uint2*>(x + (int64_t)(top - u) * M) : make_uint2(0u, 0u);
+    df_bwd_group<BW, false, 1, U, false>(rc, c64, top, n, w, xo, st);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (u < n) x[(int64_t)(top - u) * M] = xo[u][0];
   }
 }
 
@@ -105,7 +148,12 @@ __global__ void __launch_bounds__(kGroupThreads) k_grouped(const unsigned char* 
     const GReq q = reqs[tile.req];
     const int64_t j = (int64_t)tile.j0 + lane;
     if (j >= q.M) continue;
-    if (q.mode == SERVE_F64) {
+    if (q.mode == SERVE_F64 && q.pairs) {
+      if (q.width == 3)
+        lane_solve_pairs<1>(q, j);
+      else
+        lane_solve_pairs<2>(q, j);
+    } else if (q.mode == SERVE_F64) {
       if (q.width == 3)
         lane_solve_f64<1>(q, j);
       else

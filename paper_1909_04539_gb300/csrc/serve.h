@@ -13,10 +13,12 @@ struct GReq {
   const float* c32;   // primal sweep coefficients, FP32
   const float* lu_hi; // entries of the factors L, U: FP32 high parts (5 * N)
   const float* lu_lo; //   ... low parts
+  const float* dfrec; // primal coefficient pairs (SweepPlan::dfrec)
   void* B;            // SERVE_F64: double, solved in place; SERVE_F32_REFINE: float input
   double* X;          // SERVE_F32_REFINE: FP64 output (SERVE_F64: equals B)
   int64_t M;
-  int N, width, mode, pad;
+  int N, width, mode;
+  int pairs;          // SERVE_F64 in FP32 pairs (as bs_solve takes it for this handle)
 };
 
 // 32 consecutive systems of one request: one warp's work item.

@@ -184,6 +184,8 @@ cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<int64_t>& ids)
     g.c32 = h->plan[0].c32;
     g.lu_hi = h->lu_hi;
     g.lu_lo = h->lu_lo;
+    g.dfrec = h->plan[0].dfrec;
+    g.pairs = df_eligible(h->plan[0], BS_INTERLEAVED) ? 1 : 0;
     g.M = r.M;
     g.N = (int)h->N;
     g.width = h->width;

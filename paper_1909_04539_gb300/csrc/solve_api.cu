@@ -158,7 +158,10 @@ static bool fast_sweep(const SweepPlan& p, bool adjoint, int N, void* B, bs_dtyp
                                                        : sweep_df(p, adjoint, N, static_cast<double*>(B), M, st);
     return true;
   }
-  if (dtype == BS_F32 && win && p.win32 > 0 && p.rec32) {
+  // (the scalar-eps sweeps of a uniform pentadiagonal matrix, on request,
+  // run in the streaming kernels)
+  const bool uni = p.uniform && p.bw == 2 && option(BS_OPT_UNIFORM) == 2;
+  if (dtype == BS_F32 && win && !uni && p.win32 > 0 && p.rec32) {
     *e = sweep_win32<float>(p, adjoint, N, static_cast<const float*>(B), static_cast<float*>(B), M, st);
     return true;
   }
@@ -242,6 +245,7 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
   const SweepPlan& p = part ? h->part[0].blk : h->plan[0];
   cudaError_t e;
   if (!part && layout == BS_INTERLEAVED && !p.periodic && option(BS_OPT_WINDOW) != 1 && p.win32 > 0 && p.rec32 &&
+      !(p.uniform && p.bw == 2 && option(BS_OPT_UNIFORM) == 2) &&
       M % 2 == 0 && reinterpret_cast<uintptr_t>(B) % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 8 == 0)
     e = sweep_win32<__nv_bfloat16>(p, false, (int)h->N, static_cast<const __nv_bfloat16*>(B), X, M, st);
   else
