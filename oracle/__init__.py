@@ -47,6 +47,7 @@ def _load(path: str) -> ctypes.CDLL:
     L.oracle_band_grad_periodic.argtypes = [i64, dp, dp, i64, i64, i64, dp]
     L.oracle_band_grad_periodic.restype = None
     L.oracle_adi_halfstep.argtypes = [i64, i64, ctypes.c_double, dp, dp, i32]
+    L.oracle_adi_halfstep_bands.argtypes = [i64, i64, ctypes.c_double, i32, dp, dp, dp, i32, i32]
     L.oracle_cn_steps.argtypes = [i32, i64, dp, i32, dp, i64, i64, i64, i32]
     L.oracle_num_threads.argtypes = []
     L.oracle_set_threads.argtypes = [i32]
@@ -248,6 +249,25 @@ def adi_halfstep(u, r: float, implicit_axis: int) -> np.ndarray:
     ny, nx = u.shape
     out = np.zeros_like(u)
     st = lib().oracle_adi_halfstep(ny, nx, float(r), _p(u), _p(out), int(implicit_axis))
+    if st != 0:
+        raise OracleError(f"ADI solve failed (status {st})")
+    return out
+
+
+def adi_halfstep_bands(u, r: float, bands, implicit_axis: int, transpose: bool = False) -> np.ndarray:
+    """ADI half-step with the implicit operator S given by its bands (width 3
+    or 5): out = S^{-1} (I + r d2) u, or with transpose=True the transposed
+    map out = S^{-T} (I + r d2) u (the adjoint half-step); the explicit second
+    difference acts along the other axis, Dirichlet 0 outside the grid."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    b = _bands(bands)
+    ny, nx = u.shape
+    n_row = nx if implicit_axis == 0 else ny
+    if b.shape[1] != n_row:
+        raise ValueError("bands must have as many rows as the implicit axis")
+    out = np.zeros_like(u)
+    st = lib().oracle_adi_halfstep_bands(ny, nx, float(r), b.shape[0], _p(b), _p(u), _p(out), int(implicit_axis),
+                                         int(bool(transpose)))
     if st != 0:
         raise OracleError(f"ADI solve failed (status {st})")
     return out

@@ -438,3 +438,42 @@ int oracle_adi_halfstep(int64_t ny, int64_t nx, double r, const double* u,
   free(bands);
   return st;
 }
+
+/* ADI half-step with a general implicit operator and its transpose: the
+ * explicit operator E = I + r d2 (second difference, zero outside the
+ * grid) along the explicit axis, then a solve with the shared banded S
+ * (width 3 or 5, n_row x width bands of S, Sec. 3.1 / Sec. 4.1 layout) or,
+ * with transpose = 1, with S^T along the implicit axis.  transpose = 1 is
+ * the transpose of the map u -> S^{-1} E u: (S^{-1} E)^T = E^T S^{-T} = E
+ * S^{-T}, and E, acting on the other axis, commutes with S^{-T}.  Axes and
+ * storage as oracle_adi_halfstep. */
+int oracle_adi_halfstep_bands(int64_t ny, int64_t nx, double r, int width, const double* bands,
+                              const double* u, double* out, int implicit_axis, int transpose) {
+  int64_t n_sys = implicit_axis == 0 ? ny : nx;
+  int64_t n_row = implicit_axis == 0 ? nx : ny;
+  double* s = (double*)malloc(sizeof(double) * width * n_row);
+  int st;
+#pragma omp parallel for schedule(static)
+  for (int64_t y = 0; y < ny; y++)
+    for (int64_t x = 0; x < nx; x++) {
+      double c0 = u[y * nx + x], lo, hi;
+      if (implicit_axis == 0) {
+        lo = (y > 0) ? u[(y - 1) * nx + x] : 0.0;
+        hi = (y < ny - 1) ? u[(y + 1) * nx + x] : 0.0;
+      } else {
+        lo = (x > 0) ? u[y * nx + x - 1] : 0.0;
+        hi = (x < nx - 1) ? u[y * nx + x + 1] : 0.0;
+      }
+      out[y * nx + x] = c0 + r * (lo - 2.0 * c0 + hi);
+    }
+  if (transpose)
+    oracle_transpose_bands(width, n_row, bands, s);
+  else
+    for (int64_t q = 0; q < (int64_t)width * n_row; q++) s[q] = bands[q];
+  if (implicit_axis == 0)
+    st = oracle_solve(width, n_row, s, out, n_sys, 1, nx);
+  else
+    st = oracle_solve(width, n_row, s, out, n_sys, nx, 1);
+  free(s);
+  return st;
+}

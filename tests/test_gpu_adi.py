@@ -1,14 +1,18 @@
 """GPU parity of the fused ADI half-steps (explicit second difference across
 systems + shared tridiagonal solve) against the oracle, both axes, FP64
 (1e-12) and FP32 (2e-5), forward and adjoint; the autograd wrapper against
-finite differences."""
+finite differences.  The adjoint half-step S^{-T} (I + r d2) u is checked
+against the oracle's transposed half-step (oracle.adi_halfstep_bands) with a
+non-symmetric S, where it differs from the forward map, on grids whose lines
+run row-partitioned, and on the full 4096^2 grid, per line (the largest
+relative L2 error of one grid line)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
-from tests.dense import rel_l2, second_difference
+from tests.dense import rel_l2, second_difference, sys_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -103,3 +107,57 @@ def test_adi_autograd_finite_differences(bs):
     eps = 1e-6
     fd = (L(eps) - L(-eps)) / (2 * eps)
     assert abs(analytic - fd) < 1e-7 * (1 + abs(fd))
+
+
+def _line_err(out, ref, axis):
+    """Largest relative error of one system: grid rows for axis 0 (solved
+    along x), grid columns for axis 1."""
+    return sys_rel_err(out, ref, "strided" if axis == 0 else "interleaved")
+
+
+@pytest.mark.parametrize("partition", [2, 1])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
+def test_adi_nonsymmetric_operator_vs_oracle(bs, axis, adjoint, partition, dtype, tol):
+    """A non-symmetric diagonally dominant implicit operator S on a 400 x 1024
+    grid (lines of 1024 or 400 rows: row-partitioned with partition = 2),
+    forward S^{-1} E u and adjoint S^{-T} E u against the oracle per line."""
+    ny, nx, r = 400, 1024, 0.5
+    n = nx if axis == 0 else ny
+    rng = np.random.default_rng(n + axis)
+    bands = synth.random_tri_bands(n, rng)
+    u = rng.uniform(-1, 1, (ny, nx))
+    if dtype == torch.float32:
+        u = u.astype(np.float32).astype(np.float64)
+    f = bs.Factor(bands)
+    bs.set_option(bs.OPT_PARTITION, partition)
+    try:
+        out = bs.adi_halfstep(f, torch.tensor(u, dtype=dtype, device="cuda"), r, axis, adjoint=adjoint)
+        torch.cuda.synchronize()
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+    ref = oracle.adi_halfstep_bands(u, r, bands, axis, transpose=adjoint)
+    out = out.double().cpu().numpy()
+    assert rel_l2(out, ref) < tol
+    assert _line_err(out, ref, axis) < tol
+    if adjoint:  # really the transpose: the forward map differs
+        assert rel_l2(oracle.adi_halfstep_bands(u, r, bands, axis), ref) > 1e-3
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_adi_adjoint_full_grid_4096(bs, axis):
+    """The 4096 x 4096 heat-equation grid, r = 0.5: the adjoint half-step
+    (row-partitioned, as every 4096-line launch runs) in FP64 against the
+    oracle's transposed half-step on the whole grid, per line."""
+    n, r = 4096, 0.5
+    bands = synth.adi_bands(n, r)
+    f = bs.Factor(bands)
+    u = synth.adi_field(n, 1, "cuda")
+    adj = bs.adi_halfstep(f, u, r, axis, adjoint=True)
+    torch.cuda.synchronize()
+    ref = oracle.adi_halfstep_bands(u.cpu().numpy(), r, bands, axis, transpose=True)
+    out = adj.cpu().numpy()
+    assert rel_l2(out, ref) < 1e-12
+    assert _line_err(out, ref, axis) < 1e-12
+

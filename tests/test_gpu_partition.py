@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import synth
-from tests.dense import rel_l2
+from tests.dense import rel_l2, sys_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -127,8 +127,8 @@ def test_partitioned_adjoint_and_band_grad(bs, width, layout, dtype, tol):
 def test_partitioned_adi(bs, axis, adjoint, dtype, tol):
     """ADI half-steps on a 1024 x 1024 grid (the implicit axis splits into 4
     blocks of 256 rows), forward and adjoint, against the oracle's half-step
-    (the ADI operator is symmetric, so the adjoint half-step equals the
-    oracle's half-step applied in the transposed order of operators)."""
+    and its transpose (oracle.adi_halfstep_bands), and partitioned against
+    unpartitioned."""
     n, r = 1024, 0.5
     u = synth.adi_field(n, 5, "cpu", torch.float64).numpy()
     if dtype == torch.float32:
@@ -142,9 +142,9 @@ def test_partitioned_adi(bs, axis, adjoint, dtype, tol):
             outs[mode] = bs.adi_halfstep(f, ut, r, axis, adjoint=adjoint).double().cpu().numpy()
         finally:
             bs.set_option(bs.OPT_PARTITION, 0)
-    if not adjoint:
-        ref = oracle.adi_halfstep(u, r, axis)
-        assert rel_l2(outs[2], ref) < tol
+    ref = oracle.adi_halfstep_bands(u, r, synth.adi_bands(n, r), axis, transpose=adjoint)
+    assert rel_l2(outs[2], ref) < tol
+    assert sys_rel_err(outs[2], ref, "strided" if axis == 0 else "interleaved") < tol
     assert rel_l2(outs[2], outs[1]) < (1e-13 if dtype == torch.float64 else 1e-5)
 
 

@@ -297,6 +297,33 @@ def pin_adi(ny, nx, r, seed=10):
     assert rel_l2(oracle.adi_halfstep(u, r, 1), ref1) < 1e-14
 
 
+def pin_adi_bands(ny, nx, r, width, seed=11):
+    """ADI half-steps with a non-symmetric implicit operator S and their
+    transposes against dense Kronecker operators: S^{-1} E u and S^{-T} E u
+    (E = I + r d2 along the other axis), and the adjoint identity
+    <v, F(u)> = <F^T(v), u> between the forward and transposed half-steps."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1, 1, (ny, nx))
+    v = rng.uniform(-1, 1, (ny, nx))
+    Dx, Dy = second_difference(nx), second_difference(ny)
+    Ix, Iy = np.eye(nx), np.eye(ny)
+    for axis in (0, 1):
+        n = nx if axis == 0 else ny
+        bands = synth.random_tri_bands(n, rng) if width == 3 else synth.random_penta_bands(n, rng)
+        S = dense_from_bands(bands)
+        if axis == 0:
+            Sk, Ek = np.kron(Iy, S), np.kron(np.eye(ny) + r * Dy, Ix)
+        else:
+            Sk, Ek = np.kron(S, Ix), np.kron(Iy, np.eye(nx) + r * Dx)
+        fwd = oracle.adi_halfstep_bands(u, r, bands, axis)
+        adj = oracle.adi_halfstep_bands(v, r, bands, axis, transpose=True)
+        assert rel_l2(fwd.ravel(), np.linalg.solve(Sk, Ek @ u.ravel())) < 1e-13
+        assert rel_l2(adj.ravel(), np.linalg.solve(Sk.T, Ek @ v.ravel())) < 1e-13
+        assert rel_l2(adj.ravel(), (np.linalg.solve(Sk, Ek)).T @ v.ravel()) < 1e-12
+        lhs, rhs = float(np.sum(v * fwd)), float(np.sum(adj * u))
+        assert abs(lhs - rhs) < 1e-13 * (abs(lhs) + 1)
+
+
 def all_pins():
     """Every pin with a set of arguments, as (name, thunk) pairs."""
     out = []
@@ -330,6 +357,8 @@ def all_pins():
         ("periodic_band_grad", lambda: pin_periodic_band_grad()),
         ("periodic_band_grad_min", lambda: pin_periodic_band_grad(3, 2, 18)),
         ("adi_rect", lambda: pin_adi(5, 7, 0.5)),
+        ("adi_bands_tri", lambda: pin_adi_bands(6, 9, 0.5, 3)),
+        ("adi_bands_penta", lambda: pin_adi_bands(7, 8, 0.3, 5)),
         ("cn_tri", lambda: pin_cn_tri(40, 0.7, 5)),
         ("cn_penta", lambda: pin_cn_penta(30, 0.3, 4)),
         ("cn_periodic", lambda: pin_cn_periodic(24, 0.9, 6)),

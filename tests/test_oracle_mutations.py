@@ -41,6 +41,10 @@ MUTATIONS = [
     ("adi_explicit_sign", "out[y * nx + x] = c0 + r * (lo - 2.0 * c0 + hi);",
      "out[y * nx + x] = c0 - r * (lo - 2.0 * c0 + hi);", 0),
     ("adi_lhs_diag", "bands[n_row + i] = 1.0 + 2.0 * r;", "bands[n_row + i] = 1.0 + r;", 0),
+    ("adi_bands_no_transpose", "if (transpose)\n    oracle_transpose_bands(width, n_row, bands, s);",
+     "if (0)\n    oracle_transpose_bands(width, n_row, bands, s);", 0),
+    ("adi_bands_explicit_axis", "out[y * nx + x] = c0 + r * (lo - 2.0 * c0 + hi);",
+     "out[y * nx + x] = c0 + r * (lo - 2.0 * c0 - hi);", 1),
 ]
 
 
