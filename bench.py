@@ -699,6 +699,39 @@ def run_other_configs(bs, st, hbm):
     out["uniform_penta_N512_M65536"] = uni
     del B32, X32, B16, fu
 
+    # mixed-precision solve by number of refinement steps and storage type:
+    # the clamped penta batch (N = 512, M = 65536) in FP32 and BF16 storage,
+    # and stiff hyperdiffusion I + 4000 D4 (N = 512, M = 4096, condition
+    # number ~6e4), timed per call; sampled systems for the oracle comparison
+    rk = {}
+    Nr, Mr = 512, 65536
+    br = synth.clamped_hyperdiffusion_bands(Nr, 0.1)
+    fr = bs.Factor(br)
+    Bn = synth.normal_rhs(Nr, Mr, 9, "cuda")
+    colsr = np.random.default_rng(14).choice(Mr, 256, replace=False)
+    for sname, Bs in (("f32", Bn.float()), ("bf16", Bn.bfloat16())):
+        XR = torch.empty((Nr, Mr), dtype=torch.float64, device="cuda")
+        outs = {}
+        for k in (0, 1, 2, 3):
+            rk[f"penta_clamped_{sname}_k{k}_ms"] = time_alone(lambda: bs.solve_refine(fr, Bs, XR, refine_steps=k), st,
+                                                              reps=10)
+            bs.solve_refine(fr, Bs, XR, refine_steps=k)
+            torch.cuda.synchronize()
+            outs[k] = XR[:, colsr].cpu().numpy()
+        samples[f"refine_steps_{sname}"] = (br, Bs[:, colsr].double().cpu().numpy(), outs)
+        del XR
+    del Bn
+    ss = 4000.0
+    bstiff = synth.toeplitz_bands(512, (ss, -4 * ss, 1 + 6 * ss, -4 * ss, ss))
+    fs = bs.Factor(bstiff)
+    Bst = synth.uniform_rhs(512, 4096, 15, "cuda").float()
+    outs = {}
+    for k in (0, 1, 2, 3):
+        outs[k] = bs.solve_refine(fs, Bst, refine_steps=k, mode=bs.REFINE_FACTOR).cpu().numpy()
+    samples["refine_steps_stiff_f32"] = (bstiff, Bst.double().cpu().numpy(), outs)
+    out["refine_steps"] = rk
+    del fr, fs
+
     # the paper's benchmark problems as Crank-Nicolson time stepping (explicit
     # side fused into the sweep): periodic diffusion (-s, 1 + 2s, -s), N = 1024,
     # and hyperdiffusion (s, -4s, 1 + 6s, -4s, s), N = 512; M = 65536, 10 steps
@@ -921,6 +954,12 @@ def cpu_baseline(args, bands, sample, other_samples=None, target_s: float = 12.0
             r, u, full, rows = smp
             ref = oracle.adi_halfstep(oracle.adi_halfstep(u, r, 0), r, 1)
             errs["adi_4096_full_step_f64"] = float(np.linalg.norm(full - ref) / np.linalg.norm(ref))
+        elif name.startswith("refine_steps_"):
+            b, Bs, outs = smp
+            ref = oracle.solve(b, Bs)
+            for k, Xk in outs.items():
+                errs[f"{name}_k{k}_max_system"] = max_system_err(Xk, ref)
+                errs[f"{name}_k{k}"] = float(np.linalg.norm(Xk - ref) / np.linalg.norm(ref))
         elif name.startswith("cn_"):
             b, per, C0, C2 = smp
             ref = oracle.cn_steps(b, C0, 2, periodic=per)

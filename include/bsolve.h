@@ -123,32 +123,40 @@ bs_status bs_solve_bf16(bs_handle h, const void* B, float* X, bs_layout layout, 
                         bs_stream stream);
 
 /* Mixed-precision solve (FP32 storage, FP64 result): X = A^{-1} B with B
- * stored in FP32 (float[N*M], device, read only) and X written in FP64
- * (double[N*M], device).  The sweeps run in FP32; with refine_steps = 1 one
- * step of iterative refinement follows, with residuals evaluated to FP64
- * accuracy in FP32 arithmetic (FP64 coefficients split into FP32 pairs,
- * error-free products and sums) and the correction added in FP64:
- *   mode BS_REFINE_FACTOR (default, two passes per system): each triangular
- *     factor of A = L U is solved in FP32 and corrected once with its own
- *     residual -- B - L w on the way up, y - U x on the way down;
- *   mode BS_REFINE_SYSTEM (three passes): the residual of the whole system,
- *     r = B - A X0, of the FP32 solution X0 drives one correction solve
- *     through the reversed elimination A = U' L' (factorised once with the
- *     handle) so that its first sweep follows the backward sweep of X0.
+ * stored in FP32 (float[N*M], device, read only) or BF16 (b_dtype BS_BF16,
+ * bf16[N*M], widened exactly to FP32) and X written in FP64 (double[N*M],
+ * device).  The sweeps run in FP32; refinement corrects them with residuals
+ * evaluated to FP64 accuracy and adds the corrections in FP64:
+ *   mode BS_REFINE_FACTOR (default, two passes per system, one kernel): the
+ *     first step refines each triangular factor of A = L U once, solved in
+ *     FP32 with its own residual evaluated to FP64 accuracy in FP32
+ *     arithmetic (FP64 coefficients split into FP32 pairs, error-free
+ *     products and sums) -- B - L w on the way up, y - U x on the way down;
+ *   mode BS_REFINE_SYSTEM (three passes, one kernel): the first step refines
+ *     the whole system, r = B - A X0 of the FP32 solution X0 driving one
+ *     correction solve through the reversed elimination A = U' L'
+ *     (factorised once with the handle) so that its first sweep follows the
+ *     backward sweep of X0;
  *   mode BS_REFINE_AUTO: BS_REFINE_FACTOR, except for batches with fewer
  *     than 256 systems per SM, whose FP32 passes are bound by their chains
- *     of dependent rows: those are
- *     solved as an FP64 solve of B widened exactly to FP64 in X (as bs_solve
- *     does it, row-partitioned or two-ended), which is faster there and
- *     exact to FP64 rounding (not in the paper).
- * Both refinement modes reach ~1e-15 relative error on well-conditioned
- * bands.  refine_steps = 0 returns the FP32 solution widened to FP64 (mode
- * ignored).
- * X doubles as the workspace of the passes.  Only BS_INTERLEAVED and b_dtype
- * BS_F32 are implemented (BS_EUNSUPPORTED otherwise); refine_steps > 1 is
- * BS_EUNSUPPORTED.  B and X must not overlap.  BS_REFINE_SYSTEM returns
- * BS_ESINGULAR if the reversed elimination of A met a bad pivot when the
- * handle was built (the other solves still work then).
+ *     of dependent rows: those are solved as an FP64 solve of B widened
+ *     exactly to FP64 in X (as bs_solve does it, row-partitioned or
+ *     two-ended), which is faster there and exact to FP64 rounding (not in
+ *     the paper).
+ * refine_steps = 0 returns the FP32 solution widened to FP64 (mode ignored),
+ * 1 the first step above (~1e-15 relative error on well-conditioned bands);
+ * each further step (up to 8) refines the whole system once more: r = B - A X
+ * in FP64 rounded to FP32, A d = r by the FP32 sweeps (as bs_solve does it),
+ * X += d -- each step multiplies the error by about kappa(A) 2^-24, for bands
+ * too ill-conditioned for one step (stiff Crank-Nicolson hyperdiffusion
+ * I + s D4 with large s, Sec. 4.2).  Further steps and the BF16 input take
+ * stream-ordered scratch: N*M floats.
+ * Layout BS_INTERLEAVED or BS_STRIDED (B[j*N + i] in, X[j*N + i] out; the
+ * kernels run interleaved: B is transposed into scratch and X out of
+ * N*M doubles of scratch).  X doubles as the workspace of the passes.  B and
+ * X must not overlap.  BS_REFINE_SYSTEM returns BS_ESINGULAR if the reversed
+ * elimination of A met a bad pivot when the handle was built (the other
+ * solves still work then).
  * Not in the paper: the paper's solvers work in a single precision. */
 typedef enum { BS_REFINE_FACTOR = 0, BS_REFINE_SYSTEM = 1, BS_REFINE_AUTO = 2 } bs_refine_mode;
 bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,

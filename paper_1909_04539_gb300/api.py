@@ -157,15 +157,16 @@ REFINE_AUTO = 2
 
 def solve_refine(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, refine_steps: int = 1,
                  layout: str = "interleaved", stream=None, mode: int = REFINE_AUTO) -> torch.Tensor:
-    """FP32-stored B (float32), FP32 sweeps plus ``refine_steps`` (0 or 1)
-    steps of iterative refinement with FP64-accurate residuals (``mode``:
-    REFINE_FACTOR per triangular factor, two passes; REFINE_SYSTEM on
-    r = B - A X0, three passes; REFINE_AUTO as REFINE_FACTOR, but small
-    batches solved in FP64 from the widened input); returns the FP64
-    solution X (also used as workspace)."""
+    """FP32-stored (float32) or BF16-stored (bfloat16) B, FP32 sweeps plus
+    ``refine_steps`` (0..8) steps of iterative refinement with FP64-accurate
+    residuals (``mode`` for the first step: REFINE_FACTOR per triangular
+    factor, two passes; REFINE_SYSTEM on r = B - A X0, three passes;
+    REFINE_AUTO as REFINE_FACTOR, but small batches solved in FP64 from the
+    widened input; further steps on the whole system); returns the FP64
+    solution X (also used as workspace), in ``layout``."""
     M = _batch(f, B, layout, "B")
-    if B.dtype != torch.float32:
-        raise ValueError("B must be float32")
+    if B.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("B must be float32 or bfloat16")
     if X is None:
         X = torch.empty(B.shape, dtype=torch.float64, device=B.device)
     _batch(f, X, layout, "X")

@@ -26,6 +26,8 @@
 // error of a few FP32 ulps of r itself plus ~2^-48 |A||X0| -- what one step
 // of refinement needs to bring the FP32 solution to ~1e-15 relative error for
 // well-conditioned bands.
+#include <algorithm>
+
 #include "refine_math.cuh"
 
 namespace bs {
@@ -486,7 +488,7 @@ static bool refine_direct(int64_t M) { return M < (int64_t)device_info().sms * 2
 
 bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int64_t M, int steps, int mode,
                         cudaStream_t st) {
-  if (b_t != BS_F32) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: B must be BS_F32");
+  if (b_t != BS_F32) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: B must be BS_F32 here");
   if (mode == BS_REFINE_AUTO) {
     if (steps == 1 && refine_direct(M)) {
       const int64_t n = h->N * M;
@@ -511,6 +513,143 @@ bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int
   return BS_OK;
 }
 
+// ------------------------------------------------------------------------
+// More refinement steps, BF16 input, strided layout.
+//
+// Steps beyond the first run on the whole system: r = B - A X in FP64 (the
+// FP64 bands, FP64 FMAs), rounded to FP32; A d = r solved by the FP32 sweeps
+// (bs_solve, in place on r); X += d.  Each step multiplies the error by about
+// kappa(A) 2^-24, so ill-conditioned bands that one step leaves short of FP64
+// accuracy get there in a few (the FP64 residual bounds what is reachable:
+// about kappa(A) 2^-53).
+
+// r = fl32(B - A X), interleaved, FP64 arithmetic
+template <int W>
+__global__ void __launch_bounds__(256) k_resid32(const double* __restrict__ bands, int N, const float* __restrict__ B,
+                                                 const double* __restrict__ X, int64_t M, float* __restrict__ r) {
+  constexpr int H = W / 2;
+  const int64_t total = (int64_t)N * M;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / M);
+    double s = widen_exact(B[q]);
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+      const int col = i + k - H;
+      if (col >= 0 && col < N) s = fma(-bands[(int64_t)k * N + i], X[q + (int64_t)(k - H) * M], s);
+    }
+    r[q] = (float)s;
+  }
+}
+
+// X += d (d exact in FP64)
+__global__ void __launch_bounds__(256) k_add_widened(double* __restrict__ X, const float* __restrict__ d, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    X[q] += widen_exact(d[q]);
+}
+
+// out (interleaved N x M, float) = in, from an interleaved or a strided
+// (M x N) batch of float or bf16 (bf16 widened exactly); 32 x 32 tiles
+// through shared memory for the strided case
+template <typename Sin>
+__global__ void __launch_bounds__(256) k_to_interleaved_f32(const Sin* __restrict__ in, int N, int64_t M, int strided,
+                                                            float* __restrict__ out) {
+  __shared__ float tile[32][33];
+  auto val = [](Sin v) -> float {
+    if constexpr (std::is_same<Sin, float>::value)
+      return v;
+    else
+      return __bfloat162float(v);
+  };
+  if (!strided) {
+    const int64_t total = (int64_t)N * M;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+      out[q] = val(in[q]);
+    return;
+  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int64_t tiles_i = (N + 31) / 32, tiles_j = (M + 31) / 32;
+  for (int64_t t = blockIdx.x; t < tiles_i * tiles_j; t += gridDim.x) {
+    const int64_t i0 = (t % tiles_i) * 32, j0 = (t / tiles_i) * 32;
+    for (int yy = ty; yy < 32; yy += 8) {  // read rows j0 + yy (system), columns i0 + tx
+      const int64_t j = j0 + yy, i = i0 + tx;
+      if (j < M && i < N) tile[yy][tx] = val(in[j * N + i]);
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {  // write rows i0 + yy, columns j0 + tx
+      const int64_t i = i0 + yy, j = j0 + tx;
+      if (i < N && j < M) out[i * M + j] = tile[tx][yy];
+    }
+    __syncthreads();
+  }
+}
+
+// X (strided, M x N) = Xi (interleaved, N x M)
+__global__ void __launch_bounds__(256) k_to_strided_f64(const double* __restrict__ Xi, int N, int64_t M,
+                                                        double* __restrict__ X) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t tiles_i = (N + 31) / 32, tiles_j = (M + 31) / 32;
+  for (int64_t t = blockIdx.x; t < tiles_i * tiles_j; t += gridDim.x) {
+    const int64_t i0 = (t % tiles_i) * 32, j0 = (t / tiles_i) * 32;
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t i = i0 + yy, j = j0 + tx;
+      if (i < N && j < M) tile[yy][tx] = Xi[i * M + j];
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t j = j0 + yy, i = i0 + tx;
+      if (j < M && i < N) X[j * N + i] = tile[tx][yy];
+    }
+    __syncthreads();
+  }
+}
+
+static int elementwise_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)device_info().sms * 8;
+  return (int)(g > cap ? cap : (g < 1 ? 1 : g));
+}
+
+// Steps 2 .. steps on an interleaved FP32 B and FP64 X (scratch: N*M floats).
+static bs_status refine_more(bs_handle h, const float* B, double* X, int64_t M, int steps, cudaStream_t st) {
+  if (steps < 2) return BS_OK;
+  const int N = (int)h->N;
+  const int64_t n = (int64_t)N * M;
+  float* r = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&r), (size_t)n * sizeof(float), st);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(BS_ENOMEM, "bs_solve_refine: scratch")
+                                                               : cuda_error(e, "bs_solve_refine scratch");
+  bs_status s = BS_OK;
+  for (int k = 2; k <= steps && s == BS_OK; k++) {
+    if (h->width == 3)
+      k_resid32<3><<<elementwise_grid(n), 256, 0, st>>>(h->bands64, N, B, X, M, r);
+    else
+      k_resid32<5><<<elementwise_grid(n), 256, 0, st>>>(h->bands64, N, B, X, M, r);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      s = cuda_error(e, "bs_solve_refine residual");
+      break;
+    }
+    s = bs_solve(h, r, BS_F32, BS_INTERLEAVED, M, reinterpret_cast<bs_stream>(st));
+    if (s != BS_OK) break;
+    k_add_widened<<<elementwise_grid(n), 256, 0, st>>>(X, r, n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_error(e, "bs_solve_refine update");
+  }
+  const cudaError_t e2 = cudaFreeAsync(r, st);
+  if (s == BS_OK && e2 != cudaSuccess) s = cuda_error(e2, "bs_solve_refine scratch free");
+  return s;
+}
+
+// Interleaved FP32 B: the one-step kernels, then the further steps.
+static bs_status refine_interleaved(bs_handle h, const float* B, double* X, int64_t M, int steps, int mode,
+                                    cudaStream_t st) {
+  const bs_status s = launch_refine(h, B, BS_F32, X, M, steps > 1 ? 1 : steps, mode, st);
+  if (s != BS_OK) return s;
+  return refine_more(h, B, X, M, steps, st);
+}
+
 }  // namespace bs
 
 extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtype, double* X, bs_layout layout,
@@ -520,22 +659,58 @@ extern "C" bs_status bs_solve_refine(bs_handle h, const void* B, bs_dtype b_dtyp
   if (h->periodic) return set_error(BS_EUNSUPPORTED, "bs_solve_refine: not available for a periodic handle");
   if (!B || !X) return set_error(BS_EINVAL, "bs_solve_refine: null data pointer");
   if (M < 1) return set_error(BS_EINVAL, "bs_solve_refine: M must be >= 1");
-  if (layout != BS_INTERLEAVED)
-    return set_error(BS_EUNSUPPORTED, "bs_solve_refine: only the interleaved layout is implemented");
-  if (refine_steps < 0 || refine_steps > 1)
-    return set_error(BS_EUNSUPPORTED, "bs_solve_refine: refine_steps must be 0 or 1");
+  if (layout != BS_INTERLEAVED && layout != BS_STRIDED) return set_error(BS_EINVAL, "bs_solve_refine: bad layout");
+  if (b_dtype != BS_F32 && b_dtype != BS_BF16)
+    return set_error(BS_EINVAL, "bs_solve_refine: B must be BS_F32 or BS_BF16");
+  if (refine_steps < 0 || refine_steps > 8) return set_error(BS_EINVAL, "bs_solve_refine: refine_steps must be 0..8");
+  if (M > INT64_MAX / 16 / h->N) return set_error(BS_EINVAL, "bs_solve_refine: N*M too large");
   if (mode != BS_REFINE_FACTOR && mode != BS_REFINE_SYSTEM && mode != BS_REFINE_AUTO)
     return set_error(BS_EINVAL, "bs_solve_refine: bad refinement mode");
   if (refine_steps > 0 && mode == BS_REFINE_SYSTEM && !h->has_ul)
     return set_error(BS_ESINGULAR, "bs_solve_refine: the reversed elimination of this matrix met a bad pivot");
-  if (reinterpret_cast<uintptr_t>(X) % 8 || reinterpret_cast<uintptr_t>(B) % 4)
+  const size_t es = b_dtype == BS_BF16 ? 2 : 4;
+  if (reinterpret_cast<uintptr_t>(X) % 8 || reinterpret_cast<uintptr_t>(B) % es)
     return set_error(BS_EINVAL, "bs_solve_refine: misaligned pointer");
   const char* b0 = static_cast<const char*>(B);
   const char* x0 = reinterpret_cast<const char*>(X);
   const size_t nm = (size_t)h->N * (size_t)M;
-  if (b0 < x0 + nm * 8 && x0 < b0 + nm * 4) return set_error(BS_EINVAL, "bs_solve_refine: B and X overlap");
+  if (b0 < x0 + nm * 8 && x0 < b0 + nm * es) return set_error(BS_EINVAL, "bs_solve_refine: B and X overlap");
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != h->device) return set_error(BS_EINVAL, "bs_solve_refine: handle belongs to another device");
-  return launch_refine(h, B, b_dtype, X, M, refine_steps, (int)mode, reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (b_dtype == BS_F32 && layout == BS_INTERLEAVED)
+    return refine_interleaved(h, static_cast<const float*>(B), X, M, refine_steps, (int)mode, st);
+  // BF16 input and the strided layout: an interleaved FP32 copy of B (bf16
+  // widened exactly) and, for the strided layout, an interleaved FP64
+  // result, in stream-ordered scratch
+  const bool strided = layout == BS_STRIDED;
+  float* Bi = nullptr;
+  double* Xi = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Bi), nm * sizeof(float), st);
+  if (e == cudaSuccess && strided) e = cudaMallocAsync(reinterpret_cast<void**>(&Xi), nm * sizeof(double), st);
+  if (e != cudaSuccess) {
+    if (Bi) cudaFreeAsync(Bi, st);
+    return e == cudaErrorMemoryAllocation ? set_error(BS_ENOMEM, "bs_solve_refine: scratch")
+                                          : cuda_error(e, "bs_solve_refine scratch");
+  }
+  const int64_t tiles = ((int64_t)h->N + 31) / 32 * ((M + 31) / 32);
+  const int g = strided ? (int)std::min<int64_t>(tiles, (int64_t)device_info().sms * 8) : elementwise_grid((int64_t)nm);
+  if (b_dtype == BS_BF16)
+    k_to_interleaved_f32<__nv_bfloat16><<<g, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), (int)h->N, M,
+                                                           strided, Bi);
+  else
+    k_to_interleaved_f32<float><<<g, 256, 0, st>>>(static_cast<const float*>(B), (int)h->N, M, strided, Bi);
+  bs_status s = BS_OK;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) s = cuda_error(e, "bs_solve_refine input copy");
+  if (s == BS_OK) s = refine_interleaved(h, Bi, strided ? Xi : X, M, refine_steps, (int)mode, st);
+  if (s == BS_OK && strided) {
+    k_to_strided_f64<<<(int)std::min<int64_t>(tiles, (int64_t)device_info().sms * 8), 256, 0, st>>>(Xi, (int)h->N, M, X);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_error(e, "bs_solve_refine output copy");
+  }
+  cudaFreeAsync(Bi, st);
+  if (Xi) cudaFreeAsync(Xi, st);
+  return s;
 }

@@ -85,7 +85,9 @@ def test_refine_rejects_bad_arguments(bs):
     f = bs.Factor(_bands(3, 16, 0))
     B = torch.zeros(16, 8, dtype=torch.float32, device="cuda")
     with pytest.raises(bs.BsolveError):
-        bs.solve_refine(f, B, refine_steps=2)
+        bs.solve_refine(f, B, refine_steps=9)
+    with pytest.raises(bs.BsolveError):
+        bs.solve_refine(f, B, refine_steps=-1)
     with pytest.raises(bs.BsolveError):
         bs.solve_refine(f, B, mode=7)
     with pytest.raises(ValueError):
