@@ -505,10 +505,17 @@ def run_serving(bs, n_lhs=256, n_burst=192, n_poisson=10000, load=0.7, sweep=(0.
             srv.release(i)
         lat_ms = np.array(lat) * 1e3
         unk = sum(specs[r.lhs_id].N * r.M for r in stream)
+        # size classes of the server (device bytes up to 16 MiB: "small")
+        nbytes = np.array([specs[r.lhs_id].N * r.M * (12 if r.refine else 8) for r in stream])
+        classes = {}
+        for cname, sel in (("small", nbytes <= (16 << 20)), ("large", nbytes > (16 << 20))):
+            if sel.any():
+                classes[cname] = {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat_ms[sel], 50)),
+                                  "p99_ms": float(np.percentile(lat_ms[sel], 99))}
         return {"offered_requests_per_s": rate, "load_of_saturation": ld, "requests": len(stream),
                 "achieved_requests_per_s": len(stream) / t_stream, "unknowns_per_s": unk / t_stream,
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                "mean_ms": float(lat_ms.mean())}
+                "mean_ms": float(lat_ms.mean()), "by_size": classes}
 
     # sustained: Poisson at load * saturation
     pos = n_burst

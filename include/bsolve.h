@@ -91,7 +91,9 @@ bs_status bs_factor(const double* bands, int width, int64_t N, bs_handle* out);
 bs_status bs_factor_periodic(const double* bands, int64_t N, bs_handle* out);
 
 /* Release a handle's device memory.  The caller must ensure no solve using it
- * is still running (synchronise its streams first).  NULL is a no-op. */
+ * is still running (synchronise its streams first).  A handle named by server
+ * requests that have not finished (bs_server_submit) is not released:
+ * BS_EINVAL, and the handle stays valid.  NULL is a no-op. */
 bs_status bs_destroy(bs_handle h);
 
 /* Width, N and device bytes held by a handle (any pointer may be NULL). */
@@ -192,7 +194,8 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  * about 50000 (width 5) or 85000 (width 3) is rejected with BS_EINVAL and a
  * message naming the size -- use bs_band_grad there.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture (a first
+ * call on a stream that is being captured returns BS_EINVAL).  All calls
  * share the one array and it keeps the last call's contents (every partial is
  * written before it is read, so nothing needs clearing): calls that can
  * overlap on the GPU -- on different streams, or from different host threads
@@ -284,7 +287,11 @@ bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* ou
  * Requests still queued are dropped. */
 bs_status bs_server_destroy(bs_server s);
 /* Queues one request; *request_id identifies it.  BS_ENOMEM if the request
- * alone exceeds the budget (it could never be admitted); 1 <= M <= 524288. */
+ * alone exceeds the budget (it could never be admitted); 1 <= M <= 524288.
+ * host_B and host_X must be page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister, torch's pin_memory): copies from pageable memory would
+ * block the worker; other memory is rejected with BS_EINVAL.  The handle is
+ * pinned until the request has finished: bs_destroy refuses it meanwhile. */
 bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* host_X, int mode, int64_t M,
                            int64_t* request_id);
 /* Non-blocking state query; *latency_s is -1 until the request has finished. */

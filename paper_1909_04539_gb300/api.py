@@ -100,9 +100,11 @@ class Factor:
         return int(n.value)
 
     def close(self) -> None:
+        """Release the device copy (bs_destroy); raises and keeps the handle
+        while server requests that name it have not finished."""
         if getattr(self, "_h", None) is not None:
-            h, self._h = self._h, None
-            lib().bs_destroy(h)
+            check(lib().bs_destroy(self._h), "bs_destroy")
+            self._h = None
 
     def __del__(self):
         try:

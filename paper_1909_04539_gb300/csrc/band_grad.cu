@@ -20,6 +20,7 @@
 // FMAs (the kernel is bound by the FP64 pipe on GB300), 16 bytes of
 // compulsory reads (GB and X; the X halo of 2h rows per row block comes
 // from L2).
+#include <climits>
 #include <mutex>
 #include <string>
 
@@ -290,8 +291,9 @@ constexpr size_t kNoAllocScratchDoubles = size_t(1) << 18;
 static __device__ __align__(256) double g_band_grad_scratch[kNoAllocScratchDoubles];
 
 // Device address of g_band_grad_scratch on the current device, looked up on
-// the first call for that device (the device must be current).
-static cudaError_t noalloc_scratch(double** out) {
+// the first call for that device (the device must be current).  *first: the
+// lookup is still to be done (the caller refuses that during stream capture).
+static cudaError_t noalloc_scratch(double** out, cudaStream_t st, bool* capturing) {
   static std::mutex mu;
   static double* ptr[64] = {nullptr};
   int dev = 0;
@@ -299,7 +301,15 @@ static cudaError_t noalloc_scratch(double** out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
+  *capturing = false;
   if (!ptr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) {
+      *capturing = true;
+      return cudaSuccess;
+    }
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_band_grad_scratch);
     if (e != cudaSuccess) return e;
@@ -317,6 +327,7 @@ extern "C" bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const voi
   if (!valid_handle(h)) return set_error(BS_EINVAL, "bs_band_grad_noalloc: unknown handle");
   if (!GB || !X || !dbands) return set_error(BS_EINVAL, "bs_band_grad_noalloc: null data pointer");
   if (M < 1) return set_error(BS_EINVAL, "bs_band_grad_noalloc: M must be >= 1");
+  if (M > INT64_MAX / 16 / h->N) return set_error(BS_EINVAL, "bs_band_grad_noalloc: N*M too large");
   if (layout != BS_INTERLEAVED && layout != BS_STRIDED)
     return set_error(BS_EINVAL, "bs_band_grad_noalloc: bad layout");
   if (dtype != BS_F64 && dtype != BS_F32)
@@ -332,8 +343,12 @@ extern "C" bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const voi
                                     std::to_string(kNoAllocScratchDoubles) +
                                     " the fixed array holds; use bs_band_grad");
   double* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  bool capturing = false;
+  cudaError_t e = noalloc_scratch(&scratch, reinterpret_cast<cudaStream_t>(stream), &capturing);
   if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc: scratch address");
+  if (capturing)
+    return set_error(BS_EINVAL, "bs_band_grad_noalloc: the first call on a device looks up the array's address "
+                                "and must not be made while its stream is being captured");
   e = band_grad_with_scratch(h->width, N, h->periodic, GB, X, dtype, layout, M, dbands, scratch,
                              reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_error(e, "bs_band_grad_noalloc launch");

@@ -38,6 +38,18 @@ bool valid_handle(bs_handle h) {
   return h != nullptr && g_handles.count(h) != 0;
 }
 
+bool handle_ref(bs_handle h) {
+  std::lock_guard<std::mutex> lk(g_handles_mu);
+  if (h == nullptr || g_handles.count(h) == 0) return false;
+  h->server_refs++;
+  return true;
+}
+
+void handle_unref(bs_handle h) {
+  std::lock_guard<std::mutex> lk(g_handles_mu);
+  if (h != nullptr && g_handles.count(h) != 0 && h->server_refs > 0) h->server_refs--;
+}
+
 const DeviceInfo& device_info() {
   static DeviceInfo info[64];
   static bool have[64] = {false};
@@ -916,7 +928,11 @@ bs_status bs_destroy(bs_handle h) {
   if (!h) return BS_OK;
   {
     std::lock_guard<std::mutex> lk(g_handles_mu);
-    if (!g_handles.erase(h)) return set_error(BS_EINVAL, "bs_destroy: unknown handle");
+    if (!g_handles.count(h)) return set_error(BS_EINVAL, "bs_destroy: unknown handle");
+    if (h->server_refs > 0)
+      return set_error(BS_EINVAL, "bs_destroy: " + std::to_string(h->server_refs) +
+                                      " server request(s) using this handle have not finished");
+    g_handles.erase(h);
   }
   free_handle(h);
   return BS_OK;

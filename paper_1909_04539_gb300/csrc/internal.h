@@ -146,6 +146,8 @@ struct bs_factor_s {
   bs::TwistPlan twist[2];  // two-ended tridiagonal sweeps: [0] for A (plan[0], plan[2]),
                            // [1] for A^T (tplan[])
   bs::SweepPlan tplan[2];  // A^T = L U and A^T = U' L' (primal form, original row order)
+  int64_t server_refs;     // server requests naming this handle that have not finished
+                           // (guarded by the handle registry's lock; bs_destroy refuses > 0)
 };
 
 namespace bs {
@@ -153,6 +155,9 @@ namespace bs {
 bs_status set_error(bs_status s, const std::string& msg);
 bs_status cuda_error(cudaError_t e, const char* what);
 bool valid_handle(bs_handle h);
+// Pin / unpin a handle for a server request (false: unknown handle).
+bool handle_ref(bs_handle h);
+void handle_unref(bs_handle h);
 
 struct DeviceInfo {
   int sms;

@@ -11,6 +11,16 @@
 // as soon as memory and a stream are free.  Completion is observed by polling
 // the batch events; latency is host submission to host-observed completion.
 // No device-side waits are involved: a batch is a finite work list.
+//
+// Tail latency: requests are split into two size classes (arena bytes up to
+// kSmallBytes, and larger) with a queue each, so a large request waiting for
+// memory never holds back small ones, and a batch holds one class only.  With
+// two or more streams, stream 0 runs only small-request batches, so small
+// requests never queue behind the multi-millisecond copies of a large batch.
+// Inside a batch the copies go smallest first and every request has its own
+// completion event after its device-to-host copy: it finishes as soon as its
+// own results are back, not when the whole batch is.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -84,6 +94,21 @@ class Arena {
 
 enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_CANCELLED = 3, RQ_FAILED = 4 };
 
+// arena bytes up to which a request is "small"
+constexpr size_t kSmallBytes = size_t(16) << 20;
+// host<->device copies are issued in pieces of at most this many bytes, so
+// that the copy engines can interleave other streams' (small) copies with
+// a large request's instead of running them after it
+constexpr size_t kCopyChunk = size_t(8) << 20;
+
+cudaError_t copy_chunked(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (size_t o = 0; o < bytes && e == cudaSuccess; o += kCopyChunk)
+    e = cudaMemcpyAsync(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o,
+                        bytes - o < kCopyChunk ? bytes - o : kCopyChunk, kind, st);
+  return e;
+}
+
 struct Req {
   bs_handle h;
   const void* hB;
@@ -95,6 +120,7 @@ struct Req {
   double t_submit = 0, t_done = 0;
   int state = RQ_QUEUED;
   bool fail_on_admit = false;
+  bool small = true;
 };
 
 struct Slot {
@@ -104,7 +130,10 @@ struct Slot {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
-  std::vector<int64_t> reqs;
+  bool small_only = false;          // runs small-request batches only
+  std::vector<int64_t> reqs;        // the batch's requests, in copy order
+  std::vector<cudaEvent_t> ev;      // per request: its device-to-host copy done
+  std::vector<char> finished;       // per request: completion recorded
 };
 
 }  // namespace
@@ -117,7 +146,8 @@ struct bs_server_s {
   std::vector<bs::Slot> slots;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<int64_t> queue;
+  std::deque<int64_t> queue;        // small requests, arrival order
+  std::deque<int64_t> queue_large;  // large requests, arrival order
   std::unordered_map<int64_t, bs::Req> reqs;
   int64_t next_id = 1;
   std::thread worker;
@@ -137,45 +167,53 @@ size_t req_bytes(int width, int64_t N, int mode, int64_t M) {
   return mode == SERVE_F64 ? nm * 8 : nm * 4 + nm * 8;
 }
 
-// Admit queued requests (in order) while they fit; returns the admitted ids.
-std::vector<int64_t> admit(bs_server s) {
+// Admit queued requests of one class (in arrival order) while they fit;
+// returns the admitted ids.
+std::vector<int64_t> admit(bs_server s, bool small) {
   std::vector<int64_t> out;
+  std::deque<int64_t>& queue = small ? s->queue : s->queue_large;
   int tiles = 0;
-  while (!s->queue.empty() && (int)out.size() < kGroupMaxReq) {
-    const int64_t id = s->queue.front();
+  while (!queue.empty() && (int)out.size() < kGroupMaxReq) {
+    const int64_t id = queue.front();
     Req& r = s->reqs[id];
     if (r.state == RQ_CANCELLED) {
-      s->queue.pop_front();
+      queue.pop_front();
       continue;
     }
     const int t = (int)((r.M + 31) / 32);
     if (tiles + t > kGroupMaxTiles) break;
     size_t off = 0;
     if (!s->arena.alloc(r.bytes, &off)) break;  // wait for memory (arrival order is kept)
-    s->queue.pop_front();
+    queue.pop_front();
     r.off = off;
     if (r.fail_on_admit) {  // host-side fault injection for tests
       s->arena.release(off, r.bytes);
       r.state = RQ_FAILED;
       r.t_done = now_s();
       s->failed++;
+      handle_unref(r.h);
       continue;
     }
     r.state = RQ_RUNNING;
     tiles += t;
     out.push_back(id);
   }
+  // copies smallest first, so that small requests' results come back first
+  std::stable_sort(out.begin(), out.end(), [&](int64_t a, int64_t b) { return s->reqs[a].bytes < s->reqs[b].bytes; });
   return out;
 }
 
-cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<int64_t>& ids) {
+// Copies in, the grouped launch and copies out of one batch on the slot's
+// stream.  Called without the server lock: rp are the batch's requests
+// (their entries are not modified by other threads once admitted).
+cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<Req*>& rp) {
   GHeader* hdr = reinterpret_cast<GHeader*>(sl.h_work);
   GReq* greq = reinterpret_cast<GReq*>(sl.h_work + kGroupReqOff);
   GTile* gt = reinterpret_cast<GTile*>(sl.h_work + kGroupTileOff);
   int nt = 0;
   cudaError_t e = cudaSuccess;
-  for (size_t q = 0; q < ids.size() && e == cudaSuccess; q++) {
-    Req& r = s->reqs[ids[q]];
+  for (size_t q = 0; q < rp.size() && e == cudaSuccess; q++) {
+    Req& r = *rp[q];
     const bs_handle h = r.h;
     const size_t nm = (size_t)h->N * (size_t)r.M;
     char* dB = s->arena_base + r.off;
@@ -193,25 +231,45 @@ cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<int64_t>& ids)
     if (r.mode == SERVE_F64) {
       g.B = dB;
       g.X = reinterpret_cast<double*>(dB);
-      e = cudaMemcpyAsync(dB, r.hB, nm * 8, cudaMemcpyHostToDevice, sl.st);
+      e = copy_chunked(dB, r.hB, nm * 8, cudaMemcpyHostToDevice, sl.st);
     } else {
       g.X = reinterpret_cast<double*>(dB);                   // nm * 8 bytes
       g.B = dB + nm * 8;                                     // nm * 4 bytes
-      e = cudaMemcpyAsync(g.B, r.hB, nm * 4, cudaMemcpyHostToDevice, sl.st);
+      e = copy_chunked(g.B, r.hB, nm * 4, cudaMemcpyHostToDevice, sl.st);
     }
     greq[q] = g;
     for (int64_t j0 = 0; j0 < r.M; j0 += 32) gt[nt++] = GTile{(int)q, (int)j0};
   }
-  hdr->n_req = (int)ids.size();
+  hdr->n_req = (int)rp.size();
   hdr->n_tiles = nt;
   if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, sl.st);
-  for (size_t q = 0; q < ids.size() && e == cudaSuccess; q++) {
-    Req& r = s->reqs[ids[q]];
+  while (sl.ev.size() < rp.size() && e == cudaSuccess) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) sl.ev.push_back(ev);
+  }
+  for (size_t q = 0; q < rp.size() && e == cudaSuccess; q++) {
+    Req& r = *rp[q];
     const size_t nm = (size_t)r.h->N * (size_t)r.M;
-    e = cudaMemcpyAsync(r.hX, s->arena_base + r.off, nm * 8, cudaMemcpyDeviceToHost, sl.st);
+    e = copy_chunked(r.hX, s->arena_base + r.off, nm * 8, cudaMemcpyDeviceToHost, sl.st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev[q], sl.st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
   return e;
+}
+
+// Records a request's end: its arena bytes go back, its handle is unpinned.
+void finish_request(bs_server s, Req& r, bool ok, double t) {
+  s->arena.release(r.off, r.bytes);
+  r.t_done = t;
+  if (ok) {
+    r.state = RQ_DONE;
+    s->completed++;
+  } else {
+    r.state = RQ_FAILED;
+    s->failed++;
+  }
+  handle_unref(r.h);
 }
 
 void worker_loop(bs_server s) {
@@ -219,26 +277,27 @@ void worker_loop(bs_server s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
     bool progressed = false;
-    // completions
+    // completions: each request as soon as its own copy back is done; the
+    // slot when the whole batch is
     for (Slot& sl : s->slots) {
       if (!sl.busy) continue;
+      for (size_t q = 0; q < sl.reqs.size(); q++) {
+        if (sl.finished[q]) continue;
+        const cudaError_t eq = cudaEventQuery(sl.ev[q]);
+        if (eq == cudaErrorNotReady) break;  // later copies of the batch are not done either
+        if (eq != cudaSuccess) break;        // the batch event reports the failure below
+        finish_request(s, s->reqs[sl.reqs[q]], true, now_s());
+        sl.finished[q] = 1;
+        progressed = true;
+      }
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       const double t = now_s();
-      for (int64_t id : sl.reqs) {
-        Req& r = s->reqs[id];
-        s->arena.release(r.off, r.bytes);
-        r.t_done = t;
-        if (q == cudaSuccess) {
-          r.state = RQ_DONE;
-          s->completed++;
-        } else {
-          r.state = RQ_FAILED;
-          s->failed++;
-        }
-      }
+      for (size_t k = 0; k < sl.reqs.size(); k++)
+        if (!sl.finished[k]) finish_request(s, s->reqs[sl.reqs[k]], q == cudaSuccess, t);
       if (q != cudaSuccess) s->sticky = q;
       sl.reqs.clear();
+      sl.finished.clear();
       sl.busy = false;
       progressed = true;
     }
@@ -246,29 +305,38 @@ void worker_loop(bs_server s) {
     // admission and launch
     if (!s->paused) {
       for (Slot& sl : s->slots) {
-        if (sl.busy || s->queue.empty()) continue;
-        std::vector<int64_t> ids = admit(s);
+        if (sl.busy) continue;
+        // the reserved slot takes small requests; the others the class whose
+        // oldest queued request came first (falling back to the other class)
+        const bool has_small = !s->queue.empty(), has_large = !s->queue_large.empty();
+        if (!has_small && (!has_large || sl.small_only)) continue;
+        bool small = has_small;
+        if (!sl.small_only && has_large && (!has_small || s->queue_large.front() < s->queue.front())) small = false;
+        std::vector<int64_t> ids = admit(s, small);
+        if (ids.empty() && !sl.small_only && has_small && has_large) ids = admit(s, !small);
         if (ids.empty()) {
           s->cv.notify_all();  // failures injected at admission are final
-          break;
+          continue;
         }
-        const cudaError_t e = launch_batch(s, sl, ids);
+        // copies and the graph launch run without the lock (the slot and the
+        // admitted requests belong to this thread now: cancel and release
+        // refuse admitted requests, and map entries keep their addresses)
+        std::vector<Req*> rp;
+        for (int64_t id : ids) rp.push_back(&s->reqs.find(id)->second);
+        lk.unlock();
+        const cudaError_t e = launch_batch(s, sl, rp);
+        lk.lock();
         progressed = true;
         if (e != cudaSuccess) {  // nothing of this batch can be trusted: fail its requests
           s->sticky = e;
           cudaStreamSynchronize(sl.st);
           const double t = now_s();
-          for (int64_t id : ids) {
-            Req& r = s->reqs[id];
-            s->arena.release(r.off, r.bytes);
-            r.state = RQ_FAILED;
-            r.t_done = t;
-            s->failed++;
-          }
+          for (int64_t id : ids) finish_request(s, s->reqs[id], false, t);
           s->cv.notify_all();
           continue;
         }
         sl.reqs = ids;
+        sl.finished.assign(ids.size(), 0);
         sl.busy = true;
         s->batches++;
         if ((int64_t)ids.size() > s->max_batch_reqs) s->max_batch_reqs = (int64_t)ids.size();
@@ -293,11 +361,15 @@ void destroy_server(bs_server s) {
     if (sl.st) cudaStreamSynchronize(sl.st);
     if (sl.exec) cudaGraphExecDestroy(sl.exec);
     if (sl.done) cudaEventDestroy(sl.done);
+    for (cudaEvent_t ev : sl.ev) cudaEventDestroy(ev);
     if (sl.h_work) cudaFreeHost(sl.h_work);
     if (sl.d_work) cudaFree(sl.d_work);
     if (sl.st) cudaStreamDestroy(sl.st);
   }
   if (s->arena_base) cudaFree(s->arena_base);
+  // requests that never finished (dropped from the queue) unpin their handles
+  for (auto& kv : s->reqs)
+    if (kv.second.state == RQ_QUEUED || kv.second.state == RQ_RUNNING) handle_unref(kv.second.h);
   delete s;
 }
 
@@ -322,9 +394,15 @@ bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* ou
   }
   s->arena.init(hbm_budget_bytes);
   s->slots.resize(n_streams);
+  if (n_streams >= 2) s->slots[0].small_only = true;
   const int grid = grouped_grid();
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   for (Slot& sl : s->slots) {
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+    // the small-request stream gets the highest priority: its CTAs are
+    // scheduled first when SM resources free up
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.small_only ? prio_hi : prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.h_work, kGroupWorkBytes);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_work, kGroupWorkBytes);
@@ -371,10 +449,18 @@ bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* h
   if (!host_B || !host_X) return set_error(BS_EINVAL, "bs_server_submit: null buffer");
   if (mode != SERVE_F64 && mode != SERVE_F32_REFINE) return set_error(BS_EINVAL, "bs_server_submit: bad mode");
   if (M < 1 || M > (int64_t)kGroupMaxTiles * 32) return set_error(BS_EINVAL, "bs_server_submit: M out of range");
+  for (const void* p : {host_B, static_cast<const void*>(host_X)}) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return set_error(BS_EINVAL, "bs_server_submit: host buffers must be page-locked (pinned) host memory");
+    }
+  }
   const size_t bytes = req_bytes(h->width, h->N, mode, M);
   std::lock_guard<std::mutex> lk(s->mu);
   if (bytes > s->arena.size())
     return set_error(BS_ENOMEM, "bs_server_submit: request larger than the server's HBM budget");
+  if (!handle_ref(h)) return set_error(BS_EINVAL, "bs_server_submit: unknown handle");
   const int64_t id = s->next_id++;
   Req r;
   r.h = h;
@@ -384,9 +470,10 @@ bs_status bs_server_submit(bs_server s, bs_handle h, const void* host_B, void* h
   r.M = M;
   r.bytes = bytes;
   r.off = 0;
+  r.small = bytes <= kSmallBytes;
   r.t_submit = now_s();
   s->reqs[id] = r;
-  s->queue.push_back(id);
+  (r.small ? s->queue : s->queue_large).push_back(id);
   *request_id = id;
   s->cv.notify_all();
   return BS_OK;
@@ -427,6 +514,7 @@ bs_status bs_server_cancel(bs_server s, int64_t id) {
   if (it->second.state != RQ_QUEUED) return set_error(BS_EINVAL, "bs_server_cancel: request already admitted");
   it->second.state = RQ_CANCELLED;
   it->second.t_done = now_s();
+  handle_unref(it->second.h);
   s->cv.notify_all();
   return BS_OK;
 }

@@ -146,3 +146,32 @@ def test_cancel_failure_and_timeout(bs, serve):
     with pytest.raises(bs.BsolveError):
         srv.poll(subs[0][0])
     srv.close()
+
+
+def test_handle_pinned_while_requests_pending(bs, serve):
+    """bs_destroy refuses a handle that queued server requests name (the
+    worker would read its plans); once they finish or are cancelled it is
+    released normally."""
+    specs, facs = _lhs_pool(bs, 1)
+    srv = serve.Server(1 << 28, n_streams=2)
+    srv.pause(True)
+    B, X = _request(specs[0], 64, 0, 1)
+    rid = srv.submit(facs[0], B, X, 0)
+    with pytest.raises(bs.BsolveError, match="have not finished"):
+        facs[0].close()
+    # the failed close left the handle usable: still registered
+    assert facs[0].device_bytes > 0
+    srv.cancel(rid)
+    facs[0].close()
+    srv.close()
+
+
+def test_pageable_host_buffers_rejected(bs, serve):
+    specs, facs = _lhs_pool(bs, 1)
+    srv = serve.Server(1 << 26, n_streams=1)
+    B = torch.zeros((specs[0].N, 8), dtype=torch.float64)  # not pinned
+    X = torch.zeros((specs[0].N, 8), dtype=torch.float64).pin_memory()
+    with pytest.raises(bs.BsolveError, match="page-locked"):
+        srv.submit(facs[0], B, X, 0)
+    srv.close()
+
