@@ -87,6 +87,16 @@ template <int BW, bool ADJ, int V, int U, bool FULL>
 __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<double>& c64, int i0, int n,
                                              double (&f)[U][V], uint2 (&out)[U][V], DfState<V>& st) {
   constexpr bool F2 = DfCount<ADJ, BW>::F > 2;
+  // the rows' coefficient records first: their shared-memory latency
+  // overlaps the splits below
+  float4 q[U];
+  float2 q2[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int i = (FULL || u < n) ? i0 + u : i0;
+    q[u] = rc.f4[i];
+    q2[u] = F2 ? rc.f2[i] : make_float2(0.f, 0.f);
+  }
   df::Pair y[U][V];
   bool need = false;
   if (!st.f64) {
@@ -121,14 +131,6 @@ __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<doubl
     }
   }
   if (!st.f64) {
-    float4 q[U];
-    float2 q2[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int i = (FULL || u < n) ? i0 + u : i0;
-      q[u] = rc.f4[i];
-      q2[u] = F2 ? rc.f2[i] : make_float2(0.f, 0.f);
-    }
 #pragma unroll
     for (int u = 0; u < U; u++)
       if (FULL || u < n)

@@ -238,11 +238,22 @@ def test_pair_sweeps_match_oracle(lib, width, N):
     assert sys_rel_err(G, oracle.solve_adjoint(bands, B)) < 1e-13
 
 
-def test_pair_sweep_clamped_hyperdiffusion(lib):
-    """The benchmark matrix, I + 0.1 D4 clamped, N = 512."""
-    bands = synth.clamped_hyperdiffusion_bands(512, 0.1)
+@pytest.mark.parametrize("kind", ["hyper", "spline", "adi", "stiff"])
+def test_pair_sweep_structured_matrices(lib, kind):
+    """The benchmark matrix I + 0.1 D4 clamped (N = 512), the spline and ADI
+    tridiagonal matrices (N = 1024) and stiff hyperdiffusion I + 1000 D4
+    (N = 512, condition number ~1.6e4: the pairs' error grows with it, as
+    FP64's does)."""
+    bands = {"hyper": lambda: synth.clamped_hyperdiffusion_bands(512, 0.1), "spline": lambda: synth.spline_bands(1024),
+             "adi": lambda: synth.adi_bands(1024, 0.5),
+             "stiff": lambda: synth.toeplitz_bands(512, (1e3, -4e3, 1 + 6e3, -4e3, 1e3))}[kind]()
     rng = np.random.default_rng(5)
-    B = rng.standard_normal((512, 16))
-    prim, _ = _plans(bands)
-    X = np.stack([_sweep(lib, prim, True, False, 2, B[:, j]) for j in range(16)], axis=1)
-    assert sys_rel_err(X, oracle.solve(bands, B)) < 1e-13
+    N = bands.shape[1]
+    B = rng.standard_normal((N, 16))
+    prim, adj = _plans(bands)
+    bw = bands.shape[0] // 2
+    X = np.stack([_sweep(lib, prim, True, False, bw, B[:, j]) for j in range(16)], axis=1)
+    G = np.stack([_sweep(lib, adj, False, True, bw, B[:, j]) for j in range(16)], axis=1)
+    tol = 1e-12 if kind == "stiff" else 1e-13
+    assert sys_rel_err(X, oracle.solve(bands, B)) < tol
+    assert sys_rel_err(G, oracle.solve_adjoint(bands, B)) < tol
