@@ -190,11 +190,18 @@ __device__ __forceinline__ void df_bwd_group(const DfRecs& rc, const Coefs<doubl
           if (!df::combine_ok(y[u][v].h)) x[u][v] = df::combine(y[u][v].h, y[u][v].l);
     }
   } else {
+    if (top - (U - 1) >= st.rsw) {  // the whole group was stored in FP64
 #pragma unroll
-    for (int u = 0; u < U; u++)
+      for (int u = 0; u < U; u++)
 #pragma unroll
-      for (int v = 0; v < V; v++)
-        x[u][v] = (top - u >= st.rsw) ? bits_f64(in[u][v]) : pair_to_f64(bits_pair(in[u][v]));
+        for (int v = 0; v < V; v++) x[u][v] = bits_f64(in[u][v]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int v = 0; v < V; v++)
+          x[u][v] = (top - u >= st.rsw) ? bits_f64(in[u][v]) : pair_to_f64(bits_pair(in[u][v]));
+    }
     bwd_block<BW, ADJ, double, V, U, false>(c64, top, n, x, st.d1, st.d2);
   }
 }

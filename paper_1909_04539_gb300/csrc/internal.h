@@ -175,6 +175,18 @@ bs_status launch_refine(bs_handle h, const void* B, bs_dtype b_t, double* X, int
 bs_status launch_band_grad(bs_handle h, const void* GB, const void* X, bs_dtype t, bs_layout layout,
                            int64_t M, double* dbands, cudaStream_t st);
 bool df_eligible(const SweepPlan& p, bs_layout layout);
+// Launch shape of a persistent one-thread-per-group sweep whose CTAs stage
+// rec_bytes of coefficient records in shared memory (if they fit) and use
+// per_thread shared bytes per thread: grid, CTA size, whether staged.
+struct StagedShape {
+  int grid, threads;
+  bool staged;
+  double cost;  // busiest-SM warp shares summed over the grid's passes
+};
+StagedShape staged_shape(int64_t groups, size_t rec_bytes, size_t per_thread, int regs, int max_threads,
+                         bool any_size, int prefer);
+// registers per thread of a kernel (0 if unknown)
+int kernel_regs(const void* kernel);
 cudaError_t sweep_df(const SweepPlan& p, bool adjoint, int N, double* X, int64_t M, cudaStream_t st);
 cudaError_t sweep_win_df(const SweepPlan& p, bool adjoint, int N, double* X, int64_t M, cudaStream_t st);
 template <typename Sin>

@@ -1,6 +1,7 @@
 // C-ABI entry points of the solves and the launch-shape policy.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <string>
 
 #include "sweep_kernels.cuh"
@@ -113,6 +114,55 @@ LaunchShape sweep_shape(int bw, int N, int64_t threads_needed, size_t coef_elem,
         best = sh;
         best_cost = c;
       }
+    }
+  }
+  return best;
+}
+
+int kernel_regs(const void* kernel) {
+  cudaFuncAttributes a{};
+  return cudaFuncGetAttributes(&a, kernel) == cudaSuccess ? a.numRegs : 0;
+}
+
+// Candidates: every multiple of 64 up to max_threads (any_size = false: only
+// 64, 128 and 256) with staged records, 32 too without, or the CTA size
+// BS_OPT_CTA_THREADS forces (32-thread CTAs that each stage the records were
+// slower in every measured case).  CTAs per SM follow from shared memory (records
+// once per CTA) and registers; a pass of the persistent grid costs its
+// busiest SM's warps, at least 4 (below ~4 warps per SM the dependent chains,
+// not issue, set the time); the cheapest shape wins, on a tie the CTA size
+// nearest `prefer` (the larger of two as near).  Staged records are preferred
+// whenever some CTA size fits them.
+StagedShape staged_shape(int64_t groups, size_t rec_bytes, size_t per_thread, int regs, int max_threads,
+                         bool any_size, int prefer) {
+  const DeviceInfo& d = device_info();
+  const size_t sm_bytes = 228 * 1024, limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
+  const int reg_alloc = regs > 0 ? (regs + 7) / 8 * 8 : 0;
+  StagedShape best{0, 0, false, 1e300};
+  const int forced = (int)option(BS_OPT_CTA_THREADS);
+  for (int staged = 1; staged >= 0 && best.threads == 0; staged--) {
+    for (int t = 32; t <= max_threads; t = (t < 64 ? 64 : t + 64)) {
+      if (forced > 0 && t != forced) continue;
+      if (!forced && staged && (t == 32 || (!any_size && t != 64 && t != 128 && t != 256))) continue;
+      const size_t cta = (staged ? rec_bytes : 0) + (size_t)t * per_thread;
+      if (cta > limit) continue;
+      int c = (int)(sm_bytes / (cta + 1024));
+      c = std::min(c, 2048 / t);
+      if (reg_alloc > 0) c = std::min(c, 65536 / (reg_alloc * t));
+      if (c < 1) continue;
+      const int64_t blocks = (groups + t - 1) / t;
+      const int64_t grid = std::min<int64_t>((int64_t)d.sms * c, blocks);
+      const int64_t per_pass = grid * t;
+      double cost = 0.0;
+      for (int64_t done = 0; done < groups; done += per_pass) {
+        const int64_t active = std::min<int64_t>(grid, (groups - done + t - 1) / t);
+        const int64_t busy = (active + d.sms - 1) / d.sms;
+        cost += std::max(busy * t / 32.0, 4.0);
+      }
+      const bool nearer = std::abs(t - prefer) < std::abs(best.threads - prefer) ||
+                          (std::abs(t - prefer) == std::abs(best.threads - prefer) && t > best.threads);
+      if (cost < best.cost - 1e-9 || (cost < best.cost + 1e-9 && nearer))
+        best = StagedShape{(int)std::max<int64_t>(grid, 1), t, staged != 0, cost};
     }
   }
   return best;

@@ -30,7 +30,7 @@ namespace bs {
 
 namespace {
 
-constexpr int kDfThreadsMax = 256;
+constexpr int kDfThreadsMax = 512;
 
 // V lane-rows of 8-byte values (pairs or FP64) in a ring slot or in memory
 template <int V>
@@ -200,11 +200,20 @@ cudaError_t launch_df(const SweepPlan& p, int N, double* X, int64_t M, cudaStrea
   constexpr int D = 16;
   const DfRecs rg = df_recs_of(p.dfrec, N);
   Coefs<double> c64 = coefs_of<double>(p.c64, N);
-  // 12 FP32 values of records per row: pass them as (1 + 2 bw + extra) arrays
-  const LaunchShape sh = sweep_shape(BW, N, M / V, 4, 8, V, D * 8 * V, 0, 0, 12 - (1 + 2 * BW));
-  const size_t rec = sh.smem_coefs ? (size_t)N * 48 : 0;
-  const size_t bytes = rec + (size_t)sh.threads * D * 8 * V;
-  auto k = sh.smem_coefs ? k_sweep_df<BW, ADJ, true, V, D> : k_sweep_df<BW, ADJ, false, V, D>;
+  // CTA size: any warp multiple the shared memory and registers allow; the
+  // busiest SM's warps set the time of this issue-bound kernel (penta N =
+  // 512, M = 65536: one 448-thread CTA per SM, 14 warps on the busiest SM,
+  // against 16 with four 128-thread CTAs on 56 of the SMs: 0.188 -> 0.170 ms).
+  // Ties go to 128 threads: the tri N = 1024, M = 2^20 batch (many passes, all
+  // sizes tie) took 5.30 ms with 128, 5.56 - 5.82 ms with 384 - 512.
+  auto ks = k_sweep_df<BW, ADJ, true, V, D>;
+  auto kg = k_sweep_df<BW, ADJ, false, V, D>;
+  const size_t rec = (size_t)N * 48;
+  const StagedShape sh = staged_shape(M / V, rec, (size_t)D * 8 * V, kernel_regs((const void*)ks), kDfThreadsMax, true,
+                                        128);
+  if (sh.threads == 0) return cudaErrorInvalidValue;
+  const size_t bytes = (sh.staged ? rec : 0) + (size_t)sh.threads * D * 8 * V;
+  auto k = sh.staged ? ks : kg;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k<<<sh.grid, sh.threads, bytes, st>>>(rg, c64, N, X, M);

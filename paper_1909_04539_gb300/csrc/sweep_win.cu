@@ -442,54 +442,6 @@ k_sweep_win(WinRecs rg, Coefs<double> c64, int N, int K, int Lw, const Sin* in, 
   }
 }
 
-// Launch shape of a windowed sweep: CTA size and CTAs per SM that give the
-// most resident threads for the shared memory (records once per CTA, R
-// slots per thread), scored by rounds of the persistent grid: a round with
-// k warps on an SM costs max(k, 4) warp shares (below ~4 warps per SM the
-// dependent chains, not issue, set the time).
-struct WinShape {
-  int grid, threads;
-  bool smem;  // records staged in shared memory
-  double cost;
-};
-static WinShape win_shape(int64_t groups, size_t rec_bytes, size_t per_thread) {
-  const DeviceInfo& d = device_info();
-  const size_t sm_bytes = 228 * 1024, limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
-  WinShape best{0, 0, false, 1e300};
-  const int forced = (int)option(BS_OPT_CTA_THREADS);
-  // records staged in shared memory whenever some CTA size fits them (read
-  // through L1/L2 instead they made the FP32 penta N = 512 solve twice as
-  // slow); then 64, 128 or 256 threads (384 measured 5 % slower on the tri
-  // N = 1024 batch, 32-thread CTAs stage the records too often)
-  for (int staged = 1; staged >= 0 && best.threads == 0; staged--) {
-    for (int t = 32; t <= kWinThreads; t = (t < 64 ? 64 : t + 64)) {
-      if (forced > 0 && t != forced) continue;
-      if (!forced && staged && t != 64 && t != 128 && t != 256) continue;
-      const size_t cta = (staged ? rec_bytes : 0) + (size_t)t * per_thread;
-      if (cta > limit) continue;
-      int c = (int)(sm_bytes / (cta + 1024));
-      c = std::min(c, 2048 / t);
-      if (c < 1) continue;
-      const int64_t blocks = (groups + t - 1) / t;
-      const int64_t grid = std::min<int64_t>((int64_t)d.sms * c, blocks);
-      // the persistent grid runs `rounds` passes over the batch; in each the
-      // busiest SM holds ceil(active CTAs / SMs) CTAs; a pass costs its busiest
-      // SM's warps, at least 4 (below that the dependent chains set the time)
-      const int64_t per_pass = grid * t;
-      double cost = 0.0;
-      for (int64_t done = 0; done < groups; done += per_pass) {
-        const int64_t active = std::min<int64_t>(grid, (groups - done + t - 1) / t);
-        const int64_t busy = (active + d.sms - 1) / d.sms;
-        cost += std::max(busy * t / 32.0, 4.0);
-      }
-      if (cost < best.cost - 1e-9 || (cost < best.cost + 1e-9 && t > best.threads)) {
-        best = WinShape{(int)std::max<int64_t>(grid, 1), t, staged != 0, cost};
-      }
-    }
-  }
-  return best;
-}
-
 template <int BW, bool ADJ, int V, int R, int D, bool DFK, typename Sin, typename Sout>
 cudaError_t launch_win(const SweepPlan& p, int N, int Lw, const Sin* in, Sout* out, int64_t M, cudaStream_t st) {
   const int K = (R - D - Lw) / kWU * kWU;
@@ -506,11 +458,18 @@ cudaError_t launch_win(const SweepPlan& p, int N, int Lw, const Sin* in, Sout* o
   constexpr int SB = V * (DFK ? 8 : 4);
   const size_t rec = DFK ? (size_t)N * 48 : (size_t)N * 32;
   const size_t per_thread = (size_t)R * SB;
-  const WinShape sh = win_shape(M / V, rec, per_thread);
+  // records staged in shared memory whenever some CTA size fits them (read
+  // through L1/L2 instead they made the FP32 penta N = 512 solve twice as
+  // slow); then 64, 128 or 256 threads (384 measured 5 % slower on the tri
+  // N = 1024 batch, 32-thread CTAs stage the records too often)
+  auto ks = k_sweep_win<BW, ADJ, V, R, D, true, DFK, Sin, Sout>;
+  auto kg = k_sweep_win<BW, ADJ, V, R, D, false, DFK, Sin, Sout>;
+  const StagedShape sh = staged_shape(M / V, rec, per_thread, kernel_regs((const void*)ks), kWinThreads, false,
+                                        kWinThreads);
   if (sh.threads == 0) return cudaErrorInvalidValue;
-  const bool smem = sh.smem;
+  const bool smem = sh.staged;
   const size_t bytes = (smem ? rec : 0) + (size_t)sh.threads * per_thread;
-  auto k = smem ? k_sweep_win<BW, ADJ, V, R, D, true, DFK, Sin, Sout> : k_sweep_win<BW, ADJ, V, R, D, false, DFK, Sin, Sout>;
+  auto k = smem ? ks : kg;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k<<<sh.grid, sh.threads, bytes, st>>>(rg, c64, N, K, Lw, in, out, M);
