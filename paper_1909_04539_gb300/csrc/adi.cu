@@ -237,16 +237,19 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
 
 constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
 
-// X-implicit half-step: one-warp CTAs, each owning 32 rows of
-// the grid (systems).  Chunks of R grid columns (rows of the systems) move
-// through a ring of K tiles in shared memory by cp.async -- the lanes with
-// lane % R == q copy row q of the chunk for the 34 systems the warp touches
-// (its 32 plus one neighbour each side), 32 / R lanes sharing a row -- so K
-// chunks are in flight while one is swept.  The
-// forward values overwrite the swept tile, leave from it with coalesced
-// stores and come back through the same ring for the backward sweep.
+// X-implicit half-step: each warp owns 32 rows of the grid (systems) at a
+// time; the warps of a CTA share its staged coefficients and each has its
+// own ring.  Chunks of R grid columns (rows of the systems) move through a
+// ring of K tiles in shared memory by cp.async -- the lanes with lane % R == q
+// copy row q of the chunk for the 34 systems the warp touches (its 32 plus
+// one neighbour each side), 32 / R lanes sharing a row -- so K chunks are in
+// flight while one is swept.  The forward values overwrite the swept tile,
+// leave from it with coalesced stores and come back through the same ring for
+// the backward sweep.  Warps synchronise only within themselves.
+constexpr int kAdiStThreads = 128;  // largest CTA (warps per CTA: blockDim.x / 32)
+
 template <int BW, bool ADJ, bool SMEM, typename C, int K, int R>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kAdiStThreads)
 k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, int64_t M, C r, int64_t ld, int L) {
   static_assert(R == 16 || R == 32, "chunk rows");
   static_assert(kStPad <= kAdiTile, "backward tiles reuse the ring");
@@ -266,11 +269,12 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
   C* smc = reinterpret_cast<C*>(smem_raw) + fuse_elems<C, FUSE>(N);
   const Coefs<C> cf = stage_coefs<BW, ADJ, SMEM>(cf_g, N, smc);
   if constexpr (FUSE) fuse_explicit(cf.s, reinterpret_cast<double2*>(smem_raw), N, r);
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int crow = lane % R, cph = lane / R;  // chunk row and system phase of this lane's copies
   C* ringt = reinterpret_cast<C*>(smem_raw) +
              (SMEM ? align_up((fuse_elems<C, FUSE>(N) + (size_t)coef_arrays<BW>() * N) * sizeof(C), 16) / sizeof(C)
-                   : 0);
+                   : 0) +
+             (size_t)warp * K * kTile;
   auto cp = [&](C* dst, const C* src) {
     const uint32_t d = smem_u32(dst);
     if constexpr (sizeof(C) == 8)
@@ -279,7 +283,7 @@ k_adi_st2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
   };
   const int nch = (N + R - 1) / R;
-  for (int64_t wg = blockIdx.x; wg * 32 < M; wg += gridDim.x) {
+  for (int64_t wg = (int64_t)blockIdx.x * nwarps + warp; wg * 32 < M; wg += (int64_t)gridDim.x * nwarps) {
     const int64_t j0 = wg * 32;
     const int nsys = (int)((M - j0) < 32 ? (M - j0) : 32);
     const bool mine = lane < nsys;
@@ -423,16 +427,26 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
     };
     return P > 1 ? go(std::integral_constant<int, 16>{}) : go(std::integral_constant<int, 64>{});
   }
+  // Warps per CTA: one for a whole-line launch (its ring alone is 8 tiles);
+  // several for a partitioned launch, sharing the staged coefficients, so
+  // that the 2048 warps of a 4096^2 half-step (16 blocks) fit in one round:
+  // FP64 two (seven CTAs, 14 warps per SM; 0.296 ms with one warp, 0.238 with
+  // two, 0.250 with four), FP32 four (0.094, 0.092, 0.090 ms).
+  // BS_OPT_CTA_THREADS = 32, 64 or 128 (and above) forces one, two or four.
+  const int64_t forced = option(BS_OPT_CTA_THREADS);
+  const int tpb = forced > 0 ? (forced >= 128 ? 128 : (forced >= 64 ? 64 : 32))
+                             : (P > 1 ? (sizeof(C) == 8 ? 64 : 128) : 32);
   auto go = [&](auto ktag, auto rtag) -> cudaError_t {
     constexpr int K = decltype(ktag)::value;
     constexpr int R = decltype(rtag)::value;
-    const size_t tiles = (size_t)K * R * kAdiTile * sizeof(C);
+    const size_t tiles = (size_t)K * R * kAdiTile * sizeof(C);  // per warp
     const int64_t threads = ((M + 31) / 32) * 32;
-    const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, 0, tiles, 32, kFuseExtra);
+    const LaunchShape sh = sweep_shape(BW, L, threads * P, sizeof(C), sizeof(C), 1, tiles / 32, 0, tpb, kFuseExtra);
+    const size_t bytes = sh.smem + tiles * (tpb / 32);
     auto k = sh.smem_coefs ? k_adi_st2<BW, ADJ, true, C, K, R> : k_adi_st2<BW, ADJ, false, C, K, R>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sh.smem + tiles));
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k<<<dim3((sh.grid + P - 1) / P, P), 32, sh.smem + tiles, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
+    k<<<dim3((sh.grid + P - 1) / P, P), tpb, bytes, st>>>(cf, N, u, out, M, r, (int64_t)N, L);
     return cudaGetLastError();
   };
   if (P == 1) return go(std::integral_constant<int, 8>{}, std::integral_constant<int, 32>{});

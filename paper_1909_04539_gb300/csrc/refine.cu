@@ -390,6 +390,12 @@ static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* 
   const int N = (int)h->N;
   const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(h->plan[0].c32, h->lu_hi, h->lu_lo, N);
   const DeviceInfo& d = device_info();
+  // 128-thread CTAs (halved for small batches), as many per SM as shared
+  // memory holds.  The pair sweeps' policy (one 448-thread CTA per SM on the
+  // penta N = 512, M = 65536 batch) made this kernel slower there: 0.231 ->
+  // 0.275 ms.
+  auto ks = k_refine_factor<BW, D, true>;
+  auto kg = k_refine_factor<BW, D, false>;
   int tpb = 128;
   while (tpb > 32 && M < (int64_t)2 * d.sms * tpb) tpb /= 2;
   const size_t coef = (size_t)N * (FRefineRecs<BW>::R1 + FRefineRecs<BW>::R2) * sizeof(float4);
@@ -409,7 +415,7 @@ static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* 
   }
   const int64_t need = (M + tpb - 1) / tpb;
   if (grid > need) grid = need;
-  auto k = smem ? k_refine_factor<BW, D, true> : k_refine_factor<BW, D, false>;
+  auto k = smem ? ks : kg;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k<<<(int)grid, tpb, bytes, st>>>(cf, N, B, X, M);

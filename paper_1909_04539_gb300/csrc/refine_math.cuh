@@ -39,6 +39,29 @@ __device__ __forceinline__ float residual_row(float b, const float (&x)[W], cons
   return __fadd_rn(s, c);
 }
 
+// The same residual when the first term's coefficient is exactly 1 (ahi[0] =
+// 1, alo[0] = 0): that product needs no splitting, so the term is one TwoSum
+// (bitwise the value residual_row gives for finite inputs).
+template <int W>
+__device__ __forceinline__ float residual_row_unit(float b, const float (&x)[W], const float (&ahi)[W],
+                                                   const float (&alo)[W]) {
+  float s = __fsub_rn(b, x[0]);
+  const float bv0 = __fsub_rn(s, b);
+  float c = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bv0)), __fsub_rn(-x[0], bv0));
+#pragma unroll
+  for (int k = 1; k < W; k++) {
+    const float p = __fmul_rn(ahi[k], x[k]);
+    const float e = fmaf(ahi[k], x[k], -p);
+    const float t = __fsub_rn(s, p);
+    const float bv = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(-p, bv));
+    s = t;
+    c = __fadd_rn(c, __fsub_rn(err, e));
+    c = fmaf(-alo[k], x[k], c);
+  }
+  return __fadd_rn(s, c);
+}
+
 // pass 1: forward sweep of A = L U on the FP32 input b of row i
 template <int BW>
 __device__ __forceinline__ float refine_fwd(const RefineCoefs<BW>& cf, int i, float b, float& w1, float& w2) {
@@ -394,7 +417,7 @@ __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, con
         ah[W - 1] = c[u].ah[1];
         al[W - 1] = c[u].al[1];
       }
-      sig[u] = __fadd_rn(residual_row<W>(w[u], xs, ah, al), dl[u]);
+      sig[u] = __fadd_rn(residual_row_unit<W>(w[u], xs, ah, al), dl[u]);
     }
   }
   // backward sweep of the correction and the FP64 sum
