@@ -16,14 +16,31 @@
 //   2. one thread per (band, row) adds the partials of the CTAs that touched
 //      its row block, in CTA order.
 // The decomposition is a function of N, M and G only, so the result is
-// bitwise reproducible on a given device.  Work per unknown: `width` FP64
-// FMAs (the kernel is bound by the FP64 pipe on GB300), 16 bytes of
-// compulsory reads (GB and X; the X halo of 2h rows per row block comes
-// from L2).
+// bitwise reproducible on a given device.  16 bytes of compulsory reads per
+// unknown (GB and X; the X halo of 2h rows per row block comes from L2).
+//
+// Arithmetic of level 1.  FP64 data: one FP64 FMA per product (the kernel
+// is bound by the FP64 pipe).  FP32 data: a thread's products for one (band,
+// row) are summed in FP32 pairs over runs of kGradRun systems -- each product
+// exact by an FMA-based TwoProduct, added with Knuth's TwoSum, the rounding
+// errors collected in the low part -- and each run's pair is added, exactly
+// widened, to an FP64 sum: `width` products in FP32 arithmetic per unknown
+// instead of `width` FP64 FMAs (the FP64 pipe of GB300 runs at 1/64 of the
+// FP32 rate) and width / kGradRun FP64 additions.  A run of K products of
+// typical size t carries an error of about sqrt(K) 2^-48 t, so a sum of M
+// random-sign terms, of size sqrt(M) t, is off by about sqrt(K) 2^-48
+// relative (K = 16: ~1.4e-14).  Values outside [2^-32, 2^48) (besides zero)
+// could overflow or underflow the FP32 parts: a CTA that meets one in a
+// segment recomputes that segment with FP64 FMAs, so the result depends only
+// on the data.  (The same pairs for FP64 data, each value split into two
+// FP32 parts, measured slower than the FP64 FMAs: the splits cost about 20
+// integer instructions per value; penta N = 512, M = 65536: 0.33 - 0.48 ms
+// against 0.32 ms.)
 #include <climits>
 #include <mutex>
 #include <string>
 
+#include "df_math.cuh"
 #include "refine_math.cuh"
 #include "sweep_kernels.cuh"
 
@@ -69,17 +86,39 @@ size_t band_grad_scratch_bytes(int width, int N, int64_t M) {
 }
 
 template <typename T>
-__device__ __forceinline__ double load_wide(const T* p) {
+__device__ __forceinline__ double to_wide(T v) {
   if constexpr (sizeof(T) == 8)
-    return *p;
+    return v;
   else
-    return widen_exact(*p);  // integer-only widening: keeps the FP64 pipe for the FMAs
+    return widen_exact(v);  // integer-only widening: keeps the FP64 pipe for the FMAs
+}
+
+// FP32 data: products per (band, row) summed in pairs before one FP64
+// addition.
+constexpr int kGradRun = 16;
+
+// v is zero or 2^-32 <= |v| < 2^48 (the pair arithmetic's range here: the
+// products stay within [2^-64, 2^96) and a run's sums far from overflow)
+__device__ __forceinline__ bool grad_in_range(float v) {
+  const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
+  return b - ((127u - 32u) << 23) < (80u << 23) || b == 0u;
+}
+
+// a += g * x in pairs, not renormalised: a.h the running FP32 sum, a.l the
+// rounding errors of its additions (the product g * x = p + e is exact)
+__device__ __forceinline__ void grad_acc(df::Pair& a, float g, float x) {
+  const float p = df::mul(g, x);
+  const float e = df::fma_(g, x, -p);
+  float s, t;
+  df::two_sum(a.h, p, s, t);
+  a.h = s;
+  a.l = df::add(a.l, df::add(t, e));
 }
 
 // Level 1.  partial layout: [CTA][segment][band][row in block].
 // PER: periodic matrix, X rows taken modulo N.
 template <typename T, int W, bool PER>
-__global__ void __launch_bounds__(kGradThreads)
+__global__ void __launch_bounds__(kGradThreads, 2)
 k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
                     int64_t ss, double* __restrict__ partial) {
   constexpr int H = W / 2;
@@ -103,40 +142,84 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
     // rows i0 - H .. i0 + kGradRows - 1 + H of X and i0 .. of GB for system
     // j; the next system's rows are requested before the current ones are
     // used (two register sets), so each thread keeps one load batch in flight
-    // while its FMAs run
-    auto fetch = [&](int64_t j, double (&x)[NX], double (&g)[kGradRows]) {
+    // while its arithmetic runs
+    auto fetch = [&](int64_t j, T (&x)[NX], T (&g)[kGradRows]) {
 #pragma unroll
       for (int q = 0; q < NX; q++) {
         const int row = i0 - H + q;
         if constexpr (PER) {
           const int pr = ((row % N) + N) % N;
-          x[q] = load_wide(X + pr * rs + j * ss);
+          x[q] = X[pr * rs + j * ss];
         } else {
-          x[q] = (row >= 0 && row < N) ? load_wide(X + row * rs + j * ss) : 0.0;
+          x[q] = (row >= 0 && row < N) ? X[row * rs + j * ss] : T(0);
         }
       }
 #pragma unroll
       for (int r = 0; r < kGradRows; r++) {
         const int row = i0 + r;
-        g[r] = (row < N) ? load_wide(GB + row * rs + j * ss) : 0.0;
+        g[r] = (row < N) ? GB[row * rs + j * ss] : T(0);
       }
     };
-    auto accumulate = [&](const double (&x)[NX], const double (&g)[kGradRows]) {
-#pragma unroll
-      for (int r = 0; r < kGradRows; r++)
-#pragma unroll
-        for (int k = 0; k < W; k++) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
+    // the segment's systems in the order fetch / use, over both register sets
+    auto sweep = [&](auto use) {
+      T xa[NX], ga[kGradRows], xb[NX], gb[kGradRows];
+      int64_t j = jlo + threadIdx.x;
+      if (j < jhi) fetch(j, xa, ga);
+      for (; j < jhi; j += 2 * kGradThreads) {
+        const int64_t j1 = j + kGradThreads;
+        if (j1 < jhi) fetch(j1, xb, gb);
+        use(xa, ga);
+        if (j1 >= jhi) break;
+        if (j1 + kGradThreads < jhi) fetch(j1 + kGradThreads, xa, ga);
+        use(xb, gb);
+      }
     };
-    double xa[NX], ga[kGradRows], xb[NX], gb[kGradRows];
-    int64_t j = jlo + threadIdx.x;
-    if (j < jhi) fetch(j, xa, ga);
-    for (; j < jhi; j += 2 * kGradThreads) {
-      const int64_t j1 = j + kGradThreads;
-      if (j1 < jhi) fetch(j1, xb, gb);
-      accumulate(xa, ga);
-      if (j1 >= jhi) break;
-      if (j1 + kGradThreads < jhi) fetch(j1 + kGradThreads, xa, ga);
-      accumulate(xb, gb);
+    auto fp64 = [&]() {
+#pragma unroll
+      for (int v = 0; v < NV; v++) acc[v] = 0.0;
+      sweep([&](const T (&x)[NX], const T (&g)[kGradRows]) {
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++)
+#pragma unroll
+          for (int k = 0; k < W; k++)
+            acc[k * kGradRows + r] = fma(to_wide(g[r]), to_wide(x[r + k]), acc[k * kGradRows + r]);
+      });
+    };
+    if constexpr (sizeof(T) == 8) {
+      fp64();
+    } else {
+      // pairs, runs of kGradRun systems
+      bool bad = false;
+      df::Pair pa[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) pa[v] = df::Pair{0.f, 0.f};
+      int run = 0;
+      auto flush = [&]() {
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          acc[v] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+          pa[v] = df::Pair{0.f, 0.f};
+        }
+      };
+      sweep([&](const T (&x)[NX], const T (&g)[kGradRows]) {
+        bool in = true;
+#pragma unroll
+        for (int q = 0; q < NX; q++) in &= grad_in_range(x[q]);
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++) in &= grad_in_range(g[r]);
+        bad |= !in;
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++)
+#pragma unroll
+          for (int k = 0; k < W; k++) grad_acc(pa[k * kGradRows + r], g[r], x[r + k]);
+        if (++run == kGradRun) {
+          flush();
+          run = 0;
+        }
+      });
+      flush();
+      // a value outside the pairs' range anywhere in the segment: FP64 FMAs
+      if (__syncthreads_or(bad)) fp64();
     }
     // Warp reduce-scatter over the NV values (padded to 64): at each level a
     // lane keeps one half, sends the other to its partner and adds what it
