@@ -1,18 +1,21 @@
 """GPU parity of the fused ADI half-steps (explicit second difference across
-systems + shared tridiagonal solve) against the oracle, both axes, FP64
-(1e-12) and FP32 (2e-5), forward and adjoint; the autograd wrapper against
-finite differences.  The adjoint half-step S^{-T} (I + r d2) u is checked
-against the oracle's transposed half-step (oracle.adi_halfstep_bands) with a
-non-symmetric S, where it differs from the forward map, on grids whose lines
-run row-partitioned, and on the full 4096^2 grid, per line (the largest
-relative L2 error of one grid line)."""
+systems + shared tridiagonal solve) against the oracle, both axes, forward
+and adjoint; the autograd wrapper against finite differences.  Every check
+bounds the grid's relative L2 error and the relative max-norm error of every
+grid line solved as one system (tests.dense.parity): FP64 1e-12, FP32 the
+bound of one FP32 solve (tests.dense.tol32) for the explicit operator and
+for the solve of each half-step.  The adjoint half-step S^{-T} (I + r d2) u
+is checked against the oracle's transposed half-step
+(oracle.adi_halfstep_bands) with a non-symmetric S, where it differs from
+the forward map, on grids whose lines run row-partitioned, and on the full
+4096^2 grid."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
-from tests.dense import rel_l2, second_difference, sys_rel_err
+from tests.dense import parity, rel_l2, second_difference, tol32
 
 pytestmark = pytest.mark.gpu
 
@@ -25,14 +28,20 @@ def bs():
     return m
 
 
+def _lines(axis):
+    """The systems of a half-step as a layout of the (ny, nx) grid: grid rows
+    for axis 0 (solved along x), grid columns for axis 1."""
+    return "strided" if axis == 0 else "interleaved"
+
+
 def _factor(bs, n, r):
     return bs.Factor(synth.adi_bands(n, r))
 
 
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("ny,nx", [(1, 1), (3, 5), (33, 17), (100, 64), (70, 257), (1000, 777), (777, 1000)])
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
-def test_adi_halfstep(bs, axis, ny, nx, dtype, tol):
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adi_halfstep(bs, axis, ny, nx, dtype):
     r = 0.5
     n = nx if axis == 0 else ny
     if n < 2:
@@ -44,7 +53,8 @@ def test_adi_halfstep(bs, axis, ny, nx, dtype, tol):
     f = _factor(bs, n, r)
     out = bs.adi_halfstep(f, torch.tensor(u, dtype=dtype, device="cuda"), r, axis)
     torch.cuda.synchronize()
-    assert rel_l2(out.double().cpu().numpy(), oracle.adi_halfstep(u, r, axis)) < tol
+    tol = 1e-12 if dtype == torch.float64 else tol32(synth.adi_bands(n, r), ops=2)
+    parity(out.double().cpu().numpy(), oracle.adi_halfstep(u, r, axis), tol, _lines(axis))
 
 
 @pytest.mark.parametrize("axis", [0, 1])
@@ -64,13 +74,14 @@ def test_adi_adjoint_is_transpose(bs, axis):
     I = np.eye(nx * ny)
     Kxx, Kyy = np.kron(np.eye(ny), Dx), np.kron(Dy, np.eye(nx))
     T = np.linalg.solve(I - r * Kxx, I + r * Kyy) if axis == 0 else np.linalg.solve(I - r * Kyy, I + r * Kxx)
-    assert rel_l2(adj.ravel(), T.T @ g.ravel()) < 1e-12
+    parity(adj, (T.T @ g.ravel()).reshape(ny, nx), 1e-12, _lines(axis))
 
 
 def test_adi_full_grid_4096(bs):
     """The 4096 x 4096 heat-equation grid, r = 0.5, u ~ U(-1,1) (seed 0): one
     full Peaceman-Rachford step (x-implicit then y-implicit) in FP64 against
-    the oracle on the whole grid, and in FP32 within 2e-5."""
+    the oracle on the whole grid, and in FP32 within the bound of four FP32
+    operations (two explicit operators, two solves)."""
     n, r = 4096, 0.5
     f = _factor(bs, n, r)
     u = synth.adi_field(n, 0, "cuda")
@@ -81,9 +92,9 @@ def test_adi_full_grid_4096(bs):
     torch.cuda.synchronize()
     uh = u.cpu().numpy()
     ref = oracle.adi_halfstep(oracle.adi_halfstep(uh, r, 0), r, 1)
-    assert rel_l2(full.cpu().numpy(), ref) < 1e-12
+    parity(full.cpu().numpy(), ref, 1e-12, _lines(1))
     ref32 = oracle.adi_halfstep(oracle.adi_halfstep(u32.double().cpu().numpy(), r, 0), r, 1)
-    assert rel_l2(full32.double().cpu().numpy(), ref32) < 2e-5
+    parity(full32.double().cpu().numpy(), ref32, tol32(synth.adi_bands(n, r), ops=4), _lines(1))
 
 
 def test_adi_autograd_finite_differences(bs):
@@ -109,17 +120,11 @@ def test_adi_autograd_finite_differences(bs):
     assert abs(analytic - fd) < 1e-7 * (1 + abs(fd))
 
 
-def _line_err(out, ref, axis):
-    """Largest relative error of one system: grid rows for axis 0 (solved
-    along x), grid columns for axis 1."""
-    return sys_rel_err(out, ref, "strided" if axis == 0 else "interleaved")
-
-
 @pytest.mark.parametrize("partition", [2, 1])
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("adjoint", [False, True])
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
-def test_adi_nonsymmetric_operator_vs_oracle(bs, axis, adjoint, partition, dtype, tol):
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adi_nonsymmetric_operator_vs_oracle(bs, axis, adjoint, partition, dtype):
     """A non-symmetric diagonally dominant implicit operator S on a 400 x 1024
     grid (lines of 1024 or 400 rows: row-partitioned with partition = 2),
     forward S^{-1} E u and adjoint S^{-T} E u against the oracle per line."""
@@ -139,8 +144,7 @@ def test_adi_nonsymmetric_operator_vs_oracle(bs, axis, adjoint, partition, dtype
         bs.set_option(bs.OPT_PARTITION, 0)
     ref = oracle.adi_halfstep_bands(u, r, bands, axis, transpose=adjoint)
     out = out.double().cpu().numpy()
-    assert rel_l2(out, ref) < tol
-    assert _line_err(out, ref, axis) < tol
+    parity(out, ref, 1e-12 if dtype == torch.float64 else tol32(bands, ops=2), _lines(axis))
     if adjoint:  # really the transpose: the forward map differs
         assert rel_l2(oracle.adi_halfstep_bands(u, r, bands, axis), ref) > 1e-3
 
@@ -157,7 +161,5 @@ def test_adi_adjoint_full_grid_4096(bs, axis):
     adj = bs.adi_halfstep(f, u, r, axis, adjoint=True)
     torch.cuda.synchronize()
     ref = oracle.adi_halfstep_bands(u.cpu().numpy(), r, bands, axis, transpose=True)
-    out = adj.cpu().numpy()
-    assert rel_l2(out, ref) < 1e-12
-    assert _line_err(out, ref, axis) < 1e-12
+    parity(adj.cpu().numpy(), ref, 1e-12, _lines(axis))
 

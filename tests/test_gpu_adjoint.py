@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from tests.dense import rel_l2
+from tests.dense import parity, rel_l2, tol32
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +46,7 @@ def test_adjoint_and_band_grad_fp64(bs, width, N, M, layout):
     G, db = bs.solve_adjoint(f, G, layout, X=X)
     torch.cuda.synchronize()
     GB = G.cpu().numpy()
-    assert rel_l2(GB, _to(GBref, layout)) < 1e-12
+    parity(GB, _to(GBref, layout), 1e-12, layout)
     assert rel_l2(db.cpu().numpy(), dref) < 1e-12
 
 
@@ -60,7 +60,7 @@ def test_adjoint_fp32(bs, width):
     G = torch.tensor(Gh, dtype=torch.float32, device="cuda")
     bs.solve_adjoint(f, G)
     torch.cuda.synchronize()
-    assert rel_l2(G.double().cpu().numpy(), oracle.solve_adjoint(bands, Gh)) < 2e-5
+    parity(G.double().cpu().numpy(), oracle.solve_adjoint(bands, Gh), tol32(bands))
 
 
 def test_band_grad_deterministic(bs):
@@ -109,3 +109,39 @@ def test_autograd_against_finite_differences(bs, width):
     GB = oracle.solve_adjoint(bands0, W)
     assert rel_l2(B.grad.cpu().numpy(), GB) < 1e-12
     assert rel_l2(bands.grad.numpy(), oracle.band_grad(width, GB, oracle.solve(bands0, B0))) < 1e-12
+
+
+def _band_abs_bound(width, GB, X):
+    """sum_j |GB[i, j]| |X[i + k - h, j]| per band entry: the scale a rounding
+    error of the reduction is measured against."""
+    return oracle.band_grad(width, np.abs(GB), np.abs(X)) * -1.0
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "strided"])
+@pytest.mark.parametrize("width", [3, 5])
+@pytest.mark.parametrize("case", ["in_range", "huge", "tiny", "zeros"])
+def test_band_grad_fp32_data(bs, width, layout, case):
+    """FP32 band gradient (pair sums over runs of systems, FP64 sums of the
+    runs) against the oracle on the same FP32 values widened to FP64: within
+    1e-12 of the absolute-value sums per entry.  'huge' and 'tiny' put one
+    value outside [2^-32, 2^48), which sends the CTAs that meet it to FP64
+    FMAs; 'zeros' zeroes whole rows and systems."""
+    N, M = 301, 5003
+    rng = np.random.default_rng(width + 17)
+    GB = rng.uniform(-1, 1, (N, M)).astype(np.float32)
+    X = rng.uniform(-1, 1, (N, M)).astype(np.float32)
+    if case == "huge":
+        GB[7, 123] = 2.0 ** 60
+    elif case == "tiny":
+        X[150, 4000] = 2.0 ** -40
+    elif case == "zeros":
+        GB[10:20, :] = 0.0
+        X[:, 100:300] = 0.0
+    ref = oracle.band_grad(width, GB.astype(np.float64), X.astype(np.float64))
+    scale = _band_abs_bound(width, GB.astype(np.float64), X.astype(np.float64))
+    f = bs.Factor(_bands(width, N, 3))
+    db = bs.band_grad(f, torch.tensor(_to(GB, layout), device="cuda"), torch.tensor(_to(X, layout), device="cuda"),
+                      layout)
+    got = db.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300)
+    assert rel_l2(got, ref) < 1e-12

@@ -1,11 +1,11 @@
 """GPU parity of the plain sweeps against the CPU FP64 oracle, through the C
-ABI.  Tolerances (relative L2 over the whole batch):
+ABI.  Every check bounds both the relative L2 error of the batch and the
+relative max-norm error of every system (tests.dense.parity):
   FP64: 1e-12 (the stated target for every FP64 path);
-  FP32 storage and arithmetic: 2e-5 -- the matrices here are diagonally
-    dominant with condition numbers below ~10, so a forward-stable sweep in
-    FP32 (u = 6e-8) lands within ~10 kappa u;
+  FP32 storage and arithmetic: width * kappa_inf(A) * 2^-24 per matrix
+    (tests.dense.tol32; ~1e-6 for the matrices here);
   BF16 storage, FP32 arithmetic: compared with the oracle's solve of the
-    BF16-rounded B, so only the FP32 arithmetic differs: 2e-5.
+    BF16-rounded B, so only the FP32 arithmetic differs: the same bound.
 """
 import numpy as np
 import pytest
@@ -13,11 +13,11 @@ import torch
 
 import oracle
 import synth
-from tests.dense import rel_l2
+from tests.dense import parity, tol32
 
 pytestmark = pytest.mark.gpu
 
-TOL64, TOL32 = 1e-12, 2e-5
+TOL64 = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +55,7 @@ def test_config0_random_tri_fp64(bs):
         B_in = Bh if layout == "interleaved" else np.ascontiguousarray(Bh.T)
         X = _gpu_solve(bs, f, B_in, torch.float64, layout)
         ref = oracle.solve(bands, B_in, layout)
-        assert rel_l2(X, ref) < TOL64, (layout, rel_l2(X, ref))
+        parity(X, ref, TOL64, layout)
 
 
 SHAPES = [(3, 2, 1), (3, 2, 5), (3, 3, 7), (3, 33, 31), (3, 100, 1000), (3, 257, 1027), (3, 64, 4096),
@@ -69,7 +69,7 @@ def test_fp64_ragged(bs, width, N, M, layout):
     Bh = _rhs(N, M, M, layout)
     f = bs.Factor(bands)
     X = _gpu_solve(bs, f, Bh, torch.float64, layout)
-    assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL64
+    parity(X, oracle.solve(bands, Bh, layout), TOL64, layout)
 
 
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
@@ -79,7 +79,7 @@ def test_fp32_ragged(bs, width, N, M, layout):
     Bh = _rhs(N, M, M + 1, layout).astype(np.float32).astype(np.float64)
     f = bs.Factor(bands)
     X = _gpu_solve(bs, f, Bh, torch.float32, layout)
-    assert rel_l2(X, oracle.solve(bands, Bh, layout)) < TOL32
+    parity(X, oracle.solve(bands, Bh, layout), tol32(bands), layout)
 
 
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
@@ -92,7 +92,7 @@ def test_bf16_storage(bs, width, N, M, layout):
     X = bs.solve_bf16(f, B, layout=layout)
     torch.cuda.synchronize()
     ref = oracle.solve(bands, B.double().cpu().numpy(), layout)
-    assert rel_l2(X.double().cpu().numpy(), ref) < TOL32
+    parity(X.double().cpu().numpy(), ref, tol32(bands), layout)
 
 
 def test_misaligned_pointer_uses_scalar_path(bs):
@@ -106,7 +106,7 @@ def test_misaligned_pointer_uses_scalar_path(bs):
     f = bs.Factor(bands)
     bs.solve(f, B)
     torch.cuda.synchronize()
-    assert rel_l2(B.cpu().numpy(), oracle.solve(bands, Bh)) < TOL64
+    parity(B.cpu().numpy(), oracle.solve(bands, Bh), TOL64)
     assert buf[0].item() == 0.0
 
 
@@ -123,7 +123,7 @@ def test_solve_leaves_other_memory_alone(bs):
     bs.solve(f, B)
     torch.cuda.synchronize()
     assert torch.all(buf[:pad] == 12345.0) and torch.all(buf[pad + N * M:] == 12345.0)
-    assert rel_l2(B.cpu().numpy(), oracle.solve(bands, Bh)) < TOL64
+    parity(B.cpu().numpy(), oracle.solve(bands, Bh), TOL64)
 
 
 def test_deterministic(bs):
@@ -163,7 +163,7 @@ def test_config1_penta_full_size_sampled(bs):
     cols = np.union1d(cols, [0, 1, M - 2, M - 1])
     Bs = B0[:, cols].cpu().numpy()
     ref = oracle.solve(bands, Bs)
-    assert rel_l2(X[:, cols].cpu().numpy(), ref) < TOL64
+    parity(X[:, cols].cpu().numpy(), ref, TOL64)
     # every system: relative residual with the banded product on the GPU in FP64
     b = torch.tensor(bands, device="cuda")
     R = B0.clone()
@@ -175,7 +175,8 @@ def test_config1_penta_full_size_sampled(bs):
     X32 = B0.float()
     bs.solve(f, X32)
     torch.cuda.synchronize()
-    assert rel_l2(X32[:, cols].double().cpu().numpy(), ref) < TOL32
+    ref32 = oracle.solve(bands, B0[:, cols].float().double().cpu().numpy())
+    parity(X32[:, cols].double().cpu().numpy(), ref32, tol32(bands))
 
 
 @pytest.mark.parametrize("width,N,M", [(3, 64, 1024), (3, 1000, 4100), (3, 1024, 8192), (5, 512, 4096),
@@ -183,7 +184,7 @@ def test_config1_penta_full_size_sampled(bs):
 def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
     """FP32 and BF16-input solves and FP32 adjoints through the on-chip TMA
     kernel (option 2) and the streaming kernels (option 1) give the oracle's
-    answer within 2e-5, and the device status stays clean."""
+    answer within the FP32 bound, and the device status stays clean."""
     from paper_1909_04539_gb300 import api
     bands = _bands(width, N, 3 * N + M)
     Bh = np.random.default_rng(M).uniform(-1, 1, (N, M))
@@ -204,9 +205,12 @@ def test_onchip_kernel_matches_streaming_and_oracle(bs, width, N, M):
     B32 = Bh.astype(np.float32).astype(np.float64)
     Bb = torch.tensor(Bh, dtype=torch.bfloat16).double().numpy()
     ref, refa, refb = oracle.solve(bands, B32), oracle.solve_adjoint(bands, B32), oracle.solve(bands, Bb)
+    tol = tol32(bands)
     for kern in (2, 1):
         X, Y, Xb = outs[kern]
-        assert rel_l2(X, ref) < TOL32 and rel_l2(Y, refa) < TOL32 and rel_l2(Xb, refb) < TOL32
+        parity(X, ref, tol)
+        parity(Y, refa, tol)
+        parity(Xb, refb, tol)
     assert bs.device_status() == 0
 
 
@@ -229,4 +233,4 @@ def test_cta_threads_option(bs, width, N, M, dtype, cta):
         torch.cuda.synchronize()
     finally:
         bs.set_option(bs.OPT_CTA_THREADS, 0)
-    assert rel_l2(X.double().cpu().numpy(), oracle.solve(bands, Bh)) < (TOL64 if dtype == torch.float64 else TOL32)
+    parity(X.double().cpu().numpy(), oracle.solve(bands, Bh), TOL64 if dtype == torch.float64 else tol32(bands))
