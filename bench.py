@@ -59,10 +59,11 @@ NCU_TRAFFIC = {
     "refine_solve": {"bytes": 356485376 + 437087488, "sha": "f8df3951d185c4cf"},
 }
 KERNEL_SOURCES = {
-    "f64_solve": ["sweep_df.cu", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
-    "adjoint_f64": ["sweep_df.cu", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
+    "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
+    "adjoint_f64": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h",
+                    "solve_api.cu"],
     "refine_solve": ["refine.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
-    "band_grad_f64": ["band_grad.cu", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
+    "band_grad_f64": ["band_grad.cu", "df_math.cuh", "refine_math.cuh", "sweep_kernels.cuh", "internal.h"],
 }
 
 
