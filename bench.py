@@ -41,8 +41,7 @@ N_ROWS, M_SYS, S_HYPER = 512, 65536, 0.1
 METRIC = "unknowns/s & HBM GB/s vs 8 TB/s at stated rel err; serving p50/p99 latency"
 WORKLOAD = ("penta A=I+0.1*D4 clamped, N=512, M=65536 RHS ~ N(0,1) per GPU, interleaved; "
             "step = FP64 solve + FP32-stored solve with one FP64-accurate refinement step + "
-            "FP64 adjoint solve + band-gradient reduction (FP64 solve, adjoint and band gradient in "
-            "order on a high-priority stream; the mixed-precision solve beside them on a low-priority one)")
+            "FP64 adjoint solve + band-gradient reduction, in that order on one stream")
 NOMINAL_HBM_GBS = 8000.0
 
 
@@ -53,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 864354560 + 83456, "sha": "7ba2374f98630563"},
-    "f64_solve": {"bytes": None, "sha": ""},
-    "adjoint_f64": {"bytes": None, "sha": ""},
-    "refine_solve": {"bytes": 356485376 + 437087488, "sha": "f8df3951d185c4cf"},
+    "band_grad_f64": {"bytes": 863069696 + 92672, "sha": "a060a44a197aefec"},
+    "f64_solve": {"bytes": 470564096 + 434477056, "sha": "086820ffa32b22a3"},
+    "adjoint_f64": {"bytes": 463844352 + 427795456, "sha": "086820ffa32b22a3"},
+    "refine_solve": {"bytes": 355203072 + 435953408, "sha": "595a7f6d93338dc1"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
@@ -241,13 +240,14 @@ def run_ours(args):
     # per step and path: a start and an end event on the path's own stream
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
           for _ in range(args.steps)]
-    # The mixed-precision solve is independent of the FP64 chain (solve,
-    # adjoint, band gradient, which need the FP64 pipe) and mostly uses the
-    # FP32 and integer pipes, so it runs on a low-priority stream beside the
-    # chain, which runs in order on a high-priority stream.
-    lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
-    s_chain = torch.cuda.Stream(priority=hi)
-    s_ref = torch.cuda.Stream(priority=lo)
+    # The four kernels run in order on one stream.  (The mixed-precision
+    # solve is independent of the others; run beside them on a second,
+    # low-priority stream it saved nothing -- each kernel fills the GPU's
+    # issue slots or its FP64 pipe on its own, 0.889 ms per step either way
+    # -- and its sharing of the SMs stretched the other kernels' in-step
+    # durations.)
+    s_chain = torch.cuda.Stream()
+    s_ref = s_chain
     fork = [torch.cuda.Event() for _ in range(2)]
 
     def timed(e, q, stream, fn):
@@ -260,13 +260,11 @@ def run_ours(args):
         fk = fork[(k or 0) % 2]
         fk.record(st)
         s_chain.wait_event(fk)
-        s_ref.wait_event(fk)
         timed(e, 0, s_chain, lambda: bs.solve(f, X64, stream=s_chain))
+        timed(e, 1, s_chain, lambda: bs.solve_refine(f, B32, XR, stream=s_chain))
         timed(e, 2, s_chain, lambda: bs.solve_adjoint(f, G, stream=s_chain))
         timed(e, 3, s_chain, lambda: bs.band_grad(f, G, X64, dbands=db, stream=s_chain))
-        timed(e, 1, s_ref, lambda: bs.solve_refine(f, B32, XR, stream=s_ref))
         st.wait_stream(s_chain)
-        st.wait_stream(s_ref)
 
     for _ in range(args.warmup):
         step()
@@ -295,9 +293,8 @@ def run_ours(args):
     units_step = 3 * N * M  # three solves of N*M unknowns each: FP64, mixed precision, adjoint
     value = job_value(units_step, world, ms_step)
 
-    # Each kernel of the step timed alone right after the timed region (same
-    # data and streams; the in-step durations of the concurrent kernels share
-    # the SMs, so the per-kernel rooflines use these)
+    # Each kernel of the step also timed alone, back to back, right after the
+    # timed region (same data and stream)
     alone = {
         "f64_solve": time_alone(lambda: bs.solve(f, X64, stream=s_chain), s_chain, reps=20),
         "refine_solve": time_alone(lambda: bs.solve_refine(f, B32, XR, stream=s_ref), s_ref, reps=20),
@@ -339,11 +336,8 @@ def run_ours(args):
             p["fp64_fma_per_s"] = p["dp_fma"] / t_alone
             p["fp64_frac_of_derived_peak"] = p["fp64_fma_per_s"] / fp64_fma_derived
             p["fp64_frac_of_live_rate"] = p["fp64_fma_per_s"] / fp64_fma_live
-    paths["refine_solve"]["stream"] = "low priority, concurrent with the FP64 chain"
-    # the dominant kernel: the longest share of the FP64 chain, which sets the
-    # step time (the mixed-precision solve runs beside it on a low-priority
-    # stream, its in-step duration stretched by that sharing)
-    dom = max(("f64_solve", "adjoint_f64", "band_grad_f64"), key=lambda n: per[n])
+    # the dominant kernel: the longest share of the step
+    dom = max(names, key=lambda n: per[n])
     dp = paths[dom]
     t_dom = per[dom] * 1e-3
     ach = dp["bytes"] / t_dom / 1e9
