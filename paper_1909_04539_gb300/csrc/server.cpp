@@ -19,7 +19,11 @@
 // requests never queue behind the multi-millisecond copies of a large batch.
 // Inside a batch the copies go smallest first and every request has its own
 // completion event after its device-to-host copy: it finishes as soon as its
-// own results are back, not when the whole batch is.
+// own results are back, not when the whole batch is.  Each stream has a
+// launcher thread that issues its batches' copies and graph replay, so the
+// worker thread, which admits requests and observes completions, never waits
+// while the hundreds of copy pieces of a large batch are queued (issuing them
+// can block once the stream's command queue is full).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -134,6 +138,13 @@ struct Slot {
   std::vector<int64_t> reqs;        // the batch's requests, in copy order
   std::vector<cudaEvent_t> ev;      // per request: its device-to-host copy done
   std::vector<char> finished;       // per request: completion recorded
+  // launcher thread: busy && !issued while the batch's copies and replay are
+  // being queued on the stream (rp: the batch's requests); launch_err is its
+  // outcome
+  std::thread launcher;
+  bool issued = false;
+  std::vector<Req*> rp;
+  cudaError_t launch_err = cudaSuccess;
 };
 
 }  // namespace
@@ -280,7 +291,18 @@ void worker_loop(bs_server s) {
     // completions: each request as soon as its own copy back is done; the
     // slot when the whole batch is
     for (Slot& sl : s->slots) {
-      if (!sl.busy) continue;
+      if (!sl.busy || !sl.issued) continue;
+      if (sl.launch_err != cudaSuccess) {  // nothing of this batch can be trusted: fail its requests
+        s->sticky = sl.launch_err;
+        const double t = now_s();
+        for (int64_t id : sl.reqs) finish_request(s, s->reqs[id], false, t);
+        sl.reqs.clear();
+        sl.finished.clear();
+        sl.rp.clear();
+        sl.busy = false;
+        progressed = true;
+        continue;
+      }
       for (size_t q = 0; q < sl.reqs.size(); q++) {
         if (sl.finished[q]) continue;
         const cudaError_t eq = cudaEventQuery(sl.ev[q]);
@@ -298,6 +320,7 @@ void worker_loop(bs_server s) {
       if (q != cudaSuccess) s->sticky = q;
       sl.reqs.clear();
       sl.finished.clear();
+      sl.rp.clear();
       sl.busy = false;
       progressed = true;
     }
@@ -318,27 +341,20 @@ void worker_loop(bs_server s) {
           s->cv.notify_all();  // failures injected at admission are final
           continue;
         }
-        // copies and the graph launch run without the lock (the slot and the
-        // admitted requests belong to this thread now: cancel and release
-        // refuse admitted requests, and map entries keep their addresses)
-        std::vector<Req*> rp;
-        for (int64_t id : ids) rp.push_back(&s->reqs.find(id)->second);
-        lk.unlock();
-        const cudaError_t e = launch_batch(s, sl, rp);
-        lk.lock();
-        progressed = true;
-        if (e != cudaSuccess) {  // nothing of this batch can be trusted: fail its requests
-          s->sticky = e;
-          cudaStreamSynchronize(sl.st);
-          const double t = now_s();
-          for (int64_t id : ids) finish_request(s, s->reqs[id], false, t);
-          s->cv.notify_all();
-          continue;
-        }
+        // the slot's launcher thread queues the copies and the graph replay
+        // without the lock (the slot and the admitted requests belong to it
+        // until it sets `issued`: cancel and release refuse admitted
+        // requests, and map entries keep their addresses)
+        sl.rp.clear();
+        for (int64_t id : ids) sl.rp.push_back(&s->reqs.find(id)->second);
         sl.reqs = ids;
         sl.finished.assign(ids.size(), 0);
+        sl.issued = false;
+        sl.launch_err = cudaSuccess;
         sl.busy = true;
+        progressed = true;
         s->batches++;
+        s->cv.notify_all();  // wakes the slot's launcher
         if ((int64_t)ids.size() > s->max_batch_reqs) s->max_batch_reqs = (int64_t)ids.size();
       }
       int busy = 0;
@@ -353,6 +369,24 @@ void worker_loop(bs_server s) {
       else
         s->cv.wait_for(lk, std::chrono::milliseconds(5));
     }
+  }
+}
+
+// One per slot: queues each batch handed to the slot (busy && !issued).
+void launcher_loop(bs_server s, Slot* sl) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    s->cv.wait(lk, [&] { return s->stop || (sl->busy && !sl->issued); });
+    if (!(sl->busy && !sl->issued)) break;  // stopping, nothing handed over
+    const std::vector<Req*> rp = sl->rp;
+    lk.unlock();
+    cudaError_t e = launch_batch(s, *sl, rp);
+    if (e != cudaSuccess) cudaStreamSynchronize(sl->st);
+    lk.lock();
+    sl->launch_err = e;
+    sl->issued = true;
+    s->cv.notify_all();
   }
 }
 
@@ -423,6 +457,7 @@ bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* ou
     destroy_server(s);
     return cuda_error(e, "bs_server_create");
   }
+  for (Slot& sl : s->slots) sl.launcher = std::thread(launcher_loop, s, &sl);
   s->worker = std::thread(worker_loop, s);
   *out = s;
   return BS_OK;
@@ -436,6 +471,8 @@ bs_status bs_server_destroy(bs_server s) {
   }
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  for (Slot& sl : s->slots)
+    if (sl.launcher.joinable()) sl.launcher.join();
   destroy_server(s);
   return BS_OK;
 }
