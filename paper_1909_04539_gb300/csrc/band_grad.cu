@@ -35,7 +35,10 @@
 // on the data.  (The same pairs for FP64 data, each value split into two
 // FP32 parts, measured slower than the FP64 FMAs: the splits cost about 20
 // integer instructions per value; penta N = 512, M = 65536: 0.33 - 0.48 ms
-// against 0.32 ms.)
+// against 0.32 ms.  So did a layout for interleaved data in which a warp
+// reads one row of 32 systems and sums each row's products over its lanes
+// with shuffles, in pairs: 0.44 ms (FP32 data 0.37 ms) -- the per-row
+// butterfly costs ~250 warp instructions per 32 unknowns.)
 #include <climits>
 #include <mutex>
 #include <string>
