@@ -19,8 +19,9 @@
 // bitwise reproducible on a given device.  16 bytes of compulsory reads per
 // unknown (GB and X; the X halo of 2h rows per row block comes from L2).
 //
-// Arithmetic of level 1.  FP64 data: one FP64 FMA per product (the kernel
-// is bound by the FP64 pipe).  FP32 data: a thread's products for one (band,
+// Arithmetic of level 1.  FP64 data: one FP64 FMA per product for all bands
+// but the top one, whose products are summed in FP32 pairs (see
+// kGradPairBands5; the kernel is bound by the FP64 pipe).  FP32 data: a thread's products for one (band,
 // row) are summed in FP32 pairs over runs of kGradRun systems -- each product
 // exact by an FMA-based TwoProduct, added with Knuth's TwoSum, the rounding
 // errors collected in the low part -- and each run's pair is added, exactly
@@ -107,6 +108,42 @@ __device__ __forceinline__ bool grad_in_range(float v) {
   return b - ((127u - 32u) << 23) < (80u << 23) || b == 0u;
 }
 
+// FP64 data: zero or 2^-32 <= |v| < 2^48, and v as a pair (|v - (h + l)| <=
+// 2^-48 |v|)
+__device__ __forceinline__ bool grad_in_range(double v) {
+  const uint32_t hw = df::hiword(v) & 0x7fffffffu;
+  return hw - ((1023u - 32u) << 20) < (80u << 20) || (hw | df::loword(v)) == 0u;
+}
+__device__ __forceinline__ df::Pair grad_pair(double v) {
+  df::Pair y;
+  if (!df::split_fast(v, y)) y = df::Pair{0.f, 0.f};  // in range: zero
+  return y;
+}
+
+// FP64 data: the products of the top kGradPairBands bands (of 5; 3-band
+// matrices: kGradPairBands3) are summed in FP32 pairs as for FP32 data --
+// each value split once, the product a TwoProduct plus the two cross terms
+// -- and the others with FP64 FMAs, so that the FP32 and integer pipes take
+// part of the work the FP64 pipe bounds.  Measured (penta N = 512,
+// M = 65536, ms): 0 pair bands 0.321, 1: 0.281, 2: 0.295, 3: 0.329 -- the
+// splits (~16 integer instructions per value, whichever band they serve) make
+// more pair bands cost more issue slots than they save FP64 ones.  Tri
+// N = 1024, M = 2^18: 0 pair bands 1.435 ms, 1: 1.287 ms.
+constexpr int kGradPairBands5 = 1;
+constexpr int kGradPairBands3 = 1;
+
+// a += g * x for pairs of FP64 values, not renormalised
+__device__ __forceinline__ void grad_acc(df::Pair& a, df::Pair g, df::Pair x) {
+  const float p = df::mul(g.h, x.h);
+  float e = df::fma_(g.h, x.h, -p);
+  e = df::fma_(g.h, x.l, e);
+  e = df::fma_(g.l, x.h, e);
+  float s, t;
+  df::two_sum(a.h, p, s, t);
+  a.h = s;
+  a.l = df::add(a.l, df::add(t, e));
+}
+
 // a += g * x in pairs, not renormalised: a.h the running FP32 sum, a.l the
 // rounding errors of its additions (the product g * x = p + e is exact)
 __device__ __forceinline__ void grad_acc(df::Pair& a, float g, float x) {
@@ -188,8 +225,57 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
             acc[k * kGradRows + r] = fma(to_wide(g[r]), to_wide(x[r + k]), acc[k * kGradRows + r]);
       });
     };
-    if constexpr (sizeof(T) == 8) {
+    constexpr int KP = (sizeof(T) == 8) ? (W == 5 ? kGradPairBands5 : kGradPairBands3) : 0;
+    if constexpr (sizeof(T) == 8 && KP == 0) {
       fp64();
+    } else if constexpr (sizeof(T) == 8) {
+      // bands 0 .. W-KP-1 with FP64 FMAs, the top KP bands in pairs (runs of
+      // kGradRun systems, then FP64 sums of the runs)
+      constexpr int K0 = W - KP;
+      bool bad = false;
+      df::Pair pa[KP * kGradRows];
+#pragma unroll
+      for (int v = 0; v < KP * kGradRows; v++) pa[v] = df::Pair{0.f, 0.f};
+#pragma unroll
+      for (int v = 0; v < NV; v++) acc[v] = 0.0;
+      int run = 0;
+      auto flush = [&]() {
+#pragma unroll
+        for (int v = 0; v < KP * kGradRows; v++) {
+          acc[K0 * kGradRows + v] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+          pa[v] = df::Pair{0.f, 0.f};
+        }
+      };
+      sweep([&](const T (&x)[NX], const T (&g)[kGradRows]) {
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++)
+#pragma unroll
+          for (int k = 0; k < K0; k++) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
+        df::Pair gp[kGradRows], xp[NX];
+        bool in = true;
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++) {
+          in &= grad_in_range(g[r]);
+          gp[r] = grad_pair(g[r]);
+        }
+#pragma unroll
+        for (int q = K0; q < NX; q++) {
+          in &= grad_in_range(x[q]);
+          xp[q] = grad_pair(x[q]);
+        }
+        bad |= !in;
+#pragma unroll
+        for (int r = 0; r < kGradRows; r++)
+#pragma unroll
+          for (int b = 0; b < KP; b++) grad_acc(pa[b * kGradRows + r], gp[r], xp[r + K0 + b]);
+        if (++run == kGradRun) {
+          flush();
+          run = 0;
+        }
+      });
+      flush();
+      // a value outside the pairs' range anywhere in the segment: FP64 FMAs
+      if (__syncthreads_or(bad)) fp64();
     } else {
       // pairs, runs of kGradRun systems
       bool bad = false;
