@@ -20,6 +20,7 @@
 //   32 plus one neighbour each side) through a shared-memory tile.
 #include <type_traits>
 
+#include "df_math.cuh"
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -233,6 +234,229 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
   }
 }
 
+// FP64 y-implicit half-step in FP32 pairs (the arithmetic of the FP64 solves,
+// df_math.cuh): the FP64 kernel above is bound by the FP64 pipe (5 FP64
+// instructions per unknown).  Same ring and shuffles; each value is split
+// into a pair as it leaves the ring and its pair goes to the neighbouring
+// lanes; the fused stencil f = e0 c + e1 (left + right) is formed with pair
+// products and TwoSums, the forward and backward recurrences with
+// df::rec_step, the forward values go to `out` as 8-byte pairs and the
+// result as FP64 (exactly widened parts, one FP64 addition).  Coefficients
+// per row, staged once per CTA as FP32 pairs (fl32(c), fl32(c - fl32(c))):
+// (e0, e1) and (l1, l2) forward, (u1, u2) backward.  Range: the plan's sweep
+// gains are bounded (SweepPlan::df_ok), |e0|, |e1| < 2^8 (else the CTA runs
+// FP64), and inputs zero or in [2^-72, 2^91), so that every intermediate stays
+// inside FP32; a warp that meets any other input redoes its 32 columns with
+// FP64 arithmetic (u is not overwritten), so every result depends only on
+// the data.
+constexpr int kAdiDfThreadsMax = 512;
+
+__device__ __forceinline__ float2 adi_split_coef(double c) {
+  const float h = __double2float_rn(c);
+  return make_float2(h, __double2float_rn(c - (double)h));
+}
+// zero or 2^-100 <= |c| < 2^8
+__device__ __forceinline__ bool adi_coef_ok(double c) {
+  const uint32_t hw = (uint32_t)__double2hiint(c) & 0x7fffffffu;
+  return hw - ((1023u - 100u) << 20) < (108u << 20) || c == 0.0;
+}
+// the pair of an input value, or bad: zero or 2^-72 <= |v| < 2^91
+__device__ __forceinline__ df::Pair adi_pair(double v, bool& bad) {
+  df::Pair y;
+  const uint32_t hw = (uint32_t)__double2hiint(v) & 0x7fffffffu;
+  if (!df::split_fast(v, y)) y = df::Pair{0.f, 0.f};
+  bad |= !(hw - (951u << 20) < (163u << 20) || (hw | (uint32_t)__double2loint(v)) == 0u);
+  return y;
+}
+// c * v, unnormalised: TwoProduct of the high parts plus both cross terms
+__device__ __forceinline__ df::Pair adi_prod(float ch, float cl, df::Pair v) {
+  const float p = df::mul(ch, v.h);
+  float e = df::fma_(ch, v.h, -p);
+  e = df::fma_(ch, v.l, e);
+  e = df::fma_(cl, v.h, e);
+  return df::Pair{p, e};
+}
+__device__ __forceinline__ df::Pair adi_add(df::Pair a, df::Pair b) {
+  float s, t;
+  df::two_sum(a.h, b.h, s, t);
+  return df::Pair{s, df::add(df::add(a.l, b.l), t)};
+}
+
+template <int BW, int D>
+__global__ void __launch_bounds__(kAdiDfThreadsMax)
+k_adi_il2_df(Coefs<double> cf_g, int N, const double* __restrict__ u, double* __restrict__ out, int64_t M,
+             double r, int L) {
+  constexpr int U = 4;
+  static_assert(D % U == 0, "ring depth must be a multiple of the block");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {  // row block of a partitioned launch (blockIdx.y; L = N otherwise)
+    const int r0 = blockIdx.y * L;
+    N = (N - r0) < L ? (N - r0) : L;
+    cf_g = shift_coefs(cf_g, r0);
+    u += (int64_t)r0 * M;
+    out += (int64_t)r0 * M;
+  }
+  float4* ra = reinterpret_cast<float4*>(smem_raw);  // (e0, e1)
+  float4* rb = ra + N;                                // (l1, l2)
+  float4* rc = rb + N;                                // (u1, u2)
+  bool cbad = false;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double s = cf_g.s[i];
+    const double e0 = s * (1.0 - 2.0 * r), e1 = s * r;
+    const double l1 = cf_g.l1[i], l2 = BW == 2 ? cf_g.l2[i] : 0.0;
+    const double u1 = cf_g.u1[i], u2 = BW == 2 ? cf_g.u2[i] : 0.0;
+    cbad |= !(adi_coef_ok(e0) && adi_coef_ok(e1));
+    const float2 a = adi_split_coef(e0), b = adi_split_coef(e1), c1 = adi_split_coef(l1), c2 = adi_split_coef(l2),
+                 d1 = adi_split_coef(u1), d2 = adi_split_coef(u2);
+    ra[i] = make_float4(a.x, a.y, b.x, b.y);
+    rb[i] = make_float4(c1.x, c1.y, c2.x, c2.y);
+    rc[i] = make_float4(d1.x, d1.y, d2.x, d2.y);
+  }
+  const bool cta_f64 = __syncthreads_or(cbad) != 0;
+  const int lane = threadIdx.x & 31;
+  constexpr int kSlot = 16;  // [own value | outer neighbour], 8 bytes each
+  unsigned char* ring = smem_raw + (size_t)N * 3 * sizeof(float4) + (size_t)threadIdx.x * kSlot;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * kSlot;
+  const int64_t nwarps_total = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t ngroups = (M + 31) / 32;
+  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); wg < ngroups; wg += nwarps_total) {
+    const int64_t j = wg * 32 + lane;
+    const bool valid = j < M;
+    const int64_t jn = lane == 0 ? j - 1 : (lane == 31 ? j + 1 : -1);
+    const bool has_n = (lane == 0 || lane == 31) && jn >= 0 && jn < M;
+    const double* pu = u + (valid ? j : 0);
+    const double* pn = u + (has_n ? jn : 0);
+    double* po = out + (valid ? j : 0);
+    auto request = [&](int slot, int row) {
+      if (valid) cp_async8(ring_s + slot * pitch, pu + (int64_t)row * M);
+      if (has_n) cp_async8(ring_s + slot * pitch + 8, pn + (int64_t)row * M);
+    };
+    // one pass over the group's columns: PAIRS, or FP64 (coefficients from
+    // global memory, the row scale folded as in fuse_explicit)
+    auto pass = [&](auto pairs_tag) -> bool {
+      constexpr bool PAIRS = decltype(pairs_tag)::value;
+      bool bad = false;
+#pragma unroll 1
+      for (int q = 0; q < D; q++) {
+        if (q < N) request(q, q);
+        cp_commit();
+      }
+      df::Pair w1{0.f, 0.f}, w2{0.f, 0.f};
+      double d1 = 0.0, d2 = 0.0;
+#pragma unroll 1
+      for (int i0 = 0; i0 < N; i0 += U) {
+        cp_wait<D - U>();
+        __syncwarp();
+        const int n = (N - i0) < U ? (N - i0) : U;
+        const int s0 = i0 % D;
+        double c[U], outer[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const double* sl = reinterpret_cast<const double*>(ring + (size_t)(s0 + q) * pitch);
+          c[q] = valid ? sl[0] : 0.0;
+          outer[q] = has_n ? sl[1] : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          if (q < n && i0 + q + D < N) request(s0 + q, i0 + q + D);
+          cp_commit();
+        }
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const int i = i0 + q;
+          if constexpr (PAIRS) {
+            const df::Pair cp = adi_pair(c[q], bad);
+            const df::Pair op = adi_pair(outer[q], bad);
+            df::Pair lf{__shfl_up_sync(0xffffffffu, cp.h, 1), __shfl_up_sync(0xffffffffu, cp.l, 1)};
+            df::Pair rt{__shfl_down_sync(0xffffffffu, cp.h, 1), __shfl_down_sync(0xffffffffu, cp.l, 1)};
+            if (lane == 0) lf = op;
+            if (lane == 31) rt = op;
+            if (q < n && valid) {
+              const float4 ea = ra[i], lb = rb[i];
+              const df::Pair nb = adi_add(lf, rt);
+              const df::Pair f = adi_add(adi_prod(ea.x, ea.y, cp), adi_prod(ea.z, ea.w, nb));
+              const df::Pair w = df::rec_step<false, BW>(df::Pair{1.f, 0.f}, f, df::Pair{lb.x, lb.y}, w1,
+                                                         df::Pair{lb.z, lb.w}, w2);
+              w2 = w1;
+              w1 = w;
+              *reinterpret_cast<uint2*>(po + (int64_t)i * M) = make_uint2(__float_as_uint(w.h), __float_as_uint(w.l));
+            }
+          } else {
+            double lf = __shfl_up_sync(0xffffffffu, c[q], 1);
+            double rt = __shfl_down_sync(0xffffffffu, c[q], 1);
+            if (lane == 0) lf = outer[q];
+            if (lane == 31) rt = outer[q];
+            if (q < n && valid) {
+              const double s = cf_g.s[i];
+              double w = fma(s * r, lf + rt, s * (1.0 - 2.0 * r) * c[q]);
+              if (BW == 2) w = fma(-cf_g.l2[i], d2, w);
+              w = fma(-cf_g.l1[i], d1, w);
+              d2 = d1;
+              d1 = w;
+              po[(int64_t)i * M] = w;
+            }
+          }
+        }
+      }
+      cp_wait<0>();
+      __syncwarp();
+      // backward: the forward values come back through the ring
+#pragma unroll 1
+      for (int q = 0; q < D; q++) {
+        const int row = N - 1 - q;
+        if (row >= 0 && valid) cp_async8(ring_s + q * pitch, po + (int64_t)row * M);
+        cp_commit();
+      }
+      df::Pair x1{0.f, 0.f}, x2{0.f, 0.f};
+      double y1 = 0.0, y2 = 0.0;
+#pragma unroll 1
+      for (int top = N - 1; top >= 0; top -= U) {
+        cp_wait<D - U>();
+        const int n = (top + 1) < U ? (top + 1) : U;
+        const int s0 = (N - 1 - top) % D;
+        uint2 wv[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) wv[q] = *reinterpret_cast<const uint2*>(ring + (size_t)(s0 + q) * pitch);
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const int row = top - q - D;
+          if (q < n && row >= 0 && valid) cp_async8(ring_s + (s0 + q) * pitch, po + (int64_t)row * M);
+          cp_commit();
+        }
+        if (valid) {
+#pragma unroll
+          for (int q = 0; q < U; q++) {
+            if (q >= n) break;
+            const int i = top - q;
+            if constexpr (PAIRS) {
+              const float4 cu = rc[i];
+              const df::Pair w{__uint_as_float(wv[q].x), __uint_as_float(wv[q].y)};
+              const df::Pair x = df::rec_step<false, BW>(df::Pair{1.f, 0.f}, w, df::Pair{cu.x, cu.y}, x1,
+                                                         df::Pair{cu.z, cu.w}, x2);
+              x2 = x1;
+              x1 = x;
+              po[(int64_t)i * M] = df::combine_ok(x.h) ? df::combine_fast(x.h, x.l) : df::combine(x.h, x.l);
+            } else {
+              double x = __hiloint2double((int)wv[q].y, (int)wv[q].x);
+              if (BW == 2) x = fma(-cf_g.u2[i], y2, x);
+              x = fma(-cf_g.u1[i], y1, x);
+              y2 = y1;
+              y1 = x;
+              po[(int64_t)i * M] = x;
+            }
+          }
+        }
+      }
+      cp_wait<0>();
+      __syncwarp();
+      return bad;
+    };
+    if (cta_f64 || __any_sync(0xffffffffu, pass(std::true_type{}))) pass(std::false_type{});
+  }
+}
+
 // ----------------------------------------------------- implicit along x
 
 constexpr int kAdiTile = 35;  // 34 systems (32 + one neighbour each side), padded
@@ -413,6 +637,24 @@ static cudaError_t launch_adi(const SweepPlan& p, int N, const C* u, C* out, int
   constexpr int kFuseExtra = (sizeof(C) == 8 && !ADJ) ? 2 : 0;
   constexpr int kRecExtra = sizeof(C) == 4 ? 8 - coef_arrays<BW>() : kFuseExtra;
   if (axis == 1) {
+    if constexpr (sizeof(C) == 8 && !ADJ) {
+      // FP64 in FP32 pairs where the plan admits them and the records fit
+      constexpr int D = 16;
+      const size_t rec = (size_t)L * 3 * sizeof(float4);
+      if (p.df_ok && option(BS_OPT_F64_PAIRS) != 1 && rec + 64 * D * 16 + 1024 <= (size_t)device_info().smem_optin) {
+        auto k = k_adi_il2_df<BW, D>;
+        const int64_t threads = ((M + 31) / 32) * 32;
+        const StagedShape sh = staged_shape(threads * P, rec, (size_t)D * 16, kernel_regs((const void*)k),
+                                            kAdiDfThreadsMax, true, 128);
+        if (sh.threads > 0 && sh.staged) {
+          const size_t bytes = rec + (size_t)sh.threads * D * 16;
+          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+          if (e != cudaSuccess) return e;
+          k<<<dim3((sh.grid + P - 1) / P, P), sh.threads, bytes, st>>>(cf, N, u, out, M, r, L);
+          return cudaGetLastError();
+        }
+      }
+    }
     auto go = [&](auto dtag) -> cudaError_t {
       constexpr int D = decltype(dtag)::value;
       const int64_t threads = ((M + 31) / 32) * 32;

@@ -545,7 +545,7 @@ cudaError_t upload_plan(const HostPlan& hp, SweepPlan& sp, size_t& bytes) {
   return e;
 }
 
-cudaError_t upload_part(const HostPart& hp, PartPlan& pp, size_t& bytes) {
+cudaError_t upload_part(const HostPart& hp, int64_t N, PartPlan& pp, size_t& bytes) {
   pp.P = hp.P;
   pp.L = hp.L;
   pp.R = hp.R;
@@ -555,6 +555,10 @@ cudaError_t upload_part(const HostPart& hp, PartPlan& pp, size_t& bytes) {
   pp.p = hp.p;
   pp.q = hp.q;
   cudaError_t e = upload_plan(hp.blk, pp.blk, bytes);
+  {  // whether the block sweeps may run in FP32 pairs (the ADI half-steps)
+    std::vector<float> rec;
+    pp.blk.df_ok = make_df_records(hp.blk, N, rec);
+  }
   auto up = [&](const std::vector<double>& v, double** d64, float** d32) {
     std::vector<float> v32(v.size());
     for (size_t i = 0; i < v.size(); i++) v32[i] = (float)v[i];
@@ -605,7 +609,7 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
     make_windows(hp[p], N, win_rows(false), win_rows(true), hd->plan[p].win32, hd->plan[p].win_df);
   }
   if (parts) {
-    for (int p = 0; p < 2 && e == cudaSuccess; p++) e = upload_part(parts[p], hd->part[p], bytes);
+    for (int p = 0; p < 2 && e == cudaSuccess; p++) e = upload_part(parts[p], N, hd->part[p], bytes);
     hd->has_part = true;
   }
   {
