@@ -248,7 +248,9 @@ k_adi_il2(Coefs<C> cf_g, int N, const C* __restrict__ u, C* __restrict__ out, in
 // FP64), and inputs zero or in [2^-72, 2^91), so that every intermediate stays
 // inside FP32; a warp that meets any other input redoes its 32 columns with
 // FP64 arithmetic (u is not overwritten), so every result depends only on
-// the data.
+// the data.  (Forming the stencil in FP64 instead -- 3 FP64 instructions
+// and one split per unknown -- made the FP64 pipe the bound again: 198
+// against 172 us.)
 constexpr int kAdiDfThreadsMax = 512;
 
 __device__ __forceinline__ float2 adi_split_coef(double c) {
