@@ -52,7 +52,7 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 863069696 + 92672, "sha": "a060a44a197aefec"},
+    "band_grad_f64": {"bytes": 891901184 + 4947456, "sha": "8b5363f136047072"},
     "f64_solve": {"bytes": 470564096 + 434477056, "sha": "086820ffa32b22a3"},
     "adjoint_f64": {"bytes": 463844352 + 427795456, "sha": "086820ffa32b22a3"},
     "refine_solve": {"bytes": 355203072 + 435953408, "sha": "595a7f6d93338dc1"},
