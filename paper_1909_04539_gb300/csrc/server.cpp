@@ -19,7 +19,10 @@
 // requests never queue behind the multi-millisecond copies of a large batch.
 // Inside a batch the copies go smallest first and every request has its own
 // completion event after its device-to-host copy: it finishes as soon as its
-// own results are back, not when the whole batch is.  Each stream has a
+// own results are back, not when the whole batch is.  Copies go in pieces of
+// 8 MiB, at most four of a stream in flight (the launcher waits for the piece
+// issued four before), so a large batch never queues more than 32 MiB ahead
+// of another stream's copies on the copy engines.  Each stream has a
 // launcher thread that issues its batches' copies and graph replay, so the
 // worker thread, which admits requests and observes completions, never waits
 // while the hundreds of copy pieces of a large batch are queued (issuing them
@@ -105,11 +108,40 @@ constexpr size_t kSmallBytes = size_t(16) << 20;
 // a large request's instead of running them after it
 constexpr size_t kCopyChunk = size_t(8) << 20;
 
-cudaError_t copy_chunked(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+// Copy pieces of one stream in flight at a time: a piece is issued only after
+// the one issued kPaceWindow pieces earlier has finished, so that a large
+// batch never has more than kPaceWindow * kCopyChunk bytes queued before
+// another stream's copies (a few hundred microseconds of copy-engine work).
+constexpr int kPaceWindow = 4;
+
+// Per stream: an event after each piece issued, in a ring.
+struct Pacer {
+  cudaEvent_t ev[kPaceWindow] = {};
+  int64_t issued = 0;
+};
+
+// Waits (host side, bounded) for the piece issued kPaceWindow pieces ago.
+void pace_wait(Pacer& p) {
+  if (p.issued < kPaceWindow) return;
+  cudaEvent_t ev = p.ev[p.issued % kPaceWindow];
+  const auto t0 = std::chrono::steady_clock::now();
+  while (cudaEventQuery(ev) == cudaErrorNotReady) {
+    // a wait that long means the device is stuck; stop pacing this piece
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) return;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+cudaError_t copy_chunked(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st,
+                         Pacer& p) {
   cudaError_t e = cudaSuccess;
-  for (size_t o = 0; o < bytes && e == cudaSuccess; o += kCopyChunk)
+  for (size_t o = 0; o < bytes && e == cudaSuccess; o += kCopyChunk) {
+    pace_wait(p);
     e = cudaMemcpyAsync(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o,
                         bytes - o < kCopyChunk ? bytes - o : kCopyChunk, kind, st);
+    if (e == cudaSuccess) e = cudaEventRecord(p.ev[p.issued % kPaceWindow], st);
+    p.issued++;
+  }
   return e;
 }
 
@@ -145,6 +177,8 @@ struct Slot {
   bool issued = false;
   std::vector<Req*> rp;
   cudaError_t launch_err = cudaSuccess;
+  int recorded = 0;  // requests whose completion event is queued (under the server lock)
+  Pacer pace;        // the stream's copy pieces in flight
 };
 
 }  // namespace
@@ -242,11 +276,11 @@ cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<Req*>& rp) {
     if (r.mode == SERVE_F64) {
       g.B = dB;
       g.X = reinterpret_cast<double*>(dB);
-      e = copy_chunked(dB, r.hB, nm * 8, cudaMemcpyHostToDevice, sl.st);
+      e = copy_chunked(dB, r.hB, nm * 8, cudaMemcpyHostToDevice, sl.st, sl.pace);
     } else {
       g.X = reinterpret_cast<double*>(dB);                   // nm * 8 bytes
       g.B = dB + nm * 8;                                     // nm * 4 bytes
-      e = copy_chunked(g.B, r.hB, nm * 4, cudaMemcpyHostToDevice, sl.st);
+      e = copy_chunked(g.B, r.hB, nm * 4, cudaMemcpyHostToDevice, sl.st, sl.pace);
     }
     greq[q] = g;
     for (int64_t j0 = 0; j0 < r.M; j0 += 32) gt[nt++] = GTile{(int)q, (int)j0};
@@ -262,8 +296,12 @@ cudaError_t launch_batch(bs_server s, Slot& sl, const std::vector<Req*>& rp) {
   for (size_t q = 0; q < rp.size() && e == cudaSuccess; q++) {
     Req& r = *rp[q];
     const size_t nm = (size_t)r.h->N * (size_t)r.M;
-    e = copy_chunked(r.hX, s->arena_base + r.off, nm * 8, cudaMemcpyDeviceToHost, sl.st);
+    e = copy_chunked(r.hX, s->arena_base + r.off, nm * 8, cudaMemcpyDeviceToHost, sl.st, sl.pace);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev[q], sl.st);
+    if (e == cudaSuccess) {  // the worker may poll this request from now on
+      std::lock_guard<std::mutex> lk(s->mu);
+      sl.recorded = (int)q + 1;
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
   return e;
@@ -291,11 +329,12 @@ void worker_loop(bs_server s) {
     // completions: each request as soon as its own copy back is done; the
     // slot when the whole batch is
     for (Slot& sl : s->slots) {
-      if (!sl.busy || !sl.issued) continue;
-      if (sl.launch_err != cudaSuccess) {  // nothing of this batch can be trusted: fail its requests
+      if (!sl.busy) continue;
+      if (sl.issued && sl.launch_err != cudaSuccess) {  // the rest of this batch cannot be trusted: fail it
         s->sticky = sl.launch_err;
         const double t = now_s();
-        for (int64_t id : sl.reqs) finish_request(s, s->reqs[id], false, t);
+        for (size_t k = 0; k < sl.reqs.size(); k++)
+          if (!sl.finished[k]) finish_request(s, s->reqs[sl.reqs[k]], false, t);
         sl.reqs.clear();
         sl.finished.clear();
         sl.rp.clear();
@@ -303,7 +342,9 @@ void worker_loop(bs_server s) {
         progressed = true;
         continue;
       }
-      for (size_t q = 0; q < sl.reqs.size(); q++) {
+      // requests whose completion event the launcher has queued (it may
+      // still be issuing later copies of the batch)
+      for (size_t q = 0; q < (size_t)sl.recorded; q++) {
         if (sl.finished[q]) continue;
         const cudaError_t eq = cudaEventQuery(sl.ev[q]);
         if (eq == cudaErrorNotReady) break;  // later copies of the batch are not done either
@@ -312,6 +353,7 @@ void worker_loop(bs_server s) {
         sl.finished[q] = 1;
         progressed = true;
       }
+      if (!sl.issued) continue;  // the batch event is not queued yet
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       const double t = now_s();
@@ -350,6 +392,7 @@ void worker_loop(bs_server s) {
         sl.reqs = ids;
         sl.finished.assign(ids.size(), 0);
         sl.issued = false;
+        sl.recorded = 0;
         sl.launch_err = cudaSuccess;
         sl.busy = true;
         progressed = true;
@@ -396,6 +439,8 @@ void destroy_server(bs_server s) {
     if (sl.exec) cudaGraphExecDestroy(sl.exec);
     if (sl.done) cudaEventDestroy(sl.done);
     for (cudaEvent_t ev : sl.ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : sl.pace.ev)
+      if (ev) cudaEventDestroy(ev);
     if (sl.h_work) cudaFreeHost(sl.h_work);
     if (sl.d_work) cudaFree(sl.d_work);
     if (sl.st) cudaStreamDestroy(sl.st);
@@ -438,6 +483,8 @@ bs_status bs_server_create(size_t hbm_budget_bytes, int n_streams, bs_server* ou
     if (e == cudaSuccess)
       e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.small_only ? prio_hi : prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    for (int k = 0; k < kPaceWindow && e == cudaSuccess; k++)
+      e = cudaEventCreateWithFlags(&sl.pace.ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.h_work, kGroupWorkBytes);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_work, kGroupWorkBytes);
     if (e == cudaSuccess) std::memset(sl.h_work, 0, kGroupWorkBytes);
