@@ -163,3 +163,30 @@ def test_adi_adjoint_full_grid_4096(bs, axis):
     ref = oracle.adi_halfstep_bands(u.cpu().numpy(), r, bands, axis, transpose=True)
     parity(adj.cpu().numpy(), ref, 1e-12, _lines(axis))
 
+
+
+@pytest.mark.parametrize("case", ["huge", "tiny", "zeros"])
+def test_adi_pair_kernel_redo(bs, case):
+    """The FP64 y-implicit half-step runs in FP32 pairs; a warp whose columns
+    hold an input outside the pairs' range ([2^-72, 2^91), zero allowed)
+    redoes them in FP64.  Columns with 2^95, 2^-80 or zeros beside ordinary
+    ones, row-partitioned (1024 rows: 4 blocks) and not (400 rows), against
+    the oracle per line.  (r = 0.3: with r = 0.5 the stencil's centre weight
+    1 - 2r is zero, and the oracle's unfused u + r (left - 2u + right) loses
+    a huge column's neighbour terms to cancellation, which the fused form
+    keeps.)"""
+    for ny, nx in ((1024, 300), (400, 300)):
+        r = 0.3
+        rng = np.random.default_rng(ny + len(case))
+        u = rng.uniform(-1, 1, (ny, nx))
+        if case == "huge":
+            u[:, 37] *= 2.0 ** 95
+        elif case == "tiny":
+            u[100:200, 70] = 2.0 ** -80
+        else:
+            u[:, 5:40] = 0.0
+            u[10:20, :] = 0.0
+        f = _factor(bs, ny, r)
+        out = bs.adi_halfstep(f, torch.tensor(u, device="cuda"), r, 1)
+        torch.cuda.synchronize()
+        parity(out.cpu().numpy(), oracle.adi_halfstep(u, r, 1), 1e-12, _lines(1))

@@ -117,19 +117,21 @@ def _band_abs_bound(width, GB, X):
     return oracle.band_grad(width, np.abs(GB), np.abs(X)) * -1.0
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("layout", ["interleaved", "strided"])
 @pytest.mark.parametrize("width", [3, 5])
 @pytest.mark.parametrize("case", ["in_range", "huge", "tiny", "zeros"])
-def test_band_grad_fp32_data(bs, width, layout, case):
-    """FP32 band gradient (pair sums over runs of systems, FP64 sums of the
-    runs) against the oracle on the same FP32 values widened to FP64: within
-    1e-12 of the absolute-value sums per entry.  'huge' and 'tiny' put one
-    value outside [2^-32, 2^48), which sends the CTAs that meet it to FP64
-    FMAs; 'zeros' zeroes whole rows and systems."""
+def test_band_grad_pair_sums(bs, width, layout, case, dtype):
+    """Band gradient with pair sums (FP32 data: every band; FP64 data: the
+    top band) over runs of systems, FP64 sums of the runs, against the oracle
+    on the same values in FP64: within 1e-12 of the absolute-value sums per
+    entry.  'huge' and 'tiny' put one value outside [2^-32, 2^48), which
+    sends the CTAs that meet it to FP64 FMAs; 'zeros' zeroes whole rows and
+    systems."""
     N, M = 301, 5003
     rng = np.random.default_rng(width + 17)
-    GB = rng.uniform(-1, 1, (N, M)).astype(np.float32)
-    X = rng.uniform(-1, 1, (N, M)).astype(np.float32)
+    GB = rng.uniform(-1, 1, (N, M)).astype(dtype)
+    X = rng.uniform(-1, 1, (N, M)).astype(dtype)
     if case == "huge":
         GB[7, 123] = 2.0 ** 60
     elif case == "tiny":

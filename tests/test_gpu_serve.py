@@ -175,3 +175,35 @@ def test_pageable_host_buffers_rejected(bs, serve):
         srv.submit(facs[0], B, X, 0)
     srv.close()
 
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_large_request_paced_copies(bs, serve, mode):
+    """A request larger than the copy window (four 8 MiB pieces) with small
+    ones beside it: the copies are paced, every result still equals the
+    direct solve bitwise."""
+    specs, facs = _lhs_pool(bs, 3)
+    k = max(range(3), key=lambda q: specs[q].N)
+    M = (80 << 20) // (specs[k].N * 8) + 7
+    srv = serve.Server(1 << 30, n_streams=3)
+    subs = [(k, M, mode, 7)] + [(q % 3, 50 + q, q % 2, 20 + q) for q in range(6)]
+    out = []
+    for kk, MM, md, seed in subs:
+        B, X = _request(specs[kk], MM, md, seed)
+        out.append((srv.submit(facs[kk], B, X, md), kk, md, B, X))
+    for rid, *_ in out:
+        assert srv.wait(rid, 120) == "done"
+    bs.set_option(bs.OPT_PARTITION, 1)
+    bs.set_option(bs.OPT_TWISTED, 1)
+    try:
+        for rid, kk, md, B, X in out:
+            if md == 0:
+                D = bs.solve(facs[kk], B.cuda())
+            else:
+                D = bs.solve_refine(facs[kk], B.cuda(), mode=bs.REFINE_FACTOR)
+            torch.cuda.synchronize()
+            assert torch.equal(D.cpu(), X)
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+        bs.set_option(bs.OPT_TWISTED, 0)
+    srv.close()
