@@ -20,7 +20,7 @@
 // unknown (GB and X; the X halo of 2h rows per row block comes from L2).
 //
 // Arithmetic of level 1.  FP64 data: one FP64 FMA per product for all bands
-// but the top one, whose products are summed in FP32 pairs (see
+// but the top ones, whose products are summed in FP32 pairs (see
 // kGradPairBands5; the kernel is bound by the FP64 pipe).  FP32 data: a thread's products for one (band,
 // row) are summed in FP32 pairs over runs of kGradRun systems -- each product
 // exact by an FMA-based TwoProduct, added with Knuth's TwoSum, the rounding
@@ -124,13 +124,17 @@ __device__ __forceinline__ df::Pair grad_pair(double v) {
 // matrices: kGradPairBands3) are summed in FP32 pairs as for FP32 data --
 // each value split once, the product a TwoProduct plus the two cross terms
 // -- and the others with FP64 FMAs, so that the FP32 and integer pipes take
-// part of the work the FP64 pipe bounds.  Measured (penta N = 512,
-// M = 65536, ms): 0 pair bands 0.321, 1: 0.281, 2: 0.295, 3: 0.329 -- the
-// splits (~16 integer instructions per value, whichever band they serve) make
-// more pair bands cost more issue slots than they save FP64 ones.  Tri
-// N = 1024, M = 2^18: 0 pair bands 1.435 ms, 1: 1.287 ms.
-constexpr int kGradPairBands5 = 1;
+// part of the work the FP64 pipe bounds.  The FP64 sums of the pair bands'
+// runs live in shared memory (one column per thread), which leaves the
+// registers to the loads in flight.  Measured (penta N = 512, M = 65536,
+// ms): 0 pair bands 0.321; with the run sums in registers 1: 0.281, 2:
+// 0.295, 3: 0.329; in shared memory 1: 0.278, 2: 0.258, 3: 0.298 -- beyond
+// two bands the splits (~16 integer instructions per value) cost more issue
+// slots than the FP64 FMAs they replace.  Tri N = 1024, M = 2^18: 0 pair
+// bands 1.435 ms, 1: 1.282 (registers) / 1.228 (shared memory).
+constexpr int kGradPairBands5 = 2;
 constexpr int kGradPairBands3 = 1;
+constexpr bool kGradPairSmem = true;
 
 // a += g * x for pairs of FP64 values, not renormalised
 __device__ __forceinline__ void grad_acc(df::Pair& a, df::Pair g, df::Pair x) {
@@ -166,6 +170,9 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
   constexpr int NV = kGradRows * W;  // accumulators per thread
   static_assert(NV <= 64, "reduce-scatter holds at most 64 values per lane");
   __shared__ double red[kGradThreads / 32][64];
+  constexpr int KP = (sizeof(T) == 8) ? (W == 5 ? kGradPairBands5 : kGradPairBands3) : 0;
+  constexpr int KPS = (kGradPairSmem && KP > 0) ? KP * kGradRows : 1;
+  __shared__ double psum[KPS][kGradThreads];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t total = (int64_t)R * M;
   const int64_t lo = range_lo(blockIdx.x, total, gridDim.x);
@@ -225,7 +232,6 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
             acc[k * kGradRows + r] = fma(to_wide(g[r]), to_wide(x[r + k]), acc[k * kGradRows + r]);
       });
     };
-    constexpr int KP = (sizeof(T) == 8) ? (W == 5 ? kGradPairBands5 : kGradPairBands3) : 0;
     if constexpr (sizeof(T) == 8 && KP == 0) {
       fp64();
     } else if constexpr (sizeof(T) == 8) {
@@ -238,11 +244,18 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
       for (int v = 0; v < KP * kGradRows; v++) pa[v] = df::Pair{0.f, 0.f};
 #pragma unroll
       for (int v = 0; v < NV; v++) acc[v] = 0.0;
+      if constexpr (kGradPairSmem) {
+#pragma unroll
+        for (int v = 0; v < KP * kGradRows; v++) psum[v][threadIdx.x] = 0.0;
+      }
       int run = 0;
       auto flush = [&]() {
 #pragma unroll
         for (int v = 0; v < KP * kGradRows; v++) {
-          acc[K0 * kGradRows + v] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+          if constexpr (kGradPairSmem)
+            psum[v][threadIdx.x] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+          else
+            acc[K0 * kGradRows + v] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
           pa[v] = df::Pair{0.f, 0.f};
         }
       };
@@ -274,6 +287,10 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
         }
       });
       flush();
+      if constexpr (kGradPairSmem) {
+#pragma unroll
+        for (int v = 0; v < KP * kGradRows; v++) acc[K0 * kGradRows + v] = psum[v][threadIdx.x];
+      }
       // a value outside the pairs' range anywhere in the segment: FP64 FMAs
       if (__syncthreads_or(bad)) fp64();
     } else {
