@@ -260,8 +260,10 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
 // up through a ring of 4-byte rows and leaves (w, delta) in the 8-byte slots
 // of X; pass 2 streams the slots down through a ring and writes the FP64
 // solution over them.  Rows move in blocks of kRU.
+constexpr int kRefineThreadsMax = 512;
+
 template <int BW, int D, bool SMEM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kRefineThreadsMax)
 k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M) {
   static_assert(D % kRU == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -390,31 +392,28 @@ static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* 
   const int N = (int)h->N;
   const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(h->plan[0].c32, h->lu_hi, h->lu_lo, N);
   const DeviceInfo& d = device_info();
-  // 128-thread CTAs (halved for small batches), as many per SM as shared
-  // memory holds.  The pair sweeps' policy (one 448-thread CTA per SM on the
-  // penta N = 512, M = 65536 batch) made this kernel slower there: 0.231 ->
-  // 0.275 ms.
+  // CTA size from shared memory, registers and the busiest SM's warps
+  // (staged_shape), ties to the largest: this kernel runs better in fewer,
+  // larger CTAs.  Measured (ms; CTA size fixed): penta N = 512, M = 65536:
+  // 128: 0.225, 256: 0.213, 320: 0.260, 384: 0.328 (two waves), 448: 0.207,
+  // 512: 0.203; tri N = 1024, M = 2^20: 128: 5.48, 256: 5.07, 320: 4.88,
+  // 384: 4.79, 448: 5.42, 512: 5.16.
   auto ks = k_refine_factor<BW, D, true>;
   auto kg = k_refine_factor<BW, D, false>;
-  int tpb = 128;
-  while (tpb > 32 && M < (int64_t)2 * d.sms * tpb) tpb /= 2;
   const size_t coef = (size_t)N * (FRefineRecs<BW>::R1 + FRefineRecs<BW>::R2) * sizeof(float4);
-  const size_t ring = (size_t)tpb * D * 8;
-  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024) - 1024;
-  const bool smem = coef + ring <= limit;
-  const size_t bytes = (smem ? coef : 0) + ring;
-  int per_sm = (int)((228 * 1024) / (bytes + 1024));
-  if (per_sm > 2048 / tpb) per_sm = 2048 / tpb;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)d.sms * per_sm;
+  const StagedShape sh = staged_shape(M, coef, (size_t)D * 8, kernel_regs((const void*)ks), kRefineThreadsMax, true,
+                                      kRefineThreadsMax);
+  if (sh.threads == 0) return cudaErrorInvalidValue;
+  const int tpb = sh.threads;
+  const bool smem = sh.staged;
+  const size_t bytes = (smem ? coef : 0) + (size_t)tpb * D * 8;
+  int64_t grid = sh.grid;
   const int64_t budget = option(BS_OPT_INFLIGHT_BYTES);
   if (budget > 0) {
     int64_t cap = budget / ((int64_t)tpb * N * 8);
     if (cap < d.sms) cap = d.sms;
     if (grid > cap) grid = cap;
   }
-  const int64_t need = (M + tpb - 1) / tpb;
-  if (grid > need) grid = need;
   auto k = smem ? ks : kg;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
