@@ -52,10 +52,10 @@ NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
     # one capture of the kernel inside this benchmark's step (the first
     # launch of each: the accuracy-check solves or the first warm-up step)
-    "band_grad_f64": {"bytes": 891901184 + 4947456, "sha": "8b5363f136047072"},
+    "band_grad_f64": {"bytes": 894596096 + 5241856, "sha": "a7a6177e1eb9d3f0"},
     "f64_solve": {"bytes": 470564096 + 434477056, "sha": "086820ffa32b22a3"},
     "adjoint_f64": {"bytes": 463844352 + 427795456, "sha": "086820ffa32b22a3"},
-    "refine_solve": {"bytes": 355203072 + 435953408, "sha": "595a7f6d93338dc1"},
+    "refine_solve": {"bytes": 349858048 + 433706496, "sha": "85bb855f67c0fb37"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
