@@ -50,12 +50,13 @@ NOMINAL_HBM_GBS = 8000.0
 # kernel sources (for the sweeps also the launch policy in solve_api.cu, which
 # sets their grid) hash to the value they had at capture time.
 NCU_TRAFFIC = {
-    # one capture of the kernel inside this benchmark's step (the first
-    # launch of each: the accuracy-check solves or the first warm-up step)
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel
+    # inside this benchmark's step (launch list of the timed steps, or the
+    # first launch of a full capture), keyed by the hash of its sources
     "band_grad_f64": {"bytes": 894596096 + 5241856, "sha": "a7a6177e1eb9d3f0"},
-    "f64_solve": {"bytes": 470564096 + 434477056, "sha": "086820ffa32b22a3"},
-    "adjoint_f64": {"bytes": 463844352 + 427795456, "sha": "086820ffa32b22a3"},
-    "refine_solve": {"bytes": 349858048 + 433706496, "sha": "85bb855f67c0fb37"},
+    "f64_solve": {"bytes": 469910400 + 432772864, "sha": "e097e8f3f687cdc4"},
+    "adjoint_f64": {"bytes": 462895744 + 427751168, "sha": "e097e8f3f687cdc4"},
+    "refine_solve": {"bytes": 350972672 + 435089408, "sha": "4725e3d6e20cb656"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],

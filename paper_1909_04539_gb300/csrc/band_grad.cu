@@ -4,20 +4,23 @@
 // dL/dA = -GB X^T; the entries on the bands are
 //   dbands[k*N + i] = -sum_j GB[i, j] * X[i + k - h, j],   h = width / 2.
 // Two levels, fixed order, no atomics:
-//   1. the work space (row blocks of kGradRows rows) x (systems), taken in
-//      row-block-major order, is cut into G equal contiguous ranges, one per
-//      CTA of a grid that fills the device exactly once (G = SMs x resident
-//      CTAs per SM, so no partial last wave).  A CTA walks its range as at
-//      most a few segments (one per row block it touches); for each segment
-//      its threads stride over the systems accumulating in FP64, a warp
-//      reduce-scatter (shuffles) and a shared-memory pass across the warps
-//      combine them, and one partial per (CTA, segment, band, row) goes to
-//      scratch;
+//   1. the work space (groups of kGradGroups row blocks of kGradRows rows) x
+//      (systems), taken in group-major order, is cut into G equal contiguous
+//      ranges, one per CTA of a grid that fills the device exactly once (G =
+//      SMs x resident CTAs per SM, so no partial last wave).  A CTA walks its
+//      range as at most a few segments (one per block group it touches); for
+//      each segment the CTA's thread group g strides over the systems
+//      accumulating the products of the group's row block g in FP64, a warp
+//      reduce-scatter (shuffles) and a shared-memory pass across the group's
+//      warps combine them, and one partial per (CTA, segment, row block,
+//      band, row) goes to scratch;
 //   2. one thread per (band, row) adds the partials of the CTAs that touched
 //      its row block, in CTA order.
 // The decomposition is a function of N, M and G only, so the result is
 // bitwise reproducible on a given device.  16 bytes of compulsory reads per
-// unknown (GB and X; the X halo of 2h rows per row block comes from L2).
+// unknown (GB and X); the X halo of 2h rows per row block is shared with the
+// neighbouring blocks of the group, which the same CTA sweeps at the same
+// time.
 //
 // Arithmetic of level 1.  FP64 data: one FP64 FMA per product for all bands
 // but the top ones, whose products are summed in FP32 pairs (see
@@ -57,16 +60,25 @@ constexpr int kGradThreads = 256;
 // registers): penta N = 512, M = 65536: 0.321 against 0.356 ms (4 rows:
 // 0.327, 2 rows: 0.326).
 constexpr int kGradRows = 3;
+// Row blocks a CTA sweeps side by side: its threads form kGradGroups groups,
+// group g taking row block kGradGroups * rg + g of the same systems, so that
+// the X rows two neighbouring blocks share are loaded by two groups of one SM
+// at about the same time (the second load hits L1) instead of by two CTAs at
+// unrelated times (both from DRAM).
+constexpr int kGradGroups = 4;
+constexpr int kGradGroupThreads = kGradThreads / kGradGroups;
+static_assert(kGradGroupThreads % 32 == 0, "a group is whole warps");
 
 struct GradShape {
   int R;      // row blocks
+  int RG;     // groups of kGradGroups row blocks
   int G;      // CTAs
-  int S;      // most segments (row blocks) one CTA can touch
+  int S;      // most segments (block groups) one CTA can touch
   int64_t M;  // systems
 };
 
-// CTA c owns the positions [range_lo(c), range_lo(c + 1)) of the R*M work
-// space (position p = row block p / M, system p % M).
+// CTA c owns the positions [range_lo(c), range_lo(c + 1)) of the RG*M work
+// space (position p = block group p / M, system p % M).
 __host__ __device__ __forceinline__ int64_t range_lo(int64_t c, int64_t total, int64_t G) { return c * total / G; }
 
 static int grad_ctas_per_sm();
@@ -74,19 +86,20 @@ static int grad_ctas_per_sm();
 GradShape grad_shape(int N, int64_t M) {
   GradShape g{};
   g.R = (N + kGradRows - 1) / kGradRows;
+  g.RG = (g.R + kGradGroups - 1) / kGradGroups;
   g.M = M;
   g.G = device_info().sms * grad_ctas_per_sm();
-  const int64_t total = (int64_t)g.R * M;
-  // a range of ceil(total / G) positions touches at most this many row blocks
+  const int64_t total = (int64_t)g.RG * M;
+  // a range of ceil(total / G) positions touches at most this many block groups
   const int64_t per = (total + g.G - 1) / g.G;
   g.S = (int)((per + M - 1) / M) + 1;
-  if (g.S > g.R) g.S = g.R;
+  if (g.S > g.RG) g.S = g.RG;
   return g;
 }
 
 size_t band_grad_scratch_bytes(int width, int N, int64_t M) {
   const GradShape g = grad_shape(N, M);
-  return (size_t)g.G * g.S * width * kGradRows * sizeof(double);
+  return (size_t)g.G * g.S * kGradGroups * width * kGradRows * sizeof(double);
 }
 
 template <typename T>
@@ -159,12 +172,12 @@ __device__ __forceinline__ void grad_acc(df::Pair& a, float g, float x) {
   a.l = df::add(a.l, df::add(t, e));
 }
 
-// Level 1.  partial layout: [CTA][segment][band][row in block].
+// Level 1.  partial layout: [CTA][segment][group][band][row in block].
 // PER: periodic matrix, X rows taken modulo N.
 template <typename T, int W, bool PER>
 __global__ void __launch_bounds__(kGradThreads, 2)
-k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, const T* __restrict__ X, int64_t rs,
-                    int64_t ss, double* __restrict__ partial) {
+k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict__ GB, const T* __restrict__ X,
+                    int64_t rs, int64_t ss, double* __restrict__ partial) {
   constexpr int H = W / 2;
   constexpr int NX = kGradRows + 2 * H;
   constexpr int NV = kGradRows * W;  // accumulators per thread
@@ -174,14 +187,17 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
   constexpr int KPS = (kGradPairSmem && KP > 0) ? KP * kGradRows : 1;
   __shared__ double psum[KPS][kGradThreads];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t total = (int64_t)R * M;
+  const int grp = threadIdx.x / kGradGroupThreads, tg = threadIdx.x % kGradGroupThreads;
+  const int64_t total = (int64_t)RG * M;
   const int64_t lo = range_lo(blockIdx.x, total, gridDim.x);
   const int64_t hi = range_lo(blockIdx.x + 1, total, gridDim.x);
-  const int rb0 = (int)(lo / M);
+  const int rg0 = (int)(lo / M);
   for (int64_t p = lo; p < hi;) {
-    const int rb = (int)(p / M);
-    const int64_t seg_end = hi < (int64_t)(rb + 1) * M ? hi : (int64_t)(rb + 1) * M;
-    const int64_t jlo = p - (int64_t)rb * M, jhi = seg_end - (int64_t)rb * M;
+    const int rg = (int)(p / M);
+    const int64_t seg_end = hi < (int64_t)(rg + 1) * M ? hi : (int64_t)(rg + 1) * M;
+    const int rb = rg * kGradGroups + grp;
+    // a group past the last row block has no systems (its partials are not read)
+    const int64_t jlo = p - (int64_t)rg * M, jhi = rb < R ? seg_end - (int64_t)rg * M : jlo;
     const int i0 = rb * kGradRows;
     double acc[NV];
 #pragma unroll
@@ -210,14 +226,14 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
     // the segment's systems in the order fetch / use, over both register sets
     auto sweep = [&](auto use) {
       T xa[NX], ga[kGradRows], xb[NX], gb[kGradRows];
-      int64_t j = jlo + threadIdx.x;
+      int64_t j = jlo + tg;
       if (j < jhi) fetch(j, xa, ga);
-      for (; j < jhi; j += 2 * kGradThreads) {
-        const int64_t j1 = j + kGradThreads;
+      for (; j < jhi; j += 2 * kGradGroupThreads) {
+        const int64_t j1 = j + kGradGroupThreads;
         if (j1 < jhi) fetch(j1, xb, gb);
         use(xa, ga);
         if (j1 >= jhi) break;
-        if (j1 + kGradThreads < jhi) fetch(j1 + kGradThreads, xa, ga);
+        if (j1 + kGradGroupThreads < jhi) fetch(j1 + kGradGroupThreads, xa, ga);
         use(xb, gb);
       }
     };
@@ -351,11 +367,13 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
     red[warp][2 * lane] = w32[0];
     red[warp][2 * lane + 1] = w32[1];
     __syncthreads();
-    if (threadIdx.x < NV) {
+    if (threadIdx.x < NV * kGradGroups) {
+      constexpr int WG = kGradGroupThreads / 32;  // warps per group
+      const int g = threadIdx.x / NV, v = threadIdx.x % NV;
       double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < kGradThreads / 32; w++) t += red[w][threadIdx.x];
-      partial[((int64_t)blockIdx.x * S + (rb - rb0)) * NV + threadIdx.x] = t;
+      for (int w = 0; w < WG; w++) t += red[g * WG + w][v];
+      partial[(((int64_t)blockIdx.x * S + (rg - rg0)) * kGradGroups + g) * NV + v] = t;
     }
     __syncthreads();
     p = seg_end;
@@ -365,25 +383,38 @@ k_band_grad_partial(int N, int64_t M, int R, int S, const T* __restrict__ GB, co
 // Level 2: dbands[k*N + i] = -(sum over the CTAs that touched row block
 // i / kGradRows, in CTA order); 0 outside the matrix (a periodic matrix has no
 // entries outside).
-__global__ void k_band_grad_finish(int W, int N, int64_t M, int R, int G, int S, int periodic,
+__global__ void k_band_grad_finish(int W, int N, int64_t M, int RG, int G, int S, int periodic,
                                    const double* __restrict__ partial, double* __restrict__ dbands) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)W * N) return;
   const int k = (int)(t / N), i = (int)(t % N);
-  const int rb = i / kGradRows, r = i % kGradRows;
+  const int rb = i / kGradRows, r_row = i % kGradRows;
+  const int rg = rb / kGradGroups, grp = rb % kGradGroups;
   const int col = i + k - W / 2;
-  const int64_t total = (int64_t)R * M;
-  const int64_t b_lo = (int64_t)rb * M, b_hi = b_lo + M;
-  // first CTA whose range can reach row block rb
+  const int64_t total = (int64_t)RG * M;
+  const int64_t b_lo = (int64_t)rg * M, b_hi = b_lo + M;
+  // first CTA whose range can reach block group rg; the CTA ranges
+  // [c total / G, (c + 1) total / G) are stepped with integer additions
+  // (c total / G = c q + floor(c r / G), total = q G + r)
   int64_t c = b_lo * G / total - 1;
   if (c < 0) c = 0;
+  const int64_t q = total / G, r = total - q * G;
+  int64_t lo = c * q + (c * r) / G, acc = (c * r) % G;
   double s = 0.0;
   for (; c < G; c++) {
-    const int64_t lo = range_lo(c, total, G), hi = range_lo(c + 1, total, G);
+    int64_t hi = lo + q;
+    acc += r;
+    if (acc >= G) {
+      hi += 1;
+      acc -= G;
+    }
     if (lo >= b_hi) break;
-    if (hi <= b_lo || lo == hi) continue;
-    const int seg = rb - (int)(lo / M);
-    s += partial[((c * S) + seg) * (int64_t)(W * kGradRows) + k * kGradRows + r];
+    if (hi > b_lo && lo != hi) {
+      // a CTA that starts inside the group has it as its first segment
+      const int seg = lo >= b_lo ? 0 : rg - (int)(lo / M);
+      s += partial[((c * S + seg) * kGradGroups + grp) * (int64_t)(W * kGradRows) + k * kGradRows + r_row];
+    }
+    lo = hi;
   }
   dbands[t] = (periodic || (col >= 0 && col < N)) ? -s : 0.0;
 }
@@ -425,8 +456,8 @@ cudaError_t band_grad_with_scratch(int width, int N, bool periodic, const void* 
   const int64_t ss = layout == BS_INTERLEAVED ? 1 : N;
   const GradShape g = grad_shape(N, M);
 #define BS_GRAD(TT, WW, PP)                                                                         \
-  k_band_grad_partial<TT, WW, PP><<<g.G, kGradThreads, 0, st>>>(N, M, g.R, g.S, (const TT*)GB, (const TT*)X, \
-                                                                rs, ss, scratch)
+  k_band_grad_partial<TT, WW, PP><<<g.G, kGradThreads, 0, st>>>(N, M, g.R, g.RG, g.S, (const TT*)GB,       \
+                                                                (const TT*)X, rs, ss, scratch)
   if (periodic) {  // width 3 only
     if (t == BS_F64)
       BS_GRAD(double, 3, true);
@@ -447,8 +478,8 @@ cudaError_t band_grad_with_scratch(int width, int N, bool periodic, const void* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)width * N;
-  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, M, g.R, g.G, g.S, periodic ? 1 : 0, scratch,
-                                                             dbands);
+  k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, M, g.RG, g.G, g.S, periodic ? 1 : 0,
+                                                             scratch, dbands);
   return cudaGetLastError();
 }
 

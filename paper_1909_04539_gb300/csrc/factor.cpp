@@ -92,14 +92,12 @@ bool bad(double v) { return v == 0.0 || !std::isfinite(v); }
 // (p_1 = b_1), chat_i = c_i / p_i, with c_N taken as 0.  Returns the row of
 // the first bad pivot (1-based) or 0.
 int64_t tri_factor(const double* a, const double* b, const double* c, int64_t N,
-                   std::vector<double>& r, std::vector<double>& chat, std::vector<double>* piv = nullptr) {
+                   std::vector<double>& r, std::vector<double>& chat) {
   r.assign(N, 0.0);
   chat.assign(N, 0.0);
-  if (piv) piv->assign(N, 0.0);
   for (int64_t i = 0; i < N; i++) {
     const double p = (i == 0) ? b[0] : b[i] - a[i] * chat[i - 1];
     if (bad(p)) return i + 1;
-    if (piv) (*piv)[i] = p;
     r[i] = 1.0 / p;
     chat[i] = (i + 1 < N) ? c[i] * r[i] : 0.0;
   }
@@ -142,8 +140,8 @@ int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, H
                    std::vector<double>* entries = nullptr) {
   auto C = [&](HostPlan& p, int k, int64_t i) -> double& { return p.c[(size_t)k * N + i]; };
   if (width == 3) {
-    std::vector<double> r, chat, piv;
-    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat, &piv);
+    std::vector<double> r, chat;
+    const int64_t bad_row = tri_factor(bd[0], bd[1], bd[2], N, r, chat);
     if (bad_row) return bad_row;
     // primal: dhat_i = r_i d_i - (a_i r_i) dhat_{i-1};  x_i = dhat_i - chat_i x_{i+1}
     P.bw = 1;
@@ -166,12 +164,12 @@ int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, H
       C(Q, C_T, i) = r[i];
       C(Q, C_U1, i) = (i + 1 < N) ? bd[0][i + 1] * r[i] : 0.0;
     }
-    if (entries) {  // A = L U: L = (a_i sub, p_i diag), U = (1, chat_i super)
+    if (entries) {  // the primal sweep coefficients s, l1, l2, u1, u2
       entries->assign((size_t)5 * N, 0.0);
       for (int64_t i = 0; i < N; i++) {
-        (*entries)[0 * N + i] = piv[i];
-        (*entries)[1 * N + i] = (i > 0) ? bd[0][i] : 0.0;
-        (*entries)[3 * N + i] = (i + 1 < N) ? chat[i] : 0.0;
+        (*entries)[0 * N + i] = C(P, C_S, i);
+        (*entries)[1 * N + i] = C(P, C_L1, i);
+        (*entries)[3 * N + i] = C(P, C_U1, i);
       }
     }
     return 0;
@@ -208,15 +206,11 @@ int64_t make_plans(const double* const* bd, int width, int64_t N, HostPlan& P, H
     C(Q, C_U1, i) = (i + 1 < N) ? be[i + 1] * ia : 0.0;
     C(Q, C_U2, i) = (i + 2 < N) ? ep[i + 2] * ia : 0.0;
   }
-  if (entries) {  // A = L R: L = (eps_i, beta_i, alpha_i), R = (1, gamma_i, delta_i)
+  if (entries) {  // the primal sweep coefficients s, l1, l2, u1, u2
     entries->assign((size_t)5 * N, 0.0);
-    for (int64_t i = 0; i < N; i++) {
-      (*entries)[0 * N + i] = al[i];
-      (*entries)[1 * N + i] = (i >= 1) ? be[i] : 0.0;
-      (*entries)[2 * N + i] = (i >= 2) ? ep[i] : 0.0;
-      (*entries)[3 * N + i] = (i + 1 < N) ? ga[i] : 0.0;
-      (*entries)[4 * N + i] = (i + 2 < N) ? de[i] : 0.0;
-    }
+    const int idx[5] = {C_S, C_L1, C_L2, C_U1, C_U2};
+    for (int k = 0; k < 5; k++)
+      for (int64_t i = 0; i < N; i++) (*entries)[(size_t)k * N + i] = C(P, idx[k], i);
   }
   return 0;
 }

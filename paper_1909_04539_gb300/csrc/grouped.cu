@@ -95,7 +95,7 @@ __device__ void lane_solve_pairs(const GReq& q, int64_t j) {
 template <int BW>
 __device__ void lane_solve_refine(const GReq& q, int64_t j) {
   constexpr int U = 4;  // the block of the standalone kernel: same arithmetic
-  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(q.c32, q.lu_hi, q.lu_lo, q.N);
+  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(q.lu_hi, q.lu_lo, q.N);
   const int N = q.N;
   const int64_t M = q.M;
   const float* pb = static_cast<const float*>(q.B) + j;

@@ -130,11 +130,9 @@ struct bs_factor_s {
   double* bands64;         // device, width * N, entries outside the matrix zeroed
   float* bands_hi;         // device, width * N: FP32 rounding of the bands
   float* bands_lo;         // device, width * N: FP32 rounding of (band - hi)
-  // Entries of the factors A = L U (tri) / A = L R (penta), 5 * N each:
-  // [0] L diagonal (pivot / alpha), [1] L first sub-diagonal (a / beta),
-  // [2] L second sub-diagonal (0 / eps), [3] U first super-diagonal
-  // (chat / gamma), [4] U second super-diagonal (0 / delta); FP64 values
-  // split into FP32 high and low parts.
+  // The primal sweep coefficients of plan[0] as FP64 values split into FP32
+  // high and low parts, 5 * N each: [0] s, [1] l1, [2] l2 (0 for tri),
+  // [3] u1, [4] u2 (0 for tri); the high parts equal plan[0].c32.
   float* lu_hi;
   float* lu_lo;
   size_t device_bytes;

@@ -259,7 +259,11 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
 // Factor-wise refinement, two passes (see refine_math.cuh).  Pass 1 streams B
 // up through a ring of 4-byte rows and leaves (w, delta) in the 8-byte slots
 // of X; pass 2 streams the slots down through a ring and writes the FP64
-// solution over them.  Rows move in blocks of kRU.
+// solution over them.  Rows move in blocks of kRU.  (Two adjacent systems per
+// thread -- 8-byte copies of B, 16-byte slot pairs and stores, the records
+// read once for both -- measured slower: penta N = 512, M = 65536 0.199
+// against 0.178 ms, tri N = 1024, M = 2^20 4.82 against 4.66; only M = 2^18
+// gained, 0.649 against 0.659.)
 constexpr int kRefineThreadsMax = 512;
 
 template <int BW, int D, bool SMEM>
@@ -390,7 +394,7 @@ template <int BW>
 static cudaError_t launch_refine_factor_bw(bs_handle h, const float* B, double* X, int64_t M, cudaStream_t st) {
   constexpr int D = 16;
   const int N = (int)h->N;
-  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(h->plan[0].c32, h->lu_hi, h->lu_lo, N);
+  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(h->lu_hi, h->lu_lo, N);
   const DeviceInfo& d = device_info();
   // CTA size from shared memory, registers and the busiest SM's warps
   // (staged_shape), ties to the largest: this kernel runs better in fewer,

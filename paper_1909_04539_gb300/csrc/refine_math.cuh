@@ -39,29 +39,6 @@ __device__ __forceinline__ float residual_row(float b, const float (&x)[W], cons
   return __fadd_rn(s, c);
 }
 
-// The same residual when the first term's coefficient is exactly 1 (ahi[0] =
-// 1, alo[0] = 0): that product needs no splitting, so the term is one TwoSum
-// (bitwise the value residual_row gives for finite inputs).
-template <int W>
-__device__ __forceinline__ float residual_row_unit(float b, const float (&x)[W], const float (&ahi)[W],
-                                                   const float (&alo)[W]) {
-  float s = __fsub_rn(b, x[0]);
-  const float bv0 = __fsub_rn(s, b);
-  float c = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bv0)), __fsub_rn(-x[0], bv0));
-#pragma unroll
-  for (int k = 1; k < W; k++) {
-    const float p = __fmul_rn(ahi[k], x[k]);
-    const float e = fmaf(ahi[k], x[k], -p);
-    const float t = __fsub_rn(s, p);
-    const float bv = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(-p, bv));
-    s = t;
-    c = __fadd_rn(c, __fsub_rn(err, e));
-    c = fmaf(-alo[k], x[k], c);
-  }
-  return __fadd_rn(s, c);
-}
-
 // pass 1: forward sweep of A = L U on the FP32 input b of row i
 template <int BW>
 __device__ __forceinline__ float refine_fwd(const RefineCoefs<BW>& cf, int i, float b, float& w1, float& w2) {
@@ -139,6 +116,19 @@ __device__ __forceinline__ double widen_exact(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// FP32 value whose exact FP64 widening needs no special case (normal, finite)
+__device__ __forceinline__ bool widen_plain(float f) {
+  const uint32_t e = (__float_as_uint(f) >> 23) & 0xffu;
+  return e - 1u < 254u;
+}
+
+// widen_exact of a value with widen_plain(f) (normal and finite): the five
+// integer operations of the common case, no test
+__device__ __forceinline__ double widen_normal32(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return __hiloint2double((int)((((b & 0x7fffffffu) >> 3) + (896u << 20)) | (b & 0x80000000u)), (int)(b << 29));
+}
+
 // pass 3: second sweep of A = U' L' at row i and the FP64 sum X0 + d
 template <int BW>
 __device__ __forceinline__ double refine_out(const RefineCoefs<BW>& cf, int i, float x0, float z, float& d1, float& d2) {
@@ -178,67 +168,63 @@ __host__ __device__ __forceinline__ RefineCoefs<BW> make_refine_coefs(const floa
 // ---------------------------------------------------------------------------
 // Factor-wise refinement (two passes): each triangular sweep of A = L U is
 // solved in FP32 and corrected once with the residual of that triangular
-// system evaluated to FP64 accuracy:
-//   rows up  : w = L^{-1} B (FP32);  rho = B - L w;  delta = L^{-1} rho (FP32)
+// recurrence evaluated to FP64 accuracy.  With the primal sweep coefficients
+// (s, l1, l2 forward; u1, u2 backward -- the unit upper factor) held as FP64
+// values split into FP32 (hi, lo) pairs:
+//   rows up  : w_i = s b_i - l1 w_{i-1} - l2 w_{i-2}  (FP32, hi parts);
+//              rho_i = s b_i - w_i - l1 w_{i-1} - l2 w_{i-2}  (to FP64 accuracy);
+//              delta_i = rho_i - l1 delta_{i-1} - l2 delta_{i-2}  (FP32)
 //              -> y = w + delta  (kept as the pair, 8 bytes per row)
 //   rows down: x = U^{-1} fl32(y) (FP32);  sigma = y - U x;  eps = U^{-1} sigma
 //              -> X = x + eps in FP64
-// L and U are the FP64 factors (their entries split into FP32 hi/lo pairs),
-// so X solves L U X = B to ~1e-15 relative for well-conditioned bands.
+// rho is (I + Lambda)(w* - w), Lambda the strictly lower part of the forward
+// recurrence and w* its exact solution, so delta is the FP32 solution of the
+// same recurrence without the scaling by s.  X solves L U X = B to ~1e-15
+// relative for well-conditioned bands.
 
 namespace bs {
 
 template <int BW>
 struct FRefineCoefs {
-  const float* sw[5];  // FP32 sweep coefficients s, l1, l2, u1, u2 of A = L U
-  const float* Lh[3];  // L entries (diagonal, first, second sub-diagonal), high parts
-  const float* Ll[3];  //   ... low parts
-  const float* Uh[2];  // U entries (first, second super-diagonal), high parts
-  const float* Ul[2];  //   ... low parts
+  const float* hi[5];  // s, l1, l2, u1, u2: high parts (the FP32 sweep coefficients)
+  const float* lo[5];  //   ... low parts
 };
 
-// lu = FP32 primal plan (C_COUNT * N); ehi/elo = factor entries (5 * N).
+// chi/clo: the primal sweep coefficients split into FP32 parts (5 * N each).
 template <int BW>
-__host__ __device__ __forceinline__ FRefineCoefs<BW> make_frefine_coefs(const float* lu, const float* ehi,
-                                                                       const float* elo, int64_t n) {
+__host__ __device__ __forceinline__ FRefineCoefs<BW> make_frefine_coefs(const float* chi, const float* clo,
+                                                                       int64_t n) {
   FRefineCoefs<BW> cf{};
-  const int idx[5] = {C_S, C_L1, C_L2, C_U1, C_U2};
-  for (int k = 0; k < 5; k++) cf.sw[k] = lu + idx[k] * n;
-  for (int k = 0; k < 3; k++) {
-    cf.Lh[k] = ehi + k * n;
-    cf.Ll[k] = elo + k * n;
-  }
-  for (int k = 0; k < 2; k++) {
-    cf.Uh[k] = ehi + (3 + k) * n;
-    cf.Ul[k] = elo + (3 + k) * n;
+  for (int k = 0; k < 5; k++) {
+    cf.hi[k] = chi + k * n;
+    cf.lo[k] = clo + k * n;
   }
   return cf;
 }
 
 // Coefficients of one row as the two passes use them.
 template <int BW>
-struct FRow1 {  // pass 1: sweep s, l1, l2 and the L entries (diagonal, sub-diagonals), hi/lo
+struct FRow1 {  // pass 1: s, l1, l2 (hi) and their low parts
   float s, l1, l2;
-  float ah[BW + 1], al[BW + 1];
+  float sl, l1l, l2l;
 };
 template <int BW>
-struct FRow2 {  // pass 2: sweep u1, u2 and the U super-diagonal entries, hi/lo
+struct FRow2 {  // pass 2: u1, u2 (hi) and their low parts
   float u1, u2;
-  float ah[BW], al[BW];
+  float u1l, u2l;
 };
 
 __device__ __forceinline__ float4 f4_zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// The same coefficients packed per row in shared memory (records of FRecs1
-// and FRecs2 float4s), so that a row's set arrives in one or a few 128-bit
-// loads instead of one load per value.  Layout of a pass-1 record:
-// BW = 1: (s, l1, Lh0, Ll0), (Lh1, Ll1, -, -); BW = 2: (s, l1, l2, Lh0),
-// (Ll0, Lh1, Ll1, Lh2), (Ll2, -, -, -).  Pass-2 record: BW = 1:
-// (u1, Uh0, Ul0, -); BW = 2: (u1, u2, Uh0, Ul0), (Uh1, Ul1, -, -).
+// The same coefficients packed per row in shared memory (records of R1 and
+// R2 float4s), so that a row's set arrives in one or two 128-bit loads
+// instead of one load per value.  Pass-1 record: BW = 1: (s, l1, sl, l1l);
+// BW = 2: (s, l1, l2, sl), (l1l, l2l, -, -).  Pass-2 record: BW = 1: (u1,
+// u1l, -, -); BW = 2: (u1, u2, u1l, u2l).
 template <int BW>
 struct FRefineRecs {
-  static constexpr int R1 = BW == 1 ? 2 : 3;
-  static constexpr int R2 = BW == 1 ? 1 : 2;
+  static constexpr int R1 = BW == 1 ? 1 : 2;
+  static constexpr int R2 = 1;
   const float4* r1;  // N * R1
   const float4* r2;  // N * R2
 };
@@ -246,26 +232,21 @@ struct FRefineRecs {
 template <int BW>
 __device__ __forceinline__ FRow1<BW> frow1(const FRefineCoefs<BW>& cf, int i) {
   FRow1<BW> c;
-  c.s = cf.sw[0][i];
-  c.l1 = cf.sw[1][i];
-  c.l2 = (BW == 2) ? cf.sw[2][i] : 0.f;
-#pragma unroll
-  for (int k = 0; k <= BW; k++) {
-    c.ah[k] = cf.Lh[k][i];
-    c.al[k] = cf.Ll[k][i];
-  }
+  c.s = cf.hi[0][i];
+  c.l1 = cf.hi[1][i];
+  c.l2 = (BW == 2) ? cf.hi[2][i] : 0.f;
+  c.sl = cf.lo[0][i];
+  c.l1l = cf.lo[1][i];
+  c.l2l = (BW == 2) ? cf.lo[2][i] : 0.f;
   return c;
 }
 template <int BW>
 __device__ __forceinline__ FRow2<BW> frow2(const FRefineCoefs<BW>& cf, int i) {
   FRow2<BW> c;
-  c.u1 = cf.sw[3][i];
-  c.u2 = (BW == 2) ? cf.sw[4][i] : 0.f;
-#pragma unroll
-  for (int k = 0; k < BW; k++) {
-    c.ah[k] = cf.Uh[k][i];
-    c.al[k] = cf.Ul[k][i];
-  }
+  c.u1 = cf.hi[3][i];
+  c.u2 = (BW == 2) ? cf.hi[4][i] : 0.f;
+  c.u1l = cf.lo[3][i];
+  c.u2l = (BW == 2) ? cf.lo[4][i] : 0.f;
   return c;
 }
 template <int BW>
@@ -273,26 +254,22 @@ __device__ __forceinline__ FRow1<BW> frow1(const FRefineRecs<BW>& rc, int i) {
   FRow1<BW> c;
   const float4* p = rc.r1 + (size_t)i * FRefineRecs<BW>::R1;
   if constexpr (BW == 1) {
-    const float4 a = p[0], b = p[1];
-    c.s = a.x, c.l1 = a.y, c.l2 = 0.f;
-    c.ah[0] = a.z, c.al[0] = a.w, c.ah[1] = b.x, c.al[1] = b.y;
+    const float4 a = p[0];
+    c.s = a.x, c.l1 = a.y, c.l2 = 0.f, c.sl = a.z, c.l1l = a.w, c.l2l = 0.f;
   } else {
-    const float4 a = p[0], b = p[1], d = p[2];
-    c.s = a.x, c.l1 = a.y, c.l2 = a.z;
-    c.ah[0] = a.w, c.al[0] = b.x, c.ah[1] = b.y, c.al[1] = b.z, c.ah[2] = b.w, c.al[2] = d.x;
+    const float4 a = p[0], b = p[1];
+    c.s = a.x, c.l1 = a.y, c.l2 = a.z, c.sl = a.w, c.l1l = b.x, c.l2l = b.y;
   }
   return c;
 }
 template <int BW>
 __device__ __forceinline__ FRow2<BW> frow2(const FRefineRecs<BW>& rc, int i) {
   FRow2<BW> c;
-  const float4* p = rc.r2 + (size_t)i * FRefineRecs<BW>::R2;
+  const float4 a = rc.r2[i];
   if constexpr (BW == 1) {
-    const float4 a = p[0];
-    c.u1 = a.x, c.u2 = 0.f, c.ah[0] = a.y, c.al[0] = a.z;
+    c.u1 = a.x, c.u2 = 0.f, c.u1l = a.y, c.u2l = 0.f;
   } else {
-    const float4 a = p[0], b = p[1];
-    c.u1 = a.x, c.u2 = a.y, c.ah[0] = a.z, c.al[0] = a.w, c.ah[1] = b.x, c.al[1] = b.y;
+    c.u1 = a.x, c.u2 = a.y, c.u1l = a.z, c.u2l = a.w;
   }
   return c;
 }
@@ -306,19 +283,34 @@ __device__ __forceinline__ void pack_frefine_recs(const FRefineCoefs<BW>& cf, in
     const FRow1<BW> a = frow1<BW>(cf, i);
     const FRow2<BW> b = frow2<BW>(cf, i);
     float4* p1 = r1 + (size_t)i * FRefineRecs<BW>::R1;
-    float4* p2 = r2 + (size_t)i * FRefineRecs<BW>::R2;
     if constexpr (BW == 1) {
-      p1[0] = make_float4(a.s, a.l1, a.ah[0], a.al[0]);
-      p1[1] = make_float4(a.ah[1], a.al[1], 0.f, 0.f);
-      p2[0] = make_float4(b.u1, b.ah[0], b.al[0], 0.f);
+      p1[0] = make_float4(a.s, a.l1, a.sl, a.l1l);
+      r2[i] = make_float4(b.u1, b.u1l, 0.f, 0.f);
     } else {
-      p1[0] = make_float4(a.s, a.l1, a.l2, a.ah[0]);
-      p1[1] = make_float4(a.al[0], a.ah[1], a.al[1], a.ah[2]);
-      p1[2] = make_float4(a.al[2], 0.f, 0.f, 0.f);
-      p2[0] = make_float4(b.u1, b.u2, b.ah[0], b.al[0]);
-      p2[1] = make_float4(b.ah[1], b.al[1], 0.f, 0.f);
+      p1[0] = make_float4(a.s, a.l1, a.l2, a.sl);
+      p1[1] = make_float4(a.l1l, a.l2l, 0.f, 0.f);
+      r2[i] = make_float4(b.u1, b.u2, b.u1l, b.u2l);
     }
   }
+}
+
+// a - b = s + e exactly (Knuth's TwoSum on -b)
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+  s = __fsub_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(-b, bv));
+}
+
+// t + c -= (ch + cl) y with the product ch * y split exactly (FMA) and the
+// subtraction from t error-free; the low-order terms collect in c
+__device__ __forceinline__ void resid_term(float& t, float& c, float ch, float cl, float y) {
+  const float q = __fmul_rn(ch, y);
+  const float eq = fmaf(ch, y, -q);  // ch * y = q + eq exactly
+  float s, e;
+  two_diff(t, q, s, e);
+  t = s;
+  c = __fadd_rn(c, __fsub_rn(e, eq));
+  c = fmaf(-cl, y, c);
 }
 
 // Rows i0 .. i0+n-1 of the first pass.  b: the FP32 inputs; on exit w, d
@@ -328,18 +320,19 @@ __device__ __forceinline__ void pack_frefine_recs(const FRefineCoefs<BW>& cf, in
 template <int BW, int U, typename Acc>
 __device__ __forceinline__ void frefine_pass1(const Acc& cf, int i0, int n, const float (&b)[U], float (&w)[U],
                                               float (&d)[U], float& w1, float& w2, float& d1, float& d2) {
-  constexpr int W = BW + 1;
   FRow1<BW> c[U];
 #pragma unroll
   for (int u = 0; u < U; u++) c[u] = frow1<BW>(cf, (u < n) ? i0 + u : i0);
-  float wp1[U], wp2[U];
-  // forward sweep of w (the chain)
+  float wp1[U], wp2[U], p[U];
+  // forward sweep of w (the chain); p = fl(s b), the first term of both the
+  // sweep and the residual
 #pragma unroll
   for (int u = 0; u < U; u++) {
     wp1[u] = w1;
     wp2[u] = w2;
+    p[u] = __fmul_rn(b[u], c[u].s);
     if (u < n) {
-      float x = b[u] * c[u].s;
+      float x = p[u];
       if (BW == 2) x = fmaf(-c[u].l2, w2, x);
       x = fmaf(-c[u].l1, w1, x);
       w[u] = x;
@@ -353,18 +346,20 @@ __device__ __forceinline__ void frefine_pass1(const Acc& cf, int i0, int n, cons
   for (int u = 0; u < U; u++) {
     rho[u] = 0.f;
     if (u < n) {
-      float x[W];
-      x[0] = w[u];
-      x[1] = wp1[u];
-      if (BW == 2) x[W - 1] = wp2[u];
-      rho[u] = residual_row<W>(b[u], x, c[u].ah, c[u].al);
+      float cc = fmaf(c[u].sl, b[u], fmaf(c[u].s, b[u], -p[u]));  // s b = p + cc to FP64 accuracy
+      float t, e;
+      two_diff(p[u], w[u], t, e);
+      cc = __fadd_rn(cc, e);
+      resid_term(t, cc, c[u].l1, c[u].l1l, wp1[u]);
+      if (BW == 2) resid_term(t, cc, c[u].l2, c[u].l2l, wp2[u]);
+      rho[u] = __fadd_rn(t, cc);
     }
   }
   // forward sweep of the correction
 #pragma unroll
   for (int u = 0; u < U; u++) {
     if (u < n) {
-      float x = rho[u] * c[u].s;
+      float x = rho[u];
       if (BW == 2) x = fmaf(-c[u].l2, d2, x);
       x = fmaf(-c[u].l1, d1, x);
       d[u] = x;
@@ -380,7 +375,6 @@ template <int BW, int U, typename Acc>
 __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, const float (&w)[U],
                                               const float (&dl)[U], double (&X)[U], float& x1, float& x2,
                                               float& e1, float& e2) {
-  constexpr int W = BW + 1;
   FRow2<BW> c[U];
 #pragma unroll
   for (int u = 0; u < U; u++) c[u] = frow2<BW>(cf, (u < n) ? top - u : top);
@@ -390,6 +384,7 @@ __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, con
   for (int u = 0; u < U; u++) {
     xn1[u] = x1;
     xn2[u] = x2;
+    x[u] = 1.f;
     if (u < n) {
       float v = __fadd_rn(w[u], dl[u]);
       if (BW == 2) v = fmaf(-c[u].u2, x2, v);
@@ -399,38 +394,44 @@ __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, con
       x1 = v;
     }
   }
-  // residuals sigma = (w + dl) - U x of the rows
+  // residuals sigma = (w + dl) - U x of the rows (U has a unit diagonal)
   float sig[U];
 #pragma unroll
   for (int u = 0; u < U; u++) {
     sig[u] = 0.f;
     if (u < n) {
-      float xs[W], ah[W], al[W];
-      xs[0] = x[u];
-      ah[0] = 1.f;
-      al[0] = 0.f;
-      xs[1] = xn1[u];
-      ah[1] = c[u].ah[0];
-      al[1] = c[u].al[0];
-      if (BW == 2) {
-        xs[W - 1] = xn2[u];
-        ah[W - 1] = c[u].ah[1];
-        al[W - 1] = c[u].al[1];
-      }
-      sig[u] = __fadd_rn(residual_row_unit<W>(w[u], xs, ah, al), dl[u]);
+      float t, cc;
+      two_diff(w[u], x[u], t, cc);
+      resid_term(t, cc, c[u].u1, c[u].u1l, xn1[u]);
+      if (BW == 2) resid_term(t, cc, c[u].u2, c[u].u2l, xn2[u]);
+      sig[u] = __fadd_rn(__fadd_rn(t, cc), dl[u]);
     }
   }
-  // backward sweep of the correction and the FP64 sum
+  // backward sweep of the correction
+  float ev[U];
+  bool plain = true;
 #pragma unroll
   for (int u = 0; u < U; u++) {
+    ev[u] = 1.f;
     if (u < n) {
       float v = sig[u];
       if (BW == 2) v = fmaf(-c[u].u2, e2, v);
       v = fmaf(-c[u].u1, e1, v);
       e2 = e1;
       e1 = v;
-      X[u] = widen_exact(x[u]) + widen_exact(v);
+      ev[u] = v;
     }
+    plain = plain && widen_plain(x[u]) && widen_plain(ev[u]);
+  }
+  // X = x + eps in FP64: the exactly widened parts added once; one vote per
+  // block for the rare values (zero, subnormal, inf, NaN) that need the
+  // general widening
+  if (__any_sync(__activemask(), !plain)) {
+#pragma unroll
+    for (int u = 0; u < U; u++) X[u] = widen_exact(x[u]) + widen_exact(ev[u]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; u++) X[u] = widen_normal32(x[u]) + widen_normal32(ev[u]);
   }
 }
 

@@ -11,7 +11,7 @@ enum { SERVE_F64 = 0, SERVE_F32_REFINE = 1 };
 struct GReq {
   const double* c64;  // primal sweep coefficients, FP64 (C_COUNT * N)
   const float* c32;   // primal sweep coefficients, FP32
-  const float* lu_hi; // entries of the factors L, U: FP32 high parts (5 * N)
+  const float* lu_hi; // primal sweep coefficients s, l1, l2, u1, u2: FP32 high parts (5 * N)
   const float* lu_lo; //   ... low parts
   const float* dfrec; // primal coefficient pairs (SweepPlan::dfrec)
   void* B;            // SERVE_F64: double, solved in place; SERVE_F32_REFINE: float input
