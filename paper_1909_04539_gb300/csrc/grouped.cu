@@ -13,6 +13,7 @@ namespace bs {
 
 constexpr int kGroupThreads = 128;
 constexpr int kGroupU = 8;
+constexpr int kGroupD = 16;  // rows in flight per lane (the standalone kernels' ring depth)
 
 template <int BW>
 __device__ void lane_solve_f64(const GReq& q, int64_t j) {
@@ -50,93 +51,11 @@ __device__ void lane_solve_f64(const GReq& q, int64_t j) {
   }
 }
 
-// FP64 data in FP32 pairs: the row groups of the two-sweep kernel
-// (df_sweep.cuh), the forward values kept in place in B
-template <int BW>
-__device__ void lane_solve_pairs(const GReq& q, int64_t j) {
-  constexpr int U = 4;  // the block of the standalone kernel: the same switch rows
-  const DfRecs rc = df_recs_of(q.dfrec, q.N);
-  const Coefs<double> c64 = coefs_of<double>(q.c64, q.N);
-  double* x = static_cast<double*>(q.B) + j;
-  const int N = q.N;
-  const int64_t M = q.M;
-  DfState<1> st;
-  st.reset_values();
-  st.f64 = false;
-  st.rsw = N;
-#pragma unroll 1
-  for (int i0 = 0; i0 < N; i0 += U) {
-    const int n = (N - i0) < U ? (N - i0) : U;
-    double f[U][1];
-    uint2 w[U][1];
-#pragma unroll
-    for (int u = 0; u < U; u++) f[u][0] = (u < n) ? x[(int64_t)(i0 + u) * M] : 0.0;
-    df_fwd_group<BW, false, 1, U, false>(rc, c64, i0, n, f, w, st);
-#pragma unroll
-    for (int u = 0; u < U; u++)
-      if (u < n) *reinterpret_cast<uint2*>(x + (int64_t)(i0 + u) * M) = w[u][0];
-  }
-  st.reset_values();
-#pragma unroll 1
-  for (int top = N - 1; top >= 0; top -= U) {
-    const int n = (top + 1) < U ? (top + 1) : U;
-    uint2 w[U][1];
-    double xo[U][1];
-#pragma unroll
-    for (int u = 0; u < U; u++)
-      w[u][0] = (u < n) ? *reinterpret_cast<const uint2*>(x + (int64_t)(top - u) * M) : make_uint2(0u, 0u);
-    df_bwd_group<BW, false, 1, U, false>(rc, c64, top, n, w, xo, st);
-#pragma unroll
-    for (int u = 0; u < U; u++)
-      if (u < n) x[(int64_t)(top - u) * M] = xo[u][0];
-  }
-}
-
-template <int BW>
-__device__ void lane_solve_refine(const GReq& q, int64_t j) {
-  constexpr int U = 4;  // the block of the standalone kernel: same arithmetic
-  const FRefineCoefs<BW> cf = make_frefine_coefs<BW>(q.lu_hi, q.lu_lo, q.N);
-  const int N = q.N;
-  const int64_t M = q.M;
-  const float* pb = static_cast<const float*>(q.B) + j;
-  double* px = q.X + j;
-  float2* ps = reinterpret_cast<float2*>(q.X) + j;
-  {
-    float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += U) {
-      const int n = (N - i0) < U ? (N - i0) : U;
-      float b[U], w[U], d[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) b[u] = (u < n) ? pb[(int64_t)(i0 + u) * M] : 0.f;
-      frefine_pass1<BW, U>(cf, i0, n, b, w, d, w1, w2, d1, d2);
-#pragma unroll
-      for (int u = 0; u < U; u++)
-        if (u < n) ps[(int64_t)(i0 + u) * M] = make_float2(w[u], d[u]);
-    }
-  }
-  {
-    float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
-#pragma unroll 1
-    for (int top = N - 1; top >= 0; top -= U) {
-      const int n = (top + 1) < U ? (top + 1) : U;
-      float w[U], dl[U];
-      double xo[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const float2 v = (u < n) ? ps[(int64_t)(top - u) * M] : make_float2(0.f, 0.f);
-        w[u] = v.x;
-        dl[u] = v.y;
-      }
-      frefine_pass2<BW, U>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
-#pragma unroll
-      for (int u = 0; u < U; u++)
-        if (u < n) px[(int64_t)(top - u) * M] = xo[u];
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kGroupThreads) k_grouped(const unsigned char* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* ring = smem_raw + (size_t)threadIdx.x * 8;  // the lane's ring of kGroupD 8-byte slots
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * 8;
   const GHeader* hdr = reinterpret_cast<const GHeader*>(work);
   const GReq* reqs = reinterpret_cast<const GReq*>(work + kGroupReqOff);
   const GTile* tiles = reinterpret_cast<const GTile*>(work + kGroupTileOff);
@@ -149,28 +68,46 @@ __global__ void __launch_bounds__(kGroupThreads) k_grouped(const unsigned char* 
     const int64_t j = (int64_t)tile.j0 + lane;
     if (j >= q.M) continue;
     if (q.mode == SERVE_F64 && q.pairs) {
+      // the standalone pair solve's lane body, records read from global memory
+      const DfRecs rc = df_recs_of(q.dfrec, q.N);
+      const Coefs<double> c64 = coefs_of<double>(q.c64, q.N);
+      double* x = static_cast<double*>(q.B) + j;
       if (q.width == 3)
-        lane_solve_pairs<1>(q, j);
+        df_sweep_systems<1, false, 1, kGroupD>(rc, c64, q.N, x, q.M, ring, ring_s, pitch);
       else
-        lane_solve_pairs<2>(q, j);
+        df_sweep_systems<2, false, 1, kGroupD>(rc, c64, q.N, x, q.M, ring, ring_s, pitch);
     } else if (q.mode == SERVE_F64) {
       if (q.width == 3)
         lane_solve_f64<1>(q, j);
       else
         lane_solve_f64<2>(q, j);
     } else {
+      // the standalone mixed-precision kernel's lane body, coefficients read
+      // from global memory
+      const float* B = static_cast<const float*>(q.B);
       if (q.width == 3)
-        lane_solve_refine<1>(q, j);
+        refine_factor_system<1, kGroupD>(make_frefine_coefs<1>(q.lu_hi, q.lu_lo, q.N), q.N, B, q.X, q.M, j, ring,
+                                         ring_s, pitch);
       else
-        lane_solve_refine<2>(q, j);
+        refine_factor_system<2, kGroupD>(make_frefine_coefs<2>(q.lu_hi, q.lu_lo, q.N), q.N, B, q.X, q.M, j, ring,
+                                         ring_s, pitch);
     }
   }
 }
 
-int grouped_grid() { return device_info().sms * 4; }
+// One wave: the CTAs that fit on the device at once (registers and the
+// rings' shared memory decide how many per SM).
+int grouped_grid() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_grouped, kGroupThreads,
+                                                    (size_t)kGroupThreads * kGroupD * 8) != cudaSuccess ||
+      n < 1)
+    n = 1;
+  return device_info().sms * n;
+}
 
 cudaError_t launch_grouped(const unsigned char* d_work, int grid, cudaStream_t st) {
-  k_grouped<<<grid, kGroupThreads, 0, st>>>(d_work);
+  k_grouped<<<grid, kGroupThreads, (size_t)kGroupThreads * kGroupD * 8, st>>>(d_work);
   return cudaGetLastError();
 }
 

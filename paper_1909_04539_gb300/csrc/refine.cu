@@ -33,9 +33,6 @@
 namespace bs {
 
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-}
 
 // FP32 B (4-byte lane rows in pass 1), 8-byte slots in passes 2 and 3; ring of
 // D slots of 8 bytes per lane.  Rows move in blocks of kRU: a block's ring
@@ -256,20 +253,18 @@ k_refine(RefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M, int st
   }
 }
 
-// Factor-wise refinement, two passes (see refine_math.cuh).  Pass 1 streams B
-// up through a ring of 4-byte rows and leaves (w, delta) in the 8-byte slots
-// of X; pass 2 streams the slots down through a ring and writes the FP64
-// solution over them.  Rows move in blocks of kRU.  (Two adjacent systems per
-// thread -- 8-byte copies of B, 16-byte slot pairs and stores, the records
-// read once for both -- measured slower: penta N = 512, M = 65536 0.199
-// against 0.178 ms, tri N = 1024, M = 2^20 4.82 against 4.66; only M = 2^18
-// gained, 0.649 against 0.659.)
+// Factor-wise refinement, two passes (refine_factor_system in
+// refine_math.cuh, shared with the grouped serving kernel), one system per
+// thread, the coefficient records staged in shared memory once per CTA.
+// (Two adjacent systems per thread -- 8-byte copies of B, 16-byte slot pairs
+// and stores, the records read once for both -- measured slower: penta N =
+// 512, M = 65536 0.199 against 0.178 ms, tri N = 1024, M = 2^20 4.82 against
+// 4.66; only M = 2^18 gained, 0.649 against 0.659.)
 constexpr int kRefineThreadsMax = 512;
 
 template <int BW, int D, bool SMEM>
 __global__ void __launch_bounds__(kRefineThreadsMax)
 k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M) {
-  static_assert(D % kRU == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FRefineCoefs<BW> cf = cg;
   // with SMEM, every row's coefficients packed into one record per pass
@@ -290,103 +285,10 @@ k_refine_factor(FRefineCoefs<BW> cg, int N, const float* B, double* X, int64_t M
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
 
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const float* pb = B + j;
-    double* px = X + j;
-    float2* ps = reinterpret_cast<float2*>(X) + j;
-
-    // ---- pass 1 (rows up): slot <- (w, delta).  Row addresses advance by
-    // pointer increments (no 64-bit multiply per row).  One copy group per
-    // block of kRU rows (a block waits for the group committed D / kRU
-    // groups earlier); FULL blocks -- all kRU rows exist and each refills its
-    // slot -- run without per-row guards.
-    {
-      float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
-      const float* pnext = pb;  // next row to request
-#pragma unroll 1
-      for (int r = 0; r < D; r++) {
-        if (r < N) cp_async4(ring_s + r * pitch, pnext);
-        pnext += M;
-        if ((r + 1) % kRU == 0) cp_commit();
-      }
-      float2* prow = ps;  // slot of row i0
-      auto pass1 = [&](auto full_tag, int i0) {
-        constexpr bool FULL = decltype(full_tag)::value;
-        cp_wait<D / kRU - 1>();
-        const int n = FULL ? kRU : ((N - i0) < kRU ? (N - i0) : kRU);
-        const int s0 = i0 % D;
-        float b[kRU], w[kRU], d[kRU];
-#pragma unroll
-        for (int u = 0; u < kRU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-          if (FULL || (u < n && i0 + u + D < N)) cp_async4(ring_s + (s0 + u) * pitch, pnext);
-          pnext += M;
-        }
-        cp_commit();
-        if constexpr (SMEM)
-          frefine_pass1<BW, kRU>(rc, i0, n, b, w, d, w1, w2, d1, d2);
-        else
-          frefine_pass1<BW, kRU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-          if (FULL || u < n) *prow = make_float2(w[u], d[u]);
-          prow += M;
-        }
-      };
-      int i0 = 0;
-#pragma unroll 1
-      for (; i0 + kRU + D <= N; i0 += kRU) pass1(std::true_type{}, i0);
-#pragma unroll 1
-      for (; i0 < N; i0 += kRU) pass1(std::false_type{}, i0);
-      cp_wait<0>();
-    }
-    // ---- pass 2 (rows down): X
-    {
-      float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
-      const float2* pback = ps + (int64_t)(N - 1) * M;  // next slot row to request
-#pragma unroll 1
-      for (int r = 0; r < D; r++) {
-        if (N - 1 - r >= 0) cp_async8(ring_s + r * pitch, pback);
-        pback -= M;
-        if ((r + 1) % kRU == 0) cp_commit();
-      }
-      double* pout = px + (int64_t)(N - 1) * M;  // output row `top`
-      auto pass2 = [&](auto full_tag, int top) {
-        constexpr bool FULL = decltype(full_tag)::value;
-        cp_wait<D / kRU - 1>();
-        const int n = FULL ? kRU : ((top + 1) < kRU ? (top + 1) : kRU);
-        const int s0 = (N - 1 - top) % D;
-        float w[kRU], dl[kRU];
-        double xo[kRU];
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-          const float2 v = *reinterpret_cast<const float2*>(ring + (size_t)(s0 + u) * pitch);
-          w[u] = v.x;
-          dl[u] = v.y;
-        }
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-          if (FULL || (u < n && top - u - D >= 0)) cp_async8(ring_s + (s0 + u) * pitch, pback);
-          pback -= M;
-        }
-        cp_commit();
-        if constexpr (SMEM)
-          frefine_pass2<BW, kRU>(rc, top, n, w, dl, xo, x1, x2, e1, e2);
-        else
-          frefine_pass2<BW, kRU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-          if (FULL || u < n) *pout = xo[u];
-          pout -= M;
-        }
-      };
-      int top = N - 1;
-#pragma unroll 1
-      for (; top >= D + kRU - 1; top -= kRU) pass2(std::true_type{}, top);
-#pragma unroll 1
-      for (; top >= 0; top -= kRU) pass2(std::false_type{}, top);
-      cp_wait<0>();
-    }
+    if constexpr (SMEM)
+      refine_factor_system<BW, D>(rc, N, B, X, M, j, ring, ring_s, pitch);
+    else
+      refine_factor_system<BW, D>(cf, N, B, X, M, j, ring, ring_s, pitch);
   }
 }
 

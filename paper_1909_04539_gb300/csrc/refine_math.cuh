@@ -435,4 +435,111 @@ __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, con
   }
 }
 
+// Rows move in blocks of kRfU.
+constexpr int kRfU = 4;
+
+// The two passes of the factor-wise refinement for system j (column j of B
+// and X, row stride M) through the lane's ring of D slots of 8 bytes (ring:
+// its first slot, generic and shared-window addresses; pitch: bytes between
+// slots).  Pass 1 streams B up through the ring and leaves (w, delta) in the
+// 8-byte slots of X; pass 2 streams the slots down through the ring and
+// writes the FP64 solution over them.  Acc: FRefineCoefs or FRefineRecs.
+template <int BW, int D, typename Acc>
+__device__ __forceinline__ void refine_factor_system(const Acc& cf, int N, const float* B, double* X, int64_t M,
+                                                     int64_t j, const unsigned char* ring, uint32_t ring_s,
+                                                     uint32_t pitch) {
+  static_assert(D % kRfU == 0, "ring depth must be a multiple of the block");
+  const float* pb = B + j;
+  double* px = X + j;
+  float2* ps = reinterpret_cast<float2*>(X) + j;
+
+  // ---- pass 1 (rows up): slot <- (w, delta).  Row addresses advance by
+  // pointer increments (no 64-bit multiply per row).  One copy group per
+  // block of kRfU rows (a block waits for the group committed D / kRfU
+  // groups earlier); FULL blocks -- all kRfU rows exist and each refills its
+  // slot -- run without per-row guards.
+  {
+    float w1 = 0.f, w2 = 0.f, d1 = 0.f, d2 = 0.f;
+    const float* pnext = pb;  // next row to request
+#pragma unroll 1
+    for (int r = 0; r < D; r++) {
+      if (r < N) cp_async4(ring_s + r * pitch, pnext);
+      pnext += M;
+      if ((r + 1) % kRfU == 0) cp_commit();
+    }
+    float2* prow = ps;  // slot of row i0
+    auto pass1 = [&](auto full_tag, int i0) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      cp_wait<D / kRfU - 1>();
+      const int n = FULL ? kRfU : ((N - i0) < kRfU ? (N - i0) : kRfU);
+      const int s0 = i0 % D;
+      float b[kRfU], w[kRfU], d[kRfU];
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) b[u] = *reinterpret_cast<const float*>(ring + (size_t)(s0 + u) * pitch);
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) {
+        if (FULL || (u < n && i0 + u + D < N)) cp_async4(ring_s + (s0 + u) * pitch, pnext);
+        pnext += M;
+      }
+      cp_commit();
+      frefine_pass1<BW, kRfU>(cf, i0, n, b, w, d, w1, w2, d1, d2);
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) {
+        if (FULL || u < n) *prow = make_float2(w[u], d[u]);
+        prow += M;
+      }
+    };
+    int i0 = 0;
+#pragma unroll 1
+    for (; i0 + kRfU + D <= N; i0 += kRfU) pass1(std::true_type{}, i0);
+#pragma unroll 1
+    for (; i0 < N; i0 += kRfU) pass1(std::false_type{}, i0);
+    cp_wait<0>();
+  }
+  // ---- pass 2 (rows down): X
+  {
+    float x1 = 0.f, x2 = 0.f, e1 = 0.f, e2 = 0.f;
+    const float2* pback = ps + (int64_t)(N - 1) * M;  // next slot row to request
+#pragma unroll 1
+    for (int r = 0; r < D; r++) {
+      if (N - 1 - r >= 0) cp_async8(ring_s + r * pitch, pback);
+      pback -= M;
+      if ((r + 1) % kRfU == 0) cp_commit();
+    }
+    double* pout = px + (int64_t)(N - 1) * M;  // output row `top`
+    auto pass2 = [&](auto full_tag, int top) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      cp_wait<D / kRfU - 1>();
+      const int n = FULL ? kRfU : ((top + 1) < kRfU ? (top + 1) : kRfU);
+      const int s0 = (N - 1 - top) % D;
+      float w[kRfU], dl[kRfU];
+      double xo[kRfU];
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) {
+        const float2 v = *reinterpret_cast<const float2*>(ring + (size_t)(s0 + u) * pitch);
+        w[u] = v.x;
+        dl[u] = v.y;
+      }
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) {
+        if (FULL || (u < n && top - u - D >= 0)) cp_async8(ring_s + (s0 + u) * pitch, pback);
+        pback -= M;
+      }
+      cp_commit();
+      frefine_pass2<BW, kRfU>(cf, top, n, w, dl, xo, x1, x2, e1, e2);
+#pragma unroll
+      for (int u = 0; u < kRfU; u++) {
+        if (FULL || u < n) *pout = xo[u];
+        pout -= M;
+      }
+    };
+    int top = N - 1;
+#pragma unroll 1
+    for (; top >= D + kRfU - 1; top -= kRfU) pass2(std::true_type{}, top);
+#pragma unroll 1
+    for (; top >= 0; top -= kRfU) pass2(std::false_type{}, top);
+    cp_wait<0>();
+  }
+}
+
 }  // namespace bs

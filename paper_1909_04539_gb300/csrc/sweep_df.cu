@@ -32,47 +32,10 @@ namespace {
 
 constexpr int kDfThreadsMax = 512;
 
-// V lane-rows of 8-byte values (pairs or FP64) in a ring slot or in memory
-template <int V>
-__device__ __forceinline__ void ld8(const void* p, uint2 (&o)[V]) {
-  if constexpr (V == 2) {
-    const uint4 t = *reinterpret_cast<const uint4*>(p);
-    o[0] = make_uint2(t.x, t.y);
-    o[1] = make_uint2(t.z, t.w);
-  } else {
-    o[0] = *reinterpret_cast<const uint2*>(p);
-  }
-}
-template <int V>
-__device__ __forceinline__ void st8(void* p, const uint2 (&x)[V]) {
-  if constexpr (V == 2)
-    *reinterpret_cast<uint4*>(p) = make_uint4(x[0].x, x[0].y, x[1].x, x[1].y);
-  else
-    *reinterpret_cast<uint2*>(p) = x[0];
-}
-template <int V>
-__device__ __forceinline__ void ld_f64v(const void* p, double (&o)[V]) {
-  if constexpr (V == 2) {
-    const double2 t = *reinterpret_cast<const double2*>(p);
-    o[0] = t.x;
-    o[1] = t.y;
-  } else {
-    o[0] = *reinterpret_cast<const double*>(p);
-  }
-}
-template <int V>
-__device__ __forceinline__ void st_f64v(void* p, const double (&x)[V]) {
-  if constexpr (V == 2)
-    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
-  else
-    *reinterpret_cast<double*>(p) = x[0];
-}
-
 template <int BW, bool ADJ, bool SMEM, int V, int D>
 __global__ void __launch_bounds__(kDfThreadsMax)
 k_sweep_df(DfRecs rg, Coefs<double> c64, int N, double* X, int64_t M) {
-  constexpr int U = 4;  // rows per block; D is a multiple of U
-  static_assert(D % U == 0, "ring depth must be a multiple of the block");
+  static_assert(D % 4 == 0, "ring depth must be a multiple of the block");
   constexpr int SLOT = 8 * V;
   constexpr bool F2 = DfCount<ADJ, BW>::F > 2, B2 = DfCount<ADJ, BW>::B > 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -98,98 +61,8 @@ k_sweep_df(DfRecs rg, Coefs<double> c64, int N, double* X, int64_t M) {
   const uint32_t pitch = blockDim.x * SLOT;
   const int64_t ngroups = M / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
-    double* const pout = X + g * V;
-    DfState<V> st;
-    st.reset_values();
-    st.f64 = false;
-    st.rsw = N;
-    // forward sweep: rows 0..D-1 requested up front (one copy group per
-    // block of U rows); each block then waits for its group, computes and
-    // refills its slots with the rows D further down
-    const double* pnext = pout;
-#pragma unroll 1
-    for (int r = 0; r < D; r++) {
-      if (r < N) copy_row<double, V>(ring_s + r * pitch, pnext);
-      pnext += M;
-      if ((r + 1) % U == 0) cp_commit();
-    }
-    double* prow = pout;
-    auto fwd = [&](auto full_tag, int i0) {
-      constexpr bool FULL = decltype(full_tag)::value;
-      cp_wait<D / U - 1>();
-      const int n = FULL ? U : ((N - i0) < U ? (N - i0) : U);
-      const int s0 = i0 % D;
-      double f[U][V];
-      uint2 w[U][V];
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (FULL || u < n)
-          ld_f64v<V>(ring + (size_t)(s0 + u) * pitch, f[u]);
-        else
-#pragma unroll
-          for (int v = 0; v < V; v++) f[u][v] = 0.0;
-      }
-      df_fwd_group<BW, ADJ, V, U, FULL>(rc, c64, i0, n, f, w, st);
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int i = i0 + u;
-        if (FULL || u < n) {
-          const bool keep = !FULL && i + D >= N;  // tail row: stays in the ring
-          st8<V>(keep ? static_cast<void*>(ring + (size_t)(s0 + u) * pitch) : static_cast<void*>(prow), w[u]);
-          if (!keep) copy_row<double, V>(ring_s + (s0 + u) * pitch, pnext);
-        }
-        prow += M;
-        pnext += M;
-      }
-      cp_commit();
-    };
-    int i0 = 0;
-#pragma unroll 1
-    for (; i0 + U + D <= N; i0 += U) fwd(std::true_type{}, i0);
-#pragma unroll 1
-    for (; i0 < N; i0 += U) fwd(std::false_type{}, i0);
-
-    // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
-    // into the slot row i frees (blocks aligned to N - 1, one group each)
-    const int tail = N - D;
-    prow = pout + (int64_t)(N - 1) * M;
-    const double* pback = pout + (int64_t)(N - 1 - D) * M;
-    st.reset_values();
-    auto bwd = [&](auto full_tag, int top) {
-      constexpr bool FULL = decltype(full_tag)::value;
-      const int n = FULL ? U : ((top + 1) < U ? (top + 1) : U);
-      if (FULL || top - (n - 1) < tail) cp_wait<D / U - 1>();
-      uint2 w[U][V];
-      double x[U][V];
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (FULL || u < n)
-          ld8<V>(ring + (size_t)((top - u) % D) * pitch, w[u]);
-        else
-#pragma unroll
-          for (int v = 0; v < V; v++) w[u][v] = make_uint2(0u, 0u);
-      }
-      df_bwd_group<BW, ADJ, V, U, FULL>(rc, c64, top, n, w, x, st);
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int i = top - u;
-        if (FULL || u < n) {
-          st_f64v<V>(prow, x[u]);
-          if (FULL || i - D >= 0) copy_row<double, V>(ring_s + (i % D) * pitch, pback);
-        }
-        prow -= M;
-        pback -= M;
-      }
-      cp_commit();
-    };
-    int top = N - 1;
-#pragma unroll 1
-    for (; top >= D + U - 1; top -= U) bwd(std::true_type{}, top);
-#pragma unroll 1
-    for (; top >= 0; top -= U) bwd(std::false_type{}, top);
-    cp_wait<0>();
-  }
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride)
+    df_sweep_systems<BW, ADJ, V, D>(rc, c64, N, X + g * V, M, ring, ring_s, pitch);
 }
 
 template <int BW, bool ADJ, int V>
