@@ -51,12 +51,12 @@ NOMINAL_HBM_GBS = 8000.0
 # sets their grid) hash to the value they had at capture time.
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel
-    # inside this benchmark's step (launch list of the timed steps, or the
-    # first launch of a full capture), keyed by the hash of its sources
-    "band_grad_f64": {"bytes": 894596096 + 5241856, "sha": "a7a6177e1eb9d3f0"},
-    "f64_solve": {"bytes": 469910400 + 432772864, "sha": "e097e8f3f687cdc4"},
-    "adjoint_f64": {"bytes": 462895744 + 427751168, "sha": "e097e8f3f687cdc4"},
-    "refine_solve": {"bytes": 350972672 + 435089408, "sha": "4725e3d6e20cb656"},
+    # inside this benchmark's step (launch list of the timed steps), keyed by
+    # the hash of its sources
+    "band_grad_f64": {"bytes": 547086208 + 296704, "sha": "8d7569e6dd2422e1"},
+    "f64_solve": {"bytes": 469657344 + 432619136, "sha": "c8f6c18d3d2c4bb5"},
+    "adjoint_f64": {"bytes": 463263488 + 427590016, "sha": "c8f6c18d3d2c4bb5"},
+    "refine_solve": {"bytes": 351342464 + 432433792, "sha": "1cbb540b290b35a9"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],

@@ -380,43 +380,37 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
   }
 }
 
-// Level 2: dbands[k*N + i] = -(sum over the CTAs that touched row block
-// i / kGradRows, in CTA order); 0 outside the matrix (a periodic matrix has no
-// entries outside).
+// Level 2: dbands[k*N + i] = -(sum of the partials of the CTAs that touched
+// row block i / kGradRows); 0 outside the matrix (a periodic matrix has no
+// entries outside).  One warp per (band, row): lane l takes the CTAs c0 + l,
+// c0 + l + 32, .. in that order, and the lanes' sums are added in a fixed
+// butterfly order (lane 0's result is stored), so the result stays bitwise
+// reproducible.
 __global__ void k_band_grad_finish(int W, int N, int64_t M, int RG, int G, int S, int periodic,
                                    const double* __restrict__ partial, double* __restrict__ dbands) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)W * N) return;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= (int64_t)W * N) return;  // whole warps
   const int k = (int)(t / N), i = (int)(t % N);
-  const int rb = i / kGradRows, r_row = i % kGradRows;
+  const int rb = i / kGradRows, r = i % kGradRows;
   const int rg = rb / kGradGroups, grp = rb % kGradGroups;
   const int col = i + k - W / 2;
   const int64_t total = (int64_t)RG * M;
   const int64_t b_lo = (int64_t)rg * M, b_hi = b_lo + M;
-  // first CTA whose range can reach block group rg; the CTA ranges
-  // [c total / G, (c + 1) total / G) are stepped with integer additions
-  // (c total / G = c q + floor(c r / G), total = q G + r)
-  int64_t c = b_lo * G / total - 1;
-  if (c < 0) c = 0;
-  const int64_t q = total / G, r = total - q * G;
-  int64_t lo = c * q + (c * r) / G, acc = (c * r) % G;
+  // the CTA whose range [c total / G, (c + 1) total / G) holds position p is
+  // floor(((p + 1) G - 1) / total) (the last of equal starts: empty ranges hold none)
+  const int64_t c0 = ((b_lo + 1) * G - 1) / total, c1 = (b_hi * G - 1) / total;
   double s = 0.0;
-  for (; c < G; c++) {
-    int64_t hi = lo + q;
-    acc += r;
-    if (acc >= G) {
-      hi += 1;
-      acc -= G;
-    }
-    if (lo >= b_hi) break;
-    if (hi > b_lo && lo != hi) {
-      // a CTA that starts inside the group has it as its first segment
+  for (int64_t c = c0 + lane; c <= c1; c += 32) {
+    const int64_t lo = range_lo(c, total, G), hi = range_lo(c + 1, total, G);
+    if (hi > lo) {  // a CTA starting inside the group has it as its first segment
       const int seg = lo >= b_lo ? 0 : rg - (int)(lo / M);
-      s += partial[((c * S + seg) * kGradGroups + grp) * (int64_t)(W * kGradRows) + k * kGradRows + r_row];
+      s += partial[((c * S + seg) * kGradGroups + grp) * (int64_t)(W * kGradRows) + k * kGradRows + r];
     }
-    lo = hi;
   }
-  dbands[t] = (periodic || (col >= 0 && col < N)) ? -s : 0.0;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) dbands[t] = (periodic || (col >= 0 && col < N)) ? -s : 0.0;
 }
 
 template <typename T, int W, bool PER>
@@ -477,7 +471,7 @@ cudaError_t band_grad_with_scratch(int width, int N, bool periodic, const void* 
 #undef BS_GRAD
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t n = (int64_t)width * N;
+  const int64_t n = (int64_t)width * N * 32;  // one warp per output
   k_band_grad_finish<<<(int)((n + 255) / 256), 256, 0, st>>>(width, N, M, g.RG, g.G, g.S, periodic ? 1 : 0,
                                                              scratch, dbands);
   return cudaGetLastError();
