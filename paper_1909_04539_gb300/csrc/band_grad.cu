@@ -33,7 +33,7 @@
 // FP32 rate) and width / kGradRun FP64 additions.  A run of K products of
 // typical size t carries an error of about sqrt(K) 2^-48 t, so a sum of M
 // random-sign terms, of size sqrt(M) t, is off by about sqrt(K) 2^-48
-// relative (K = 16: ~1.4e-14).  Values outside [2^-32, 2^48) (besides zero)
+// relative (K = 32: ~2e-14).  Values outside [2^-32, 2^48) (besides zero)
 // could overflow or underflow the FP32 parts: a CTA that meets one in a
 // segment recomputes that segment with FP64 FMAs, so the result depends only
 // on the data.  (The same pairs for FP64 data, each value split into two
@@ -110,9 +110,11 @@ __device__ __forceinline__ double to_wide(T v) {
     return widen_exact(v);  // integer-only widening: keeps the FP64 pipe for the FMAs
 }
 
-// FP32 data: products per (band, row) summed in pairs before one FP64
-// addition.
-constexpr int kGradRun = 16;
+// Products per (band, row) summed in pairs before one FP64 addition (FP32
+// data; the pair bands of FP64 data).  Measured against runs of 16 (ms,
+// penta N = 512, M = 65536): FP64 data 0.2443 against 0.2517, FP32 data
+// 0.1898 against 0.2022 (fewer FP64 additions; results within 1.4e-14).
+constexpr int kGradRun = 32;
 
 // v is zero or 2^-32 <= |v| < 2^48 (the pair arithmetic's range here: the
 // products stay within [2^-64, 2^96) and a run's sums far from overflow)
@@ -143,8 +145,10 @@ __device__ __forceinline__ df::Pair grad_pair(double v) {
 // ms): 0 pair bands 0.321; with the run sums in registers 1: 0.281, 2:
 // 0.295, 3: 0.329; in shared memory 1: 0.278, 2: 0.258, 3: 0.298 -- beyond
 // two bands the splits (~16 integer instructions per value) cost more issue
-// slots than the FP64 FMAs they replace.  Tri N = 1024, M = 2^18: 0 pair
-// bands 1.435 ms, 1: 1.282 (registers) / 1.228 (shared memory).
+// slots than the FP64 FMAs they replace (so did one warp in four or eight
+// taking all five bands in pairs: 0.326 / 0.298 against 0.244 ms, its
+// registers spilled).  Tri N = 1024, M = 2^18: 0 pair bands 1.435 ms, 1:
+// 1.282 (registers) / 1.228 (shared memory).
 constexpr int kGradPairBands5 = 2;
 constexpr int kGradPairBands3 = 1;
 constexpr bool kGradPairSmem = true;
