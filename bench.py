@@ -320,8 +320,8 @@ def run_ours(args):
         "f64_solve": {"bytes": 16 * nm, "arith": "fp32 pairs (FP64 data in and out)"},
         "refine_solve": {"bytes": 12 * nm, "arith": "fp32 sweeps + error-free fp32 residuals, fp64 sum"},
         "adjoint_f64": {"bytes": 16 * nm, "arith": "fp32 pairs (FP64 data in and out)"},
-        "band_grad_f64": {"bytes": 16 * nm, "arith": "fp64 FMAs for 3 of the 5 bands (3 FMA per unknown), "
-                          "FP32 pairs for the other two", "dp_fma": 3 * nm},
+        "band_grad_f64": {"bytes": 16 * nm, "arith": "fp64 FMAs for 3 of the 5 products per unknown (those "
+                          "with the lower X rows of a thread's window), FP32 pairs for the other two", "dp_fma": 3 * nm},
     }
     for n, p in paths.items():
         p["ncu_dram_bytes"] = ncu_traffic(n)
@@ -397,7 +397,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "width": 5, "layout": "interleaved",
                    "arithmetic": "FP64 data; the FP64 solve and adjoint in FP32 pairs (48 significant bits, "
                                  "error-free transformations), the band gradient in FP64 FMAs for 3 of its 5 "
-                                 "bands and FP32 pairs for the other two, the mixed-precision solve in FP32 with "
+                                 "products per unknown and FP32 pairs for the other two, the mixed-precision "
+                                 "solve in FP32 with "
                                  "error-free residuals",
                    "l2": "no flush: FP64 operands (256 MiB) exceed L2; the FP32 input is re-read after >1 GiB of other traffic",
                    "parallelism": f"replicas x{world} (systems partitioned, no collective)"},

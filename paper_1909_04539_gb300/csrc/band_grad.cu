@@ -22,13 +22,14 @@
 // neighbouring blocks of the group, which the same CTA sweeps at the same
 // time.
 //
-// Arithmetic of level 1.  FP64 data: one FP64 FMA per product for all bands
-// but the top ones, whose products are summed in FP32 pairs (see
-// kGradPairBands5; the kernel is bound by the FP64 pipe).  FP32 data: a thread's products for one (band,
-// row) are summed in FP32 pairs over runs of kGradRun systems -- each product
-// exact by an FMA-based TwoProduct, added with Knuth's TwoSum, the rounding
-// errors collected in the low part -- and each run's pair is added, exactly
-// widened, to an FP64 sum: `width` products in FP32 arithmetic per unknown
+// Arithmetic of level 1.  FP64 data: one FP64 FMA per product except for
+// the products of the top X rows of a thread's window, which are summed in
+// FP32 pairs (see kGradSplit5; the kernel is bound by the FP64 pipe).  FP32
+// data: a thread's products for one (band, row) are summed in FP32 pairs
+// over runs of kGradRun systems -- each product exact by an FMA-based
+// TwoProduct, added with Knuth's TwoSum, the rounding errors collected in
+// the low part -- and each run's pair is added, exactly widened, to an FP64
+// sum: `width` products in FP32 arithmetic per unknown
 // instead of `width` FP64 FMAs (the FP64 pipe of GB300 runs at 1/64 of the
 // FP32 rate) and width / kGradRun FP64 additions.  A run of K products of
 // typical size t carries an error of about sqrt(K) 2^-48 t, so a sum of M
@@ -36,10 +37,10 @@
 // relative (K = 32: ~2e-14).  Values outside [2^-32, 2^48) (besides zero)
 // could overflow or underflow the FP32 parts: a CTA that meets one in a
 // segment recomputes that segment with FP64 FMAs, so the result depends only
-// on the data.  (The same pairs for FP64 data, each value split into two
-// FP32 parts, measured slower than the FP64 FMAs: the splits cost about 20
-// integer instructions per value; penta N = 512, M = 65536: 0.33 - 0.48 ms
-// against 0.32 ms.  So did a layout for interleaved data in which a warp
+// on the data.  (The same pairs for all products of FP64 data, each value
+// split into two FP32 parts, measured slower than the FP64 FMAs: the splits
+// cost about 20 integer instructions per value; penta N = 512, M = 65536:
+// 0.33 - 0.48 ms against 0.32 ms.  So did a layout for interleaved data in which a warp
 // reads one row of 32 systems and sums each row's products over its lanes
 // with shuffles, in pairs: 0.44 ms (FP32 data 0.37 ms) -- the per-row
 // butterfly costs ~250 warp instructions per 32 unknowns.)
@@ -135,23 +136,42 @@ __device__ __forceinline__ df::Pair grad_pair(double v) {
   return y;
 }
 
-// FP64 data: the products of the top kGradPairBands bands (of 5; 3-band
-// matrices: kGradPairBands3) are summed in FP32 pairs as for FP32 data --
-// each value split once, the product a TwoProduct plus the two cross terms
-// -- and the others with FP64 FMAs, so that the FP32 and integer pipes take
-// part of the work the FP64 pipe bounds.  The FP64 sums of the pair bands'
-// runs live in shared memory (one column per thread), which leaves the
-// registers to the loads in flight.  Measured (penta N = 512, M = 65536,
-// ms): 0 pair bands 0.321; with the run sums in registers 1: 0.281, 2:
-// 0.295, 3: 0.329; in shared memory 1: 0.278, 2: 0.258, 3: 0.298 -- beyond
-// two bands the splits (~16 integer instructions per value) cost more issue
-// slots than the FP64 FMAs they replace (so did one warp in four or eight
-// taking all five bands in pairs: 0.326 / 0.298 against 0.244 ms, its
-// registers spilled).  Tri N = 1024, M = 2^18: 0 pair bands 1.435 ms, 1:
-// 1.282 (registers) / 1.228 (shared memory).
-constexpr int kGradPairBands5 = 2;
-constexpr int kGradPairBands3 = 1;
+// FP64 data: the products g[r] x[r + k] whose X row lies at or above index
+// kGradSplit of the thread's window of NX rows (r + k >= kGradSplit) are
+// summed in FP32 pairs as for FP32 data -- each value they need split once,
+// the product a TwoProduct plus the two cross terms -- and the others with
+// FP64 FMAs, so that the FP32 and integer pipes take part of the work the
+// FP64 pipe bounds; the X rows below the split are never converted.  The
+// FP64 sums of the pair products' runs live in shared memory (one column per
+// thread), which leaves the registers to the loads in flight.  Measured
+// (penta N = 512, M = 65536, ms): all products in FP64 0.321; the top pair
+// bands (k >= 5 - n) with the run sums in registers n = 1: 0.281, 2: 0.295,
+// 3: 0.329; in shared memory 1: 0.278, 2: 0.258, 3: 0.298 (with the
+// row-block groups and runs of 32: 2: 0.2415, 3: 0.288); by split row,
+// kGradSplit = 4 (6 pair products, 6 values split): 0.2375, 3 (9, 7):
+// 0.260, 2 (12, 8): 0.279 -- beyond six products the splits and the spilled
+// registers cost more issue slots than the FP64 FMAs they replace (so did one
+// warp in four or eight taking all products in pairs: 0.326 / 0.298 against
+// 0.244 ms).  Tri N = 1024, M = 2^18: all FP64 1.435 ms, the top band in pairs
+// 1.228, then 1.280 with the groups; kGradSplit = 3 (3 products, 5 values):
+// 1.227, 2 (6, 6): 1.280.
 constexpr bool kGradPairSmem = true;
+constexpr int kGradSplit5 = 4;
+constexpr int kGradSplit3 = 3;
+
+// Position of the pair product (r, k), r + k >= S, among all of them in (k,
+// r) order; their count for (r, k) = (-1, -1).
+template <int W, int S>
+__host__ __device__ constexpr int pair_slot(int r, int k) {
+  int n = 0;
+  for (int kk = 0; kk < W; kk++)
+    for (int rr = 0; rr < kGradRows; rr++)
+      if (rr + kk >= S) {
+        if (rr == r && kk == k) return n;
+        n++;
+      }
+  return n;
+}
 
 // a += g * x for pairs of FP64 values, not renormalised
 __device__ __forceinline__ void grad_acc(df::Pair& a, df::Pair g, df::Pair x) {
@@ -187,8 +207,9 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
   constexpr int NV = kGradRows * W;  // accumulators per thread
   static_assert(NV <= 64, "reduce-scatter holds at most 64 values per lane");
   __shared__ double red[kGradThreads / 32][64];
-  constexpr int KP = (sizeof(T) == 8) ? (W == 5 ? kGradPairBands5 : kGradPairBands3) : 0;
-  constexpr int KPS = (kGradPairSmem && KP > 0) ? KP * kGradRows : 1;
+  constexpr int SP = (sizeof(T) == 8) ? (W == 5 ? kGradSplit5 : kGradSplit3) : NX;
+  constexpr int NP = pair_slot<W, SP>(-1, -1);  // pair products (FP64 data)
+  constexpr int KPS = (kGradPairSmem && NP > 0) ? NP : 1;
   __shared__ double psum[KPS][kGradThreads];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = threadIdx.x / kGradGroupThreads, tg = threadIdx.x % kGradGroupThreads;
@@ -252,38 +273,42 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
             acc[k * kGradRows + r] = fma(to_wide(g[r]), to_wide(x[r + k]), acc[k * kGradRows + r]);
       });
     };
-    if constexpr (sizeof(T) == 8 && KP == 0) {
+    if constexpr (sizeof(T) == 8 && NP == 0) {
       fp64();
     } else if constexpr (sizeof(T) == 8) {
-      // bands 0 .. W-KP-1 with FP64 FMAs, the top KP bands in pairs (runs of
-      // kGradRun systems, then FP64 sums of the runs)
-      constexpr int K0 = W - KP;
+      // products with r + k < SP with FP64 FMAs, the others in pairs (runs
+      // of kGradRun systems, then FP64 sums of the runs)
       bool bad = false;
-      df::Pair pa[KP * kGradRows];
+      df::Pair pa[NP];
 #pragma unroll
-      for (int v = 0; v < KP * kGradRows; v++) pa[v] = df::Pair{0.f, 0.f};
+      for (int v = 0; v < NP; v++) pa[v] = df::Pair{0.f, 0.f};
 #pragma unroll
       for (int v = 0; v < NV; v++) acc[v] = 0.0;
       if constexpr (kGradPairSmem) {
 #pragma unroll
-        for (int v = 0; v < KP * kGradRows; v++) psum[v][threadIdx.x] = 0.0;
+        for (int v = 0; v < NP; v++) psum[v][threadIdx.x] = 0.0;
       }
       int run = 0;
       auto flush = [&]() {
 #pragma unroll
-        for (int v = 0; v < KP * kGradRows; v++) {
-          if constexpr (kGradPairSmem)
-            psum[v][threadIdx.x] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
-          else
-            acc[K0 * kGradRows + v] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
-          pa[v] = df::Pair{0.f, 0.f};
-        }
+        for (int k = 0; k < W; k++)
+#pragma unroll
+          for (int r = 0; r < kGradRows; r++)
+            if (r + k >= SP) {
+              const int v = pair_slot<W, SP>(r, k);
+              if constexpr (kGradPairSmem)
+                psum[v][threadIdx.x] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+              else
+                acc[k * kGradRows + r] += widen_exact(pa[v].h) + widen_exact(pa[v].l);
+              pa[v] = df::Pair{0.f, 0.f};
+            }
       };
       sweep([&](const T (&x)[NX], const T (&g)[kGradRows]) {
 #pragma unroll
         for (int r = 0; r < kGradRows; r++)
 #pragma unroll
-          for (int k = 0; k < K0; k++) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
+          for (int k = 0; k < W; k++)
+            if (r + k < SP) acc[k * kGradRows + r] = fma(g[r], x[r + k], acc[k * kGradRows + r]);
         df::Pair gp[kGradRows], xp[NX];
         bool in = true;
 #pragma unroll
@@ -292,7 +317,7 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
           gp[r] = grad_pair(g[r]);
         }
 #pragma unroll
-        for (int q = K0; q < NX; q++) {
+        for (int q = SP; q < NX; q++) {
           in &= grad_in_range(x[q]);
           xp[q] = grad_pair(x[q]);
         }
@@ -300,7 +325,8 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
 #pragma unroll
         for (int r = 0; r < kGradRows; r++)
 #pragma unroll
-          for (int b = 0; b < KP; b++) grad_acc(pa[b * kGradRows + r], gp[r], xp[r + K0 + b]);
+          for (int k = 0; k < W; k++)
+            if (r + k >= SP) grad_acc(pa[pair_slot<W, SP>(r, k)], gp[r], xp[r + k]);
         if (++run == kGradRun) {
           flush();
           run = 0;
@@ -309,7 +335,10 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
       flush();
       if constexpr (kGradPairSmem) {
 #pragma unroll
-        for (int v = 0; v < KP * kGradRows; v++) acc[K0 * kGradRows + v] = psum[v][threadIdx.x];
+        for (int k = 0; k < W; k++)
+#pragma unroll
+          for (int r = 0; r < kGradRows; r++)
+            if (r + k >= SP) acc[k * kGradRows + r] = psum[pair_slot<W, SP>(r, k)][threadIdx.x];
       }
       // a value outside the pairs' range anywhere in the segment: FP64 FMAs
       if (__syncthreads_or(bad)) fp64();
