@@ -207,3 +207,44 @@ def test_large_request_paced_copies(bs, serve, mode):
         bs.set_option(bs.OPT_PARTITION, 0)
         bs.set_option(bs.OPT_TWISTED, 0)
     srv.close()
+
+
+@pytest.mark.parametrize("width", [3, 5])
+def test_short_systems_through_the_rings(bs, serve, width):
+    """Requests whose N is below, at and just above the grouped kernel's ring
+    depth (16 rows) and not a multiple of its 4-row blocks: each result equals
+    the direct solve bitwise and the oracle's to 1e-12."""
+    Ns = [2, 3, 5, 7, 12, 15, 16, 17, 19, 21, 34] if width == 3 else [4, 5, 7, 12, 15, 16, 17, 19, 21, 34]
+    rng = np.random.default_rng(width)
+    facs = []
+    for N in Ns:
+        bands = synth.random_tri_bands(N, rng) if width == 3 else synth.random_penta_bands(N, rng)
+        facs.append((bands, bs.Factor(bands)))
+    srv = serve.Server(1 << 30, n_streams=2)
+    out = []
+    for q, (bands, f) in enumerate(facs):
+        for mode in (0, 1):
+            M = 1 + 37 * q + 5 * mode
+            g = np.random.default_rng(1000 + 10 * q + mode)
+            B = torch.tensor(g.uniform(-1, 1, (f.N, M)), dtype=torch.float64 if mode == 0 else torch.float32)
+            B = B.pin_memory()
+            X = torch.empty((f.N, M), dtype=torch.float64).pin_memory()
+            out.append((srv.submit(f, B, X, mode), bands, f, mode, B, X))
+    for rid, *_ in out:
+        assert srv.wait(rid, 60) == "done"
+    bs.set_option(bs.OPT_PARTITION, 1)
+    bs.set_option(bs.OPT_TWISTED, 1)
+    try:
+        for rid, bands, f, mode, B, X in out:
+            if mode == 0:
+                D = bs.solve(f, B.cuda())
+            else:
+                D = bs.solve_refine(f, B.cuda(), mode=bs.REFINE_FACTOR)
+            torch.cuda.synchronize()
+            assert torch.equal(D.cpu(), X), (f.N, mode)
+            ref = oracle.solve(bands, B.double().numpy())
+            assert rel_l2(X.numpy(), ref) < 1e-12, (f.N, mode)
+    finally:
+        bs.set_option(bs.OPT_PARTITION, 0)
+        bs.set_option(bs.OPT_TWISTED, 0)
+    srv.close()
