@@ -188,11 +188,12 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  * device array inside the library (2 MiB, held on every GPU that loads the
  * library until the process exits) and allocates nothing.  The caller still
  * provides GB, X and dbands as for bs_band_grad.
- * Limit: the partial sums need about (N / 3 + 2 G) x 3 x width doubles
- * (row blocks of 3 rows; G = the reduction's CTA count, SMs x resident CTAs
- * per SM: 304 on GB300) and the array holds 262144 of them: on GB300 N above
- * about 50000 (width 5) or 85000 (width 3) is rejected with BS_EINVAL and a
- * message naming the size -- use bs_band_grad there.
+ * Limit: the partial sums need about (N / 3 + 8 G) x 3 x width doubles
+ * (row blocks of 3 rows taken four at a time; G = the reduction's CTA count,
+ * SMs x resident CTAs per SM: 304 on GB300) and the array holds 262144 of
+ * them: on GB300 N above about 47000 (width 5) or 80000 (width 3) is
+ * rejected with BS_EINVAL and a message naming the size -- use bs_band_grad
+ * there.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture (a first
  * call on a stream that is being captured returns BS_EINVAL).  All calls
