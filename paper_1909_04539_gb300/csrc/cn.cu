@@ -19,6 +19,7 @@
 // of the solve is applied as in the plain periodic sweeps.
 #include <type_traits>
 
+#include "df_math.cuh"
 #include "sweep_kernels.cuh"
 
 namespace bs {
@@ -235,8 +236,198 @@ static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, in
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ FP64 steps in FP32 pairs
+//
+// The native FP64 kernel above issues 2 W FP64 instructions per unknown (the
+// explicit product and the two sweeps), so the FP64 pipe bounds it.  For an
+// FP64 batch whose handle allows pairs (cn_pairs: the band entries and the
+// explicit side's row sums in range, factor.cpp; and the pair sweeps' own
+// check) a step runs instead as two passes: the explicit side X <- (2I - A) X
+// in FP32 pairs (k_cn_explicit_df, in place, each value rounded once to
+// FP64), then the FP64 solve in pairs (sweep_df.cu).
+//
+// One thread per system; the rows arrive through a per-lane cp.async ring of
+// kCnDfD slots, one copy group per block of 4 input rows; after the block of
+// input rows r0 .. r0+3 the thread holds the window of rows r0 - 2 BW ..
+// r0 + 3, as pairs and as the FP64 values, and forms the output rows
+// r0 - BW .. r0 + 3 - BW (the rows it overwrites have all been read).  (Rows
+// cut into blocks of 128 per thread, for four times the threads, need the
+// result in a second batch -- neighbouring blocks read each other's rows --
+// and measured slower with the copy back: penta N = 512, M = 65536, one step
+// 0.446 against 0.397 ms.)  Each
+// product e_k(i) C_{i+k-BW} is a TwoProduct of the high parts plus the two
+// cross terms, the sum TwoSums of the high parts with the rest in the low
+// part, as in the pair sweeps.  A lane that meets an input outside the pairs'
+// range computes the rest of its system with FP64 FMAs, so each result
+// depends only on its own system.  The band entries are staged per CTA as
+// (hi, lo) pairs.
+constexpr int kCnDfThreads = 256;
+constexpr int kCnDfD = 16;
+
+template <int BW>
+__global__ void __launch_bounds__(kCnDfThreads)
+k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, const double* __restrict__ b64,
+                 int N, double* X, int64_t M) {
+  constexpr int W = 2 * BW + 1;
+  constexpr int U = 4;
+  constexpr int D = kCnDfD;
+  constexpr int NW = 2 * BW + U;  // window: input rows r0 - 2 BW .. r0 + 3
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* rec = reinterpret_cast<float2*>(smem_raw);  // rec[i W + k]: band k of row i as (hi, lo)
+  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
+    const int i = t / W, k = t - i * W;
+    rec[t] = make_float2(bhi[(size_t)k * N + i], blo[(size_t)k * N + i]);
+  }
+  __syncthreads();
+  unsigned char* ring = smem_raw + align_up((size_t)N * W * sizeof(float2), 16) + (size_t)threadIdx.x * 8;
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t pitch = blockDim.x * 8;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    double* const px = X + j;
+    const double* pnext = px;  // next input row to request
+#pragma unroll 1
+    for (int r = 0; r < D; r++) {
+      if (r < N) cp_async8(ring_s + r * pitch, pnext);
+      pnext += M;
+      if ((r + 1) % U == 0) cp_commit();
+    }
+    df::Pair y[NW];
+    double d[NW];
+#pragma unroll
+    for (int q = 0; q < NW; q++) {
+      y[q] = df::Pair{0.f, 0.f};
+      d[q] = 0.0;
+    }
+    bool f64 = false;  // this lane runs FP64 FMAs from here on
+#pragma unroll 1
+    for (int r0 = 0; r0 - BW < N; r0 += U) {
+      cp_wait<D / U - 1>();
+#pragma unroll
+      for (int q = 0; q < 2 * BW; q++) {
+        y[q] = y[q + U];
+        d[q] = d[q + U];
+      }
+      const int s0 = r0 % D;
+      bool need = false;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int r = r0 + u;
+        double v = 0.0;
+        if (r < N) v = *reinterpret_cast<const double*>(ring + (size_t)(s0 + u) * pitch);
+        d[2 * BW + u] = v;
+        y[2 * BW + u] = df::Pair{0.f, 0.f};
+        if (r < N && !f64) need |= !df::split_fast(v, y[2 * BW + u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (r0 + u + D < N) cp_async8(ring_s + (s0 + u) * pitch, pnext);
+        pnext += M;
+      }
+      cp_commit();
+      if (__any_sync(__activemask(), need)) {
+        if (need) {  // zeros or range edges: the careful split, or FP64 from here on
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            bool ok = true;
+            y[2 * BW + u] = df::split(d[2 * BW + u], ok);
+            f64 |= !ok;
+          }
+        }
+      }
+      // output rows i = r0 + u - BW: window entries u .. u + 2 BW
+      double out[U];
+      float oh[U], ol[U];
+      bool odd = false;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int i = r0 + u - BW;
+        out[u] = 0.0;
+        if (i < 0 || i >= N) continue;
+        const float2* ci = rec + (size_t)i * W;
+        if (!f64) {
+          float s = df::mul(2.f, y[u + BW].h), lo = df::mul(2.f, y[u + BW].l);
+#pragma unroll
+          for (int k = 0; k < W; k++) {
+            const float2 c = ci[k];
+            const df::Pair z = y[u + k];
+            const float p = df::mul(c.x, z.h);
+            float e = df::fma_(c.x, z.h, -p);
+            e = df::fma_(c.x, z.l, e);
+            e = df::fma_(c.y, z.h, e);
+            float t;
+            df::two_sum(s, -p, s, t);
+            lo = df::add(lo, df::sub(t, e));
+          }
+          df::fast_two_sum(s, lo, oh[u], ol[u]);
+          odd |= !df::combine_ok(oh[u]);
+          out[u] = df::combine_fast(oh[u], ol[u]);  // replaced below where !combine_ok
+        } else {
+          double f = 2.0 * d[u + BW];
+#pragma unroll
+          for (int k = 0; k < W; k++) f = fma(-b64[(size_t)k * N + i], d[u + k], f);
+          out[u] = f;
+        }
+      }
+      if (__any_sync(__activemask(), odd)) {
+        if (odd) {  // results below 2^-70 (zeros): the careful combination
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const int i = r0 + u - BW;
+            if (i >= 0 && i < N && !f64 && !df::combine_ok(oh[u])) out[u] = df::combine(oh[u], ol[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int i = r0 + u - BW;
+        if (i >= 0 && i < N) px[(int64_t)i * M] = out[u];
+      }
+    }
+    cp_wait<0>();
+  }
+}
+
+static size_t cn_df_smem(int width, int64_t N) {
+  return align_up((size_t)N * width * sizeof(float2), 16) + (size_t)kCnDfThreads * kCnDfD * 8;
+}
+
+// FP64 steps take the pair passes when the handle allows them and the staged
+// band pairs and rings fit in shared memory.
+static bool cn_pair_path(bs_handle h) {
+  const DeviceInfo& d = device_info();
+  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024);
+  return h->cn_pairs && df_eligible(h->plan[0], BS_INTERLEAVED) && cn_df_smem(h->width, h->N) <= limit;
+}
+
+template <int BW>
+static cudaError_t launch_cn_explicit_df(bs_handle h, double* X, int64_t M, cudaStream_t st) {
+  const int N = (int)h->N;
+  const size_t bytes = cn_df_smem(2 * BW + 1, N);
+  auto k = k_cn_explicit_df<BW>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kCnDfThreads, bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)device_info().sms * per_sm;
+  const int64_t need = (M + kCnDfThreads - 1) / kCnDfThreads;
+  if (grid > need) grid = need;
+  k<<<(int)grid, kCnDfThreads, bytes, st>>>(h->bands_hi, h->bands_lo, h->bands64, N, X, M);
+  return cudaGetLastError();
+}
+
 template <typename C, int VEC>
 static cudaError_t cn_dispatch(bs_handle h, C* X, int64_t M, cudaStream_t st) {
+  if constexpr (sizeof(C) == 8) {
+    if (cn_pair_path(h)) {  // explicit side, then the solve, both in pairs
+      const cudaError_t e =
+          h->width == 3 ? launch_cn_explicit_df<1>(h, X, M, st) : launch_cn_explicit_df<2>(h, X, M, st);
+      if (e != cudaSuccess) return e;
+      return sweep_df(h->plan[0], false, (int)h->N, X, M, st);
+    }
+  }
   const SweepPlan& p = h->plan[0];
   const int N = (int)h->N;
   const C* bands;

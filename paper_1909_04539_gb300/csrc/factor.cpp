@@ -567,6 +567,26 @@ cudaError_t upload_part(const HostPart& hp, int64_t N, PartPlan& pp, size_t& byt
   return e;
 }
 
+// The explicit side e = 2I - A of a Crank-Nicolson step in FP32 pairs (cn.cu)
+// keeps the pairs' range and accuracy when every band entry is zero or of
+// magnitude in [2^-20, 2^20] (products with inputs in the pairs' range stay
+// inside FP32's) and every row's sum of |e| entries is at most 16 (its
+// rounding, ~2^-48 of that sum times |C|, then stays near FP64's).
+bool cn_pairs_ok(int width, int64_t N, const std::vector<double>& b64) {
+  const int h = width / 2;
+  for (int64_t i = 0; i < N; i++) {
+    double sum = 0.0;
+    for (int k = 0; k < width; k++) {
+      const double b = b64[(size_t)k * N + i];
+      const double a = std::fabs(b);
+      if (!(a == 0.0 || (a >= 0x1p-20 && a <= 0x1p20))) return false;
+      sum += std::fabs((k == h ? 2.0 : 0.0) - b);
+    }
+    if (!(sum <= 16.0)) return false;
+  }
+  return true;
+}
+
 // Copies the host plans, factor entries and bands (b64, width * N) of one
 // LHS to the current device and registers the handle.
 bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool periodic,
@@ -636,6 +656,7 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   hd->device_bytes = bytes;
   hd->has_ul = has_ul;
   hd->periodic = periodic;
+  hd->cn_pairs = !periodic && cn_pairs_ok(width, N, b64);
   {
     std::lock_guard<std::mutex> lk(g_handles_mu);
     g_handles.insert(hd);

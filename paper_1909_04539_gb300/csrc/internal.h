@@ -141,6 +141,9 @@ struct bs_factor_s {
   bs::PartPlan part[2];    // [0] for A, [1] for A^T
   bool periodic;           // cyclic tridiagonal (bs_factor_periodic): bands64 holds the
                            // corner entries a_1 (band 0, row 0) and c_N (band 2, row N-1)
+  bool cn_pairs;           // the explicit side 2I - A of a Crank-Nicolson step may run in
+                           // FP32 pairs: every band entry 0 or in [2^-20, 2^20] and every
+                           // row's sum of |2I - A| entries at most 16 (cn.cu)
   bs::TwistPlan twist[2];  // two-ended tridiagonal sweeps: [0] for A (plan[0], plan[2]),
                            // [1] for A^T (tplan[])
   bs::SweepPlan tplan[2];  // A^T = L U and A^T = U' L' (primal form, original row order)

@@ -95,3 +95,34 @@ def test_zero_steps_and_errors(bs):
     C = torch.zeros(8, 16, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError, match="interleaved"):
         bs.cn_steps(f, C, 1, layout="strided")
+
+
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_fp64_steps_pairs_and_native_with_edge_values(bs, pairs):
+    """FP64 steps of a non-periodic handle run the explicit side and the solve
+    in FP32 pairs by default (option 0) and natively on request (1).  The
+    batch mixes ordinary systems with ones the pairs' range cannot hold
+    (values near 2^300 and 2^-300, a subnormal entry) and a zero system;
+    those lanes compute in FP64.  Every system against the oracle."""
+    N, M = 37, 70
+    bands = synth.clamped_hyperdiffusion_bands(N, 0.3)
+    rng = np.random.default_rng(11)
+    C0 = rng.uniform(-1, 1, (N, M))
+    C0[:, 3] *= 2.0 ** 300
+    C0[:, 4] *= 2.0 ** -300
+    C0[:, 5] = 0.0
+    C0[5, 6] = 5e-324
+    C0[:, 40] *= 2.0 ** 90  # inside the pairs' range, near its top
+    f = bs.Factor(bands)
+    bs.set_option(bs.OPT_F64_PAIRS, pairs)
+    try:
+        X = _run(bs, f, C0, torch.float64, 3)
+    finally:
+        bs.set_option(bs.OPT_F64_PAIRS, 0)
+    ref = oracle.cn_steps(bands, C0, 3)
+    for j in range(M):
+        scale = np.abs(ref[:, j]).max()
+        if scale == 0.0:
+            assert np.all(X[:, j] == 0.0), j
+        else:
+            assert np.abs(X[:, j] - ref[:, j]).max() <= 1e-12 * scale, j
