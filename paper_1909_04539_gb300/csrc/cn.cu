@@ -19,8 +19,7 @@
 // of the solve is applied as in the plain periodic sweeps.
 #include <type_traits>
 
-#include "df_math.cuh"
-#include "sweep_kernels.cuh"
+#include "df_sweep.cuh"
 
 namespace bs {
 
@@ -242,50 +241,71 @@ static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, in
 // explicit product and the two sweeps), so the FP64 pipe bounds it.  For an
 // FP64 batch whose handle allows pairs (cn_pairs: the band entries and the
 // explicit side's row sums in range, factor.cpp; and the pair sweeps' own
-// check) a step runs instead as two passes: the explicit side X <- (2I - A) X
-// in FP32 pairs (k_cn_explicit_df, in place, each value rounded once to
-// FP64), then the FP64 solve in pairs (sweep_df.cu).
+// check) a step runs instead in k_cn_df: the FP64 solve in FP32 pairs of
+// sweep_df.cu whose forward sweep takes as its input the explicit side
+// (2I - A) C, formed in pairs from the rows as they arrive -- each product
+// e_k(i) C_{i+k-BW} a TwoProduct of the high parts plus the two cross terms,
+// the sum TwoSums of the high parts with the rest in the low part -- so a
+// step reads C once and writes it once plus the forward values' round trip.
+// Measured (penta N = 512, M = 65536, ms per step): native 0.682; an
+// explicit pass in pairs followed by the pair solve 0.396; fused 0.315.
 //
-// One thread per system; the rows arrive through a per-lane cp.async ring of
-// kCnDfD slots, one copy group per block of 4 input rows; after the block of
-// input rows r0 .. r0+3 the thread holds the window of rows r0 - 2 BW ..
-// r0 + 3, as pairs and as the FP64 values, and forms the output rows
-// r0 - BW .. r0 + 3 - BW (the rows it overwrites have all been read).  (Rows
-// cut into blocks of 128 per thread, for four times the threads, need the
-// result in a second batch -- neighbouring blocks read each other's rows --
-// and measured slower with the copy back: penta N = 512, M = 65536, one step
-// 0.446 against 0.397 ms.)  Each
-// product e_k(i) C_{i+k-BW} is a TwoProduct of the high parts plus the two
-// cross terms, the sum TwoSums of the high parts with the rest in the low
-// part, as in the pair sweeps.  A lane that meets an input outside the pairs'
-// range computes the rest of its system with FP64 FMAs, so each result
-// depends only on its own system.  The band entries are staged per CTA as
-// (hi, lo) pairs.
-constexpr int kCnDfThreads = 256;
-constexpr int kCnDfD = 16;
+// One thread per system; input rows arrive through the per-lane ring in
+// blocks of 4 (rows 4b .. 4b+3 at step b), the thread keeps the window of
+// input rows 4b - 2 BW .. 4b + 3 as pairs and FP64 values, and the forward
+// sweep runs BW rows behind, over rows 4b - BW .. 4b + 3 - BW.
+// A row's ring slot is refilled with row + D as soon as the row enters the
+// window; the forward values of the last D rows stay in their slots, the
+// others go to C in place, and the backward sweep is the pair solve's
+// (df_sweep_backward).  A lane that meets an input outside the pairs' range
+// runs the rest of its system in FP64 from the current block of rows on.
+constexpr int kCnFusedThreadsMax = 512;
 
-template <int BW>
-__global__ void __launch_bounds__(kCnDfThreads)
-k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, const double* __restrict__ b64,
-                 int N, double* X, int64_t M) {
+template <int BW, bool SMEM, int D>
+__global__ void __launch_bounds__(kCnFusedThreadsMax)
+k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float* __restrict__ blo,
+        const double* __restrict__ b64, int N, double* X, int64_t M) {
   constexpr int W = 2 * BW + 1;
   constexpr int U = 4;
-  constexpr int D = kCnDfD;
-  constexpr int NW = 2 * BW + U;  // window: input rows r0 - 2 BW .. r0 + 3
+  constexpr int NW = 2 * BW + U;
+  static_assert(D % U == 0, "ring depth must be a multiple of the block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* rec = reinterpret_cast<float2*>(smem_raw);  // rec[i W + k]: band k of row i as (hi, lo)
+  DfRecs rc = rg;
+  size_t rec_bytes = 0;
+  float2* bp = reinterpret_cast<float2*>(smem_raw);  // band pairs, bp[i W + k]
+  if constexpr (SMEM) {
+    constexpr bool F2 = DfCount<false, BW>::F > 2, B2 = DfCount<false, BW>::B > 2;
+    float4* f4 = reinterpret_cast<float4*>(smem_raw);
+    float4* b4 = f4 + N;
+    float2* f2 = reinterpret_cast<float2*>(b4 + N);
+    float2* b2 = f2 + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      f4[i] = rg.f4[i];
+      b4[i] = rg.b4[i];
+      if (F2) f2[i] = rg.f2[i];
+      if (B2) b2[i] = rg.b2[i];
+    }
+    rc = DfRecs{f4, b4, f2, b2};
+    bp = reinterpret_cast<float2*>(b2 + N);
+    rec_bytes = (size_t)N * 48;
+  }
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, k = t - i * W;
-    rec[t] = make_float2(bhi[(size_t)k * N + i], blo[(size_t)k * N + i]);
+    bp[t] = make_float2(bhi[(size_t)k * N + i], blo[(size_t)k * N + i]);
   }
   __syncthreads();
-  unsigned char* ring = smem_raw + align_up((size_t)N * W * sizeof(float2), 16) + (size_t)threadIdx.x * 8;
+  unsigned char* ring =
+      smem_raw + align_up(rec_bytes + (size_t)N * W * sizeof(float2), 16) + (size_t)threadIdx.x * 8;
   const uint32_t ring_s = smem_u32(ring);
   const uint32_t pitch = blockDim.x * 8;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    double* const px = X + j;
-    const double* pnext = px;  // next input row to request
+    double* const pout = X + j;
+    DfState<1> st;
+    st.reset_values();
+    st.f64 = false;
+    st.rsw = N;
+    const double* pnext = pout;
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
       if (r < N) cp_async8(ring_s + r * pitch, pnext);
@@ -299,7 +319,7 @@ k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, c
       y[q] = df::Pair{0.f, 0.f};
       d[q] = 0.0;
     }
-    bool f64 = false;  // this lane runs FP64 FMAs from here on
+    double* prow = pout - (int64_t)BW * M;  // forward output row 4b - BW
 #pragma unroll 1
     for (int r0 = 0; r0 - BW < N; r0 += U) {
       cp_wait<D / U - 1>();
@@ -317,7 +337,7 @@ k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, c
         if (r < N) v = *reinterpret_cast<const double*>(ring + (size_t)(s0 + u) * pitch);
         d[2 * BW + u] = v;
         y[2 * BW + u] = df::Pair{0.f, 0.f};
-        if (r < N && !f64) need |= !df::split_fast(v, y[2 * BW + u]);
+        if (r < N && !st.f64) need |= !df::split_fast(v, y[2 * BW + u]);
       }
 #pragma unroll
       for (int u = 0; u < U; u++) {
@@ -325,28 +345,34 @@ k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, c
         pnext += M;
       }
       cp_commit();
+      const int i0 = r0 - BW;  // forward rows i0 .. i0 + 3 (those in [0, N))
       if (__any_sync(__activemask(), need)) {
         if (need) {  // zeros or range edges: the careful split, or FP64 from here on
+          bool bad = false;
 #pragma unroll
           for (int u = 0; u < U; u++) {
             bool ok = true;
             y[2 * BW + u] = df::split(d[2 * BW + u], ok);
-            f64 |= !ok;
+            bad |= !ok;
+          }
+          if (bad && !st.f64) {
+            st.f64 = true;
+            st.rsw = i0 > 0 ? i0 : 0;
+            st.d1[0] = pair_to_f64(st.p1[0]);
+            st.d2[0] = pair_to_f64(st.p2[0]);
           }
         }
       }
-      // output rows i = r0 + u - BW: window entries u .. u + 2 BW
-      double out[U];
-      float oh[U], ol[U];
-      bool odd = false;
+      uint2 wout[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const int i = r0 + u - BW;
-        out[u] = 0.0;
+        const int i = i0 + u;
+        wout[u] = make_uint2(0u, 0u);
         if (i < 0 || i >= N) continue;
-        const float2* ci = rec + (size_t)i * W;
-        if (!f64) {
-          float s = df::mul(2.f, y[u + BW].h), lo = df::mul(2.f, y[u + BW].l);
+        const float2* ci = bp + (size_t)i * W;
+        if (!st.f64) {
+          // f = (2I - A) C at row i in pairs: window entries u .. u + 2 BW
+          float sh = df::mul(2.f, y[u + BW].h), lo = df::mul(2.f, y[u + BW].l);
 #pragma unroll
           for (int k = 0; k < W; k++) {
             const float2 c = ci[k];
@@ -356,76 +382,80 @@ k_cn_explicit_df(const float* __restrict__ bhi, const float* __restrict__ blo, c
             e = df::fma_(c.x, z.l, e);
             e = df::fma_(c.y, z.h, e);
             float t;
-            df::two_sum(s, -p, s, t);
+            df::two_sum(sh, -p, sh, t);
             lo = df::add(lo, df::sub(t, e));
           }
-          df::fast_two_sum(s, lo, oh[u], ol[u]);
-          odd |= !df::combine_ok(oh[u]);
-          out[u] = df::combine_fast(oh[u], ol[u]);  // replaced below where !combine_ok
+          df::Pair f;
+          df::fast_two_sum(sh, lo, f.h, f.l);
+          const float4 q = rc.f4[i];
+          const float2 q2 = BW == 2 ? rc.f2[i] : make_float2(0.f, 0.f);
+          const df::Pair w = df_row<true, BW>(q, q2, f, st.p1[0], st.p2[0]);
+          st.p2[0] = st.p1[0];
+          st.p1[0] = w;
+          wout[u] = pair_bits(w);
         } else {
-          double f = 2.0 * d[u + BW];
+          double f[1] = {2.0 * d[u + BW]};
 #pragma unroll
-          for (int k = 0; k < W; k++) f = fma(-b64[(size_t)k * N + i], d[u + k], f);
-          out[u] = f;
+          for (int k = 0; k < W; k++) f[0] = fma(-b64[(size_t)k * N + i], d[u + k], f[0]);
+          fwd_step<BW, false, double, 1>(c64, i, f, st.d1, st.d2);
+          wout[u] = f64_bits(f[0]);
         }
       }
-      if (__any_sync(__activemask(), odd)) {
-        if (odd) {  // results below 2^-70 (zeros): the careful combination
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            const int i = r0 + u - BW;
-            if (i >= 0 && i < N && !f64 && !df::combine_ok(oh[u])) out[u] = df::combine(oh[u], ol[u]);
-          }
-        }
-      }
+      // the forward values: the last D rows stay in their ring slots (not
+      // refilled), the others go to C
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const int i = r0 + u - BW;
-        if (i >= 0 && i < N) px[(int64_t)i * M] = out[u];
+        const int i = i0 + u;
+        if (i >= 0 && i < N) {
+          if (i + D >= N)
+            *reinterpret_cast<uint2*>(ring + (size_t)(i % D) * pitch) = wout[u];
+          else
+            *reinterpret_cast<uint2*>(prow) = wout[u];
+        }
+        prow += M;
       }
     }
     cp_wait<0>();
+    df_sweep_backward<BW, false, 1, D>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
   }
 }
 
-static size_t cn_df_smem(int width, int64_t N) {
-  return align_up((size_t)N * width * sizeof(float2), 16) + (size_t)kCnDfThreads * kCnDfD * 8;
-}
-
-// FP64 steps take the pair passes when the handle allows them and the staged
-// band pairs and rings fit in shared memory.
+// FP64 steps take the fused pair kernel when the handle allows pairs and
+// its staged records, band pairs and rings fit in shared memory.
 static bool cn_pair_path(bs_handle h) {
-  const DeviceInfo& d = device_info();
-  const size_t limit = (size_t)(d.smem_optin > 0 ? d.smem_optin : 48 * 1024);
-  return h->cn_pairs && df_eligible(h->plan[0], BS_INTERLEAVED) && cn_df_smem(h->width, h->N) <= limit;
+  return h->cn_pairs && df_eligible(h->plan[0], BS_INTERLEAVED);
 }
 
+// The fused step; cudaErrorInvalidValue (nothing launched) when the staged
+// records, band pairs and rings do not fit in shared memory.  CTA size from
+// the busiest-SM model with ties to the largest (penta N = 512, M = 65536:
+// 64-thread CTAs, four per SM by shared memory, 0.442 ms; ties to the largest
+// 0.315 ms).
 template <int BW>
-static cudaError_t launch_cn_explicit_df(bs_handle h, double* X, int64_t M, cudaStream_t st) {
+static cudaError_t launch_cn_df(bs_handle h, double* X, int64_t M, cudaStream_t st) {
+  constexpr int D = 16;  // rows in flight per lane
   const int N = (int)h->N;
-  const size_t bytes = cn_df_smem(2 * BW + 1, N);
-  auto k = k_cn_explicit_df<BW>;
+  const SweepPlan& p = h->plan[0];
+  const DfRecs rg = df_recs_of(p.dfrec, N);
+  const Coefs<double> c64 = coefs_of<double>(p.c64, N);
+  const size_t rec = align_up((size_t)N * 48 + (size_t)N * (2 * BW + 1) * sizeof(float2), 16);
+  auto k = k_cn_df<BW, true, D>;
+  const StagedShape sh =
+      staged_shape(M, rec, (size_t)D * 8, kernel_regs((const void*)k), kCnFusedThreadsMax, true, kCnFusedThreadsMax);
+  if (sh.threads == 0 || !sh.staged) return cudaErrorInvalidValue;
+  const size_t bytes = rec + (size_t)sh.threads * D * 8;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kCnDfThreads, bytes);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)device_info().sms * per_sm;
-  const int64_t need = (M + kCnDfThreads - 1) / kCnDfThreads;
-  if (grid > need) grid = need;
-  k<<<(int)grid, kCnDfThreads, bytes, st>>>(h->bands_hi, h->bands_lo, h->bands64, N, X, M);
+  k<<<sh.grid, sh.threads, bytes, st>>>(rg, c64, h->bands_hi, h->bands_lo, h->bands64, N, X, M);
   return cudaGetLastError();
 }
 
 template <typename C, int VEC>
 static cudaError_t cn_dispatch(bs_handle h, C* X, int64_t M, cudaStream_t st) {
   if constexpr (sizeof(C) == 8) {
-    if (cn_pair_path(h)) {  // explicit side, then the solve, both in pairs
-      const cudaError_t e =
-          h->width == 3 ? launch_cn_explicit_df<1>(h, X, M, st) : launch_cn_explicit_df<2>(h, X, M, st);
-      if (e != cudaSuccess) return e;
-      return sweep_df(h->plan[0], false, (int)h->N, X, M, st);
+    if (cn_pair_path(h)) {  // the explicit side fused into the pair solve
+      const cudaError_t e = h->width == 3 ? launch_cn_df<1>(h, X, M, st) : launch_cn_df<2>(h, X, M, st);
+      if (e != cudaErrorInvalidValue) return e;  // else: too large for shared memory, native below
     }
   }
   const SweepPlan& p = h->plan[0];

@@ -242,6 +242,56 @@ __device__ __forceinline__ void st_f64v(void* p, const double (&x)[V]) {
     *reinterpret_cast<double*>(p) = x[0];
 }
 
+// The backward sweep of df_sweep_systems, after a forward sweep that left the
+// forward values of rows 0 .. N-D-1 at pout (as 8-byte patterns) and those of
+// rows N-D .. N-1 in the ring slots (row i in slot i % D), with st as the
+// forward sweep left it (its switch row kept).
+template <int BW, bool ADJ, int V, int D>
+__device__ __forceinline__ void df_sweep_backward(const DfRecs& rc, const Coefs<double>& c64, int N, double* pout,
+                                                  int64_t M, unsigned char* ring, uint32_t ring_s, uint32_t pitch,
+                                                  DfState<V>& st) {
+  constexpr int U = 4;
+  // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
+  // into the slot row i frees (blocks aligned to N - 1, one group each)
+  const int tail = N - D;
+  double* prow = pout + (int64_t)(N - 1) * M;
+  const double* pback = pout + (int64_t)(N - 1 - D) * M;
+  st.reset_values();
+  auto bwd = [&](auto full_tag, int top) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    const int n = FULL ? U : ((top + 1) < U ? (top + 1) : U);
+    if (FULL || top - (n - 1) < tail) cp_wait<D / U - 1>();
+    uint2 w[U][V];
+    double x[U][V];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (FULL || u < n)
+        ld8<V>(ring + (size_t)((top - u) % D) * pitch, w[u]);
+      else
+#pragma unroll
+        for (int v = 0; v < V; v++) w[u][v] = make_uint2(0u, 0u);
+    }
+    df_bwd_group<BW, ADJ, V, U, FULL>(rc, c64, top, n, w, x, st);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int i = top - u;
+      if (FULL || u < n) {
+        st_f64v<V>(prow, x[u]);
+        if (FULL || i - D >= 0) copy_row<double, V>(ring_s + (i % D) * pitch, pback);
+      }
+      prow -= M;
+      pback -= M;
+    }
+    cp_commit();
+  };
+  int top = N - 1;
+#pragma unroll 1
+  for (; top >= D + U - 1; top -= U) bwd(std::true_type{}, top);
+#pragma unroll 1
+  for (; top >= 0; top -= U) bwd(std::false_type{}, top);
+  cp_wait<0>();
+}
+
 // The two sweeps of the V systems at pout (row stride M) through the
 // lane's ring of D slots of 8 V bytes (ring: its first slot, generic and
 // shared-window addresses; pitch: bytes between slots): rows 0..D-1 are
@@ -303,46 +353,8 @@ __device__ __forceinline__ void df_sweep_systems(const DfRecs& rc, const Coefs<d
   for (; i0 + U + D <= N; i0 += U) fwd(std::true_type{}, i0);
 #pragma unroll 1
   for (; i0 < N; i0 += U) fwd(std::false_type{}, i0);
-
-  // backward sweep: rows N-1 .. N-D are in the ring; row i - D is requested
-  // into the slot row i frees (blocks aligned to N - 1, one group each)
-  const int tail = N - D;
-  prow = pout + (int64_t)(N - 1) * M;
-  const double* pback = pout + (int64_t)(N - 1 - D) * M;
-  st.reset_values();
-  auto bwd = [&](auto full_tag, int top) {
-    constexpr bool FULL = decltype(full_tag)::value;
-    const int n = FULL ? U : ((top + 1) < U ? (top + 1) : U);
-    if (FULL || top - (n - 1) < tail) cp_wait<D / U - 1>();
-    uint2 w[U][V];
-    double x[U][V];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      if (FULL || u < n)
-        ld8<V>(ring + (size_t)((top - u) % D) * pitch, w[u]);
-      else
-#pragma unroll
-        for (int v = 0; v < V; v++) w[u][v] = make_uint2(0u, 0u);
-    }
-    df_bwd_group<BW, ADJ, V, U, FULL>(rc, c64, top, n, w, x, st);
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int i = top - u;
-      if (FULL || u < n) {
-        st_f64v<V>(prow, x[u]);
-        if (FULL || i - D >= 0) copy_row<double, V>(ring_s + (i % D) * pitch, pback);
-      }
-      prow -= M;
-      pback -= M;
-    }
-    cp_commit();
-  };
-  int top = N - 1;
-#pragma unroll 1
-  for (; top >= D + U - 1; top -= U) bwd(std::true_type{}, top);
-#pragma unroll 1
-  for (; top >= 0; top -= U) bwd(std::false_type{}, top);
-  cp_wait<0>();
+  df_sweep_backward<BW, ADJ, V, D>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
 }
+
 
 }  // namespace bs

@@ -51,7 +51,7 @@ def test_periodic_diffusion(bs, N, M, sigma, steps, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("N,M,steps", [(4, 1, 1), (5, 7, 2), (64, 512, 3), (513, 2050, 2)])
+@pytest.mark.parametrize("N,M,steps", [(4, 1, 1), (5, 7, 2), (64, 512, 3), (513, 2050, 2), (3000, 40, 1)])
 def test_hyperdiffusion_penta(bs, N, M, steps, dtype):
     """The paper's second benchmark (Sec. 4.2) with zero boundary values:
     (s, -4s, 1 + 6s, -4s, s)."""
