@@ -214,7 +214,12 @@ bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const void* X, bs_dt
  * explicit side is applied while the forward sweep reads the rows (no
  * separate stencil pass); for a periodic handle it wraps around and the
  * Sherman-Morrison correction is fused as in bs_solve.  One kernel launch
- * per step, stream-ordered.  BS_EUNSUPPORTED for the strided layout. */
+ * per step, stream-ordered.  FP64 steps of a non-periodic handle whose band
+ * entries are zero or of magnitude in [2^-20, 2^20] and whose explicit side
+ * has every row's sum of |entries| at most 16 run in FP32 pairs like
+ * bs_solve's FP64 path (errors of a few 1e-14 instead of 1e-15; the
+ * BS_OPT_F64_PAIRS option set to 1 keeps FP64 arithmetic).
+ * BS_EUNSUPPORTED for the strided layout. */
 bs_status bs_cn_steps(bs_handle h, void* C, bs_dtype dtype, bs_layout layout, int64_t M, int steps,
                       bs_stream stream);
 
@@ -392,12 +397,14 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    for it when every sweep coefficient has magnitude in [2^-100, 2^100)
  *    (or is 0) and the sweeps' gains are at most 2^24 (intermediates at most
  *    2^24 times the largest input); other handles always take native FP64.
- *    A warp of systems that meets an input outside the pairs' range (nonzero
- *    |x| < 2^-72 or >= 2^101, inf, NaN) continues those systems in native
- *    FP64 from that row on.  0 (default): pairs where admitted, two systems
- *    per thread when the batch has at least 2 x 256 systems per SM (else
- *    one); 1: native FP64 always; 2: pairs with one system per thread; 3:
- *    pairs with two systems per thread (even M and 16-byte aligned data).
+ *    A system that meets an input outside the pairs' range (nonzero
+ *    |x| < 2^-72 or >= 2^101, inf, NaN) continues in native FP64 from that
+ *    row on.  0 (default): pairs where admitted, two systems per thread when
+ *    the batch has at least 2 x 256 systems per SM (else one); 1: native
+ *    FP64 always; 2: pairs with one system per thread; 3: pairs with two
+ *    systems per thread (even M and 16-byte aligned data).  The FP64 steps
+ *    of bs_cn_steps follow it too (1: native FP64; otherwise pairs where
+ *    admitted, one system per thread).
  *  BS_OPT_WINDOW: windowed sweeps that keep the forward-sweep values on chip
  *    (not in the paper).  For the matrices the method targets, a backward
  *    sweep started from zero at some row instead of from the true solution

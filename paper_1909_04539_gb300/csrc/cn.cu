@@ -420,8 +420,9 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
   }
 }
 
-// FP64 steps take the fused pair kernel when the handle allows pairs and
-// its staged records, band pairs and rings fit in shared memory.
+// FP64 steps try the fused pair kernel when the handle allows pairs (the
+// launch then checks that its staged records, band pairs and rings fit in
+// shared memory).
 static bool cn_pair_path(bs_handle h) {
   return h->cn_pairs && df_eligible(h->plan[0], BS_INTERLEAVED);
 }
