@@ -53,10 +53,10 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel
     # inside this benchmark's step (launch list of the timed steps), keyed by
     # the hash of its sources
-    "band_grad_f64": {"bytes": 546697600 + 192384, "sha": "8951e9af699c3bea"},
-    "f64_solve": {"bytes": 470403840 + 432905344, "sha": "c8f6c18d3d2c4bb5"},
-    "adjoint_f64": {"bytes": 463514496 + 427856640, "sha": "c8f6c18d3d2c4bb5"},
-    "refine_solve": {"bytes": 351270528 + 432446208, "sha": "1cbb540b290b35a9"},
+    "band_grad_f64": {"bytes": 546472448 + 130816, "sha": "294c336442a5eab8"},
+    "f64_solve": {"bytes": 470668416 + 432776832, "sha": "a6709a121809bcbc"},
+    "adjoint_f64": {"bytes": 464095872 + 428080768, "sha": "a6709a121809bcbc"},
+    "refine_solve": {"bytes": 351484416 + 432412928, "sha": "dea7148a8334397b"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],
