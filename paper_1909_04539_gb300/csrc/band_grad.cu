@@ -376,29 +376,48 @@ k_band_grad_partial(int N, int64_t M, int R, int RG, int S, const T* __restrict_
       // a value outside the pairs' range anywhere in the segment: FP64 FMAs
       if (__syncthreads_or(bad)) fp64();
     }
-    // Warp reduce-scatter over the NV values (padded to 64): at each level a
-    // lane keeps one half, sends the other to its partner and adds what it
-    // receives, so that lane l ends with the warp sums of values 2l, 2l + 1.
-    double w32[32];
+    // Warp reduce-scatter over the NV values: at each level a lane keeps one
+    // half, sends the other to its partner and adds what it receives.  Up to
+    // 16 values (every use here): four halvings leave lane l with value
+    // l / 2 summed over 16 lanes, and a last exchange with lane l ^ 1 makes
+    // it the warp sum -- 16 FP64 additions per lane (63 when padded to 64).
+    if constexpr (NV <= 16) {
+      double w16[16];
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-      const double a = (i < NV) ? acc[i < NV ? i : 0] : 0.0;
-      const double b = (i + 32 < NV) ? acc[i + 32 < NV ? i + 32 : 0] : 0.0;
-      const bool up = lane & 16;
-      const double keep = up ? b : a, send = up ? a : b;
-      w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
+      for (int i = 0; i < 16; i++) w16[i] = (i < NV) ? acc[i < NV ? i : 0] : 0.0;
 #pragma unroll
-    for (int o = 8, n = 16; o >= 1; o >>= 1, n >>= 1) {
+      for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
 #pragma unroll
-      for (int i = 0; i < n; i++) {
-        const bool up = lane & o;
-        const double keep = up ? w32[i + n] : w32[i], send = up ? w32[i] : w32[i + n];
-        w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        for (int i = 0; i < n; i++) {
+          const bool up = lane & o;
+          const double keep = up ? w16[i + n] : w16[i], send = up ? w16[i] : w16[i + n];
+          w16[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
       }
+      w16[0] += __shfl_xor_sync(0xffffffffu, w16[0], 1);
+      if ((lane & 1) == 0) red[warp][lane >> 1] = w16[0];
+    } else {  // padded to 64: lane l ends with the warp sums of values 2l, 2l + 1
+      double w32[32];
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const double a = (i < NV) ? acc[i < NV ? i : 0] : 0.0;
+        const double b = (i + 32 < NV) ? acc[i + 32 < NV ? i + 32 : 0] : 0.0;
+        const bool up = lane & 16;
+        const double keep = up ? b : a, send = up ? a : b;
+        w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int o = 8, n = 16; o >= 1; o >>= 1, n >>= 1) {
+#pragma unroll
+        for (int i = 0; i < n; i++) {
+          const bool up = lane & o;
+          const double keep = up ? w32[i + n] : w32[i], send = up ? w32[i] : w32[i + n];
+          w32[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      red[warp][2 * lane] = w32[0];
+      red[warp][2 * lane + 1] = w32[1];
     }
-    red[warp][2 * lane] = w32[0];
-    red[warp][2 * lane + 1] = w32[1];
     __syncthreads();
     if (threadIdx.x < NV * kGradGroups) {
       constexpr int WG = kGradGroupThreads / 32;  // warps per group
