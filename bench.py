@@ -53,10 +53,10 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel
     # inside this benchmark's step (launch list of the timed steps), keyed by
     # the hash of its sources
-    "band_grad_f64": {"bytes": 546280832 + 146176, "sha": "48c6229cf26ea2e7"},
-    "f64_solve": {"bytes": 470668416 + 432776832, "sha": "a6709a121809bcbc"},
-    "adjoint_f64": {"bytes": 464095872 + 428080768, "sha": "a6709a121809bcbc"},
-    "refine_solve": {"bytes": 351484416 + 432412928, "sha": "dea7148a8334397b"},
+    "band_grad_f64": {"bytes": 546093056 + 141312, "sha": "64108a499aa00103"},
+    "f64_solve": {"bytes": 470581504 + 431310080, "sha": "9c678e6d1456bd9a"},
+    "adjoint_f64": {"bytes": 464063488 + 427904768, "sha": "9c678e6d1456bd9a"},
+    "refine_solve": {"bytes": 351479808 + 432544000, "sha": "1ea2c7ce3cedb3ca"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],

@@ -387,8 +387,7 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    (BS_EINVAL).  The result does not depend on it.
  *  BS_OPT_F64_PAIRS: arithmetic of the FP64 (BS_F64) solves of bs_solve and
  *    bs_solve_adjoint that run one thread per system (not row-partitioned,
- *    not two-ended), interleaved layout, non-periodic handle (not in the
- *    paper).  GB300 issues FP64 instructions at ~1/66 of the FP32 rate, so
+ *    not two-ended), interleaved layout (not in the paper).  GB300 issues FP64 instructions at ~1/66 of the FP32 rate, so
  *    these sweeps carry every value as an unevaluated sum of two FP32 numbers
  *    (48 significant bits) formed with error-free products and sums, and
  *    convert the FP64 data with integer operations: FP64 in, FP64 out,
@@ -397,9 +396,12 @@ bs_status bs_server_stats(bs_server s, int64_t* out, int n);
  *    for it when every sweep coefficient has magnitude in [2^-100, 2^100)
  *    (or is 0) and the sweeps' gains are at most 2^24 (intermediates at most
  *    2^24 times the largest input); other handles always take native FP64.
- *    A system that meets an input outside the pairs' range (nonzero
- *    |x| < 2^-72 or >= 2^101, inf, NaN) continues in native FP64 from that
- *    row on.  0 (default): pairs where admitted, two systems per thread when
+ *    A periodic handle also carries its Sherman-Morrison sum and correction
+ *    in pairs (bs_factor_periodic scales the two weight vectors by a power
+ *    of two and admits them when, so scaled, sum |pw| <= 2^20 and
+ *    max |pc| lies in [2^-40, 2^20]).  A system that meets an input outside
+ *    the pairs' range (nonzero |x| < 2^-72 or >= 2^101, for a periodic
+ *    handle >= 2^80; inf, NaN) continues in native FP64 from that row on.  0 (default): pairs where admitted, two systems per thread when
  *    the batch has at least 2 x 256 systems per SM (else one); 1: native
  *    FP64 always; 2: pairs with one system per thread; 3: pairs with two
  *    systems per thread (even M and 16-byte aligned data).  The FP64 steps

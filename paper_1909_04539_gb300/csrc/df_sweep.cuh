@@ -25,6 +25,8 @@ struct DfRecs {
   const float4* b4;
   const float2* f2;
   const float2* b2;
+  const float4* pq = nullptr;  // periodic plans: scaled (pw', pc') pairs per row (SweepPlan::dfper)
+  double per_unscale = 1.0;    // sigma = per_unscale sigma'
 };
 
 __host__ __device__ inline DfRecs df_recs_of(const float* dfrec, int64_t N) {
@@ -79,11 +81,40 @@ struct DfState {
       d1[v] = d2[v] = 0.0;
     }
   }
+  // periodic plans: sigma' = sum pw'_i f_i of the forward sweep in pairs
+  // (the FP64 sigma = 2^-k sigma' after a switch), read by the backward sweep
+  df::Pair sig[V];
+  double dsig[V];
+  __device__ __forceinline__ void reset_sigma() {
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      sig[v] = dpair(0.f, 0.f);
+      dsig[v] = 0.0;
+    }
+  }
 };
+
+// s + (ch + cl) y in pairs, unnormalised: the product a TwoProduct of the high
+// parts plus both cross terms, the sum a TwoSum of the high parts
+__device__ __forceinline__ df::Pair df_muladd(df::Pair s, float ch, float cl, df::Pair y) {
+  const float p = df::mul(ch, y.h);
+  float e = df::fma_(ch, y.h, -p);
+  e = df::fma_(ch, y.l, e);
+  e = df::fma_(cl, y.h, e);
+  float h, t;
+  df::two_sum(s.h, p, h, t);
+  return dpair(h, df::add(s.l, df::add(t, e)));
+}
+
+// Periodic plans keep inputs below 2^80 in pairs (their correction term
+// sigma pc_i then stays inside FP32); larger ones go to FP64.
+__device__ __forceinline__ bool df_per_small(double f) {
+  return ((uint32_t)__double2hiint(f) & 0x7fffffffu) < ((1023u + 80u) << 20);
+}
 
 // Forward group: rows i0 .. i0+n-1 (FULL: n == U), FP64 inputs f; out: the
 // forward values as 8-byte patterns (pairs, or FP64 from rsw on).
-template <int BW, bool ADJ, int V, int U, bool FULL>
+template <int BW, bool ADJ, int V, int U, bool FULL, bool PER = false>
 __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<double>& c64, int i0, int n,
                                              double (&f)[U][V], uint2 (&out)[U][V], DfState<V>& st) {
   constexpr bool F2 = DfCount<ADJ, BW>::F > 2;
@@ -105,7 +136,7 @@ __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<doubl
 #pragma unroll
       for (int v = 0; v < V; v++) {
         y[u][v] = dpair(0.f, 0.f);
-        if (FULL || u < n) need |= !df::split_fast(f[u][v], y[u][v]);
+        if (FULL || u < n) need |= !df::split_fast(f[u][v], y[u][v]) || (PER && !df_per_small(f[u][v]));
       }
   }
   if (__any_sync(__activemask(), need)) {
@@ -116,7 +147,10 @@ __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<doubl
 #pragma unroll
         for (int v = 0; v < V; v++) {
           bool ok = true;
-          if (FULL || u < n) y[u][v] = df::split(f[u][v], ok);
+          if (FULL || u < n) {
+            y[u][v] = df::split(f[u][v], ok);
+            if (PER) ok = ok && df_per_small(f[u][v]);
+          }
           bad |= !ok;
         }
       if (bad) {
@@ -126,7 +160,23 @@ __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<doubl
         for (int v = 0; v < V; v++) {
           st.d1[v] = pair_to_f64(st.p1[v]);
           st.d2[v] = pair_to_f64(st.p2[v]);
+          if (PER) st.dsig[v] = pair_to_f64(st.sig[v]) * rc.per_unscale;
         }
+      }
+    }
+  }
+  if constexpr (PER) {  // sigma += pw_i f_i outside the rows without correction terms (pw' in pairs)
+    if (i0 < c64.per_lo || i0 + n > c64.per_hi) {
+      if (!st.f64) {
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          if (FULL || u < n) {
+            const float4 w = rc.pq[i0 + u];
+#pragma unroll
+            for (int v = 0; v < V; v++) st.sig[v] = df_muladd(st.sig[v], w.x, w.y, y[u][v]);
+          }
+      } else {
+        per_dot<double, V, U>(c64, i0, n, f, st.dsig);
       }
     }
   }
@@ -152,10 +202,13 @@ __device__ __forceinline__ void df_fwd_group(const DfRecs& rc, const Coefs<doubl
 
 // Backward group: rows top, top-1, .., top-n+1; in: their forward values as
 // stored by df_fwd_group (8-byte patterns); x: the solution in FP64.
-template <int BW, bool ADJ, int V, int U, bool FULL>
+template <int BW, bool ADJ, int V, int U, bool FULL, bool PER = false>
 __device__ __forceinline__ void df_bwd_group(const DfRecs& rc, const Coefs<double>& c64, int top, int n,
                                              const uint2 (&in)[U][V], double (&x)[U][V], DfState<V>& st) {
   constexpr bool B2 = DfCount<ADJ, BW>::B > 2;
+  // periodic plans: x_i = y_i - sigma pc_i outside the rows without
+  // correction terms (the recurrence keeps the uncorrected y)
+  const bool corr = PER && (top + 1 - n < c64.per_lo || top + 1 > c64.per_hi);
   if (!st.f64) {
     float4 q[U];
     float2 q2[U];
@@ -176,6 +229,11 @@ __device__ __forceinline__ void df_bwd_group(const DfRecs& rc, const Coefs<doubl
           y[u][v] = df_row<ADJ, BW>(q[u], q2[u], bits_pair(in[u][v]), st.p1[v], st.p2[v]);
           st.p2[v] = st.p1[v];
           st.p1[v] = y[u][v];
+          if (PER && corr) {
+            const float4 w = rc.pq[top - u];
+            const df::Pair z = df_muladd(y[u][v], -w.z, -w.w, st.sig[v]);
+            df::fast_two_sum(z.h, z.l, y[u][v].h, y[u][v].l);
+          }
           need |= !df::combine_ok(y[u][v].h);
         }
         x[u][v] = df::combine_fast(y[u][v].h, y[u][v].l);
@@ -203,6 +261,7 @@ __device__ __forceinline__ void df_bwd_group(const DfRecs& rc, const Coefs<doubl
           x[u][v] = (top - u >= st.rsw) ? bits_f64(in[u][v]) : pair_to_f64(bits_pair(in[u][v]));
     }
     bwd_block<BW, ADJ, double, V, U, false>(c64, top, n, x, st.d1, st.d2);
+    if (PER && corr) per_fix<double, V, U>(c64, top, n, x, st.dsig);
   }
 }
 
@@ -246,7 +305,7 @@ __device__ __forceinline__ void st_f64v(void* p, const double (&x)[V]) {
 // forward values of rows 0 .. N-D-1 at pout (as 8-byte patterns) and those of
 // rows N-D .. N-1 in the ring slots (row i in slot i % D), with st as the
 // forward sweep left it (its switch row kept).
-template <int BW, bool ADJ, int V, int D>
+template <int BW, bool ADJ, int V, int D, bool PER = false>
 __device__ __forceinline__ void df_sweep_backward(const DfRecs& rc, const Coefs<double>& c64, int N, double* pout,
                                                   int64_t M, unsigned char* ring, uint32_t ring_s, uint32_t pitch,
                                                   DfState<V>& st) {
@@ -271,7 +330,7 @@ __device__ __forceinline__ void df_sweep_backward(const DfRecs& rc, const Coefs<
 #pragma unroll
         for (int v = 0; v < V; v++) w[u][v] = make_uint2(0u, 0u);
     }
-    df_bwd_group<BW, ADJ, V, U, FULL>(rc, c64, top, n, w, x, st);
+    df_bwd_group<BW, ADJ, V, U, FULL, PER>(rc, c64, top, n, w, x, st);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int i = top - u;
@@ -298,7 +357,7 @@ __device__ __forceinline__ void df_sweep_backward(const DfRecs& rc, const Coefs<
 // requested up front, one copy group per block of U = 4 rows; the forward
 // values go to pout in place as pairs, the last D stay in the ring; the
 // backward sweep streams them back and writes X in FP64.
-template <int BW, bool ADJ, int V, int D>
+template <int BW, bool ADJ, int V, int D, bool PER = false>
 __device__ __forceinline__ void df_sweep_systems(const DfRecs& rc, const Coefs<double>& c64, int N,
                                                  double* pout, int64_t M, unsigned char* ring,
                                                  uint32_t ring_s, uint32_t pitch) {
@@ -306,6 +365,7 @@ __device__ __forceinline__ void df_sweep_systems(const DfRecs& rc, const Coefs<d
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
   DfState<V> st;
   st.reset_values();
+  if (PER) st.reset_sigma();
   st.f64 = false;
   st.rsw = N;
   // forward sweep: rows 0..D-1 requested up front (one copy group per
@@ -334,7 +394,7 @@ __device__ __forceinline__ void df_sweep_systems(const DfRecs& rc, const Coefs<d
 #pragma unroll
         for (int v = 0; v < V; v++) f[u][v] = 0.0;
     }
-    df_fwd_group<BW, ADJ, V, U, FULL>(rc, c64, i0, n, f, w, st);
+    df_fwd_group<BW, ADJ, V, U, FULL, PER>(rc, c64, i0, n, f, w, st);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int i = i0 + u;
@@ -353,7 +413,7 @@ __device__ __forceinline__ void df_sweep_systems(const DfRecs& rc, const Coefs<d
   for (; i0 + U + D <= N; i0 += U) fwd(std::true_type{}, i0);
 #pragma unroll 1
   for (; i0 < N; i0 += U) fwd(std::false_type{}, i0);
-  df_sweep_backward<BW, ADJ, V, D>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
+  df_sweep_backward<BW, ADJ, V, D, PER>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
 }
 
 

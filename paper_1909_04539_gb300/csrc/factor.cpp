@@ -221,6 +221,7 @@ void free_handle(bs_handle h) {
     if (p.c64) cudaFree(p.c64);
     if (p.c32) cudaFree(p.c32);
     if (p.dfrec) cudaFree(p.dfrec);
+    if (p.dfper) cudaFree(p.dfper);
     if (p.rec32) cudaFree(p.rec32);
   }
   if (h->bands64) cudaFree(h->bands64);
@@ -463,6 +464,43 @@ bool make_df_records(const HostPlan& hp, int64_t N, std::vector<float>& rec) {
   return ok && std::isfinite(g) && g <= std::ldexp(1.0, 24);
 }
 
+// The Sherman-Morrison weights of a periodic plan as FP32 pairs, per row
+// (pw hi, pw lo, pc hi, pc lo) (layout of SweepPlan::dfper), scaled by an
+// exact power of two: pw' = 2^k pw with max |pw'| in [1, 2), pc' = 2^-k pc,
+// so that sigma' pc' = sigma pc (unscale = 2^-k).  Weights decay
+// geometrically away from the first and last rows; the small ones may fall
+// below the FP32 range and drop out, each changing x by less than 2^-120
+// of max |f|.  Returns whether the pair sweeps may carry the correction:
+// all weights finite, sum |pw'| <= 2^20 and max |pc'| in [2^-40, 2^20] (or
+// zero), so that with inputs below 2^80 (the pair sweeps of a periodic plan
+// take larger ones to FP64) sigma' stays below 2^100 and sigma' pc' below
+// 2^120.
+bool make_df_periodic(const HostPlan& hp, int64_t N, std::vector<float>& rec, double& unscale) {
+  bool ok = true;
+  double wmax = 0.0, cmax = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    const double w = hp.c[(size_t)C_PW * N + i], c = hp.c[(size_t)C_PC * N + i];
+    if (!std::isfinite(w) || !std::isfinite(c)) ok = false;
+    wmax = std::fmax(wmax, std::fabs(w));
+    cmax = std::fmax(cmax, std::fabs(c));
+  }
+  const int k = (ok && wmax > 0.0) ? -std::ilogb(wmax) : 0;
+  unscale = std::ldexp(1.0, -k);
+  double sum = 0.0;
+  rec.assign((size_t)4 * N, 0.f);
+  for (int64_t i = 0; i < N && ok; i++) {
+    const double w = std::ldexp(hp.c[(size_t)C_PW * N + i], k), c = std::ldexp(hp.c[(size_t)C_PC * N + i], -k);
+    sum += std::fabs(w);
+    const float wh = (float)w, ch = (float)c;
+    rec[4 * i] = wh;
+    rec[4 * i + 1] = (float)(w - (double)wh);
+    rec[4 * i + 2] = ch;
+    rec[4 * i + 3] = (float)(c - (double)ch);
+  }
+  const double cm = std::ldexp(cmax, -k);
+  return ok && k > -1000 && k < 1000 && sum <= 0x1p20 && (cmax == 0.0 || (cm >= 0x1p-40 && cm <= 0x1p20));
+}
+
 // Window lengths of the windowed sweeps (sweep_win.cu) of one plan.  A
 // backward sweep started from zero at row e instead of from the true x_e,
 // x_{e+1} is off at row j < e by psi1_j x_e + psi2_j x_{e+1}, where psi1,
@@ -607,14 +645,23 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   size_t bytes = 0;
   cudaError_t e = cudaSuccess;
   for (int p = 0; p < 3 && e == cudaSuccess; p++) e = upload_plan(hp[p], hd->plan[p], bytes);
-  // FP32-pair sweep records of the primal and adjoint plans (not periodic)
-  for (int p = 0; p < 2 && e == cudaSuccess && !periodic; p++) {
+  // FP32-pair sweep records of the primal and adjoint plans (periodic plans:
+  // and their correction weights); FP32 records and windows (not periodic)
+  for (int p = 0; p < 2 && e == cudaSuccess; p++) {
     std::vector<float> rec;
     hd->plan[p].df_ok = make_df_records(hp[p], N, rec);
     e = cudaMalloc(&hd->plan[p].dfrec, sizeof(float) * rec.size());
     if (e == cudaSuccess)
       e = cudaMemcpy(hd->plan[p].dfrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice);
     bytes += sizeof(float) * rec.size();
+    if (periodic) {
+      hd->plan[p].df_ok = make_df_periodic(hp[p], N, rec, hd->plan[p].dfper_unscale) && hd->plan[p].df_ok;
+      if (e == cudaSuccess) e = cudaMalloc(&hd->plan[p].dfper, sizeof(float) * rec.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(hd->plan[p].dfper, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice);
+      bytes += sizeof(float) * rec.size();
+      continue;
+    }
     make_rec32(hp[p], N, rec);
     if (e == cudaSuccess) e = cudaMalloc(&hd->plan[p].rec32, sizeof(float) * rec.size());
     if (e == cudaSuccess)

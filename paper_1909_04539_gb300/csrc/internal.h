@@ -60,6 +60,11 @@ struct SweepPlan {
   // inside the FP32 range for inputs below 2^101 (see make_df_records)
   float* dfrec;
   bool df_ok;
+  // periodic plans: per row the correction weights (pw', pc') = (2^k pw,
+  // 2^-k pc) as FP32 pairs, (pw' hi, pw' lo, pc' hi, pc' lo) as float4 x N
+  // (device; null otherwise); dfper_unscale = 2^-k (sigma = 2^-k sigma')
+  float* dfper;
+  double dfper_unscale;
   // Windowed sweeps (sweep_win.cu): FP32 records, per row forward
   // (s, l1, l2, 0) and backward (t, u1, u2, 0) as float4 (device, 32 N
   // bytes); win32 / win_df: rows after which a backward sweep started from

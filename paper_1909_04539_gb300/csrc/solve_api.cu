@@ -197,9 +197,9 @@ bool use_partition(bs_handle h, int64_t M) {
 // applies (the caller runs the streaming kernels).
 static bool fast_sweep(const SweepPlan& p, bool adjoint, int N, void* B, bs_dtype dtype, bs_layout layout,
                        int64_t M, cudaStream_t st, cudaError_t* e) {
-  if (layout != BS_INTERLEAVED || p.periodic) return false;
+  if (layout != BS_INTERLEAVED) return false;
   const bool win = option(BS_OPT_WINDOW) != 1;
-  if (dtype == BS_F64 && df_eligible(p, layout)) {
+  if (dtype == BS_F64 && df_eligible(p, layout)) {  // periodic plans too (no windows)
     // pairs: the two-sweep kernel unless windows are asked for (the pair
     // arithmetic is bound by instruction issue, and the windowed sweep's extra
     // backward steps cost more than the forward values' round trip through
@@ -208,6 +208,7 @@ static bool fast_sweep(const SweepPlan& p, bool adjoint, int N, void* B, bs_dtyp
                                                        : sweep_df(p, adjoint, N, static_cast<double*>(B), M, st);
     return true;
   }
+  if (p.periodic) return false;
   // (the scalar-eps sweeps of a uniform pentadiagonal matrix, on request,
   // run in the streaming kernels)
   const bool uni = p.uniform && p.bw == 2 && option(BS_OPT_UNIFORM) == 2;

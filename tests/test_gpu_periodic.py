@@ -191,3 +191,75 @@ def test_periodic_weak_dominance(bs, b):
         bs.solve(f, B, layout)
         ref = oracle.periodic_tri_solve(-1.0, b, -1.0, B_in, layout)
         parity(B.cpu().numpy(), ref, TOL64, layout)
+
+
+@pytest.fixture
+def pair_mode(bs):
+    yield lambda m: bs.set_option(bs.OPT_F64_PAIRS, m)
+    bs.set_option(bs.OPT_F64_PAIRS, 0)
+
+
+def _solve_both(bs, f, Bh):
+    X = torch.tensor(Bh, device="cuda")
+    bs.solve(f, X)
+    G = torch.tensor(Bh, device="cuda")
+    bs.solve_adjoint(f, G)
+    return X.cpu().numpy(), G.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("N,M", [(3, 2), (4, 1), (5, 34), (64, 1024), (257, 1030), (1030, 4096)])
+def test_periodic_fp64_pairs(bs, pair_mode, N, M, mode):
+    """FP64 periodic solves carried in FP32 pairs (BS_OPT_F64_PAIRS 2: one
+    system per thread, 3: two): the Sherman-Morrison sum sigma and the
+    correction x_i = y_i - sigma pc_i (Sec. 3.3) in pair arithmetic, primal
+    and adjoint, against the oracle at the FP64 tolerance; they differ from
+    the native FP64 solve (option 1) by the pairs' rounding only."""
+    bands, Bh = _case(N, M, 5 * N + M, "interleaved")
+    Bh = Bh * np.ldexp(1.0, np.random.default_rng(N).integers(-20, 20, M))
+    f = bs.Factor(bands, periodic=True)
+    pair_mode(mode)
+    Xp, Gp = _solve_both(bs, f, Bh)
+    pair_mode(1)
+    Xn, Gn = _solve_both(bs, f, Bh)
+    ref_x = oracle.periodic_tri_solve_bands(bands, Bh)
+    ref_g = oracle.periodic_solve_adjoint(bands, Bh)
+    parity(Xp, ref_x, TOL64)
+    parity(Gp, ref_g, TOL64)
+    parity(Xn, ref_x, 1e-14)
+    parity(Gn, ref_g, 1e-14)
+    if N * M > 1000:  # the pair path ran: its rounding differs from FP64's
+        assert not np.array_equal(Xp, Xn)
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_periodic_pairs_out_of_range_inputs(bs, pair_mode, mode):
+    """Inputs the periodic pair sweeps do not hold (|x| >= 2^80, so that the
+    correction stays inside FP32; 1e200; 1e-200; an FP64 subnormal) send
+    their warp to native FP64 from that row on, sigma carried over; NaN and
+    inf poison only their own system; a zero system stays zero."""
+    pair_mode(mode)
+    N, M = 300, 4096
+    bands = synth.random_periodic_bands(N, np.random.default_rng(21))
+    Bh = np.random.default_rng(22).uniform(-1, 1, (N, M))
+    specials = {70: ("scale", 1e200), 200: ("scale", 1e-200), 333: ("one", 5e-324), 501: ("one", 2.0 ** 85),
+                502: ("one", 2.0 ** 80), 640: ("one", 1e-25), 900: ("nan", np.nan), 1300: ("inf", np.inf),
+                2000: ("zero", 0.0)}
+    for j, (kind, v) in specials.items():
+        row = (j * 7) % N
+        if kind == "scale":
+            Bh[:, j] *= v
+        elif kind == "zero":
+            Bh[:, j] = 0.0
+        else:
+            Bh[row, j] = v
+    f = bs.Factor(bands, periodic=True)
+    X, G = _solve_both(bs, f, Bh)
+    finite = [j for j in range(M) if np.all(np.isfinite(Bh[:, j]))]
+    bad = [j for j in range(M) if j not in finite]
+    refs = (oracle.periodic_tri_solve_bands(bands, Bh[:, finite]), oracle.periodic_solve_adjoint(bands, Bh[:, finite]))
+    for got, ref in zip((X, G), refs):
+        parity(got[:, finite], ref, TOL64)
+        for j in bad:
+            assert not np.all(np.isfinite(got[:, j]))
+    assert np.all(X[:, 2000] == 0) and np.all(G[:, 2000] == 0)
