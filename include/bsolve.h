@@ -214,11 +214,14 @@ bs_status bs_band_grad_noalloc(bs_handle h, const void* GB, const void* X, bs_dt
  * explicit side is applied while the forward sweep reads the rows (no
  * separate stencil pass); for a periodic handle it wraps around and the
  * Sherman-Morrison correction is fused as in bs_solve.  One kernel launch
- * per step, stream-ordered.  FP64 steps of a non-periodic handle whose band
- * entries are zero or of magnitude in [2^-20, 2^20] and whose explicit side
- * has every row's sum of |entries| at most 16 run in FP32 pairs like
- * bs_solve's FP64 path (errors of a few 1e-14 instead of 1e-15; the
- * BS_OPT_F64_PAIRS option set to 1 keeps FP64 arithmetic).
+ * per step, stream-ordered.  FP64 steps of a handle whose band entries
+ * (corners included) are zero or of magnitude in [2^-20, 2^20] and whose
+ * explicit side has every row's sum of |entries| at most 16 run in FP32
+ * pairs like bs_solve's FP64 path, the Sherman-Morrison terms of a periodic
+ * handle included (errors of a few 1e-14 instead of 1e-15; the
+ * BS_OPT_F64_PAIRS option set to 1 keeps FP64 arithmetic).  A system with
+ * a value the pairs do not hold (|C| >= 2^97, 2^76 for a periodic handle;
+ * nonzero |C| < 2^-72; inf, NaN) continues in FP64 from that row on.
  * BS_EUNSUPPORTED for the strided layout. */
 bs_status bs_cn_steps(bs_handle h, void* C, bs_dtype dtype, bs_layout layout, int64_t M, int steps,
                       bs_stream stream);

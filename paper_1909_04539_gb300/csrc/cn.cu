@@ -258,17 +258,34 @@ static cudaError_t launch_cn(const SweepPlan& p, const C* bands, int N, C* X, in
 // window; the forward values of the last D rows stay in their slots, the
 // others go to C in place, and the backward sweep is the pair solve's
 // (df_sweep_backward).  A lane that meets an input outside the pairs' range
-// runs the rest of its system in FP64 from the current block of rows on.
+// runs the rest of its system in FP64 from the current block of rows on; the
+// range is |C| < 2^97 (the explicit side's row sums are at most 16, so the
+// sweep's inputs stay below the pair solve's 2^101), for a periodic handle
+// 2^76 (its Sherman-Morrison sum then stays inside FP32, see df_sweep.cuh).
+//
+// PER (periodic tridiagonal handle): the explicit side wraps around -- row
+// -1 of the window is C_{N-1}, read before the sweep, and row N is C_0,
+// kept from the first block -- and the forward sweep accumulates the
+// Sherman-Morrison sum over the explicit side's rows, the backward sweep
+// applies the correction (df_sweep_backward with PER).
 constexpr int kCnFusedThreadsMax = 512;
 
-template <int BW, bool SMEM, int D>
+// |v| < 2^e (or v zero / any value below; NaN and inf fail)
+template <int E>
+__device__ __forceinline__ bool cn_pair_small(double v) {
+  return ((uint32_t)__double2hiint(v) & 0x7fffffffu) < ((1023u + E) << 20);
+}
+
+template <int BW, bool SMEM, int D, bool PER>
 __global__ void __launch_bounds__(kCnFusedThreadsMax)
 k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float* __restrict__ blo,
         const double* __restrict__ b64, int N, double* X, int64_t M) {
   constexpr int W = 2 * BW + 1;
   constexpr int U = 4;
   constexpr int NW = 2 * BW + U;
+  constexpr int kTop = PER ? 76 : 97;
   static_assert(D % U == 0, "ring depth must be a multiple of the block");
+  static_assert(!PER || BW == 1, "periodic handles are tridiagonal");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DfRecs rc = rg;
   size_t rec_bytes = 0;
@@ -279,15 +296,17 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
     float4* b4 = f4 + N;
     float2* f2 = reinterpret_cast<float2*>(b4 + N);
     float2* b2 = f2 + N;
+    float4* pq = reinterpret_cast<float4*>(b2 + N);  // periodic: the (pw', pc') pairs
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       f4[i] = rg.f4[i];
       b4[i] = rg.b4[i];
       if (F2) f2[i] = rg.f2[i];
       if (B2) b2[i] = rg.b2[i];
+      if (PER) pq[i] = rg.pq[i];
     }
-    rc = DfRecs{f4, b4, f2, b2};
-    bp = reinterpret_cast<float2*>(b2 + N);
-    rec_bytes = (size_t)N * 48;
+    rc = DfRecs{f4, b4, f2, b2, PER ? pq : nullptr, rg.per_unscale};
+    bp = reinterpret_cast<float2*>(pq + (PER ? N : 0));
+    rec_bytes = (size_t)N * (PER ? 64 : 48);
   }
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, k = t - i * W;
@@ -303,8 +322,10 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
     double* const pout = X + j;
     DfState<1> st;
     st.reset_values();
+    if (PER) st.reset_sigma();
     st.f64 = false;
     st.rsw = N;
+    double c0 = 0.0;  // periodic: C_0, row N of the window
     const double* pnext = pout;
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
@@ -318,6 +339,19 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
     for (int q = 0; q < NW; q++) {
       y[q] = df::Pair{0.f, 0.f};
       d[q] = 0.0;
+    }
+    if constexpr (PER) {  // row -1 of the first window: C_{N-1}
+      const double v = pout[(int64_t)(N - 1) * M];
+      d[NW - 1] = v;
+      bool ok = df::split_fast(v, y[NW - 1]) && cn_pair_small<kTop>(v);
+      if (!ok) {
+        ok = true;
+        y[NW - 1] = df::split(v, ok);
+        if (!(ok && cn_pair_small<kTop>(v))) {
+          st.f64 = true;
+          st.rsw = 0;
+        }
+      }
     }
     double* prow = pout - (int64_t)BW * M;  // forward output row 4b - BW
 #pragma unroll 1
@@ -335,9 +369,12 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
         const int r = r0 + u;
         double v = 0.0;
         if (r < N) v = *reinterpret_cast<const double*>(ring + (size_t)(s0 + u) * pitch);
+        if (PER && r == 0) c0 = v;
+        if (PER && r == N) v = c0;
         d[2 * BW + u] = v;
         y[2 * BW + u] = df::Pair{0.f, 0.f};
-        if (r < N && !st.f64) need |= !df::split_fast(v, y[2 * BW + u]);
+        if ((r < N || (PER && r == N)) && !st.f64)
+          need |= !df::split_fast(v, y[2 * BW + u]) || !cn_pair_small<kTop>(v);
       }
 #pragma unroll
       for (int u = 0; u < U; u++) {
@@ -353,13 +390,14 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
           for (int u = 0; u < U; u++) {
             bool ok = true;
             y[2 * BW + u] = df::split(d[2 * BW + u], ok);
-            bad |= !ok;
+            bad |= !(ok && cn_pair_small<kTop>(d[2 * BW + u]));
           }
           if (bad && !st.f64) {
             st.f64 = true;
             st.rsw = i0 > 0 ? i0 : 0;
             st.d1[0] = pair_to_f64(st.p1[0]);
             st.d2[0] = pair_to_f64(st.p2[0]);
+            if (PER) st.dsig[0] = pair_to_f64(st.sig[0]) * rc.per_unscale;
           }
         }
       }
@@ -387,6 +425,10 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
           }
           df::Pair f;
           df::fast_two_sum(sh, lo, f.h, f.l);
+          if (PER && (i < c64.per_lo || i >= c64.per_hi)) {  // sigma' += pw'_i f_i
+            const float4 w = rc.pq[i];
+            st.sig[0] = df_muladd(st.sig[0], w.x, w.y, f);
+          }
           const float4 q = rc.f4[i];
           const float2 q2 = BW == 2 ? rc.f2[i] : make_float2(0.f, 0.f);
           const df::Pair w = df_row<true, BW>(q, q2, f, st.p1[0], st.p2[0]);
@@ -397,6 +439,7 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
           double f[1] = {2.0 * d[u + BW]};
 #pragma unroll
           for (int k = 0; k < W; k++) f[0] = fma(-b64[(size_t)k * N + i], d[u + k], f[0]);
+          if (PER && (i < c64.per_lo || i >= c64.per_hi)) st.dsig[0] = fma(c64.pw[i], f[0], st.dsig[0]);
           fwd_step<BW, false, double, 1>(c64, i, f, st.d1, st.d2);
           wout[u] = f64_bits(f[0]);
         }
@@ -416,7 +459,7 @@ k_cn_df(DfRecs rg, Coefs<double> c64, const float* __restrict__ bhi, const float
       }
     }
     cp_wait<0>();
-    df_sweep_backward<BW, false, 1, D>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
+    df_sweep_backward<BW, false, 1, D, PER>(rc, c64, N, pout, M, ring, ring_s, pitch, st);
   }
 }
 
@@ -432,15 +475,21 @@ static bool cn_pair_path(bs_handle h) {
 // the busiest-SM model with ties to the largest (penta N = 512, M = 65536:
 // 64-thread CTAs, four per SM by shared memory, 0.442 ms; ties to the largest
 // 0.315 ms).
-template <int BW>
+template <int BW, bool PER>
 static cudaError_t launch_cn_df(bs_handle h, double* X, int64_t M, cudaStream_t st) {
   constexpr int D = 16;  // rows in flight per lane
   const int N = (int)h->N;
   const SweepPlan& p = h->plan[0];
-  const DfRecs rg = df_recs_of(p.dfrec, N);
-  const Coefs<double> c64 = coefs_of<double>(p.c64, N);
-  const size_t rec = align_up((size_t)N * 48 + (size_t)N * (2 * BW + 1) * sizeof(float2), 16);
-  auto k = k_cn_df<BW, true, D>;
+  DfRecs rg = df_recs_of(p.dfrec, N);
+  Coefs<double> c64 = coefs_of<double>(p.c64, N);
+  if (PER) {
+    rg.pq = reinterpret_cast<const float4*>(p.dfper);
+    rg.per_unscale = p.dfper_unscale;
+    c64.per_lo = p.per_lo;
+    c64.per_hi = p.per_hi;
+  }
+  const size_t rec = align_up((size_t)N * (PER ? 64 : 48) + (size_t)N * (2 * BW + 1) * sizeof(float2), 16);
+  auto k = k_cn_df<BW, true, D, PER>;
   const StagedShape sh =
       staged_shape(M, rec, (size_t)D * 8, kernel_regs((const void*)k), kCnFusedThreadsMax, true, kCnFusedThreadsMax);
   if (sh.threads == 0 || !sh.staged) return cudaErrorInvalidValue;
@@ -455,7 +504,9 @@ template <typename C, int VEC>
 static cudaError_t cn_dispatch(bs_handle h, C* X, int64_t M, cudaStream_t st) {
   if constexpr (sizeof(C) == 8) {
     if (cn_pair_path(h)) {  // the explicit side fused into the pair solve
-      const cudaError_t e = h->width == 3 ? launch_cn_df<1>(h, X, M, st) : launch_cn_df<2>(h, X, M, st);
+      const cudaError_t e = h->periodic     ? launch_cn_df<1, true>(h, X, M, st)
+                            : h->width == 3 ? launch_cn_df<1, false>(h, X, M, st)
+                                            : launch_cn_df<2, false>(h, X, M, st);
       if (e != cudaErrorInvalidValue) return e;  // else: too large for shared memory, native below
     }
   }

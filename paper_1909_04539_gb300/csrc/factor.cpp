@@ -703,7 +703,7 @@ bs_status upload_handle(int width, int64_t N, HostPlan* hp, bool has_ul, bool pe
   hd->device_bytes = bytes;
   hd->has_ul = has_ul;
   hd->periodic = periodic;
-  hd->cn_pairs = !periodic && cn_pairs_ok(width, N, b64);
+  hd->cn_pairs = cn_pairs_ok(width, N, b64);
   {
     std::lock_guard<std::mutex> lk(g_handles_mu);
     g_handles.insert(hd);

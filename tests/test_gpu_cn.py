@@ -97,32 +97,62 @@ def test_zero_steps_and_errors(bs):
         bs.cn_steps(f, C, 1, layout="strided")
 
 
+@pytest.mark.parametrize("kind", ["penta", "periodic"])
 @pytest.mark.parametrize("pairs", [0, 1])
-def test_fp64_steps_pairs_and_native_with_edge_values(bs, pairs):
-    """FP64 steps of a non-periodic handle run the explicit side and the solve
-    in FP32 pairs by default (option 0) and natively on request (1).  The
-    batch mixes ordinary systems with ones the pairs' range cannot hold
-    (values near 2^300 and 2^-300, a subnormal entry) and a zero system;
+def test_fp64_steps_pairs_and_native_with_edge_values(bs, pairs, kind):
+    """FP64 steps run the explicit side and the solve in FP32 pairs by
+    default (option 0) and natively on request (1); for a periodic handle
+    the explicit side wraps around and the Sherman-Morrison sum and
+    correction are carried in pairs too.  The batch mixes ordinary systems
+    with ones the pairs' range cannot hold (values near 2^300 and 2^-300, a
+    subnormal entry; 2^80 for the periodic handle, 2^100 for the banded one,
+    in the last or the first row, the rows the periodic explicit side wraps
+    to) and a zero system;
     those lanes compute in FP64.  Every system against the oracle."""
     N, M = 37, 70
-    bands = synth.clamped_hyperdiffusion_bands(N, 0.3)
+    per = kind == "periodic"
+    bands = (synth.periodic_toeplitz_bands(N, (-0.7, 2.4, -0.7)) if per
+             else synth.clamped_hyperdiffusion_bands(N, 0.3))
     rng = np.random.default_rng(11)
     C0 = rng.uniform(-1, 1, (N, M))
     C0[:, 3] *= 2.0 ** 300
     C0[:, 4] *= 2.0 ** -300
     C0[:, 5] = 0.0
     C0[5, 6] = 5e-324
-    C0[:, 40] *= 2.0 ** 90  # inside the pairs' range, near its top
-    f = bs.Factor(bands)
+    C0[:, 40] *= 2.0 ** (70 if per else 90)  # inside the pairs' range, near its top
+    C0[N - 1, 41] = 2.0 ** (80 if per else 100)  # above it, in the last row
+    C0[0, 42] = -(2.0 ** (80 if per else 100))   # above it, in the first row
+    f = bs.Factor(bands, periodic=per)
     bs.set_option(bs.OPT_F64_PAIRS, pairs)
     try:
         X = _run(bs, f, C0, torch.float64, 3)
     finally:
         bs.set_option(bs.OPT_F64_PAIRS, 0)
-    ref = oracle.cn_steps(bands, C0, 3)
+    ref = oracle.cn_steps(bands, C0, 3, periodic=per)
     for j in range(M):
         scale = np.abs(ref[:, j]).max()
         if scale == 0.0:
             assert np.all(X[:, j] == 0.0), j
         else:
             assert np.abs(X[:, j] - ref[:, j]).max() <= 1e-12 * scale, j
+
+
+@pytest.mark.parametrize("N,M,sigma", [(3, 2, 0.3), (4, 1, 1.0), (5, 33, 2.0), (64, 1000, 0.25), (600, 513, 1.0)])
+def test_periodic_pairs_against_native(bs, N, M, sigma):
+    """Periodic diffusion steps in FP32 pairs (the default) and native FP64
+    (BS_OPT_F64_PAIRS = 1): both within the FP64 tolerance of the oracle,
+    and different in their rounding (the pair kernel ran)."""
+    bands = synth.periodic_toeplitz_bands(N, (-sigma, 1 + 2 * sigma, -sigma))
+    C0 = np.random.default_rng(N * M).uniform(-1, 1, (N, M))
+    f = bs.Factor(bands, periodic=True)
+    Xp = _run(bs, f, C0, torch.float64, 3)
+    bs.set_option(bs.OPT_F64_PAIRS, 1)
+    try:
+        Xn = _run(bs, f, C0, torch.float64, 3)
+    finally:
+        bs.set_option(bs.OPT_F64_PAIRS, 0)
+    ref = oracle.cn_steps(bands, C0, 3, periodic=True)
+    parity(Xp, ref, TOL64)
+    parity(Xn, ref, 1e-14)
+    if N * M > 1000:
+        assert not np.array_equal(Xp, Xn)
