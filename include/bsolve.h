@@ -195,8 +195,8 @@ bs_status bs_solve_adjoint(bs_handle h, void* G, bs_dtype dtype, bs_layout layou
  * rejected with BS_EINVAL and a message naming the size -- use bs_band_grad
  * there.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture (a first
- * call on a stream that is being captured returns BS_EINVAL).  All calls
+ * device current); a first call made while its stream is being captured
+ * returns BS_EINVAL.  All calls
  * share the one array and it keeps the last call's contents (every partial is
  * written before it is read, so nothing needs clearing): calls that can
  * overlap on the GPU -- on different streams, or from different host threads
