@@ -53,10 +53,10 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel
     # inside this benchmark's step (launch list of the timed steps), keyed by
     # the hash of its sources
-    "band_grad_f64": {"bytes": 546093056 + 141312, "sha": "64108a499aa00103"},
-    "f64_solve": {"bytes": 470581504 + 431310080, "sha": "9c678e6d1456bd9a"},
-    "adjoint_f64": {"bytes": 464063488 + 427904768, "sha": "9c678e6d1456bd9a"},
-    "refine_solve": {"bytes": 351479808 + 432544000, "sha": "1ea2c7ce3cedb3ca"},
+    "band_grad_f64": {"bytes": 546271744 + 125184, "sha": "7ad65a6ac4c1fb1b"},
+    "f64_solve": {"bytes": 470340608 + 431424768, "sha": "9c678e6d1456bd9a"},
+    "adjoint_f64": {"bytes": 463214848 + 427328768, "sha": "9c678e6d1456bd9a"},
+    "refine_solve": {"bytes": 347321600 + 428031232, "sha": "85b7f7b0d60a8d88"},
 }
 KERNEL_SOURCES = {
     "f64_solve": ["sweep_df.cu", "df_sweep.cuh", "df_math.cuh", "sweep_kernels.cuh", "internal.h", "solve_api.cu"],

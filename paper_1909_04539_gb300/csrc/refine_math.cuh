@@ -317,42 +317,47 @@ __device__ __forceinline__ void resid_term(float& t, float& c, float ch, float c
 // hold the pairs (w, delta) to keep.  (w1, w2), (d1, d2): the two previous
 // rows of each recurrence.  Acc: FRefineCoefs or FRefineRecs (the same
 // values, so the same result).
+//
+// The FP32 sweep forms w = ((p - q2) - q1) with p = fl(s b) and
+// q_k = fl(l_k w_k) (TwoProducts: l_k w_k = q_k + eq_k exactly) and both
+// subtractions error-free (TwoSums: errors e1, e2), so that the residual
+//   rho = s b - w - l1 w1 - l2 w2  (FP64 coefficients s = s_hi + s_lo, ..)
+//       = cc + e1 + e2 - eq1 - eq2 - l1_lo w1 - l2_lo w2,
+// cc = s b - p to FP64 accuracy: every term is already of the size of the
+// residual, so plain FP32 sums carry it to ~2^-24 of itself.
 template <int BW, int U, typename Acc>
 __device__ __forceinline__ void frefine_pass1(const Acc& cf, int i0, int n, const float (&b)[U], float (&w)[U],
                                               float (&d)[U], float& w1, float& w2, float& d1, float& d2) {
   FRow1<BW> c[U];
 #pragma unroll
   for (int u = 0; u < U; u++) c[u] = frow1<BW>(cf, (u < n) ? i0 + u : i0);
-  float wp1[U], wp2[U], p[U];
-  // forward sweep of w (the chain); p = fl(s b), the first term of both the
-  // sweep and the residual
-#pragma unroll
-  for (int u = 0; u < U; u++) {
-    wp1[u] = w1;
-    wp2[u] = w2;
-    p[u] = __fmul_rn(b[u], c[u].s);
-    if (u < n) {
-      float x = p[u];
-      if (BW == 2) x = fmaf(-c[u].l2, w2, x);
-      x = fmaf(-c[u].l1, w1, x);
-      w[u] = x;
-      w2 = w1;
-      w1 = x;
-    }
-  }
-  // residuals of the rows (independent of each other)
+  // forward sweep of w (the chain) with the rounding errors of its
+  // products and differences kept as the residual's terms
   float rho[U];
 #pragma unroll
   for (int u = 0; u < U; u++) {
     rho[u] = 0.f;
+    w[u] = 0.f;
     if (u < n) {
-      float cc = fmaf(c[u].sl, b[u], fmaf(c[u].s, b[u], -p[u]));  // s b = p + cc to FP64 accuracy
-      float t, e;
-      two_diff(p[u], w[u], t, e);
-      cc = __fadd_rn(cc, e);
-      resid_term(t, cc, c[u].l1, c[u].l1l, wp1[u]);
-      if (BW == 2) resid_term(t, cc, c[u].l2, c[u].l2l, wp2[u]);
-      rho[u] = __fadd_rn(t, cc);
+      const float p = __fmul_rn(b[u], c[u].s);
+      float r = fmaf(c[u].sl, b[u], fmaf(c[u].s, b[u], -p));  // s b = p + r to FP64 accuracy
+      float x = p, e;
+      if (BW == 2) {
+        const float q2 = __fmul_rn(c[u].l2, w2);
+        r = __fsub_rn(r, fmaf(c[u].l2, w2, -q2));
+        r = fmaf(-c[u].l2l, w2, r);
+        two_diff(p, q2, x, e);
+        r = __fadd_rn(r, e);
+      }
+      const float q1 = __fmul_rn(c[u].l1, w1);
+      r = __fsub_rn(r, fmaf(c[u].l1, w1, -q1));
+      r = fmaf(-c[u].l1l, w1, r);
+      float y;
+      two_diff(x, q1, y, e);
+      rho[u] = __fadd_rn(r, e);
+      w[u] = y;
+      w2 = w1;
+      w1 = y;
     }
   }
   // forward sweep of the correction
@@ -371,6 +376,10 @@ __device__ __forceinline__ void frefine_pass1(const Acc& cf, int i0, int n, cons
 
 // Rows top, top-1, .., top-n+1 of the second pass: (w, dl) the kept pairs;
 // returns the FP64 solution in X.  (x1, x2), (e1, e2): the two rows below.
+// As in pass 1 the FP32 sweep x = ((w - q2) - q1) + dl, q_k = fl(u_k x_k),
+// takes its differences and its sum error-free (errors g1, g2, g3), so that
+// the residual of U x = w + dl (U has a unit diagonal) is
+//   sigma = g1 + g2 + g3 - eq1 - eq2 - u1_lo x1 - u2_lo x2.
 template <int BW, int U, typename Acc>
 __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, const float (&w)[U],
                                               const float (&dl)[U], double (&X)[U], float& x1, float& x2,
@@ -378,33 +387,32 @@ __device__ __forceinline__ void frefine_pass2(const Acc& cf, int top, int n, con
   FRow2<BW> c[U];
 #pragma unroll
   for (int u = 0; u < U; u++) c[u] = frow2<BW>(cf, (u < n) ? top - u : top);
-  float x[U], xn1[U], xn2[U];
-  // backward sweep of x on the rounded pair (the chain)
+  float x[U], sig[U];
+  // backward sweep of x (the chain) with its residual terms
 #pragma unroll
   for (int u = 0; u < U; u++) {
-    xn1[u] = x1;
-    xn2[u] = x2;
     x[u] = 1.f;
+    sig[u] = 0.f;
     if (u < n) {
-      float v = __fadd_rn(w[u], dl[u]);
-      if (BW == 2) v = fmaf(-c[u].u2, x2, v);
-      v = fmaf(-c[u].u1, x1, v);
+      float a = w[u], r = 0.f, g;
+      if (BW == 2) {
+        const float q2 = __fmul_rn(c[u].u2, x2);
+        r = fmaf(-c[u].u2l, x2, -fmaf(c[u].u2, x2, -q2));
+        two_diff(w[u], q2, a, g);
+        r = __fadd_rn(r, g);
+      }
+      const float q1 = __fmul_rn(c[u].u1, x1);
+      r = __fsub_rn(r, fmaf(c[u].u1, x1, -q1));
+      r = fmaf(-c[u].u1l, x1, r);
+      float a2;
+      two_diff(a, q1, a2, g);
+      r = __fadd_rn(r, g);
+      float v;
+      two_diff(a2, -dl[u], v, g);  // a2 + dl
+      sig[u] = __fadd_rn(r, g);
       x[u] = v;
       x2 = x1;
       x1 = v;
-    }
-  }
-  // residuals sigma = (w + dl) - U x of the rows (U has a unit diagonal)
-  float sig[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) {
-    sig[u] = 0.f;
-    if (u < n) {
-      float t, cc;
-      two_diff(w[u], x[u], t, cc);
-      resid_term(t, cc, c[u].u1, c[u].u1l, xn1[u]);
-      if (BW == 2) resid_term(t, cc, c[u].u2, c[u].u2l, xn2[u]);
-      sig[u] = __fadd_rn(__fadd_rn(t, cc), dl[u]);
     }
   }
   // backward sweep of the correction
