@@ -38,6 +38,19 @@ static void sweep_impl(const double* s, const double* l1, const double* l2, cons
   delete[] w;
 }
 
+// s + (ch + cl) y in pairs, unnormalised, in the operation order of the
+// periodic pair sweeps (TwoProduct of the high parts plus both cross terms,
+// TwoSum of the high parts)
+static Pair muladd(Pair s, float ch, float cl, Pair y) {
+  const float p = mul(ch, y.h);
+  float e = fma_(ch, y.h, -p);
+  e = fma_(ch, y.l, e);
+  e = fma_(cl, y.h, e);
+  float h, t;
+  two_sum(s.h, p, h, t);
+  return Pair{h, add(s.l, add(t, e))};
+}
+
 extern "C" {
 
 // x[n] -> h[n], l[n], ok[n]
@@ -84,6 +97,45 @@ void df_two_sum(const float* a, const float* b, float* s, float* t, long n) {
 void df_sweep(const double* s, const double* l1, const double* l2, const double* t, const double* u1,
               const double* u2, int has_s, int has_t, int bw, long N, const double* f, double* x) {
   sweep_impl(s, l1, l2, t, u1, u2, has_s, has_t, bw, N, f, x);
+}
+
+// One system of a periodic tridiagonal solve in pair arithmetic, as the
+// periodic pair sweeps run it (Sherman-Morrison, Sec. 3.3): the tridiagonal
+// recurrences of the corner-free matrix (coefficients as for df_sweep, bw 1),
+// sigma' = sum pw'_i f_i accumulated in pairs during the forward sweep over
+// the rows outside [per_lo, per_hi), and x_i = y_i - sigma' pc'_i formed in
+// pairs after each backward row there, the recurrence keeping y.  pw, pc:
+// the scaled weights as (hi, lo) float pairs (4 N floats: pw hi, pw lo, pc
+// hi, pc lo per row).
+void df_sweep_periodic(const double* s, const double* l1, const double* t, const double* u1, int has_s, int has_t,
+                       const float* pq, long per_lo, long per_hi, long N, const double* f, double* x) {
+  auto P = [](double c) {
+    const float h = (float)c;
+    return Pair{h, (float)(c - (double)h)};
+  };
+  Pair* w = new Pair[N];
+  const Pair z{0.f, 0.f};
+  Pair sig{0.f, 0.f};
+  for (long i = 0; i < N; i++) {
+    bool ok = true;
+    const Pair F = split(f[i], ok);
+    if (i < per_lo || i >= per_hi) sig = muladd(sig, pq[4 * i], pq[4 * i + 1], F);
+    const Pair Y1 = i >= 1 ? w[i - 1] : z;
+    w[i] = has_s ? rec_step<true, 1>(P(s[i]), F, P(l1[i]), Y1, z, z)
+                 : rec_step<false, 1>(Pair{1.f, 0.f}, F, P(l1[i]), Y1, z, z);
+  }
+  Pair x1 = z;
+  for (long i = N - 1; i >= 0; i--) {
+    Pair y = has_t ? rec_step<true, 1>(P(t[i]), w[i], P(u1[i]), x1, z, z)
+                   : rec_step<false, 1>(Pair{1.f, 0.f}, w[i], P(u1[i]), x1, z, z);
+    x1 = y;
+    if (i < per_lo || i >= per_hi) {
+      const Pair c = muladd(y, -pq[4 * i + 2], -pq[4 * i + 3], sig);
+      fast_two_sum(c.h, c.l, y.h, y.l);
+    }
+    x[i] = combine(y.h, y.l);
+  }
+  delete[] w;
 }
 
 }  // extern "C"

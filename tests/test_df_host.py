@@ -10,7 +10,11 @@ single precision, no FMA contraction) through tests/host/df_host.cpp:
 - TwoSum: exact for arbitrary operands (checked in exact rational arithmetic);
 - the two sweeps run as the kernel runs them, on tridiagonal and
   pentadiagonal systems, primal and adjoint, against the FP64 oracle per
-  system at 1e-13 (the library's tolerance for this path is 1e-12).
+  system at 1e-13 (the library's tolerance for this path is 1e-12);
+- the periodic (cyclic) tridiagonal solve as the periodic pair sweeps run
+  it -- the Sherman-Morrison sum and correction (Sec. 3.3) in pairs with the
+  weights scaled by a power of two -- primal and adjoint, against the
+  oracle's periodic solve per system at 1e-13.
 """
 import ctypes
 import os
@@ -51,6 +55,8 @@ def lib():
     L.df_combine_fast.argtypes = [P(np.float32), P(np.float32), P(np.float64), P(np.int32), ctypes.c_long]
     d = P(np.float64)
     L.df_sweep.argtypes = [d, d, d, d, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, d, d]
+    L.df_sweep_periodic.argtypes = [d, d, d, d, ctypes.c_int, ctypes.c_int, P(np.float32), ctypes.c_long,
+                                    ctypes.c_long, ctypes.c_long, d, d]
     return L
 
 
@@ -257,3 +263,79 @@ def test_pair_sweep_structured_matrices(lib, kind):
     tol = 1e-12 if kind == "stiff" else 1e-13
     assert sys_rel_err(X, oracle.solve(bands, B)) < tol
     assert sys_rel_err(G, oracle.solve_adjoint(bands, B)) < tol
+
+
+def _periodic_setup(bands):
+    """The corner-free matrix A' = A - u v^T of a cyclic tridiagonal A
+    (gamma = -b_1, u = (gamma, 0, .., 0, c_N), v = (1, 0, .., 0, a_1 /
+    gamma), Sec. 3.3), its recurrence coefficients, and the Sherman-Morrison
+    weights of the primal and adjoint solves: z = A'^{-1} u, q = A'^{-T} v,
+    primal (pw, pc) = (q, z / (1 + v.z)), adjoint (z, q / (1 + v.z));
+    entries below 2^-60 max / N dropped, the middle rows where both vanish
+    recorded as [lo, hi)."""
+    a, b, c = (np.asarray(r, dtype=np.float64) for r in bands)
+    N = a.size
+    gam = -b[0]
+    v_last = a[0] / gam
+    mod = np.stack([np.where(np.arange(N) > 0, a, 0.0), b.copy(), np.where(np.arange(N) < N - 1, c, 0.0)])
+    mod[1, 0] = b[0] - gam
+    mod[1, N - 1] = b[N - 1] - c[N - 1] * v_last
+    u = np.zeros(N)
+    u[0], u[N - 1] = gam, c[N - 1]
+    v = np.zeros(N)
+    v[0], v[N - 1] = 1.0, v_last
+    z = oracle.solve(mod, u[:, None])[:, 0]
+    q = oracle.solve_adjoint(mod, v[:, None])[:, 0]
+    den = 1.0 + z[0] + v_last * z[N - 1]
+    tq, tz = np.abs(q).max() * 2.0 ** -60 / N, np.abs(z).max() * 2.0 ** -60 / N
+    keep = (np.abs(q) > tq) | (np.abs(z) > tz)
+    q, z = np.where(keep, q, 0.0), np.where(keep, z, 0.0)
+    lo = max([i + 1 for i in range(N // 2) if keep[i]], default=0)
+    hi = min([i for i in range(N // 2, N) if keep[i]], default=N)
+    lo = min(lo, hi)
+    prim, adj = _plans(mod)
+    return (prim, (q, z / den)), (adj, (z, q / den)), lo, hi
+
+
+def _scaled_pairs(pw, pc):
+    """(pw', pc') = (2^k pw, 2^-k pc), max |pw'| in [1, 2), as (hi, lo) float
+    pairs per row: 4 N floats."""
+    k = 1 - int(np.frexp(np.abs(pw).max())[1])
+    w, cc = np.ldexp(pw, k), np.ldexp(pc, -k)
+    wh, ch = w.astype(np.float32), cc.astype(np.float32)
+    wl, cl = (w - wh).astype(np.float32), (cc - ch).astype(np.float32)
+    return np.ascontiguousarray(np.stack([wh, wl, ch, cl], axis=1).ravel())
+
+
+def _periodic_sweep(L, coefs, weights, lo, hi, has_s, has_t, f):
+    s, l1, _, t, u1, _ = (np.ascontiguousarray(c, np.float64) for c in coefs)
+    x = np.empty(f.size)
+    L.df_sweep_periodic(s, l1, t, u1, int(has_s), int(has_t), _scaled_pairs(*weights), lo, hi, f.size,
+                        np.ascontiguousarray(f), x)
+    return x
+
+
+PERIODIC = {
+    "random_N3": lambda: synth.random_periodic_bands(3, np.random.default_rng(1)),
+    "random_N5": lambda: synth.random_periodic_bands(5, np.random.default_rng(2)),
+    "random_N37": lambda: synth.random_periodic_bands(37, np.random.default_rng(3)),
+    "random_N300": lambda: synth.random_periodic_bands(300, np.random.default_rng(4)),
+    "diffusion_N1024": lambda: synth.periodic_toeplitz_bands(1024, (-0.5, 2.0, -0.5)),
+    "spline_N1024": lambda: synth.periodic_toeplitz_bands(1024, (1 / 6, 4 / 6, 1 / 6)),
+    "weak_N512": lambda: synth.periodic_toeplitz_bands(512, (-1.0, 2.05, -1.0)),
+    "nonsymmetric_N64": lambda: synth.periodic_toeplitz_bands(64, (0.3, 2.0, -0.6)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(PERIODIC))
+def test_periodic_pair_sweeps_match_oracle(lib, case):
+    bands = PERIODIC[case]()
+    N = bands.shape[1]
+    rng = np.random.default_rng(N)
+    M = 16
+    B = rng.standard_normal((N, M)) * np.ldexp(1.0, rng.integers(-30, 30, M))
+    (prim, pw), (adj, aw), lo, hi = _periodic_setup(bands)
+    X = np.stack([_periodic_sweep(lib, prim, pw, lo, hi, True, False, B[:, j]) for j in range(M)], axis=1)
+    G = np.stack([_periodic_sweep(lib, adj, aw, lo, hi, False, True, B[:, j]) for j in range(M)], axis=1)
+    assert sys_rel_err(X, oracle.periodic_tri_solve_bands(bands, B)) < 1e-13
+    assert sys_rel_err(G, oracle.periodic_solve_adjoint(bands, B)) < 1e-13
