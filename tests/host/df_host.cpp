@@ -138,4 +138,73 @@ void df_sweep_periodic(const double* s, const double* l1, const double* t, const
   delete[] w;
 }
 
+// One Crank-Nicolson step C <- A^{-1} (2I - A) C of one system as the fused
+// pair kernel runs it: the explicit side f_i = 2 C_i - sum_k A(i, i+k-h)
+// C_{i+k-h} in pairs (each band entry as a (hi, lo) pair, each product a
+// TwoProduct of the high parts plus the cross terms, the sum TwoSums of the
+// high parts with the rest in the low part, renormalised), then the pair
+// solve of A (plan coefficients as for df_sweep).  bands: width x N doubles
+// (row k = entries A(i, i+k-h), zero outside the matrix unless periodic);
+// periodic (width 3): the window wraps around and pq, per_lo, per_hi carry
+// the Sherman-Morrison weights as for df_sweep_periodic.
+void df_cn_step(const double* bands, int width, int periodic, const double* s, const double* l1, const double* l2,
+                const double* u1, const double* u2, const float* pq, long per_lo, long per_hi, long N,
+                const double* c, double* x) {
+  auto P = [](double v) {
+    const float h = (float)v;
+    return Pair{h, (float)(v - (double)h)};
+  };
+  const int h = width / 2;
+  const int bw = h;
+  Pair* y = new Pair[N];
+  Pair* w = new Pair[N];
+  for (long i = 0; i < N; i++) {
+    bool ok = true;
+    y[i] = split(c[i], ok);
+  }
+  const Pair z{0.f, 0.f};
+  Pair sig{0.f, 0.f};
+  for (long i = 0; i < N; i++) {
+    float sh = mul(2.f, y[i].h), lo = mul(2.f, y[i].l);
+    for (int k = 0; k < width; k++) {
+      long j = i + k - h;
+      Pair zz = z;
+      if (j >= 0 && j < N)
+        zz = y[j];
+      else if (periodic)
+        zz = y[(j + N) % N];
+      const Pair cp = P(bands[(long)k * N + i]);
+      const float p = mul(cp.h, zz.h);
+      float e = fma_(cp.h, zz.h, -p);
+      e = fma_(cp.h, zz.l, e);
+      e = fma_(cp.l, zz.h, e);
+      float t;
+      two_sum(sh, -p, sh, t);
+      lo = add(lo, sub(t, e));
+    }
+    Pair f;
+    fast_two_sum(sh, lo, f.h, f.l);
+    if (periodic && (i < per_lo || i >= per_hi)) sig = muladd(sig, pq[4 * i], pq[4 * i + 1], f);
+    const Pair Y1 = i >= 1 ? w[i - 1] : z, Y2 = i >= 2 ? w[i - 2] : z;
+    const Pair B2 = bw == 2 ? P(l2[i]) : z;
+    w[i] = bw == 2 ? rec_step<true, 2>(P(s[i]), f, P(l1[i]), Y1, B2, Y2)
+                   : rec_step<true, 1>(P(s[i]), f, P(l1[i]), Y1, B2, Y2);
+  }
+  Pair x1 = z, x2 = z;
+  for (long i = N - 1; i >= 0; i--) {
+    const Pair B2 = bw == 2 ? P(u2[i]) : z;
+    Pair v = bw == 2 ? rec_step<false, 2>(Pair{1.f, 0.f}, w[i], P(u1[i]), x1, B2, x2)
+                     : rec_step<false, 1>(Pair{1.f, 0.f}, w[i], P(u1[i]), x1, B2, x2);
+    x2 = x1;
+    x1 = v;
+    if (periodic && (i < per_lo || i >= per_hi)) {
+      const Pair cc = muladd(v, -pq[4 * i + 2], -pq[4 * i + 3], sig);
+      fast_two_sum(cc.h, cc.l, v.h, v.l);
+    }
+    x[i] = combine(v.h, v.l);
+  }
+  delete[] y;
+  delete[] w;
+}
+
 }  // extern "C"

@@ -14,7 +14,11 @@ single precision, no FMA contraction) through tests/host/df_host.cpp:
 - the periodic (cyclic) tridiagonal solve as the periodic pair sweeps run
   it -- the Sherman-Morrison sum and correction (Sec. 3.3) in pairs with the
   weights scaled by a power of two -- primal and adjoint, against the
-  oracle's periodic solve per system at 1e-13.
+  oracle's periodic solve per system at 1e-13;
+- Crank-Nicolson steps as the fused pair kernel runs them (the explicit
+  side 2I - A formed in pairs from the rows, then the pair solve; periodic:
+  wrapped and with the Sherman-Morrison terms), banded tri / penta and
+  cyclic tri, against the oracle's steps per system at 1e-13.
 """
 import ctypes
 import os
@@ -57,6 +61,8 @@ def lib():
     L.df_sweep.argtypes = [d, d, d, d, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, d, d]
     L.df_sweep_periodic.argtypes = [d, d, d, d, ctypes.c_int, ctypes.c_int, P(np.float32), ctypes.c_long,
                                     ctypes.c_long, ctypes.c_long, d, d]
+    L.df_cn_step.argtypes = [d, ctypes.c_int, ctypes.c_int, d, d, d, d, d, P(np.float32), ctypes.c_long,
+                             ctypes.c_long, ctypes.c_long, d, d]
     return L
 
 
@@ -339,3 +345,48 @@ def test_periodic_pair_sweeps_match_oracle(lib, case):
     G = np.stack([_periodic_sweep(lib, adj, aw, lo, hi, False, True, B[:, j]) for j in range(M)], axis=1)
     assert sys_rel_err(X, oracle.periodic_tri_solve_bands(bands, B)) < 1e-13
     assert sys_rel_err(G, oracle.periodic_solve_adjoint(bands, B)) < 1e-13
+
+
+def _cn_pairs(L, bands, periodic, C0, steps):
+    """`steps` Crank-Nicolson steps of every column of C0 in pair arithmetic."""
+    width, N = bands.shape
+    b = np.ascontiguousarray(bands, dtype=np.float64)
+    if periodic:
+        (prim, pw), _, lo, hi = _periodic_setup(bands)
+        pq = _scaled_pairs(*pw)
+    else:
+        prim, _ = _plans(bands)
+        pq, lo, hi = np.zeros(4 * N, np.float32), 0, N
+    s, l1, l2, _, u1, u2 = (np.ascontiguousarray(c, np.float64) for c in prim)
+    C = np.array(C0, dtype=np.float64)
+    for _ in range(steps):
+        for j in range(C.shape[1]):
+            x = np.empty(N)
+            L.df_cn_step(b, width, int(periodic), s, l1, l2, u1, u2, pq, lo, hi, N, np.ascontiguousarray(C[:, j]), x)
+            C[:, j] = x
+    return C
+
+
+CN = {
+    "hyperdiffusion_N512": (lambda: synth.toeplitz_bands(512, (0.1, -0.4, 1.6, -0.4, 0.1)), False),
+    "clamped_hyper_N64": (lambda: synth.clamped_hyperdiffusion_bands(64, 0.3), False),
+    "random_tri_N100": (lambda: synth.random_tri_bands(100, np.random.default_rng(7)), False),
+    "periodic_diffusion_N1024": (lambda: synth.periodic_toeplitz_bands(1024, (-0.5, 2.0, -0.5)), True),
+    "periodic_diffusion_N3": (lambda: synth.periodic_toeplitz_bands(3, (-0.3, 1.6, -0.3)), True),
+    "periodic_random_N40": (lambda: synth.random_periodic_bands(40, np.random.default_rng(8)), True),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CN))
+def test_cn_pair_steps_match_oracle(lib, case):
+    make, periodic = CN[case]
+    bands = make()
+    N = bands.shape[1]
+    C0 = np.random.default_rng(N + 1).uniform(-1, 1, (N, 6))
+    got = _cn_pairs(lib, bands, periodic, C0, 3)
+    ref = oracle.cn_steps(bands, C0, 3, periodic=periodic)
+    # per system, relative to its starting values: the steps damp most
+    # modes (the cyclic N = 3 case keeps only the mean), so the result can
+    # be far smaller than the values whose rounding it carries
+    err = np.abs(got - ref).max(axis=0) / np.abs(C0).max(axis=0)
+    assert err.max() < 1e-13, err.max()
