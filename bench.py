@@ -87,7 +87,7 @@ def ncu_traffic(path_name: str):
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "MEASURED_PEAKS.json (driver-measured copy bandwidth)"
+            return json.load(f), "MEASURED_PEAKS.json (measured copy bandwidth of this GPU model)"
     except OSError:
         return {"hbm_gbs": 6800.0}, "profiling-recipe fallback 6.8 TB/s"
 
